@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Benchmark: energy + full gradient evaluations per second on GB300.
+
+Workload (default): the transverse-field Ising chain n=20, J=1, h_i ~ U[0.5,1.5], with the
+L=6 RY/RZ + CZ brick-wall ansatz and a batch of B=64 parameter sets; one step = one
+call of the whole hot path (gate tables, the batched causal-cone kernel with its adjoint,
+and the FP64 term/gradient reductions) for all 64 sets. Synthetic, seeded inputs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tlq|reference]
+
+``--impl reference`` times the CPU oracle (complex128 statevector with its own adjoint)
+on the host cores over a bounded sample of the same workload. Under torchrun each rank
+runs an independent replica (no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "expectation+gradient evals/sec"
+UNIT = "grad-evals/s"
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="tlq", choices=["tlq", "reference"])
+    ap.add_argument("--workload", default="tfim_n20_L6_B64")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2112_10239_gb300 import workloads as W
+    if name == "tfim_n20_L6_B64":
+        return W.tfim_n20_L6_B64()
+    if name == "tfim_n500_L4_B256":
+        return W.tfim_n500_L4_B256()
+    if name == "tfim_n8_L2_B1":
+        return W.tfim_n8_L2()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def algorithmic_flops(B_mod, ctx, c, h, prob, grad=True):
+    """Algorithmic FP32 flops of one batched cone launch (forward, measurement, adjoint).
+
+    Per cone of true width w (A = 2^w amplitudes), with R rotations, D diagonal layers and
+    Pd parametrised diagonal gates in the cone:
+      forward   A * (6 R + 6 D)       real 2x2 rotation on (re, im): 6 flop/amp; one complex
+                                      multiply per amplitude per diagonal layer
+      measure   A * 8                 <psi|P|psi> and lambda = P psi
+      adjoint   A * (4 R + 12 R + 12 D + 3 D + Pd)
+                                      Im<lam|G|psi> (4/amp), un-apply on psi and lam (2 x 6),
+                                      diagonal un-apply (2 x 6), Im(conj(lam) psi) (3) and one
+                                      signed add per parametrised diagonal gate
+    Padding to the kernel's minimum width is not counted.
+    """
+    n_terms = len(prob.terms)
+    _, lo, w, _ = B_mod.tlq_plan_info(ctx.h, c.h, h.h, n_terms)
+    nrot, ndiag, npdiag, _ = B_mod.tlq_plan_cone_stats(ctx.h, c.h, h.h, n_terms)
+    A = np.power(2.0, w.astype(np.float64))
+    f = A * (6 * nrot + 6 * ndiag + 8)
+    if grad:
+        f += A * (16 * nrot + 15 * ndiag + npdiag)
+    return float(np.sum(f)) * prob.B
+
+
+def run_reference(args, rank):
+    """CPU oracle arm: each step evaluates energy + gradient of a sample of the workload's
+    parameter sets with the complex128 statevector and its adjoint."""
+    if rank != 0:
+        return
+    from oracle import dense
+    from oracle.dense import omp_threads
+    prob = workload(args.workload)
+    sample = 2 if prob.n >= 16 else prob.B
+    sets = [prob.theta[i % prob.B] for i in range(sample)]
+
+    def step():
+        for th in sets:
+            dense.grad_adjoint(prob.n, prob.gates, prob.terms, th, prob.n_params)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = sample * args.steps / dt
+    cores = omp_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": prob.n, "L": prob.meta.get("L"), "B": prob.B,
+                   "sample_sets_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} of the {prob.B} parameter sets per step, dense 2^{prob.n} "
+                                   f"complex128 statevector + adjoint"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(prob, budget_s=12.0):
+    """The oracle as it stands on this host's cores over a bounded sample of the workload."""
+    from oracle import dense
+    from oracle.dense import omp_threads
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        th = prob.theta[done % prob.B]
+        dense.grad_adjoint(prob.n, prob.gates, prob.terms, th, prob.n_params)
+        done += 1
+        if time.perf_counter() - t0 > budget_s or done >= prob.B:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+            "sample": f"{done} parameter sets of the workload (dense 2^{prob.n} complex128 statevector "
+                      f"+ adjoint), {dt:.1f} s wall"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from __graft_entry__ import build
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+    from paper_2112_10239_gb300 import binding as B
+
+    prob = workload(args.workload)
+    ctx = B.Context(device=local)
+    c, h = ctx.problem(prob)
+    Bsz, P = prob.theta.shape
+    dev = torch.device("cuda", local)
+    theta_d = torch.tensor(prob.theta, dtype=torch.float64, device=dev)
+    E_d = torch.empty(Bsz, dtype=torch.float64, device=dev)
+    G_d = torch.empty(Bsz, P, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    B.tlq_profile_enable(ctx.h, True)
+
+    def step():
+        B.tlq_expectation_grad_dev(ctx.h, c.h, h.h, theta_d.data_ptr(), Bsz, B.TLQ_FP32, E_d.data_ptr(),
+                                   G_d.data_ptr(), stream.cuda_stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    step_ms, kern_ms, launches = [], [], 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()                      # evict L2 between timed steps (untimed)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        ms, nl = B.tlq_profile_last(ctx.h)
+        kern_ms.append(ms)
+        launches += nl
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * Bsz * args.steps / total_s
+
+    # end to end through the host-pointer API (H2D of theta and D2H of energy + gradient inside)
+    theta_h = np.ascontiguousarray(prob.theta)
+    for _ in range(3):
+        B.tlq_expectation_grad(ctx.h, c.h, h.h, theta_h)
+    e2e_t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        E_h, G_h = B.tlq_expectation_grad(ctx.h, c.h, h.h, theta_h)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = world * Bsz * len(e2e_t) / sum(e2e_t)
+
+    # roofline of the dominant kernel (the batched cone kernel), ALU-bound FP32
+    peaks, peak_kind = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flops = algorithmic_flops(B, ctx, c, h, prob, grad=True)
+    kern_mean_ms = float(np.mean(kern_ms))
+    achieved = flops / (kern_mean_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "cone_kernel<float,grad> (batched causal cones + adjoint)",
+                "kernel_ms": kern_mean_ms, "algorithmic_flops": flops,
+                "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x {sm_max:.0f} MHz"}
+
+    if rank == 0:
+        cpu = cpu_baseline(prob)
+        sm = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": prob.n, "L": prob.meta.get("L"), "B": Bsz,
+                       "n_params": P, "terms": len(prob.terms), "l2": "flushed: 256 MiB write between timed steps",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "latency_ms": {"p50": sm[len(sm) // 2], "p99": sm[min(len(sm) - 1, int(math.ceil(0.99 * len(sm))) - 1)],
+                           "per": f"batch of {Bsz} parameter sets"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(theta_h.nbytes),
+                    "d2h_bytes_per_step": int(E_h.nbytes + G_h.nbytes)},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "peak_source": peak_kind,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    c.close()
+    h.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * tlq.h -- C-ABI of the GB300 expectation-value / gradient engine.
+ *
+ * What the library computes (TensorLy-Quantum, arXiv:2112.10239):
+ *   Sec. 2: circuits are built from pre-defined gates, operators and states;
+ *   Sec. 3: the forward pass is the expectation value <H> of a circuit's output
+ *           state against a Hamiltonian given as a sum of local Pauli terms (the
+ *           transverse-field Ising model there), and the backward pass is the full
+ *           gradient nabla <H> with respect to every rotation angle;
+ *   Sec. 4: "causality-simplified contraction" (listed there as future work) --
+ *           for nearest-neighbour circuits each term is contracted over its causal
+ *           cone only, so the cost does not grow with the qubit count.
+ *
+ * Conventions fixed by this library (the paper states none of them):
+ *   - the initial state is |0...0>; qubit q is bit q of the amplitude index;
+ *   - RX(a) = exp(-i a X/2), RY(a) = exp(-i a Y/2) = [[c,-s],[s,c]],
+ *     RZ(a) = exp(-i a Z/2), RZZ(a) = exp(-i a Z(x)Z/2), CZ = diag(1,1,1,-1),
+ *     with c = cos(a/2), s = sin(a/2);
+ *   - a gate takes theta[param] when param >= 0, else its fixed `angle`;
+ *   - gradients are dE/dtheta_p summed over every gate carrying parameter p.
+ *
+ * General rules:
+ *   - Every call returns a tlq_status; nothing throws across the ABI and nothing
+ *     aborts the process. On failure tlq_last_error() gives a message
+ *     (thread-local; valid until the thread's next failing call).
+ *   - Handles are owned by the library from *_create until *_destroy. Gate and term
+ *     arrays are copied at create time; the caller keeps ownership of its arrays.
+ *   - theta/energy/grad buffers are borrowed for the duration of a synchronous call,
+ *     or, for tlq_submit, until tlq_poll returns TLQ_OK for that ticket.
+ *   - Angles are FP64 on the boundary; energies and gradients are FP64.
+ *   - A context and its handles may be used from one thread at a time, except
+ *     tlq_submit / tlq_poll, which are thread-safe.
+ */
+#ifndef TLQ_H
+#define TLQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tlq_ctx_s* tlq_ctx;
+typedef struct tlq_circuit_s* tlq_circuit;
+typedef struct tlq_ham_s* tlq_ham;
+typedef uint64_t tlq_ticket;
+
+typedef enum {
+    TLQ_OK = 0,
+    TLQ_EINVAL = 1,       /* malformed argument or descriptor */
+    TLQ_ENOMEM = 2,       /* device memory budget or allocation exceeded */
+    TLQ_EAGAIN = 3,       /* tlq_poll: request still pending */
+    TLQ_ETIMEOUT = 4,     /* tlq_poll: waited timeout_us without completion */
+    TLQ_ECUDA = 5,        /* a CUDA runtime call failed */
+    TLQ_EKERNEL = 6,      /* a kernel reported an internal error word */
+    TLQ_EUNSUPPORTED = 7  /* valid request outside what the library implements */
+} tlq_status;
+
+typedef enum {
+    TLQ_FP32 = 0,      /* complex64 states, FP32 arithmetic; FP64 gate tables' source
+                          angles and FP64 reductions across terms */
+    TLQ_MIXED_TC = 1,  /* reserved for tensor-core fused gate blocks; currently runs the
+                          FP32 path (same accuracy contract) */
+    TLQ_FP64_REF = 2   /* complex128 correctness mode of the same kernels (slow) */
+} tlq_precision;
+
+typedef enum { TLQ_RX = 0, TLQ_RY = 1, TLQ_RZ = 2, TLQ_RZZ = 3, TLQ_CZ = 4 } tlq_gate_kind;
+
+/* One gate. q1 is the second qubit of RZZ/CZ (ignored, conventionally -1, for
+ * one-qubit gates). param = -1 selects the fixed `angle` (radians); CZ ignores both. */
+typedef struct {
+    int32_t kind;     /* tlq_gate_kind */
+    int32_t q0, q1;
+    int32_t param;
+    double angle;
+} tlq_gate;
+
+/* One Pauli term coeff * P, P = prod_k letter_k acting on sites[k].
+ * `paulis` holds nsites letters from {'X','Y','Z'} (no terminator needed). */
+typedef struct {
+    double coeff;
+    int32_t nsites;
+    const int32_t* sites;
+    const char* paulis;
+} tlq_term;
+
+typedef struct {
+    int device;              /* CUDA device ordinal; -1 = host-only context (validation and
+                                planning only; every compute call returns TLQ_EUNSUPPORTED) */
+    size_t mem_budget;       /* bytes of device memory the context may hold (0 = 80% of free) */
+    int max_slots;           /* tlq_submit: requests admitted concurrently (0 = 64) */
+    tlq_precision default_prec;
+    int fuse_k;              /* reserved (fused block size); 0 = default */
+} tlq_config;
+
+/* Create a context on cfg->device: one CUDA stream, a device workspace and, for the
+ * serving calls, a scheduler thread started on first tlq_submit. cfg may be NULL
+ * (device 0, defaults). *out is set only on TLQ_OK. */
+tlq_status tlq_init(const tlq_config* cfg, tlq_ctx* out);
+
+/* Wait for all submitted work, stop the scheduler and free every device resource of
+ * the context. Circuits and Hamiltonians created on it must not be used afterwards
+ * (destroy them first; tlq_destroy also frees any that are left). NULL is a no-op. */
+tlq_status tlq_destroy(tlq_ctx ctx);
+
+/* Validate and copy a gate list (Sec. 2: circuits composed of gates).
+ * EINVAL when: n_qubits < 1 or > 2^20; a qubit is out of [0, n_qubits); q0 == q1 for a
+ * two-qubit gate; an unknown kind; param >= n_params or param < -1; n_gates < 0.
+ * The execution path (per-term light cones for nearest-neighbour circuits, a dense
+ * statevector otherwise) is chosen when the circuit is first paired with a Hamiltonian. */
+tlq_status tlq_circuit_create(tlq_ctx ctx, int32_t n_qubits, const tlq_gate* gates, int32_t n_gates,
+                              int32_t n_params, tlq_circuit* out);
+tlq_status tlq_circuit_destroy(tlq_circuit c);
+
+/* Validate and copy a Pauli-sum Hamiltonian (Sec. 3: H as a sum of local terms, never a
+ * dense matrix). EINVAL when: a site is out of range; a letter is not X/Y/Z; a site
+ * repeats inside one term; nsites < 1; n_terms < 1. */
+tlq_status tlq_hamiltonian_create(tlq_ctx ctx, int32_t n_qubits, const tlq_term* terms, int32_t n_terms,
+                                  tlq_ham* out);
+tlq_status tlq_hamiltonian_destroy(tlq_ham h);
+
+/* Forward pass (Sec. 3, <H>): energy[b] = <psi(theta_b)| H |psi(theta_b)> for b < B.
+ * theta: host, row-major [B][n_params] FP64. energy: host [B] FP64. Synchronous.
+ * EINVAL: B <= 0, null pointers, circuit/Hamiltonian qubit counts differ.
+ * ENOMEM: the call's workspace exceeds the context's budget. */
+tlq_status tlq_expectation(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta, int32_t B,
+                           tlq_precision prec, double* energy);
+
+/* Forward + backward (Sec. 3, <H> and nabla <H>): as tlq_expectation plus
+ * grad[b][p] = dE_b / dtheta_p (host, row-major [B][n_params], FP64). Synchronous. */
+tlq_status tlq_expectation_grad(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta, int32_t B,
+                                tlq_precision prec, double* energy, double* grad);
+
+/* Device-pointer variant for callers that keep tensors on the GPU (the PyTorch path):
+ * theta_dev [B][n_params], energy_dev [B], grad_dev [B][n_params] (nullable: energy
+ * only) are device pointers on the context's device; all work is enqueued on
+ * cuda_stream (a cudaStream_t; NULL = the context's own stream) and the call returns
+ * without synchronising. The outputs are valid once that stream reaches this point.
+ * The workspace is owned by the context: do not enqueue a second call on another
+ * stream until this one has completed. */
+tlq_status tlq_expectation_grad_dev(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta_dev,
+                                    int32_t B, tlq_precision prec, double* energy_dev, double* grad_dev,
+                                    void* cuda_stream);
+
+/* Serving (continuous batching): enqueue one request; returns at once with a ticket.
+ * theta: host [B][n_params]; energy: host [B]; grad: host [B][n_params] when want_grad.
+ * The buffers are borrowed until tlq_poll returns TLQ_OK for the ticket. Requests are
+ * admitted as slots and device memory free up, packed with the other admitted requests
+ * into batched launches, and overlap on the device with batches already in flight.
+ * Results do not depend on what else is in the batch. Circuit and Hamiltonian must stay
+ * alive until the request completes. EINVAL as for tlq_expectation; ENOMEM only if the
+ * request alone can never fit the budget. */
+tlq_status tlq_submit(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta, int32_t B, int want_grad,
+                      tlq_precision prec, double* energy, double* grad, tlq_ticket* out);
+
+/* TLQ_OK: done (outputs written, ticket retired); TLQ_EAGAIN: pending and
+ * timeout_us == 0; TLQ_ETIMEOUT: still pending after timeout_us microseconds (a negative
+ * timeout waits until completion); any other status: the request failed (ticket retired).
+ * EINVAL for an unknown or already retired ticket. */
+tlq_status tlq_poll(tlq_ctx ctx, tlq_ticket t, int64_t timeout_us);
+
+/* Thread-local message of the calling thread's last failure ("" if none). */
+const char* tlq_last_error(tlq_ctx ctx);
+
+/* ---- introspection (host-side; no device work) -------------------------------------- */
+
+typedef enum { TLQ_PATH_CONE = 0, TLQ_PATH_DENSE = 1 } tlq_path;
+
+/* Plan summary for (c, h): the chosen path; for the cone path, per term t < n_terms the
+ * window start lo[t] and width w[t] (clipped to the chain) and the number of gates in its
+ * cone ngates[t]. Any of lo/w/ngates may be NULL. Works on host-only contexts. */
+tlq_status tlq_plan_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* path, int32_t* lo, int32_t* w,
+                         int32_t* ngates);
+
+/* Per-term cone statistics for (c, h) on the cone path: rotations nrot[t], diagonal
+ * layers ndiag[t] and parametrised diagonal gates npdiag[t] inside term t's cone, and the
+ * width weff[t] the kernel runs (the cone padded to at least 8 qubits). Used to count the
+ * algorithmic work of a call. Any array may be NULL. TLQ_EUNSUPPORTED on the dense path. */
+tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* nrot, int32_t* ndiag,
+                               int32_t* npdiag, int32_t* weff);
+
+/* Kernel timing for benchmarks. While enabled, every compute call records CUDA events
+ * around its dominant kernel (the batched cone kernel, or the dense pass sequence) on the
+ * stream it launches on. tlq_profile_last waits for the last call's events and returns
+ * that kernel's device time in milliseconds and the number of kernels the call launched. */
+tlq_status tlq_profile_enable(tlq_ctx ctx, int on);
+tlq_status tlq_profile_last(tlq_ctx ctx, float* kernel_ms, int32_t* launches);
+
+/* Serving statistics since the context was created: completed requests, latency
+ * percentiles (seconds from tlq_submit to completion on the device) and the mean number
+ * of requests per batched launch. Any out pointer may be NULL. */
+tlq_status tlq_serving_stats(tlq_ctx ctx, int64_t* completed, double* p50_s, double* p99_s,
+                             double* mean_batch);
+
+/* Version of this ABI (major * 10000 + minor * 100 + patch). */
+int32_t tlq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TLQ_H */

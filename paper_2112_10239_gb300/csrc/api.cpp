@@ -1,0 +1,620 @@
+// C-ABI implementation: validation, handles, plan cache, workspace and the synchronous
+// and device-pointer entry points. Serving (tlq_submit / tlq_poll) is in serving.cpp.
+#include "runtime.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <set>
+
+namespace tlq {
+
+static thread_local std::string t_err;
+
+void set_error(const std::string& msg) { t_err = msg; }
+const char* get_error() { return t_err.c_str(); }
+
+#define TLQ_CUDA(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+            return TLQ_ECUDA;                                                               \
+        }                                                                                   \
+    } while (0)
+
+PlanEntry::~PlanEntry() {
+    cudaFree(d_cones);
+    cudaFree(d_prog);
+    cudaFree(d_term_coeff);
+    cudaFree(d_pmap_off);
+    cudaFree(d_pmap_idx);
+    cudaFree(d_pmap_coeff);
+    cudaFree(d_gates);
+    cudaFree(d_dprog);
+    cudaFree(d_dterms);
+    cudaFree(d_items);
+    cudaFree(d_chunks);
+}
+
+template <typename T>
+static tlq_status upload(const std::vector<T>& v, T** out, size_t* bytes) {
+    *out = nullptr;
+    if (v.empty()) return TLQ_OK;
+    TLQ_CUDA(cudaMalloc((void**)out, v.size() * sizeof(T)));
+    TLQ_CUDA(cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *bytes += v.size() * sizeof(T);
+    return TLQ_OK;
+}
+
+#define TLQ_TRY(x)                          \
+    do {                                    \
+        tlq_status s_ = (x);                \
+        if (s_ != TLQ_OK) return s_;        \
+    } while (0)
+
+tlq_status get_plan(Context* ctx, Circuit* c, Ham* h, std::shared_ptr<PlanEntry>* out) {
+    auto key = std::make_pair(c->id, h->id);
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) { *out = it->second; return TLQ_OK; }
+    std::string err;
+    auto plan = make_plan(*c, *h, &err);
+    if (!plan) { set_error(err); return TLQ_EINVAL; }
+    auto pe = std::make_shared<PlanEntry>();
+    pe->plan = plan;
+    pe->circ_id = c->id;
+    pe->ham_id = h->id;
+    if (!ctx->host_only()) {
+        size_t bytes = 0;
+        std::vector<tlq_gate> gates = c->gates;
+        TLQ_TRY(upload(gates, &pe->d_gates, &bytes));
+        TLQ_TRY(upload(plan->term_coeff, &pe->d_term_coeff, &bytes));
+        if (plan->path == TLQ_PATH_CONE) {
+            TLQ_TRY(upload(plan->cones, &pe->d_cones, &bytes));
+            TLQ_TRY(upload(plan->prog, &pe->d_prog, &bytes));
+            TLQ_TRY(upload(plan->pmap_off, &pe->d_pmap_off, &bytes));
+            TLQ_TRY(upload(plan->pmap_idx, &pe->d_pmap_idx, &bytes));
+            TLQ_TRY(upload(plan->pmap_coeff, &pe->d_pmap_coeff, &bytes));
+        }
+        pe->device_bytes = bytes;
+        ctx->held += bytes;
+    }
+    ctx->plans[key] = pe;
+    *out = pe;
+    return TLQ_OK;
+}
+
+int team_bytes_host(int W, int tt, bool fp64, bool grad, bool smem_state);
+
+static int smem_optin(int device) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    return v > 2048 ? v - 1024 : 48 * 1024;
+}
+
+tlq_status ensure_worklist(Context* ctx, PlanEntry& pe, const Circuit& c, int B, bool fp64, bool grad) {
+    (void)c;
+    if (pe.wl_B == B && pe.wl_fp64 == fp64 && pe.wl_grad == grad) return TLQ_OK;
+    const Plan& P = *pe.plan;
+    const int T = (int)P.cones.size();
+    std::vector<int> order(T);
+    for (int t = 0; t < T; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P.cones[a].W > P.cones[b].W; });
+    const int smax = smem_optin(ctx->device);
+    std::vector<int32_t> items;
+    std::vector<ChunkDev> smem_chunks, glob_chunks;
+    int smem_bytes = 0, gsmem_bytes = 0, g_maxW = 0;
+    size_t k = 0;
+    while (k < order.size()) {
+        const int W = P.cones[order[k]].W;
+        size_t k2 = k;
+        while (k2 < order.size() && P.cones[order[k2]].W == W) ++k2;
+        int tt = std::min(kCtaThreads, 1 << (W - 4));
+        int tb = team_bytes_host(W, tt, fp64, grad, true);
+        int nteams = std::min(kCtaThreads / tt, smax / tb);
+        bool global = (W > kMaxSmemConeW) || nteams < 1 || (tt == kCtaThreads && (1 << (W - 4)) != tt);
+        if (global) {
+            tt = kCtaThreads;
+            tb = team_bytes_host(W, tt, fp64, grad, false);
+            nteams = 1;
+        }
+        const int first_item = (int)items.size() / 2;
+        for (size_t i = k; i < k2; ++i)
+            for (int b = 0; b < B; ++b) { items.push_back(order[i]); items.push_back(b); }
+        const int nit = (int)items.size() / 2 - first_item;
+        for (int f = 0; f < nit; f += nteams) {
+            ChunkDev ch{};
+            ch.W = W;
+            ch.first = first_item + f;
+            ch.count = std::min(nteams, nit - f);
+            ch.tt = tt;
+            ch.team_bytes = tb;
+            (global ? glob_chunks : smem_chunks).push_back(ch);
+        }
+        if (global) { gsmem_bytes = std::max(gsmem_bytes, tb); g_maxW = std::max(g_maxW, W); }
+        else smem_bytes = std::max(smem_bytes, nteams * tb);
+        k = k2;
+    }
+    std::vector<ChunkDev> chunks = smem_chunks;
+    chunks.insert(chunks.end(), glob_chunks.begin(), glob_chunks.end());
+    cudaFree(pe.d_items);
+    cudaFree(pe.d_chunks);
+    pe.d_items = nullptr;
+    pe.d_chunks = nullptr;
+    size_t bytes = 0;
+    TLQ_TRY(upload(items, &pe.d_items, &bytes));
+    TLQ_TRY(upload(chunks, &pe.d_chunks, &bytes));
+    pe.n_chunks_smem = (int)smem_chunks.size();
+    pe.n_chunks = (int)chunks.size();
+    pe.smem_bytes = smem_bytes;
+    pe.gsmem_bytes = gsmem_bytes;
+    pe.g_maxW = g_maxW;
+    pe.wl_B = B;
+    pe.wl_fp64 = fp64;
+    pe.wl_grad = grad;
+    return TLQ_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int global_grid(const PlanEntry& pe, int sm_count) {
+    const int ng = pe.n_chunks - pe.n_chunks_smem;
+    return std::max(0, std::min(ng, sm_count));
+}
+
+size_t cone_workspace_bytes(const PlanEntry& pe, const Circuit& c, int B, bool fp64, bool grad, int g_grid) {
+    const Plan& P = *pe.plan;
+    const size_t r2 = fp64 ? 16 : 8;
+    size_t s = 0;
+    s += align256((size_t)B * c.gates.size() * r2);
+    s += align256((size_t)B * P.cones.size() * sizeof(double));
+    if (grad) s += align256((size_t)B * std::max<int32_t>(1, P.n_slots) * sizeof(double));
+    if (g_grid > 0) s += align256((size_t)g_grid * ((size_t)1 << pe.g_maxW) * r2 * (grad ? 2 : 1));
+    return s + 1024;
+}
+
+tlq_status run_device(Context* ctx, Circuit* c, Ham* h, const double* theta_dev, int B, tlq_precision prec,
+                      double* energy_dev, double* grad_dev, void* stream, Workspace* ws) {
+    std::shared_ptr<PlanEntry> pe;
+    TLQ_TRY(get_plan(ctx, c, h, &pe));
+    const Plan& P = *pe->plan;
+    const bool fp64 = prec == TLQ_FP64_REF;
+    const bool grad = grad_dev != nullptr;
+    if (P.path != TLQ_PATH_CONE) {
+        set_error("dense statevector path not available for this request: " + P.why_dense);
+        return TLQ_EUNSUPPORTED;
+    }
+    TLQ_TRY(ensure_worklist(ctx, *pe, *c, B, fp64, grad));
+    const int g_grid = global_grid(*pe, ctx->sm_count);
+    const size_t need = cone_workspace_bytes(*pe, *c, B, fp64, grad, g_grid);
+    if (ws->cap - ws->used < need) {
+        set_error("workspace too small");
+        return TLQ_ENOMEM;
+    }
+    ConeLaunch L;
+    L.cones = pe->d_cones;
+    L.prog = pe->d_prog;
+    L.term_coeff = pe->d_term_coeff;
+    L.pmap_off = pe->d_pmap_off;
+    L.pmap_idx = pe->d_pmap_idx;
+    L.pmap_coeff = pe->d_pmap_coeff;
+    L.gates = pe->d_gates;
+    L.n_gates = (int32_t)c->gates.size();
+    L.n_params = c->n_params;
+    L.n_terms = (int32_t)P.cones.size();
+    L.n_slots = P.n_slots;
+    L.B = B;
+    L.theta = theta_dev;
+    L.items = pe->d_items;
+    L.chunks = pe->d_chunks;
+    L.n_chunks_smem = pe->n_chunks_smem;
+    L.n_chunks = pe->n_chunks;
+    L.smem_bytes = pe->smem_bytes;
+    L.gsmem_bytes = pe->gsmem_bytes;
+    L.g_maxW = pe->g_maxW;
+    const size_t r2 = fp64 ? 16 : 8;
+    L.gate_table = ws->take((size_t)B * c->gates.size() * r2);
+    L.e_part = (double*)ws->take((size_t)B * P.cones.size() * sizeof(double));
+    L.g_part = grad ? (double*)ws->take((size_t)B * std::max<int32_t>(1, P.n_slots) * sizeof(double)) : nullptr;
+    L.g_grid = g_grid;
+    L.gscratch_slot = g_grid > 0 ? ((size_t)1 << pe->g_maxW) * r2 * (grad ? 2 : 1) : 0;
+    L.gscratch = g_grid > 0 ? ws->take((size_t)g_grid * L.gscratch_slot) : nullptr;
+    L.counters = ctx->d_counters;
+    L.err = ctx->d_err;
+    L.energy = energy_dev;
+    L.grad = grad_dev;
+    L.fp64 = fp64;
+    L.sm_count = ctx->sm_count;
+    if (ctx->profile) { L.ev_begin = ctx->prof_ev[0]; L.ev_end = ctx->prof_ev[1]; }
+    int rc = launch_cone(L, stream);
+    ctx->last_launches = L.launches;
+    if (rc != 0) {
+        set_error(std::string("cone launch: ") + cudaGetErrorString((cudaError_t)rc));
+        return TLQ_ECUDA;
+    }
+    return TLQ_OK;
+}
+
+// Size the context workspace for one call (plus its I/O buffers); grow-only.
+static tlq_status reserve(Context* ctx, size_t bytes) {
+    ctx->ws.used = 0;
+    if (ctx->ws.cap >= bytes) return TLQ_OK;
+    const size_t others = ctx->held - ctx->ws.cap;
+    if (others + bytes > ctx->budget) {
+        set_error("request needs " + std::to_string(bytes) + " bytes of workspace; budget " +
+                  std::to_string(ctx->budget) + " bytes, " + std::to_string(others) + " held elsewhere");
+        return TLQ_ENOMEM;
+    }
+    size_t nb = std::max(bytes, ctx->ws.cap + ctx->ws.cap / 2);
+    if (others + nb > ctx->budget) nb = bytes;
+    TLQ_CUDA(cudaStreamSynchronize((cudaStream_t)ctx->stream));
+    if (ctx->ws.base) cudaFree(ctx->ws.base);
+    ctx->held -= ctx->ws.cap;
+    ctx->ws.base = nullptr;
+    ctx->ws.cap = 0;
+    cudaError_t e = cudaMalloc(&ctx->ws.base, nb);
+    if (e != cudaSuccess) {
+        set_error(std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+        return TLQ_ENOMEM;
+    }
+    ctx->ws.cap = nb;
+    ctx->held += nb;
+    return TLQ_OK;
+}
+
+static tlq_status ensure_pinned(Context* ctx, size_t bytes) {
+    if (ctx->h_pinned_cap >= bytes) return TLQ_OK;
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    ctx->h_pinned = nullptr;
+    ctx->h_pinned_cap = 0;
+    TLQ_CUDA(cudaMallocHost(&ctx->h_pinned, bytes));
+    ctx->h_pinned_cap = bytes;
+    return TLQ_OK;
+}
+
+}  // namespace tlq
+
+using namespace tlq;
+
+struct tlq_ctx_s : Context {};
+struct tlq_circuit_s : Circuit {};
+struct tlq_ham_s : Ham {};
+
+extern "C" {
+
+int32_t tlq_version(void) { return 10000; }
+
+const char* tlq_last_error(tlq_ctx) { return get_error(); }
+
+tlq_status tlq_init(const tlq_config* cfg_in, tlq_ctx* out) {
+    if (!out) { set_error("tlq_init: out is NULL"); return TLQ_EINVAL; }
+    tlq_config cfg{};
+    cfg.device = 0;
+    if (cfg_in) cfg = *cfg_in;
+    if (cfg.max_slots <= 0) cfg.max_slots = 64;
+    if (cfg.default_prec < TLQ_FP32 || cfg.default_prec > TLQ_FP64_REF) {
+        set_error("tlq_init: unknown default precision");
+        return TLQ_EINVAL;
+    }
+    auto* ctx = new tlq_ctx_s();
+    ctx->cfg = cfg;
+    ctx->device = cfg.device;
+    if (cfg.device >= 0) {
+        int ndev = 0;
+        cudaError_t e = cudaGetDeviceCount(&ndev);
+        if (e != cudaSuccess || cfg.device >= ndev) {
+            set_error(std::string("tlq_init: no CUDA device ") + std::to_string(cfg.device) +
+                      (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : std::string()));
+            delete ctx;
+            return e != cudaSuccess ? TLQ_ECUDA : TLQ_EINVAL;
+        }
+        auto fail = [&](cudaError_t err, const char* what) {
+            set_error(std::string("tlq_init: ") + what + ": " + cudaGetErrorString(err));
+            delete ctx;
+            return TLQ_ECUDA;
+        };
+        if ((e = cudaSetDevice(cfg.device)) != cudaSuccess) return fail(e, "cudaSetDevice");
+        cudaStream_t st;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
+        ctx->stream = st;
+        cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cfg.device);
+        size_t freeb = 0, totalb = 0;
+        cudaMemGetInfo(&freeb, &totalb);
+        ctx->budget = cfg.mem_budget ? cfg.mem_budget : (size_t)(0.8 * (double)freeb);
+        if ((e = cudaMalloc((void**)&ctx->d_counters, 64)) != cudaSuccess) return fail(e, "counters");
+        ctx->d_err = ctx->d_counters + 4;
+        ctx->held = 64;
+    }
+    *out = ctx;
+    return TLQ_OK;
+}
+
+tlq_status tlq_destroy(tlq_ctx ctx) {
+    if (!ctx) return TLQ_OK;
+    scheduler_stop(ctx);
+    if (!ctx->host_only()) {
+        cudaSetDevice(ctx->device);
+        cudaStreamSynchronize((cudaStream_t)ctx->stream);
+    }
+    ctx->plans.clear();
+    for (Circuit* c : ctx->circuits) delete static_cast<tlq_circuit_s*>(c);
+    for (Ham* h : ctx->hams) delete static_cast<tlq_ham_s*>(h);
+    if (!ctx->host_only()) {
+        cudaFree(ctx->ws.base);
+        cudaFree(ctx->d_counters);
+        if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+        if (ctx->prof_ev[0]) cudaEventDestroy((cudaEvent_t)ctx->prof_ev[0]);
+        if (ctx->prof_ev[1]) cudaEventDestroy((cudaEvent_t)ctx->prof_ev[1]);
+        cudaStreamDestroy((cudaStream_t)ctx->stream);
+    }
+    delete ctx;
+    return TLQ_OK;
+}
+
+tlq_status tlq_circuit_create(tlq_ctx ctx, int32_t n, const tlq_gate* gates, int32_t n_gates, int32_t n_params,
+                              tlq_circuit* out) {
+    if (!ctx || !out) { set_error("tlq_circuit_create: NULL context or out"); return TLQ_EINVAL; }
+    if (n < 1 || n > (1 << 20)) { set_error("tlq_circuit_create: n_qubits out of [1, 2^20]"); return TLQ_EINVAL; }
+    if (n_gates < 0 || (n_gates > 0 && !gates)) { set_error("tlq_circuit_create: bad gate array"); return TLQ_EINVAL; }
+    if (n_params < 0) { set_error("tlq_circuit_create: n_params < 0"); return TLQ_EINVAL; }
+    for (int i = 0; i < n_gates; ++i) {
+        const tlq_gate& g = gates[i];
+        std::string where = "tlq_circuit_create: gate " + std::to_string(i) + ": ";
+        if (g.kind < TLQ_RX || g.kind > TLQ_CZ) { set_error(where + "unknown kind"); return TLQ_EINVAL; }
+        if (g.q0 < 0 || g.q0 >= n) { set_error(where + "qubit out of range"); return TLQ_EINVAL; }
+        const bool two = g.kind == TLQ_RZZ || g.kind == TLQ_CZ;
+        if (two) {
+            if (g.q1 < 0 || g.q1 >= n) { set_error(where + "second qubit out of range"); return TLQ_EINVAL; }
+            if (g.q1 == g.q0) { set_error(where + "q0 == q1"); return TLQ_EINVAL; }
+        }
+        if (g.kind != TLQ_CZ && (g.param < -1 || g.param >= n_params)) {
+            set_error(where + "param index out of range");
+            return TLQ_EINVAL;
+        }
+    }
+    auto* c = new tlq_circuit_s();
+    c->ctx = ctx;
+    c->n = n;
+    c->n_params = n_params;
+    c->gates.assign(gates, gates + n_gates);
+    for (auto& g : c->gates) {
+        if (g.kind != TLQ_RZZ && g.kind != TLQ_CZ) g.q1 = -1;
+        if (g.kind == TLQ_CZ) g.param = -1;
+    }
+    plan_circuit_layers(*c);
+    c->id = ctx->next_id++;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->circuits.push_back(c);
+    }
+    *out = c;
+    return TLQ_OK;
+}
+
+static void evict_plans(Context* ctx, uint64_t circ_id, uint64_t ham_id) {
+    for (auto it = ctx->plans.begin(); it != ctx->plans.end();) {
+        if (it->first.first == circ_id || it->first.second == ham_id) {
+            ctx->held -= it->second->device_bytes;
+            it = ctx->plans.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+tlq_status tlq_circuit_destroy(tlq_circuit c) {
+    if (!c) return TLQ_OK;
+    Context* ctx = c->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->host_only()) cudaStreamSynchronize((cudaStream_t)ctx->stream);
+    evict_plans(ctx, c->id, 0);
+    ctx->circuits.erase(std::remove(ctx->circuits.begin(), ctx->circuits.end(), (Circuit*)c), ctx->circuits.end());
+    delete c;
+    return TLQ_OK;
+}
+
+tlq_status tlq_hamiltonian_create(tlq_ctx ctx, int32_t n, const tlq_term* terms, int32_t n_terms, tlq_ham* out) {
+    if (!ctx || !out) { set_error("tlq_hamiltonian_create: NULL context or out"); return TLQ_EINVAL; }
+    if (n < 1 || n > (1 << 20)) { set_error("tlq_hamiltonian_create: n_qubits out of [1, 2^20]"); return TLQ_EINVAL; }
+    if (n_terms < 1 || !terms) { set_error("tlq_hamiltonian_create: need at least one term"); return TLQ_EINVAL; }
+    auto* h = new tlq_ham_s();
+    h->ctx = ctx;
+    h->n = n;
+    for (int t = 0; t < n_terms; ++t) {
+        const tlq_term& T = terms[t];
+        std::string where = "tlq_hamiltonian_create: term " + std::to_string(t) + ": ";
+        if (T.nsites < 1 || !T.sites || !T.paulis) { set_error(where + "empty term"); delete h; return TLQ_EINVAL; }
+        Term tm;
+        tm.coeff = T.coeff;
+        std::set<int> seen;
+        for (int k = 0; k < T.nsites; ++k) {
+            const int s = T.sites[k];
+            const char l = T.paulis[k];
+            if (s < 0 || s >= n) { set_error(where + "site out of range"); delete h; return TLQ_EINVAL; }
+            if (l != 'X' && l != 'Y' && l != 'Z') { set_error(where + "unknown Pauli letter"); delete h; return TLQ_EINVAL; }
+            if (!seen.insert(s).second) { set_error(where + "duplicate site"); delete h; return TLQ_EINVAL; }
+            tm.sites.push_back(s);
+            tm.letters.push_back(l);
+        }
+        h->terms.push_back(std::move(tm));
+    }
+    h->id = ctx->next_id++;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->hams.push_back(h);
+    }
+    *out = h;
+    return TLQ_OK;
+}
+
+tlq_status tlq_hamiltonian_destroy(tlq_ham h) {
+    if (!h) return TLQ_OK;
+    Context* ctx = h->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->host_only()) cudaStreamSynchronize((cudaStream_t)ctx->stream);
+    evict_plans(ctx, 0, h->id);
+    ctx->hams.erase(std::remove(ctx->hams.begin(), ctx->hams.end(), (Ham*)h), ctx->hams.end());
+    delete h;
+    return TLQ_OK;
+}
+
+static tlq_status check_pair(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t B, tlq_precision prec) {
+    if (!ctx || !c || !h) { set_error("NULL context, circuit or Hamiltonian"); return TLQ_EINVAL; }
+    if (c->ctx != ctx || h->ctx != ctx) { set_error("circuit or Hamiltonian belongs to another context"); return TLQ_EINVAL; }
+    if (c->n != h->n) { set_error("circuit and Hamiltonian qubit counts differ"); return TLQ_EINVAL; }
+    if (B <= 0) { set_error("B must be positive"); return TLQ_EINVAL; }
+    if (prec < TLQ_FP32 || prec > TLQ_FP64_REF) { set_error("unknown precision"); return TLQ_EINVAL; }
+    if (ctx->host_only()) { set_error("host-only context: no device work"); return TLQ_EUNSUPPORTED; }
+    return TLQ_OK;
+}
+
+static tlq_status sync_call(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta, int32_t B, tlq_precision prec,
+                            double* energy, double* grad) {
+    TLQ_TRY(check_pair(ctx, c, h, B, prec));
+    if (!theta && c->n_params > 0) { set_error("theta is NULL"); return TLQ_EINVAL; }
+    if (!energy) { set_error("energy is NULL"); return TLQ_EINVAL; }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TLQ_CUDA(cudaSetDevice(ctx->device));
+    std::shared_ptr<PlanEntry> pe;
+    TLQ_TRY(get_plan(ctx, c, h, &pe));
+    const bool fp64 = prec == TLQ_FP64_REF;
+    const bool want_grad = grad != nullptr;
+    size_t work = 0;
+    if (pe->plan->path == TLQ_PATH_CONE) {
+        TLQ_TRY(ensure_worklist(ctx, *pe, *c, B, fp64, want_grad));
+        work = cone_workspace_bytes(*pe, *c, B, fp64, want_grad, std::max(0, std::min(pe->n_chunks - pe->n_chunks_smem, ctx->sm_count)));
+    }
+    const size_t P = (size_t)std::max(1, c->n_params);
+    const size_t th_b = (size_t)B * P * sizeof(double);
+    const size_t e_b = (size_t)B * sizeof(double);
+    const size_t g_b = want_grad ? (size_t)B * P * sizeof(double) : 0;
+    TLQ_TRY(reserve(ctx, work + th_b + e_b + g_b + 4096));
+    TLQ_TRY(ensure_pinned(ctx, th_b + e_b + g_b + 64));
+    cudaStream_t st = (cudaStream_t)ctx->stream;
+    double* d_theta = (double*)ctx->ws.take(th_b);
+    double* d_e = (double*)ctx->ws.take(e_b);
+    double* d_g = want_grad ? (double*)ctx->ws.take(g_b) : nullptr;
+    char* hp = (char*)ctx->h_pinned;
+    if (c->n_params > 0) std::memcpy(hp, theta, (size_t)B * c->n_params * sizeof(double));
+    TLQ_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), st));
+    if (c->n_params > 0) TLQ_CUDA(cudaMemcpyAsync(d_theta, hp, (size_t)B * c->n_params * sizeof(double), cudaMemcpyHostToDevice, st));
+    TLQ_TRY(run_device(ctx, c, h, d_theta, B, prec, d_e, d_g, st, &ctx->ws));
+    int32_t* h_err = (int32_t*)(hp + th_b + e_b + g_b);
+    TLQ_CUDA(cudaMemcpyAsync(hp + th_b, d_e, e_b, cudaMemcpyDeviceToHost, st));
+    if (want_grad) TLQ_CUDA(cudaMemcpyAsync(hp + th_b + e_b, d_g, (size_t)B * c->n_params * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TLQ_CUDA(cudaMemcpyAsync(h_err, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    TLQ_CUDA(cudaStreamSynchronize(st));
+    if (*h_err != 0) {
+        set_error("kernel error word " + std::to_string(*h_err));
+        return TLQ_EKERNEL;
+    }
+    std::memcpy(energy, hp + th_b, e_b);
+    if (want_grad) std::memcpy(grad, hp + th_b + e_b, (size_t)B * c->n_params * sizeof(double));
+    return TLQ_OK;
+}
+
+tlq_status tlq_expectation(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta, int32_t B, tlq_precision prec,
+                           double* energy) {
+    return sync_call(ctx, c, h, theta, B, prec, energy, nullptr);
+}
+
+tlq_status tlq_expectation_grad(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta, int32_t B,
+                                tlq_precision prec, double* energy, double* grad) {
+    if (!grad) { set_error("grad is NULL"); return TLQ_EINVAL; }
+    return sync_call(ctx, c, h, theta, B, prec, energy, grad);
+}
+
+tlq_status tlq_expectation_grad_dev(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta_dev, int32_t B,
+                                    tlq_precision prec, double* energy_dev, double* grad_dev, void* cuda_stream) {
+    TLQ_TRY(check_pair(ctx, c, h, B, prec));
+    if ((!theta_dev && c->n_params > 0) || !energy_dev) { set_error("NULL device pointer"); return TLQ_EINVAL; }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TLQ_CUDA(cudaSetDevice(ctx->device));
+    std::shared_ptr<PlanEntry> pe;
+    TLQ_TRY(get_plan(ctx, c, h, &pe));
+    const bool fp64 = prec == TLQ_FP64_REF;
+    size_t work = 0;
+    if (pe->plan->path == TLQ_PATH_CONE) {
+        TLQ_TRY(ensure_worklist(ctx, *pe, *c, B, fp64, grad_dev != nullptr));
+        work = cone_workspace_bytes(*pe, *c, B, fp64, grad_dev != nullptr,
+                                    std::max(0, std::min(pe->n_chunks - pe->n_chunks_smem, ctx->sm_count)));
+    }
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : (cudaStream_t)ctx->stream;
+    if (ctx->ws.cap < work + 4096) {
+        // the workspace is reallocated: make sure no earlier call on another stream still uses it
+        TLQ_CUDA(cudaDeviceSynchronize());
+    }
+    TLQ_TRY(reserve(ctx, work + 4096));
+    return run_device(ctx, c, h, theta_dev, B, prec, energy_dev, grad_dev, st, &ctx->ws);
+}
+
+tlq_status tlq_plan_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* path, int32_t* lo, int32_t* w,
+                         int32_t* ngates) {
+    if (!ctx || !c || !h) { set_error("NULL handle"); return TLQ_EINVAL; }
+    if (c->n != h->n) { set_error("circuit and Hamiltonian qubit counts differ"); return TLQ_EINVAL; }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    std::shared_ptr<PlanEntry> pe;
+    TLQ_TRY(get_plan(ctx, c, h, &pe));
+    const Plan& P = *pe->plan;
+    if (path) *path = P.path;
+    if (P.path == TLQ_PATH_CONE) {
+        for (size_t t = 0; t < P.cones.size(); ++t) {
+            if (lo) lo[t] = P.cone_lo[t];
+            if (w) w[t] = P.cone_wtrue[t];
+            if (ngates) ngates[t] = P.cone_gates[t];
+        }
+    }
+    return TLQ_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* nrot, int32_t* ndiag, int32_t* npdiag,
+                               int32_t* weff) {
+    if (!ctx || !c || !h) { set_error("NULL handle"); return TLQ_EINVAL; }
+    if (c->n != h->n) { set_error("circuit and Hamiltonian qubit counts differ"); return TLQ_EINVAL; }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    std::shared_ptr<PlanEntry> pe;
+    TLQ_TRY(get_plan(ctx, c, h, &pe));
+    const Plan& P = *pe->plan;
+    if (P.path != TLQ_PATH_CONE) { set_error("not on the cone path"); return TLQ_EUNSUPPORTED; }
+    for (size_t t = 0; t < P.cones.size(); ++t) {
+        if (nrot) nrot[t] = P.cone_nrot[t];
+        if (ndiag) ndiag[t] = P.cone_ndiag[t];
+        if (npdiag) npdiag[t] = P.cone_npdiag[t];
+        if (weff) weff[t] = P.cones[t].W;
+    }
+    return TLQ_OK;
+}
+
+tlq_status tlq_profile_enable(tlq_ctx ctx, int on) {
+    if (!ctx) { set_error("NULL context"); return TLQ_EINVAL; }
+    if (ctx->host_only()) { set_error("host-only context"); return TLQ_EUNSUPPORTED; }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TLQ_CUDA(cudaSetDevice(ctx->device));
+    if (on && !ctx->prof_ev[0]) {
+        cudaEvent_t a, b;
+        TLQ_CUDA(cudaEventCreate(&a));
+        TLQ_CUDA(cudaEventCreate(&b));
+        ctx->prof_ev[0] = a;
+        ctx->prof_ev[1] = b;
+    }
+    ctx->profile = on != 0;
+    return TLQ_OK;
+}
+
+tlq_status tlq_profile_last(tlq_ctx ctx, float* kernel_ms, int32_t* launches) {
+    if (!ctx) { set_error("NULL context"); return TLQ_EINVAL; }
+    if (!ctx->profile || !ctx->prof_ev[0]) { set_error("profiling is not enabled"); return TLQ_EINVAL; }
+    TLQ_CUDA(cudaEventSynchronize((cudaEvent_t)ctx->prof_ev[1]));
+    float ms = 0;
+    TLQ_CUDA(cudaEventElapsedTime(&ms, (cudaEvent_t)ctx->prof_ev[0], (cudaEvent_t)ctx->prof_ev[1]));
+    if (kernel_ms) *kernel_ms = ms;
+    if (launches) *launches = ctx->last_launches;
+    return TLQ_OK;
+}
+
+}  // extern "C"

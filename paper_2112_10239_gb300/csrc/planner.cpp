@@ -1,0 +1,241 @@
+// Host planner: layer structure of a circuit and per-term causal cones.
+//
+// TensorLy-Quantum (arXiv:2112.10239) contracts the whole ket network, the operator and
+// the bra network along an optimised path (Sec. 1, Sec. 3) and lists
+// "causality-simplified contraction" as future work (Sec. 4). This planner implements
+// that restriction: for each Pauli term it walks the circuit backwards and keeps only
+// the gates that can influence the term, so each term becomes a small dense problem on
+// a window of W chain sites whose size does not depend on the qubit count.
+//
+// Light-cone rule (Heisenberg picture, backwards through layer l = (rotations R_l,
+// diagonal gates D_l)):
+//   * D_l: the diagonal gates commute with each other. If the operator is still
+//     diagonal (Z-only) they commute with it and drop out. Otherwise every diagonal gate
+//     touching the support is kept and its qubits join the support (one step per layer,
+//     because the new qubits only carry Z factors, which commute with D_l).
+//   * R_l: rotations on support qubits are kept; after one the operator is no longer
+//     diagonal. Rotations never grow the support.
+// Gates outside the cone commute past the operator and cancel, so simulating only the
+// kept gates on the window from |0...0> gives the exact term value.
+#include "internal.h"
+
+#include <algorithm>
+#include <cstring>
+
+namespace tlq {
+
+static bool is_diag(int kind) { return kind == TLQ_RZ || kind == TLQ_RZZ || kind == TLQ_CZ; }
+static bool is_two(int kind) { return kind == TLQ_RZZ || kind == TLQ_CZ; }
+
+std::string plan_circuit_layers(Circuit& c) {
+    // Greedy grouping in gate order: a rotation joins the open rotation step if its qubit
+    // is still free there; diagonal gates join the open diagonal step. No reordering.
+    struct Step { bool diag; std::vector<int> g; std::vector<char> used; };
+    std::vector<Step> steps;
+    c.nearest_neighbour = true;
+    for (int i = 0; i < (int)c.gates.size(); ++i) {
+        const tlq_gate& g = c.gates[i];
+        if (is_two(g.kind) && std::abs(g.q0 - g.q1) != 1) c.nearest_neighbour = false;
+        if (is_diag(g.kind)) {
+            if (steps.empty() || !steps.back().diag) steps.push_back(Step{true, {}, {}});
+            steps.back().g.push_back(i);
+        } else {
+            if (steps.empty() || steps.back().diag || steps.back().used[g.q0]) {
+                steps.push_back(Step{false, {}, std::vector<char>(c.n, 0)});
+            }
+            steps.back().g.push_back(i);
+            steps.back().used[g.q0] = 1;
+        }
+    }
+    c.layers.clear();
+    size_t k = 0;
+    while (k < steps.size() && steps[k].diag) ++k;   // diagonal gates on |0..0>: global phase
+    for (; k < steps.size(); ++k) {
+        Circuit::Layer L;
+        L.rot = steps[k].g;
+        if (k + 1 < steps.size() && steps[k + 1].diag) { L.diag = steps[k + 1].g; ++k; }
+        c.layers.push_back(std::move(L));
+    }
+    return "";
+}
+
+namespace {
+
+struct LayerIndex {
+    // per layer: rotation gate on qubit q (or -1); diagonal gates touching q
+    std::vector<std::vector<int>> rot_at;                 // [L][n]
+    std::vector<std::vector<std::vector<int>>> diag_at;   // [L][n] -> gates
+};
+
+LayerIndex index_layers(const Circuit& c) {
+    LayerIndex ix;
+    const int L = (int)c.layers.size();
+    ix.rot_at.assign(L, std::vector<int>(c.n, -1));
+    ix.diag_at.assign(L, std::vector<std::vector<int>>(c.n));
+    for (int l = 0; l < L; ++l) {
+        for (int g : c.layers[l].rot) ix.rot_at[l][c.gates[g].q0] = g;
+        for (int g : c.layers[l].diag) {
+            const tlq_gate& G = c.gates[g];
+            ix.diag_at[l][G.q0].push_back(g);
+            if (is_two(G.kind)) ix.diag_at[l][G.q1].push_back(g);
+        }
+    }
+    return ix;
+}
+
+}  // namespace
+
+std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err) {
+    auto P = std::make_shared<Plan>();
+    const int T = (int)h.terms.size();
+    const int L = (int)c.layers.size();
+    P->term_coeff.resize(T);
+    for (int t = 0; t < T; ++t) P->term_coeff[t] = h.terms[t].coeff;
+
+    if (!c.nearest_neighbour) {
+        P->path = TLQ_PATH_DENSE;
+        P->why_dense = "two-qubit gate between non-adjacent qubits";
+        return P;
+    }
+    const LayerIndex ix = index_layers(c);
+    std::vector<char> inS(c.n, 0), inc(c.gates.size(), 0);
+    P->cones.resize(T);
+    P->cone_lo.resize(T);
+    P->cone_wtrue.resize(T);
+    P->cone_gates.resize(T);
+    P->cone_nrot.assign(T, 0);
+    P->cone_ndiag.assign(T, 0);
+    P->cone_npdiag.assign(T, 0);
+    std::vector<std::vector<std::pair<int32_t, double>>> pentries(c.n_params);
+    int32_t slot_total = 0;
+
+    for (int t = 0; t < T; ++t) {
+        const Term& term = h.terms[t];
+        std::vector<int> S(term.sites.begin(), term.sites.end());
+        for (int q : S) inS[q] = 1;
+        bool diag_op = true;
+        for (char ch : term.letters) if (ch != 'Z') diag_op = false;
+        std::vector<int> kept;   // gate indices in the cone
+        for (int l = L - 1; l >= 0; --l) {
+            if (!diag_op && !c.layers[l].diag.empty()) {
+                std::vector<int> grow;
+                for (int q : S) {
+                    for (int g : ix.diag_at[l][q]) {
+                        if (inc[g]) continue;
+                        inc[g] = 1;
+                        kept.push_back(g);
+                        const tlq_gate& G = c.gates[g];
+                        if (!inS[G.q0]) { inS[G.q0] = 1; grow.push_back(G.q0); }
+                        if (is_two(G.kind) && !inS[G.q1]) { inS[G.q1] = 1; grow.push_back(G.q1); }
+                    }
+                }
+                S.insert(S.end(), grow.begin(), grow.end());
+            }
+            for (int q : S) {
+                int g = ix.rot_at[l][q];
+                if (g >= 0 && !inc[g]) { inc[g] = 1; kept.push_back(g); diag_op = false; }
+            }
+        }
+        int lo = *std::min_element(S.begin(), S.end());
+        int hi = *std::max_element(S.begin(), S.end());
+        for (int q : S) inS[q] = 0;
+        for (int g : kept) inc[g] = 0;
+        const int wtrue = hi - lo + 1;
+        int W = std::max(wtrue, kMinConeW);
+        P->cone_lo[t] = lo;
+        P->cone_wtrue[t] = wtrue;
+        P->cone_gates[t] = (int32_t)kept.size();
+        P->max_w = std::max(P->max_w, W);
+        if (W > kMaxConeW) {
+            P->path = TLQ_PATH_DENSE;
+            P->why_dense = "light cone wider than " + std::to_string(kMaxConeW) + " qubits";
+            return P;
+        }
+        // Emit the program in forward layer order.
+        std::sort(kept.begin(), kept.end());
+        ConeDev cd{};
+        cd.term = t;
+        cd.W = W;
+        cd.prog_off = (int32_t)P->prog.size();
+        cd.slot_off = slot_total;
+        int32_t nslot = 0;
+        auto kept_has = [&](int g) { return std::binary_search(kept.begin(), kept.end(), g); };
+        std::vector<int32_t> body, layer_off;
+        int32_t nlayers = 0;
+        for (int l = 0; l < L; ++l) {
+            std::vector<int> rot, diag;
+            for (int g : c.layers[l].rot) if (kept_has(g)) rot.push_back(g);
+            for (int g : c.layers[l].diag) if (kept_has(g)) diag.push_back(g);
+            if (rot.empty() && diag.empty()) continue;
+            std::sort(rot.begin(), rot.end(), [&](int a, int b) { return c.gates[a].q0 < c.gates[b].q0; });
+            // split the diagonal gates so no layer exceeds kMaxDiagParams parametrised gates
+            std::vector<std::vector<int>> dparts(1);
+            int np = 0;
+            for (int g : diag) {
+                if (c.gates[g].param >= 0 && c.gates[g].kind != TLQ_CZ) {
+                    if (np == kMaxDiagParams) { dparts.emplace_back(); np = 0; }
+                    ++np;
+                }
+                dparts.back().push_back(g);
+            }
+            for (size_t part = 0; part < dparts.size(); ++part) {
+                const std::vector<int>& rr = part == 0 ? rot : std::vector<int>();
+                const std::vector<int>& dd = dparts[part];
+                layer_off.push_back((int32_t)body.size());
+                body.push_back((int32_t)rr.size());
+                body.push_back((int32_t)dd.size());
+                P->cone_nrot[t] += (int32_t)rr.size();
+                if (!dd.empty()) P->cone_ndiag[t] += 1;
+                for (int g : rr) {
+                    const tlq_gate& G = c.gates[g];
+                    int32_t slot = G.param >= 0 ? nslot++ : -1;
+                    if (slot >= 0) pentries[G.param].push_back({slot_total + slot, term.coeff});
+                    body.push_back((G.q0 - lo) | (G.kind << 8));
+                    body.push_back(g);
+                    body.push_back(slot);
+                }
+                for (int g : dd) {
+                    const tlq_gate& G = c.gates[g];
+                    int32_t slot = (G.param >= 0 && G.kind != TLQ_CZ) ? nslot++ : -1;
+                    if (slot >= 0) P->cone_npdiag[t] += 1;
+                    if (slot >= 0) pentries[G.param].push_back({slot_total + slot, term.coeff});
+                    int j0 = G.q0 - lo, j1 = is_two(G.kind) ? G.q1 - lo : 255;
+                    if (is_two(G.kind) && j1 < j0) std::swap(j0, j1);
+                    body.push_back(G.kind | (j0 << 8) | (j1 << 16));
+                    body.push_back(g);
+                    body.push_back(slot);
+                }
+                ++nlayers;
+            }
+        }
+        P->prog.push_back(nlayers);
+        P->prog.insert(P->prog.end(), layer_off.begin(), layer_off.end());
+        P->prog.insert(P->prog.end(), body.begin(), body.end());
+        cd.nslots = nslot;
+        slot_total += nslot;
+        uint32_t flip = 0, zy = 0;
+        int ny = 0;
+        for (size_t k = 0; k < term.sites.size(); ++k) {
+            uint32_t bit = 1u << (term.sites[k] - lo);
+            char ch = term.letters[k];
+            if (ch == 'X' || ch == 'Y') flip |= bit;
+            if (ch == 'Y' || ch == 'Z') zy |= bit;
+            if (ch == 'Y') ++ny;
+        }
+        cd.flip = flip;
+        cd.zy = zy;
+        cd.ny = ny;
+        P->cones[t] = cd;
+    }
+    P->n_slots = slot_total;
+    P->pmap_off.assign(c.n_params + 1, 0);
+    for (int p = 0; p < c.n_params; ++p) P->pmap_off[p + 1] = P->pmap_off[p] + (int32_t)pentries[p].size();
+    P->pmap_idx.reserve(P->pmap_off.back());
+    P->pmap_coeff.reserve(P->pmap_off.back());
+    for (int p = 0; p < c.n_params; ++p)
+        for (auto& e : pentries[p]) { P->pmap_idx.push_back(e.first); P->pmap_coeff.push_back(e.second); }
+    (void)err;
+    return P;
+}
+
+}  // namespace tlq

@@ -1,0 +1,94 @@
+// Host runtime objects behind the C-ABI (context, device plan cache, workspace).
+#pragma once
+
+#include "internal.h"
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+
+namespace tlq {
+
+void set_error(const std::string& msg);
+const char* get_error();
+
+// Device copy of a Plan plus the work list for the last batch size used.
+struct PlanEntry {
+    std::shared_ptr<Plan> plan;
+    uint64_t circ_id = 0, ham_id = 0;
+    // cone path device buffers
+    ConeDev* d_cones = nullptr;
+    int32_t* d_prog = nullptr;
+    double* d_term_coeff = nullptr;
+    int32_t* d_pmap_off = nullptr;
+    int32_t* d_pmap_idx = nullptr;
+    double* d_pmap_coeff = nullptr;
+    tlq_gate* d_gates = nullptr;
+    // dense path device buffers
+    int32_t* d_dprog = nullptr;
+    int32_t dprog_len = 0;
+    int32_t* d_dterms = nullptr;
+    // work list cache (keyed by batch size and precision)
+    int wl_B = -1;
+    bool wl_fp64 = false;
+    bool wl_grad = false;
+    int32_t* d_items = nullptr;
+    ChunkDev* d_chunks = nullptr;
+    int n_chunks_smem = 0, n_chunks = 0;
+    int smem_bytes = 0, gsmem_bytes = 0, g_maxW = 0;
+    size_t device_bytes = 0;
+    ~PlanEntry();
+};
+
+struct Workspace {
+    void* base = nullptr;
+    size_t cap = 0;
+    size_t used = 0;
+    void* take(size_t bytes) {
+        used = (used + 255) & ~(size_t)255;
+        void* p = (char*)base + used;
+        used += bytes;
+        return p;
+    }
+};
+
+struct Request;
+struct Scheduler;
+
+struct Context {
+    int device = -1;
+    tlq_config cfg{};
+    void* stream = nullptr;          // cudaStream_t
+    int sm_count = 0;
+    size_t budget = 0;
+    size_t held = 0;                 // bytes currently held (plans + workspace)
+    Workspace ws;
+    int32_t* d_counters = nullptr;   // [2]
+    int32_t* d_err = nullptr;        // kernel error word
+    void* h_pinned = nullptr;        // pinned staging
+    size_t h_pinned_cap = 0;
+    std::mutex mu;                   // guards the plan cache and workspace
+    std::map<std::pair<uint64_t, uint64_t>, std::shared_ptr<PlanEntry>> plans;
+    std::vector<Circuit*> circuits;
+    std::vector<Ham*> hams;
+    std::atomic<uint64_t> next_id{1};
+    Scheduler* sched = nullptr;
+    bool profile = false;            // record events around the dominant kernel
+    void* prof_ev[2] = {nullptr, nullptr};
+    int last_launches = 0;
+    bool host_only() const { return device < 0; }
+};
+
+// Prepared launch of one (circuit, Hamiltonian, batch) on the cone path.
+tlq_status get_plan(Context* ctx, Circuit* c, Ham* h, std::shared_ptr<PlanEntry>* out);
+tlq_status ensure_worklist(Context* ctx, PlanEntry& pe, const Circuit& c, int B, bool fp64, bool grad);
+// Bytes of workspace a launch needs (excluding the work list).
+size_t cone_workspace_bytes(const PlanEntry& pe, const Circuit& c, int B, bool fp64, bool grad, int g_grid);
+tlq_status run_device(Context* ctx, Circuit* c, Ham* h, const double* theta_dev, int B, tlq_precision prec,
+                      double* energy_dev, double* grad_dev, void* stream, Workspace* ws);
+
+void scheduler_stop(Context* ctx);
+
+}  // namespace tlq

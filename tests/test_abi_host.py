@@ -1,0 +1,124 @@
+"""Host-side checks of the C-ABI library (no GPU): it loads, exports every symbol that
+include/tlq.h declares, validates descriptors, and plans the exact causal cones."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2112_10239_gb300 import build as tlq_build
+from paper_2112_10239_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    tlq_build.build()
+    from paper_2112_10239_gb300 import binding
+    return binding
+
+
+@pytest.fixture()
+def hctx(B):
+    ctx = B.Context(device=-1)
+    yield ctx
+    ctx.close()
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "tlq.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tlq_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(B):
+    L = B.lib()
+    syms = header_symbols()
+    assert len(syms) >= 14
+    for s in syms:
+        assert hasattr(L, s), s
+    assert sorted(B.SYMBOLS) == syms
+    assert B.tlq_version() == 10000
+
+
+def test_struct_layout_matches_header(B):
+    # tlq_gate: 4 x int32 + double = 24 bytes; tlq_term: double, int32, 2 pointers.
+    assert ctypes.sizeof(B.tlq_gate) == 24
+    assert B.tlq_term.sites.offset == 16
+
+
+def _err(B, fn, *a):
+    with pytest.raises(B.TLQError) as ei:
+        fn(*a)
+    return ei.value.status
+
+
+def test_circuit_validation(B, hctx):
+    ok = [(W.RY, 0, -1, 0, 0.0), (W.CZ, 0, 1, -1, 0.0)]
+    c = hctx.circuit(2, ok, 1)
+    c.close()
+    bad = [
+        ([(W.RY, 2, -1, 0, 0.0)], 1),          # qubit out of range
+        ([(W.CZ, 0, 0, -1, 0.0)], 1),          # q0 == q1
+        ([(W.RZZ, 0, 5, 0, 0.0)], 1),          # second qubit out of range
+        ([(W.RY, 0, -1, 1, 0.0)], 1),          # param >= n_params
+        ([(W.RY, 0, -1, -2, 0.0)], 1),         # param < -1
+        ([(9, 0, -1, 0, 0.0)], 1),             # unknown kind
+    ]
+    for gates, P in bad:
+        assert _err(B, B.tlq_circuit_create, hctx.h, 2, gates, P) == B.TLQ_EINVAL
+    assert _err(B, B.tlq_circuit_create, hctx.h, 0, ok, 1) == B.TLQ_EINVAL
+
+
+def test_hamiltonian_validation(B, hctx):
+    h = hctx.hamiltonian(3, [(1.0, (0, 1), "ZZ"), (0.5, (2,), "X")])
+    h.close()
+    for terms in ([(1.0, (0, 3), "ZZ")], [(1.0, (0,), "Q")], [(1.0, (1, 1), "ZZ")], [(1.0, (), "")]):
+        assert _err(B, B.tlq_hamiltonian_create, hctx.h, 3, terms) == B.TLQ_EINVAL
+    assert _err(B, B.tlq_hamiltonian_create, hctx.h, 3, []) == B.TLQ_EINVAL
+
+
+def test_host_only_context_refuses_compute(B, hctx):
+    p = W.tfim_n8_L2()
+    c, h = hctx.problem(p)
+    assert _err(B, B.tlq_expectation, hctx.h, c.h, h.h, p.theta) == B.TLQ_EUNSUPPORTED
+    # mismatched qubit counts
+    h2 = hctx.hamiltonian(9, [(1.0, (0,), "Z")])
+    assert _err(B, B.tlq_expectation, hctx.h, c.h, h2.h, p.theta) == B.TLQ_EINVAL
+
+
+@pytest.mark.parametrize("n,L", [(8, 2), (20, 6), (40, 4), (30, 7)])
+def test_planner_exact_cone_widths(B, hctx, n, L):
+    # ZZ terms: 2L sites, X terms: 2L+1 sites, clipped at the chain ends.
+    p = W.tfim_problem(n, L, 1, seed=0)
+    c, h = hctx.problem(p)
+    path, lo, w, ng = B.tlq_plan_info(hctx.h, c.h, h.h, len(p.terms))
+    assert path == B.TLQ_PATH_CONE
+    for t, (_, sites, letters) in enumerate(p.terms):
+        i = sites[0]
+        if letters == "ZZ":
+            want_lo, want_hi = max(0, i - (L - 1)), min(n - 1, i + 1 + (L - 1))
+        else:
+            want_lo, want_hi = max(0, i - L), min(n - 1, i + L)
+        assert (lo[t], lo[t] + w[t] - 1) == (want_lo, want_hi), (t, letters)
+
+
+def test_planner_window_inside_oracle_window(B, hctx):
+    # The oracle's plain gate-by-gate light cone is a superset of the exact cone.
+    from oracle import windows
+    p = W.random_local_problem(16, 3, 1, seed=4)
+    c, h = hctx.problem(p)
+    path, lo, w, ng = B.tlq_plan_info(hctx.h, c.h, h.h, len(p.terms))
+    assert path == B.TLQ_PATH_CONE
+    for t, (_, sites, _) in enumerate(p.terms):
+        qubits, keep = windows.cone(p.gates, sites)
+        assert min(qubits) <= lo[t] and lo[t] + w[t] - 1 <= max(qubits)
+        assert ng[t] <= len(keep)
+
+
+def test_non_local_circuit_goes_dense(B, hctx):
+    p = W.qaoa_problem(10, 2, 1, seed=0)
+    c, h = hctx.problem(p)
+    path, *_ = B.tlq_plan_info(hctx.h, c.h, h.h, len(p.terms))
+    assert path == B.TLQ_PATH_DENSE
