@@ -231,7 +231,8 @@ def main():
     E_d = torch.empty(Bsz, dtype=torch.float64, device=dev)
     G_d = torch.empty(Bsz, P, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)       # a real stream handle (the legacy default is 0)
+    torch.cuda.set_stream(stream)
     B.tlq_profile_enable(ctx.h, True)
 
     def step():

@@ -158,6 +158,12 @@ tlq_status ensure_worklist(Context* ctx, PlanEntry& pe, const Circuit& c, int B,
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Bytes of one CTA's global-memory cone states (padded psi, and lam for gradients).
+static size_t global_slot_bytes(int W, bool fp64, bool grad) {
+    const size_t amps = ((size_t)1 << W) + ((size_t)1 << (W - 3));
+    return align256(amps * (fp64 ? 16 : 8) * (grad ? 2 : 1));
+}
+
 static int global_grid(const PlanEntry& pe, int sm_count) {
     const int ng = pe.n_chunks - pe.n_chunks_smem;
     return std::max(0, std::min(ng, sm_count));
@@ -170,7 +176,7 @@ size_t cone_workspace_bytes(const PlanEntry& pe, const Circuit& c, int B, bool f
     s += align256((size_t)B * c.gates.size() * r2);
     s += align256((size_t)B * P.cones.size() * sizeof(double));
     if (grad) s += align256((size_t)B * std::max<int32_t>(1, P.n_slots) * sizeof(double));
-    if (g_grid > 0) s += align256((size_t)g_grid * ((size_t)1 << pe.g_maxW) * r2 * (grad ? 2 : 1));
+    if (g_grid > 0) s += align256((size_t)g_grid * global_slot_bytes(pe.g_maxW, fp64, grad));
     return s + 1024;
 }
 
@@ -218,7 +224,7 @@ tlq_status run_device(Context* ctx, Circuit* c, Ham* h, const double* theta_dev,
     L.e_part = (double*)ws->take((size_t)B * P.cones.size() * sizeof(double));
     L.g_part = grad ? (double*)ws->take((size_t)B * std::max<int32_t>(1, P.n_slots) * sizeof(double)) : nullptr;
     L.g_grid = g_grid;
-    L.gscratch_slot = g_grid > 0 ? ((size_t)1 << pe->g_maxW) * r2 * (grad ? 2 : 1) : 0;
+    L.gscratch_slot = g_grid > 0 ? global_slot_bytes(pe->g_maxW, fp64, grad) : 0;
     L.gscratch = g_grid > 0 ? ws->take((size_t)g_grid * L.gscratch_slot) : nullptr;
     L.counters = ctx->d_counters;
     L.err = ctx->d_err;

@@ -32,46 +32,53 @@ template <typename real> struct R2;
 template <> struct R2<float> { using T = float2; };
 template <> struct R2<double> { using T = double2; };
 
-// Bank-conflict-free placement of amplitude a: XOR the low 4 index bits with bits 4..7.
-// For every pass (registers on bits [s, s+4) with s = 0 or s >= 4) the 16 lanes of a
-// half-warp (8-byte words) or 8 lanes of a quarter-warp (16-byte words) then hit distinct
-// banks. It is a bijection on [0, 2^W).
-__host__ __device__ __forceinline__ int swz(int a) { return a ^ ((a >> 4) & 15); }
+// Shared-memory placement of amplitude a: two padding slots after every 16 amplitudes,
+// P(a) = a + 2*floor(a/16). A pass holds 16 amplitudes per thread on window bits
+// [s, s+4). For s = 0 a thread's 16 amplitudes are contiguous (vector loads) and
+// consecutive threads start 18 slots apart, so the 8 lanes of a 128-bit phase hit distinct
+// banks; for s >= 4 the 16 lanes of a half-warp read consecutive slots. In both cases
+// amplitude j of a thread sits at P(base) + j * stride, stride = 1 (s = 0) or
+// 2^s + 2^(s-3) (s >= 4), so addressing costs one add per amplitude.
+__host__ __device__ __forceinline__ int pad16(int a) { return a + ((a >> 4) << 1); }
+__host__ __device__ __forceinline__ int padded_amps(int W) { return (1 << W) + (1 << (W - 3)); }
+__host__ __device__ __forceinline__ int pass_stride(int s) { return s == 0 ? 1 : (1 << s) + (1 << (s - 3)); }
 
 // ---- per-team shared-memory layout ----------------------------------------------------
+//
+// [psi][lam] padded states (shared tier only), the diagonal phase table (chunk 0: the
+// low 7 window bits, padded by one entry per 16; chunk 1: bits 7..13 plus the crossing
+// bit 6; chunk 2: bits 14.. plus crossing bit 13), two layer-info buffers (rotation
+// (c, s), kind and gradient slot per window qubit; alternating by layer) and the
+// double-buffered per-warp gradient partials.
 
 struct TeamLayout {
-    int psi, lam, tab, cs, kinds, rslot, red, bytes;
-    int nch;            // phase-table chunks
-    int tab_off[3];     // entry offsets of the chunk tables
+    int psi, lam, tab, info, red, bytes;
+    int tab1, tab2;     // entry offsets of chunk tables 1 and 2
+    int tab_entries;    // total table entries (unpadded) built per layer
 };
 
 __host__ __device__ inline int nwarps_of(int tt) { return tt >= 32 ? tt / 32 : 1; }
+__host__ __device__ inline int info_bytes(int real_bytes) { return 32 * 2 * real_bytes + 64 * 4; }
 
 __host__ __device__ inline TeamLayout team_layout(int W, int tt, int real_bytes, bool grad, bool smem_state) {
     TeamLayout L{};
     const int r2 = 2 * real_bytes;
     int off = 0;
     L.psi = off;
-    if (smem_state) off += (1 << W) * r2;
+    if (smem_state) off += padded_amps(W) * r2;
     L.lam = off;
-    if (smem_state && grad) off += (1 << W) * r2;
-    L.nch = (W + 6) / 7;
-    int ent = 0;
-    for (int c = 0; c < L.nch; ++c) {
-        int bc = (W - 7 * c) < 7 ? (W - 7 * c) : 7;
-        L.tab_off[c] = ent;
-        ent += c == 0 ? (1 << bc) : (1 << (bc + 1));
-    }
+    if (smem_state && grad) off += padded_amps(W) * r2;
+    const int b1 = (W - 7) < 7 ? (W - 7) : 7;
+    const int b2 = W > 14 ? W - 14 : 0;
+    L.tab1 = 136;
+    L.tab2 = L.tab1 + (1 << (b1 + 1));
+    const int slots = L.tab2 + (b2 > 0 ? (1 << (b2 + 1)) : 0);
+    L.tab_entries = 128 + (1 << (b1 + 1)) + (b2 > 0 ? (1 << (b2 + 1)) : 0);
     L.tab = off;
-    off += ent * r2;
-    L.cs = off;
-    off += 32 * r2;
-    L.kinds = off;
-    off += 32 * 4;
-    L.rslot = off;
-    off += 32 * 4;
+    off += slots * r2;
     off = (off + 15) & ~15;
+    L.info = off;
+    off += 2 * info_bytes(real_bytes);
     L.red = off;
     off += 2 * kMaxPassSlots * nwarps_of(tt) * real_bytes;
     L.bytes = (off + 15) & ~15;
@@ -113,13 +120,53 @@ __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
     return r;
 }
 
+template <typename T2>
+__device__ __forceinline__ void load16(T2 (&v)[16], const T2* p, int stride) {
+    if (stride == 1) {
+        if constexpr (sizeof(T2) == 8) {
+            const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float4 t = q[i];
+                v[2 * i].x = t.x;
+                v[2 * i].y = t.y;
+                v[2 * i + 1].x = t.z;
+                v[2 * i + 1].y = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = p[j];
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = p[j * stride];
+    }
+}
+
+template <typename T2>
+__device__ __forceinline__ void store16(const T2 (&v)[16], T2* p, int stride) {
+    if (stride == 1) {
+        if constexpr (sizeof(T2) == 8) {
+            float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) p[j] = v[j];
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) p[j * stride] = v[j];
+    }
+}
+
 // RY(a) on register bit K: [[c,-s],[s,c]] on (amp with bit 0, amp with bit 1).
 template <int K, typename T2, typename real>
 __device__ __forceinline__ void apply_ry(T2 (&v)[16], real c, real s) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
         if (j & (1 << K)) continue;
-        T2 a0 = v[j], a1 = v[j | (1 << K)];
+        const T2 a0 = v[j], a1 = v[j | (1 << K)];
         v[j].x = c * a0.x - s * a1.x;
         v[j].y = c * a0.y - s * a1.y;
         v[j | (1 << K)].x = s * a0.x + c * a1.x;
@@ -133,7 +180,7 @@ __device__ __forceinline__ void apply_rx(T2 (&v)[16], real c, real s) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
         if (j & (1 << K)) continue;
-        T2 a0 = v[j], a1 = v[j | (1 << K)];
+        const T2 a0 = v[j], a1 = v[j | (1 << K)];
         v[j].x = c * a0.x + s * a1.y;
         v[j].y = c * a0.y - s * a1.x;
         v[j | (1 << K)].x = c * a1.x + s * a0.y;
@@ -147,37 +194,61 @@ __device__ __forceinline__ void apply_rot(T2 (&v)[16], int kind, real c, real s)
     else apply_rx<K>(v, c, s);
 }
 
-// Im <lam| G |psi> over the pairs of register bit K, G = Y (RY) or X (RX).
+// Im <lam| Y |psi> over the pairs of register bit K (Y|0> = i|1>, Y|1> = -i|0>):
+// sum over pairs of Re(conj(l1) p0) - Re(conj(l0) p1).
 template <int K, typename T2, typename real>
-__device__ __forceinline__ real grad_rot(const T2 (&p)[16], const T2 (&l)[16], int kind) {
+__device__ __forceinline__ real grad_y(const T2 (&p)[16], const T2 (&l)[16]) {
     real acc = 0;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
         if (j & (1 << K)) continue;
         const T2 p0 = p[j], p1 = p[j | (1 << K)], l0 = l[j], l1 = l[j | (1 << K)];
-        if (kind == TLQ_RY) {
-            // Y|0> = i|1>, Y|1> = -i|0>: Im<l|Y p> = Re(conj(l1) p0) - Re(conj(l0) p1)
-            acc += (l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y);
-        } else {
-            // Im<l|X p> = Im(conj(l0) p1 + conj(l1) p0)
-            acc += (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
-        }
+        acc += (l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y);
     }
     return acc;
 }
 
-// Diagonal phase of window index x: product of the per-chunk table entries.
-template <typename T2>
-__device__ __forceinline__ T2 phase_of(const T2* tab, const TeamLayout& TL, int W, int x) {
-    T2 ph = tab[x & 127];
-    if (W > 7) {
+// Im <lam| X |psi> = sum over pairs of Im(conj(l0) p1 + conj(l1) p0).
+template <int K, typename T2, typename real>
+__device__ __forceinline__ real grad_x(const T2 (&p)[16], const T2 (&l)[16]) {
+    real acc = 0;
 #pragma unroll
-        for (int c = 1; c < 3; ++c) {
-            if (c >= TL.nch) break;
-            const int bc = (W - 7 * c) < 7 ? (W - 7 * c) : 7;
-            const int idx = ((x >> (7 * c)) & ((1 << bc) - 1)) | (((x >> (7 * c - 1)) & 1) << bc);
-            ph = cmul(ph, tab[TL.tab_off[c] + idx]);
-        }
+    for (int j = 0; j < 16; ++j) {
+        if (j & (1 << K)) continue;
+        const T2 p0 = p[j], p1 = p[j | (1 << K)], l0 = l[j], l1 = l[j | (1 << K)];
+        acc += (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
+    }
+    return acc;
+}
+
+// Adjoint step of one rotation on register bit K: gradient, then un-apply on psi and lam.
+template <int K, typename T2, typename real>
+__device__ __forceinline__ real adjoint_rot(T2 (&p)[16], T2 (&l)[16], int kind, real c, real s_neg) {
+    real g;
+    if (kind == TLQ_RY) {
+        g = grad_y<K, T2, real>(p, l);
+        apply_ry<K>(p, c, s_neg);
+        apply_ry<K>(l, c, s_neg);
+    } else {
+        g = grad_x<K, T2, real>(p, l);
+        apply_rx<K>(p, c, s_neg);
+        apply_rx<K>(l, c, s_neg);
+    }
+    return g;
+}
+
+// Diagonal phase of window index x: the product of the chunk-table entries.
+template <typename T2>
+__device__ __forceinline__ T2 phase_of(const T2* tab, int tab1, int tab2, int W, int x) {
+    const int t0 = x & 127;
+    T2 ph = tab[t0 + (t0 >> 4)];
+    const int b1 = (W - 7) < 7 ? (W - 7) : 7;
+    const int i1 = ((x >> 7) & ((1 << b1) - 1)) | (((x >> 6) & 1) << b1);
+    ph = cmul(ph, tab[tab1 + i1]);
+    if (W > 14) {
+        const int b2 = W - 14;
+        const int i2 = ((x >> 14) & ((1 << b2) - 1)) | (((x >> 13) & 1) << b2);
+        ph = cmul(ph, tab[tab2 + i2]);
     }
     return ph;
 }
@@ -200,41 +271,64 @@ struct ConeArgs {
     size_t gscratch_slot;
 };
 
-// Stage one layer's rotation parameters and build its diagonal phase table (conjugated
-// for the adjoint direction). Returns the live-group mask (bit g: window bits [4g,4g+4)).
+template <typename T2>
+struct TeamMem {
+    T2* psi;
+    T2* lam;
+    T2* tab;
+    unsigned char* info;   // two buffers of info_bytes
+    void* red;
+    int tab1, tab2, tab_entries, W;
+};
+
+template <typename T2>
+__device__ __forceinline__ T2* info_cs(const TeamMem<T2>& M, int par) {
+    return reinterpret_cast<T2*>(M.info + par * info_bytes((int)sizeof(T2) / 2));
+}
+template <typename T2>
+__device__ __forceinline__ int* info_kinds(const TeamMem<T2>& M, int par) {
+    return reinterpret_cast<int*>(M.info + par * info_bytes((int)sizeof(T2) / 2) + 32 * sizeof(T2));
+}
+template <typename T2>
+__device__ __forceinline__ int* info_rslot(const TeamMem<T2>& M, int par) {
+    return info_kinds(M, par) + 32;
+}
+
+// Stage one layer: rotation parameters per window qubit into info buffer `par`, and the
+// diagonal phase table (conjugated for the adjoint direction). Ends with a team barrier.
 template <typename real, typename T2>
-__device__ unsigned stage_layer(const int32_t* lp, int W, const T2* GT, const Team& tm, const TeamLayout& TL,
-                                unsigned char* tb, bool conj_phase) {
-    T2* cs = reinterpret_cast<T2*>(tb + TL.cs);
-    int* kinds = reinterpret_cast<int*>(tb + TL.kinds);
-    int* rslot = reinterpret_cast<int*>(tb + TL.rslot);
-    T2* tab = reinterpret_cast<T2*>(tb + TL.tab);
+__device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, const TeamMem<T2>& M, int par,
+                            bool conj_phase) {
+    const int W = M.W;
+    T2* cs = info_cs(M, par);
+    int* kinds = info_kinds(M, par);
+    int* rslot = info_rslot(M, par);
     const int nrot = lp[0], ndiag = lp[1];
     const int32_t* rot = lp + 2;
     const int32_t* dg = rot + 3 * nrot;
-    tm.sync();   // previous users of cs/kinds/rslot/tab are done
-    for (int j = tm.tid; j < 32; j += tm.tt) kinds[j] = -1;
-    tm.sync();
-    for (int k = tm.tid; k < nrot; k += tm.tt) {
-        const int w0 = rot[3 * k];
-        const int j = w0 & 255;
-        kinds[j] = w0 >> 8;
-        T2 v = GT[rot[3 * k + 1]];
-        cs[j] = v;
-        rslot[j] = rot[3 * k + 2];
+    for (int j = tm.tid; j < W; j += tm.tt) {
+        int kk = -1;
+        for (int k = 0; k < nrot; ++k)
+            if ((rot[3 * k] & 255) == j) kk = k;
+        if (kk >= 0) {
+            kinds[j] = rot[3 * kk] >> 8;
+            cs[j] = GT[rot[3 * kk + 1]];
+            rslot[j] = rot[3 * kk + 2];
+        } else {
+            kinds[j] = -1;
+        }
     }
     if (ndiag > 0) {
-        int total = TL.nch == 1 ? (1 << W) : 0;
-        if (TL.nch > 1) {
-            const int bl = (W - 7 * (TL.nch - 1));
-            total = TL.tab_off[TL.nch - 1] + (1 << (bl + 1));
-        }
-        for (int e = tm.tid; e < total; e += tm.tt) {
-            int c = 0;
-            while (c + 1 < TL.nch && e >= TL.tab_off[c + 1]) ++c;
-            const int idx = e - TL.tab_off[c];
-            const int lo = 7 * c;
-            const int bc = (W - lo) < 7 ? (W - lo) : 7;
+        const int b1 = (W - 7) < 7 ? (W - 7) : 7;
+        for (int e = tm.tid; e < M.tab_entries; e += tm.tt) {
+            int lo, bc, idx, slot;
+            if (e < 128) {
+                lo = 0; bc = 7; idx = e; slot = e + (e >> 4);
+            } else if (e < 128 + (2 << b1)) {
+                lo = 7; bc = b1; idx = e - 128; slot = M.tab1 + idx;
+            } else {
+                lo = 14; bc = W - 14; idx = e - 128 - (2 << b1); slot = M.tab2 + idx;
+            }
             T2 ph;
             ph.x = 1;
             ph.y = 0;
@@ -244,83 +338,73 @@ __device__ unsigned stage_layer(const int32_t* lp, int W, const T2* GT, const Te
                 const bool two = (kind != TLQ_RZ);
                 const int own = two ? j1 : j0;
                 if (own < lo || own >= lo + bc) continue;
-                auto bit_of = [&](int q) -> int {
-                    if (q >= lo) return (idx >> (q - lo)) & 1;
-                    return (idx >> bc) & 1;   // q == lo - 1, the crossing bit
-                };
+                const int bit0 = j0 >= lo ? (idx >> (j0 - lo)) & 1 : (idx >> bc) & 1;
                 if (kind == TLQ_CZ) {
-                    if (bit_of(j0) & bit_of(j1)) { ph.x = -ph.x; ph.y = -ph.y; }
+                    const int bit1 = (idx >> (j1 - lo)) & 1;
+                    if (bit0 & bit1) { ph.x = -ph.x; ph.y = -ph.y; }
                     continue;
                 }
                 const T2 g = GT[dg[3 * k + 1]];
-                const int odd = two ? (bit_of(j0) ^ bit_of(j1)) : bit_of(j0);
+                const int odd = two ? (bit0 ^ ((idx >> (j1 - lo)) & 1)) : bit0;
                 T2 f;
                 f.x = g.x;
-                f.y = odd ? g.y : -g.y;   // exp(-i a z/2): z = +1 -> e^{-ia/2}
+                f.y = odd ? g.y : -g.y;   // exp(-i a z / 2) with z = +1 for bit 0
                 ph = cmul(ph, f);
             }
             if (conj_phase) ph.y = -ph.y;
-            tab[e] = ph;
+            M.tab[slot] = ph;
         }
     }
     tm.sync();
-    unsigned live = 0;
-    for (int g = 0; 4 * g < W; ++g) {
-        bool any = false;
-        for (int q = 4 * g; q < 4 * g + 4 && q < W; ++q) any |= kinds[q] >= 0;
-        if (any) live |= 1u << g;
-    }
-    return live;
 }
 
-// Forward pass over register bits [s, s+4): rotations on `apply` bits, then the
-// diagonal phase when `diag`.
+// Forward pass on register bits [s, s+4): rotations on the bits in `m`, then the
+// layer's diagonal phase when `diag`.
 template <typename real, typename T2>
-__device__ void pass_fwd(T2* psi, int W, int s, unsigned apply, bool diag, const Team& tm, const TeamLayout& TL,
-                         unsigned char* tb) {
-    const T2* cs = reinterpret_cast<const T2*>(tb + TL.cs);
-    const int* kinds = reinterpret_cast<const int*>(tb + TL.kinds);
-    const T2* tab = reinterpret_cast<const T2*>(tb + TL.tab);
+__device__ void pass_fwd(T2* psi, int s, unsigned m, bool diag, const Team& tm, const TeamMem<T2>& M, int par) {
+    const int W = M.W;
+    const T2* cs = info_cs(M, par);
+    const int* kinds = info_kinds(M, par);
     int kd[4];
     real c[4], sn[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        kd[k] = (apply >> k) & 1 ? kinds[s + k] : -1;
-        T2 v = cs[s + k];
+        kd[k] = (m >> k) & 1 ? kinds[s + k] : -1;
+        const T2 v = cs[s + k];
         c[k] = v.x;
         sn[k] = v.y;
     }
     const int nout = 1 << (W - 4);
     const int lowmask = (1 << s) - 1;
+    const int stride = pass_stride(s);
     for (int o = tm.tid; o < nout; o += tm.tt) {
         const int base = (o & lowmask) | ((o >> s) << (s + 4));
+        T2* p = psi + pad16(base);
         T2 v[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = psi[swz(base | (j << s))];
+        load16(v, p, stride);
         if (kd[0] >= 0) apply_rot<0>(v, kd[0], c[0], sn[0]);
         if (kd[1] >= 0) apply_rot<1>(v, kd[1], c[1], sn[1]);
         if (kd[2] >= 0) apply_rot<2>(v, kd[2], c[2], sn[2]);
         if (kd[3] >= 0) apply_rot<3>(v, kd[3], c[3], sn[3]);
         if (diag) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = cmul(v[j], phase_of(tab, TL, W, base | (j << s)));
+            for (int j = 0; j < 16; ++j) v[j] = cmul(v[j], phase_of(M.tab, M.tab1, M.tab2, W, base | (j << s)));
         }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) psi[swz(base | (j << s))] = v[j];
+        store16(v, p, stride);
     }
 }
 
-// Adjoint pass over register bits [s, s+4): when `diag`, emit Im<lam|Z..|psi> for the
-// layer's parametrised diagonal gates and un-apply the diagonal; then for each rotation
-// on `apply` bits emit Im<lam|G|psi> and un-apply it from psi and lam.
-// Per-warp partial sums go to red[slot * nw + warp]: slots 0..3 rotations (register bit),
-// slots 4.. diagonal gates in program order.
+// Adjoint pass on register bits [s, s+4): when `diag`, emit Im<lam|Z..|psi> for the layer's
+// parametrised diagonal gates and un-apply the diagonal; then for each rotation on the bits
+// in `m`, emit Im<lam|G|psi> and un-apply it from psi and lam. Per-warp partial sums go to
+// red[slot * nw + warp]: slots 0..3 rotations (register bit), 4.. diagonal gates in program
+// order.
 template <typename real, typename T2>
-__device__ void pass_bwd(T2* psi, T2* lam, int W, int s, unsigned apply, bool diag, const int32_t* dg, int ndiag,
-                         const Team& tm, const TeamLayout& TL, unsigned char* tb, real* red) {
-    const T2* cs = reinterpret_cast<const T2*>(tb + TL.cs);
-    const int* kinds = reinterpret_cast<const int*>(tb + TL.kinds);
-    const T2* tab = reinterpret_cast<const T2*>(tb + TL.tab);
+__device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, bool diag, const int32_t* dg, int ndiag,
+                         const Team& tm, const TeamMem<T2>& M, int par, real* red) {
+    const int W = M.W;
+    const T2* cs = info_cs(M, par);
+    const int* kinds = info_kinds(M, par);
     const int nw = nwarps_of(tm.tt);
     const int warp = tm.tt >= 32 ? (tm.tid >> 5) : 0;
     const bool leader = tm.tt >= 32 ? ((tm.tid & 31) == 0) : (tm.tid == 0);
@@ -328,67 +412,55 @@ __device__ void pass_bwd(T2* psi, T2* lam, int W, int s, unsigned apply, bool di
     real c[4], sn[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        kd[k] = (apply >> k) & 1 ? kinds[s + k] : -1;
-        T2 v = cs[s + k];
+        kd[k] = (m >> k) & 1 ? kinds[s + k] : -1;
+        const T2 v = cs[s + k];
         c[k] = v.x;
         sn[k] = -v.y;   // un-apply: angle -> -angle
     }
     const int nout = 1 << (W - 4);
     const int lowmask = (1 << s) - 1;
+    const int stride = pass_stride(s);
     bool first = true;
-    for (int o = tm.tid; o < nout || (first && o - tm.tid < nout); o += tm.tt) {
-        // every team thread takes part in the reductions, even without an amplitude block
-        const bool has = o < nout;
-        const int base = has ? ((o & lowmask) | ((o >> s) << (s + 4))) : 0;
+    for (int o = tm.tid; o < nout; o += tm.tt) {
+        const int base = (o & lowmask) | ((o >> s) << (s + 4));
+        T2* pp = psi + pad16(base);
+        T2* lp = lam + pad16(base);
         T2 p[16], l[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            if (has) {
-                p[j] = psi[swz(base | (j << s))];
-                l[j] = lam[swz(base | (j << s))];
-            } else {
-                p[j].x = p[j].y = 0;
-                l[j].x = l[j].y = 0;
-            }
-        }
+        load16(p, pp, stride);
+        load16(l, lp, stride);
         if (diag) {
-            // w_x = Im(conj(lam_x) psi_x); dE/da for RZ on q: sum_x z_q(x) w_x; RZZ: z_q0 z_q1 w_x.
-            real S = 0, Sk[4] = {0, 0, 0, 0}, Sp[3] = {0, 0, 0};
+            // w_x = Im(conj(lam_x) psi_x); dE/da is sum_x z_q(x) w_x for RZ on q and
+            // sum_x z_q0(x) z_q1(x) w_x for RZZ on (q0, q1 = q0 + 1).
+            real S = 0, Sk0 = 0, Sk1 = 0, Sk2 = 0, Sk3 = 0, Sp0 = 0, Sp1 = 0, Sp2 = 0;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const real w = l[j].x * p[j].y - l[j].y * p[j].x;
                 S += w;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) Sk[k] += ((j >> k) & 1) ? -w : w;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) Sp[k] += (((j >> k) ^ (j >> (k + 1))) & 1) ? -w : w;
+                Sk0 += (j & 1) ? -w : w;
+                Sk1 += (j & 2) ? -w : w;
+                Sk2 += (j & 4) ? -w : w;
+                Sk3 += (j & 8) ? -w : w;
+                Sp0 += ((j ^ (j >> 1)) & 1) ? -w : w;
+                Sp1 += (((j >> 1) ^ (j >> 2)) & 1) ? -w : w;
+                Sp2 += (((j >> 2) ^ (j >> 3)) & 1) ? -w : w;
             }
             int sl = 4;
             for (int k = 0; k < ndiag; ++k) {
-                const int w0 = dg[3 * k];
                 if (dg[3 * k + 2] < 0) continue;
+                const int w0 = dg[3 * k];
                 const int kind = w0 & 255, j0 = (w0 >> 8) & 255, j1 = (w0 >> 16) & 255;
                 real val;
-                const bool in0 = j0 >= s && j0 < s + 4;
+                const int k0 = j0 - s;
+                const bool in0 = (unsigned)k0 < 4u;
                 if (kind == TLQ_RZ) {
-                    if (in0) {
-                        const int k0 = j0 - s;
-                        val = k0 == 0 ? Sk[0] : k0 == 1 ? Sk[1] : k0 == 2 ? Sk[2] : Sk[3];
-                    } else {
-                        val = ((base >> j0) & 1) ? -S : S;
-                    }
+                    if (in0) val = k0 == 0 ? Sk0 : k0 == 1 ? Sk1 : k0 == 2 ? Sk2 : Sk3;
+                    else val = ((base >> j0) & 1) ? -S : S;
                 } else {   // RZZ on (j0, j1 = j0 + 1)
-                    const bool in1 = j1 >= s && j1 < s + 4;
-                    if (in0 && in1) {
-                        const int k0 = j0 - s;
-                        val = k0 == 0 ? Sp[0] : k0 == 1 ? Sp[1] : Sp[2];
-                    } else if (in0) {   // j0 = s + 3, j1 outside
-                        val = ((base >> j1) & 1) ? -Sk[3] : Sk[3];
-                    } else if (in1) {   // j1 = s, j0 = s - 1 outside
-                        val = ((base >> j0) & 1) ? -Sk[0] : Sk[0];
-                    } else {
-                        val = (((base >> j0) ^ (base >> j1)) & 1) ? -S : S;
-                    }
+                    const bool in1 = (unsigned)(j1 - s) < 4u;
+                    if (in0 && in1) val = k0 == 0 ? Sp0 : k0 == 1 ? Sp1 : Sp2;
+                    else if (in0) val = ((base >> j1) & 1) ? -Sk3 : Sk3;   // j0 = s + 3
+                    else if (in1) val = ((base >> j0) & 1) ? -Sk0 : Sk0;   // j1 = s
+                    else val = (((base >> j0) ^ (base >> j1)) & 1) ? -S : S;
                 }
                 val = team_warp_sum(val, tm);
                 if (leader) {
@@ -399,16 +471,19 @@ __device__ void pass_bwd(T2* psi, T2* lam, int W, int s, unsigned apply, bool di
             }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const T2 ph = phase_of(tab, TL, W, base | (j << s));   // already conjugated
+                const T2 ph = phase_of(M.tab, M.tab1, M.tab2, W, base | (j << s));   // conjugated table
                 p[j] = cmul(p[j], ph);
                 l[j] = cmul(l[j], ph);
             }
         }
-        real gk[4] = {0, 0, 0, 0};
-        if (kd[0] >= 0) { gk[0] = grad_rot<0, T2, real>(p, l, kd[0]); apply_rot<0>(p, kd[0], c[0], sn[0]); apply_rot<0>(l, kd[0], c[0], sn[0]); }
-        if (kd[1] >= 0) { gk[1] = grad_rot<1, T2, real>(p, l, kd[1]); apply_rot<1>(p, kd[1], c[1], sn[1]); apply_rot<1>(l, kd[1], c[1], sn[1]); }
-        if (kd[2] >= 0) { gk[2] = grad_rot<2, T2, real>(p, l, kd[2]); apply_rot<2>(p, kd[2], c[2], sn[2]); apply_rot<2>(l, kd[2], c[2], sn[2]); }
-        if (kd[3] >= 0) { gk[3] = grad_rot<3, T2, real>(p, l, kd[3]); apply_rot<3>(p, kd[3], c[3], sn[3]); apply_rot<3>(l, kd[3], c[3], sn[3]); }
+        real g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+        if (kd[0] >= 0) g0 = adjoint_rot<0, T2, real>(p, l, kd[0], c[0], sn[0]);
+        if (kd[1] >= 0) g1 = adjoint_rot<1, T2, real>(p, l, kd[1], c[1], sn[1]);
+        if (kd[2] >= 0) g2 = adjoint_rot<2, T2, real>(p, l, kd[2], c[2], sn[2]);
+        if (kd[3] >= 0) g3 = adjoint_rot<3, T2, real>(p, l, kd[3], c[3], sn[3]);
+        store16(p, pp, stride);
+        store16(l, lp, stride);
+        const real gk[4] = {g0, g1, g2, g3};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (kd[k] < 0) continue;
@@ -418,24 +493,18 @@ __device__ void pass_bwd(T2* psi, T2* lam, int W, int s, unsigned apply, bool di
                 *dst = first ? val : *dst + val;
             }
         }
-        if (has) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                psi[swz(base | (j << s))] = p[j];
-                lam[swz(base | (j << s))] = l[j];
-            }
-        }
         first = false;
     }
 }
 
-// Sum the per-warp partials of one pass in fixed order and store them as FP64 slots.
-template <typename real>
-__device__ void flush_pass(const real* red, int nw, unsigned apply, int s, const int* kinds, const int* rslot,
+// Sum the per-warp partials of one adjoint pass in fixed order and store them as FP64 slots.
+template <typename real, typename T2>
+__device__ void flush_pass(const real* red, int nw, unsigned m, int s, const TeamMem<T2>& M, int par,
                            const int32_t* dg, int ndiag, bool diag, double* gdst, const Team& tm) {
-    // rotation slots
+    const int* kinds = info_kinds(M, par);
+    const int* rslot = info_rslot(M, par);
     for (int k = tm.tid; k < 4; k += tm.tt) {
-        if (!((apply >> k) & 1) || kinds[s + k] < 0) continue;
+        if (!((m >> k) & 1) || kinds[s + k] < 0) continue;
         const int slot = rslot[s + k];
         if (slot < 0) continue;
         double acc = 0;
@@ -456,9 +525,10 @@ __device__ void flush_pass(const real* red, int nw, unsigned apply, int s, const
     }
 }
 
-// <psi|P|psi> for the cone's Pauli term; when GRAD also lam = P psi.
+// <psi|P|psi> for the cone's Pauli term; when GRAD also lam = P psi. Ends with a barrier.
 template <typename real, typename T2, bool GRAD>
-__device__ double measure(T2* psi, T2* lam, int W, const ConeDev& cd, const Team& tm, real* red) {
+__device__ double measure(const TeamMem<T2>& M, const ConeDev& cd, const Team& tm, real* red) {
+    const int W = M.W;
     const int nout = 1 << (W - 4);
     T2 f0;   // (-i)^ny
     const int ny = cd.ny & 3;
@@ -466,16 +536,20 @@ __device__ double measure(T2* psi, T2* lam, int W, const ConeDev& cd, const Team
     f0.y = ny == 1 ? -1 : ny == 3 ? 1 : 0;
     real acc = 0;
     for (int o = tm.tid; o < nout; o += tm.tt) {
-#pragma unroll 4
+        const int x0 = o << 4;
+        T2 a[16];
+        load16(a, M.psi + pad16(x0), 1);
+        T2 lv[16];
+#pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int x = (o << 4) | j;
-            const T2 a = psi[swz(x)];
-            const T2 v = psi[swz(x ^ (int)cd.flip)];
-            T2 lv = cmul(f0, v);
-            if (__popc((unsigned)x & cd.zy) & 1) { lv.x = -lv.x; lv.y = -lv.y; }
-            if (GRAD) lam[swz(x)] = lv;
-            acc += a.x * lv.x + a.y * lv.y;
+            const int x = x0 | j;
+            const T2 v = M.psi[pad16(x ^ (int)cd.flip)];
+            T2 t = cmul(f0, v);
+            if (__popc((unsigned)x & cd.zy) & 1) { t.x = -t.x; t.y = -t.y; }
+            lv[j] = t;
+            acc += a[j].x * t.x + a[j].y * t.y;
         }
+        if (GRAD) store16(lv, M.lam + pad16(x0), 1);
     }
     acc = team_warp_sum(acc, tm);
     const int nw = nwarps_of(tm.tt);
@@ -494,79 +568,97 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
     using T2 = typename R2<real>::T;
     const ConeDev cd = A.cones[cone_idx];
     const TeamLayout TL = team_layout(W, tm.tt, (int)sizeof(real), GRAD, !GLOBAL);
-    T2* psi;
-    T2* lam;
+    TeamMem<T2> M;
     if (GLOBAL) {
         unsigned char* g = reinterpret_cast<unsigned char*>(A.gscratch) + (size_t)blockIdx.x * A.gscratch_slot;
-        psi = reinterpret_cast<T2*>(g);
-        lam = psi + (1 << W);
+        M.psi = reinterpret_cast<T2*>(g);
+        M.lam = M.psi + padded_amps(W);
     } else {
-        psi = reinterpret_cast<T2*>(tb + TL.psi);
-        lam = reinterpret_cast<T2*>(tb + TL.lam);
+        M.psi = reinterpret_cast<T2*>(tb + TL.psi);
+        M.lam = reinterpret_cast<T2*>(tb + TL.lam);
     }
+    M.tab = reinterpret_cast<T2*>(tb + TL.tab);
+    M.info = tb + TL.info;
+    M.red = tb + TL.red;
+    M.tab1 = TL.tab1;
+    M.tab2 = TL.tab2;
+    M.tab_entries = TL.tab_entries;
+    M.W = W;
     const T2* GT = reinterpret_cast<const T2*>(A.gate_table) + (size_t)b * A.n_gates;
-    real* red = reinterpret_cast<real*>(tb + TL.red);
+    real* red = reinterpret_cast<real*>(M.red);
     const int nw = nwarps_of(tm.tt);
     // |0...0>
-    for (int x = tm.tid; x < (1 << W); x += tm.tt) {
+    for (int x = tm.tid; x < padded_amps(W); x += tm.tt) {
         T2 z;
         z.x = x == 0 ? 1 : 0;
         z.y = 0;
-        psi[x] = z;   // swz(0) == 0
+        M.psi[x] = z;   // pad16(0) == 0
     }
     const int32_t* prog = A.prog + cd.prog_off;
     const int nl = prog[0];
     const int32_t* lofs = prog + 1;
     const int32_t* body = prog + 1 + nl;
+    tm.sync();
     for (int li = 0; li < nl; ++li) {
         const int32_t* lp = body + lofs[li];
-        const int ndiag = lp[1];
-        unsigned live = stage_layer<real, T2>(lp, W, GT, tm, TL, tb, false);
-        int last = -1;
-        for (int g = 0; 4 * g < W; ++g) if ((live >> g) & 1) last = g;
-        if (last < 0 && ndiag > 0) { live = 1; last = 0; }
-        for (int g = 0; g <= last; ++g) {
-            if (!((live >> g) & 1)) continue;
-            const int s = 4 * g < W - 4 ? 4 * g : W - 4;
-            unsigned apply = 0;
-            for (int k = 0; k < 4; ++k) {
-                const int q = s + k;
-                if (q >= 4 * g && q < 4 * g + 4) apply |= 1u << k;
+        const int nrot = lp[0], ndiag = lp[1];
+        const int par = li & 1;
+        unsigned todo = 0;
+        for (int k = 0; k < nrot; ++k) todo |= 1u << (lp[2 + 3 * k] & 255);
+        stage_layer<real, T2>(lp, GT, tm, M, par, false);
+        bool first = true;
+        while (todo || (first && ndiag > 0)) {
+            int s;
+            unsigned m;
+            if (todo) {
+                const int bt = __ffs(todo) - 1;
+                s = bt < 4 ? 0 : (bt < W - 4 ? bt : W - 4);
+                m = (todo >> s) & 15u;
+                todo &= ~(15u << s);
+            } else {
+                s = W - 4;
+                m = 0;
             }
-            pass_fwd<real, T2>(psi, W, s, apply, g == last && ndiag > 0, tm, TL, tb);
+            pass_fwd<real, T2>(M.psi, s, m, todo == 0 && ndiag > 0, tm, M, par);
             tm.sync();
+            first = false;
         }
     }
-    const double e = measure<real, T2, GRAD>(psi, lam, W, cd, tm, red);
+    const double e = measure<real, T2, GRAD>(M, cd, tm, red);
     if (tm.tid == 0) A.e_part[(size_t)b * A.n_terms + cd.term] = e;
     if (!GRAD) return;
-    tm.sync();
     double* gdst = A.g_part + (size_t)b * A.n_slots + cd.slot_off;
-    const int* kinds = reinterpret_cast<const int*>(tb + TL.kinds);
-    const int* rslot = reinterpret_cast<const int*>(tb + TL.rslot);
-    int parity = 0;
+    int rpar = 0;
     for (int li = nl - 1; li >= 0; --li) {
         const int32_t* lp = body + lofs[li];
         const int nrot = lp[0], ndiag = lp[1];
         const int32_t* dg = lp + 2 + 3 * nrot;
-        unsigned live = stage_layer<real, T2>(lp, W, GT, tm, TL, tb, true);
-        int first = -1;
-        for (int g = 0; 4 * g < W; ++g) if ((live >> g) & 1) { first = g; break; }
-        if (first < 0 && ndiag > 0) { live = 1; first = 0; }
-        for (int g = first; g >= 0 && 4 * g < W; ++g) {
-            if (!((live >> g) & 1)) continue;
-            const int s = 4 * g < W - 4 ? 4 * g : W - 4;
-            unsigned apply = 0;
-            for (int k = 0; k < 4; ++k) {
-                const int q = s + k;
-                if (q >= 4 * g && q < 4 * g + 4) apply |= 1u << k;
+        const int par = li & 1;
+        unsigned todo = 0;
+        for (int k = 0; k < nrot; ++k) todo |= 1u << (lp[2 + 3 * k] & 255);
+        stage_layer<real, T2>(lp, GT, tm, M, par, true);
+        bool first = true;
+        while (todo || (first && ndiag > 0)) {
+            int s;
+            unsigned m;
+            if (todo) {
+                const int bt = 31 - __clz(todo);
+                s = bt - 3;
+                if (s < 4) s = bt >= 4 ? 4 : 0;
+                if (s > W - 4) s = W - 4;
+                m = (todo >> s) & 15u;
+                todo &= ~(15u << s);
+            } else {
+                s = W - 4;
+                m = 0;
             }
-            real* rb = red + parity * kMaxPassSlots * nw;
-            const bool dpass = (g == first) && ndiag > 0;
-            pass_bwd<real, T2>(psi, lam, W, s, apply, dpass, dg, ndiag, tm, TL, tb, rb);
+            real* rb = red + rpar * kMaxPassSlots * nw;
+            const bool dpass = first && ndiag > 0;
+            pass_bwd<real, T2>(M.psi, M.lam, s, m, dpass, dg, ndiag, tm, M, par, rb);
             tm.sync();
-            flush_pass<real>(rb, nw, apply, s, kinds, rslot, dg, ndiag, dpass, gdst, tm);
-            parity ^= 1;
+            flush_pass<real, T2>(rb, nw, m, s, M, par, dg, ndiag, dpass, gdst, tm);
+            rpar ^= 1;
+            first = false;
         }
     }
 }
@@ -584,12 +676,12 @@ __global__ void __launch_bounds__(kCtaThreads, 1) cone_kernel(ConeArgs A) {
         const ChunkDev ch = A.chunks[c];
         const int tt = ch.tt;
         const int team = threadIdx.x / tt;
-        const int nteams = kCtaThreads / tt;
-        if (ch.W < kMinConeW || ch.W > kMaxConeW || tt < 16 || (!GLOBAL && (1 << (ch.W - 4)) != tt && tt != kCtaThreads)) {
+        if (ch.W < kMinConeW || ch.W > kMaxConeW || tt < 16 || tt > kCtaThreads ||
+            (!GLOBAL && (1 << (ch.W - 4)) != tt)) {
             if (threadIdx.x == 0) atomicOr(A.err, 1);
             continue;
         }
-        if (team < ch.count && team < nteams) {
+        if (team < ch.count) {
             Team tm;
             tm.tid = threadIdx.x - team * tt;
             tm.tt = tt;
