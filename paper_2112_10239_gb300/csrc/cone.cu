@@ -58,7 +58,7 @@ struct TeamLayout {
 };
 
 __host__ __device__ inline int nwarps_of(int tt) { return tt >= 32 ? tt / 32 : 1; }
-__host__ __device__ inline int info_bytes(int real_bytes) { return 32 * 2 * real_bytes + 64 * 4; }
+__host__ __device__ inline int info_bytes(int real_bytes) { return 32 * 2 * real_bytes + 4 * 32 * 4; }
 
 __host__ __device__ inline TeamLayout team_layout(int W, int tt, int real_bytes, bool grad, bool smem_state) {
     TeamLayout L{};
@@ -105,8 +105,12 @@ struct Team {
 
 template <typename real>
 __device__ __forceinline__ real team_warp_sum(real v, const Team& tm) {
-    const int top = tm.tt < 32 ? tm.tt : 32;
-    for (int off = top >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(tm.mask, v, off);
+    if (tm.tt >= 32) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    } else {
+        for (int off = tm.tt >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(tm.mask, v, off);
+    }
     return v;
 }
 
@@ -293,9 +297,19 @@ template <typename T2>
 __device__ __forceinline__ int* info_rslot(const TeamMem<T2>& M, int par) {
     return info_kinds(M, par) + 32;
 }
+template <typename T2>
+__device__ __forceinline__ int* info_zslot(const TeamMem<T2>& M, int par) {
+    return info_kinds(M, par) + 64;
+}
+template <typename T2>
+__device__ __forceinline__ int* info_pslot(const TeamMem<T2>& M, int par) {
+    return info_kinds(M, par) + 96;
+}
 
-// Stage one layer: rotation parameters per window qubit into info buffer `par`, and the
-// diagonal phase table (conjugated for the adjoint direction). Ends with a team barrier.
+// Stage one layer from its per-qubit records: rotation parameters and gradient slots into
+// info buffer `par`, and the diagonal phase table (conjugated for the adjoint direction).
+// A table entry is the product of the RZ factors of its chunk's qubits and the RZZ/CZ
+// factors of the pairs whose upper qubit lies in the chunk. Ends with a team barrier.
 template <typename real, typename T2>
 __device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, const TeamMem<T2>& M, int par,
                             bool conj_phase) {
@@ -303,22 +317,20 @@ __device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, con
     T2* cs = info_cs(M, par);
     int* kinds = info_kinds(M, par);
     int* rslot = info_rslot(M, par);
-    const int nrot = lp[0], ndiag = lp[1];
-    const int32_t* rot = lp + 2;
-    const int32_t* dg = rot + 3 * nrot;
+    int* zslot = info_zslot(M, par);
+    int* pslot = info_pslot(M, par);
+    const int has_diag = lp[0];
+    const int32_t* R = lp + kLayerHeader;
     for (int j = tm.tid; j < W; j += tm.tt) {
-        int kk = -1;
-        for (int k = 0; k < nrot; ++k)
-            if ((rot[3 * k] & 255) == j) kk = k;
-        if (kk >= 0) {
-            kinds[j] = rot[3 * kk] >> 8;
-            cs[j] = GT[rot[3 * kk + 1]];
-            rslot[j] = rot[3 * kk + 2];
-        } else {
-            kinds[j] = -1;
-        }
+        const int32_t* r = R + j * kRecWords;
+        const int rg = r[0];
+        kinds[j] = rg >= 0 ? (r[1] & 255) : -1;
+        if (rg >= 0) cs[j] = GT[rg];
+        rslot[j] = (r[1] >> 8) - 1;
+        zslot[j] = r[3];
+        pslot[j] = (r[5] >> 8) - 1;
     }
-    if (ndiag > 0) {
+    if (has_diag) {
         const int b1 = (W - 7) < 7 ? (W - 7) : 7;
         for (int e = tm.tid; e < M.tab_entries; e += tm.tt) {
             int lo, bc, idx, slot;
@@ -332,24 +344,33 @@ __device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, con
             T2 ph;
             ph.x = 1;
             ph.y = 0;
-            for (int k = 0; k < ndiag; ++k) {
-                const int w0 = dg[3 * k];
-                const int kind = w0 & 255, j0 = (w0 >> 8) & 255, j1 = (w0 >> 16) & 255;
-                const bool two = (kind != TLQ_RZ);
-                const int own = two ? j1 : j0;
-                if (own < lo || own >= lo + bc) continue;
-                const int bit0 = j0 >= lo ? (idx >> (j0 - lo)) & 1 : (idx >> bc) & 1;
-                if (kind == TLQ_CZ) {
-                    const int bit1 = (idx >> (j1 - lo)) & 1;
-                    if (bit0 & bit1) { ph.x = -ph.x; ph.y = -ph.y; }
-                    continue;
+            int prev = lo > 0 ? (idx >> bc) & 1 : 0;   // bit of qubit lo - 1 (crossing bit)
+            for (int k = 0; k < bc; ++k) {
+                const int q = lo + k;
+                const int bq = (idx >> k) & 1;
+                const int32_t* r = R + q * kRecWords;
+                if (r[2] >= 0) {   // RZ(a) on q: e^{-ia/2} for bit 0, e^{+ia/2} for bit 1
+                    const T2 g = GT[r[2]];
+                    T2 f;
+                    f.x = g.x;
+                    f.y = bq ? g.y : -g.y;
+                    ph = cmul(ph, f);
                 }
-                const T2 g = GT[dg[3 * k + 1]];
-                const int odd = two ? (bit0 ^ ((idx >> (j1 - lo)) & 1)) : bit0;
-                T2 f;
-                f.x = g.x;
-                f.y = odd ? g.y : -g.y;   // exp(-i a z / 2) with z = +1 for bit 0
-                ph = cmul(ph, f);
+                if (q > 0) {
+                    const int32_t* rp = r - kRecWords;   // pair (q - 1, q)
+                    if (rp[4] >= 0) {
+                        if ((rp[5] & 255) == TLQ_CZ) {
+                            if (prev & bq) { ph.x = -ph.x; ph.y = -ph.y; }
+                        } else {
+                            const T2 g = GT[rp[4]];
+                            T2 f;
+                            f.x = g.x;
+                            f.y = (prev ^ bq) ? g.y : -g.y;
+                            ph = cmul(ph, f);
+                        }
+                    }
+                }
+                prev = bq;
             }
             if (conj_phase) ph.y = -ph.y;
             M.tab[slot] = ph;
@@ -400,8 +421,8 @@ __device__ void pass_fwd(T2* psi, int s, unsigned m, bool diag, const Team& tm, 
 // red[slot * nw + warp]: slots 0..3 rotations (register bit), 4.. diagonal gates in program
 // order.
 template <typename real, typename T2>
-__device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, bool diag, const int32_t* dg, int ndiag,
-                         const Team& tm, const TeamMem<T2>& M, int par, real* red) {
+__device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, bool diag, const Team& tm, const TeamMem<T2>& M,
+                         int par, real* red) {
     const int W = M.W;
     const T2* cs = info_cs(M, par);
     const int* kinds = info_kinds(M, par);
@@ -444,30 +465,35 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, bool diag, const i
                 Sp1 += (((j >> 1) ^ (j >> 2)) & 1) ? -w : w;
                 Sp2 += (((j >> 2) ^ (j >> 3)) & 1) ? -w : w;
             }
-            int sl = 4;
-            for (int k = 0; k < ndiag; ++k) {
-                if (dg[3 * k + 2] < 0) continue;
-                const int w0 = dg[3 * k];
-                const int kind = w0 & 255, j0 = (w0 >> 8) & 255, j1 = (w0 >> 16) & 255;
-                real val;
+            const int* zslot = info_zslot(M, par);
+            const int* pslot = info_pslot(M, par);
+            for (int j0 = 0; j0 < W; ++j0) {
                 const int k0 = j0 - s;
                 const bool in0 = (unsigned)k0 < 4u;
-                if (kind == TLQ_RZ) {
+                if (zslot[j0] >= 0) {
+                    real val;
                     if (in0) val = k0 == 0 ? Sk0 : k0 == 1 ? Sk1 : k0 == 2 ? Sk2 : Sk3;
                     else val = ((base >> j0) & 1) ? -S : S;
-                } else {   // RZZ on (j0, j1 = j0 + 1)
+                    val = team_warp_sum(val, tm);
+                    if (leader) {
+                        real* dst = red + (4 + 2 * j0) * nw + warp;
+                        *dst = first ? val : *dst + val;
+                    }
+                }
+                if (pslot[j0] >= 0) {   // RZZ on (j0, j0 + 1)
+                    const int j1 = j0 + 1;
                     const bool in1 = (unsigned)(j1 - s) < 4u;
+                    real val;
                     if (in0 && in1) val = k0 == 0 ? Sp0 : k0 == 1 ? Sp1 : Sp2;
                     else if (in0) val = ((base >> j1) & 1) ? -Sk3 : Sk3;   // j0 = s + 3
                     else if (in1) val = ((base >> j0) & 1) ? -Sk0 : Sk0;   // j1 = s
                     else val = (((base >> j0) ^ (base >> j1)) & 1) ? -S : S;
+                    val = team_warp_sum(val, tm);
+                    if (leader) {
+                        real* dst = red + (5 + 2 * j0) * nw + warp;
+                        *dst = first ? val : *dst + val;
+                    }
                 }
-                val = team_warp_sum(val, tm);
-                if (leader) {
-                    real* dst = red + sl * nw + warp;
-                    *dst = first ? val : *dst + val;
-                }
-                ++sl;
             }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -499,29 +525,26 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, bool diag, const i
 
 // Sum the per-warp partials of one adjoint pass in fixed order and store them as FP64 slots.
 template <typename real, typename T2>
-__device__ void flush_pass(const real* red, int nw, unsigned m, int s, const TeamMem<T2>& M, int par,
-                           const int32_t* dg, int ndiag, bool diag, double* gdst, const Team& tm) {
+__device__ void flush_pass(const real* red, int nw, unsigned m, int s, const TeamMem<T2>& M, int par, bool diag,
+                           double* gdst, const Team& tm) {
     const int* kinds = info_kinds(M, par);
     const int* rslot = info_rslot(M, par);
-    for (int k = tm.tid; k < 4; k += tm.tt) {
-        if (!((m >> k) & 1) || kinds[s + k] < 0) continue;
-        const int slot = rslot[s + k];
-        if (slot < 0) continue;
-        double acc = 0;
-        for (int w = 0; w < nw; ++w) acc += (double)red[k * nw + w];
-        gdst[slot] = acc;
-    }
-    if (!diag) return;
-    int sl = 4;
-    for (int k = 0; k < ndiag; ++k) {
-        const int slot = dg[3 * k + 2];
-        if (slot < 0) continue;
-        if (((sl - 4) % tm.tt) == tm.tid) {
-            double acc = 0;
-            for (int w = 0; w < nw; ++w) acc += (double)red[sl * nw + w];
-            gdst[slot] = acc;
+    const int* zslot = info_zslot(M, par);
+    const int* pslot = info_pslot(M, par);
+    const int nred = diag ? 4 + 2 * M.W : 4;
+    for (int t = tm.tid; t < nred; t += tm.tt) {
+        int slot;
+        if (t < 4) {
+            if (!((m >> t) & 1) || kinds[s + t] < 0) continue;
+            slot = rslot[s + t];
+        } else {
+            const int j = (t - 4) >> 1;
+            slot = ((t - 4) & 1) ? pslot[j] : zslot[j];
         }
-        ++sl;
+        if (slot < 0) continue;
+        real acc = 0;
+        for (int w = 0; w < nw; ++w) acc += red[t * nw + w];
+        gdst[slot] = (double)acc;
     }
 }
 
@@ -557,10 +580,10 @@ __device__ double measure(const TeamMem<T2>& M, const ConeDev& cd, const Team& t
     const bool leader = tm.tt >= 32 ? ((tm.tid & 31) == 0) : (tm.tid == 0);
     if (leader) red[warp] = acc;
     tm.sync();
-    double e = 0;
-    for (int w = 0; w < nw; ++w) e += (double)red[w];
+    real e = 0;
+    for (int w = 0; w < nw; ++w) e += red[w];
     tm.sync();
-    return e;
+    return (double)e;
 }
 
 template <typename real, bool GRAD, bool GLOBAL>
@@ -601,10 +624,9 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
     tm.sync();
     for (int li = 0; li < nl; ++li) {
         const int32_t* lp = body + lofs[li];
-        const int nrot = lp[0], ndiag = lp[1];
+        const int ndiag = lp[0];
         const int par = li & 1;
-        unsigned todo = 0;
-        for (int k = 0; k < nrot; ++k) todo |= 1u << (lp[2 + 3 * k] & 255);
+        unsigned todo = (unsigned)lp[1];
         stage_layer<real, T2>(lp, GT, tm, M, par, false);
         bool first = true;
         while (todo || (first && ndiag > 0)) {
@@ -631,11 +653,9 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
     int rpar = 0;
     for (int li = nl - 1; li >= 0; --li) {
         const int32_t* lp = body + lofs[li];
-        const int nrot = lp[0], ndiag = lp[1];
-        const int32_t* dg = lp + 2 + 3 * nrot;
+        const int ndiag = lp[0];
         const int par = li & 1;
-        unsigned todo = 0;
-        for (int k = 0; k < nrot; ++k) todo |= 1u << (lp[2 + 3 * k] & 255);
+        unsigned todo = (unsigned)lp[1];
         stage_layer<real, T2>(lp, GT, tm, M, par, true);
         bool first = true;
         while (todo || (first && ndiag > 0)) {
@@ -654,9 +674,9 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
             }
             real* rb = red + rpar * kMaxPassSlots * nw;
             const bool dpass = first && ndiag > 0;
-            pass_bwd<real, T2>(M.psi, M.lam, s, m, dpass, dg, ndiag, tm, M, par, rb);
+            pass_bwd<real, T2>(M.psi, M.lam, s, m, dpass, tm, M, par, rb);
             tm.sync();
-            flush_pass<real, T2>(rb, nw, m, s, M, par, dg, ndiag, dpass, gdst, tm);
+            flush_pass<real, T2>(rb, nw, m, s, M, par, dpass, gdst, tm);
             rpar ^= 1;
             first = false;
         }

@@ -44,16 +44,19 @@ struct ChunkDev {
 
 // Program encoding (int32 words) of one cone:
 //   [nlayers, off_0 .. off_{nlayers-1}, body]
-// where body + off_l holds layer l (forward order):
-//   [nrot, ndiag,  nrot x {j | kind<<8, gate, slot},  ndiag x {kind | j0<<8 | j1<<16, gate, slot}]
-// kind uses tlq_gate_kind; j1 = 255 for RZ; slot = -1 when the gate carries no parameter
-// (fixed angle or CZ). Rotation entries are sorted by j; j0 < j1 for two-qubit gates.
+// where body + off_l holds layer l (forward order): a header
+//   [has_diag, live (window-bit mask of rotations), 0, 0]
+// followed by one record of kRecWords words per window qubit j:
+//   [rot_gate, rot_kind | (slot+1) << 8, rz_gate, rz_slot, pair_gate, pair_kind | (slot+1) << 8]
+// rot_* is the layer's RX/RY on j, rz_* its RZ on j, pair_* its RZZ or CZ on (j, j+1);
+// gate = -1 and slot = -1 mean absent / no parameter. Gates index the circuit's gate list.
+constexpr int kRecWords = 6;
+constexpr int kLayerHeader = 4;
 constexpr int kMinConeW = 8;       // narrower cones are padded to this width
 constexpr int kMaxSmemConeW = 13;  // widest cone kept in shared memory (FP32)
 constexpr int kMaxConeW = 20;      // widest cone on the cone path (global-memory tier)
 constexpr int kCtaThreads = 512;
-constexpr int kMaxPassSlots = 64;  // gradient values reduced per pass (diag + rotations)
-constexpr int kMaxDiagParams = 56; // parametrised diagonal gates per layer of one cone
+constexpr int kMaxPassSlots = 4 + 2 * 20;  // gradient values per adjoint pass: 4 rotations + RZ/pair per qubit
 
 // ---------------------------------------------------------------------------------------
 // Host-side objects.

@@ -151,7 +151,10 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
             P->why_dense = "light cone wider than " + std::to_string(kMaxConeW) + " qubits";
             return P;
         }
-        // Emit the program in forward layer order.
+        // Emit the program in forward layer order: per layer a header and one fixed record
+        // per window qubit (see internal.h). A layer whose cone gates put two RZ on one
+        // qubit or two two-qubit gates on one pair is split into several layers (the
+        // diagonal gates commute, so any split is exact).
         std::sort(kept.begin(), kept.end());
         ConeDev cd{};
         cd.term = t;
@@ -167,44 +170,75 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
             for (int g : c.layers[l].rot) if (kept_has(g)) rot.push_back(g);
             for (int g : c.layers[l].diag) if (kept_has(g)) diag.push_back(g);
             if (rot.empty() && diag.empty()) continue;
-            std::sort(rot.begin(), rot.end(), [&](int a, int b) { return c.gates[a].q0 < c.gates[b].q0; });
-            // split the diagonal gates so no layer exceeds kMaxDiagParams parametrised gates
-            std::vector<std::vector<int>> dparts(1);
-            int np = 0;
+            // sub-layers: position-disjoint groups of diagonal gates
+            std::vector<std::vector<int>> parts(1);
+            std::vector<std::vector<char>> zused(1, std::vector<char>(W, 0)), pused(1, std::vector<char>(W, 0));
             for (int g : diag) {
-                if (c.gates[g].param >= 0 && c.gates[g].kind != TLQ_CZ) {
-                    if (np == kMaxDiagParams) { dparts.emplace_back(); np = 0; }
-                    ++np;
+                const tlq_gate& G = c.gates[g];
+                const bool two = is_two(G.kind);
+                const int j = std::min(G.q0, two ? G.q1 : G.q0) - lo;
+                size_t p = 0;
+                while (p < parts.size() && (two ? pused[p][j] : zused[p][j])) ++p;
+                if (p == parts.size()) {
+                    parts.emplace_back();
+                    zused.emplace_back(W, 0);
+                    pused.emplace_back(W, 0);
                 }
-                dparts.back().push_back(g);
+                (two ? pused[p][j] : zused[p][j]) = 1;
+                parts[p].push_back(g);
             }
-            for (size_t part = 0; part < dparts.size(); ++part) {
-                const std::vector<int>& rr = part == 0 ? rot : std::vector<int>();
-                const std::vector<int>& dd = dparts[part];
-                layer_off.push_back((int32_t)body.size());
-                body.push_back((int32_t)rr.size());
-                body.push_back((int32_t)dd.size());
-                P->cone_nrot[t] += (int32_t)rr.size();
-                if (!dd.empty()) P->cone_ndiag[t] += 1;
-                for (int g : rr) {
-                    const tlq_gate& G = c.gates[g];
-                    int32_t slot = G.param >= 0 ? nslot++ : -1;
-                    if (slot >= 0) pentries[G.param].push_back({slot_total + slot, term.coeff});
-                    body.push_back((G.q0 - lo) | (G.kind << 8));
-                    body.push_back(g);
-                    body.push_back(slot);
+            for (size_t part = 0; part < parts.size(); ++part) {
+                std::vector<int32_t> rec((size_t)W * kRecWords, -1);
+                for (int j = 0; j < W; ++j) {
+                    rec[(size_t)j * kRecWords + 1] = 0;
+                    rec[(size_t)j * kRecWords + 5] = 0;
                 }
+                uint32_t live = 0;
+                if (part == 0) {
+                    for (int g : rot) {
+                        const tlq_gate& G = c.gates[g];
+                        const int j = G.q0 - lo;
+                        const int32_t slot = G.param >= 0 ? nslot++ : -1;
+                        if (slot >= 0) pentries[G.param].push_back({slot_total + slot, term.coeff});
+                        rec[(size_t)j * kRecWords + 0] = g;
+                        rec[(size_t)j * kRecWords + 1] = G.kind | ((slot + 1) << 8);
+                        live |= 1u << j;
+                        P->cone_nrot[t] += 1;
+                    }
+                }
+                // diagonal gates: slots in (qubit, RZ before pair) order
+                std::vector<int> dd = parts[part];
+                std::sort(dd.begin(), dd.end(), [&](int a, int b) {
+                    const tlq_gate &A = c.gates[a], &Bg = c.gates[b];
+                    const int ja = std::min(A.q0, is_two(A.kind) ? A.q1 : A.q0);
+                    const int jb = std::min(Bg.q0, is_two(Bg.kind) ? Bg.q1 : Bg.q0);
+                    if (ja != jb) return ja < jb;
+                    return is_two(A.kind) < is_two(Bg.kind);
+                });
                 for (int g : dd) {
                     const tlq_gate& G = c.gates[g];
-                    int32_t slot = (G.param >= 0 && G.kind != TLQ_CZ) ? nslot++ : -1;
-                    if (slot >= 0) P->cone_npdiag[t] += 1;
-                    if (slot >= 0) pentries[G.param].push_back({slot_total + slot, term.coeff});
-                    int j0 = G.q0 - lo, j1 = is_two(G.kind) ? G.q1 - lo : 255;
-                    if (is_two(G.kind) && j1 < j0) std::swap(j0, j1);
-                    body.push_back(G.kind | (j0 << 8) | (j1 << 16));
-                    body.push_back(g);
-                    body.push_back(slot);
+                    const bool two = is_two(G.kind);
+                    const int j = std::min(G.q0, two ? G.q1 : G.q0) - lo;
+                    const int32_t slot = (G.param >= 0 && G.kind != TLQ_CZ) ? nslot++ : -1;
+                    if (slot >= 0) {
+                        pentries[G.param].push_back({slot_total + slot, term.coeff});
+                        P->cone_npdiag[t] += 1;
+                    }
+                    if (two) {
+                        rec[(size_t)j * kRecWords + 4] = g;
+                        rec[(size_t)j * kRecWords + 5] = G.kind | ((slot + 1) << 8);
+                    } else {
+                        rec[(size_t)j * kRecWords + 2] = g;
+                        rec[(size_t)j * kRecWords + 3] = slot;
+                    }
                 }
+                if (!dd.empty()) P->cone_ndiag[t] += 1;
+                layer_off.push_back((int32_t)body.size());
+                body.push_back(dd.empty() ? 0 : 1);
+                body.push_back((int32_t)live);
+                body.push_back(0);
+                body.push_back(0);
+                body.insert(body.end(), rec.begin(), rec.end());
                 ++nlayers;
             }
         }
