@@ -143,6 +143,24 @@ tlq_status tlq_expectation_grad_dev(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const
                                     int32_t B, tlq_precision prec, double* energy_dev, double* grad_dev,
                                     void* cuda_stream);
 
+/* Allocation-free variant of tlq_expectation_grad_dev (FP32, nearest-neighbour circuits).
+ * The paper has no counterpart: this serves callers that cannot allocate device memory
+ * when they evaluate -- e.g. a host application whose own allocator owns the whole GPU and
+ * accounts for every byte, or a latency-critical loop that cannot take the implicit device
+ * synchronisation of cudaMalloc. Arguments are as for tlq_expectation_grad_dev (device
+ * pointers; grad_dev may be NULL for energies only; work enqueued on cuda_stream, NULL =
+ * the context's stream; no synchronisation). All working memory (a copy of the plan, the
+ * work list, gate tables, per-term partials, gradient slots, counters) comes from one
+ * 16 MiB array compiled into the library, which every GPU that loads the library holds
+ * until the process exits; no cudaMalloc/cudaFree or other allocating routine is called.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress),
+ * so make the first call on each device before any stream capture. Calls share the array:
+ * calls whose work overlaps on the GPU race and must be serialised by the caller.
+ * TLQ_ENOMEM (with the byte count in tlq_last_error) when the call needs more than the
+ * array holds; TLQ_EUNSUPPORTED for circuits that need the dense statevector path. */
+tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta_dev, int32_t B,
+                                       double* energy_dev, double* grad_dev, void* cuda_stream);
+
 /* Serving (continuous batching): enqueue one request; returns at once with a ticket.
  * theta: host [B][n_params]; energy: host [B]; grad: host [B][n_params] when want_grad.
  * The buffers are borrowed until tlq_poll returns TLQ_OK for the ticket. Requests are

@@ -27,7 +27,7 @@ SYMBOLS = ["tlq_init", "tlq_destroy", "tlq_circuit_create", "tlq_circuit_destroy
            "tlq_hamiltonian_create", "tlq_hamiltonian_destroy", "tlq_expectation",
            "tlq_expectation_grad", "tlq_expectation_grad_dev", "tlq_submit", "tlq_poll",
            "tlq_last_error", "tlq_plan_info", "tlq_plan_cone_stats", "tlq_profile_enable",
-           "tlq_profile_last", "tlq_serving_stats", "tlq_version"]
+           "tlq_profile_last", "tlq_serving_stats", "tlq_version", "tlq_expectation_grad_static"]
 
 
 class tlq_gate(ctypes.Structure):
@@ -82,6 +82,7 @@ def lib():
         L.tlq_plan_cone_stats.argtypes = [vp, vp, vp, ip, ip, ip, ip]
         L.tlq_profile_enable.argtypes = [vp, ctypes.c_int]
         L.tlq_profile_last.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ip]
+        L.tlq_expectation_grad_static.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp, vp, vp]
         L.tlq_serving_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), dp, dp, dp]
         L.tlq_version.argtypes = []
         L.tlq_version.restype = ctypes.c_int32
@@ -184,6 +185,14 @@ def tlq_expectation_grad_dev(ctx, circ, ham, theta_ptr, B, prec, energy_ptr, gra
                                                  ctypes.c_void_p(energy_ptr),
                                                  ctypes.c_void_p(grad_ptr) if grad_ptr else None,
                                                  ctypes.c_void_p(stream_ptr) if stream_ptr else None), ctx)
+
+
+def tlq_expectation_grad_static(ctx, circ, ham, theta_ptr, B, energy_ptr, grad_ptr, stream_ptr):
+    """Allocation-free device-pointer call (scratch from the library's static array)."""
+    return _check(lib().tlq_expectation_grad_static(ctx, circ, ham, ctypes.c_void_p(theta_ptr), B,
+                                                    ctypes.c_void_p(energy_ptr),
+                                                    ctypes.c_void_p(grad_ptr) if grad_ptr else None,
+                                                    ctypes.c_void_p(stream_ptr) if stream_ptr else None), ctx)
 
 
 def tlq_submit(ctx, circ, ham, theta, energy, grad, prec=TLQ_FP32):

@@ -1,0 +1,297 @@
+// Allocation-free variant of the batched cone kernel launch (tlq_expectation_grad_static).
+//
+// Some callers cannot allocate device memory when they evaluate a circuit: a host
+// application whose own memory manager owns the whole GPU and must account for every
+// byte, or a latency-critical loop that cannot afford the implicit device
+// synchronisation of cudaMalloc/cudaFree. For them this entry point takes all of its
+// working memory -- the copy of the plan, the work list, the gate tables, the per-term
+// partial energies, the gradient slots and the work counters -- from one fixed array
+// compiled into the library, instead of the context's growable workspace.
+//
+// The array is a file-scope __device__ object of kStaticScratchBytes; every GPU that
+// loads the library holds it until the process exits. Host code cannot use the array's
+// name as a device address, so its address is looked up with cudaGetSymbolAddress once
+// per device (on the first call on that device, with that device current) and that
+// pointer is handed to the kernels. All calls share the one array and it keeps whatever
+// the last call left there; the work counters that must start at zero are cleared by
+// every call. Two calls whose work overlaps on the GPU (different streams, or the same
+// context used from two threads) race on the array and must be serialised by the caller.
+#include "runtime.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+namespace tlq {
+
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;   // 16 MiB
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+int team_bytes_host(int W, int tt, bool fp64, bool grad, bool smem_state);
+
+namespace {
+
+std::mutex g_mu;
+void* g_scratch_ptr[256] = {nullptr};   // device address of g_static_scratch per device
+
+// Set-up, once per device: the device must be current.
+tlq_status static_scratch(int device, void** out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (device < 0 || device >= 256) {
+        set_error("static scratch: device ordinal out of range");
+        return TLQ_EINVAL;
+    }
+    if (!g_scratch_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error(std::string("static scratch: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+            return TLQ_ECUDA;
+        }
+        g_scratch_ptr[device] = p;
+    }
+    *out = g_scratch_ptr[device];
+    return TLQ_OK;
+}
+
+// Host-side plan and work list for one (context, circuit, Hamiltonian, batch), cached by a
+// fingerprint of the circuit and Hamiltonian contents (host memory only).
+struct HostPlan {
+    uint64_t key[4];
+    std::shared_ptr<Plan> plan;
+    int B = -1;
+    bool grad = false;
+    std::vector<int32_t> items;
+    std::vector<ChunkDev> chunks;
+    int n_chunks_smem = 0, smem_bytes = 0, gsmem_bytes = 0, g_maxW = 0;
+};
+std::vector<std::unique_ptr<HostPlan>> g_plans;   // small LRU, guarded by g_mu
+
+uint64_t mix(uint64_t h, uint64_t v) {
+    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    return h;
+}
+
+void fingerprint(const Context* ctx, const Circuit& c, const Ham& h, uint64_t out[4]) {
+    uint64_t a = mix((uint64_t)(uintptr_t)ctx, (uint64_t)c.n);
+    a = mix(a, (uint64_t)c.n_params);
+    for (const tlq_gate& g : c.gates) {
+        a = mix(a, ((uint64_t)(uint32_t)g.kind << 32) | (uint32_t)g.q0);
+        a = mix(a, ((uint64_t)(uint32_t)g.q1 << 32) | (uint32_t)g.param);
+        uint64_t bits;
+        std::memcpy(&bits, &g.angle, 8);
+        a = mix(a, bits);
+    }
+    uint64_t b = mix(0x243f6a8885a308d3ull, (uint64_t)h.n);
+    for (const Term& t : h.terms) {
+        uint64_t bits;
+        std::memcpy(&bits, &t.coeff, 8);
+        b = mix(b, bits);
+        for (int s : t.sites) b = mix(b, (uint64_t)(uint32_t)s);
+        for (char ch : t.letters) b = mix(b, (uint64_t)(unsigned char)ch);
+    }
+    out[0] = a;
+    out[1] = b;
+    out[2] = c.gates.size();
+    out[3] = h.terms.size();
+}
+
+void build_host_worklist(HostPlan& hp, int B, bool grad, int smax) {
+    const Plan& P = *hp.plan;
+    const int T = (int)P.cones.size();
+    std::vector<int> order(T);
+    for (int t = 0; t < T; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P.cones[a].W > P.cones[b].W; });
+    hp.items.clear();
+    std::vector<ChunkDev> sm, gl;
+    hp.smem_bytes = hp.gsmem_bytes = hp.g_maxW = 0;
+    size_t k = 0;
+    while (k < order.size()) {
+        const int W = P.cones[order[k]].W;
+        size_t k2 = k;
+        while (k2 < order.size() && P.cones[order[k2]].W == W) ++k2;
+        int tt = std::min(kCtaThreads, 1 << (W - 4));
+        int tb = team_bytes_host(W, tt, false, grad, true);
+        int nteams = std::min(kCtaThreads / tt, smax / tb);
+        const bool global = (W > kMaxSmemConeW) || nteams < 1;
+        if (global) {
+            tt = kCtaThreads;
+            tb = team_bytes_host(W, tt, false, grad, false);
+            nteams = 1;
+        }
+        const int first = (int)hp.items.size() / 2;
+        for (size_t i = k; i < k2; ++i)
+            for (int b = 0; b < B; ++b) { hp.items.push_back(order[i]); hp.items.push_back(b); }
+        const int nit = (int)hp.items.size() / 2 - first;
+        for (int f = 0; f < nit; f += nteams) {
+            ChunkDev ch{};
+            ch.W = W;
+            ch.first = first + f;
+            ch.count = std::min(nteams, nit - f);
+            ch.tt = tt;
+            ch.team_bytes = tb;
+            (global ? gl : sm).push_back(ch);
+        }
+        if (global) { hp.gsmem_bytes = std::max(hp.gsmem_bytes, tb); hp.g_maxW = std::max(hp.g_maxW, W); }
+        else hp.smem_bytes = std::max(hp.smem_bytes, nteams * tb);
+        k = k2;
+    }
+    hp.chunks = sm;
+    hp.chunks.insert(hp.chunks.end(), gl.begin(), gl.end());
+    hp.n_chunks_smem = (int)sm.size();
+    hp.B = B;
+    hp.grad = grad;
+}
+
+struct Carve {
+    unsigned char* base;
+    size_t used = 0;
+    void* take(size_t bytes) {
+        used = (used + 255) & ~(size_t)255;
+        void* p = base + used;
+        used += bytes;
+        return p;
+    }
+};
+
+}  // namespace
+}  // namespace tlq
+
+using namespace tlq;
+
+extern "C" tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta_dev,
+                                                  int32_t B, double* energy_dev, double* grad_dev, void* cuda_stream) {
+    Context* C = reinterpret_cast<Context*>(ctx);
+    Circuit* Ci = reinterpret_cast<Circuit*>(c);
+    Ham* Hm = reinterpret_cast<Ham*>(h);
+    if (!C || !Ci || !Hm) { set_error("tlq_expectation_grad_static: NULL handle"); return TLQ_EINVAL; }
+    if (Ci->ctx != C || Hm->ctx != C) { set_error("tlq_expectation_grad_static: handle from another context"); return TLQ_EINVAL; }
+    if (Ci->n != Hm->n) { set_error("tlq_expectation_grad_static: qubit counts differ"); return TLQ_EINVAL; }
+    if (B <= 0) { set_error("tlq_expectation_grad_static: B must be positive"); return TLQ_EINVAL; }
+    if ((!theta_dev && Ci->n_params > 0) || !energy_dev) { set_error("tlq_expectation_grad_static: NULL device pointer"); return TLQ_EINVAL; }
+    if (C->host_only()) { set_error("tlq_expectation_grad_static: host-only context"); return TLQ_EUNSUPPORTED; }
+    std::lock_guard<std::mutex> lk(C->mu);
+    cudaError_t e = cudaSetDevice(C->device);
+    if (e != cudaSuccess) { set_error(std::string("cudaSetDevice: ") + cudaGetErrorString(e)); return TLQ_ECUDA; }
+    void* scratch = nullptr;
+    tlq_status st = static_scratch(C->device, &scratch);
+    if (st != TLQ_OK) return st;
+    const bool grad = grad_dev != nullptr;
+
+    uint64_t key[4];
+    fingerprint(C, *Ci, *Hm, key);
+    HostPlan* hp = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        for (auto& p : g_plans)
+            if (std::equal(key, key + 4, p->key)) { hp = p.get(); break; }
+        if (!hp) {
+            std::string err;
+            auto plan = make_plan(*Ci, *Hm, &err);
+            if (!plan) { set_error(err); return TLQ_EINVAL; }
+            if (g_plans.size() >= 16) g_plans.erase(g_plans.begin());
+            g_plans.emplace_back(new HostPlan());
+            hp = g_plans.back().get();
+            std::copy(key, key + 4, hp->key);
+            hp->plan = plan;
+        }
+        if (hp->plan->path != TLQ_PATH_CONE) {
+            set_error("tlq_expectation_grad_static: only nearest-neighbour circuits (cone path) are supported");
+            return TLQ_EUNSUPPORTED;
+        }
+        if (hp->B != B || hp->grad != grad) {
+            int smax = 0;
+            cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, C->device);
+            smax = smax > 2048 ? smax - 1024 : 48 * 1024;
+            build_host_worklist(*hp, B, grad, smax);
+        }
+    }
+    const Plan& P = *hp->plan;
+    const int G = (int)Ci->gates.size();
+    const int T = (int)P.cones.size();
+    const int S = std::max<int32_t>(1, P.n_slots);
+    const int n_glob = (int)hp->chunks.size() - hp->n_chunks_smem;
+    const int g_grid = std::max(0, std::min(n_glob, C->sm_count));
+    const size_t amps = hp->g_maxW > 0 ? ((size_t)1 << hp->g_maxW) + ((size_t)1 << (hp->g_maxW - 3)) : 0;
+    const size_t gslot = ((amps * 8 * (grad ? 2 : 1)) + 255) & ~(size_t)255;
+
+    // carve the static array
+    Carve cv{reinterpret_cast<unsigned char*>(scratch)};
+    tlq_gate* d_gates = (tlq_gate*)cv.take((size_t)std::max(1, G) * sizeof(tlq_gate));
+    ConeDev* d_cones = (ConeDev*)cv.take(P.cones.size() * sizeof(ConeDev));
+    int32_t* d_prog = (int32_t*)cv.take(P.prog.size() * sizeof(int32_t));
+    double* d_tc = (double*)cv.take(P.term_coeff.size() * sizeof(double));
+    int32_t* d_poff = (int32_t*)cv.take(P.pmap_off.size() * sizeof(int32_t));
+    int32_t* d_pidx = (int32_t*)cv.take(std::max<size_t>(1, P.pmap_idx.size()) * sizeof(int32_t));
+    double* d_pco = (double*)cv.take(std::max<size_t>(1, P.pmap_coeff.size()) * sizeof(double));
+    int32_t* d_items = (int32_t*)cv.take(hp->items.size() * sizeof(int32_t));
+    ChunkDev* d_chunks = (ChunkDev*)cv.take(hp->chunks.size() * sizeof(ChunkDev));
+    void* d_gt = cv.take((size_t)B * std::max(1, G) * sizeof(float2));
+    double* d_e = (double*)cv.take((size_t)B * T * sizeof(double));
+    double* d_g = grad ? (double*)cv.take((size_t)B * S * sizeof(double)) : nullptr;
+    int32_t* d_cnt = (int32_t*)cv.take(64);
+    void* d_gs = g_grid > 0 ? cv.take((size_t)g_grid * gslot) : nullptr;
+    if (cv.used > kStaticScratchBytes) {
+        set_error("tlq_expectation_grad_static: this call needs " + std::to_string(cv.used) +
+                  " bytes of scratch; the library's static array holds " + std::to_string(kStaticScratchBytes) +
+                  " bytes (use tlq_expectation_grad_dev, or a smaller batch)");
+        return TLQ_ENOMEM;
+    }
+    cudaStream_t strm = cuda_stream ? (cudaStream_t)cuda_stream : (cudaStream_t)C->stream;
+    auto put = [&](void* dst, const void* src, size_t bytes) {
+        if (bytes && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, strm);
+    };
+    put(d_gates, Ci->gates.data(), (size_t)G * sizeof(tlq_gate));
+    put(d_cones, P.cones.data(), P.cones.size() * sizeof(ConeDev));
+    put(d_prog, P.prog.data(), P.prog.size() * sizeof(int32_t));
+    put(d_tc, P.term_coeff.data(), P.term_coeff.size() * sizeof(double));
+    put(d_poff, P.pmap_off.data(), P.pmap_off.size() * sizeof(int32_t));
+    put(d_pidx, P.pmap_idx.data(), P.pmap_idx.size() * sizeof(int32_t));
+    put(d_pco, P.pmap_coeff.data(), P.pmap_coeff.size() * sizeof(double));
+    put(d_items, hp->items.data(), hp->items.size() * sizeof(int32_t));
+    put(d_chunks, hp->chunks.data(), hp->chunks.size() * sizeof(ChunkDev));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 64, strm);   // work counters and error word start at 0
+    if (e != cudaSuccess) { set_error(std::string("tlq_expectation_grad_static: copy: ") + cudaGetErrorString(e)); return TLQ_ECUDA; }
+
+    ConeLaunch L;
+    L.cones = d_cones;
+    L.prog = d_prog;
+    L.term_coeff = d_tc;
+    L.pmap_off = d_poff;
+    L.pmap_idx = d_pidx;
+    L.pmap_coeff = d_pco;
+    L.gates = d_gates;
+    L.n_gates = G;
+    L.n_params = Ci->n_params;
+    L.n_terms = T;
+    L.n_slots = P.n_slots;
+    L.B = B;
+    L.theta = theta_dev;
+    L.items = d_items;
+    L.chunks = d_chunks;
+    L.n_chunks_smem = hp->n_chunks_smem;
+    L.n_chunks = (int)hp->chunks.size();
+    L.smem_bytes = hp->smem_bytes;
+    L.gsmem_bytes = hp->gsmem_bytes;
+    L.g_maxW = hp->g_maxW;
+    L.gate_table = d_gt;
+    L.e_part = d_e;
+    L.g_part = d_g;
+    L.gscratch = d_gs;
+    L.gscratch_slot = gslot;
+    L.g_grid = g_grid;
+    L.counters = d_cnt;
+    L.err = d_cnt + 4;
+    L.energy = energy_dev;
+    L.grad = grad_dev;
+    L.fp64 = false;
+    L.sm_count = C->sm_count;
+    const int rc = launch_cone(L, strm);
+    if (rc != 0) {
+        set_error(std::string("tlq_expectation_grad_static: launch: ") + cudaGetErrorString((cudaError_t)rc));
+        return TLQ_ECUDA;
+    }
+    return TLQ_OK;
+}
