@@ -32,8 +32,12 @@ PlanEntry::~PlanEntry() {
     cudaFree(d_pmap_idx);
     cudaFree(d_pmap_coeff);
     cudaFree(d_gates);
-    cudaFree(d_dprog);
-    cudaFree(d_dterms);
+    cudaFree(d_dlayers);
+    cudaFree(d_dclasses);
+    cudaFree(d_ddists);
+    cudaFree(d_dzterms);
+    cudaFree(d_dtab_gate);
+    cudaFree(d_dtab_mult);
     cudaFree(d_items);
     cudaFree(d_chunks);
 }
@@ -60,7 +64,7 @@ tlq_status get_plan(Context* ctx, Circuit* c, Ham* h, std::shared_ptr<PlanEntry>
     if (it != ctx->plans.end()) { *out = it->second; return TLQ_OK; }
     std::string err;
     auto plan = make_plan(*c, *h, &err);
-    if (!plan) { set_error(err); return TLQ_EINVAL; }
+    if (!plan) { set_error(err); return TLQ_EUNSUPPORTED; }
     auto pe = std::make_shared<PlanEntry>();
     pe->plan = plan;
     pe->circ_id = c->id;
@@ -76,6 +80,15 @@ tlq_status get_plan(Context* ctx, Circuit* c, Ham* h, std::shared_ptr<PlanEntry>
             TLQ_TRY(upload(plan->pmap_off, &pe->d_pmap_off, &bytes));
             TLQ_TRY(upload(plan->pmap_idx, &pe->d_pmap_idx, &bytes));
             TLQ_TRY(upload(plan->pmap_coeff, &pe->d_pmap_coeff, &bytes));
+        }
+        if (plan->dense) {
+            const DensePlan& D = *plan->dense;
+            TLQ_TRY(upload(D.layers, &pe->d_dlayers, &bytes));
+            TLQ_TRY(upload(D.classes, &pe->d_dclasses, &bytes));
+            TLQ_TRY(upload(D.dists, &pe->d_ddists, &bytes));
+            TLQ_TRY(upload(D.zterms, &pe->d_dzterms, &bytes));
+            TLQ_TRY(upload(D.tab_gate, &pe->d_dtab_gate, &bytes));
+            TLQ_TRY(upload(D.tab_mult, &pe->d_dtab_mult, &bytes));
         }
         pe->device_bytes = bytes;
         ctx->held += bytes;
@@ -180,6 +193,65 @@ size_t cone_workspace_bytes(const PlanEntry& pe, const Circuit& c, int B, bool f
     return s + 1024;
 }
 
+size_t dense_workspace_bytes(const PlanEntry& pe, const Circuit& c, int B) {
+    const DensePlan& D = *pe.plan->dense;
+    size_t s = 0;
+    s += align256((size_t)B * std::max<size_t>(1, c.gates.size()) * 8);
+    s += align256((size_t)B * std::max<size_t>(1, D.tab_gate.size()) * 8);
+    s += align256(((size_t)1 << D.n_eff) * 8);
+    s += align256(dense_partial_count(D.n_eff) * sizeof(double));
+    return s + 1024;
+}
+
+static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const double* theta_dev, int B,
+                            double* energy_dev, bool per_gate, void* stream, Workspace* ws) {
+    const DensePlan& D = *pe.plan->dense;
+    const size_t need = dense_workspace_bytes(pe, c, B);
+    if (ws->cap - ws->used < need) {
+        set_error("workspace too small for the dense state");
+        return TLQ_ENOMEM;
+    }
+    DenseLaunch L;
+    L.n_eff = D.n_eff;
+    L.n_passes = (int32_t)D.passes.size();
+    L.layers = pe.d_dlayers;
+    L.classes = pe.d_dclasses;
+    L.dists = pe.d_ddists;
+    L.energy_class_off = D.energy_class_off;
+    L.energy_nclass = D.energy_nclass;
+    L.zterms = pe.d_dzterms;
+    L.n_zterms = (int32_t)D.zterms.size();
+    L.n_xterms = (int32_t)D.xterms.size();
+    L.tab_gate = pe.d_dtab_gate;
+    L.tab_mult = pe.d_dtab_mult;
+    L.tab_entries = (int32_t)D.tab_gate.size();
+    L.gates = pe.d_gates;
+    L.n_gates = (int32_t)c.gates.size();
+    L.n_params = c.n_params;
+    L.B = B;
+    L.theta = theta_dev;
+    L.gate_table = ws->take((size_t)B * std::max<size_t>(1, c.gates.size()) * 8);
+    L.phase_tab = ws->take((size_t)B * std::max<size_t>(1, D.tab_gate.size()) * 8);
+    L.state = ws->take(((size_t)1 << D.n_eff) * 8);
+    L.partial = (double*)ws->take(dense_partial_count(D.n_eff) * sizeof(double));
+    L.energy = energy_dev;
+    L.per_gate = per_gate;
+    L.sm_count = ctx->sm_count;
+    L.host_gates = c.gates.data();
+    L.host_passes = D.passes.data();
+    L.host_xterms = D.xterms.data();
+    L.host_all_terms = D.all_terms.data();
+    L.n_all_terms = (int32_t)D.all_terms.size();
+    if (ctx->profile) { L.ev_begin = ctx->prof_ev[0]; L.ev_end = ctx->prof_ev[1]; }
+    const int rc = launch_dense(L, stream);
+    ctx->last_launches = L.launches;
+    if (rc != 0) {
+        set_error(std::string("dense launch: ") + cudaGetErrorString((cudaError_t)rc));
+        return TLQ_ECUDA;
+    }
+    return TLQ_OK;
+}
+
 tlq_status run_device(Context* ctx, Circuit* c, Ham* h, const double* theta_dev, int B, tlq_precision prec,
                       double* energy_dev, double* grad_dev, void* stream, Workspace* ws) {
     std::shared_ptr<PlanEntry> pe;
@@ -187,9 +259,18 @@ tlq_status run_device(Context* ctx, Circuit* c, Ham* h, const double* theta_dev,
     const Plan& P = *pe->plan;
     const bool fp64 = prec == TLQ_FP64_REF;
     const bool grad = grad_dev != nullptr;
-    if (P.path != TLQ_PATH_CONE) {
-        set_error("dense statevector path not available for this request: " + P.why_dense);
-        return TLQ_EUNSUPPORTED;
+    const bool plain = ctx->cfg.fuse_k == 1;
+    if (P.path != TLQ_PATH_CONE || plain) {
+        if (!P.dense) {
+            set_error("no dense statevector plan for this request (n > " + std::to_string(kDenseMaxQubits) + ")");
+            return TLQ_EUNSUPPORTED;
+        }
+        if (grad || fp64) {
+            set_error(std::string("the dense statevector path computes FP32 energies only (") +
+                      (P.path == TLQ_PATH_DENSE ? P.why_dense : std::string("plain per-gate mode")) + ")");
+            return TLQ_EUNSUPPORTED;
+        }
+        return run_dense(ctx, *pe, *c, theta_dev, B, energy_dev, plain || !P.dense->fits_fused, stream, ws);
     }
     TLQ_TRY(ensure_worklist(ctx, *pe, *c, B, fp64, grad));
     const int g_grid = global_grid(*pe, ctx->sm_count);
@@ -487,9 +568,11 @@ static tlq_status sync_call(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double*
     const bool fp64 = prec == TLQ_FP64_REF;
     const bool want_grad = grad != nullptr;
     size_t work = 0;
-    if (pe->plan->path == TLQ_PATH_CONE) {
+    if (pe->plan->path == TLQ_PATH_CONE && ctx->cfg.fuse_k != 1) {
         TLQ_TRY(ensure_worklist(ctx, *pe, *c, B, fp64, want_grad));
         work = cone_workspace_bytes(*pe, *c, B, fp64, want_grad, std::max(0, std::min(pe->n_chunks - pe->n_chunks_smem, ctx->sm_count)));
+    } else if (pe->plan->dense) {
+        work = dense_workspace_bytes(*pe, *c, B);
     }
     const size_t P = (size_t)std::max(1, c->n_params);
     const size_t th_b = (size_t)B * P * sizeof(double);
@@ -541,10 +624,12 @@ tlq_status tlq_expectation_grad_dev(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const
     TLQ_TRY(get_plan(ctx, c, h, &pe));
     const bool fp64 = prec == TLQ_FP64_REF;
     size_t work = 0;
-    if (pe->plan->path == TLQ_PATH_CONE) {
+    if (pe->plan->path == TLQ_PATH_CONE && ctx->cfg.fuse_k != 1) {
         TLQ_TRY(ensure_worklist(ctx, *pe, *c, B, fp64, grad_dev != nullptr));
         work = cone_workspace_bytes(*pe, *c, B, fp64, grad_dev != nullptr,
                                     std::max(0, std::min(pe->n_chunks - pe->n_chunks_smem, ctx->sm_count)));
+    } else if (pe->plan->dense) {
+        work = dense_workspace_bytes(*pe, *c, B);
     }
     cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : (cudaStream_t)ctx->stream;
     if (ctx->ws.cap < work + 4096) {

@@ -26,22 +26,9 @@
 #include <cuda_runtime.h>
 #include <cstdio>
 
+#include "gates.cuh"
+
 namespace tlq {
-
-template <typename real> struct R2;
-template <> struct R2<float> { using T = float2; };
-template <> struct R2<double> { using T = double2; };
-
-// Shared-memory placement of amplitude a: two padding slots after every 16 amplitudes,
-// P(a) = a + 2*floor(a/16). A pass holds 16 amplitudes per thread on window bits
-// [s, s+4). For s = 0 a thread's 16 amplitudes are contiguous (vector loads) and
-// consecutive threads start 18 slots apart, so the 8 lanes of a 128-bit phase hit distinct
-// banks; for s >= 4 the 16 lanes of a half-warp read consecutive slots. In both cases
-// amplitude j of a thread sits at P(base) + j * stride, stride = 1 (s = 0) or
-// 2^s + 2^(s-3) (s >= 4), so addressing costs one add per amplitude.
-__host__ __device__ __forceinline__ int pad16(int a) { return a + ((a >> 4) << 1); }
-__host__ __device__ __forceinline__ int padded_amps(int W) { return (1 << W) + (1 << (W - 3)); }
-__host__ __device__ __forceinline__ int pass_stride(int s) { return s == 0 ? 1 : (1 << s) + (1 << (s - 3)); }
 
 // ---- per-team shared-memory layout ----------------------------------------------------
 //
@@ -112,133 +99,6 @@ __device__ __forceinline__ real team_warp_sum(real v, const Team& tm) {
         for (int off = tm.tt >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(tm.mask, v, off);
     }
     return v;
-}
-
-// ---- complex helpers ---------------------------------------------------------------------
-
-template <typename T2>
-__device__ __forceinline__ T2 cmul(T2 a, T2 b) {
-    T2 r;
-    r.x = a.x * b.x - a.y * b.y;
-    r.y = a.x * b.y + a.y * b.x;
-    return r;
-}
-
-template <typename T2>
-__device__ __forceinline__ void load16(T2 (&v)[16], const T2* p, int stride) {
-    if (stride == 1) {
-        if constexpr (sizeof(T2) == 8) {
-            const float4* q = reinterpret_cast<const float4*>(p);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float4 t = q[i];
-                v[2 * i].x = t.x;
-                v[2 * i].y = t.y;
-                v[2 * i + 1].x = t.z;
-                v[2 * i + 1].y = t.w;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = p[j];
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = p[j * stride];
-    }
-}
-
-template <typename T2>
-__device__ __forceinline__ void store16(const T2 (&v)[16], T2* p, int stride) {
-    if (stride == 1) {
-        if constexpr (sizeof(T2) == 8) {
-            float4* q = reinterpret_cast<float4*>(p);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) q[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) p[j] = v[j];
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) p[j * stride] = v[j];
-    }
-}
-
-// RY(a) on register bit K: [[c,-s],[s,c]] on (amp with bit 0, amp with bit 1).
-template <int K, typename T2, typename real>
-__device__ __forceinline__ void apply_ry(T2 (&v)[16], real c, real s) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        if (j & (1 << K)) continue;
-        const T2 a0 = v[j], a1 = v[j | (1 << K)];
-        v[j].x = c * a0.x - s * a1.x;
-        v[j].y = c * a0.y - s * a1.y;
-        v[j | (1 << K)].x = s * a0.x + c * a1.x;
-        v[j | (1 << K)].y = s * a0.y + c * a1.y;
-    }
-}
-
-// RX(a) on register bit K: [[c,-is],[-is,c]].
-template <int K, typename T2, typename real>
-__device__ __forceinline__ void apply_rx(T2 (&v)[16], real c, real s) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        if (j & (1 << K)) continue;
-        const T2 a0 = v[j], a1 = v[j | (1 << K)];
-        v[j].x = c * a0.x + s * a1.y;
-        v[j].y = c * a0.y - s * a1.x;
-        v[j | (1 << K)].x = c * a1.x + s * a0.y;
-        v[j | (1 << K)].y = c * a1.y - s * a0.x;
-    }
-}
-
-template <int K, typename T2, typename real>
-__device__ __forceinline__ void apply_rot(T2 (&v)[16], int kind, real c, real s) {
-    if (kind == TLQ_RY) apply_ry<K>(v, c, s);
-    else apply_rx<K>(v, c, s);
-}
-
-// Im <lam| Y |psi> over the pairs of register bit K (Y|0> = i|1>, Y|1> = -i|0>):
-// sum over pairs of Re(conj(l1) p0) - Re(conj(l0) p1).
-template <int K, typename T2, typename real>
-__device__ __forceinline__ real grad_y(const T2 (&p)[16], const T2 (&l)[16]) {
-    real acc = 0;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        if (j & (1 << K)) continue;
-        const T2 p0 = p[j], p1 = p[j | (1 << K)], l0 = l[j], l1 = l[j | (1 << K)];
-        acc += (l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y);
-    }
-    return acc;
-}
-
-// Im <lam| X |psi> = sum over pairs of Im(conj(l0) p1 + conj(l1) p0).
-template <int K, typename T2, typename real>
-__device__ __forceinline__ real grad_x(const T2 (&p)[16], const T2 (&l)[16]) {
-    real acc = 0;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        if (j & (1 << K)) continue;
-        const T2 p0 = p[j], p1 = p[j | (1 << K)], l0 = l[j], l1 = l[j | (1 << K)];
-        acc += (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
-    }
-    return acc;
-}
-
-// Adjoint step of one rotation on register bit K: gradient, then un-apply on psi and lam.
-template <int K, typename T2, typename real>
-__device__ __forceinline__ real adjoint_rot(T2 (&p)[16], T2 (&l)[16], int kind, real c, real s_neg) {
-    real g;
-    if (kind == TLQ_RY) {
-        g = grad_y<K, T2, real>(p, l);
-        apply_ry<K>(p, c, s_neg);
-        apply_ry<K>(l, c, s_neg);
-    } else {
-        g = grad_x<K, T2, real>(p, l);
-        apply_rx<K>(p, c, s_neg);
-        apply_rx<K>(l, c, s_neg);
-    }
-    return g;
 }
 
 // Diagonal phase of window index x: the product of the chunk-table entries.

@@ -1,0 +1,423 @@
+// Dense statevector path on GB300: circuits whose two-qubit gates are not nearest-neighbour
+// (e.g. QAOA on a random 3-regular graph). TensorLy-Quantum (arXiv:2112.10239) contrasts its
+// factorised networks with the "traditional vector representation" of a state (Sec. 1);
+// this file is that representation, tuned for HBM streaming.
+//
+// The 2^n complex64 state lives in HBM. Each layer (rotations, then commuting diagonal
+// gates) is applied in passes over tiles of 2^13 amplitudes staged in shared memory:
+//   * a low tile is 2^13 contiguous amplitudes (qubits 0..12);
+//   * a strided tile keeps qubits 0..3 (16 contiguous amplitudes = 128 bytes per row) and
+//     9 higher qubits a..a+8 as its 512 rows.
+// Inside a tile the rotations on the tile's qubits run as 16-amplitude register passes
+// (gates.cuh). The layer's diagonal gates are applied in the layer's last pass: RZ/RZZ gates
+// sharing one angle form a class whose phase exp(-i a/2 (N - 2c)) depends only on the count
+// c of "odd" terms, obtained with popcounts over per-distance masks and looked up in a small
+// per-layer table; CZ gates contribute (-1)^(count of 11 pairs). The energy of Z/ZZ terms is
+// accumulated in the final pass from the same counts; X/Y terms are measured by a separate
+// streaming kernel. Reductions run in a fixed order, so results are deterministic.
+//
+// The plain per-gate path (one full-state sweep per gate, per-term measurement sweeps) is
+// kept as the baseline the fused passes are compared against.
+#include "gates.cuh"
+
+#include <cstdio>
+
+namespace tlq {
+
+namespace {
+
+constexpr int kTile = 1 << kDenseTileBits;        // 8192 amplitudes
+constexpr int kThreads = 512;                     // 16 amplitudes per thread per register pass
+constexpr int kMaxLayerClasses = kDenseMaxLayerClasses;
+constexpr int kMaxDistWords = kDenseMaxDistWords;  // (d, mask) int pairs staged in shared memory
+constexpr int kMaxTab = kDenseMaxTab;              // phase-table entries staged per layer
+
+struct PassArgs {
+    DensePassDev pass;
+    const DenseLayerDev* layers;
+    const DenseClassDev* classes;
+    const int32_t* dists;
+    int32_t energy_class_off, energy_nclass;
+    const DenseZTermDev* zterms;
+    int32_t n_zterms;
+    const tlq_gate* gates;
+    const float2* GT;       // gate table of this set
+    const float2* ptab;     // phase tables of this set
+    float2* state;
+    int32_t n_eff;
+    double* partial;        // per-tile energy partials
+};
+
+// Global amplitude index of local tile index t.
+__device__ __forceinline__ uint32_t tile_x(const DensePassDev& p, uint32_t tile, uint32_t t) {
+    if (!p.strided) return (tile << kDenseTileBits) | t;
+    const uint32_t lo = tile & ((1u << (p.a - 4)) - 1u);
+    const uint32_t hi = tile >> (p.a - 4);
+    return (t & 15u) | (lo << 4) | ((t >> 4) << p.a) | (hi << (p.a + kDenseStridedBits));
+}
+
+__device__ __forceinline__ int class_count(const DenseClassDev& c, const int32_t* dist, uint32_t x) {
+    int cnt;
+    if (c.kind == 1) {
+        cnt = 0;
+        for (int k = 0; k < c.ndist; ++k) cnt += __popc((x & (x >> dist[2 * k])) & (uint32_t)dist[2 * k + 1]);
+    } else {
+        cnt = __popc(x & c.single);
+        for (int k = 0; k < c.ndist; ++k) cnt += __popc((x ^ (x >> dist[2 * k])) & (uint32_t)dist[2 * k + 1]);
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* tile = reinterpret_cast<float2*>(smem_raw);                               // padded_amps(13)
+    float2* s_tab = tile + padded_amps(kDenseTileBits);                              // kMaxTab
+    int32_t* s_dist = reinterpret_cast<int32_t*>(s_tab + kMaxTab);                   // kMaxDistWords
+    DenseClassDev* s_cls = reinterpret_cast<DenseClassDev*>(s_dist + kMaxDistWords); // kMaxLayerClasses
+    float* s_red = reinterpret_cast<float*>(s_cls + kMaxLayerClasses);               // 16
+    const DensePassDev& P = A.pass;
+    const uint32_t t_id = blockIdx.x;
+    const int tid = threadIdx.x;
+
+    // load the tile (float4 = 2 amplitudes; rows of 16 amplitudes stay contiguous)
+    {
+        const float4* src = reinterpret_cast<const float4*>(A.state);
+#pragma unroll
+        for (int k = 0; k < kTile / 2 / kThreads; ++k) {
+            const uint32_t i = 2u * (uint32_t)(tid + kThreads * k);
+            const float4 v = src[tile_x(P, t_id, i) >> 1];
+            *reinterpret_cast<float4*>(tile + pad16((int)i)) = v;
+        }
+    }
+    // stage the diagonal classes of this pass's layer and the energy classes
+    const bool diag = P.diag_layer >= 0;
+    int ncl = 0, cl_first = 0;
+    if (diag) {
+        const DenseLayerDev L = A.layers[P.diag_layer];
+        ncl = L.nclass;
+        cl_first = L.class_off;
+    }
+    const int nec = P.measure ? A.energy_nclass : 0;
+    if (tid < ncl) s_cls[tid] = A.classes[cl_first + tid];
+    if (tid < nec) s_cls[ncl + tid] = A.classes[A.energy_class_off + tid];
+    __syncthreads();
+    {
+        // distance words and phase-table entries of the staged classes
+        int woff = 0, toff = 0;
+        for (int c = 0; c < ncl + nec; ++c) {
+            const DenseClassDev& C = s_cls[c];
+            for (int w = tid; w < 2 * C.ndist; w += kThreads) s_dist[woff + w] = A.dists[2 * C.dist_off + w];
+            if (C.kind == 0)
+                for (int e = tid; e <= C.nterms; e += kThreads) s_tab[toff + e] = A.ptab[C.tab_off + e];
+            woff += 2 * C.ndist;
+            toff += C.kind == 0 ? C.nterms + 1 : 0;
+        }
+    }
+    __syncthreads();
+
+    float eacc = 0.f;
+    for (int g = 0; g < P.ngroups; ++g) {
+        const int s = P.group_s[g];
+        const unsigned m = P.group_mask[g];
+        int kd[4];
+        float c[4], sn[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            kd[k] = -1;
+            c[k] = 1.f;
+            sn[k] = 0.f;
+            if ((m >> k) & 1) {
+                const int gate = P.gate[s + k];
+                kd[k] = A.gates[gate].kind;
+                const float2 v = A.GT[gate];
+                c[k] = v.x;
+                sn[k] = v.y;
+            }
+        }
+        const int lowmask = (1 << s) - 1;
+        const int stride = pass_stride(s);
+        const int base = (tid & lowmask) | ((tid >> s) << (s + 4));
+        float2* p = tile + pad16(base);
+        float2 v[16];
+        load16(v, p, stride);
+        if (kd[0] >= 0) apply_rot<0>(v, kd[0], c[0], sn[0]);
+        if (kd[1] >= 0) apply_rot<1>(v, kd[1], c[1], sn[1]);
+        if (kd[2] >= 0) apply_rot<2>(v, kd[2], c[2], sn[2]);
+        if (kd[3] >= 0) apply_rot<3>(v, kd[3], c[3], sn[3]);
+        if (g == P.ngroups - 1 && (diag || P.measure)) {
+#pragma unroll 4
+            for (int j = 0; j < 16; ++j) {
+                const uint32_t x = tile_x(P, t_id, (uint32_t)(base | (j << s)));
+                int woff = 0, toff = 0;
+                float2 ph = make_float2(1.f, 0.f);
+                for (int ci = 0; ci < ncl; ++ci) {
+                    const DenseClassDev& C = s_cls[ci];
+                    const int cnt = class_count(C, s_dist + woff, x);
+                    if (C.kind == 0) ph = cmul(ph, s_tab[toff + cnt]);
+                    else if (cnt & 1) { ph.x = -ph.x; ph.y = -ph.y; }
+                    woff += 2 * C.ndist;
+                    toff += C.kind == 0 ? C.nterms + 1 : 0;
+                }
+                if (diag) v[j] = cmul(v[j], ph);
+                if (P.measure) {
+                    float ez = 0.f;
+                    for (int ci = ncl; ci < ncl + nec; ++ci) {
+                        const DenseClassDev& C = s_cls[ci];
+                        const int cnt = class_count(C, s_dist + woff, x);
+                        ez += (float)C.coeff * (float)(C.nterms - 2 * cnt);
+                        woff += 2 * C.ndist;
+                    }
+                    for (int k = 0; k < A.n_zterms; ++k) {
+                        const DenseZTermDev Z = A.zterms[k];
+                        ez += (__popc(x & Z.mask) & 1) ? -(float)Z.coeff : (float)Z.coeff;
+                    }
+                    eacc += (v[j].x * v[j].x + v[j].y * v[j].y) * ez;
+                }
+            }
+        }
+        store16(v, p, stride);
+        __syncthreads();
+    }
+    if (P.store) {
+        float4* dst = reinterpret_cast<float4*>(A.state);
+#pragma unroll
+        for (int k = 0; k < kTile / 2 / kThreads; ++k) {
+            const uint32_t i = 2u * (uint32_t)(tid + kThreads * k);
+            dst[tile_x(P, t_id, i) >> 1] = *reinterpret_cast<const float4*>(tile + pad16((int)i));
+        }
+    }
+    if (P.measure) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, off);
+        if ((tid & 31) == 0) s_red[tid >> 5] = eacc;
+        __syncthreads();
+        if (tid == 0) {
+            float e = 0.f;
+            for (int w = 0; w < kThreads / 32; ++w) e += s_red[w];
+            A.partial[t_id] = (double)e;
+        }
+    }
+}
+
+size_t dense_pass_smem() {
+    return (size_t)padded_amps(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
+           kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * sizeof(DenseClassDev) + 16 * sizeof(float);
+}
+
+// ---- gate tables and phase tables ---------------------------------------------------------
+
+__global__ void dense_gate_table_kernel(const tlq_gate* gates, int n_gates, const double* theta, int n_params,
+                                        float2* out) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_gates) return;
+    const tlq_gate G = gates[g];
+    const double a = G.param >= 0 ? theta[G.param] : G.angle;
+    double s, c;
+    sincos(0.5 * a, &s, &c);
+    out[g] = make_float2((float)c, (float)s);
+}
+
+// entry e: exp(-i a/2 * mult[e]) with a the angle of gate tab_gate[e]
+__global__ void dense_phase_table_kernel(const tlq_gate* gates, const int32_t* tab_gate, const int32_t* tab_mult,
+                                         int entries, const double* theta, float2* out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= entries) return;
+    const tlq_gate G = gates[tab_gate[e]];
+    const double a = G.param >= 0 ? theta[G.param] : G.angle;
+    double s, c;
+    sincos(0.5 * a * (double)tab_mult[e], &s, &c);
+    out[e] = make_float2((float)c, (float)-s);
+}
+
+// ---- measurement of one Pauli term (X/Y letters, or any term on the per-gate path) ---------
+
+constexpr int kMeasBlocks = 1024;
+constexpr int kMeasThreads = 256;
+
+__global__ void __launch_bounds__(kMeasThreads) term_measure_kernel(const float2* psi, uint64_t N, uint32_t flip,
+                                                                    uint32_t zy, int ny, double* partial) {
+    float2 f0;   // (-i)^ny
+    const int q = ny & 3;
+    f0.x = q == 0 ? 1.f : q == 2 ? -1.f : 0.f;
+    f0.y = q == 1 ? -1.f : q == 3 ? 1.f : 0.f;
+    float acc = 0.f;
+    for (uint64_t x = (uint64_t)blockIdx.x * kMeasThreads + threadIdx.x; x < N; x += (uint64_t)gridDim.x * kMeasThreads) {
+        const float2 a = psi[x];
+        const float2 v = psi[x ^ flip];
+        float2 t = cmul(f0, v);
+        if (__popc((uint32_t)x & zy) & 1) { t.x = -t.x; t.y = -t.y; }
+        acc += a.x * t.x + a.y * t.y;
+    }
+    __shared__ float red[kMeasThreads / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float e = 0.f;
+        for (int w = 0; w < kMeasThreads / 32; ++w) e += red[w];
+        partial[blockIdx.x] = (double)e;
+    }
+}
+
+struct Neumaier {
+    double s = 0, c = 0;
+    __device__ void add(double x) {
+        const double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    __device__ double value() const { return s + c; }
+};
+
+// out[0] (+)= coeff * sum of partial[0..n) in fixed order
+__global__ void reduce_partials_kernel(const double* partial, int n, double coeff, double* out, int accumulate) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Neumaier acc;
+    if (accumulate) acc.add(*out);
+    for (int i = 0; i < n; ++i) acc.add(coeff * partial[i]);
+    *out = acc.value();
+}
+
+// ---- plain per-gate sweeps (baseline) -----------------------------------------------------
+
+__global__ void pergate_rot_kernel(float2* psi, uint64_t half, int q, int kind, const float2* GT, int gate) {
+    const float2 cs = GT[gate];
+    const float c = cs.x, s = cs.y;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < half; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x0 = ((i >> q) << (q + 1)) | (i & ((1ull << q) - 1));
+        const uint64_t x1 = x0 | (1ull << q);
+        const float2 a0 = psi[x0], a1 = psi[x1];
+        float2 b0, b1;
+        if (kind == TLQ_RY) {
+            b0 = make_float2(c * a0.x - s * a1.x, c * a0.y - s * a1.y);
+            b1 = make_float2(s * a0.x + c * a1.x, s * a0.y + c * a1.y);
+        } else {
+            b0 = make_float2(c * a0.x + s * a1.y, c * a0.y - s * a1.x);
+            b1 = make_float2(c * a1.x + s * a0.y, c * a1.y - s * a0.x);
+        }
+        psi[x0] = b0;
+        psi[x1] = b1;
+    }
+}
+
+__global__ void pergate_diag_kernel(float2* psi, uint64_t N, int kind, int q0, int q1, const float2* GT, int gate) {
+    float2 f0 = make_float2(1.f, 0.f), f1 = f0;
+    if (kind != TLQ_CZ) {
+        const float2 cs = GT[gate];
+        f0 = make_float2(cs.x, -cs.y);   // z = +1
+        f1 = make_float2(cs.x, cs.y);    // z = -1
+    }
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+        const int b0 = (int)((x >> q0) & 1);
+        if (kind == TLQ_RZ) {
+            psi[x] = cmul(psi[x], b0 ? f1 : f0);
+        } else {
+            const int b1 = (int)((x >> q1) & 1);
+            if (kind == TLQ_CZ) {
+                if (b0 & b1) { float2 v = psi[x]; psi[x] = make_float2(-v.x, -v.y); }
+            } else {
+                psi[x] = cmul(psi[x], (b0 ^ b1) ? f1 : f0);
+            }
+        }
+    }
+}
+
+__global__ void init_state_kernel(float2* psi, uint64_t N) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x)
+        psi[x] = make_float2(x == 0 ? 1.f : 0.f, 0.f);
+}
+
+}  // namespace
+
+size_t dense_partial_count(int n_eff) {
+    const size_t tiles = (size_t)1 << (n_eff - kDenseTileBits);
+    return tiles > (size_t)kMeasBlocks ? tiles : (size_t)kMeasBlocks;
+}
+
+int launch_dense(DenseLaunch& L, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    const uint64_t N = 1ull << L.n_eff;
+    const int grid_sweep = L.sm_count * 8;
+    float2* psi = (float2*)L.state;
+    int launches = 0;
+    const size_t smem = dense_pass_smem();
+    if ((e = cudaFuncSetAttribute(dense_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return (int)e;
+    for (int b = 0; b < L.B; ++b) {
+        const double* th = L.theta + (size_t)b * L.n_params;
+        float2* GT = (float2*)L.gate_table + (size_t)b * L.n_gates;
+        float2* PT = (float2*)L.phase_tab + (size_t)b * (L.tab_entries > 0 ? L.tab_entries : 1);
+        if (L.n_gates > 0) {
+            dense_gate_table_kernel<<<(L.n_gates + 255) / 256, 256, 0, st>>>(L.gates, L.n_gates, th, L.n_params, GT);
+            ++launches;
+        }
+        if (L.tab_entries > 0 && !L.per_gate) {
+            dense_phase_table_kernel<<<(L.tab_entries + 255) / 256, 256, 0, st>>>(L.gates, L.tab_gate, L.tab_mult,
+                                                                                 L.tab_entries, th, PT);
+            ++launches;
+        }
+        init_state_kernel<<<grid_sweep, 256, 0, st>>>(psi, N);
+        ++launches;
+        if (b == 0 && L.ev_begin && (e = cudaEventRecord((cudaEvent_t)L.ev_begin, st)) != cudaSuccess) return (int)e;
+        double* eout = L.energy + b;
+        if ((e = cudaMemsetAsync(eout, 0, sizeof(double), st)) != cudaSuccess) return (int)e;
+        if (L.per_gate) {
+            for (int g = 0; g < L.n_gates; ++g) {
+                const tlq_gate G = L.host_gates[g];
+                if (G.kind == TLQ_RX || G.kind == TLQ_RY)
+                    pergate_rot_kernel<<<grid_sweep, 256, 0, st>>>(psi, N / 2, G.q0, G.kind, GT, g);
+                else
+                    pergate_diag_kernel<<<grid_sweep, 256, 0, st>>>(psi, N, G.kind, G.q0, G.q1, GT, g);
+                ++launches;
+            }
+            for (int t = 0; t < L.n_all_terms; ++t) {
+                const DenseXTermDev T = L.host_all_terms[t];
+                term_measure_kernel<<<kMeasBlocks, kMeasThreads, 0, st>>>(psi, N, T.flip, T.zy, T.ny, L.partial);
+                reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, kMeasBlocks, T.coeff, eout, 1);
+                launches += 2;
+            }
+        } else {
+            const int ntiles = (int)(N >> kDenseTileBits);
+            PassArgs A;
+            A.layers = L.layers;
+            A.classes = L.classes;
+            A.dists = L.dists;
+            A.energy_class_off = L.energy_class_off;
+            A.energy_nclass = L.energy_nclass;
+            A.zterms = L.zterms;
+            A.n_zterms = L.n_zterms;
+            A.gates = L.gates;
+            A.GT = GT;
+            A.ptab = PT;
+            A.state = psi;
+            A.n_eff = L.n_eff;
+            A.partial = L.partial;
+            bool measured = false;
+            for (int p = 0; p < L.n_passes; ++p) {
+                A.pass = L.host_passes[p];
+                dense_pass_kernel<<<ntiles, kThreads, smem, st>>>(A);
+                ++launches;
+                if (A.pass.measure) measured = true;
+            }
+            if (measured) {
+                reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, ntiles, 1.0, eout, 1);
+                ++launches;
+            }
+            for (int t = 0; t < L.n_xterms; ++t) {
+                const DenseXTermDev T = L.host_xterms[t];
+                term_measure_kernel<<<kMeasBlocks, kMeasThreads, 0, st>>>(psi, N, T.flip, T.zy, T.ny, L.partial);
+                reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, kMeasBlocks, T.coeff, eout, 1);
+                launches += 2;
+            }
+        }
+        if (b == L.B - 1 && L.ev_end && (e = cudaEventRecord((cudaEvent_t)L.ev_end, st)) != cudaSuccess) return (int)e;
+        if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+    }
+    L.launches = launches;
+    return 0;
+}
+
+}  // namespace tlq

@@ -58,6 +58,68 @@ constexpr int kMaxConeW = 20;      // widest cone on the cone path (global-memor
 constexpr int kCtaThreads = 512;
 constexpr int kMaxPassSlots = 4 + 2 * 20;  // gradient values per adjoint pass: 4 rotations + RZ/pair per qubit
 
+// Dense statevector path (circuits with non-adjacent two-qubit gates): the 2^n state lives
+// in HBM and is processed in passes over tiles of 2^13 amplitudes. A "low" tile is 2^13
+// contiguous amplitudes (qubits 0..12); a "strided" tile keeps qubits 0..3 (16 contiguous
+// amplitudes, 128 bytes) and 9 higher qubits a..a+8. Inside a tile, rotations run as
+// 16-amplitude register passes; the diagonal gates of a layer are grouped into angle
+// classes and applied from a phase table indexed by a popcount.
+constexpr int kDenseTileBits = 13;
+constexpr int kDenseStridedBits = 9;
+constexpr int kDenseMaxQubits = 31;
+constexpr int kDenseMaxLayerClasses = 64;  // per layer (+ energy classes)
+constexpr int kDenseMaxDistWords = 512;
+constexpr int kDenseMaxTab = 1024;
+
+struct DensePassDev {
+    int32_t strided;          // 0: low tile, 1: strided tile
+    int32_t a;                // strided: global qubit of local bit 4
+    int32_t ngroups;          // register sub-passes
+    int32_t diag_layer;       // -1, or the layer whose diagonal follows this pass's rotations
+    int32_t measure;          // accumulate the Z-type energy after the rotations (and diagonal)
+    int32_t store;            // write the tile back (0: read-only measurement pass)
+    int32_t group_s[4];       // local start bit of each sub-pass
+    uint32_t group_mask[4];   // bits (relative to group_s) carrying a rotation
+    int32_t gate[16];         // rotation gate per local bit (-1 none)
+};
+
+// A class of diagonal terms counted by popcounts over distance masks:
+//   kind 0: RZ/RZZ gates sharing one angle; phase exp(-i a/2 (N - 2 c)), c = sum_d popc((x ^ x>>d) & M_d)
+//           + popc(x & single), looked up in a table of N+1 entries at tab_off;
+//   kind 1: CZ gates; sign (-1)^c with c = sum_d popc((x & x>>d) & M_d);
+//   kind 2: Z / ZZ energy terms sharing one coefficient; energy coeff * (N - 2 c) per amplitude.
+struct DenseClassDev {
+    int32_t kind;
+    int32_t gate;
+    int32_t nterms;
+    int32_t ndist;
+    int32_t dist_off;         // (d, mask) pairs in the distance array
+    int32_t tab_off;
+    uint32_t single;
+    int32_t pad;
+    double coeff;
+};
+struct DenseLayerDev { int32_t nclass, class_off, pad0, pad1; };
+struct DenseXTermDev { uint32_t flip, zy; int32_t ny, pad; double coeff; };   // terms with X/Y letters
+struct DenseZTermDev { uint32_t mask; int32_t pad; double coeff; };           // Z strings of 3+ sites
+
+struct DensePlan {
+    int n_eff = 0;                          // qubits of the state (>= kDenseTileBits; extra qubits stay |0>)
+    std::vector<DensePassDev> passes;
+    std::vector<DenseLayerDev> layers;
+    std::vector<DenseClassDev> classes;     // diagonal-layer classes, then energy classes
+    std::vector<int32_t> dists;             // (d, mask) pairs
+    int32_t energy_class_off = 0, energy_nclass = 0;
+    std::vector<DenseZTermDev> zterms;
+    std::vector<DenseXTermDev> xterms;
+    std::vector<int32_t> tab_gate;          // per phase-table entry: gate providing the angle
+    std::vector<int32_t> tab_mult;          // per entry: N - 2c
+    std::vector<DenseXTermDev> all_terms;   // every term (plain per-gate path measures them one by one)
+    int max_classes_per_layer = 0;
+    int max_dists = 0;
+    bool fits_fused = true;                 // staged class data fits the pass kernel's shared memory
+};
+
 // ---------------------------------------------------------------------------------------
 // Host-side objects.
 // ---------------------------------------------------------------------------------------
@@ -110,7 +172,10 @@ struct Plan {
     std::vector<double> term_coeff;       // per term
     int max_w = 0;
     std::string why_dense;                // reason the dense path was chosen
+    std::shared_ptr<DensePlan> dense;     // dense statevector plan (when n <= kDenseMaxQubits)
 };
+
+std::shared_ptr<DensePlan> make_dense_plan(const Circuit& c, const Ham& h, std::string* err);
 
 std::string plan_circuit_layers(Circuit& c);   // fills c.layers; returns "" or error
 std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err);
@@ -167,25 +232,46 @@ int launch_cone(ConeLaunch& L, void* stream);
 int cone_smem_grid(bool fp64, bool grad, int smem_bytes, int sm_count);
 
 struct DenseLaunch {
-    int n = 0;
-    const int32_t* prog = nullptr;        // dense layer program (device)
-    int32_t prog_len = 0;
+    int n_eff = 0;
+    const DensePassDev* passes = nullptr;
+    int32_t n_passes = 0;
+    const DenseLayerDev* layers = nullptr;
+    const DenseClassDev* classes = nullptr;
+    const int32_t* dists = nullptr;
+    int32_t energy_class_off = 0, energy_nclass = 0;
+    const DenseZTermDev* zterms = nullptr;
+    int32_t n_zterms = 0;
+    const DenseXTermDev* xterms = nullptr;
+    int32_t n_xterms = 0;
+    const int32_t* tab_gate = nullptr;
+    const int32_t* tab_mult = nullptr;
+    int32_t tab_entries = 0;
+    int32_t max_classes = 0, max_dists = 0;
     const tlq_gate* gates = nullptr;
     int32_t n_gates = 0, n_params = 0, B = 0;
-    const double* theta = nullptr;
-    const int32_t* term_desc = nullptr;   // per term: flip, zy, ny (int32 x4)
-    const double* term_coeff = nullptr;
-    int32_t n_terms = 0;
-    void* gate_table = nullptr;
-    void* state = nullptr;                // 2^n real2
-    double* partial = nullptr;            // reduction scratch
-    int32_t* err = nullptr;
-    double* energy = nullptr;
-    bool fp64 = false;
+    const double* theta = nullptr;        // [B][n_params]
+    // workspace
+    void* gate_table = nullptr;           // [B][n_gates] float2
+    void* phase_tab = nullptr;            // [B][tab_entries] float2
+    void* state = nullptr;                // 2^n_eff float2
+    double* partial = nullptr;            // per-tile / per-block partial sums
+    double* xpart = nullptr;              // [n_xterms] per set
+    // outputs
+    double* energy = nullptr;             // [B]
     bool per_gate = false;                // plain per-gate sweeps (baseline)
     int sm_count = 0;
+    void* ev_begin = nullptr;
+    void* ev_end = nullptr;
+    int launches = 0;
+    // host copies (pass descriptors go to the kernel by value)
+    const tlq_gate* host_gates = nullptr;
+    const DensePassDev* host_passes = nullptr;
+    const DenseXTermDev* host_xterms = nullptr;
+    const DenseXTermDev* host_all_terms = nullptr;
+    int32_t n_all_terms = 0;
 };
+size_t dense_partial_count(int n_eff);
 
-int launch_dense(const DenseLaunch& L, void* stream);
+int launch_dense(DenseLaunch& L, void* stream);
 
 }  // namespace tlq

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 
 namespace tlq {
 
@@ -92,10 +93,15 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
     P->term_coeff.resize(T);
     for (int t = 0; t < T; ++t) P->term_coeff[t] = h.terms[t].coeff;
 
+    if (c.n <= kDenseMaxQubits) {
+        std::string derr;
+        P->dense = make_dense_plan(c, h, &derr);
+    }
     if (!c.nearest_neighbour) {
         P->path = TLQ_PATH_DENSE;
         P->why_dense = "two-qubit gate between non-adjacent qubits";
-        return P;
+        if (!P->dense && err) *err = "non-local circuit on more than " + std::to_string(kDenseMaxQubits) + " qubits";
+        return P->dense ? P : nullptr;
     }
     const LayerIndex ix = index_layers(c);
     std::vector<char> inS(c.n, 0), inc(c.gates.size(), 0);
@@ -149,7 +155,9 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
         if (W > kMaxConeW) {
             P->path = TLQ_PATH_DENSE;
             P->why_dense = "light cone wider than " + std::to_string(kMaxConeW) + " qubits";
-            return P;
+            if (!P->dense && err) *err = "light cones wider than " + std::to_string(kMaxConeW) + " qubits on more than " +
+                                         std::to_string(kDenseMaxQubits) + " qubits";
+            return P->dense ? P : nullptr;
         }
         // Emit the program in forward layer order: per layer a header and one fixed record
         // per window qubit (see internal.h). A layer whose cone gates put two RZ on one
@@ -270,6 +278,246 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
         for (auto& e : pentries[p]) { P->pmap_idx.push_back(e.first); P->pmap_coeff.push_back(e.second); }
     (void)err;
     return P;
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Dense statevector plan.
+// ---------------------------------------------------------------------------------------
+
+namespace {
+
+// Collects pairs/singles of one class; returns false if the position is already used
+// (the caller then opens another class with the same angle).
+struct ClassBuild {
+    int kind = 0, gate = -1;
+    double coeff = 0;
+    std::map<int, uint32_t> dist;   // d -> mask of lower qubits
+    uint32_t single = 0;
+    int nterms = 0;
+    bool add_pair(int u, int v) {
+        if (u > v) std::swap(u, v);
+        uint32_t& m = dist[v - u];
+        if (m & (1u << u)) return false;
+        m |= 1u << u;
+        ++nterms;
+        return true;
+    }
+    bool add_single(int q) {
+        if (single & (1u << q)) return false;
+        single |= 1u << q;
+        ++nterms;
+        return true;
+    }
+};
+
+void emit_class(DensePlan& D, const ClassBuild& cb) {
+    DenseClassDev c{};
+    c.kind = cb.kind;
+    c.gate = cb.gate;
+    c.nterms = cb.nterms;
+    c.dist_off = (int32_t)D.dists.size() / 2;
+    c.ndist = (int32_t)cb.dist.size();
+    for (auto& kv : cb.dist) { D.dists.push_back(kv.first); D.dists.push_back((int32_t)kv.second); }
+    c.single = cb.single;
+    c.coeff = cb.coeff;
+    c.tab_off = -1;
+    if (cb.kind == 0) {
+        c.tab_off = (int32_t)D.tab_gate.size();
+        for (int k = 0; k <= cb.nterms; ++k) {
+            D.tab_gate.push_back(cb.gate);
+            D.tab_mult.push_back(cb.nterms - 2 * k);
+        }
+    }
+    D.max_dists = std::max(D.max_dists, c.ndist);
+    D.classes.push_back(c);
+}
+
+// Adds one term to the first class of `list` that accepts it, or opens a new class.
+template <typename F>
+void place(std::vector<ClassBuild>& list, const ClassBuild& proto, F add) {
+    for (auto& cb : list)
+        if (add(cb)) return;
+    list.push_back(proto);
+    add(list.back());
+}
+
+}  // namespace
+
+std::shared_ptr<DensePlan> make_dense_plan(const Circuit& c, const Ham& h, std::string* err) {
+    if (c.n > kDenseMaxQubits) {
+        if (err) *err = "dense statevector path needs n <= " + std::to_string(kDenseMaxQubits);
+        return nullptr;
+    }
+    auto D = std::make_shared<DensePlan>();
+    const int n_eff = std::max(c.n, kDenseTileBits);
+    D->n_eff = n_eff;
+    // diagonal classes per layer
+    const int L = (int)c.layers.size();
+    for (int l = 0; l < L; ++l) {
+        DenseLayerDev ld{};
+        ld.class_off = (int32_t)D->classes.size();
+        std::map<std::pair<int, uint64_t>, std::vector<ClassBuild>> xor_cls;   // key: (param or -1, angle bits)
+        std::vector<ClassBuild> and_cls;
+        for (int g : c.layers[l].diag) {
+            const tlq_gate& G = c.gates[g];
+            if (G.kind == TLQ_CZ) {
+                ClassBuild proto;
+                proto.kind = 1;
+                place(and_cls, proto, [&](ClassBuild& cb) { return cb.add_pair(G.q0, G.q1); });
+                continue;
+            }
+            uint64_t bits = 0;
+            if (G.param < 0) std::memcpy(&bits, &G.angle, 8);
+            auto& list = xor_cls[{G.param, bits}];
+            ClassBuild proto;
+            proto.kind = 0;
+            proto.gate = g;
+            if (G.kind == TLQ_RZZ) place(list, proto, [&](ClassBuild& cb) { return cb.add_pair(G.q0, G.q1); });
+            else place(list, proto, [&](ClassBuild& cb) { return cb.add_single(G.q0); });
+        }
+        for (auto& kv : xor_cls)
+            for (auto& cb : kv.second) emit_class(*D, cb);
+        for (auto& cb : and_cls) emit_class(*D, cb);
+        ld.nclass = (int32_t)D->classes.size() - ld.class_off;
+        D->max_classes_per_layer = std::max(D->max_classes_per_layer, (int)ld.nclass);
+        D->layers.push_back(ld);
+    }
+    // energy: Z/ZZ terms in coefficient classes, longer Z strings, and X/Y terms
+    D->energy_class_off = (int32_t)D->classes.size();
+    std::map<uint64_t, std::vector<ClassBuild>> ecls;
+    for (const Term& t : h.terms) {
+        bool zonly = true;
+        for (char ch : t.letters) zonly &= (ch == 'Z');
+        if (zonly && t.sites.size() <= 2) {
+            uint64_t bits;
+            std::memcpy(&bits, &t.coeff, 8);
+            ClassBuild proto;
+            proto.kind = 2;
+            proto.coeff = t.coeff;
+            if (t.sites.size() == 2)
+                place(ecls[bits], proto, [&](ClassBuild& cb) { return cb.add_pair(t.sites[0], t.sites[1]); });
+            else
+                place(ecls[bits], proto, [&](ClassBuild& cb) { return cb.add_single(t.sites[0]); });
+        } else if (zonly) {
+            DenseZTermDev z{};
+            for (int s : t.sites) z.mask |= 1u << s;
+            z.coeff = t.coeff;
+            D->zterms.push_back(z);
+        }
+        {
+            DenseXTermDev x{};
+            for (size_t k = 0; k < t.sites.size(); ++k) {
+                const uint32_t bit = 1u << t.sites[k];
+                const char ch = t.letters[k];
+                if (ch == 'X' || ch == 'Y') x.flip |= bit;
+                if (ch == 'Y' || ch == 'Z') x.zy |= bit;
+                if (ch == 'Y') ++x.ny;
+            }
+            x.coeff = t.coeff;
+            D->all_terms.push_back(x);
+        }
+        if (!zonly) {
+            DenseXTermDev x{};
+            for (size_t k = 0; k < t.sites.size(); ++k) {
+                const uint32_t bit = 1u << t.sites[k];
+                const char ch = t.letters[k];
+                if (ch == 'X' || ch == 'Y') x.flip |= bit;
+                if (ch == 'Y' || ch == 'Z') x.zy |= bit;
+                if (ch == 'Y') ++x.ny;
+            }
+            x.coeff = t.coeff;
+            D->xterms.push_back(x);
+        }
+    }
+    for (auto& kv : ecls)
+        for (auto& cb : kv.second) emit_class(*D, cb);
+    D->energy_nclass = (int32_t)D->classes.size() - D->energy_class_off;
+
+    // pass schedule: per layer a low pass (qubits 0..12) and strided passes of 9 qubits
+    std::vector<int> chunk_a;
+    for (int a = kDenseTileBits; a < n_eff; a += kDenseStridedBits)
+        chunk_a.push_back(std::min(a, n_eff - kDenseStridedBits));
+    auto plan_groups = [](DensePassDev& p, uint32_t bits) {
+        p.ngroups = 0;
+        while (bits) {
+            const int b = __builtin_ctz(bits);
+            const int s = b < 4 ? 0 : std::min(b, kDenseTileBits - 4);
+            p.group_s[p.ngroups] = s;
+            p.group_mask[p.ngroups] = (bits >> s) & 15u;
+            bits &= ~(15u << s);
+            ++p.ngroups;
+        }
+    };
+    auto blank = [](int strided, int a) {
+        DensePassDev p{};
+        p.strided = strided;
+        p.a = a;
+        p.diag_layer = -1;
+        p.store = 1;
+        for (int i = 0; i < 16; ++i) p.gate[i] = -1;
+        return p;
+    };
+    for (int l = 0; l < L; ++l) {
+        std::vector<char> done(n_eff, 0);
+        const size_t first = D->passes.size();
+        DensePassDev low = blank(0, 0);
+        uint32_t lowbits = 0;
+        for (int g : c.layers[l].rot) {
+            const int q = c.gates[g].q0;
+            if (q < kDenseTileBits) { low.gate[q] = g; lowbits |= 1u << q; done[q] = 1; }
+        }
+        if (lowbits) { plan_groups(low, lowbits); D->passes.push_back(low); }
+        for (int a : chunk_a) {
+            DensePassDev p = blank(1, a);
+            uint32_t bits = 0;
+            for (int g : c.layers[l].rot) {
+                const int q = c.gates[g].q0;
+                if (q >= a && q < a + kDenseStridedBits && !done[q]) {
+                    p.gate[4 + q - a] = g;
+                    bits |= 1u << (4 + q - a);
+                    done[q] = 1;
+                }
+            }
+            if (bits) { plan_groups(p, bits); D->passes.push_back(p); }
+        }
+        if (!c.layers[l].diag.empty()) {
+            if (D->passes.size() == first) {
+                DensePassDev p = blank(0, 0);
+                p.ngroups = 1;
+                p.group_s[0] = kDenseTileBits - 4;
+                p.group_mask[0] = 0;
+                D->passes.push_back(p);
+            }
+            D->passes.back().diag_layer = l;
+        }
+    }
+    if (D->energy_nclass > 0 || !D->zterms.empty()) {
+        if (D->passes.empty()) {
+            DensePassDev p = blank(0, 0);
+            p.ngroups = 1;
+            p.group_s[0] = kDenseTileBits - 4;
+            p.group_mask[0] = 0;
+            p.store = 0;
+            D->passes.push_back(p);
+        }
+        D->passes.back().measure = 1;
+    }
+    // the pass kernel stages one layer's classes plus the energy classes in shared memory
+    int e_words = 0;
+    for (int k = 0; k < D->energy_nclass; ++k) e_words += 2 * D->classes[D->energy_class_off + k].ndist;
+    for (const DenseLayerDev& ld : D->layers) {
+        int words = e_words, tab = 0;
+        for (int k = 0; k < ld.nclass; ++k) {
+            const DenseClassDev& cl = D->classes[ld.class_off + k];
+            words += 2 * cl.ndist;
+            tab += cl.kind == 0 ? cl.nterms + 1 : 0;
+        }
+        if (ld.nclass + D->energy_nclass > kDenseMaxLayerClasses || words > kDenseMaxDistWords || tab > kDenseMaxTab)
+            D->fits_fused = false;
+    }
+    if (D->energy_nclass > kDenseMaxLayerClasses || e_words > kDenseMaxDistWords) D->fits_fused = false;
+    return D;
 }
 
 }  // namespace tlq

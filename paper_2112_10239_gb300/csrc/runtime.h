@@ -27,9 +27,12 @@ struct PlanEntry {
     double* d_pmap_coeff = nullptr;
     tlq_gate* d_gates = nullptr;
     // dense path device buffers
-    int32_t* d_dprog = nullptr;
-    int32_t dprog_len = 0;
-    int32_t* d_dterms = nullptr;
+    DenseLayerDev* d_dlayers = nullptr;
+    DenseClassDev* d_dclasses = nullptr;
+    int32_t* d_ddists = nullptr;
+    DenseZTermDev* d_dzterms = nullptr;
+    int32_t* d_dtab_gate = nullptr;
+    int32_t* d_dtab_mult = nullptr;
     // work list cache (keyed by batch size and precision)
     int wl_B = -1;
     bool wl_fp64 = false;

@@ -1,0 +1,147 @@
+"""GPU parity of the dense statevector path (through the C-ABI) against the CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dense
+from paper_2112_10239_gb300 import workloads as W
+from parity import check_energy
+
+pytestmark = pytest.mark.gpu
+
+
+def _energy(ctx, prob, theta=None):
+    from paper_2112_10239_gb300 import binding as B
+    c, h = ctx.problem(prob)
+    try:
+        path, *_ = B.tlq_plan_info(ctx.h, c.h, h.h, len(prob.terms))
+        E = B.tlq_expectation(ctx.h, c.h, h.h, prob.theta if theta is None else theta)
+        return E, path
+    finally:
+        c.close()
+        h.close()
+
+
+def _oracle(prob, theta):
+    return np.array([dense.energy(prob.n, prob.gates, prob.terms, th) for th in theta])
+
+
+@pytest.fixture(scope="module")
+def plain_ctx():
+    """A context whose fuse_k = 1 selects plain per-gate sweeps (the baseline path)."""
+    from paper_2112_10239_gb300 import binding as B
+    cfg = B.tlq_config(0, 0, 0, B.TLQ_FP32, 1)
+    import ctypes
+    h = ctypes.c_void_p()
+    B._check(B.lib().tlq_init(ctypes.byref(cfg), ctypes.byref(h)))
+    ctx = B.Context.__new__(B.Context)
+    ctx.h = h
+    yield ctx
+    ctx.close()
+
+
+@pytest.mark.parametrize("n,p,seed", [(10, 1, 0), (12, 2, 1), (14, 3, 2), (16, 4, 3), (20, 4, 4)])
+def test_qaoa_reduced_vs_oracle(tlq, n, p, seed):
+    from paper_2112_10239_gb300 import binding as B
+    prob = W.qaoa_problem(n, p, 3, seed)
+    E, path = _energy(tlq, prob)
+    assert path == B.TLQ_PATH_DENSE
+    check_energy(E, _oracle(prob, prob.theta))
+
+
+def test_qaoa_n24_vs_oracle(tlq):
+    prob = W.qaoa_problem(24, 4, 1, seed=7)
+    E, _ = _energy(tlq, prob)
+    check_energy(E, _oracle(prob, prob.theta))
+
+
+def test_qaoa_n28_closed_forms(tlq):
+    # full size: p=1 from |0..0> gives E = |edges| cos^2(beta_1); every beta = 0 gives E = |edges|
+    prob = W.qaoa_n28_p4(B=2)
+    m = len(prob.meta["edges"])
+    assert m == 42
+    E, _ = _energy(tlq, prob)
+    assert np.all(np.abs(E) <= m + 1e-4)
+    th = prob.theta.copy()
+    th[:, 1::2] = 0.0
+    E0, _ = _energy(tlq, prob, th)
+    check_energy(E0, [m, m])
+    one = W.qaoa_problem(28, 1, 3, seed=2, edges=prob.meta["edges"])
+    E1, _ = _energy(tlq, one)
+    check_energy(E1, [m * math.cos(b) ** 2 for b in one.theta[:, 1]])
+
+
+def test_qaoa_n28_deterministic(tlq):
+    prob = W.qaoa_n28_p4()
+    a, _ = _energy(tlq, prob)
+    b, _ = _energy(tlq, prob)
+    assert a[0] == b[0]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_nonlocal_mixed_circuits(tlq, seed):
+    # non-adjacent RZZ/CZ, RX/RY/RZ with distinct angles, X/Y/Z terms of 1-3 sites
+    rng = np.random.default_rng(50 + seed)
+    n = int(rng.integers(4, 15))
+    gates, P = [], 0
+    for _ in range(3):
+        for q in range(n):
+            gates.append((W.RY if rng.random() < 0.5 else W.RX, q, -1, P, 0.0)); P += 1
+        for q in range(n):
+            if rng.random() < 0.5:
+                gates.append((W.RZ, q, -1, P, 0.0)); P += 1
+        for _ in range(n):
+            u, v = rng.choice(n, 2, replace=False)
+            if rng.random() < 0.5:
+                gates.append((W.CZ, int(u), int(v), -1, 0.0))
+            else:
+                gates.append((W.RZZ, int(u), int(v), P, 0.0)); P += 1
+    terms = []
+    for _ in range(2 * n):
+        k = int(rng.integers(1, 4))
+        sites = tuple(int(s) for s in rng.choice(n, k, replace=False))
+        terms.append((float(rng.uniform(-1, 1)), sites, "".join("XYZ"[int(rng.integers(3))] for _ in sites)))
+    theta = rng.uniform(0, 2 * math.pi, size=(2, P))
+    prob = W.Problem(n=n, gates=gates, n_params=P, terms=terms, theta=theta)
+    E, _ = _energy(tlq, prob)
+    check_energy(E, _oracle(prob, theta))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_tiny_dense(tlq, n):
+    gates = [(W.RY, q, -1, q, 0.0) for q in range(n)]
+    if n >= 3:
+        gates.append((W.RZZ, 0, 2, n, 0.0))
+    P = n + (1 if n >= 3 else 0)
+    terms = [(1.0, (0,), "X")] + ([(0.5, (0, n - 1), "ZZ")] if n > 1 else [])
+    theta = np.random.default_rng(n).uniform(0, 6, size=(1, P))
+    prob = W.Problem(n=n, gates=gates, n_params=P, terms=terms, theta=theta)
+    E, _ = _energy(tlq, prob)
+    check_energy(E, _oracle(prob, theta))
+
+
+def test_plain_per_gate_baseline(plain_ctx, tlq):
+    # the per-gate sweep baseline agrees with the fused passes and the oracle
+    prob = W.qaoa_problem(16, 3, 2, seed=11)
+    Ep, _ = _energy(plain_ctx, prob)
+    Ef, _ = _energy(tlq, prob)
+    Er = _oracle(prob, prob.theta)
+    check_energy(Ep, Er)
+    check_energy(Ef, Er)
+    t = W.tfim_problem(12, 3, 2, seed=1, h_range=(0.5, 1.5))   # cone-path circuit run as plain sweeps
+    Ept, _ = _energy(plain_ctx, t)
+    check_energy(Ept, _oracle(t, t.theta))
+
+
+def test_dense_gradient_reports_unsupported(tlq):
+    from paper_2112_10239_gb300 import binding as B
+    prob = W.qaoa_problem(10, 1, 1, seed=0)
+    c, h = tlq.problem(prob)
+    try:
+        with pytest.raises(B.TLQError) as ei:
+            B.tlq_expectation_grad(tlq.h, c.h, h.h, prob.theta)
+        assert ei.value.status == B.TLQ_EUNSUPPORTED
+    finally:
+        c.close()
+        h.close()
