@@ -235,6 +235,7 @@ static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const
     L.state = ws->take(((size_t)1 << D.n_eff) * 8);
     L.partial = (double*)ws->take(dense_partial_count(D.n_eff) * sizeof(double));
     L.energy = energy_dev;
+    L.err = ctx->d_err;
     L.per_gate = per_gate;
     L.sm_count = ctx->sm_count;
     L.host_gates = c.gates.data();

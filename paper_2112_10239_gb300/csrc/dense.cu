@@ -45,7 +45,8 @@ struct PassArgs {
     const float2* ptab;     // phase tables of this set
     float2* state;
     int32_t n_eff;
-    double* partial;        // per-tile energy partials
+    double* partial;        // per-CTA energy partials
+    int32_t* err;           // kernel error word
 };
 
 // Global amplitude index of local tile index t.
@@ -68,28 +69,47 @@ __device__ __forceinline__ int class_count(const DenseClassDev& c, const int32_t
     return cnt;
 }
 
-__global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassArgs A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* tile = reinterpret_cast<float2*>(smem_raw);                               // padded_amps(13)
-    float2* s_tab = tile + padded_amps(kDenseTileBits);                              // kMaxTab
+// ---- asynchronous tile copies ------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Each thread copies its 8 x 16 bytes (2 amplitudes each) of tile `t` into the padded
+// shared buffer with cp.async (global -> shared without a register round trip), then
+// commits them as one group.
+__device__ __forceinline__ void issue_tile(const DensePassDev& P, uint32_t t, const float2* state, float2* buf,
+                                           int tid) {
+#pragma unroll
+    for (int k = 0; k < kTile / 2 / kThreads; ++k) {
+        const uint32_t i = 2u * (uint32_t)(tid + kThreads * k);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(buf + pad16((int)i))),
+                     "l"(state + tile_x(P, t, i))
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void wait_tiles() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Persistent pass kernel: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// with two shared-memory tile buffers; the cp.async copy of the next tile runs while the
+// current one is processed. The last register pass writes its 16 amplitudes straight to HBM.
+__global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_constant__ PassArgs A) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2* bufs = reinterpret_cast<float2*>(smem_raw);                              // 2 x padded_amps(13)
+    float2* s_tab = bufs + 2 * padded_amps(kDenseTileBits);                          // kMaxTab
     int32_t* s_dist = reinterpret_cast<int32_t*>(s_tab + kMaxTab);                   // kMaxDistWords
     DenseClassDev* s_cls = reinterpret_cast<DenseClassDev*>(s_dist + kMaxDistWords); // kMaxLayerClasses
     float* s_red = reinterpret_cast<float*>(s_cls + kMaxLayerClasses);               // 16
     const DensePassDev& P = A.pass;
-    const uint32_t t_id = blockIdx.x;
     const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const uint32_t ntiles = 1u << (A.n_eff - kDenseTileBits);
 
-    // load the tile (float4 = 2 amplitudes; rows of 16 amplitudes stay contiguous)
-    {
-        const float4* src = reinterpret_cast<const float4*>(A.state);
-#pragma unroll
-        for (int k = 0; k < kTile / 2 / kThreads; ++k) {
-            const uint32_t i = 2u * (uint32_t)(tid + kThreads * k);
-            const float4 v = src[tile_x(P, t_id, i) >> 1];
-            *reinterpret_cast<float4*>(tile + pad16((int)i)) = v;
-        }
-    }
-    // stage the diagonal classes of this pass's layer and the energy classes
+    if (blockIdx.x < ntiles) issue_tile(P, blockIdx.x, A.state, bufs, tid);
+
+    // stage the diagonal classes of this pass's layer and the energy classes (once per CTA)
     const bool diag = P.diag_layer >= 0;
     int ncl = 0, cl_first = 0;
     if (diag) {
@@ -102,7 +122,6 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassArgs A) {
     if (tid < nec) s_cls[ncl + tid] = A.classes[A.energy_class_off + tid];
     __syncthreads();
     {
-        // distance words and phase-table entries of the staged classes
         int woff = 0, toff = 0;
         for (int c = 0; c < ncl + nec; ++c) {
             const DenseClassDev& C = s_cls[c];
@@ -113,94 +132,106 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassArgs A) {
             toff += C.kind == 0 ? C.nterms + 1 : 0;
         }
     }
+    // rotation parameters of every sub-pass (the same for all tiles)
+    int kd_all[4][4];
+    float c_all[4][4], s_all[4][4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            kd_all[g][k] = -1;
+            c_all[g][k] = 1.f;
+            s_all[g][k] = 0.f;
+            if (g < P.ngroups && ((P.group_mask[g] >> k) & 1)) {
+                const int gate = P.gate[P.group_s[g] + k];
+                kd_all[g][k] = A.gates[gate].kind;
+                const float2 v = A.GT[gate];
+                c_all[g][k] = v.x;
+                s_all[g][k] = v.y;
+            }
+        }
+    }
     __syncthreads();
 
     float eacc = 0.f;
-    for (int g = 0; g < P.ngroups; ++g) {
-        const int s = P.group_s[g];
-        const unsigned m = P.group_mask[g];
-        int kd[4];
-        float c[4], sn[4];
+    int i = 0;
+    for (uint32_t t_id = blockIdx.x; t_id < ntiles; t_id += gridDim.x, ++i) {
+        const int b = i & 1;
+        float2* tile = bufs + b * padded_amps(kDenseTileBits);
+        wait_tiles();        // this thread's copies of tile t_id have landed
+        __syncthreads();     // ... and everyone else's
+        const uint32_t next = t_id + gridDim.x;
+        if (next < ntiles) issue_tile(P, next, A.state, bufs + (b ^ 1) * padded_amps(kDenseTileBits), tid);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            kd[k] = -1;
-            c[k] = 1.f;
-            sn[k] = 0.f;
-            if ((m >> k) & 1) {
-                const int gate = P.gate[s + k];
-                kd[k] = A.gates[gate].kind;
-                const float2 v = A.GT[gate];
-                c[k] = v.x;
-                sn[k] = v.y;
+        for (int g = 0; g < 4; ++g) {
+            if (g >= P.ngroups) break;
+            const int s = P.group_s[g];
+            const int lowmask = (1 << s) - 1;
+            const int stride = pass_stride(s);
+            const int base = (tid & lowmask) | ((tid >> s) << (s + 4));
+            float2* p = tile + pad16(base);
+            float2 v[16];
+            load16(v, p, stride);
+            if (kd_all[g][0] >= 0) apply_rot<0>(v, kd_all[g][0], c_all[g][0], s_all[g][0]);
+            if (kd_all[g][1] >= 0) apply_rot<1>(v, kd_all[g][1], c_all[g][1], s_all[g][1]);
+            if (kd_all[g][2] >= 0) apply_rot<2>(v, kd_all[g][2], c_all[g][2], s_all[g][2]);
+            if (kd_all[g][3] >= 0) apply_rot<3>(v, kd_all[g][3], c_all[g][3], s_all[g][3]);
+            if (g < P.ngroups - 1) {
+                store16(v, p, stride);
+                __syncthreads();
+                continue;
             }
-        }
-        const int lowmask = (1 << s) - 1;
-        const int stride = pass_stride(s);
-        const int base = (tid & lowmask) | ((tid >> s) << (s + 4));
-        float2* p = tile + pad16(base);
-        float2 v[16];
-        load16(v, p, stride);
-        if (kd[0] >= 0) apply_rot<0>(v, kd[0], c[0], sn[0]);
-        if (kd[1] >= 0) apply_rot<1>(v, kd[1], c[1], sn[1]);
-        if (kd[2] >= 0) apply_rot<2>(v, kd[2], c[2], sn[2]);
-        if (kd[3] >= 0) apply_rot<3>(v, kd[3], c[3], sn[3]);
-        if (g == P.ngroups - 1 && (diag || P.measure)) {
-#pragma unroll 4
+            // last register pass: diagonal, energy, and the write-back to HBM
+#pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const uint32_t x = tile_x(P, t_id, (uint32_t)(base | (j << s)));
-                int woff = 0, toff = 0;
-                float2 ph = make_float2(1.f, 0.f);
-                for (int ci = 0; ci < ncl; ++ci) {
-                    const DenseClassDev& C = s_cls[ci];
-                    const int cnt = class_count(C, s_dist + woff, x);
-                    if (C.kind == 0) ph = cmul(ph, s_tab[toff + cnt]);
-                    else if (cnt & 1) { ph.x = -ph.x; ph.y = -ph.y; }
-                    woff += 2 * C.ndist;
-                    toff += C.kind == 0 ? C.nterms + 1 : 0;
-                }
-                if (diag) v[j] = cmul(v[j], ph);
-                if (P.measure) {
-                    float ez = 0.f;
-                    for (int ci = ncl; ci < ncl + nec; ++ci) {
+                if (diag || P.measure) {
+                    int woff = 0, toff = 0;
+                    float2 ph = make_float2(1.f, 0.f);
+                    for (int ci = 0; ci < ncl; ++ci) {
                         const DenseClassDev& C = s_cls[ci];
                         const int cnt = class_count(C, s_dist + woff, x);
-                        ez += (float)C.coeff * (float)(C.nterms - 2 * cnt);
+                        if (C.kind == 0) ph = cmul(ph, s_tab[toff + cnt]);
+                        else if (cnt & 1) { ph.x = -ph.x; ph.y = -ph.y; }
                         woff += 2 * C.ndist;
+                        toff += C.kind == 0 ? C.nterms + 1 : 0;
                     }
-                    for (int k = 0; k < A.n_zterms; ++k) {
-                        const DenseZTermDev Z = A.zterms[k];
-                        ez += (__popc(x & Z.mask) & 1) ? -(float)Z.coeff : (float)Z.coeff;
+                    if (diag) v[j] = cmul(v[j], ph);
+                    if (P.measure) {
+                        float ez = 0.f;
+                        for (int ci = ncl; ci < ncl + nec; ++ci) {
+                            const DenseClassDev& C = s_cls[ci];
+                            const int cnt = class_count(C, s_dist + woff, x);
+                            ez += (float)C.coeff * (float)(C.nterms - 2 * cnt);
+                            woff += 2 * C.ndist;
+                        }
+                        for (int k = 0; k < A.n_zterms; ++k) {
+                            const DenseZTermDev Z = A.zterms[k];
+                            ez += (__popc(x & Z.mask) & 1) ? -(float)Z.coeff : (float)Z.coeff;
+                        }
+                        eacc += (v[j].x * v[j].x + v[j].y * v[j].y) * ez;
                     }
-                    eacc += (v[j].x * v[j].x + v[j].y * v[j].y) * ez;
                 }
+                if (P.store) A.state[x] = v[j];
             }
         }
-        store16(v, p, stride);
-        __syncthreads();
-    }
-    if (P.store) {
-        float4* dst = reinterpret_cast<float4*>(A.state);
-#pragma unroll
-        for (int k = 0; k < kTile / 2 / kThreads; ++k) {
-            const uint32_t i = 2u * (uint32_t)(tid + kThreads * k);
-            dst[tile_x(P, t_id, i) >> 1] = *reinterpret_cast<const float4*>(tile + pad16((int)i));
-        }
+        __syncthreads();   // the buffer is free for the copy issued in the next iteration
     }
     if (P.measure) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, off);
-        if ((tid & 31) == 0) s_red[tid >> 5] = eacc;
+        if (lane == 0) s_red[warp] = eacc;
         __syncthreads();
         if (tid == 0) {
             float e = 0.f;
             for (int w = 0; w < kThreads / 32; ++w) e += s_red[w];
-            A.partial[t_id] = (double)e;
+            A.partial[blockIdx.x] = (double)e;
         }
     }
 }
 
 size_t dense_pass_smem() {
-    return (size_t)padded_amps(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
+    return 2 * (size_t)padded_amps(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
            kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * sizeof(DenseClassDev) + 16 * sizeof(float);
 }
 
@@ -395,15 +426,17 @@ int launch_dense(DenseLaunch& L, void* stream) {
             A.state = psi;
             A.n_eff = L.n_eff;
             A.partial = L.partial;
+            A.err = L.err;
+            const int grid = ntiles < L.sm_count ? ntiles : L.sm_count;
             bool measured = false;
             for (int p = 0; p < L.n_passes; ++p) {
                 A.pass = L.host_passes[p];
-                dense_pass_kernel<<<ntiles, kThreads, smem, st>>>(A);
+                dense_pass_kernel<<<grid, kThreads, smem, st>>>(A);
                 ++launches;
                 if (A.pass.measure) measured = true;
             }
             if (measured) {
-                reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, ntiles, 1.0, eout, 1);
+                reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, grid, 1.0, eout, 1);
                 ++launches;
             }
             for (int t = 0; t < L.n_xterms; ++t) {

@@ -67,9 +67,9 @@ constexpr int kMaxPassSlots = 4 + 2 * 20;  // gradient values per adjoint pass: 
 constexpr int kDenseTileBits = 13;
 constexpr int kDenseStridedBits = 9;
 constexpr int kDenseMaxQubits = 31;
-constexpr int kDenseMaxLayerClasses = 64;  // per layer (+ energy classes)
+constexpr int kDenseMaxLayerClasses = 48;  // per layer (+ energy classes)
 constexpr int kDenseMaxDistWords = 512;
-constexpr int kDenseMaxTab = 1024;
+constexpr int kDenseMaxTab = 768;
 
 struct DensePassDev {
     int32_t strided;          // 0: low tile, 1: strided tile
@@ -254,8 +254,9 @@ struct DenseLaunch {
     void* gate_table = nullptr;           // [B][n_gates] float2
     void* phase_tab = nullptr;            // [B][tab_entries] float2
     void* state = nullptr;                // 2^n_eff float2
-    double* partial = nullptr;            // per-tile / per-block partial sums
+    double* partial = nullptr;            // per-CTA / per-block partial sums
     double* xpart = nullptr;              // [n_xterms] per set
+    int32_t* err = nullptr;               // kernel error word
     // outputs
     double* energy = nullptr;             // [B]
     bool per_gate = false;                // plain per-gate sweeps (baseline)
