@@ -117,17 +117,21 @@ def tlq_destroy(ctx):
     return _check(lib().tlq_destroy(ctx))
 
 
+GATE_DTYPE = np.dtype([("kind", "<i4"), ("q0", "<i4"), ("q1", "<i4"), ("param", "<i4"), ("angle", "<f8")])
+
+
 def gate_array(gates):
-    arr = (tlq_gate * max(1, len(gates)))()
-    for i, (k, q0, q1, p, a) in enumerate(gates):
-        arr[i] = tlq_gate(int(k), int(q0), int(q1), int(p), float(a))
+    """Gate tuples -> a contiguous array laid out as tlq_gate (kept alive by the caller)."""
+    arr = np.array([tuple(g) for g in gates] if len(gates) else [(0, 0, -1, -1, 0.0)], dtype=GATE_DTYPE)
+    assert arr.itemsize == ctypes.sizeof(tlq_gate)
     return arr
 
 
 def tlq_circuit_create(ctx, n, gates, n_params):
     arr = gate_array(gates)
     h = ctypes.c_void_p()
-    _check(lib().tlq_circuit_create(ctx, n, arr, len(gates), n_params, ctypes.byref(h)), ctx)
+    _check(lib().tlq_circuit_create(ctx, n, arr.ctypes.data_as(ctypes.POINTER(tlq_gate)), len(gates), n_params,
+                                    ctypes.byref(h)), ctx)
     return h
 
 

@@ -30,7 +30,7 @@ PlanEntry::~PlanEntry() {
     cudaFree(d_term_coeff);
     cudaFree(d_pmap_off);
     cudaFree(d_pmap_idx);
-    cudaFree(d_pmap_coeff);
+    cudaFree(d_pmap_term);
     cudaFree(d_gates);
     cudaFree(d_dlayers);
     cudaFree(d_dclasses);
@@ -79,7 +79,7 @@ tlq_status get_plan(Context* ctx, Circuit* c, Ham* h, std::shared_ptr<PlanEntry>
             TLQ_TRY(upload(plan->prog, &pe->d_prog, &bytes));
             TLQ_TRY(upload(plan->pmap_off, &pe->d_pmap_off, &bytes));
             TLQ_TRY(upload(plan->pmap_idx, &pe->d_pmap_idx, &bytes));
-            TLQ_TRY(upload(plan->pmap_coeff, &pe->d_pmap_coeff, &bytes));
+            TLQ_TRY(upload(plan->pmap_term, &pe->d_pmap_term, &bytes));
         }
         if (plan->dense) {
             const DensePlan& D = *plan->dense;
@@ -286,7 +286,7 @@ tlq_status run_device(Context* ctx, Circuit* c, Ham* h, const double* theta_dev,
     L.term_coeff = pe->d_term_coeff;
     L.pmap_off = pe->d_pmap_off;
     L.pmap_idx = pe->d_pmap_idx;
-    L.pmap_coeff = pe->d_pmap_coeff;
+    L.pmap_term = pe->d_pmap_term;
     L.gates = pe->d_gates;
     L.n_gates = (int32_t)c->gates.size();
     L.n_params = c->n_params;

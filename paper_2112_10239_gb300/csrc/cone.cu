@@ -133,6 +133,7 @@ struct ConeArgs {
     int32_t* err;
     void* gscratch;
     size_t gscratch_slot;
+    const SetRec* sets;     // per-set records (serving batches), or null: one plan, strided sets
 };
 
 template <typename T2>
@@ -449,7 +450,8 @@ __device__ double measure(const TeamMem<T2>& M, const ConeDev& cd, const Team& t
 template <typename real, bool GRAD, bool GLOBAL>
 __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm, unsigned char* tb, int W) {
     using T2 = typename R2<real>::T;
-    const ConeDev cd = A.cones[cone_idx];
+    const SetRec* R = A.sets ? A.sets + b : nullptr;
+    const ConeDev cd = R ? R->cones[cone_idx] : A.cones[cone_idx];
     const TeamLayout TL = team_layout(W, tm.tt, (int)sizeof(real), GRAD, !GLOBAL);
     TeamMem<T2> M;
     if (GLOBAL) {
@@ -467,7 +469,7 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
     M.tab2 = TL.tab2;
     M.tab_entries = TL.tab_entries;
     M.W = W;
-    const T2* GT = reinterpret_cast<const T2*>(A.gate_table) + (size_t)b * A.n_gates;
+    const T2* GT = reinterpret_cast<const T2*>(A.gate_table) + (R ? (size_t)R->gt_off : (size_t)b * A.n_gates);
     real* red = reinterpret_cast<real*>(M.red);
     const int nw = nwarps_of(tm.tt);
     // |0...0>
@@ -477,7 +479,7 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
         z.y = 0;
         M.psi[x] = z;   // pad16(0) == 0
     }
-    const int32_t* prog = A.prog + cd.prog_off;
+    const int32_t* prog = (R ? R->prog : A.prog) + cd.prog_off;
     const int nl = prog[0];
     const int32_t* lofs = prog + 1;
     const int32_t* body = prog + 1 + nl;
@@ -507,9 +509,9 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
         }
     }
     const double e = measure<real, T2, GRAD>(M, cd, tm, red);
-    if (tm.tid == 0) A.e_part[(size_t)b * A.n_terms + cd.term] = e;
+    if (tm.tid == 0) A.e_part[(R ? (size_t)R->e_off : (size_t)b * A.n_terms) + cd.term] = e;
     if (!GRAD) return;
-    double* gdst = A.g_part + (size_t)b * A.n_slots + cd.slot_off;
+    double* gdst = A.g_part + (R ? (size_t)R->g_off : (size_t)b * A.n_slots) + cd.slot_off;
     int rpar = 0;
     for (int li = nl - 1; li >= 0; --li) {
         const int32_t* lp = body + lofs[li];
@@ -615,13 +617,13 @@ __global__ void energy_reduce_kernel(const double* e_part, const double* coeff, 
     energy[b] = acc.value();
 }
 
-__global__ void grad_reduce_kernel(const double* g_part, const int32_t* off, const int32_t* idx, const double* coeff,
-                                   int P, int S, int B, double* grad) {
+__global__ void grad_reduce_kernel(const double* g_part, const int32_t* off, const int32_t* idx, const int32_t* term,
+                                   const double* coeff, int P, int S, int B, double* grad) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)B * P) return;
     const int b = (int)(i / P), p = (int)(i % P);
     Neumaier acc;
-    for (int k = off[p]; k < off[p + 1]; ++k) acc.add(coeff[k] * g_part[(size_t)b * S + idx[k]]);
+    for (int k = off[p]; k < off[p + 1]; ++k) acc.add(coeff[term[k]] * g_part[(size_t)b * S + idx[k]]);
     grad[i] = acc.value();
 }
 
@@ -651,6 +653,7 @@ static int launch_cone_t(const ConeLaunch& L, cudaStream_t st, int begin, int en
     A.err = L.err;
     A.gscratch = L.gscratch;
     A.gscratch_slot = L.gscratch_slot;
+    A.sets = nullptr;
     const int n = end - begin;
     if (grid > n) grid = n;
     kern<<<grid, kCtaThreads, smem, st>>>(A);
@@ -712,10 +715,110 @@ int launch_cone(ConeLaunch& L, void* stream) {
     if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     if (grad) {
         const long long n = (long long)L.B * L.n_params;
-        grad_reduce_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(L.g_part, L.pmap_off, L.pmap_idx, L.pmap_coeff,
+        grad_reduce_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(L.g_part, L.pmap_off, L.pmap_idx, L.pmap_term, L.term_coeff,
                                                                    L.n_params, L.n_slots, L.B, L.grad);
         if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     }
+    return 0;
+}
+
+// ---- serving batches: per-set records --------------------------------------------------------
+
+template <typename real>
+__global__ void batch_gate_table_kernel(const SetRec* sets, typename R2<real>::T* out) {
+    const SetRec& R = sets[blockIdx.y];
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= R.n_gates) return;
+    const tlq_gate G = R.gates[g];
+    const double a = G.param >= 0 ? R.theta[G.param] : G.angle;
+    double s, c;
+    sincos(0.5 * a, &s, &c);
+    typename R2<real>::T v;
+    v.x = (real)c;
+    v.y = (real)s;
+    out[R.gt_off + g] = v;
+}
+
+__global__ void batch_energy_kernel(const SetRec* sets, int n_sets, const double* e_part) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_sets) return;
+    const SetRec& R = sets[b];
+    Neumaier acc;
+    for (int t = 0; t < R.n_terms; ++t) acc.add(R.term_coeff[t] * e_part[R.e_off + t]);
+    *R.energy = acc.value();
+}
+
+__global__ void batch_grad_kernel(const SetRec* sets, const double* g_part) {
+    const SetRec& R = sets[blockIdx.y];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!R.grad || p >= R.n_params) return;
+    Neumaier acc;
+    for (int k = R.pmap_off[p]; k < R.pmap_off[p + 1]; ++k)
+        acc.add(R.term_coeff[R.pmap_term[k]] * g_part[R.g_off + R.pmap_idx[k]]);
+    R.grad[p] = acc.value();
+}
+
+template <typename real, bool GRAD, bool GLOBAL>
+static int launch_batch_t(const BatchLaunch& L, cudaStream_t st, int begin, int end, int smem, int grid,
+                          int32_t* counter) {
+    if (end <= begin) return 0;
+    auto kern = cone_kernel<real, GRAD, GLOBAL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return (int)e;
+    ConeArgs A{};
+    A.items = L.items;
+    A.chunks = L.chunks;
+    A.chunk_begin = begin;
+    A.chunk_end = end;
+    A.gate_table = L.gate_table;
+    A.e_part = L.e_part;
+    A.g_part = L.g_part;
+    A.counter = counter;
+    A.err = L.err;
+    A.gscratch = L.gscratch;
+    A.gscratch_slot = L.gscratch_slot;
+    A.sets = L.sets;
+    const int n = end - begin;
+    if (grid > n) grid = n;
+    if (grid < 1) grid = 1;
+    kern<<<grid, kCtaThreads, smem, st>>>(A);
+    return (int)cudaGetLastError();
+}
+
+template <typename real>
+static int launch_batch_all(BatchLaunch& L, cudaStream_t st) {
+    int rc;
+    const int g0 = cone_smem_grid(sizeof(real) == 8, false, L.smem_bytes[0] > 0 ? L.smem_bytes[0] : 1024, L.sm_count);
+    const int g1 = cone_smem_grid(sizeof(real) == 8, true, L.smem_bytes[1] > 0 ? L.smem_bytes[1] : 1024, L.sm_count);
+    if ((rc = launch_batch_t<real, false, false>(L, st, L.range[0], L.range[1], L.smem_bytes[0], g0, L.counters + 0))) return rc;
+    if ((rc = launch_batch_t<real, false, true>(L, st, L.range[1], L.range[2], L.gsmem_bytes[0], L.g_grid, L.counters + 1))) return rc;
+    if ((rc = launch_batch_t<real, true, false>(L, st, L.range[2], L.range[3], L.smem_bytes[1], g1, L.counters + 2))) return rc;
+    if ((rc = launch_batch_t<real, true, true>(L, st, L.range[3], L.range[4], L.gsmem_bytes[1], L.g_grid, L.counters + 3))) return rc;
+    for (int k = 0; k < 4; ++k) L.launches += L.range[k + 1] > L.range[k];
+    return 0;
+}
+
+int launch_cone_batch(BatchLaunch& L, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    L.launches = 0;
+    if (L.n_sets <= 0) return 0;
+    const dim3 gk((L.max_gates + 255) / 256 > 0 ? (L.max_gates + 255) / 256 : 1, L.n_sets);
+    if (L.fp64) batch_gate_table_kernel<double><<<gk, 256, 0, st>>>(L.sets, (double2*)L.gate_table);
+    else batch_gate_table_kernel<float><<<gk, 256, 0, st>>>(L.sets, (float2*)L.gate_table);
+    if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+    if ((e = cudaMemsetAsync(L.counters, 0, 4 * sizeof(int32_t), st)) != cudaSuccess) return (int)e;
+    const int rc = L.fp64 ? launch_batch_all<double>(L, st) : launch_batch_all<float>(L, st);
+    if (rc) return rc;
+    batch_energy_kernel<<<(L.n_sets + 127) / 128, 128, 0, st>>>(L.sets, L.n_sets, L.e_part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+    if (L.max_params > 0 && L.range[4] > L.range[2]) {
+        const dim3 gg((L.max_params + 255) / 256, L.n_sets);
+        batch_grad_kernel<<<gg, 256, 0, st>>>(L.sets, L.g_part);
+        if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+        ++L.launches;
+    }
+    L.launches += 2;
     return 0;
 }
 

@@ -165,10 +165,10 @@ struct Plan {
     std::vector<int32_t> cone_ndiag;      // layers with diagonal gates in each cone
     std::vector<int32_t> cone_npdiag;     // parametrised diagonal gates in each cone
     int32_t n_slots = 0;                  // gradient slots per parameter set
-    // slot -> parameter map, CSR by parameter: g[p] = sum_i coeff[i] * part[idx[i]]
+    // slot -> parameter map, CSR by parameter: g[p] = sum_i term_coeff[term[i]] * part[idx[i]]
     std::vector<int32_t> pmap_off;        // n_params + 1
     std::vector<int32_t> pmap_idx;
-    std::vector<double> pmap_coeff;
+    std::vector<int32_t> pmap_term;       // term owning each entry (its coefficient scales the slot)
     std::vector<double> term_coeff;       // per term
     int max_w = 0;
     std::string why_dense;                // reason the dense path was chosen
@@ -193,7 +193,7 @@ struct ConeLaunch {
     const double* term_coeff = nullptr;
     const int32_t* pmap_off = nullptr;
     const int32_t* pmap_idx = nullptr;
-    const double* pmap_coeff = nullptr;
+    const int32_t* pmap_term = nullptr;
     const tlq_gate* gates = nullptr;      // circuit gate list on the device
     int32_t n_gates = 0;
     int32_t n_params = 0;
@@ -229,6 +229,46 @@ struct ConeLaunch {
 };
 
 int launch_cone(ConeLaunch& L, void* stream);
+
+// One parameter set of a serving batch: where its plan, angles, partial sums and outputs
+// live. Sets of different circuits share one launch through these records.
+struct SetRec {
+    const ConeDev* cones;
+    const int32_t* prog;
+    const tlq_gate* gates;
+    const double* theta;        // this set's angles [n_params]
+    const double* term_coeff;
+    const int32_t* pmap_off;
+    const int32_t* pmap_idx;
+    const int32_t* pmap_term;
+    double* energy;             // this set's energy (device)
+    double* grad;               // this set's gradient [n_params] (device) or null
+    int64_t gt_off, e_off, g_off;   // offsets into the batch's gate table, term energies, slots
+    int32_t n_gates, n_params, n_terms, n_slots;
+};
+
+struct BatchLaunch {
+    const SetRec* sets = nullptr;     // device [n_sets]
+    int32_t n_sets = 0, max_gates = 0, max_params = 0;
+    const int32_t* items = nullptr;   // (cone, set) pairs
+    const ChunkDev* chunks = nullptr;
+    // chunk ranges: forward-only smem, forward-only global, gradient smem, gradient global
+    int32_t range[5] = {0, 0, 0, 0, 0};
+    int32_t smem_bytes[2] = {0, 0};   // shared tier: forward, gradient
+    int32_t gsmem_bytes[2] = {0, 0};  // global tier: forward, gradient
+    void* gate_table = nullptr;
+    double* e_part = nullptr;
+    double* g_part = nullptr;
+    void* gscratch = nullptr;
+    size_t gscratch_slot = 0;
+    int32_t g_grid = 0;
+    int32_t* counters = nullptr;      // [4]
+    int32_t* err = nullptr;
+    bool fp64 = false;
+    int sm_count = 0;
+    int launches = 0;
+};
+int launch_cone_batch(BatchLaunch& L, void* stream);
 int cone_smem_grid(bool fp64, bool grad, int smem_bytes, int sm_count);
 
 struct DenseLaunch {

@@ -225,7 +225,7 @@ extern "C" tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tl
     double* d_tc = (double*)cv.take(P.term_coeff.size() * sizeof(double));
     int32_t* d_poff = (int32_t*)cv.take(P.pmap_off.size() * sizeof(int32_t));
     int32_t* d_pidx = (int32_t*)cv.take(std::max<size_t>(1, P.pmap_idx.size()) * sizeof(int32_t));
-    double* d_pco = (double*)cv.take(std::max<size_t>(1, P.pmap_coeff.size()) * sizeof(double));
+    int32_t* d_pterm = (int32_t*)cv.take(std::max<size_t>(1, P.pmap_term.size()) * sizeof(int32_t));
     int32_t* d_items = (int32_t*)cv.take(hp->items.size() * sizeof(int32_t));
     ChunkDev* d_chunks = (ChunkDev*)cv.take(hp->chunks.size() * sizeof(ChunkDev));
     void* d_gt = cv.take((size_t)B * std::max(1, G) * sizeof(float2));
@@ -249,7 +249,7 @@ extern "C" tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tl
     put(d_tc, P.term_coeff.data(), P.term_coeff.size() * sizeof(double));
     put(d_poff, P.pmap_off.data(), P.pmap_off.size() * sizeof(int32_t));
     put(d_pidx, P.pmap_idx.data(), P.pmap_idx.size() * sizeof(int32_t));
-    put(d_pco, P.pmap_coeff.data(), P.pmap_coeff.size() * sizeof(double));
+    put(d_pterm, P.pmap_term.data(), P.pmap_term.size() * sizeof(int32_t));
     put(d_items, hp->items.data(), hp->items.size() * sizeof(int32_t));
     put(d_chunks, hp->chunks.data(), hp->chunks.size() * sizeof(ChunkDev));
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 64, strm);   // work counters and error word start at 0
@@ -261,7 +261,7 @@ extern "C" tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tl
     L.term_coeff = d_tc;
     L.pmap_off = d_poff;
     L.pmap_idx = d_pidx;
-    L.pmap_coeff = d_pco;
+    L.pmap_term = d_pterm;
     L.gates = d_gates;
     L.n_gates = G;
     L.n_params = Ci->n_params;

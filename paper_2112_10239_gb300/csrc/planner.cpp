@@ -66,6 +66,8 @@ struct LayerIndex {
     // per layer: rotation gate on qubit q (or -1); diagonal gates touching q
     std::vector<std::vector<int>> rot_at;                 // [L][n]
     std::vector<std::vector<std::vector<int>>> diag_at;   // [L][n] -> gates
+    std::vector<int> layer_of;                            // gate -> layer (-1: dropped)
+    std::vector<char> is_rot;                             // gate is a layer rotation
 };
 
 LayerIndex index_layers(const Circuit& c) {
@@ -73,7 +75,11 @@ LayerIndex index_layers(const Circuit& c) {
     const int L = (int)c.layers.size();
     ix.rot_at.assign(L, std::vector<int>(c.n, -1));
     ix.diag_at.assign(L, std::vector<std::vector<int>>(c.n));
+    ix.layer_of.assign(c.gates.size(), -1);
+    ix.is_rot.assign(c.gates.size(), 0);
     for (int l = 0; l < L; ++l) {
+        for (int g : c.layers[l].rot) { ix.layer_of[g] = l; ix.is_rot[g] = 1; }
+        for (int g : c.layers[l].diag) ix.layer_of[g] = l;
         for (int g : c.layers[l].rot) ix.rot_at[l][c.gates[g].q0] = g;
         for (int g : c.layers[l].diag) {
             const tlq_gate& G = c.gates[g];
@@ -112,7 +118,7 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
     P->cone_nrot.assign(T, 0);
     P->cone_ndiag.assign(T, 0);
     P->cone_npdiag.assign(T, 0);
-    std::vector<std::vector<std::pair<int32_t, double>>> pentries(c.n_params);
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> pentries(c.n_params);   // (slot, term)
     int32_t slot_total = 0;
 
     for (int t = 0; t < T; ++t) {
@@ -170,33 +176,40 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
         cd.prog_off = (int32_t)P->prog.size();
         cd.slot_off = slot_total;
         int32_t nslot = 0;
-        auto kept_has = [&](int g) { return std::binary_search(kept.begin(), kept.end(), g); };
         std::vector<int32_t> body, layer_off;
         int32_t nlayers = 0;
-        for (int l = 0; l < L; ++l) {
+        // gates of a layer have consecutive indices, so the sorted cone gates come in layer order
+        size_t kp = 0;
+        while (kp < kept.size()) {
+            const int l = ix.layer_of[kept[kp]];
             std::vector<int> rot, diag;
-            for (int g : c.layers[l].rot) if (kept_has(g)) rot.push_back(g);
-            for (int g : c.layers[l].diag) if (kept_has(g)) diag.push_back(g);
-            if (rot.empty() && diag.empty()) continue;
+            while (kp < kept.size() && ix.layer_of[kept[kp]] == l) {
+                (ix.is_rot[kept[kp]] ? rot : diag).push_back(kept[kp]);
+                ++kp;
+            }
             // sub-layers: position-disjoint groups of diagonal gates
             std::vector<std::vector<int>> parts(1);
-            std::vector<std::vector<char>> zused(1, std::vector<char>(W, 0)), pused(1, std::vector<char>(W, 0));
+            std::vector<uint32_t> zused(1, 0u), pused(1, 0u);   // window-bit masks (W <= 20)
             for (int g : diag) {
                 const tlq_gate& G = c.gates[g];
                 const bool two = is_two(G.kind);
                 const int j = std::min(G.q0, two ? G.q1 : G.q0) - lo;
+                const uint32_t bit = 1u << j;
                 size_t p = 0;
-                while (p < parts.size() && (two ? pused[p][j] : zused[p][j])) ++p;
+                while (p < parts.size() && ((two ? pused[p] : zused[p]) & bit)) ++p;
                 if (p == parts.size()) {
                     parts.emplace_back();
-                    zused.emplace_back(W, 0);
-                    pused.emplace_back(W, 0);
+                    zused.push_back(0u);
+                    pused.push_back(0u);
                 }
-                (two ? pused[p][j] : zused[p][j]) = 1;
+                (two ? pused[p] : zused[p]) |= bit;
                 parts[p].push_back(g);
             }
             for (size_t part = 0; part < parts.size(); ++part) {
-                std::vector<int32_t> rec((size_t)W * kRecWords, -1);
+                layer_off.push_back((int32_t)body.size());
+                const size_t hdr = body.size();
+                body.resize(hdr + kLayerHeader + (size_t)W * kRecWords, -1);
+                int32_t* rec = body.data() + hdr + kLayerHeader;
                 for (int j = 0; j < W; ++j) {
                     rec[(size_t)j * kRecWords + 1] = 0;
                     rec[(size_t)j * kRecWords + 5] = 0;
@@ -207,7 +220,7 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                         const tlq_gate& G = c.gates[g];
                         const int j = G.q0 - lo;
                         const int32_t slot = G.param >= 0 ? nslot++ : -1;
-                        if (slot >= 0) pentries[G.param].push_back({slot_total + slot, term.coeff});
+                        if (slot >= 0) pentries[G.param].push_back({slot_total + slot, t});
                         rec[(size_t)j * kRecWords + 0] = g;
                         rec[(size_t)j * kRecWords + 1] = G.kind | ((slot + 1) << 8);
                         live |= 1u << j;
@@ -215,7 +228,7 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                     }
                 }
                 // diagonal gates: slots in (qubit, RZ before pair) order
-                std::vector<int> dd = parts[part];
+                std::vector<int>& dd = parts[part];
                 std::sort(dd.begin(), dd.end(), [&](int a, int b) {
                     const tlq_gate &A = c.gates[a], &Bg = c.gates[b];
                     const int ja = std::min(A.q0, is_two(A.kind) ? A.q1 : A.q0);
@@ -229,7 +242,7 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                     const int j = std::min(G.q0, two ? G.q1 : G.q0) - lo;
                     const int32_t slot = (G.param >= 0 && G.kind != TLQ_CZ) ? nslot++ : -1;
                     if (slot >= 0) {
-                        pentries[G.param].push_back({slot_total + slot, term.coeff});
+                        pentries[G.param].push_back({slot_total + slot, t});
                         P->cone_npdiag[t] += 1;
                     }
                     if (two) {
@@ -241,12 +254,10 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                     }
                 }
                 if (!dd.empty()) P->cone_ndiag[t] += 1;
-                layer_off.push_back((int32_t)body.size());
-                body.push_back(dd.empty() ? 0 : 1);
-                body.push_back((int32_t)live);
-                body.push_back(0);
-                body.push_back(0);
-                body.insert(body.end(), rec.begin(), rec.end());
+                body[hdr + 0] = dd.empty() ? 0 : 1;
+                body[hdr + 1] = (int32_t)live;
+                body[hdr + 2] = 0;
+                body[hdr + 3] = 0;
                 ++nlayers;
             }
         }
@@ -273,9 +284,9 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
     P->pmap_off.assign(c.n_params + 1, 0);
     for (int p = 0; p < c.n_params; ++p) P->pmap_off[p + 1] = P->pmap_off[p] + (int32_t)pentries[p].size();
     P->pmap_idx.reserve(P->pmap_off.back());
-    P->pmap_coeff.reserve(P->pmap_off.back());
+    P->pmap_term.reserve(P->pmap_off.back());
     for (int p = 0; p < c.n_params; ++p)
-        for (auto& e : pentries[p]) { P->pmap_idx.push_back(e.first); P->pmap_coeff.push_back(e.second); }
+        for (auto& e : pentries[p]) { P->pmap_idx.push_back(e.first); P->pmap_term.push_back(e.second); }
     (void)err;
     return P;
 }

@@ -24,7 +24,7 @@ struct PlanEntry {
     double* d_term_coeff = nullptr;
     int32_t* d_pmap_off = nullptr;
     int32_t* d_pmap_idx = nullptr;
-    double* d_pmap_coeff = nullptr;
+    int32_t* d_pmap_term = nullptr;
     tlq_gate* d_gates = nullptr;
     // dense path device buffers
     DenseLayerDev* d_dlayers = nullptr;
@@ -57,7 +57,7 @@ struct Workspace {
     }
 };
 
-struct Request;
+
 struct Scheduler;
 
 struct Context {
