@@ -202,6 +202,170 @@ def cpu_baseline(prob, budget_s=12.0):
                       f"+ adjoint), {dt:.1f} s wall"}
 
 
+def serving_replay(B, device, count, rate, seed=4):
+    """Replay a Poisson request stream (n ~ U[16,400], L ~ U[2,8], h ~ U[0.5,1.5], 30% with
+    gradient) open-loop through tlq_submit/tlq_poll, and the same arrivals served one at a
+    time through the synchronous calls (the plain path). Circuits are created once per
+    (n, L) shape and kept resident; each request has its own Hamiltonian and angles."""
+    import threading
+    from paper_2112_10239_gb300 import workloads as W
+    reqs = W.serving_stream(count, rate, seed)
+
+    def prepare(ctx):
+        circ, hams = {}, []
+        for r in reqs:
+            p = r.problem
+            key = (p.n, p.meta["L"])
+            if key not in circ:
+                circ[key] = ctx.circuit(p.n, p.gates, p.n_params)
+            hams.append(ctx.hamiltonian(p.n, p.terms))
+        return circ, hams
+
+    # warm-up in a throwaway context (module loading, kernel attributes)
+    with B.Context(device=device) as wctx:
+        c0, h0 = wctx.problem(reqs[0].problem)
+        B.tlq_expectation(wctx.h, c0.h, h0.h, reqs[0].problem.theta)
+
+    # batched serving
+    ctx = B.Context(device=device)
+    circ, hams = prepare(ctx)
+    outs = [(np.zeros(1), np.zeros((1, r.problem.n_params)) if r.want_grad else None) for r in reqs]
+    tickets = [None] * count
+    ready = threading.Semaphore(0)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            due = t0 + r.t_arrival
+            while True:
+                d = due - time.perf_counter()
+                if d <= 0:
+                    break
+                time.sleep(d if d > 2e-3 else 0)
+            p = r.problem
+            tickets[i] = B.tlq_submit(ctx.h, circ[(p.n, p.meta["L"])].h, hams[i].h, p.theta, outs[i][0], outs[i][1])
+            ready.release()
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    for i in range(count):
+        ready.acquire()
+        B.tlq_poll(ctx.h, tickets[i], -1)
+    t_end = time.perf_counter()
+    th.join()
+    n_done, p50, p99, mean_batch = B.tlq_serving_stats(ctx.h)
+    batched = {"throughput_rps": count / (t_end - t0), "p50_ms": 1e3 * p50, "p99_ms": 1e3 * p99,
+               "mean_batch": mean_batch, "completed": n_done}
+    ctx.close()
+
+    # plain path: one request at a time through the synchronous calls, same arrivals
+    ctx = B.Context(device=device)
+    circ, hams = prepare(ctx)
+    lat = []
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        due = t0 + r.t_arrival
+        while time.perf_counter() < due:
+            pass
+        p = r.problem
+        c = circ[(p.n, p.meta["L"])]
+        if r.want_grad:
+            B.tlq_expectation_grad(ctx.h, c.h, hams[i].h, p.theta)
+        else:
+            B.tlq_expectation(ctx.h, c.h, hams[i].h, p.theta)
+        lat.append(time.perf_counter() - due)
+    t_end = time.perf_counter()
+    ctx.close()
+    lat.sort()
+    plain = {"throughput_rps": count / (t_end - t0), "p50_ms": 1e3 * lat[len(lat) // 2],
+             "p99_ms": 1e3 * lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]}
+    return {"requests": count, "rate_per_s": rate, "grad_fraction": 0.3, "n": [16, 400], "L": [2, 8],
+            "batched": batched, "one_at_a_time": plain}
+
+
+def device_steps(B, ctx, c, h, prob, grad, steps, dev, flush):
+    """Time `steps` device-pointer calls (inputs resident, L2 flushed between steps)."""
+    import torch
+    Bsz, P = prob.theta.shape
+    stream = torch.cuda.current_stream(dev)
+    theta_d = torch.tensor(prob.theta, dtype=torch.float64, device=dev)
+    E_d = torch.empty(Bsz, dtype=torch.float64, device=dev)
+    G_d = torch.empty(Bsz, P, dtype=torch.float64, device=dev) if grad else None
+
+    def step():
+        B.tlq_expectation_grad_dev(ctx.h, c.h, h.h, theta_d.data_ptr(), Bsz, B.TLQ_FP32, E_d.data_ptr(),
+                                   G_d.data_ptr() if grad else None, stream.cuda_stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    step_ms, kern_ms, launches = [], [], 0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        ms, nl = B.tlq_profile_last(ctx.h)
+        kern_ms.append(ms)
+        launches = nl
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+    return float(np.median(step_ms)), float(np.median(kern_ms)), launches
+
+
+def extra_workloads(B, dev, local, flush, peaks):
+    """The other workloads, each with its own throughput and roofline (not the headline)."""
+    import ctypes
+    from paper_2112_10239_gb300 import workloads as W
+    out = {}
+    # n=500, L=4 transverse-field Ising chain, 256 sets, energy + gradient (the paper's n=500 shape)
+    prob = W.tfim_n500_L4_B256()
+    with B.Context(device=local) as ctx:
+        c, h = ctx.problem(prob)
+        B.tlq_profile_enable(ctx.h, True)
+        ms, kms, nl = device_steps(B, ctx, c, h, prob, True, 5, dev, flush)
+        flops = algorithmic_flops(B, ctx, c, h, prob, grad=True)
+        peak = 152 * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        out["tfim_n500_L4_B256"] = {
+            "value": prob.B / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "launches": nl,
+            "roofline": {"bound": "alu", "achieved": flops / (kms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / (kms * 1e-3) / 1e12 / peak, "kernel_ms": kms}}
+        c.close()
+        h.close()
+    # n=28 QAOA on a 3-regular graph (dense statevector), fused passes vs plain per-gate sweeps
+    prob = W.qaoa_n28_p4()
+    res = {}
+    for name, fk in (("fused", 0), ("per_gate", 1)):
+        cfg = B.tlq_config(local, 0, 0, B.TLQ_FP32, fk)
+        hnd = ctypes.c_void_p()
+        B._check(B.lib().tlq_init(ctypes.byref(cfg), ctypes.byref(hnd)))
+        ctx = B.Context.__new__(B.Context)
+        ctx.h = hnd
+        c, h = ctx.problem(prob)
+        B.tlq_profile_enable(ctx.h, True)
+        ms, kms, nl = device_steps(B, ctx, c, h, prob, False, 5 if fk == 0 else 2, dev, flush)
+        res[name] = (ms, kms, nl)
+        c.close()
+        h.close()
+        ctx.close()
+    ms, kms, nl = res["fused"]
+    passes = nl - 4          # gate table, phase tables, state init and the final reduction
+    state_bytes = 8 * (1 << prob.n)
+    achieved = passes * 2 * state_bytes / (kms * 1e-3) / 1e9
+    out["qaoa_n28_p4"] = {
+        "value": 1.0 / (ms * 1e-3), "unit": "evals/s", "ms_per_eval": ms,
+        "per_gate_ms_per_eval": res["per_gate"][0], "speedup_vs_per_gate": res["per_gate"][0] / ms,
+        "passes": passes,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                     "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                     "kernel": "dense_pass_kernel x passes (read + write of the 2 GiB state each)",
+                     "kernel_ms": kms}}
+    # serving: Poisson arrivals, continuous batching vs one request at a time
+    out["serving"] = serving_replay(B, local, 2000, 2000.0)
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -296,6 +460,7 @@ def main():
                 "kernel_ms": kern_mean_ms, "algorithmic_flops": flops,
                 "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x {sm_max:.0f} MHz"}
 
+    extras = extra_workloads(B, dev, local, flush, peaks) if rank == 0 else {}
     if rank == 0:
         cpu = cpu_baseline(prob)
         sm = sorted(step_ms)
@@ -315,6 +480,7 @@ def main():
             "peak_source": peak_kind,
             "cpu_baseline": cpu,
             "clocks": clk,
+            "other_workloads": extras,
         }
         print(json.dumps(line), flush=True)
     c.close()

@@ -139,21 +139,34 @@ def tlq_circuit_destroy(c):
     return _check(lib().tlq_circuit_destroy(c))
 
 
+TERM_DTYPE = np.dtype([("coeff", "<f8"), ("nsites", "<i4"), ("pad", "<i4"), ("sites", "<u8"), ("paulis", "<u8")])
+
+
 def term_array(terms):
-    arr = (tlq_term * max(1, len(terms)))()
-    keep = []
-    for i, (c, sites, letters) in enumerate(terms):
-        s = (ctypes.c_int32 * max(1, len(sites)))(*[int(x) for x in sites])
-        l = ctypes.c_char_p(letters.encode())
-        keep.append((s, l))
-        arr[i] = tlq_term(float(c), len(sites), s, l)
-    return arr, keep
+    """Term tuples -> an array laid out as tlq_term plus the flat site/letter arrays its
+    pointers refer to (the caller keeps all three alive for the call)."""
+    T = max(1, len(terms))
+    counts = np.array([len(s) for _, s, _ in terms] or [0], dtype=np.int64)
+    flat_sites = np.array([x for _, s, _ in terms for x in s] or [0], dtype=np.int32)
+    flat_letters = np.frombuffer(("".join(l for _, _, l in terms) or "Z").encode(), dtype=np.uint8).copy()
+    off = np.zeros(T, dtype=np.int64)
+    if len(terms) > 1:
+        off[1:] = np.cumsum(counts)[:-1]
+    arr = np.zeros(T, dtype=TERM_DTYPE)
+    if len(terms):
+        arr["coeff"] = [float(c) for c, _, _ in terms]
+        arr["nsites"] = counts
+        arr["sites"] = flat_sites.ctypes.data + 4 * off
+        arr["paulis"] = flat_letters.ctypes.data + off
+    assert arr.itemsize == ctypes.sizeof(tlq_term)
+    return arr, (flat_sites, flat_letters)
 
 
 def tlq_hamiltonian_create(ctx, n, terms):
     arr, keep = term_array(terms)
     h = ctypes.c_void_p()
-    _check(lib().tlq_hamiltonian_create(ctx, n, arr, len(terms), ctypes.byref(h)), ctx)
+    _check(lib().tlq_hamiltonian_create(ctx, n, arr.ctypes.data_as(ctypes.POINTER(tlq_term)), len(terms),
+                                        ctypes.byref(h)), ctx)
     del keep
     return h
 

@@ -48,8 +48,15 @@ class Problem:
         return int(self.theta.shape[0])
 
 
+_BRICKWALL_CACHE: dict = {}
+
+
 def brickwall_gates(n: int, L: int) -> list:
-    """RY/RZ + CZ brick-wall gate list with ``p = l*2n + kind*n + q``."""
+    """RY/RZ + CZ brick-wall gate list with ``p = l*2n + kind*n + q`` (memoised; treat the
+    returned list as read-only)."""
+    key = (n, L)
+    if key in _BRICKWALL_CACHE:
+        return _BRICKWALL_CACHE[key]
     gates = []
     for l in range(L):
         for q in range(n):
@@ -60,6 +67,7 @@ def brickwall_gates(n: int, L: int) -> list:
             gates.append((CZ, q, q + 1, -1, 0.0))
         for q in range(1, n - 1, 2):
             gates.append((CZ, q, q + 1, -1, 0.0))
+    _BRICKWALL_CACHE[key] = gates
     return gates
 
 
