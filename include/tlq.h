@@ -163,19 +163,22 @@ tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tlq_ham h, co
 
 /* Serving (continuous batching): enqueue one request; returns at once with a ticket.
  * theta: host [B][n_params]; energy: host [B]; grad: host [B][n_params] when want_grad.
- * The buffers are borrowed until tlq_poll returns TLQ_OK for the ticket. Requests are
- * admitted as slots and device memory free up, packed with the other admitted requests
- * into batched launches, and overlap on the device with batches already in flight.
- * Results do not depend on what else is in the batch. Circuit and Hamiltonian must stay
- * alive until the request completes. EINVAL as for tlq_expectation; ENOMEM only if the
- * request alone can never fit the budget. */
+ * The buffers are borrowed until tlq_poll returns for the ticket; the circuit and the
+ * Hamiltonian must stay alive until then too. Planning runs on the library's planner
+ * threads (plans are cached by circuit/Hamiltonian structure). Requests are admitted as
+ * request slots and device memory free up, packed with the other admitted requests into
+ * batched launches, and overlap on the device with batches already in flight. Results do
+ * not depend on what else is in the batch. The call itself fails with EINVAL as
+ * tlq_expectation does (and ENOMEM for B above 8192); failures found while planning --
+ * EUNSUPPORTED for circuits that need the dense statevector path, ENOMEM for a request
+ * that can never fit half of the memory budget -- are returned by tlq_poll. */
 tlq_status tlq_submit(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta, int32_t B, int want_grad,
                       tlq_precision prec, double* energy, double* grad, tlq_ticket* out);
 
 /* TLQ_OK: done (outputs written, ticket retired); TLQ_EAGAIN: pending and
  * timeout_us == 0; TLQ_ETIMEOUT: still pending after timeout_us microseconds (a negative
- * timeout waits until completion); any other status: the request failed (ticket retired).
- * EINVAL for an unknown or already retired ticket. */
+ * timeout waits until completion); any other status: the request failed (ticket retired,
+ * message in tlq_last_error). EINVAL for an unknown or already retired ticket. */
 tlq_status tlq_poll(tlq_ctx ctx, tlq_ticket t, int64_t timeout_us);
 
 /* Thread-local message of the calling thread's last failure ("" if none). */

@@ -118,9 +118,12 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
     P->cone_nrot.assign(T, 0);
     P->cone_ndiag.assign(T, 0);
     P->cone_npdiag.assign(T, 0);
-    std::vector<std::vector<std::pair<int32_t, int32_t>>> pentries(c.n_params);   // (slot, term)
+    struct PEntry { int32_t param, slot, term; };
+    std::vector<PEntry> pentries;   // gradient slots in emission order
     int32_t slot_total = 0;
 
+    std::vector<std::pair<int, int>> dpart;   // (diagonal gate, sub-layer) of one layer
+    std::vector<uint32_t> zmask, pmask;
     for (int t = 0; t < T; ++t) {
         const Term& term = h.terms[t];
         std::vector<int> S(term.sites.begin(), term.sites.end());
@@ -182,84 +185,96 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
         size_t kp = 0;
         while (kp < kept.size()) {
             const int l = ix.layer_of[kept[kp]];
-            std::vector<int> rot, diag;
-            while (kp < kept.size() && ix.layer_of[kept[kp]] == l) {
-                (ix.is_rot[kept[kp]] ? rot : diag).push_back(kept[kp]);
-                ++kp;
-            }
-            // sub-layers: position-disjoint groups of diagonal gates
-            std::vector<std::vector<int>> parts(1);
-            std::vector<uint32_t> zused(1, 0u), pused(1, 0u);   // window-bit masks (W <= 20)
-            for (int g : diag) {
+            size_t kp2 = kp;
+            while (kp2 < kept.size() && ix.layer_of[kept[kp2]] == l) ++kp2;
+            // sub-layers: each diagonal gate goes to the first part where its position is free
+            int nparts = 1;
+            dpart.clear();
+            zmask.assign(1, 0u);
+            pmask.assign(1, 0u);
+            for (size_t k = kp; k < kp2; ++k) {
+                const int g = kept[k];
+                if (ix.is_rot[g]) continue;
                 const tlq_gate& G = c.gates[g];
                 const bool two = is_two(G.kind);
-                const int j = std::min(G.q0, two ? G.q1 : G.q0) - lo;
-                const uint32_t bit = 1u << j;
-                size_t p = 0;
-                while (p < parts.size() && ((two ? pused[p] : zused[p]) & bit)) ++p;
-                if (p == parts.size()) {
-                    parts.emplace_back();
-                    zused.push_back(0u);
-                    pused.push_back(0u);
+                const uint32_t bit = 1u << (std::min(G.q0, two ? G.q1 : G.q0) - lo);
+                int part = 0;
+                while (part < nparts && ((two ? pmask[part] : zmask[part]) & bit)) ++part;
+                if (part == nparts) {
+                    ++nparts;
+                    zmask.push_back(0u);
+                    pmask.push_back(0u);
                 }
-                (two ? pused[p] : zused[p]) |= bit;
-                parts[p].push_back(g);
+                (two ? pmask[part] : zmask[part]) |= bit;
+                dpart.push_back({g, part});
             }
-            for (size_t part = 0; part < parts.size(); ++part) {
+            for (int part = 0; part < nparts; ++part) {
                 layer_off.push_back((int32_t)body.size());
                 const size_t hdr = body.size();
                 body.resize(hdr + kLayerHeader + (size_t)W * kRecWords, -1);
                 int32_t* rec = body.data() + hdr + kLayerHeader;
-                for (int j = 0; j < W; ++j) {
-                    rec[(size_t)j * kRecWords + 1] = 0;
-                    rec[(size_t)j * kRecWords + 5] = 0;
+                for (int jj = 0; jj < W; ++jj) {
+                    rec[(size_t)jj * kRecWords + 1] = 0;
+                    rec[(size_t)jj * kRecWords + 5] = 0;
                 }
                 uint32_t live = 0;
                 if (part == 0) {
-                    for (int g : rot) {
-                        const tlq_gate& G = c.gates[g];
-                        const int j = G.q0 - lo;
-                        const int32_t slot = G.param >= 0 ? nslot++ : -1;
-                        if (slot >= 0) pentries[G.param].push_back({slot_total + slot, t});
-                        rec[(size_t)j * kRecWords + 0] = g;
-                        rec[(size_t)j * kRecWords + 1] = G.kind | ((slot + 1) << 8);
-                        live |= 1u << j;
-                        P->cone_nrot[t] += 1;
+                    for (size_t k = kp; k < kp2; ++k) {
+                        const int g = kept[k];
+                        if (!ix.is_rot[g]) continue;
+                        const int jj = c.gates[g].q0 - lo;
+                        rec[(size_t)jj * kRecWords + 0] = g;
+                        live |= 1u << jj;
                     }
                 }
-                // diagonal gates: slots in (qubit, RZ before pair) order
-                std::vector<int>& dd = parts[part];
-                std::sort(dd.begin(), dd.end(), [&](int a, int b) {
-                    const tlq_gate &A = c.gates[a], &Bg = c.gates[b];
-                    const int ja = std::min(A.q0, is_two(A.kind) ? A.q1 : A.q0);
-                    const int jb = std::min(Bg.q0, is_two(Bg.kind) ? Bg.q1 : Bg.q0);
-                    if (ja != jb) return ja < jb;
-                    return is_two(A.kind) < is_two(Bg.kind);
-                });
-                for (int g : dd) {
-                    const tlq_gate& G = c.gates[g];
+                bool any_diag = false;
+                for (const auto& dp : dpart) {
+                    if (dp.second != part) continue;
+                    const tlq_gate& G = c.gates[dp.first];
                     const bool two = is_two(G.kind);
-                    const int j = std::min(G.q0, two ? G.q1 : G.q0) - lo;
-                    const int32_t slot = (G.param >= 0 && G.kind != TLQ_CZ) ? nslot++ : -1;
-                    if (slot >= 0) {
-                        pentries[G.param].push_back({slot_total + slot, t});
-                        P->cone_npdiag[t] += 1;
+                    const int jj = std::min(G.q0, two ? G.q1 : G.q0) - lo;
+                    rec[(size_t)jj * kRecWords + (two ? 4 : 2)] = dp.first;
+                    any_diag = true;
+                }
+                // gradient slots: rotations by window position, then RZ / pair gates by position
+                for (int jj = 0; jj < W; ++jj) {
+                    int32_t* r = rec + (size_t)jj * kRecWords;
+                    if (r[0] < 0) continue;
+                    const tlq_gate& G = c.gates[r[0]];
+                    const int32_t slot = G.param >= 0 ? nslot++ : -1;
+                    if (slot >= 0) pentries.push_back({G.param, slot_total + slot, t});
+                    r[1] = G.kind | ((slot + 1) << 8);
+                    P->cone_nrot[t] += 1;
+                }
+                for (int jj = 0; jj < W; ++jj) {
+                    int32_t* r = rec + (size_t)jj * kRecWords;
+                    if (r[2] >= 0) {
+                        const tlq_gate& G = c.gates[r[2]];
+                        const int32_t slot = G.param >= 0 ? nslot++ : -1;
+                        if (slot >= 0) {
+                            pentries.push_back({G.param, slot_total + slot, t});
+                            P->cone_npdiag[t] += 1;
+                        }
+                        r[3] = slot;
                     }
-                    if (two) {
-                        rec[(size_t)j * kRecWords + 4] = g;
-                        rec[(size_t)j * kRecWords + 5] = G.kind | ((slot + 1) << 8);
-                    } else {
-                        rec[(size_t)j * kRecWords + 2] = g;
-                        rec[(size_t)j * kRecWords + 3] = slot;
+                    if (r[4] >= 0) {
+                        const tlq_gate& G = c.gates[r[4]];
+                        const int32_t slot = (G.param >= 0 && G.kind != TLQ_CZ) ? nslot++ : -1;
+                        if (slot >= 0) {
+                            pentries.push_back({G.param, slot_total + slot, t});
+                            P->cone_npdiag[t] += 1;
+                        }
+                        r[5] = G.kind | ((slot + 1) << 8);
                     }
                 }
-                if (!dd.empty()) P->cone_ndiag[t] += 1;
-                body[hdr + 0] = dd.empty() ? 0 : 1;
+                if (any_diag) P->cone_ndiag[t] += 1;
+                body[hdr + 0] = any_diag ? 1 : 0;
                 body[hdr + 1] = (int32_t)live;
                 body[hdr + 2] = 0;
                 body[hdr + 3] = 0;
                 ++nlayers;
             }
+            kp = kp2;
         }
         P->prog.push_back(nlayers);
         P->prog.insert(P->prog.end(), layer_off.begin(), layer_off.end());
@@ -282,11 +297,19 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
     }
     P->n_slots = slot_total;
     P->pmap_off.assign(c.n_params + 1, 0);
-    for (int p = 0; p < c.n_params; ++p) P->pmap_off[p + 1] = P->pmap_off[p] + (int32_t)pentries[p].size();
-    P->pmap_idx.reserve(P->pmap_off.back());
-    P->pmap_term.reserve(P->pmap_off.back());
-    for (int p = 0; p < c.n_params; ++p)
-        for (auto& e : pentries[p]) { P->pmap_idx.push_back(e.first); P->pmap_term.push_back(e.second); }
+    // CSR by parameter (counting sort keeps emission order within a parameter)
+    for (const PEntry& e : pentries) P->pmap_off[e.param + 1] += 1;
+    for (int q = 0; q < c.n_params; ++q) P->pmap_off[q + 1] += P->pmap_off[q];
+    P->pmap_idx.assign(pentries.size(), 0);
+    P->pmap_term.assign(pentries.size(), 0);
+    {
+        std::vector<int32_t> fill(P->pmap_off.begin(), P->pmap_off.end() - 1);
+        for (const PEntry& e : pentries) {
+            const int32_t k = fill[e.param]++;
+            P->pmap_idx[k] = e.slot;
+            P->pmap_term[k] = e.term;
+        }
+    }
     (void)err;
     return P;
 }

@@ -40,6 +40,8 @@ constexpr int kMaxBatchSets = 8192;
 
 struct ServeRequest {
     tlq_ticket id = 0;
+    Circuit* c = nullptr;                 // borrowed until the request completes
+    Ham* h = nullptr;
     int B = 0;
     bool grad = false;
     bool fp64 = false;
@@ -112,7 +114,11 @@ struct Scheduler {
     std::thread th;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<ServeRequest*> queue;
+    std::deque<ServeRequest*> queue;        // planned, waiting for admission
+    std::deque<ServeRequest*> plan_queue;   // submitted, waiting for a planner thread
+    std::condition_variable cv_plan;
+    std::vector<std::thread> planners;
+    int planning = 0;
     std::unordered_map<tlq_ticket, ServeRequest*> all;
     uint64_t next_ticket = 1;
     bool stop = false;
@@ -152,6 +158,7 @@ struct Scheduler {
     }
 
     void run();
+    void plan_loop();
     bool launch(Slot& s, std::vector<ServeRequest*>& batch);
     void finish(Slot& s);
     size_t request_bytes(const ServeRequest& r) const;
@@ -427,6 +434,54 @@ void Scheduler::finish(Slot& sl) {
     sl.busy = false;
 }
 
+// Planner threads: plan (or fetch the cached plan of) each submitted request, copy what the
+// batch needs, and hand it to the scheduler. Failures complete the request with an error.
+void Scheduler::plan_loop() {
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+        cv_plan.wait(lk, [&] { return stop || !plan_queue.empty(); });
+        if (plan_queue.empty()) {
+            if (stop) break;
+            continue;
+        }
+        ServeRequest* r = plan_queue.front();
+        plan_queue.pop_front();
+        ++planning;
+        lk.unlock();
+        std::string err;
+        auto plan = plan_for(*r->c, *r->h, &err);
+        tlq_status st = TLQ_OK;
+        if (!plan) {
+            st = TLQ_EUNSUPPORTED;
+            r->err = "tlq_submit: " + err;
+        } else if (plan->path != TLQ_PATH_CONE) {
+            st = TLQ_EUNSUPPORTED;
+            r->err = "tlq_submit: only nearest-neighbour circuits (the causal-cone path) are served; use tlq_expectation";
+        } else {
+            r->plan = plan;
+            r->gates = r->c->gates;
+            r->term_coeff.reserve(r->h->terms.size());
+            for (const Term& t : r->h->terms) r->term_coeff.push_back(t.coeff);
+            r->bytes = request_bytes(*r);
+            if (r->bytes > ctx->budget / 2) {
+                st = TLQ_ENOMEM;
+                r->err = "tlq_submit: request needs " + std::to_string(r->bytes) + " bytes; a batch may hold " +
+                         std::to_string(ctx->budget / 2);
+            }
+        }
+        lk.lock();
+        --planning;
+        if (st != TLQ_OK) {
+            r->status = st;
+            r->done = true;
+            cv_done.notify_all();
+        } else {
+            queue.push_back(r);
+            cv_work.notify_one();
+        }
+    }
+}
+
 void Scheduler::run() {
     cudaSetDevice(ctx->device);
     for (Slot& s : slots) {
@@ -493,7 +548,7 @@ void Scheduler::run() {
             }
             progressed = true;
         }
-        if (stop && queue.empty() && !slots[0].busy && !slots[1].busy) break;
+        if (stop && queue.empty() && plan_queue.empty() && planning == 0 && !slots[0].busy && !slots[1].busy) break;
         if (!progressed) {
             if (slots[0].busy || slots[1].busy) {
                 lk.unlock();
@@ -521,6 +576,9 @@ void scheduler_stop(Context* ctx) {
         std::lock_guard<std::mutex> lk(S->mu);
         S->stop = true;
     }
+    S->cv_plan.notify_all();
+    for (std::thread& t : S->planners)
+        if (t.joinable()) t.join();
     S->cv_work.notify_all();
     if (S->th.joinable()) S->th.join();
     for (auto& kv : S->all) delete kv.second;
@@ -545,6 +603,7 @@ tlq_status tlq_submit(tlq_ctx ctx_h, tlq_circuit c_h, tlq_ham h_h, const double*
     if (c->ctx != ctx || h->ctx != ctx) { set_error("tlq_submit: handle from another context"); return TLQ_EINVAL; }
     if (c->n != h->n) { set_error("tlq_submit: circuit and Hamiltonian qubit counts differ"); return TLQ_EINVAL; }
     if (B <= 0) { set_error("tlq_submit: B must be positive"); return TLQ_EINVAL; }
+    if (B > kMaxBatchSets) { set_error("tlq_submit: B exceeds the batch limit of " + std::to_string(kMaxBatchSets)); return TLQ_ENOMEM; }
     if ((!theta && c->n_params > 0) || !energy || (want_grad && !grad)) { set_error("tlq_submit: NULL buffer"); return TLQ_EINVAL; }
     if (prec < TLQ_FP32 || prec > TLQ_FP64_REF) { set_error("tlq_submit: unknown precision"); return TLQ_EINVAL; }
     if (ctx->host_only()) { set_error("tlq_submit: host-only context"); return TLQ_EUNSUPPORTED; }
@@ -555,17 +614,15 @@ tlq_status tlq_submit(tlq_ctx ctx_h, tlq_circuit c_h, tlq_ham h_h, const double*
             ctx->sched = new Scheduler();
             ctx->sched->ctx = ctx;
             ctx->sched->th = std::thread([s = ctx->sched] { s->run(); });
+            const unsigned hw = std::thread::hardware_concurrency();
+            const int np = (int)std::max(1u, std::min(8u, hw / 2));
+            for (int k = 0; k < np; ++k) ctx->sched->planners.emplace_back([s = ctx->sched] { s->plan_loop(); });
         }
         S = ctx->sched;
     }
-    std::string err;
-    auto plan = S->plan_for(*c, *h, &err);
-    if (!plan) { set_error("tlq_submit: " + err); return TLQ_EUNSUPPORTED; }
-    if (plan->path != TLQ_PATH_CONE) {
-        set_error("tlq_submit: only nearest-neighbour circuits (the causal-cone path) are served; use tlq_expectation");
-        return TLQ_EUNSUPPORTED;
-    }
     auto* r = new ServeRequest();
+    r->c = c;
+    r->h = h;
     r->B = B;
     r->grad = want_grad != 0;
     r->fp64 = prec == TLQ_FP64_REF;
@@ -573,26 +630,15 @@ tlq_status tlq_submit(tlq_ctx ctx_h, tlq_circuit c_h, tlq_ham h_h, const double*
     r->theta = theta;
     r->energy = energy;
     r->grad_out = want_grad ? grad : nullptr;
-    r->plan = plan;
-    r->gates = c->gates;
-    r->term_coeff.reserve(h->terms.size());
-    for (const Term& t : h->terms) r->term_coeff.push_back(t.coeff);
-    r->bytes = S->request_bytes(*r);
-    if (r->bytes > ctx->budget / 2 || (size_t)B > (size_t)8192) {
-        set_error("tlq_submit: request needs " + std::to_string(r->bytes) + " bytes; a batch may hold " +
-                  std::to_string(ctx->budget / 2));
-        delete r;
-        return TLQ_ENOMEM;
-    }
     {
         std::lock_guard<std::mutex> lk(S->mu);
         r->id = S->next_ticket++;
         r->t_submit = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
         S->all[r->id] = r;
-        S->queue.push_back(r);
+        S->plan_queue.push_back(r);
         *out = r->id;
     }
-    S->cv_work.notify_one();
+    S->cv_plan.notify_one();
     return TLQ_OK;
 }
 

@@ -161,13 +161,21 @@ def test_admission_budget_and_unsupported():
         hd = small.problem(prob)
         E = np.zeros(prob.B)
         G = np.zeros(prob.theta.shape)
+        th = np.ascontiguousarray(prob.theta)
+        t = B.tlq_submit(small.h, hd[0].h, hd[1].h, th, E, G)
         with pytest.raises(B.TLQError) as ei:
-            B.tlq_submit(small.h, hd[0].h, hd[1].h, np.ascontiguousarray(prob.theta), E, G)
+            B.tlq_poll(small.h, t, -1)
         assert ei.value.status == B.TLQ_ENOMEM
         q = W.qaoa_problem(10, 1, 1, seed=0)   # non-local: dense path, not served
         hq = small.problem(q)
+        thq = np.ascontiguousarray(q.theta)
+        Eq = np.zeros(1)
+        t = B.tlq_submit(small.h, hq[0].h, hq[1].h, thq, Eq, None)
         with pytest.raises(B.TLQError) as ei:
-            B.tlq_submit(small.h, hq[0].h, hq[1].h, np.ascontiguousarray(q.theta), np.zeros(1), None)
+            B.tlq_poll(small.h, t, -1)
         assert ei.value.status == B.TLQ_EUNSUPPORTED
+        with pytest.raises(B.TLQError) as ei:
+            B.tlq_poll(small.h, t, 0)   # failed tickets are retired too
+        assert ei.value.status == B.TLQ_EINVAL
     finally:
         small.close()
