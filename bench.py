@@ -125,11 +125,11 @@ class ClockSampler:
 def algorithmic_flops(B_mod, ctx, c, h, prob, grad=True):
     """Algorithmic FP32 flops of one batched cone launch (forward, measurement, adjoint).
 
-    Per cone of true width w (A = 2^w amplitudes), with R rotations, D diagonal layers and
-    Pd parametrised diagonal gates in the cone:
+    Per work cone of true width w (A = 2^w amplitudes), with R rotations, D diagonal layers,
+    Pd parametrised diagonal gates and m terms measured on its window:
       forward   A * (6 R + 6 D)       real 2x2 rotation on (re, im): 6 flop/amp; one complex
                                       multiply per amplitude per diagonal layer
-      measure   A * 8                 <psi|P|psi> and lambda = P psi
+      measure   A * 8 m               <psi|P_t|psi> and lambda += c_t P_t psi per term
       adjoint   A * (4 R + 12 R + 12 D + 3 D + Pd)
                                       Im<lam|G|psi> (4/amp), un-apply on psi and lam (2 x 6),
                                       diagonal un-apply (2 x 6), Im(conj(lam) psi) (3) and one
@@ -137,10 +137,9 @@ def algorithmic_flops(B_mod, ctx, c, h, prob, grad=True):
     Padding to the kernel's minimum width is not counted.
     """
     n_terms = len(prob.terms)
-    _, lo, w, _ = B_mod.tlq_plan_info(ctx.h, c.h, h.h, n_terms)
-    nrot, ndiag, npdiag, _ = B_mod.tlq_plan_cone_stats(ctx.h, c.h, h.h, n_terms)
+    nrot, ndiag, npdiag, _, w, nterms = B_mod.tlq_plan_cone_stats(ctx.h, c.h, h.h, n_terms)
     A = np.power(2.0, w.astype(np.float64))
-    f = A * (6 * nrot + 6 * ndiag + 8)
+    f = A * (6 * nrot + 6 * ndiag + 8 * nterms)
     if grad:
         f += A * (16 * nrot + 15 * ndiag + npdiag)
     return float(np.sum(f)) * prob.B

@@ -194,12 +194,15 @@ typedef enum { TLQ_PATH_CONE = 0, TLQ_PATH_DENSE = 1 } tlq_path;
 tlq_status tlq_plan_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* path, int32_t* lo, int32_t* w,
                          int32_t* ngates);
 
-/* Per-term cone statistics for (c, h) on the cone path: rotations nrot[t], diagonal
- * layers ndiag[t] and parametrised diagonal gates npdiag[t] inside term t's cone, and the
- * width weff[t] the kernel runs (the cone padded to at least 8 qubits). Used to count the
- * algorithmic work of a call. Any array may be NULL. TLQ_EUNSUPPORTED on the dense path. */
-tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* nrot, int32_t* ndiag,
-                               int32_t* npdiag, int32_t* weff);
+/* Work-cone statistics for (c, h) on the cone path. Terms whose causal cone lies inside
+ * another term's window are measured on that window, so the plan has *ncones <= n_terms
+ * work cones. For cone k: rotations nrot[k], diagonal layers ndiag[k] and parametrised
+ * diagonal gates npdiag[k] it simulates, the width weff[k] the kernel runs (padded to at
+ * least 8 qubits), its true width wtrue[k] and the number of terms nterms[k] measured on it.
+ * Arrays must hold n_terms entries; any pointer may be NULL. Used to count the algorithmic
+ * work of a call. TLQ_EUNSUPPORTED on the dense path. */
+tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* ncones, int32_t* nrot, int32_t* ndiag,
+                               int32_t* npdiag, int32_t* weff, int32_t* wtrue, int32_t* nterms);
 
 /* Kernel timing for benchmarks. While enabled, every compute call records CUDA events
  * around its dominant kernel (the batched cone kernel, or the dense pass sequence) on the

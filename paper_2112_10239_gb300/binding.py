@@ -79,7 +79,7 @@ def lib():
         L.tlq_last_error.argtypes = [vp]
         L.tlq_last_error.restype = ctypes.c_char_p
         L.tlq_plan_info.argtypes = [vp, vp, vp, ip, ip, ip, ip]
-        L.tlq_plan_cone_stats.argtypes = [vp, vp, vp, ip, ip, ip, ip]
+        L.tlq_plan_cone_stats.argtypes = [vp, vp, vp, ip, ip, ip, ip, ip, ip, ip]
         L.tlq_profile_enable.argtypes = [vp, ctypes.c_int]
         L.tlq_profile_last.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ip]
         L.tlq_expectation_grad_static.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp, vp, vp]
@@ -242,10 +242,12 @@ def tlq_plan_info(ctx, circ, ham, n_terms):
 
 
 def tlq_plan_cone_stats(ctx, circ, ham, n_terms):
+    """Per work cone: (nrot, ndiag, npdiag, weff, wtrue, nterms), arrays of length ncones."""
     ip = ctypes.POINTER(ctypes.c_int32)
-    out = [np.zeros(n_terms, dtype=np.int32) for _ in range(4)]
-    _check(lib().tlq_plan_cone_stats(ctx, circ, ham, *[a.ctypes.data_as(ip) for a in out]), ctx)
-    return tuple(out)   # nrot, ndiag, npdiag, weff
+    nc = ctypes.c_int32()
+    out = [np.zeros(max(1, n_terms), dtype=np.int32) for _ in range(6)]
+    _check(lib().tlq_plan_cone_stats(ctx, circ, ham, ctypes.byref(nc), *[a.ctypes.data_as(ip) for a in out]), ctx)
+    return tuple(a[:nc.value] for a in out)
 
 
 def tlq_profile_enable(ctx, on=True):

@@ -26,6 +26,7 @@ const char* get_error() { return t_err.c_str(); }
 
 PlanEntry::~PlanEntry() {
     cudaFree(d_cones);
+    cudaFree(d_meas);
     cudaFree(d_prog);
     cudaFree(d_term_coeff);
     cudaFree(d_pmap_off);
@@ -76,6 +77,7 @@ tlq_status get_plan(Context* ctx, Circuit* c, Ham* h, std::shared_ptr<PlanEntry>
         TLQ_TRY(upload(plan->term_coeff, &pe->d_term_coeff, &bytes));
         if (plan->path == TLQ_PATH_CONE) {
             TLQ_TRY(upload(plan->cones, &pe->d_cones, &bytes));
+            TLQ_TRY(upload(plan->meas, &pe->d_meas, &bytes));
             TLQ_TRY(upload(plan->prog, &pe->d_prog, &bytes));
             TLQ_TRY(upload(plan->pmap_off, &pe->d_pmap_off, &bytes));
             TLQ_TRY(upload(plan->pmap_idx, &pe->d_pmap_idx, &bytes));
@@ -187,7 +189,7 @@ size_t cone_workspace_bytes(const PlanEntry& pe, const Circuit& c, int B, bool f
     const size_t r2 = fp64 ? 16 : 8;
     size_t s = 0;
     s += align256((size_t)B * c.gates.size() * r2);
-    s += align256((size_t)B * P.cones.size() * sizeof(double));
+    s += align256((size_t)B * P.term_coeff.size() * sizeof(double));
     if (grad) s += align256((size_t)B * std::max<int32_t>(1, P.n_slots) * sizeof(double));
     if (g_grid > 0) s += align256((size_t)g_grid * global_slot_bytes(pe.g_maxW, fp64, grad));
     return s + 1024;
@@ -282,6 +284,7 @@ tlq_status run_device(Context* ctx, Circuit* c, Ham* h, const double* theta_dev,
     }
     ConeLaunch L;
     L.cones = pe->d_cones;
+    L.meas = pe->d_meas;
     L.prog = pe->d_prog;
     L.term_coeff = pe->d_term_coeff;
     L.pmap_off = pe->d_pmap_off;
@@ -290,7 +293,7 @@ tlq_status run_device(Context* ctx, Circuit* c, Ham* h, const double* theta_dev,
     L.gates = pe->d_gates;
     L.n_gates = (int32_t)c->gates.size();
     L.n_params = c->n_params;
-    L.n_terms = (int32_t)P.cones.size();
+    L.n_terms = (int32_t)P.term_coeff.size();
     L.n_slots = P.n_slots;
     L.B = B;
     L.theta = theta_dev;
@@ -303,7 +306,7 @@ tlq_status run_device(Context* ctx, Circuit* c, Ham* h, const double* theta_dev,
     L.g_maxW = pe->g_maxW;
     const size_t r2 = fp64 ? 16 : 8;
     L.gate_table = ws->take((size_t)B * c->gates.size() * r2);
-    L.e_part = (double*)ws->take((size_t)B * P.cones.size() * sizeof(double));
+    L.e_part = (double*)ws->take((size_t)B * P.term_coeff.size() * sizeof(double));
     L.g_part = grad ? (double*)ws->take((size_t)B * std::max<int32_t>(1, P.n_slots) * sizeof(double)) : nullptr;
     L.g_grid = g_grid;
     L.gscratch_slot = g_grid > 0 ? global_slot_bytes(pe->g_maxW, fp64, grad) : 0;
@@ -651,7 +654,7 @@ tlq_status tlq_plan_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* path, i
     const Plan& P = *pe->plan;
     if (path) *path = P.path;
     if (P.path == TLQ_PATH_CONE) {
-        for (size_t t = 0; t < P.cones.size(); ++t) {
+        for (size_t t = 0; t < P.cone_lo.size(); ++t) {
             if (lo) lo[t] = P.cone_lo[t];
             if (w) w[t] = P.cone_wtrue[t];
             if (ngates) ngates[t] = P.cone_gates[t];
@@ -664,8 +667,8 @@ tlq_status tlq_plan_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* path, i
 
 extern "C" {
 
-tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* nrot, int32_t* ndiag, int32_t* npdiag,
-                               int32_t* weff) {
+tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* ncones, int32_t* nrot, int32_t* ndiag,
+                               int32_t* npdiag, int32_t* weff, int32_t* wtrue, int32_t* nterms) {
     if (!ctx || !c || !h) { set_error("NULL handle"); return TLQ_EINVAL; }
     if (c->n != h->n) { set_error("circuit and Hamiltonian qubit counts differ"); return TLQ_EINVAL; }
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -673,11 +676,14 @@ tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n
     TLQ_TRY(get_plan(ctx, c, h, &pe));
     const Plan& P = *pe->plan;
     if (P.path != TLQ_PATH_CONE) { set_error("not on the cone path"); return TLQ_EUNSUPPORTED; }
+    if (ncones) *ncones = (int32_t)P.cones.size();
     for (size_t t = 0; t < P.cones.size(); ++t) {
         if (nrot) nrot[t] = P.cone_nrot[t];
         if (ndiag) ndiag[t] = P.cone_ndiag[t];
         if (npdiag) npdiag[t] = P.cone_npdiag[t];
         if (weff) weff[t] = P.cones[t].W;
+        if (wtrue) wtrue[t] = P.group_wtrue[t];
+        if (nterms) nterms[t] = P.cones[t].nmterms;
     }
     return TLQ_OK;
 }

@@ -121,6 +121,8 @@ __device__ __forceinline__ T2 phase_of(const T2* tab, int tab1, int tab2, int W,
 
 struct ConeArgs {
     const ConeDev* cones;
+    const MeasDev* meas;
+    const double* term_coeff;
     const int32_t* prog;
     const int32_t* items;
     const ChunkDev* chunks;
@@ -409,42 +411,55 @@ __device__ void flush_pass(const real* red, int nw, unsigned m, int s, const Tea
     }
 }
 
-// <psi|P|psi> for the cone's Pauli term; when GRAD also lam = P psi. Ends with a barrier.
+// <psi|P_t|psi> for every term t measured on this window, written to e_out[term]; when
+// GRAD also lam = sum_t c_t P_t psi (the term coefficients folded into the adjoint).
+// Ends with a team barrier.
 template <typename real, typename T2, bool GRAD>
-__device__ double measure(const TeamMem<T2>& M, const ConeDev& cd, const Team& tm, real* red) {
+__device__ void measure(const TeamMem<T2>& M, const MeasDev* mt, int nmt, const double* coeff, double* e_out,
+                        const Team& tm, real* red) {
     const int W = M.W;
     const int nout = 1 << (W - 4);
-    T2 f0;   // (-i)^ny
-    const int ny = cd.ny & 3;
-    f0.x = ny == 0 ? 1 : ny == 2 ? -1 : 0;
-    f0.y = ny == 1 ? -1 : ny == 3 ? 1 : 0;
-    real acc = 0;
-    for (int o = tm.tid; o < nout; o += tm.tt) {
-        const int x0 = o << 4;
-        T2 a[16];
-        load16(a, M.psi + pad16(x0), 1);
-        T2 lv[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int x = x0 | j;
-            const T2 v = M.psi[pad16(x ^ (int)cd.flip)];
-            T2 t = cmul(f0, v);
-            if (__popc((unsigned)x & cd.zy) & 1) { t.x = -t.x; t.y = -t.y; }
-            lv[j] = t;
-            acc += a[j].x * t.x + a[j].y * t.y;
-        }
-        if (GRAD) store16(lv, M.lam + pad16(x0), 1);
-    }
-    acc = team_warp_sum(acc, tm);
     const int nw = nwarps_of(tm.tt);
     const int warp = tm.tt >= 32 ? (tm.tid >> 5) : 0;
     const bool leader = tm.tt >= 32 ? ((tm.tid & 31) == 0) : (tm.tid == 0);
-    if (leader) red[warp] = acc;
-    tm.sync();
-    real e = 0;
-    for (int w = 0; w < nw; ++w) e += red[w];
-    tm.sync();
-    return (double)e;
+    for (int k = 0; k < nmt; ++k) {
+        const MeasDev md = mt[k];
+        T2 f0;   // (-i)^ny
+        const int ny = md.ny & 3;
+        f0.x = ny == 0 ? 1 : ny == 2 ? -1 : 0;
+        f0.y = ny == 1 ? -1 : ny == 3 ? 1 : 0;
+        const real ck = GRAD ? (real)coeff[md.term] : (real)0;
+        real acc = 0;
+        for (int o = tm.tid; o < nout; o += tm.tt) {
+            const int x0 = o << 4;
+            T2 a[16];
+            load16(a, M.psi + pad16(x0), 1);
+            T2 lv[16];
+            if (GRAD && k > 0) load16(lv, M.lam + pad16(x0), 1);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int x = x0 | j;
+                const T2 v = M.psi[pad16(x ^ (int)md.flip)];
+                T2 t = cmul(f0, v);
+                if (__popc((unsigned)x & md.zy) & 1) { t.x = -t.x; t.y = -t.y; }
+                acc += a[j].x * t.x + a[j].y * t.y;
+                if (GRAD) {
+                    if (k == 0) { lv[j].x = ck * t.x; lv[j].y = ck * t.y; }
+                    else { lv[j].x += ck * t.x; lv[j].y += ck * t.y; }
+                }
+            }
+            if (GRAD) store16(lv, M.lam + pad16(x0), 1);
+        }
+        acc = team_warp_sum(acc, tm);
+        if (leader) red[warp] = acc;
+        tm.sync();
+        if (tm.tid == 0) {
+            real e = 0;
+            for (int w = 0; w < nw; ++w) e += red[w];
+            e_out[md.term] = (double)e;
+        }
+        tm.sync();
+    }
 }
 
 template <typename real, bool GRAD, bool GLOBAL>
@@ -508,8 +523,8 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
             first = false;
         }
     }
-    const double e = measure<real, T2, GRAD>(M, cd, tm, red);
-    if (tm.tid == 0) A.e_part[(R ? (size_t)R->e_off : (size_t)b * A.n_terms) + cd.term] = e;
+    measure<real, T2, GRAD>(M, (R ? R->meas : A.meas) + cd.mterm_off, cd.nmterms, R ? R->term_coeff : A.term_coeff,
+                            A.e_part + (R ? (size_t)R->e_off : (size_t)b * A.n_terms), tm, red);
     if (!GRAD) return;
     double* gdst = A.g_part + (R ? (size_t)R->g_off : (size_t)b * A.n_slots) + cd.slot_off;
     int rpar = 0;
@@ -623,7 +638,7 @@ __global__ void grad_reduce_kernel(const double* g_part, const int32_t* off, con
     if (i >= (long long)B * P) return;
     const int b = (int)(i / P), p = (int)(i % P);
     Neumaier acc;
-    for (int k = off[p]; k < off[p + 1]; ++k) acc.add(coeff[term[k]] * g_part[(size_t)b * S + idx[k]]);
+    for (int k = off[p]; k < off[p + 1]; ++k) acc.add((term[k] >= 0 ? coeff[term[k]] : 1.0) * g_part[(size_t)b * S + idx[k]]);
     grad[i] = acc.value();
 }
 
@@ -638,6 +653,8 @@ static int launch_cone_t(const ConeLaunch& L, cudaStream_t st, int begin, int en
     if (e != cudaSuccess) return (int)e;
     ConeArgs A;
     A.cones = L.cones;
+    A.meas = L.meas;
+    A.term_coeff = L.term_coeff;
     A.prog = L.prog;
     A.items = L.items;
     A.chunks = L.chunks;
@@ -754,7 +771,7 @@ __global__ void batch_grad_kernel(const SetRec* sets, const double* g_part) {
     if (!R.grad || p >= R.n_params) return;
     Neumaier acc;
     for (int k = R.pmap_off[p]; k < R.pmap_off[p + 1]; ++k)
-        acc.add(R.term_coeff[R.pmap_term[k]] * g_part[R.g_off + R.pmap_idx[k]]);
+        acc.add((R.pmap_term[k] >= 0 ? R.term_coeff[R.pmap_term[k]] : 1.0) * g_part[R.g_off + R.pmap_idx[k]]);
     R.grad[p] = acc.value();
 }
 

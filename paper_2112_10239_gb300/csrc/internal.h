@@ -20,15 +20,24 @@ namespace tlq {
 
 // One term's causal cone: a window of W qubits starting at chain site `lo` (window
 // qubit j is chain qubit lo + j; qubits past the chain end are padding and stay |0>).
+// One cone of work: a window shared by one or more terms (a term whose own causal cone fits
+// inside another term's window is measured on that window).
 struct ConeDev {
-    int32_t term;       // term index (row of the per-term energy buffer)
     int32_t W;          // effective window width (>= kMinConeW)
     int32_t prog_off;   // offset of the cone's program in the int32 program array
     int32_t slot_off;   // first gradient slot of this cone
+    int32_t nslots;     // gradient slots of this cone
+    int32_t mterm_off;  // first of this cone's measured terms in the MeasDev array
+    int32_t nmterms;    // terms measured on this window
+    int32_t pad[2];
+};
+
+// A term measured on a cone's window: P = (-i)^ny (-1)^popc(x & zy) X^flip.
+struct MeasDev {
+    int32_t term;       // term index (row of the per-term energy buffer, coefficient index)
     uint32_t flip;      // window-bit mask of X/Y letters
     uint32_t zy;        // window-bit mask of Y/Z letters (sign (-1)^bit)
-    int32_t ny;         // number of Y letters: overall factor (-i)^ny
-    int32_t nslots;     // gradient slots of this cone
+    int32_t ny;         // number of Y letters
 };
 
 // A chunk of work for one CTA: `count` (cone, set) items of equal width W starting at
@@ -53,6 +62,7 @@ struct ChunkDev {
 constexpr int kRecWords = 6;
 constexpr int kLayerHeader = 4;
 constexpr int kMinConeW = 8;       // narrower cones are padded to this width
+constexpr int kMaxGroupTerms = 8;  // terms measured on one shared window
 constexpr int kMaxSmemConeW = 13;  // widest cone kept in shared memory (FP32)
 constexpr int kMaxConeW = 20;      // widest cone on the cone path (global-memory tier)
 constexpr int kCtaThreads = 512;
@@ -156,16 +166,19 @@ struct Ham {
 struct Plan {
     tlq_path path = TLQ_PATH_CONE;
     // cone path
-    std::vector<ConeDev> cones;           // one per term
+    std::vector<ConeDev> cones;           // one per term group (shared window)
+    std::vector<MeasDev> meas;            // measured terms of all cones
+    std::vector<int32_t> group_wtrue;     // true width of each group's window
     std::vector<int32_t> prog;            // programs of all cones
     std::vector<int32_t> cone_gates;      // gates in each cone (introspection)
     std::vector<int32_t> cone_lo;         // window start per term
     std::vector<int32_t> cone_wtrue;      // true (unpadded, clipped) width per term
-    std::vector<int32_t> cone_nrot;       // rotations in each cone
-    std::vector<int32_t> cone_ndiag;      // layers with diagonal gates in each cone
-    std::vector<int32_t> cone_npdiag;     // parametrised diagonal gates in each cone
+    std::vector<int32_t> cone_nrot;       // rotations in each group cone
+    std::vector<int32_t> cone_ndiag;      // layers with diagonal gates in each group cone
+    std::vector<int32_t> cone_npdiag;     // parametrised diagonal gates in each group cone
     int32_t n_slots = 0;                  // gradient slots per parameter set
-    // slot -> parameter map, CSR by parameter: g[p] = sum_i term_coeff[term[i]] * part[idx[i]]
+    // slot -> parameter map, CSR by parameter: g[p] = sum_i part[idx[i]] (the term coefficients are
+    // folded into the adjoint's lambda; term[i] = -1)
     std::vector<int32_t> pmap_off;        // n_params + 1
     std::vector<int32_t> pmap_idx;
     std::vector<int32_t> pmap_term;       // term owning each entry (its coefficient scales the slot)
@@ -189,6 +202,7 @@ struct DevPlan;   // device copy of a Plan (owned by the context cache)
 struct ConeLaunch {
     // device pointers
     const ConeDev* cones = nullptr;
+    const MeasDev* meas = nullptr;
     const int32_t* prog = nullptr;
     const double* term_coeff = nullptr;
     const int32_t* pmap_off = nullptr;
@@ -234,6 +248,7 @@ int launch_cone(ConeLaunch& L, void* stream);
 // live. Sets of different circuits share one launch through these records.
 struct SetRec {
     const ConeDev* cones;
+    const MeasDev* meas;
     const int32_t* prog;
     const tlq_gate* gates;
     const double* theta;        // this set's angles [n_params]

@@ -210,7 +210,7 @@ extern "C" tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tl
     }
     const Plan& P = *hp->plan;
     const int G = (int)Ci->gates.size();
-    const int T = (int)P.cones.size();
+    const int T = (int)P.term_coeff.size();
     const int S = std::max<int32_t>(1, P.n_slots);
     const int n_glob = (int)hp->chunks.size() - hp->n_chunks_smem;
     const int g_grid = std::max(0, std::min(n_glob, C->sm_count));
@@ -221,6 +221,7 @@ extern "C" tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tl
     Carve cv{reinterpret_cast<unsigned char*>(scratch)};
     tlq_gate* d_gates = (tlq_gate*)cv.take((size_t)std::max(1, G) * sizeof(tlq_gate));
     ConeDev* d_cones = (ConeDev*)cv.take(P.cones.size() * sizeof(ConeDev));
+    MeasDev* d_meas = (MeasDev*)cv.take(P.meas.size() * sizeof(MeasDev));
     int32_t* d_prog = (int32_t*)cv.take(P.prog.size() * sizeof(int32_t));
     double* d_tc = (double*)cv.take(P.term_coeff.size() * sizeof(double));
     int32_t* d_poff = (int32_t*)cv.take(P.pmap_off.size() * sizeof(int32_t));
@@ -245,6 +246,7 @@ extern "C" tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tl
     };
     put(d_gates, Ci->gates.data(), (size_t)G * sizeof(tlq_gate));
     put(d_cones, P.cones.data(), P.cones.size() * sizeof(ConeDev));
+    put(d_meas, P.meas.data(), P.meas.size() * sizeof(MeasDev));
     put(d_prog, P.prog.data(), P.prog.size() * sizeof(int32_t));
     put(d_tc, P.term_coeff.data(), P.term_coeff.size() * sizeof(double));
     put(d_poff, P.pmap_off.data(), P.pmap_off.size() * sizeof(int32_t));
@@ -257,6 +259,7 @@ extern "C" tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tl
 
     ConeLaunch L;
     L.cones = d_cones;
+    L.meas = d_meas;
     L.prog = d_prog;
     L.term_coeff = d_tc;
     L.pmap_off = d_poff;

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <iterator>
 #include <map>
 
 namespace tlq {
@@ -111,26 +112,25 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
     }
     const LayerIndex ix = index_layers(c);
     std::vector<char> inS(c.n, 0), inc(c.gates.size(), 0);
-    P->cones.resize(T);
     P->cone_lo.resize(T);
     P->cone_wtrue.resize(T);
     P->cone_gates.resize(T);
-    P->cone_nrot.assign(T, 0);
-    P->cone_ndiag.assign(T, 0);
-    P->cone_npdiag.assign(T, 0);
     struct PEntry { int32_t param, slot, term; };
     std::vector<PEntry> pentries;   // gradient slots in emission order
     int32_t slot_total = 0;
 
     std::vector<std::pair<int, int>> dpart;   // (diagonal gate, sub-layer) of one layer
     std::vector<uint32_t> zmask, pmask;
+    // ---- phase 1: each term's own causal cone ----
+    std::vector<std::vector<int>> tkept(T);
+    std::vector<int> tlo(T), thi(T);
     for (int t = 0; t < T; ++t) {
         const Term& term = h.terms[t];
         std::vector<int> S(term.sites.begin(), term.sites.end());
         for (int q : S) inS[q] = 1;
         bool diag_op = true;
         for (char ch : term.letters) if (ch != 'Z') diag_op = false;
-        std::vector<int> kept;   // gate indices in the cone
+        std::vector<int>& kept = tkept[t];   // gate indices in the cone
         for (int l = L - 1; l >= 0; --l) {
             if (!diag_op && !c.layers[l].diag.empty()) {
                 std::vector<int> grow;
@@ -151,15 +151,18 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                 if (g >= 0 && !inc[g]) { inc[g] = 1; kept.push_back(g); diag_op = false; }
             }
         }
-        int lo = *std::min_element(S.begin(), S.end());
-        int hi = *std::max_element(S.begin(), S.end());
+        const int lo = *std::min_element(S.begin(), S.end());
+        const int hi = *std::max_element(S.begin(), S.end());
         for (int q : S) inS[q] = 0;
         for (int g : kept) inc[g] = 0;
+        std::sort(kept.begin(), kept.end());
+        tlo[t] = lo;
+        thi[t] = hi;
         const int wtrue = hi - lo + 1;
-        int W = std::max(wtrue, kMinConeW);
         P->cone_lo[t] = lo;
         P->cone_wtrue[t] = wtrue;
         P->cone_gates[t] = (int32_t)kept.size();
+        const int W = std::max(wtrue, kMinConeW);
         P->max_w = std::max(P->max_w, W);
         if (W > kMaxConeW) {
             P->path = TLQ_PATH_DENSE;
@@ -168,13 +171,53 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                                          std::to_string(kDenseMaxQubits) + " qubits";
             return P->dense ? P : nullptr;
         }
+    }
+    // ---- phase 2: terms whose window lies inside another term's window share its cone ----
+    // (one forward pass and one adjoint pass with lambda = sum_t c_t P_t psi serve all of them;
+    // the window simulates the union of the members' cone gates, exact for each member)
+    std::vector<int> order(T);
+    for (int t = 0; t < T; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return thi[a] - tlo[a] > thi[b] - tlo[b]; });
+    std::vector<std::vector<int>> members;
+    std::vector<int> glo, ghi;
+    std::vector<std::vector<int>> by_lo(c.n);
+    for (int t : order) {
+        int found = -1;
+        for (int lo = tlo[t]; lo >= 0 && lo >= tlo[t] - kMaxConeW && found < 0; --lo)
+            for (int gidx : by_lo[lo])
+                if (ghi[gidx] >= thi[t] && members[gidx].size() < (size_t)kMaxGroupTerms) { found = gidx; break; }
+        if (found < 0) {
+            found = (int)members.size();
+            members.emplace_back();
+            glo.push_back(tlo[t]);
+            ghi.push_back(thi[t]);
+            by_lo[tlo[t]].push_back(found);
+        }
+        members[found].push_back(t);
+    }
+    const int NG = (int)members.size();
+    P->cones.resize(NG);
+    P->cone_nrot.assign(NG, 0);
+    P->cone_ndiag.assign(NG, 0);
+    P->cone_npdiag.assign(NG, 0);
+    P->group_wtrue.assign(NG, 0);
+    // ---- phase 3: one program per group ----
+    for (int t = 0; t < NG; ++t) {
+        std::sort(members[t].begin(), members[t].end());
+        std::vector<int> kept;
+        for (int m : members[t]) {
+            std::vector<int> merged;
+            std::set_union(kept.begin(), kept.end(), tkept[m].begin(), tkept[m].end(), std::back_inserter(merged));
+            kept.swap(merged);
+        }
+        const int lo = glo[t];
+        const int W = std::max(ghi[t] - glo[t] + 1, kMinConeW);
+        P->group_wtrue[t] = ghi[t] - glo[t] + 1;
         // Emit the program in forward layer order: per layer a header and one fixed record
         // per window qubit (see internal.h). A layer whose cone gates put two RZ on one
         // qubit or two two-qubit gates on one pair is split into several layers (the
         // diagonal gates commute, so any split is exact).
-        std::sort(kept.begin(), kept.end());
         ConeDev cd{};
-        cd.term = t;
         cd.W = W;
         cd.prog_off = (int32_t)P->prog.size();
         cd.slot_off = slot_total;
@@ -242,7 +285,7 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                     if (r[0] < 0) continue;
                     const tlq_gate& G = c.gates[r[0]];
                     const int32_t slot = G.param >= 0 ? nslot++ : -1;
-                    if (slot >= 0) pentries.push_back({G.param, slot_total + slot, t});
+                    if (slot >= 0) pentries.push_back({G.param, slot_total + slot, -1});
                     r[1] = G.kind | ((slot + 1) << 8);
                     P->cone_nrot[t] += 1;
                 }
@@ -252,7 +295,7 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                         const tlq_gate& G = c.gates[r[2]];
                         const int32_t slot = G.param >= 0 ? nslot++ : -1;
                         if (slot >= 0) {
-                            pentries.push_back({G.param, slot_total + slot, t});
+                            pentries.push_back({G.param, slot_total + slot, -1});
                             P->cone_npdiag[t] += 1;
                         }
                         r[3] = slot;
@@ -261,7 +304,7 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                         const tlq_gate& G = c.gates[r[4]];
                         const int32_t slot = (G.param >= 0 && G.kind != TLQ_CZ) ? nslot++ : -1;
                         if (slot >= 0) {
-                            pentries.push_back({G.param, slot_total + slot, t});
+                            pentries.push_back({G.param, slot_total + slot, -1});
                             P->cone_npdiag[t] += 1;
                         }
                         r[5] = G.kind | ((slot + 1) << 8);
@@ -281,18 +324,21 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
         P->prog.insert(P->prog.end(), body.begin(), body.end());
         cd.nslots = nslot;
         slot_total += nslot;
-        uint32_t flip = 0, zy = 0;
-        int ny = 0;
-        for (size_t k = 0; k < term.sites.size(); ++k) {
-            uint32_t bit = 1u << (term.sites[k] - lo);
-            char ch = term.letters[k];
-            if (ch == 'X' || ch == 'Y') flip |= bit;
-            if (ch == 'Y' || ch == 'Z') zy |= bit;
-            if (ch == 'Y') ++ny;
+        cd.mterm_off = (int32_t)P->meas.size();
+        cd.nmterms = (int32_t)members[t].size();
+        for (int m : members[t]) {
+            const Term& term = h.terms[m];
+            MeasDev md{};
+            md.term = m;
+            for (size_t q = 0; q < term.sites.size(); ++q) {
+                const uint32_t bit = 1u << (term.sites[q] - lo);
+                const char ch = term.letters[q];
+                if (ch == 'X' || ch == 'Y') md.flip |= bit;
+                if (ch == 'Y' || ch == 'Z') md.zy |= bit;
+                if (ch == 'Y') ++md.ny;
+            }
+            P->meas.push_back(md);
         }
-        cd.flip = flip;
-        cd.zy = zy;
-        cd.ny = ny;
         P->cones[t] = cd;
     }
     P->n_slots = slot_total;

@@ -20,6 +20,7 @@ struct PlanEntry {
     uint64_t circ_id = 0, ham_id = 0;
     // cone path device buffers
     ConeDev* d_cones = nullptr;
+    MeasDev* d_meas = nullptr;
     int32_t* d_prog = nullptr;
     double* d_term_coeff = nullptr;
     int32_t* d_pmap_off = nullptr;

@@ -189,10 +189,11 @@ int smem_optin_dev(int device) {
 
 size_t Scheduler::request_bytes(const ServeRequest& r) const {
     const Plan& P = *r.plan;
-    const size_t G = r.gates.size(), T = P.cones.size(), E = P.pmap_idx.size();
+    const size_t G = r.gates.size(), T = P.term_coeff.size(), E = P.pmap_idx.size();
     const size_t r2 = r.fp64 ? 16 : 8;
     size_t s = 0;
-    s += al(G * sizeof(tlq_gate)) + al(T * sizeof(ConeDev)) + al(P.prog.size() * 4) + al(T * 8);
+    s += al(G * sizeof(tlq_gate)) + al(P.cones.size() * sizeof(ConeDev)) + al(P.meas.size() * sizeof(MeasDev)) +
+         al(P.prog.size() * 4) + al(T * 8);
     s += al((P.pmap_off.size()) * 4) + 2 * al(std::max<size_t>(1, E) * 4);
     s += al((size_t)r.B * std::max(1, r.n_params) * 8);                      // theta
     s += (size_t)r.B * (sizeof(SetRec) + T * 8 + sizeof(ChunkDev));           // records, items, chunks
@@ -282,13 +283,14 @@ bool Scheduler::launch(Slot& sl, std::vector<ServeRequest*>& batch) {
     const size_t o_sets = take((size_t)n_sets * sizeof(SetRec));
     const size_t o_items = take(items.size() * 4);
     const size_t o_chunks = take(chunks.size() * sizeof(ChunkDev));
-    struct ROff { size_t gates, cones, prog, tc, poff, pidx, pterm, theta; };
+    struct ROff { size_t gates, cones, meas, prog, tc, poff, pidx, pterm, theta; };
     std::vector<ROff> ro(batch.size());
     for (size_t i = 0; i < batch.size(); ++i) {
         const ServeRequest& r = *batch[i];
         const Plan& P = *r.plan;
         ro[i].gates = take(std::max<size_t>(1, r.gates.size()) * sizeof(tlq_gate));
         ro[i].cones = take(P.cones.size() * sizeof(ConeDev));
+        ro[i].meas = take(P.meas.size() * sizeof(MeasDev));
         ro[i].prog = take(P.prog.size() * 4);
         ro[i].tc = take(r.term_coeff.size() * 8);
         ro[i].poff = take(P.pmap_off.size() * 4);
@@ -307,7 +309,7 @@ bool Scheduler::launch(Slot& sl, std::vector<ServeRequest*>& batch) {
     size_t gt_total = 0, e_total = 0, g_total = 0;
     for (ServeRequest* r : batch) {
         gt_total += (size_t)r->B * r->gates.size();
-        e_total += (size_t)r->B * r->plan->cones.size();
+        e_total += (size_t)r->B * r->plan->term_coeff.size();
         if (r->grad) g_total += (size_t)r->B * r->plan->n_slots;
     }
     const size_t o_gt = take(std::max<size_t>(1, gt_total) * r2);
@@ -346,6 +348,7 @@ bool Scheduler::launch(Slot& sl, std::vector<ServeRequest*>& batch) {
         const Plan& P = *r.plan;
         std::memcpy(H + ro[i].gates, r.gates.data(), r.gates.size() * sizeof(tlq_gate));
         std::memcpy(H + ro[i].cones, P.cones.data(), P.cones.size() * sizeof(ConeDev));
+        std::memcpy(H + ro[i].meas, P.meas.data(), P.meas.size() * sizeof(MeasDev));
         std::memcpy(H + ro[i].prog, P.prog.data(), P.prog.size() * 4);
         std::memcpy(H + ro[i].tc, r.term_coeff.data(), r.term_coeff.size() * 8);
         std::memcpy(H + ro[i].poff, P.pmap_off.data(), P.pmap_off.size() * 4);
@@ -355,6 +358,7 @@ bool Scheduler::launch(Slot& sl, std::vector<ServeRequest*>& batch) {
         for (int b = 0; b < r.B; ++b, ++gs) {
             SetRec& R = sets[gs];
             R.cones = (const ConeDev*)(D + ro[i].cones);
+            R.meas = (const MeasDev*)(D + ro[i].meas);
             R.prog = (const int32_t*)(D + ro[i].prog);
             R.gates = (const tlq_gate*)(D + ro[i].gates);
             R.theta = (const double*)(D + ro[i].theta) + (size_t)b * r.n_params;
@@ -369,10 +373,10 @@ bool Scheduler::launch(Slot& sl, std::vector<ServeRequest*>& batch) {
             R.g_off = (int64_t)g;
             R.n_gates = (int32_t)r.gates.size();
             R.n_params = r.n_params;
-            R.n_terms = (int32_t)P.cones.size();
+            R.n_terms = (int32_t)P.term_coeff.size();
             R.n_slots = P.n_slots;
             gt += r.gates.size();
-            e += P.cones.size();
+            e += P.term_coeff.size();
             if (r.grad) g += P.n_slots;
         }
     }
