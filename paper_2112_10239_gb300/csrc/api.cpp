@@ -35,6 +35,7 @@ PlanEntry::~PlanEntry() {
     cudaFree(d_gates);
     cudaFree(d_dlayers);
     cudaFree(d_dclasses);
+    cudaFree(d_dpcd);
     cudaFree(d_ddists);
     cudaFree(d_dzterms);
     cudaFree(d_dtab_gate);
@@ -87,6 +88,7 @@ tlq_status get_plan(Context* ctx, Circuit* c, Ham* h, std::shared_ptr<PlanEntry>
             const DensePlan& D = *plan->dense;
             TLQ_TRY(upload(D.layers, &pe->d_dlayers, &bytes));
             TLQ_TRY(upload(D.classes, &pe->d_dclasses, &bytes));
+            TLQ_TRY(upload(D.pcd, &pe->d_dpcd, &bytes));
             TLQ_TRY(upload(D.dists, &pe->d_ddists, &bytes));
             TLQ_TRY(upload(D.zterms, &pe->d_dzterms, &bytes));
             TLQ_TRY(upload(D.tab_gate, &pe->d_dtab_gate, &bytes));
@@ -128,7 +130,7 @@ tlq_status ensure_worklist(Context* ctx, PlanEntry& pe, const Circuit& c, int B,
         int tt = std::min(kCtaThreads, 1 << (W - 4));
         int tb = team_bytes_host(W, tt, fp64, grad, true);
         int nteams = std::min(kCtaThreads / tt, smax / tb);
-        bool global = (W > kMaxSmemConeW) || nteams < 1 || (tt == kCtaThreads && (1 << (W - 4)) != tt);
+        bool global = (W > kMaxSmemConeW) || nteams < 1;
         if (global) {
             tt = kCtaThreads;
             tb = team_bytes_host(W, tt, fp64, grad, false);
@@ -218,6 +220,7 @@ static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const
     L.n_passes = (int32_t)D.passes.size();
     L.layers = pe.d_dlayers;
     L.classes = pe.d_dclasses;
+    L.pcd = pe.d_dpcd;
     L.dists = pe.d_ddists;
     L.energy_class_off = D.energy_class_off;
     L.energy_nclass = D.energy_nclass;

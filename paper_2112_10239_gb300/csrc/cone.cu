@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) cone_kernel(ConeArgs A) {
         const int tt = ch.tt;
         const int team = threadIdx.x / tt;
         if (ch.W < kMinConeW || ch.W > kMaxConeW || tt < 16 || tt > kCtaThreads ||
-            (!GLOBAL && (1 << (ch.W - 4)) != tt)) {
+            (!GLOBAL && ((1 << (ch.W - 4)) < kCtaThreads ? (1 << (ch.W - 4)) : kCtaThreads) != tt)) {
             if (threadIdx.x == 0) atomicOr(A.err, 1);
             continue;
         }

@@ -36,6 +36,7 @@ struct PassArgs {
     DensePassDev pass;
     const DenseLayerDev* layers;
     const DenseClassDev* classes;
+    const DensePassClassDev* pcd;
     const int32_t* dists;
     int32_t energy_class_off, energy_nclass;
     const DenseZTermDev* zterms;
@@ -101,7 +102,8 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
     float2* s_tab = bufs + 2 * padded_amps(kDenseTileBits);                          // kMaxTab
     int32_t* s_dist = reinterpret_cast<int32_t*>(s_tab + kMaxTab);                   // kMaxDistWords
     DenseClassDev* s_cls = reinterpret_cast<DenseClassDev*>(s_dist + kMaxDistWords); // kMaxLayerClasses
-    float* s_red = reinterpret_cast<float*>(s_cls + kMaxLayerClasses);               // 16
+    DensePassClassDev* s_pcd = reinterpret_cast<DensePassClassDev*>(s_cls + kMaxLayerClasses);
+    float* s_red = reinterpret_cast<float*>(s_pcd + kMaxLayerClasses);               // 16
     const DensePassDev& P = A.pass;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -120,6 +122,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
     const int nec = P.measure ? A.energy_nclass : 0;
     if (tid < ncl) s_cls[tid] = A.classes[cl_first + tid];
     if (tid < nec) s_cls[ncl + tid] = A.classes[A.energy_class_off + tid];
+    if (tid < ncl + nec && P.pcd_off >= 0) s_pcd[tid] = A.pcd[P.pcd_off + tid];
     __syncthreads();
     {
         int woff = 0, toff = 0;
@@ -130,25 +133,6 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
                 for (int e = tid; e <= C.nterms; e += kThreads) s_tab[toff + e] = A.ptab[C.tab_off + e];
             woff += 2 * C.ndist;
             toff += C.kind == 0 ? C.nterms + 1 : 0;
-        }
-    }
-    // rotation parameters of every sub-pass (the same for all tiles)
-    int kd_all[4][4];
-    float c_all[4][4], s_all[4][4];
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            kd_all[g][k] = -1;
-            c_all[g][k] = 1.f;
-            s_all[g][k] = 0.f;
-            if (g < P.ngroups && ((P.group_mask[g] >> k) & 1)) {
-                const int gate = P.gate[P.group_s[g] + k];
-                kd_all[g][k] = A.gates[gate].kind;
-                const float2 v = A.GT[gate];
-                c_all[g][k] = v.x;
-                s_all[g][k] = v.y;
-            }
         }
     }
     __syncthreads();
@@ -162,57 +146,98 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
         __syncthreads();     // ... and everyone else's
         const uint32_t next = t_id + gridDim.x;
         if (next < ntiles) issue_tile(P, next, A.state, bufs + (b ^ 1) * padded_amps(kDenseTileBits), tid);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            if (g >= P.ngroups) break;
+        for (int g = 0; g < P.ngroups; ++g) {
             const int s = P.group_s[g];
+            const unsigned m = P.group_mask[g];
+            int kd[4];
+            float c[4], sn[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                kd[k] = -1;
+                c[k] = 1.f;
+                sn[k] = 0.f;
+                if ((m >> k) & 1) {
+                    const int gate = P.gate[s + k];
+                    kd[k] = A.gates[gate].kind;
+                    const float2 v = A.GT[gate];
+                    c[k] = v.x;
+                    sn[k] = v.y;
+                }
+            }
             const int lowmask = (1 << s) - 1;
             const int stride = pass_stride(s);
             const int base = (tid & lowmask) | ((tid >> s) << (s + 4));
             float2* p = tile + pad16(base);
             float2 v[16];
             load16(v, p, stride);
-            if (kd_all[g][0] >= 0) apply_rot<0>(v, kd_all[g][0], c_all[g][0], s_all[g][0]);
-            if (kd_all[g][1] >= 0) apply_rot<1>(v, kd_all[g][1], c_all[g][1], s_all[g][1]);
-            if (kd_all[g][2] >= 0) apply_rot<2>(v, kd_all[g][2], c_all[g][2], s_all[g][2]);
-            if (kd_all[g][3] >= 0) apply_rot<3>(v, kd_all[g][3], c_all[g][3], s_all[g][3]);
+            if (kd[0] >= 0) apply_rot<0>(v, kd[0], c[0], sn[0]);
+            if (kd[1] >= 0) apply_rot<1>(v, kd[1], c[1], sn[1]);
+            if (kd[2] >= 0) apply_rot<2>(v, kd[2], c[2], sn[2]);
+            if (kd[3] >= 0) apply_rot<3>(v, kd[3], c[3], sn[3]);
             if (g < P.ngroups - 1) {
                 store16(v, p, stride);
                 __syncthreads();
                 continue;
             }
-            // last register pass: diagonal, energy, and the write-back to HBM
+            // last register pass: diagonal phase and energy from split class counts, then the
+            // write-back to HBM straight from registers
+            if (diag || P.measure) {
+                const uint32_t xb = tile_x(P, t_id, (uint32_t)base);   // register bits are zero in base
+                float2 ph[16];
+                float ez[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const uint32_t x = tile_x(P, t_id, (uint32_t)(base | (j << s)));
-                if (diag || P.measure) {
-                    int woff = 0, toff = 0;
-                    float2 ph = make_float2(1.f, 0.f);
-                    for (int ci = 0; ci < ncl; ++ci) {
-                        const DenseClassDev& C = s_cls[ci];
-                        const int cnt = class_count(C, s_dist + woff, x);
-                        if (C.kind == 0) ph = cmul(ph, s_tab[toff + cnt]);
-                        else if (cnt & 1) { ph.x = -ph.x; ph.y = -ph.y; }
-                        woff += 2 * C.ndist;
-                        toff += C.kind == 0 ? C.nterms + 1 : 0;
+                for (int j = 0; j < 16; ++j) {
+                    ph[j] = make_float2(1.f, 0.f);
+                    ez[j] = 0.f;
+                }
+                int woff = 0, toff = 0;
+                for (int ci = 0; ci < ncl + nec; ++ci) {
+                    const DenseClassDev& C = s_cls[ci];
+                    const DensePassClassDev& pc = s_pcd[ci];
+                    const int cnt0 = class_count(C, s_dist + woff, xb);
+                    int Ak[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int inter = __popc(xb & pc.N[k]);
+                        Ak[k] = C.kind == 1 ? inter : __popc(pc.N[k]) - 2 * inter + (int)((pc.single >> k) & 1u);
                     }
-                    if (diag) v[j] = cmul(v[j], ph);
+                    const uint32_t cw0 = pc.C[0], cw1 = pc.C[1], cw2 = pc.C[2], cw3 = pc.C[3];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const uint32_t cw = (j >> 2) == 0 ? cw0 : (j >> 2) == 1 ? cw1 : (j >> 2) == 2 ? cw2 : cw3;
+                        int cnt = cnt0 + (int)((cw >> (8 * (j & 3))) & 255u);
+                        if (j & 1) cnt += Ak[0];
+                        if (j & 2) cnt += Ak[1];
+                        if (j & 4) cnt += Ak[2];
+                        if (j & 8) cnt += Ak[3];
+                        if (ci < ncl) {
+                            if (C.kind == 0) ph[j] = cmul(ph[j], s_tab[toff + cnt]);
+                            else if (cnt & 1) { ph[j].x = -ph[j].x; ph[j].y = -ph[j].y; }
+                        } else {
+                            ez[j] += (float)C.coeff * (float)(C.nterms - 2 * cnt);
+                        }
+                    }
+                    woff += 2 * C.ndist;
+                    toff += (ci < ncl && C.kind == 0) ? C.nterms + 1 : 0;
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (diag) v[j] = cmul(v[j], ph[j]);
                     if (P.measure) {
-                        float ez = 0.f;
-                        for (int ci = ncl; ci < ncl + nec; ++ci) {
-                            const DenseClassDev& C = s_cls[ci];
-                            const int cnt = class_count(C, s_dist + woff, x);
-                            ez += (float)C.coeff * (float)(C.nterms - 2 * cnt);
-                            woff += 2 * C.ndist;
+                        if (A.n_zterms > 0) {
+                            const uint32_t x = tile_x(P, t_id, (uint32_t)(base | (j << s)));
+                            for (int k = 0; k < A.n_zterms; ++k) {
+                                const DenseZTermDev Z = A.zterms[k];
+                                ez[j] += (__popc(x & Z.mask) & 1) ? -(float)Z.coeff : (float)Z.coeff;
+                            }
                         }
-                        for (int k = 0; k < A.n_zterms; ++k) {
-                            const DenseZTermDev Z = A.zterms[k];
-                            ez += (__popc(x & Z.mask) & 1) ? -(float)Z.coeff : (float)Z.coeff;
-                        }
-                        eacc += (v[j].x * v[j].x + v[j].y * v[j].y) * ez;
+                        eacc += (v[j].x * v[j].x + v[j].y * v[j].y) * ez[j];
                     }
                 }
-                if (P.store) A.state[x] = v[j];
+            }
+            if (P.store) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) A.state[tile_x(P, t_id, (uint32_t)(base | (j << s)))] = v[j];
             }
         }
         __syncthreads();   // the buffer is free for the copy issued in the next iteration
@@ -232,7 +257,8 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
 
 size_t dense_pass_smem() {
     return 2 * (size_t)padded_amps(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
-           kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * sizeof(DenseClassDev) + 16 * sizeof(float);
+           kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * (sizeof(DenseClassDev) + sizeof(DensePassClassDev)) +
+           16 * sizeof(float);
 }
 
 // ---- gate tables and phase tables ---------------------------------------------------------
@@ -415,6 +441,7 @@ int launch_dense(DenseLaunch& L, void* stream) {
             PassArgs A;
             A.layers = L.layers;
             A.classes = L.classes;
+            A.pcd = L.pcd;
             A.dists = L.dists;
             A.energy_class_off = L.energy_class_off;
             A.energy_nclass = L.energy_nclass;

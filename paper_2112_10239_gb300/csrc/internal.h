@@ -63,7 +63,7 @@ constexpr int kRecWords = 6;
 constexpr int kLayerHeader = 4;
 constexpr int kMinConeW = 8;       // narrower cones are padded to this width
 constexpr int kMaxGroupTerms = 8;  // terms measured on one shared window
-constexpr int kMaxSmemConeW = 13;  // widest cone kept in shared memory (FP32)
+constexpr int kMaxSmemConeW = 14;  // widest cone kept in shared memory (when it fits: FP32 forward at 14)
 constexpr int kMaxConeW = 20;      // widest cone on the cone path (global-memory tier)
 constexpr int kCtaThreads = 512;
 constexpr int kMaxPassSlots = 4 + 2 * 20;  // gradient values per adjoint pass: 4 rotations + RZ/pair per qubit
@@ -91,6 +91,20 @@ struct DensePassDev {
     int32_t group_s[4];       // local start bit of each sub-pass
     uint32_t group_mask[4];   // bits (relative to group_s) carrying a rotation
     int32_t gate[16];         // rotation gate per local bit (-1 none)
+    int32_t pcd_off;          // first DensePassClassDev of this pass's staged classes (-1 none)
+    int32_t pad[3];
+};
+
+// Per pass and class, the split of the class's count over the last register pass: with x_b
+// the thread's base index (the 4 register bits zero) and j the register bits,
+//   count(x_b | j) = count(x_b) + sum_k j_k A_k + C[j],
+// A_k = popc(N_k) - 2 popc(x_b & N_k) + single_k (XOR counts) or popc(x_b & N_k) (AND counts),
+// N_k = partners outside the register bits of register bit k, C[j] = count of the pairs inside.
+struct DensePassClassDev {
+    uint32_t N[4];
+    uint32_t single;          // bit k: register bit k carries a single-qubit term
+    uint32_t C[4];            // C[j] in byte j % 4 of word j / 4
+    uint32_t pad[3];
 };
 
 // A class of diagonal terms counted by popcounts over distance masks:
@@ -125,6 +139,7 @@ struct DensePlan {
     std::vector<int32_t> tab_gate;          // per phase-table entry: gate providing the angle
     std::vector<int32_t> tab_mult;          // per entry: N - 2c
     std::vector<DenseXTermDev> all_terms;   // every term (plain per-gate path measures them one by one)
+    std::vector<DensePassClassDev> pcd;     // per pass: split counts of its staged classes
     int max_classes_per_layer = 0;
     int max_dists = 0;
     bool fits_fused = true;                 // staged class data fits the pass kernel's shared memory
@@ -292,6 +307,7 @@ struct DenseLaunch {
     int32_t n_passes = 0;
     const DenseLayerDev* layers = nullptr;
     const DenseClassDev* classes = nullptr;
+    const DensePassClassDev* pcd = nullptr;
     const int32_t* dists = nullptr;
     int32_t energy_class_off = 0, energy_nclass = 0;
     const DenseZTermDev* zterms = nullptr;

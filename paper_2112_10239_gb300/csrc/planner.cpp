@@ -583,6 +583,55 @@ std::shared_ptr<DensePlan> make_dense_plan(const Circuit& c, const Ham& h, std::
         }
         D->passes.back().measure = 1;
     }
+    // split counts of the classes each pass evaluates in its last register pass
+    for (DensePassDev& pass : D->passes) {
+        pass.pcd_off = -1;
+        if (pass.diag_layer < 0 && !pass.measure) continue;
+        const int s = pass.group_s[pass.ngroups - 1];
+        int gbit[4];
+        uint32_t gmask = 0;
+        for (int k = 0; k < 4; ++k) {
+            const int local = s + k;
+            gbit[k] = pass.strided ? (local < 4 ? local : pass.a + local - 4) : local;
+            gmask |= 1u << gbit[k];
+        }
+        auto kof = [&](int q) { for (int k = 0; k < 4; ++k) if (gbit[k] == q) return k; return -1; };
+        pass.pcd_off = (int32_t)D->pcd.size();
+        auto add = [&](const DenseClassDev& cl) {
+            DensePassClassDev pc{};
+            uint32_t cnt[16] = {0};
+            for (int k = 0; k < cl.ndist; ++k) {
+                const int d = D->dists[2 * (cl.dist_off + k)];
+                const uint32_t M = (uint32_t)D->dists[2 * (cl.dist_off + k) + 1];
+                for (int u = 0; u < 32; ++u) {
+                    if (!((M >> u) & 1)) continue;
+                    const int v = u + d;
+                    const int ku = kof(u), kv = kof(v);
+                    if (ku >= 0 && kv >= 0) {
+                        for (int j = 0; j < 16; ++j) {
+                            const int bu = (j >> ku) & 1, bv = (j >> kv) & 1;
+                            cnt[j] += cl.kind == 1 ? (bu & bv) : (bu ^ bv);
+                        }
+                    } else if (ku >= 0) {
+                        pc.N[ku] |= 1u << v;
+                    } else if (kv >= 0) {
+                        pc.N[kv] |= 1u << u;
+                    }
+                }
+            }
+            for (int k = 0; k < 4; ++k)
+                if ((cl.single >> gbit[k]) & 1) pc.single |= 1u << k;
+            for (int j = 0; j < 16; ++j) pc.C[j >> 2] |= cnt[j] << (8 * (j & 3));
+            D->pcd.push_back(pc);
+        };
+        if (pass.diag_layer >= 0) {
+            const DenseLayerDev& ld = D->layers[pass.diag_layer];
+            for (int k = 0; k < ld.nclass; ++k) add(D->classes[ld.class_off + k]);
+        }
+        if (pass.measure)
+            for (int k = 0; k < D->energy_nclass; ++k) add(D->classes[D->energy_class_off + k]);
+        (void)gmask;
+    }
     // the pass kernel stages one layer's classes plus the energy classes in shared memory
     int e_words = 0;
     for (int k = 0; k < D->energy_nclass; ++k) e_words += 2 * D->classes[D->energy_class_off + k].ndist;

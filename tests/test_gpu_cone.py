@@ -149,3 +149,19 @@ def test_repeated_calls_identical(tlq):
     a = _run(tlq, prob)
     b = _run(tlq, prob)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_width14_forward_in_shared_memory(tlq):
+    # L=7 with ZZ terms only, energies only: every window is 14 wide and runs in shared
+    # memory with two amplitude blocks per thread.
+    from paper_2112_10239_gb300 import binding as B
+    p = W.tfim_problem(22, 7, 3, seed=8, h_range=(0.5, 1.5))
+    prob = W.Problem(p.n, p.gates, p.n_params, [t for t in p.terms if t[2] == "ZZ"], p.theta)
+    c, h = tlq.problem(prob)
+    _, _, _, weff, _, _ = B.tlq_plan_cone_stats(tlq.h, c.h, h.h, len(prob.terms))
+    c.close()
+    h.close()
+    assert max(weff) == 14
+    E, _ = _run(tlq, prob, grad=False)
+    Er, _ = _oracle(prob, prob.theta, grad=False)
+    check_energy(E, Er)
