@@ -36,6 +36,7 @@ PlanEntry::~PlanEntry() {
     cudaFree(d_dlayers);
     cudaFree(d_dclasses);
     cudaFree(d_dpcd);
+    cudaFree(d_dstage);
     cudaFree(d_ddists);
     cudaFree(d_dzterms);
     cudaFree(d_dtab_gate);
@@ -89,6 +90,7 @@ tlq_status get_plan(Context* ctx, Circuit* c, Ham* h, std::shared_ptr<PlanEntry>
             TLQ_TRY(upload(D.layers, &pe->d_dlayers, &bytes));
             TLQ_TRY(upload(D.classes, &pe->d_dclasses, &bytes));
             TLQ_TRY(upload(D.pcd, &pe->d_dpcd, &bytes));
+            TLQ_TRY(upload(D.stage, &pe->d_dstage, &bytes));
             TLQ_TRY(upload(D.dists, &pe->d_ddists, &bytes));
             TLQ_TRY(upload(D.zterms, &pe->d_dzterms, &bytes));
             TLQ_TRY(upload(D.tab_gate, &pe->d_dtab_gate, &bytes));
@@ -221,6 +223,7 @@ static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const
     L.layers = pe.d_dlayers;
     L.classes = pe.d_dclasses;
     L.pcd = pe.d_dpcd;
+    L.stage = pe.d_dstage;
     L.dists = pe.d_ddists;
     L.energy_class_off = D.energy_class_off;
     L.energy_nclass = D.energy_nclass;

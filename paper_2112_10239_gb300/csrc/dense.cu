@@ -37,6 +37,7 @@ struct PassArgs {
     const DenseLayerDev* layers;
     const DenseClassDev* classes;
     const DensePassClassDev* pcd;
+    const int32_t* stage;
     const int32_t* dists;
     int32_t energy_class_off, energy_nclass;
     const DenseZTermDev* zterms;
@@ -103,7 +104,9 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
     int32_t* s_dist = reinterpret_cast<int32_t*>(s_tab + kMaxTab);                   // kMaxDistWords
     DenseClassDev* s_cls = reinterpret_cast<DenseClassDev*>(s_dist + kMaxDistWords); // kMaxLayerClasses
     DensePassClassDev* s_pcd = reinterpret_cast<DensePassClassDev*>(s_cls + kMaxLayerClasses);
-    float* s_red = reinterpret_cast<float*>(s_pcd + kMaxLayerClasses);               // 16
+    int32_t* s_woff = reinterpret_cast<int32_t*>(s_pcd + kMaxLayerClasses);        // kMaxLayerClasses
+    int32_t* s_toff = s_woff + kMaxLayerClasses;                                    // kMaxLayerClasses
+    float* s_red = reinterpret_cast<float*>(s_toff + kMaxLayerClasses);              // 16
     const DensePassDev& P = A.pass;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -111,29 +114,28 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
 
     if (blockIdx.x < ntiles) issue_tile(P, blockIdx.x, A.state, bufs, tid);
 
-    // stage the diagonal classes of this pass's layer and the energy classes (once per CTA)
-    const bool diag = P.diag_layer >= 0;
-    int ncl = 0, cl_first = 0;
-    if (diag) {
-        const DenseLayerDev L = A.layers[P.diag_layer];
-        ncl = L.nclass;
-        cl_first = L.class_off;
-    }
-    const int nec = P.measure ? A.energy_nclass : 0;
-    if (tid < ncl) s_cls[tid] = A.classes[cl_first + tid];
-    if (tid < nec) s_cls[ncl + tid] = A.classes[A.energy_class_off + tid];
-    if (tid < ncl + nec && P.pcd_off >= 0) s_pcd[tid] = A.pcd[P.pcd_off + tid];
+    // stage this pass's classes (diagonal phases of the layers it completes, and the energy
+    // classes in the final pass) with their distance words, phase tables and split counts
+    const int nst = P.nstage;
+    if (tid < nst) s_cls[tid] = A.classes[A.stage[P.stage_off + tid]];
     __syncthreads();
-    {
+    if (tid == 0) {
         int woff = 0, toff = 0;
-        for (int c = 0; c < ncl + nec; ++c) {
-            const DenseClassDev& C = s_cls[c];
-            for (int w = tid; w < 2 * C.ndist; w += kThreads) s_dist[woff + w] = A.dists[2 * C.dist_off + w];
-            if (C.kind == 0)
-                for (int e = tid; e <= C.nterms; e += kThreads) s_tab[toff + e] = A.ptab[C.tab_off + e];
-            woff += 2 * C.ndist;
-            toff += C.kind == 0 ? C.nterms + 1 : 0;
+        for (int c = 0; c < nst; ++c) {
+            s_woff[c] = woff;
+            s_toff[c] = toff;
+            woff += 2 * s_cls[c].ndist;
+            toff += s_cls[c].kind == 0 ? s_cls[c].nterms + 1 : 0;
         }
+    }
+    for (int g = 0; g < P.ngroups; ++g)
+        for (int k = tid; k < P.group_ncls[g]; k += kThreads) s_pcd[P.group_cls[g] + k] = A.pcd[P.group_pcd[g] + k];
+    __syncthreads();
+    for (int c = 0; c < nst; ++c) {
+        const DenseClassDev& C = s_cls[c];
+        for (int w = tid; w < 2 * C.ndist; w += kThreads) s_dist[s_woff[c] + w] = A.dists[2 * C.dist_off + w];
+        if (C.kind == 0)
+            for (int e = tid; e <= C.nterms; e += kThreads) s_tab[s_toff[c] + e] = A.ptab[C.tab_off + e];
     }
     __syncthreads();
 
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
                 c[k] = 1.f;
                 sn[k] = 0.f;
                 if ((m >> k) & 1) {
-                    const int gate = P.gate[s + k];
+                    const int gate = P.gate[g][k];
                     kd[k] = A.gates[gate].kind;
                     const float2 v = A.GT[gate];
                     c[k] = v.x;
@@ -174,14 +176,10 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
             if (kd[1] >= 0) apply_rot<1>(v, kd[1], c[1], sn[1]);
             if (kd[2] >= 0) apply_rot<2>(v, kd[2], c[2], sn[2]);
             if (kd[3] >= 0) apply_rot<3>(v, kd[3], c[3], sn[3]);
-            if (g < P.ngroups - 1) {
-                store16(v, p, stride);
-                __syncthreads();
-                continue;
-            }
-            // last register pass: diagonal phase and energy from split class counts, then the
-            // write-back to HBM straight from registers
-            if (diag || P.measure) {
+            // after this group: diagonal phases of a completed layer and/or the energy, from split
+            // class counts; the last group then writes straight to HBM from registers
+            const int ncls = P.group_ncls[g];
+            if (ncls > 0 || g == P.measure_group) {
                 const uint32_t xb = tile_x(P, t_id, (uint32_t)base);   // register bits are zero in base
                 float2 ph[16];
                 float ez[16];
@@ -190,10 +188,13 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
                     ph[j] = make_float2(1.f, 0.f);
                     ez[j] = 0.f;
                 }
-                int woff = 0, toff = 0;
-                for (int ci = 0; ci < ncl + nec; ++ci) {
+                bool any_phase = false, any_energy = g == P.measure_group;
+                for (int ci = P.group_cls[g]; ci < P.group_cls[g] + ncls; ++ci) {
                     const DenseClassDev& C = s_cls[ci];
                     const DensePassClassDev& pc = s_pcd[ci];
+                    const int woff = s_woff[ci], toff = s_toff[ci];
+                    any_phase |= C.kind != 2;
+                    any_energy |= C.kind == 2;
                     const int cnt0 = class_count(C, s_dist + woff, xb);
                     int Ak[4];
 #pragma unroll
@@ -210,20 +211,15 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
                         if (j & 2) cnt += Ak[1];
                         if (j & 4) cnt += Ak[2];
                         if (j & 8) cnt += Ak[3];
-                        if (ci < ncl) {
-                            if (C.kind == 0) ph[j] = cmul(ph[j], s_tab[toff + cnt]);
-                            else if (cnt & 1) { ph[j].x = -ph[j].x; ph[j].y = -ph[j].y; }
-                        } else {
-                            ez[j] += (float)C.coeff * (float)(C.nterms - 2 * cnt);
-                        }
+                        if (C.kind == 0) ph[j] = cmul(ph[j], s_tab[toff + cnt]);
+                        else if (C.kind == 1) { if (cnt & 1) { ph[j].x = -ph[j].x; ph[j].y = -ph[j].y; } }
+                        else ez[j] += (float)C.coeff * (float)(C.nterms - 2 * cnt);
                     }
-                    woff += 2 * C.ndist;
-                    toff += (ci < ncl && C.kind == 0) ? C.nterms + 1 : 0;
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    if (diag) v[j] = cmul(v[j], ph[j]);
-                    if (P.measure) {
+                    if (any_phase) v[j] = cmul(v[j], ph[j]);
+                    if (any_energy) {
                         if (A.n_zterms > 0) {
                             const uint32_t x = tile_x(P, t_id, (uint32_t)(base | (j << s)));
                             for (int k = 0; k < A.n_zterms; ++k) {
@@ -235,14 +231,17 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
                     }
                 }
             }
-            if (P.store) {
+            if (g < P.ngroups - 1) {
+                store16(v, p, stride);
+                __syncthreads();
+            } else if (P.store) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) A.state[tile_x(P, t_id, (uint32_t)(base | (j << s)))] = v[j];
             }
         }
         __syncthreads();   // the buffer is free for the copy issued in the next iteration
     }
-    if (P.measure) {
+    if (P.measure_group >= 0) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, off);
         if (lane == 0) s_red[warp] = eacc;
@@ -258,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
 size_t dense_pass_smem() {
     return 2 * (size_t)padded_amps(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
            kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * (sizeof(DenseClassDev) + sizeof(DensePassClassDev)) +
-           16 * sizeof(float);
+           2 * kMaxLayerClasses * sizeof(int32_t) + 16 * sizeof(float);
 }
 
 // ---- gate tables and phase tables ---------------------------------------------------------
@@ -442,6 +441,7 @@ int launch_dense(DenseLaunch& L, void* stream) {
             A.layers = L.layers;
             A.classes = L.classes;
             A.pcd = L.pcd;
+            A.stage = L.stage;
             A.dists = L.dists;
             A.energy_class_off = L.energy_class_off;
             A.energy_nclass = L.energy_nclass;
@@ -460,7 +460,7 @@ int launch_dense(DenseLaunch& L, void* stream) {
                 A.pass = L.host_passes[p];
                 dense_pass_kernel<<<grid, kThreads, smem, st>>>(A);
                 ++launches;
-                if (A.pass.measure) measured = true;
+                if (A.pass.measure_group >= 0) measured = true;
             }
             if (measured) {
                 reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, grid, 1.0, eout, 1);

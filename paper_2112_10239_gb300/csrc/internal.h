@@ -81,18 +81,26 @@ constexpr int kDenseMaxLayerClasses = 48;  // per layer (+ energy classes)
 constexpr int kDenseMaxDistWords = 512;
 constexpr int kDenseMaxTab = 768;
 
+constexpr int kDenseMaxGroups = 8;
+
+// One streaming pass over all tiles. Its register passes ("groups") may span a layer
+// boundary: the group that completes a layer's rotations is followed by that layer's
+// diagonal, and later groups already apply the next layer's rotations on this tile's qubits.
 struct DensePassDev {
-    int32_t strided;          // 0: low tile, 1: strided tile
-    int32_t a;                // strided: global qubit of local bit 4
-    int32_t ngroups;          // register sub-passes
-    int32_t diag_layer;       // -1, or the layer whose diagonal follows this pass's rotations
-    int32_t measure;          // accumulate the Z-type energy after the rotations (and diagonal)
-    int32_t store;            // write the tile back (0: read-only measurement pass)
-    int32_t group_s[4];       // local start bit of each sub-pass
-    uint32_t group_mask[4];   // bits (relative to group_s) carrying a rotation
-    int32_t gate[16];         // rotation gate per local bit (-1 none)
-    int32_t pcd_off;          // first DensePassClassDev of this pass's staged classes (-1 none)
-    int32_t pad[3];
+    int32_t strided;                      // 0: low tile, 1: strided tile
+    int32_t a;                            // strided: global qubit of local bit 4
+    int32_t ngroups;
+    int32_t store;                        // write the tile back (0: read-only measurement pass)
+    int32_t nstage;                       // classes staged in shared memory for this pass
+    int32_t stage_off;                    // their indices in DensePlan::stage
+    int32_t measure_group;                // group after which the energy is accumulated (-1 none)
+    int32_t pad;
+    int32_t group_s[kDenseMaxGroups];     // local start bit of each register pass
+    uint32_t group_mask[kDenseMaxGroups]; // register bits carrying a rotation
+    int32_t group_cls[kDenseMaxGroups];   // first staged class evaluated after the group's rotations
+    int32_t group_ncls[kDenseMaxGroups];  // how many (diagonal phases and/or energy classes)
+    int32_t group_pcd[kDenseMaxGroups];   // first DensePassClassDev of those classes
+    int32_t gate[kDenseMaxGroups][4];     // rotation gate per register bit (-1 none)
 };
 
 // Per pass and class, the split of the class's count over the last register pass: with x_b
@@ -139,7 +147,8 @@ struct DensePlan {
     std::vector<int32_t> tab_gate;          // per phase-table entry: gate providing the angle
     std::vector<int32_t> tab_mult;          // per entry: N - 2c
     std::vector<DenseXTermDev> all_terms;   // every term (plain per-gate path measures them one by one)
-    std::vector<DensePassClassDev> pcd;     // per pass: split counts of its staged classes
+    std::vector<DensePassClassDev> pcd;     // per (pass, group, class): split counts
+    std::vector<int32_t> stage;             // per pass: classes staged in shared memory
     int max_classes_per_layer = 0;
     int max_dists = 0;
     bool fits_fused = true;                 // staged class data fits the pass kernel's shared memory
@@ -308,6 +317,7 @@ struct DenseLaunch {
     const DenseLayerDev* layers = nullptr;
     const DenseClassDev* classes = nullptr;
     const DensePassClassDev* pcd = nullptr;
+    const int32_t* stage = nullptr;
     const int32_t* dists = nullptr;
     int32_t energy_class_off = 0, energy_nclass = 0;
     const DenseZTermDev* zterms = nullptr;

@@ -514,138 +514,185 @@ std::shared_ptr<DensePlan> make_dense_plan(const Circuit& c, const Ham& h, std::
         for (auto& cb : kv.second) emit_class(*D, cb);
     D->energy_nclass = (int32_t)D->classes.size() - D->energy_class_off;
 
-    // pass schedule: per layer a low pass (qubits 0..12) and strided passes of 9 qubits
+    // Pass schedule. Tile patterns: the low tile (qubits 0..12) and strided tiles covering 9
+    // higher qubits each. Greedy: each pass takes the pattern covering the most pending
+    // rotations of the current layer; when a pass completes a layer it applies the layer's
+    // diagonal right there and continues with the next layer's rotations on the same tile.
     std::vector<int> chunk_a;
     for (int a = kDenseTileBits; a < n_eff; a += kDenseStridedBits)
         chunk_a.push_back(std::min(a, n_eff - kDenseStridedBits));
-    auto plan_groups = [](DensePassDev& p, uint32_t bits) {
-        p.ngroups = 0;
-        while (bits) {
-            const int b = __builtin_ctz(bits);
-            const int s = b < 4 ? 0 : std::min(b, kDenseTileBits - 4);
-            p.group_s[p.ngroups] = s;
-            p.group_mask[p.ngroups] = (bits >> s) & 15u;
-            bits &= ~(15u << s);
-            ++p.ngroups;
-        }
-    };
     auto blank = [](int strided, int a) {
         DensePassDev p{};
         p.strided = strided;
         p.a = a;
-        p.diag_layer = -1;
         p.store = 1;
-        for (int i = 0; i < 16; ++i) p.gate[i] = -1;
+        p.measure_group = -1;
+        for (int g = 0; g < kDenseMaxGroups; ++g) {
+            p.group_cls[g] = -1;
+            p.group_pcd[g] = -1;
+            for (int k = 0; k < 4; ++k) p.gate[g][k] = -1;
+        }
         return p;
     };
-    for (int l = 0; l < L; ++l) {
-        std::vector<char> done(n_eff, 0);
-        const size_t first = D->passes.size();
-        DensePassDev low = blank(0, 0);
-        uint32_t lowbits = 0;
-        for (int g : c.layers[l].rot) {
-            const int q = c.gates[g].q0;
-            if (q < kDenseTileBits) { low.gate[q] = g; lowbits |= 1u << q; done[q] = 1; }
+    // local bit of global qubit q in a pattern (-1: not in the tile); patterns: -1 low, else chunk
+    auto local_of = [&](int pat, int q) -> int {
+        if (pat < 0) return q < kDenseTileBits ? q : -1;
+        const int a = chunk_a[pat];
+        if (q < 4) return q;
+        return (q >= a && q < a + kDenseStridedBits) ? 4 + q - a : -1;
+    };
+    struct GroupDiag { int pass, group, layer; };     // diagonal (or energy: layer = -1) after a group
+    std::vector<GroupDiag> gdiag;
+    std::vector<int> pend;                            // pending rotation gates of layer l
+    int l = 0;
+    auto load_layer = [&]() {
+        pend.clear();
+        if (l < L) pend = c.layers[l].rot;
+    };
+    load_layer();
+    while (l < L) {
+        // choose the pattern with the most pending rotations
+        int best = -1, bestn = -1;
+        for (int pat = -1; pat < (int)chunk_a.size(); ++pat) {
+            int cnt = 0;
+            for (int g : pend) cnt += local_of(pat, c.gates[g].q0) >= 0;
+            if (cnt > bestn) { bestn = cnt; best = pat; }
         }
-        if (lowbits) { plan_groups(low, lowbits); D->passes.push_back(low); }
-        for (int a : chunk_a) {
-            DensePassDev p = blank(1, a);
+        DensePassDev pass = blank(best >= 0, best >= 0 ? chunk_a[best] : 0);
+        const int pi = (int)D->passes.size();
+        for (;;) {
+            // rotations of layer l on this tile
             uint32_t bits = 0;
-            for (int g : c.layers[l].rot) {
-                const int q = c.gates[g].q0;
-                if (q >= a && q < a + kDenseStridedBits && !done[q]) {
-                    p.gate[4 + q - a] = g;
-                    bits |= 1u << (4 + q - a);
-                    done[q] = 1;
-                }
+            int gate_at[16];
+            for (int k = 0; k < 16; ++k) gate_at[k] = -1;
+            std::vector<int> rest;
+            for (int g : pend) {
+                const int lb = local_of(best, c.gates[g].q0);
+                if (lb >= 0 && !((bits >> lb) & 1)) { bits |= 1u << lb; gate_at[lb] = g; }
+                else rest.push_back(g);
             }
-            if (bits) { plan_groups(p, bits); D->passes.push_back(p); }
-        }
-        if (!c.layers[l].diag.empty()) {
-            if (D->passes.size() == first) {
-                DensePassDev p = blank(0, 0);
-                p.ngroups = 1;
-                p.group_s[0] = kDenseTileBits - 4;
-                p.group_mask[0] = 0;
-                D->passes.push_back(p);
+            int need = 0;
+            for (uint32_t b2 = bits; b2;) {
+                const int b = __builtin_ctz(b2);
+                const int s = b < 4 ? 0 : std::min(b, kDenseTileBits - 4);
+                b2 &= ~(15u << s);
+                ++need;
             }
-            D->passes.back().diag_layer = l;
+            const bool completes = rest.empty();
+            if (pass.ngroups + std::max(need, completes ? 1 : 0) > kDenseMaxGroups) break;
+            while (bits) {
+                const int b = __builtin_ctz(bits);
+                const int s = b < 4 ? 0 : std::min(b, kDenseTileBits - 4);
+                const int gi = pass.ngroups++;
+                pass.group_s[gi] = s;
+                pass.group_mask[gi] = (bits >> s) & 15u;
+                for (int k = 0; k < 4; ++k)
+                    if ((pass.group_mask[gi] >> k) & 1) pass.gate[gi][k] = gate_at[s + k];
+                bits &= ~(15u << s);
+            }
+            pend = rest;
+            if (!completes) break;
+            // layer l done on the whole state: its diagonal follows the last group
+            if (pass.ngroups == 0) {
+                pass.group_s[0] = kDenseTileBits - 4;
+                pass.group_mask[0] = 0;
+                pass.ngroups = 1;
+            }
+            if (!c.layers[l].diag.empty()) gdiag.push_back({pi, pass.ngroups - 1, l});
+            ++l;
+            load_layer();
+            if (l >= L) break;
+            if (pass.ngroups >= kDenseMaxGroups) break;
         }
+        if (pass.ngroups == 0) {   // nothing fit (cannot happen with 8 groups) -- keep the loop finite
+            pass.group_s[0] = kDenseTileBits - 4;
+            pass.group_mask[0] = 0;
+            pass.ngroups = 1;
+        }
+        D->passes.push_back(pass);
     }
-    if (D->energy_nclass > 0 || !D->zterms.empty()) {
+    const bool want_energy = D->energy_nclass > 0 || !D->zterms.empty();
+    if (want_energy) {
         if (D->passes.empty()) {
             DensePassDev p = blank(0, 0);
             p.ngroups = 1;
             p.group_s[0] = kDenseTileBits - 4;
-            p.group_mask[0] = 0;
             p.store = 0;
             D->passes.push_back(p);
         }
-        D->passes.back().measure = 1;
+        gdiag.push_back({(int)D->passes.size() - 1, D->passes.back().ngroups - 1, -1});
+        D->passes.back().measure_group = D->passes.back().ngroups - 1;
     }
-    // split counts of the classes each pass evaluates in its last register pass
-    for (DensePassDev& pass : D->passes) {
-        pass.pcd_off = -1;
-        if (pass.diag_layer < 0 && !pass.measure) continue;
-        const int s = pass.group_s[pass.ngroups - 1];
-        int gbit[4];
-        uint32_t gmask = 0;
-        for (int k = 0; k < 4; ++k) {
-            const int local = s + k;
-            gbit[k] = pass.strided ? (local < 4 ? local : pass.a + local - 4) : local;
-            gmask |= 1u << gbit[k];
-        }
-        auto kof = [&](int q) { for (int k = 0; k < 4; ++k) if (gbit[k] == q) return k; return -1; };
-        pass.pcd_off = (int32_t)D->pcd.size();
-        auto add = [&](const DenseClassDev& cl) {
-            DensePassClassDev pc{};
-            uint32_t cnt[16] = {0};
-            for (int k = 0; k < cl.ndist; ++k) {
-                const int d = D->dists[2 * (cl.dist_off + k)];
-                const uint32_t M = (uint32_t)D->dists[2 * (cl.dist_off + k) + 1];
-                for (int u = 0; u < 32; ++u) {
-                    if (!((M >> u) & 1)) continue;
-                    const int v = u + d;
-                    const int ku = kof(u), kv = kof(v);
-                    if (ku >= 0 && kv >= 0) {
-                        for (int j = 0; j < 16; ++j) {
-                            const int bu = (j >> ku) & 1, bv = (j >> kv) & 1;
-                            cnt[j] += cl.kind == 1 ? (bu & bv) : (bu ^ bv);
+    // stage lists and split counts: per pass, the classes of every group that evaluates some
+    for (int pi = 0; pi < (int)D->passes.size(); ++pi) {
+        DensePassDev& pass = D->passes[pi];
+        pass.stage_off = (int32_t)D->stage.size();
+        for (const GroupDiag& gd : gdiag) {
+            if (gd.pass != pi) continue;
+            const int gi = gd.group;
+            int first_cls, ncls;
+            if (gd.layer >= 0) {
+                first_cls = D->layers[gd.layer].class_off;
+                ncls = D->layers[gd.layer].nclass;
+            } else {
+                first_cls = D->energy_class_off;
+                ncls = D->energy_nclass;
+            }
+            if (pass.group_ncls[gi] == 0) {
+                pass.group_cls[gi] = (int32_t)D->stage.size() - pass.stage_off;
+                pass.group_pcd[gi] = (int32_t)D->pcd.size();
+            }
+            pass.group_ncls[gi] += ncls;
+            const int s = pass.group_s[gi];
+            int gbit[4];
+            for (int k = 0; k < 4; ++k) {
+                const int local = s + k;
+                gbit[k] = pass.strided ? (local < 4 ? local : pass.a + local - 4) : local;
+            }
+            auto kof = [&](int q) { for (int k = 0; k < 4; ++k) if (gbit[k] == q) return k; return -1; };
+            for (int ci = first_cls; ci < first_cls + ncls; ++ci) {
+                const DenseClassDev& cl = D->classes[ci];
+                D->stage.push_back(ci);
+                DensePassClassDev pc{};
+                uint32_t cnt[16] = {0};
+                for (int k = 0; k < cl.ndist; ++k) {
+                    const int d = D->dists[2 * (cl.dist_off + k)];
+                    const uint32_t M = (uint32_t)D->dists[2 * (cl.dist_off + k) + 1];
+                    for (int u = 0; u < 32; ++u) {
+                        if (!((M >> u) & 1)) continue;
+                        const int v = u + d;
+                        const int ku = kof(u), kv = kof(v);
+                        if (ku >= 0 && kv >= 0) {
+                            for (int jj = 0; jj < 16; ++jj) {
+                                const int bu = (jj >> ku) & 1, bv = (jj >> kv) & 1;
+                                cnt[jj] += cl.kind == 1 ? (bu & bv) : (bu ^ bv);
+                            }
+                        } else if (ku >= 0) {
+                            pc.N[ku] |= 1u << v;
+                        } else if (kv >= 0) {
+                            pc.N[kv] |= 1u << u;
                         }
-                    } else if (ku >= 0) {
-                        pc.N[ku] |= 1u << v;
-                    } else if (kv >= 0) {
-                        pc.N[kv] |= 1u << u;
                     }
                 }
+                for (int k = 0; k < 4; ++k)
+                    if ((cl.single >> gbit[k]) & 1) pc.single |= 1u << k;
+                for (int jj = 0; jj < 16; ++jj) pc.C[jj >> 2] |= cnt[jj] << (8 * (jj & 3));
+                D->pcd.push_back(pc);
             }
-            for (int k = 0; k < 4; ++k)
-                if ((cl.single >> gbit[k]) & 1) pc.single |= 1u << k;
-            for (int j = 0; j < 16; ++j) pc.C[j >> 2] |= cnt[j] << (8 * (j & 3));
-            D->pcd.push_back(pc);
-        };
-        if (pass.diag_layer >= 0) {
-            const DenseLayerDev& ld = D->layers[pass.diag_layer];
-            for (int k = 0; k < ld.nclass; ++k) add(D->classes[ld.class_off + k]);
         }
-        if (pass.measure)
-            for (int k = 0; k < D->energy_nclass; ++k) add(D->classes[D->energy_class_off + k]);
-        (void)gmask;
+        pass.nstage = (int32_t)D->stage.size() - pass.stage_off;
     }
-    // the pass kernel stages one layer's classes plus the energy classes in shared memory
-    int e_words = 0;
-    for (int k = 0; k < D->energy_nclass; ++k) e_words += 2 * D->classes[D->energy_class_off + k].ndist;
-    for (const DenseLayerDev& ld : D->layers) {
-        int words = e_words, tab = 0;
-        for (int k = 0; k < ld.nclass; ++k) {
-            const DenseClassDev& cl = D->classes[ld.class_off + k];
+    // shared-memory capacity of the pass kernel
+    for (const DensePassDev& pass : D->passes) {
+        int words = 0, tab = 0;
+        for (int k = 0; k < pass.nstage; ++k) {
+            const DenseClassDev& cl = D->classes[D->stage[pass.stage_off + k]];
             words += 2 * cl.ndist;
             tab += cl.kind == 0 ? cl.nterms + 1 : 0;
         }
-        if (ld.nclass + D->energy_nclass > kDenseMaxLayerClasses || words > kDenseMaxDistWords || tab > kDenseMaxTab)
+        if (pass.nstage > kDenseMaxLayerClasses || words > kDenseMaxDistWords || tab > kDenseMaxTab)
             D->fits_fused = false;
     }
-    if (D->energy_nclass > kDenseMaxLayerClasses || e_words > kDenseMaxDistWords) D->fits_fused = false;
     return D;
 }
 

@@ -31,6 +31,7 @@ struct PlanEntry {
     DenseLayerDev* d_dlayers = nullptr;
     DenseClassDev* d_dclasses = nullptr;
     DensePassClassDev* d_dpcd = nullptr;
+    int32_t* d_dstage = nullptr;
     int32_t* d_ddists = nullptr;
     DenseZTermDev* d_dzterms = nullptr;
     int32_t* d_dtab_gate = nullptr;
