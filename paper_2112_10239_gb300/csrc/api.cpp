@@ -119,7 +119,10 @@ tlq_status ensure_worklist(Context* ctx, PlanEntry& pe, const Circuit& c, int B,
     const int T = (int)P.cones.size();
     std::vector<int> order(T);
     for (int t = 0; t < T; ++t) order[t] = t;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P.cones[a].W > P.cones[b].W; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (P.cones[a].W != P.cones[b].W) return P.cones[a].W > P.cones[b].W;
+        return P.cone_cost[a] > P.cone_cost[b];   // longest first within a width class
+    });
     const int smax = smem_optin(ctx->device);
     std::vector<int32_t> items;
     std::vector<ChunkDev> smem_chunks, glob_chunks;

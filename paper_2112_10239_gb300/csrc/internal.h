@@ -193,6 +193,7 @@ struct Plan {
     std::vector<ConeDev> cones;           // one per term group (shared window)
     std::vector<MeasDev> meas;            // measured terms of all cones
     std::vector<int32_t> group_wtrue;     // true width of each group's window
+    std::vector<double> cone_cost;        // estimated work of each cone (longest first within a width)
     std::vector<int32_t> prog;            // programs of all cones
     std::vector<int32_t> cone_gates;      // gates in each cone (introspection)
     std::vector<int32_t> cone_lo;         // window start per term

@@ -201,6 +201,7 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
     P->cone_ndiag.assign(NG, 0);
     P->cone_npdiag.assign(NG, 0);
     P->group_wtrue.assign(NG, 0);
+    P->cone_cost.assign(NG, 0.0);
     // ---- phase 3: one program per group ----
     for (int t = 0; t < NG; ++t) {
         std::sort(members[t].begin(), members[t].end());
@@ -311,6 +312,7 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                     }
                 }
                 if (any_diag) P->cone_ndiag[t] += 1;
+                P->cone_cost[t] += (double)(__builtin_popcount(live) + (any_diag ? 1 : 0)) * (double)(1 << W);
                 body[hdr + 0] = any_diag ? 1 : 0;
                 body[hdr + 1] = (int32_t)live;
                 body[hdr + 2] = 0;
@@ -324,6 +326,7 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
         P->prog.insert(P->prog.end(), body.begin(), body.end());
         cd.nslots = nslot;
         slot_total += nslot;
+        P->cone_cost[t] += (double)members[t].size() * (double)(1 << W);
         cd.mterm_off = (int32_t)P->meas.size();
         cd.nmterms = (int32_t)members[t].size();
         for (int m : members[t]) {
