@@ -18,6 +18,7 @@ import argparse
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -39,10 +40,15 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tlq", choices=["tlq", "reference"])
-    ap.add_argument("--workload", default="tfim_n20_L6_B64")
+    ap.add_argument("--workload", default="tfim_n20_L6_B64",
+                    help="tfim_n20_L6_B64 (default), tfim_n500_L4_B256, tfim_n8_L2_B1 or qaoa_n<N>_p<P> "
+                         "(3-regular graph, dense statevector path, one parameter set)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the chosen workload only: no other workloads, serving replay or CPU baseline "
+                         "(short runs for a profiler)")
     return ap.parse_args()
 
 
@@ -54,6 +60,12 @@ def workload(name):
         return W.tfim_n500_L4_B256()
     if name == "tfim_n8_L2_B1":
         return W.tfim_n8_L2()
+    m = re.fullmatch(r"qaoa_n(\d+)_p(\d+)", name)
+    if m:
+        n, p = int(m.group(1)), int(m.group(2))
+        if not 13 <= n <= 31 or p < 1:
+            raise SystemExit("qaoa workloads take 13 <= n <= 31 and p >= 1")
+        return W.qaoa_problem(n, p, 1, seed=2, name=name)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -282,7 +294,23 @@ def serving_replay(B, device, count, rate, seed=4):
             "batched": batched, "one_at_a_time": plain}
 
 
-def device_steps(B, ctx, c, h, prob, grad, steps, dev, flush):
+def dense_bytes(B, ctx, c, h, grad):
+    """HBM bytes one evaluation of the dense pass sequence moves (the pass schedule's own
+    traffic): every forward pass reads and writes the 2^n complex64 state; with the gradient
+    the final pass also writes lam = H psi, each reverse pass reads and writes psi and lam
+    (the last one only reads), and X/Y strings add a gather sweep that reads psi and lam
+    and writes lam."""
+    n_eff, passes, n_x, _ = B.tlq_plan_dense_info(ctx.h, c.h, h.h)
+    S = 8 * (1 << n_eff)
+    total = passes * 2 * S
+    if grad:
+        total += S + max(0, passes - 1) * 4 * S + (2 * S if passes > 0 else 0)
+        if n_x:
+            total += 3 * S
+    return total, passes
+
+
+def device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3):
     """Time `steps` device-pointer calls (inputs resident, L2 flushed between steps)."""
     import torch
     Bsz, P = prob.theta.shape
@@ -295,7 +323,7 @@ def device_steps(B, ctx, c, h, prob, grad, steps, dev, flush):
         B.tlq_expectation_grad_dev(ctx.h, c.h, h.h, theta_d.data_ptr(), Bsz, B.TLQ_FP32, E_d.data_ptr(),
                                    G_d.data_ptr() if grad else None, stream.cuda_stream)
 
-    for _ in range(3):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     step_ms, kern_ms, launches = [], [], 0
@@ -332,10 +360,12 @@ def extra_workloads(B, dev, local, flush, peaks):
                          "frac": flops / (kms * 1e-3) / 1e12 / peak, "kernel_ms": kms}}
         c.close()
         h.close()
-    # n=28 QAOA on a 3-regular graph (dense statevector), fused passes vs plain per-gate sweeps
+    # n=28 QAOA on a 3-regular graph (dense statevector): energy and energy + gradient, fused
+    # passes vs the plain per-gate sweeps
     prob = W.qaoa_n28_p4()
     res = {}
-    for name, fk in (("fused", 0), ("per_gate", 1)):
+    for name, fk, grad, steps in (("fused", 0, False, 5), ("fused_grad", 0, True, 5),
+                                  ("per_gate", 1, False, 2), ("per_gate_grad", 1, True, 1)):
         cfg = B.tlq_config(local, 0, 0, B.TLQ_FP32, fk)
         hnd = ctypes.c_void_p()
         B._check(B.lib().tlq_init(ctypes.byref(cfg), ctypes.byref(hnd)))
@@ -343,23 +373,32 @@ def extra_workloads(B, dev, local, flush, peaks):
         ctx.h = hnd
         c, h = ctx.problem(prob)
         B.tlq_profile_enable(ctx.h, True)
-        ms, kms, nl = device_steps(B, ctx, c, h, prob, False, 5 if fk == 0 else 2, dev, flush)
-        res[name] = (ms, kms, nl)
+        ms, kms, nl = device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3 if fk == 0 else 1)
+        nbytes, passes = dense_bytes(B, ctx, c, h, grad)
+        res[name] = (ms, kms, nl, nbytes, passes)
         c.close()
         h.close()
         ctx.close()
-    ms, kms, nl = res["fused"]
-    passes = nl - 4          # gate table, phase tables, state init and the final reduction
-    state_bytes = 8 * (1 << prob.n)
-    achieved = passes * 2 * state_bytes / (kms * 1e-3) / 1e9
+
+    def hbm(key, kernel):
+        ms, kms, nl, nbytes, passes = res[key]
+        achieved = nbytes / (kms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None, "kernel": kernel,
+                "kernel_ms": kms, "bytes_per_eval": nbytes}
+
     out["qaoa_n28_p4"] = {
-        "value": 1.0 / (ms * 1e-3), "unit": "evals/s", "ms_per_eval": ms,
-        "per_gate_ms_per_eval": res["per_gate"][0], "speedup_vs_per_gate": res["per_gate"][0] / ms,
-        "passes": passes,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                     "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
-                     "kernel": "dense_pass_kernel x passes (read + write of the 2 GiB state each)",
-                     "kernel_ms": kms}}
+        "value": 1.0 / (res["fused"][0] * 1e-3), "unit": "evals/s", "ms_per_eval": res["fused"][0],
+        "per_gate_ms_per_eval": res["per_gate"][0], "speedup_vs_per_gate": res["per_gate"][0] / res["fused"][0],
+        "passes": res["fused"][4], "launches": res["fused"][2],
+        "roofline": hbm("fused", "dense_pass_kernel x passes (read + write of the 2 GiB state each)")}
+    out["qaoa_n28_p4_grad"] = {
+        "value": 1.0 / (res["fused_grad"][0] * 1e-3), "unit": "grad-evals/s", "ms_per_eval": res["fused_grad"][0],
+        "per_gate_ms_per_eval": res["per_gate_grad"][0],
+        "speedup_vs_per_gate": res["per_gate_grad"][0] / res["fused_grad"][0],
+        "launches": res["fused_grad"][2],
+        "roofline": hbm("fused_grad", "forward dense_pass_kernel x passes, then dense_adjoint_kernel x passes "
+                                      "(psi and lam read + written)")}
     # serving: Poisson arrivals, continuous batching vs one request at a time
     out["serving"] = serving_replay(B, local, 2000, 2000.0)
     return out
@@ -450,18 +489,27 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    flops = algorithmic_flops(B, ctx, c, h, prob, grad=True)
     kern_mean_ms = float(np.mean(kern_ms))
-    achieved = flops / (kern_mean_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": "cone_kernel<float,grad> (batched causal cones + adjoint)",
-                "kernel_ms": kern_mean_ms, "algorithmic_flops": flops,
-                "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x {sm_max:.0f} MHz"}
+    path, *_ = B.tlq_plan_info(ctx.h, c.h, h.h, len(prob.terms))
+    if path == B.TLQ_PATH_DENSE:
+        nbytes, passes = dense_bytes(B, ctx, c, h, True)
+        achieved = nbytes / (kern_mean_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                    "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                    "kernel": "dense_pass_kernel + dense_adjoint_kernel (forward and reverse passes)",
+                    "kernel_ms": kern_mean_ms, "bytes_per_eval": nbytes, "passes": passes}
+    else:
+        flops = algorithmic_flops(B, ctx, c, h, prob, grad=True)
+        achieved = flops / (kern_mean_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tflops, "traffic": None,
+                    "kernel": "cone_kernel<float,grad> (batched causal cones + adjoint)",
+                    "kernel_ms": kern_mean_ms, "algorithmic_flops": flops,
+                    "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x {sm_max:.0f} MHz"}
 
-    extras = extra_workloads(B, dev, local, flush, peaks) if rank == 0 else {}
+    extras = extra_workloads(B, dev, local, flush, peaks) if rank == 0 and not args.no_extras else {}
     if rank == 0:
-        cpu = cpu_baseline(prob)
+        cpu = None if args.no_extras else cpu_baseline(prob)
         sm = sorted(step_ms)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

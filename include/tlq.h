@@ -128,7 +128,11 @@ tlq_status tlq_expectation(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* 
                            tlq_precision prec, double* energy);
 
 /* Forward + backward (Sec. 3, <H> and nabla <H>): as tlq_expectation plus
- * grad[b][p] = dE_b / dtheta_p (host, row-major [B][n_params], FP64). Synchronous. */
+ * grad[b][p] = dE_b / dtheta_p (host, row-major [B][n_params], FP64). Synchronous.
+ * A parameter shared by several gates gets the sum of their derivatives; parameters no
+ * gate uses get 0. Both paths compute the gradient by the adjoint method; on the dense
+ * statevector path it holds a second 2^n complex64 state (lambda = H psi) while it runs,
+ * and TLQ_FP64_REF returns TLQ_EUNSUPPORTED there (that path is FP32 only). */
 tlq_status tlq_expectation_grad(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta, int32_t B,
                                 tlq_precision prec, double* energy, double* grad);
 
@@ -203,6 +207,16 @@ tlq_status tlq_plan_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* path, i
  * work of a call. TLQ_EUNSUPPORTED on the dense path. */
 tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* ncones, int32_t* nrot, int32_t* ndiag,
                                int32_t* npdiag, int32_t* weff, int32_t* wtrue, int32_t* nterms);
+
+/* Dense statevector plan of (c, h): the state's qubit count *n_eff (n, at least 13), the
+ * number of streaming passes *n_passes one forward evaluation makes over the state (the
+ * adjoint makes as many again, in reverse), the number of Pauli strings with X/Y letters
+ * *n_xterms measured by separate sweeps, and *fused = 1 when the fused passes are used
+ * (0: the plan's staged data exceed the pass kernel's shared memory and the plain per-gate
+ * sweeps run instead). Any out pointer may be NULL. TLQ_EUNSUPPORTED when (c, h) has no
+ * dense plan (more than 31 qubits). */
+tlq_status tlq_plan_dense_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n_eff, int32_t* n_passes,
+                               int32_t* n_xterms, int32_t* fused);
 
 /* Kernel timing for benchmarks. While enabled, every compute call records CUDA events
  * around its dominant kernel (the batched cone kernel, or the dense pass sequence) on the

@@ -27,7 +27,8 @@ SYMBOLS = ["tlq_init", "tlq_destroy", "tlq_circuit_create", "tlq_circuit_destroy
            "tlq_hamiltonian_create", "tlq_hamiltonian_destroy", "tlq_expectation",
            "tlq_expectation_grad", "tlq_expectation_grad_dev", "tlq_submit", "tlq_poll",
            "tlq_last_error", "tlq_plan_info", "tlq_plan_cone_stats", "tlq_profile_enable",
-           "tlq_profile_last", "tlq_serving_stats", "tlq_version", "tlq_expectation_grad_static"]
+           "tlq_profile_last", "tlq_serving_stats", "tlq_version", "tlq_expectation_grad_static",
+           "tlq_plan_dense_info"]
 
 
 class tlq_gate(ctypes.Structure):
@@ -80,6 +81,7 @@ def lib():
         L.tlq_last_error.restype = ctypes.c_char_p
         L.tlq_plan_info.argtypes = [vp, vp, vp, ip, ip, ip, ip]
         L.tlq_plan_cone_stats.argtypes = [vp, vp, vp, ip, ip, ip, ip, ip, ip, ip]
+        L.tlq_plan_dense_info.argtypes = [vp, vp, vp, ip, ip, ip, ip]
         L.tlq_profile_enable.argtypes = [vp, ctypes.c_int]
         L.tlq_profile_last.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ip]
         L.tlq_expectation_grad_static.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp, vp, vp]
@@ -248,6 +250,13 @@ def tlq_plan_cone_stats(ctx, circ, ham, n_terms):
     out = [np.zeros(max(1, n_terms), dtype=np.int32) for _ in range(6)]
     _check(lib().tlq_plan_cone_stats(ctx, circ, ham, ctypes.byref(nc), *[a.ctypes.data_as(ip) for a in out]), ctx)
     return tuple(a[:nc.value] for a in out)
+
+
+def tlq_plan_dense_info(ctx, circ, ham):
+    """(n_eff, n_passes, n_xterms, fused) of the dense statevector plan."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib().tlq_plan_dense_info(ctx, circ, ham, *[ctypes.byref(x) for x in v]), ctx)
+    return tuple(x.value for x in v)
 
 
 def tlq_profile_enable(ctx, on=True):

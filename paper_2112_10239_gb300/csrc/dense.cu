@@ -49,6 +49,7 @@ struct PassArgs {
     int32_t n_eff;
     double* partial;        // per-CTA energy partials
     int32_t* err;           // kernel error word
+    float2* lam;            // gradient mode, final pass: lam = (diagonal part of H) psi, else null
 };
 
 // Global amplitude index of local tile index t.
@@ -94,6 +95,58 @@ __device__ __forceinline__ void issue_tile(const DensePassDev& P, uint32_t t, co
 
 __device__ __forceinline__ void wait_tiles() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Stage a pass's classes (diagonal phases of the layers it completes, and the energy
+// classes in the final pass) with their distance words, phase tables and split counts.
+// Called by every thread of the CTA; ends with a barrier.
+__device__ void stage_classes(const DensePassDev& P, const DenseClassDev* classes, const DensePassClassDev* pcd,
+                              const int32_t* stage, const int32_t* dists, const float2* ptab, DenseClassDev* s_cls,
+                              DensePassClassDev* s_pcd, int32_t* s_woff, int32_t* s_toff, int32_t* s_dist,
+                              float2* s_tab, int tid) {
+    const int nst = P.nstage;
+    if (tid < nst) s_cls[tid] = classes[stage[P.stage_off + tid]];
+    __syncthreads();
+    if (tid == 0) {
+        int woff = 0, toff = 0;
+        for (int c = 0; c < nst; ++c) {
+            s_woff[c] = woff;
+            s_toff[c] = toff;
+            woff += 2 * s_cls[c].ndist;
+            toff += s_cls[c].kind == 0 ? s_cls[c].nterms + 1 : 0;
+        }
+    }
+    for (int g = 0; g < P.ngroups; ++g)
+        for (int k = tid; k < P.group_ncls[g]; k += kThreads) s_pcd[P.group_cls[g] + k] = pcd[P.group_pcd[g] + k];
+    __syncthreads();
+    for (int c = 0; c < nst; ++c) {
+        const DenseClassDev& C = s_cls[c];
+        for (int w = tid; w < 2 * C.ndist; w += kThreads) s_dist[s_woff[c] + w] = dists[2 * C.dist_off + w];
+        if (C.kind == 0)
+            for (int e = tid; e <= C.nterms; e += kThreads) s_tab[s_toff[c] + e] = ptab[C.tab_off + e];
+    }
+    __syncthreads();
+}
+
+// Split class count of amplitude j of a register pass: count(x_b | j) from the count at the
+// thread's base index, the per-bit deltas A_k and the in-group pairs C[j] (see DensePassClassDev).
+__device__ __forceinline__ void split_deltas(const DenseClassDev& C, const DensePassClassDev& pc, uint32_t xb,
+                                             int (&Ak)[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int inter = __popc(xb & pc.N[k]);
+        Ak[k] = C.kind == 1 ? inter : __popc(pc.N[k]) - 2 * inter + (int)((pc.single >> k) & 1u);
+    }
+}
+
+__device__ __forceinline__ int split_count(const DensePassClassDev& pc, int cnt0, const int (&Ak)[4], int j) {
+    const uint32_t cw = pc.C[j >> 2];
+    int cnt = cnt0 + (int)((cw >> (8 * (j & 3))) & 255u);
+    if (j & 1) cnt += Ak[0];
+    if (j & 2) cnt += Ak[1];
+    if (j & 4) cnt += Ak[2];
+    if (j & 8) cnt += Ak[3];
+    return cnt;
+}
+
 // Persistent pass kernel: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // with two shared-memory tile buffers; the cp.async copy of the next tile runs while the
 // current one is processed. The last register pass writes its 16 amplitudes straight to HBM.
@@ -114,30 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
 
     if (blockIdx.x < ntiles) issue_tile(P, blockIdx.x, A.state, bufs, tid);
 
-    // stage this pass's classes (diagonal phases of the layers it completes, and the energy
-    // classes in the final pass) with their distance words, phase tables and split counts
-    const int nst = P.nstage;
-    if (tid < nst) s_cls[tid] = A.classes[A.stage[P.stage_off + tid]];
-    __syncthreads();
-    if (tid == 0) {
-        int woff = 0, toff = 0;
-        for (int c = 0; c < nst; ++c) {
-            s_woff[c] = woff;
-            s_toff[c] = toff;
-            woff += 2 * s_cls[c].ndist;
-            toff += s_cls[c].kind == 0 ? s_cls[c].nterms + 1 : 0;
-        }
-    }
-    for (int g = 0; g < P.ngroups; ++g)
-        for (int k = tid; k < P.group_ncls[g]; k += kThreads) s_pcd[P.group_cls[g] + k] = A.pcd[P.group_pcd[g] + k];
-    __syncthreads();
-    for (int c = 0; c < nst; ++c) {
-        const DenseClassDev& C = s_cls[c];
-        for (int w = tid; w < 2 * C.ndist; w += kThreads) s_dist[s_woff[c] + w] = A.dists[2 * C.dist_off + w];
-        if (C.kind == 0)
-            for (int e = tid; e <= C.nterms; e += kThreads) s_tab[s_toff[c] + e] = A.ptab[C.tab_off + e];
-    }
-    __syncthreads();
+    stage_classes(P, A.classes, A.pcd, A.stage, A.dists, A.ptab, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab, tid);
 
     float eacc = 0.f;
     int i = 0;
@@ -228,6 +258,8 @@ __global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_co
                             }
                         }
                         eacc += (v[j].x * v[j].x + v[j].y * v[j].y) * ez[j];
+                        if (A.lam)
+                            A.lam[tile_x(P, t_id, (uint32_t)(base | (j << s)))] = make_float2(ez[j] * v[j].x, ez[j] * v[j].y);
                     }
                 }
             }
@@ -258,6 +290,209 @@ size_t dense_pass_smem() {
     return 2 * (size_t)padded_amps(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
            kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * (sizeof(DenseClassDev) + sizeof(DensePassClassDev)) +
            2 * kMaxLayerClasses * sizeof(int32_t) + 16 * sizeof(float);
+}
+
+// ---- adjoint passes (gradient) ----------------------------------------------------------------
+//
+// The gradient follows the adjoint method: with lam = H psi at the end of the circuit, walk the
+// gates backwards; a gate exp(-i a G/2) contributes dE/da = Im <lam|G|psi> with both states
+// taken right after it, then is un-applied to both. Gates that commute with G may sit between
+// that point and the one where the sum is taken, which lets a whole register group (rotations on
+// four distinct qubits) and a whole diagonal layer be handled at once:
+//   * diagonal class with angle a: sum_x Im(conj(lam_x) psi_x) (N - 2c(x)), then both states
+//     times the conjugate phase (the sum is unchanged by a common phase, so its order is free);
+//   * RX / RY on register bit k: the pair sums of gates.cuh, then the inverse rotation.
+// One adjoint kernel reverses one forward pass: groups in reverse order, each group's diagonal
+// classes before its rotations. psi and lam tiles share the CTA's shared memory (one buffer
+// each); the next tile's copies start as soon as the last group has read its registers.
+
+struct AdjArgs {
+    DensePassDev pass;
+    const DenseClassDev* classes;
+    const DensePassClassDev* pcd;
+    const int32_t* stage;
+    const int32_t* dists;
+    const tlq_gate* gates;
+    const float2* GT;       // gate table of this set
+    const float2* ptab;     // phase tables of this set
+    float2* psi;
+    float2* lam;
+    int32_t n_eff;
+    double* gpart;          // [kDenseAdjSlots][gridDim.x] gradient partials of this pass
+};
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    return x;
+}
+
+template <int K>
+__device__ __forceinline__ void adjoint_bit(const AdjArgs& A, int g, float2 (&v)[16], float2 (&u)[16], double* acc,
+                                            int lane) {
+    const int gate = A.pass.gate[g][K];
+    const float2 cs = A.GT[gate];
+    float gk = adjoint_rot<K, float2, float>(v, u, A.gates[gate].kind, cs.x, -cs.y);
+    gk = warp_sum(gk);
+    if (lane == 0) acc[4 * g + K] += (double)gk;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) dense_adjoint_kernel(const __grid_constant__ AdjArgs A) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2* bpsi = reinterpret_cast<float2*>(smem_raw);                               // padded_amps(13)
+    float2* blam = bpsi + padded_amps(kDenseTileBits);                                // padded_amps(13)
+    double* s_gacc = reinterpret_cast<double*>(blam + padded_amps(kDenseTileBits));   // [16 warps][slots]
+    float2* s_tab = reinterpret_cast<float2*>(s_gacc + (kThreads / 32) * kDenseAdjSlots);
+    int32_t* s_dist = reinterpret_cast<int32_t*>(s_tab + kMaxTab);
+    DenseClassDev* s_cls = reinterpret_cast<DenseClassDev*>(s_dist + kMaxDistWords);
+    DensePassClassDev* s_pcd = reinterpret_cast<DensePassClassDev*>(s_cls + kMaxLayerClasses);
+    int32_t* s_woff = reinterpret_cast<int32_t*>(s_pcd + kMaxLayerClasses);
+    int32_t* s_toff = s_woff + kMaxLayerClasses;
+    const DensePassDev& P = A.pass;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const uint32_t ntiles = 1u << (A.n_eff - kDenseTileBits);
+
+    if (blockIdx.x < ntiles) {
+        issue_tile(P, blockIdx.x, A.psi, bpsi, tid);
+        issue_tile(P, blockIdx.x, A.lam, blam, tid);
+    }
+    for (int k = tid; k < (kThreads / 32) * kDenseAdjSlots; k += kThreads) s_gacc[k] = 0.0;
+    stage_classes(P, A.classes, A.pcd, A.stage, A.dists, A.ptab, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab, tid);
+    double* acc = s_gacc + warp * kDenseAdjSlots;   // written by lane 0 of this warp only
+
+    for (uint32_t t_id = blockIdx.x; t_id < ntiles; t_id += gridDim.x) {
+        wait_tiles();
+        __syncthreads();
+        for (int g = P.ngroups - 1; g >= 0; --g) {
+            const int s = P.group_s[g];
+            const int stride = pass_stride(s);
+            const int base = (tid & ((1 << s) - 1)) | ((tid >> s) << (s + 4));
+            float2 v[16], u[16];
+            load16(v, bpsi + pad16(base), stride);
+            load16(u, blam + pad16(base), stride);
+            if (g == 0) {
+                __syncthreads();   // every thread holds its amplitudes: both buffers are free
+                const uint32_t next = t_id + gridDim.x;
+                if (next < ntiles) {
+                    issue_tile(P, next, A.psi, bpsi, tid);
+                    issue_tile(P, next, A.lam, blam, tid);
+                }
+            }
+            // the diagonal classes applied after this group in the forward pass
+            const int ncls = P.group_ncls[g];
+            if (ncls > 0) {
+                const uint32_t xb = tile_x(P, t_id, (uint32_t)base);
+                for (int ci = P.group_cls[g]; ci < P.group_cls[g] + ncls; ++ci) {
+                    const DenseClassDev& C = s_cls[ci];
+                    if (C.kind == 2) continue;   // energy classes: nothing to undo
+                    const DensePassClassDev& pc = s_pcd[ci];
+                    const int cnt0 = class_count(C, s_dist + s_woff[ci], xb);
+                    int Ak[4];
+                    split_deltas(C, pc, xb, Ak);
+                    if (C.kind == 0) {
+                        const int toff = s_toff[ci];
+                        float gsum = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int cnt = split_count(pc, cnt0, Ak, j);
+                            gsum += (u[j].x * v[j].y - u[j].y * v[j].x) * (float)(C.nterms - 2 * cnt);
+                            float2 ph = s_tab[toff + cnt];
+                            ph.y = -ph.y;
+                            v[j] = cmul(v[j], ph);
+                            u[j] = cmul(u[j], ph);
+                        }
+                        gsum = warp_sum(gsum);
+                        if (lane == 0) acc[4 * kDenseMaxGroups + ci] += (double)gsum;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (split_count(pc, cnt0, Ak, j) & 1) {
+                                v[j].x = -v[j].x;
+                                v[j].y = -v[j].y;
+                                u[j].x = -u[j].x;
+                                u[j].y = -u[j].y;
+                            }
+                        }
+                    }
+                }
+            }
+            // the group's rotations: gradient, then the inverse rotation on both states
+            const unsigned m = P.group_mask[g];
+            if (m & 1u) adjoint_bit<0>(A, g, v, u, acc, lane);
+            if (m & 2u) adjoint_bit<1>(A, g, v, u, acc, lane);
+            if (m & 4u) adjoint_bit<2>(A, g, v, u, acc, lane);
+            if (m & 8u) adjoint_bit<3>(A, g, v, u, acc, lane);
+            if (g > 0) {
+                store16(v, bpsi + pad16(base), stride);
+                store16(u, blam + pad16(base), stride);
+                __syncthreads();
+            } else if (P.store) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const uint32_t x = tile_x(P, t_id, (uint32_t)(base | (j << s)));
+                    A.psi[x] = v[j];
+                    A.lam[x] = u[j];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < kDenseAdjSlots; k += kThreads) {
+        double sum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sum += s_gacc[w * kDenseAdjSlots + k];
+        A.gpart[(size_t)k * gridDim.x + blockIdx.x] = sum;
+    }
+}
+
+size_t dense_adjoint_smem() {
+    return 2 * (size_t)padded_amps(kDenseTileBits) * sizeof(float2) +
+           (size_t)(kThreads / 32) * kDenseAdjSlots * sizeof(double) + kMaxTab * sizeof(float2) +
+           kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * (sizeof(DenseClassDev) + sizeof(DensePassClassDev)) +
+           2 * kMaxLayerClasses * sizeof(int32_t);
+}
+
+// lam (+)= sum_t c_t P_t psi over Pauli strings given by (flip, zy, ny):
+// (P psi)_x = (-i)^ny (-1)^popc(x & zy) psi_{x ^ flip}.
+__global__ void lambda_terms_kernel(const float2* psi, float2* lam, uint64_t N, const DenseXTermDev* terms, int nterms,
+                                    int accumulate) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+        float2 out = accumulate ? lam[x] : make_float2(0.f, 0.f);
+        for (int t = 0; t < nterms; ++t) {
+            const DenseXTermDev T = terms[t];
+            const int q = T.ny & 3;
+            const float2 f0 = make_float2(q == 0 ? 1.f : q == 2 ? -1.f : 0.f, q == 1 ? -1.f : q == 3 ? 1.f : 0.f);
+            float2 v = cmul(f0, psi[x ^ T.flip]);
+            const float c = (__popc((uint32_t)x & T.zy) & 1) ? -(float)T.coeff : (float)T.coeff;
+            out.x += c * v.x;
+            out.y += c * v.y;
+        }
+        lam[x] = out;
+    }
+}
+
+// grad[p] = sum over the entries of parameter p of sum over CTAs of the pass partials, one warp
+// per parameter; each lane sums a fixed subset in order, then a fixed shuffle tree.
+__global__ void dense_grad_reduce_kernel(const double* gpart, int grid, const int32_t* off, const int32_t* idx,
+                                         int n_params, double* grad) {
+    const int p = (int)((blockIdx.x * (uint32_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (p >= n_params) return;
+    double s = 0.0, c = 0.0;   // Neumaier
+    for (int e = off[p]; e < off[p + 1]; ++e) {
+        const double* row = gpart + (size_t)idx[e] * grid;
+        for (int k = lane; k < grid; k += 32) {
+            const double x = row[k];
+            const double t = s + x;
+            if (fabs(s) >= fabs(x)) c += (s - t) + x;
+            else c += (x - t) + s;
+            s = t;
+        }
+    }
+    double v = s + c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) grad[p] = v;
 }
 
 // ---- gate tables and phase tables ---------------------------------------------------------
@@ -338,9 +573,10 @@ __global__ void reduce_partials_kernel(const double* partial, int n, double coef
 
 // ---- plain per-gate sweeps (baseline) -----------------------------------------------------
 
-__global__ void pergate_rot_kernel(float2* psi, uint64_t half, int q, int kind, const float2* GT, int gate) {
+// sgn = -1 applies the inverse rotation (adjoint sweep)
+__global__ void pergate_rot_kernel(float2* psi, uint64_t half, int q, int kind, const float2* GT, int gate, float sgn) {
     const float2 cs = GT[gate];
-    const float c = cs.x, s = cs.y;
+    const float c = cs.x, s = sgn * cs.y;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < half; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t x0 = ((i >> q) << (q + 1)) | (i & ((1ull << q) - 1));
         const uint64_t x1 = x0 | (1ull << q);
@@ -358,12 +594,13 @@ __global__ void pergate_rot_kernel(float2* psi, uint64_t half, int q, int kind, 
     }
 }
 
-__global__ void pergate_diag_kernel(float2* psi, uint64_t N, int kind, int q0, int q1, const float2* GT, int gate) {
+__global__ void pergate_diag_kernel(float2* psi, uint64_t N, int kind, int q0, int q1, const float2* GT, int gate,
+                                    float sgn) {
     float2 f0 = make_float2(1.f, 0.f), f1 = f0;
     if (kind != TLQ_CZ) {
         const float2 cs = GT[gate];
-        f0 = make_float2(cs.x, -cs.y);   // z = +1
-        f1 = make_float2(cs.x, cs.y);    // z = -1
+        f0 = make_float2(cs.x, -sgn * cs.y);   // z = +1
+        f1 = make_float2(cs.x, sgn * cs.y);    // z = -1
     }
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
         const int b0 = (int)((x >> q0) & 1);
@@ -380,6 +617,42 @@ __global__ void pergate_diag_kernel(float2* psi, uint64_t N, int kind, int q0, i
     }
 }
 
+// Im <lam| G |psi> of one gate over the whole state (G = X_q, Y_q, Z_q or Z_q0 Z_q1), per block.
+__global__ void __launch_bounds__(kMeasThreads) pergate_grad_kernel(const float2* psi, const float2* lam, uint64_t N,
+                                                                    int kind, int q0, int q1, double* partial) {
+    float acc = 0.f;
+    if (kind == TLQ_RX || kind == TLQ_RY) {
+        const uint64_t half = N / 2;
+        for (uint64_t i = (uint64_t)blockIdx.x * kMeasThreads + threadIdx.x; i < half;
+             i += (uint64_t)gridDim.x * kMeasThreads) {
+            const uint64_t x0 = ((i >> q0) << (q0 + 1)) | (i & ((1ull << q0) - 1));
+            const uint64_t x1 = x0 | (1ull << q0);
+            const float2 p0 = psi[x0], p1 = psi[x1], l0 = lam[x0], l1 = lam[x1];
+            if (kind == TLQ_RY) acc += (l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y);
+            else acc += (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
+        }
+    } else {
+        for (uint64_t x = (uint64_t)blockIdx.x * kMeasThreads + threadIdx.x; x < N;
+             x += (uint64_t)gridDim.x * kMeasThreads) {
+            const float2 p = psi[x], l = lam[x];
+            int odd = (int)((x >> q0) & 1);
+            if (kind == TLQ_RZZ) odd ^= (int)((x >> q1) & 1);
+            const float w = l.x * p.y - l.y * p.x;
+            acc += odd ? -w : w;
+        }
+    }
+    __shared__ float red[kMeasThreads / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float e = 0.f;
+        for (int w = 0; w < kMeasThreads / 32; ++w) e += red[w];
+        partial[blockIdx.x] = (double)e;
+    }
+}
+
 __global__ void init_state_kernel(float2* psi, uint64_t N) {
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x)
         psi[x] = make_float2(x == 0 ? 1.f : 0.f, 0.f);
@@ -392,20 +665,83 @@ size_t dense_partial_count(int n_eff) {
     return tiles > (size_t)kMeasBlocks ? tiles : (size_t)kMeasBlocks;
 }
 
+int dense_grid(int n_eff, int sm_count) {
+    const int ntiles = 1 << (n_eff - kDenseTileBits);
+    return ntiles < sm_count ? ntiles : sm_count;
+}
+
+namespace {
+
+// Plain path: one sweep per gate forward, per-term measurement sweeps, and for the gradient
+// lam = H psi by one gather sweep, then per gate (last to first) one gradient sweep and the
+// inverse gate on both states.
+int launch_pergate(DenseLaunch& L, cudaStream_t st, int b, const float2* GT, double* eout, double* gout, int& launches) {
+    const uint64_t N = 1ull << L.n_eff;
+    const int grid_sweep = L.sm_count * 8;
+    float2* psi = (float2*)L.state;
+    float2* lam = (float2*)L.lam;
+    for (int g = 0; g < L.n_gates; ++g) {
+        const tlq_gate G = L.host_gates[g];
+        if (G.kind == TLQ_RX || G.kind == TLQ_RY)
+            pergate_rot_kernel<<<grid_sweep, 256, 0, st>>>(psi, N / 2, G.q0, G.kind, GT, g, 1.f);
+        else
+            pergate_diag_kernel<<<grid_sweep, 256, 0, st>>>(psi, N, G.kind, G.q0, G.q1, GT, g, 1.f);
+        ++launches;
+    }
+    for (int t = 0; t < L.n_all_terms; ++t) {
+        const DenseXTermDev T = L.host_all_terms[t];
+        term_measure_kernel<<<kMeasBlocks, kMeasThreads, 0, st>>>(psi, N, T.flip, T.zy, T.ny, L.partial);
+        reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, kMeasBlocks, T.coeff, eout, 1);
+        launches += 2;
+    }
+    if (!gout) return 0;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(gout, 0, sizeof(double) * (size_t)L.n_params, st)) != cudaSuccess) return (int)e;
+    lambda_terms_kernel<<<grid_sweep, 256, 0, st>>>(psi, lam, N, L.all_terms, L.n_all_terms, 0);
+    ++launches;
+    for (int g = L.n_gates - 1; g >= 0; --g) {
+        const tlq_gate G = L.host_gates[g];
+        if (G.param >= 0) {
+            pergate_grad_kernel<<<kMeasBlocks, kMeasThreads, 0, st>>>(psi, lam, N, G.kind, G.q0, G.q1, L.partial);
+            reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, kMeasBlocks, 1.0, gout + G.param, 1);
+            launches += 2;
+        }
+        if (g == 0) break;
+        for (float2* st_ptr : {psi, lam}) {
+            if (G.kind == TLQ_RX || G.kind == TLQ_RY)
+                pergate_rot_kernel<<<grid_sweep, 256, 0, st>>>(st_ptr, N / 2, G.q0, G.kind, GT, g, -1.f);
+            else
+                pergate_diag_kernel<<<grid_sweep, 256, 0, st>>>(st_ptr, N, G.kind, G.q0, G.q1, GT, g, -1.f);
+            ++launches;
+        }
+    }
+    (void)b;
+    return 0;
+}
+
+}  // namespace
+
 int launch_dense(DenseLaunch& L, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     const uint64_t N = 1ull << L.n_eff;
     const int grid_sweep = L.sm_count * 8;
     float2* psi = (float2*)L.state;
+    float2* lam = (float2*)L.lam;
     int launches = 0;
     const size_t smem = dense_pass_smem();
+    const size_t asmem = dense_adjoint_smem();
     if ((e = cudaFuncSetAttribute(dense_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return (int)e;
+    if (L.grad && !L.per_gate &&
+        (e = cudaFuncSetAttribute(dense_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem)) !=
+            cudaSuccess)
         return (int)e;
     for (int b = 0; b < L.B; ++b) {
         const double* th = L.theta + (size_t)b * L.n_params;
         float2* GT = (float2*)L.gate_table + (size_t)b * L.n_gates;
         float2* PT = (float2*)L.phase_tab + (size_t)b * (L.tab_entries > 0 ? L.tab_entries : 1);
+        double* gout = L.grad ? L.grad + (size_t)b * L.n_params : nullptr;
         if (L.n_gates > 0) {
             dense_gate_table_kernel<<<(L.n_gates + 255) / 256, 256, 0, st>>>(L.gates, L.n_gates, th, L.n_params, GT);
             ++launches;
@@ -421,22 +757,9 @@ int launch_dense(DenseLaunch& L, void* stream) {
         double* eout = L.energy + b;
         if ((e = cudaMemsetAsync(eout, 0, sizeof(double), st)) != cudaSuccess) return (int)e;
         if (L.per_gate) {
-            for (int g = 0; g < L.n_gates; ++g) {
-                const tlq_gate G = L.host_gates[g];
-                if (G.kind == TLQ_RX || G.kind == TLQ_RY)
-                    pergate_rot_kernel<<<grid_sweep, 256, 0, st>>>(psi, N / 2, G.q0, G.kind, GT, g);
-                else
-                    pergate_diag_kernel<<<grid_sweep, 256, 0, st>>>(psi, N, G.kind, G.q0, G.q1, GT, g);
-                ++launches;
-            }
-            for (int t = 0; t < L.n_all_terms; ++t) {
-                const DenseXTermDev T = L.host_all_terms[t];
-                term_measure_kernel<<<kMeasBlocks, kMeasThreads, 0, st>>>(psi, N, T.flip, T.zy, T.ny, L.partial);
-                reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, kMeasBlocks, T.coeff, eout, 1);
-                launches += 2;
-            }
+            const int rc = launch_pergate(L, st, b, GT, eout, gout, launches);
+            if (rc) return rc;
         } else {
-            const int ntiles = (int)(N >> kDenseTileBits);
             PassArgs A;
             A.layers = L.layers;
             A.classes = L.classes;
@@ -454,10 +777,15 @@ int launch_dense(DenseLaunch& L, void* stream) {
             A.n_eff = L.n_eff;
             A.partial = L.partial;
             A.err = L.err;
-            const int grid = ntiles < L.sm_count ? ntiles : L.sm_count;
+            A.lam = nullptr;
+            const int grid = dense_grid(L.n_eff, L.sm_count);
             bool measured = false;
             for (int p = 0; p < L.n_passes; ++p) {
                 A.pass = L.host_passes[p];
+                if (gout) {
+                    A.pass.store = 1;   // the adjoint starts from the final state in HBM
+                    if (A.pass.measure_group >= 0) A.lam = lam;
+                }
                 dense_pass_kernel<<<grid, kThreads, smem, st>>>(A);
                 ++launches;
                 if (A.pass.measure_group >= 0) measured = true;
@@ -471,6 +799,36 @@ int launch_dense(DenseLaunch& L, void* stream) {
                 term_measure_kernel<<<kMeasBlocks, kMeasThreads, 0, st>>>(psi, N, T.flip, T.zy, T.ny, L.partial);
                 reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, kMeasBlocks, T.coeff, eout, 1);
                 launches += 2;
+            }
+            if (gout) {
+                // lam = H psi: the diagonal part was written by the measuring pass; X/Y strings here
+                if (L.n_xterms > 0 || !measured) {
+                    lambda_terms_kernel<<<grid_sweep, 256, 0, st>>>(psi, lam, N, L.xterms, L.n_xterms, measured ? 1 : 0);
+                    ++launches;
+                }
+                AdjArgs R;
+                R.classes = L.classes;
+                R.pcd = L.pcd;
+                R.stage = L.stage;
+                R.dists = L.dists;
+                R.gates = L.gates;
+                R.GT = GT;
+                R.ptab = PT;
+                R.psi = psi;
+                R.lam = lam;
+                R.n_eff = L.n_eff;
+                for (int p = L.n_passes - 1; p >= 0; --p) {
+                    R.pass = L.host_passes[p];
+                    R.pass.store = p > 0;   // the first pass's inputs are not needed again
+                    R.gpart = L.gpart + (size_t)p * kDenseAdjSlots * grid;
+                    dense_adjoint_kernel<<<grid, kThreads, asmem, st>>>(R);
+                    ++launches;
+                }
+                if (L.n_params > 0) {
+                    dense_grad_reduce_kernel<<<(L.n_params + 7) / 8, 256, 0, st>>>(L.gpart, grid, L.adj_off, L.adj_idx,
+                                                                                 L.n_params, gout);
+                    ++launches;
+                }
             }
         }
         if (b == L.B - 1 && L.ev_end && (e = cudaEventRecord((cudaEvent_t)L.ev_end, st)) != cudaSuccess) return (int)e;

@@ -82,6 +82,8 @@ constexpr int kDenseMaxDistWords = 512;
 constexpr int kDenseMaxTab = 768;
 
 constexpr int kDenseMaxGroups = 8;
+// Gradient slots of one adjoint pass: 4 rotations per register group, then one per staged class.
+constexpr int kDenseAdjSlots = 4 * kDenseMaxGroups + kDenseMaxLayerClasses;
 
 // One streaming pass over all tiles. Its register passes ("groups") may span a layer
 // boundary: the group that completes a layer's rotations is followed by that layer's
@@ -149,6 +151,10 @@ struct DensePlan {
     std::vector<DenseXTermDev> all_terms;   // every term (plain per-gate path measures them one by one)
     std::vector<DensePassClassDev> pcd;     // per (pass, group, class): split counts
     std::vector<int32_t> stage;             // per pass: classes staged in shared memory
+    // adjoint: for parameter p, entries adj_idx[adj_off[p] .. adj_off[p+1]) are the
+    // (pass * kDenseAdjSlots + slot) gradient slots that carry it, in a fixed order
+    std::vector<int32_t> adj_off;
+    std::vector<int32_t> adj_idx;
     int max_classes_per_layer = 0;
     int max_dists = 0;
     bool fits_fused = true;                 // staged class data fits the pass kernel's shared memory
@@ -193,7 +199,6 @@ struct Plan {
     std::vector<ConeDev> cones;           // one per term group (shared window)
     std::vector<MeasDev> meas;            // measured terms of all cones
     std::vector<int32_t> group_wtrue;     // true width of each group's window
-    std::vector<double> cone_cost;        // estimated work of each cone (longest first within a width)
     std::vector<int32_t> prog;            // programs of all cones
     std::vector<int32_t> cone_gates;      // gates in each cone (introspection)
     std::vector<int32_t> cone_lo;         // window start per term
@@ -325,6 +330,9 @@ struct DenseLaunch {
     int32_t n_zterms = 0;
     const DenseXTermDev* xterms = nullptr;
     int32_t n_xterms = 0;
+    const DenseXTermDev* all_terms = nullptr;   // device copy (per-gate adjoint)
+    const int32_t* adj_off = nullptr;           // DensePlan::adj_off / adj_idx (device)
+    const int32_t* adj_idx = nullptr;
     const int32_t* tab_gate = nullptr;
     const int32_t* tab_mult = nullptr;
     int32_t tab_entries = 0;
@@ -339,8 +347,11 @@ struct DenseLaunch {
     double* partial = nullptr;            // per-CTA / per-block partial sums
     double* xpart = nullptr;              // [n_xterms] per set
     int32_t* err = nullptr;               // kernel error word
+    void* lam = nullptr;                  // gradient mode: 2^n_eff float2 adjoint state
+    double* gpart = nullptr;              // gradient mode: [n_passes][kDenseAdjSlots][grid] partials
     // outputs
     double* energy = nullptr;             // [B]
+    double* grad = nullptr;               // [B][n_params] or null (energies only)
     bool per_gate = false;                // plain per-gate sweeps (baseline)
     int sm_count = 0;
     void* ev_begin = nullptr;
@@ -354,6 +365,7 @@ struct DenseLaunch {
     int32_t n_all_terms = 0;
 };
 size_t dense_partial_count(int n_eff);
+int dense_grid(int n_eff, int sm_count);
 
 int launch_dense(DenseLaunch& L, void* stream);
 

@@ -201,7 +201,6 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
     P->cone_ndiag.assign(NG, 0);
     P->cone_npdiag.assign(NG, 0);
     P->group_wtrue.assign(NG, 0);
-    P->cone_cost.assign(NG, 0.0);
     // ---- phase 3: one program per group ----
     for (int t = 0; t < NG; ++t) {
         std::sort(members[t].begin(), members[t].end());
@@ -312,7 +311,6 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                     }
                 }
                 if (any_diag) P->cone_ndiag[t] += 1;
-                P->cone_cost[t] += (double)(__builtin_popcount(live) + (any_diag ? 1 : 0)) * (double)(1 << W);
                 body[hdr + 0] = any_diag ? 1 : 0;
                 body[hdr + 1] = (int32_t)live;
                 body[hdr + 2] = 0;
@@ -326,7 +324,6 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
         P->prog.insert(P->prog.end(), body.begin(), body.end());
         cd.nslots = nslot;
         slot_total += nslot;
-        P->cone_cost[t] += (double)members[t].size() * (double)(1 << W);
         cd.mterm_off = (int32_t)P->meas.size();
         cd.nmterms = (int32_t)members[t].size();
         for (int m : members[t]) {
@@ -684,6 +681,31 @@ std::shared_ptr<DensePlan> make_dense_plan(const Circuit& c, const Ham& h, std::
             }
         }
         pass.nstage = (int32_t)D->stage.size() - pass.stage_off;
+    }
+    // adjoint slots: rotation k of group g -> 4g + k; staged class ci (kind 0, a parameter) ->
+    // 4 * kDenseMaxGroups + ci; collected per parameter with a counting sort (pass-major order)
+    {
+        std::vector<std::pair<int32_t, int32_t>> ent;   // (param, pass * slots + slot)
+        for (int pi = 0; pi < (int)D->passes.size(); ++pi) {
+            const DensePassDev& pass = D->passes[pi];
+            for (int g = 0; g < pass.ngroups; ++g)
+                for (int k = 0; k < 4; ++k) {
+                    const int gate = pass.gate[g][k];
+                    if (gate >= 0 && c.gates[gate].param >= 0)
+                        ent.push_back({c.gates[gate].param, pi * kDenseAdjSlots + 4 * g + k});
+                }
+            for (int ci = 0; ci < pass.nstage && ci < kDenseMaxLayerClasses; ++ci) {
+                const DenseClassDev& cl = D->classes[D->stage[pass.stage_off + ci]];
+                if (cl.kind == 0 && c.gates[cl.gate].param >= 0)
+                    ent.push_back({c.gates[cl.gate].param, pi * kDenseAdjSlots + 4 * kDenseMaxGroups + ci});
+            }
+        }
+        D->adj_off.assign(c.n_params + 1, 0);
+        for (auto& e : ent) ++D->adj_off[e.first + 1];
+        for (int p = 0; p < c.n_params; ++p) D->adj_off[p + 1] += D->adj_off[p];
+        D->adj_idx.assign(ent.size(), 0);
+        std::vector<int32_t> fill(D->adj_off.begin(), D->adj_off.end() - 1);
+        for (auto& e : ent) D->adj_idx[fill[e.first]++] = e.second;
     }
     // shared-memory capacity of the pass kernel
     for (const DensePassDev& pass : D->passes) {

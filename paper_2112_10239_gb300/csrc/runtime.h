@@ -36,6 +36,10 @@ struct PlanEntry {
     DenseZTermDev* d_dzterms = nullptr;
     int32_t* d_dtab_gate = nullptr;
     int32_t* d_dtab_mult = nullptr;
+    DenseXTermDev* d_dxterms = nullptr;
+    DenseXTermDev* d_dallterms = nullptr;
+    int32_t* d_dadj_off = nullptr;
+    int32_t* d_dadj_idx = nullptr;
     // work list cache (keyed by batch size and precision)
     int wl_B = -1;
     bool wl_fp64 = false;

@@ -234,3 +234,41 @@ def random_local_problem(n: int, L: int, B: int, seed: int, kinds=("RY", "RX"),
     theta = rng.uniform(0.0, 2.0 * math.pi, size=(B, P))
     return Problem(n=n, gates=gates, n_params=P, terms=terms, theta=theta,
                    name=f"local_n{n}_L{L}", meta={"L": L, "layout": "local"})
+
+
+def random_nonlocal_problem(n: int, L: int, B: int, seed: int) -> Problem:
+    """A layered circuit with two-qubit gates between arbitrary qubit pairs (dense path):
+    per layer RX or RY (drawn per qubit) on every qubit, RZ on a random half, then n
+    two-qubit gates on random pairs, each CZ or RZZ with its own angle; one in five RZ/RZZ
+    reuses the previous parameter (shared angles) and one RZ per layer has a fixed angle.
+    Hamiltonian: 2n random Pauli strings of 1-3 sites over X, Y, Z, coefficients U(-1, 1)."""
+    rng = np.random.default_rng(seed)
+    gates, P = [], 0
+    for _ in range(L):
+        for q in range(n):
+            gates.append((RY if rng.random() < 0.5 else RX, q, -1, P, 0.0))
+            P += 1
+        for q in range(n):
+            if rng.random() < 0.5:
+                if P > 0 and rng.random() < 0.2:
+                    gates.append((RZ, q, -1, P - 1, 0.0))
+                else:
+                    gates.append((RZ, q, -1, P, 0.0))
+                    P += 1
+        gates.append((RZ, int(rng.integers(n)), -1, -1, float(rng.uniform(0, 2 * np.pi))))
+        for _ in range(n if n > 1 else 0):
+            u, v = (int(x) for x in rng.choice(n, 2, replace=False))
+            if rng.random() < 0.5:
+                gates.append((CZ, u, v, -1, 0.0))
+            elif P > 0 and rng.random() < 0.2:
+                gates.append((RZZ, u, v, P - 1, 0.0))
+            else:
+                gates.append((RZZ, u, v, P, 0.0))
+                P += 1
+    terms = []
+    for _ in range(2 * n):
+        k = int(rng.integers(1, min(3, n) + 1))
+        sites = tuple(int(s) for s in rng.choice(n, k, replace=False))
+        terms.append((float(rng.uniform(-1, 1)), sites, "".join("XYZ"[int(rng.integers(3))] for _ in sites)))
+    theta = rng.uniform(0, 2 * np.pi, size=(B, P))
+    return Problem(n=n, gates=gates, n_params=P, terms=terms, theta=theta, name=f"nonlocal_n{n}_L{L}")

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import dense
 from paper_2112_10239_gb300 import workloads as W
-from parity import check_energy
+from parity import check_energy, check_grad
 
 pytestmark = pytest.mark.gpu
 
@@ -134,13 +134,114 @@ def test_plain_per_gate_baseline(plain_ctx, tlq):
     check_energy(Ept, _oracle(t, t.theta))
 
 
-def test_dense_gradient_reports_unsupported(tlq):
+def _grad(ctx, prob, theta=None):
+    from paper_2112_10239_gb300 import binding as B
+    c, h = ctx.problem(prob)
+    try:
+        return B.tlq_expectation_grad(ctx.h, c.h, h.h, prob.theta if theta is None else theta)
+    finally:
+        c.close()
+        h.close()
+
+
+def _oracle_grad(prob, theta):
+    out = [dense.grad_adjoint(prob.n, prob.gates, prob.terms, th, prob.n_params) for th in theta]
+    return np.array([e for e, _ in out]), np.array([g for _, g in out])
+
+
+@pytest.mark.parametrize("n,p,seed", [(10, 1, 0), (12, 2, 1), (14, 3, 2), (16, 4, 3), (18, 4, 5)])
+def test_qaoa_gradient_vs_oracle(tlq, n, p, seed):
+    prob = W.qaoa_problem(n, p, 2, seed)
+    E, g = _grad(tlq, prob)
+    Er, gr = _oracle_grad(prob, prob.theta)
+    check_energy(E, Er)
+    check_grad(g, gr)
+    # the energy of the gradient call equals the energy-only call
+    E2, _ = _energy(tlq, prob)
+    assert np.array_equal(E, E2)
+
+
+def test_qaoa_n24_gradient_vs_oracle(tlq):
+    prob = W.qaoa_problem(24, 4, 1, seed=7)
+    E, g = _grad(tlq, prob)
+    Er, gr = _oracle_grad(prob, prob.theta)
+    check_energy(E, Er)
+    check_grad(g, gr)
+
+
+def test_qaoa_n28_gradient_closed_form(tlq):
+    # full size, p = 1: E = |edges| cos^2 beta, dE/dgamma = 0, dE/dbeta = -|edges| sin 2 beta
+    full = W.qaoa_n28_p4()
+    m = len(full.meta["edges"])
+    one = W.qaoa_problem(28, 1, 3, seed=2, edges=full.meta["edges"])
+    E, g = _grad(tlq, one)
+    check_energy(E, [m * math.cos(b) ** 2 for b in one.theta[:, 1]])
+    want = np.stack([np.zeros(3), -m * np.sin(2 * one.theta[:, 1])], axis=1)
+    check_grad(g, want)
+
+
+def test_qaoa_n28_p4_gradient_fused_equals_plain(plain_ctx, tlq):
+    # full size p = 4: the fused adjoint passes against the plain per-gate adjoint sweeps
+    # (two independent kernel paths), and gamma_1 (a global phase on |0..0>) has zero gradient
+    prob = W.qaoa_n28_p4()
+    E, g = _grad(tlq, prob)
+    Ep, gp = _grad(plain_ctx, prob)
+    check_energy(E, Ep)
+    check_grad(g, gp)
+    assert abs(g[0, 0]) <= 1e-4 * max(1.0, float(np.max(np.abs(g))))
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_nonlocal_mixed_gradients(tlq, seed):
+    # X/Y/Z strings (lam needs the gather kernel), RZ singles, CZ, fixed angles, shared angles
+    rng = np.random.default_rng(70 + seed)
+    prob = W.random_nonlocal_problem(int(rng.integers(3, 15)), int(rng.integers(1, 4)), 2, 300 + seed)
+    E, g = _grad(tlq, prob)
+    Er, gr = _oracle_grad(prob, prob.theta)
+    check_energy(E, Er)
+    check_grad(g, gr)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_tiny_dense_gradient(tlq, n):
+    gates = [(W.RY, q, -1, q, 0.0) for q in range(n)] + [(W.RX, q, -1, n + q, 0.0) for q in range(n)]
+    P = 2 * n
+    if n >= 3:
+        gates.append((W.RZZ, 0, 2, P, 0.0))
+        gates.append((W.RY, 1, -1, P + 1, 0.0))
+        P += 2
+    terms = [(1.0, (0,), "X")] + ([(0.5, (0, n - 1), "ZZ"), (-0.25, (n - 1,), "Y")] if n > 1 else [])
+    theta = np.random.default_rng(n).uniform(0, 6, size=(2, P))
+    prob = W.Problem(n=n, gates=gates, n_params=P, terms=terms, theta=theta)
+    E, g = _grad(tlq, prob)
+    Er, gr = _oracle_grad(prob, theta)
+    check_energy(E, Er)
+    check_grad(g, gr)
+
+
+def test_plain_per_gate_gradient(plain_ctx, tlq):
+    for prob in (W.qaoa_problem(14, 3, 2, seed=12), W.random_nonlocal_problem(9, 2, 2, seed=5),
+                 W.tfim_problem(10, 3, 2, seed=1, h_range=(0.5, 1.5))):
+        E, g = _grad(plain_ctx, prob)
+        Er, gr = _oracle_grad(prob, prob.theta)
+        check_energy(E, Er)
+        check_grad(g, gr)
+
+
+def test_dense_gradient_deterministic(tlq):
+    prob = W.qaoa_problem(20, 4, 2, seed=9)
+    a = _grad(tlq, prob)
+    b = _grad(tlq, prob)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_dense_fp64_reports_unsupported(tlq):
     from paper_2112_10239_gb300 import binding as B
     prob = W.qaoa_problem(10, 1, 1, seed=0)
     c, h = tlq.problem(prob)
     try:
         with pytest.raises(B.TLQError) as ei:
-            B.tlq_expectation_grad(tlq.h, c.h, h.h, prob.theta)
+            B.tlq_expectation_grad(tlq.h, c.h, h.h, prob.theta, B.TLQ_FP64_REF)
         assert ei.value.status == B.TLQ_EUNSUPPORTED
     finally:
         c.close()

@@ -233,6 +233,10 @@ def test_qaoa_closed_forms(seed):
     for th in p.theta:
         # p = 1 from |0..0>: RZZ is a global phase, so E = |edges| cos^2 beta.
         assert dense.energy(n, p.gates, p.terms, th) == pytest.approx(m * math.cos(th[1]) ** 2, abs=1e-12)
+        # and its gradient: dE/dgamma_1 = 0 (a global phase), dE/dbeta_1 = -|edges| sin(2 beta)
+        _, g = dense.grad_adjoint(n, p.gates, p.terms, th, p.n_params)
+        assert g[0] == pytest.approx(0.0, abs=1e-12)
+        assert g[1] == pytest.approx(-m * math.sin(2 * th[1]), abs=1e-12)
     q = W.qaoa_problem(n, 3, 1, seed)
     th = q.theta[0].copy()
     th[1::2] = 0.0   # every beta = 0: the state stays |0..0> up to phase
