@@ -11,10 +11,12 @@ Layout:
   * ``windows``      -- per-term light-cone windows for nearest-neighbour circuits that are
                         too wide for a full statevector (naive gate-by-gate support tracking).
   * ``ed``           -- exact diagonalisation with an explicit 2^n x 2^n Hamiltonian (n <= 10).
+  * ``density``      -- reduced density operators of pure states (the partial trace by its
+                        definition, TensorLy-Quantum Sec. 2 / Sec. 3).
 """
 from .dense import (energy, energy_terms, grad_adjoint, grad_param_shift, grad_fd,
                     statevector, pauli_expectation)
-from . import windows, ed
+from . import windows, ed, density
 
 __all__ = ["energy", "energy_terms", "grad_adjoint", "grad_param_shift", "grad_fd",
-           "statevector", "pauli_expectation", "windows", "ed"]
+           "statevector", "pauli_expectation", "windows", "ed", "density"]

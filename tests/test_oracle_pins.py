@@ -280,3 +280,80 @@ def test_relabel_invariance():
     mt = [(c, tuple(n - 1 - s for s in sites), l) for (c, sites, l) in p.terms]
     assert dense.energy(n, mg, mt, p.theta[0]) == pytest.approx(
         dense.energy(n, p.gates, p.terms, p.theta[0]), abs=1e-13)
+
+
+# ---- partial trace (reduced density operators of pure states) ---------------------------
+
+_PAULI = {"I": np.eye(2), "X": np.array([[0, 1], [1, 0]], dtype=complex),
+          "Y": np.array([[0, -1j], [1j, 0]]), "Z": np.diag([1.0, -1.0]).astype(complex)}
+
+
+def _kron_sites(mats_by_site, keep):
+    """Operator on the kept qubits with bit t of the index = qubit keep[t]."""
+    out = np.eye(1, dtype=complex)
+    for q in sorted(keep, reverse=True):   # most significant factor first
+        out = np.kron(out, mats_by_site[q])
+    return out
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_partial_trace_product_state(seed):
+    # |psi> = prod_q RZ(b_q) RY(a_q) |0>: every reduced state is the product of the
+    # single-qubit states phi_q = (cos(a/2) e^{-ib/2}, sin(a/2) e^{ib/2}).
+    from oracle import density
+    rng = np.random.default_rng(seed)
+    n = 6
+    a, b = rng.uniform(0, 2 * np.pi, n), rng.uniform(0, 2 * np.pi, n)
+    gates = [(W.RY, q, -1, q, 0.0) for q in range(n)] + [(W.RZ, q, -1, n + q, 0.0) for q in range(n)]
+    psi = dense.statevector(n, gates, np.concatenate([a, b]))
+    phi = {q: np.array([math.cos(a[q] / 2) * np.exp(-0.5j * b[q]), math.sin(a[q] / 2) * np.exp(0.5j * b[q])])
+           for q in range(n)}
+    for keep in ([0], [2], [1, 4], [0, 3, 5], list(range(n))):
+        rho = density.reduced_density(psi, n, keep)
+        want = _kron_sites({q: np.outer(phi[q], phi[q].conj()) for q in keep}, keep)
+        assert np.max(np.abs(rho - want)) < 1e-13
+
+
+def test_partial_trace_bell_and_ghz():
+    from oracle import density
+    half = math.pi / 2
+    bell = dense.statevector(2, [(W.RY, 0, -1, -1, half), (W.RY, 1, -1, -1, half), (W.CZ, 0, 1, -1, 0.0),
+                                 (W.RY, 1, -1, -1, -half)], [0.0])
+    for keep in ([0], [1]):
+        assert np.max(np.abs(density.reduced_density(bell, 2, keep) - np.eye(2) / 2)) < 1e-14
+    n = 5
+    gates = [(W.RY, 0, -1, -1, half)]
+    for t in range(1, n):
+        gates += [(W.RY, t, -1, -1, half), (W.CZ, t - 1, t, -1, 0.0), (W.RY, t, -1, -1, -half)]
+    ghz = dense.statevector(n, gates, [0.0])
+    rho = density.reduced_density(ghz, n, [3, 0])
+    want = np.zeros((4, 4))
+    want[0, 0] = want[3, 3] = 0.5
+    assert np.max(np.abs(rho - want)) < 1e-14
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_partial_trace_properties_and_pauli_expectations(seed):
+    # random entangled state: rho_A is Hermitian, PSD, of unit trace, and Tr(rho_A P_A)
+    # equals <psi|P_A|psi> evaluated on the full state by the C oracle
+    from oracle import density
+    rng = np.random.default_rng(40 + seed)
+    prob = W.random_nonlocal_problem(7, 2, 1, seed=seed)
+    psi = dense.statevector(prob.n, prob.gates, prob.theta[0])
+    for _ in range(4):
+        m = int(rng.integers(1, prob.n + 1))
+        keep = sorted(int(q) for q in rng.choice(prob.n, m, replace=False))
+        rho = density.reduced_density(psi, prob.n, keep)
+        assert abs(np.trace(rho) - 1) < 1e-13
+        assert np.max(np.abs(rho - rho.conj().T)) < 1e-14
+        assert np.min(np.linalg.eigvalsh(rho)) > -1e-13
+        for _ in range(3):
+            k = int(rng.integers(1, m + 1))
+            sites = [int(q) for q in rng.choice(keep, k, replace=False)]
+            letters = "".join("XYZ"[int(rng.integers(3))] for _ in sites)
+            P = _kron_sites({q: _PAULI[letters[sites.index(q)]] if q in sites else _PAULI["I"] for q in keep}, keep)
+            want = dense.pauli_expectation(prob.n, psi, sites, letters)
+            assert abs(np.trace(rho @ P).real - want) < 1e-13
+    # keeping every qubit gives the pure density operator itself
+    full = density.reduced_density(psi, prob.n, range(prob.n))
+    assert np.max(np.abs(full - np.outer(psi, psi.conj()))) < 1e-15
