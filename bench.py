@@ -399,8 +399,61 @@ def extra_workloads(B, dev, local, flush, peaks):
         "launches": res["fused_grad"][2],
         "roofline": hbm("fused_grad", "forward dense_pass_kernel x passes, then dense_adjoint_kernel x passes "
                                       "(psi and lam read + written)")}
+    # partial traces of an n=20 state down to m=14 and m=10 qubits (the paper's density-operator
+    # sizes): rho_A = Psi Psi^dagger; FP32 ALU-bound (m=14 also writes a 2 GiB output)
+    out.update(partial_trace_workloads(B, dev, local, flush, peaks))
     # serving: Poisson arrivals, continuous batching vs one request at a time
     out["serving"] = serving_replay(B, local, 2000, 2000.0)
+    return out
+
+
+def partial_trace_workloads(B, dev, local, flush, peaks, n=20, ms=(14, 10), steps=10):
+    """Device time of tlq_partial_trace_dev on a seeded random n-qubit state, and the oracle
+    (numpy: one reshape/transpose and one complex128 matrix product) on the host."""
+    import torch
+    from oracle import density
+    rng = np.random.default_rng(11)
+    psi = rng.normal(size=2 ** n) + 1j * rng.normal(size=2 ** n)
+    psi /= np.linalg.norm(psi)
+    psi_d = torch.tensor(psi.astype(np.complex64).view(np.float32), device=dev)
+    peak = 152 * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    out = {}
+    with B.Context(device=local) as ctx:
+        B.tlq_profile_enable(ctx.h, True)
+        stream = torch.cuda.current_stream(dev)
+        for m in ms:
+            keep = list(range(n - m, n)) if m == ms[0] else list(range(m))
+            rho_d = torch.empty(2 * 4 ** m, dtype=torch.float32, device=dev)
+            for _ in range(3):
+                B.tlq_partial_trace_dev(ctx.h, psi_d.data_ptr(), n, keep, rho_d.data_ptr(), stream.cuda_stream)
+            torch.cuda.synchronize()
+            t, kt = [], []
+            for _ in range(steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                B.tlq_partial_trace_dev(ctx.h, psi_d.data_ptr(), n, keep, rho_d.data_ptr(), stream.cuda_stream)
+                b.record(stream)
+                kms, nl = B.tlq_profile_last(ctx.h)
+                b.synchronize()
+                t.append(a.elapsed_time(b))
+                kt.append(kms)
+            D, K = 2 ** m, 2 ** (n - m)
+            flops = 8.0 * D * (D + 1) / 2 * K      # Hermitian half of rho = Psi Psi^dagger
+            kms = float(np.median(kt))
+            t0 = time.perf_counter()
+            density.reduced_density(psi, n, keep)
+            cpu_s = time.perf_counter() - t0
+            del rho_d
+            out[f"partial_trace_n{n}_m{m}"] = {
+                "value": 1e3 / float(np.median(t)), "unit": "traces/s", "ms": float(np.median(t)), "launches": nl,
+                "keep": f"qubits {keep[0]}..{keep[-1]}",
+                "roofline": {"bound": "alu", "achieved": flops / (kms * 1e-3) / 1e12, "peak": peak,
+                             "unit": "TFLOP/s", "frac": flops / (kms * 1e-3) / 1e12 / peak, "kernel_ms": kms,
+                             "output_bytes": 8 * D * D,
+                             "output_write_floor_ms": 8 * D * D / (float(peaks["hbm_gbs"]) * 1e9) * 1e3},
+                "cpu_baseline": {"value": 1.0 / cpu_s, "unit": "traces/s", "kind": "oracle",
+                                 "cores": len(os.sched_getaffinity(0)), "sample": "one full trace (numpy complex128)"}}
     return out
 
 

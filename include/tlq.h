@@ -190,6 +190,40 @@ const char* tlq_last_error(tlq_ctx ctx);
 
 /* ---- introspection (host-side; no device work) -------------------------------------- */
 
+/* Partial trace of a pure state (Sec. 2: partial traces of density operators; Sec. 3,
+ * Fig. 1 left: full-rank partial traces from n to m qubits): for rho = |psi><psi| and the
+ * kept qubits A = keep[0..m) (any order, distinct),
+ *   rho_A[i][j] = sum_k psi(i, k) conj(psi(j, k)),
+ * where psi(i, k) is the amplitude whose kept qubits hold the bits of i and whose traced
+ * qubits hold the bits of k. Bit q of a state index is qubit q; bit t of i (and j) is the
+ * t-th lowest kept qubit, bit u of k the u-th lowest traced qubit.
+ * psi_dev: device, 2^n complex64 as interleaved (re, im) floats, 1 <= n <= 31, not modified.
+ * rho_dev: device, 2^m x 2^m complex64 row-major (interleaved), 1 <= m <= min(n, 15); the
+ * full matrix is written and is exactly Hermitian (real diagonal; each entry below the
+ * diagonal is the conjugate of its mirror). keep: host array of m qubit indices, read
+ * during the call.
+ * Work is enqueued on cuda_stream (NULL = the context's stream) without synchronising; a
+ * workspace of about 8 * 2^n bytes is taken from the context (plus 8 * 4^m bytes per k-range
+ * split when the output is small). Outputs of m >= 7 run on the tensor cores (TF32 operands
+ * split into high and low parts, three products each, FP32 accumulation: about 2^-20
+ * relative error per product), smaller ones on FP32 CUDA cores; results are deterministic.
+ * A tensor-core wait that gives up (after about a second) leaves the output incomplete and
+ * sets the context's kernel error word, which tlq_reduced_density reports as EKERNEL.
+ * EINVAL: NULL pointers, n or m out of range, a kept qubit out of range or repeated. */
+tlq_status tlq_partial_trace_dev(tlq_ctx ctx, const float* psi_dev, int32_t n, const int32_t* keep, int32_t m,
+                                 float* rho_dev, void* cuda_stream);
+
+/* Reduced density operator of a circuit's output state on the kept qubits (Sec. 2):
+ * rho_A of U(theta)|0..0> as above, for one parameter set theta (host, [n_params] FP64).
+ * rho: host, 2^m x 2^m complex128 row-major as interleaved (re, im) doubles, 1 <= m <= 14.
+ * Circuits on n <= 31 qubits run on the dense statevector path; a nearest-neighbour circuit
+ * on more qubits is simulated on the window of the kept qubits' backward light cone (exact:
+ * gates outside the cone do not change rho_A), which must span at most 31 qubits.
+ * Synchronous; FP32 state and sums. EINVAL as for tlq_partial_trace_dev; EUNSUPPORTED for a
+ * non-local circuit on more than 31 qubits or a light cone wider than 31 qubits. */
+tlq_status tlq_reduced_density(tlq_ctx ctx, tlq_circuit c, const double* theta, const int32_t* keep, int32_t m,
+                               double* rho);
+
 typedef enum { TLQ_PATH_CONE = 0, TLQ_PATH_DENSE = 1 } tlq_path;
 
 /* Plan summary for (c, h): the chosen path; for the cone path, per term t < n_terms the

@@ -28,7 +28,7 @@ SYMBOLS = ["tlq_init", "tlq_destroy", "tlq_circuit_create", "tlq_circuit_destroy
            "tlq_expectation_grad", "tlq_expectation_grad_dev", "tlq_submit", "tlq_poll",
            "tlq_last_error", "tlq_plan_info", "tlq_plan_cone_stats", "tlq_profile_enable",
            "tlq_profile_last", "tlq_serving_stats", "tlq_version", "tlq_expectation_grad_static",
-           "tlq_plan_dense_info"]
+           "tlq_plan_dense_info", "tlq_partial_trace_dev", "tlq_reduced_density"]
 
 
 class tlq_gate(ctypes.Structure):
@@ -82,6 +82,8 @@ def lib():
         L.tlq_plan_info.argtypes = [vp, vp, vp, ip, ip, ip, ip]
         L.tlq_plan_cone_stats.argtypes = [vp, vp, vp, ip, ip, ip, ip, ip, ip, ip]
         L.tlq_plan_dense_info.argtypes = [vp, vp, vp, ip, ip, ip, ip]
+        L.tlq_partial_trace_dev.argtypes = [vp, vp, ctypes.c_int32, ip, ctypes.c_int32, vp, vp]
+        L.tlq_reduced_density.argtypes = [vp, vp, dp, ip, ctypes.c_int32, dp]
         L.tlq_profile_enable.argtypes = [vp, ctypes.c_int]
         L.tlq_profile_last.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ip]
         L.tlq_expectation_grad_static.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp, vp, vp]
@@ -257,6 +259,24 @@ def tlq_plan_dense_info(ctx, circ, ham):
     v = [ctypes.c_int32() for _ in range(4)]
     _check(lib().tlq_plan_dense_info(ctx, circ, ham, *[ctypes.byref(x) for x in v]), ctx)
     return tuple(x.value for x in v)
+
+
+def tlq_partial_trace_dev(ctx, psi_ptr, n, keep, rho_ptr, stream_ptr=None):
+    """Device-pointer partial trace: psi_ptr -> 2^n complex64, rho_ptr -> 2^m x 2^m complex64."""
+    k = np.ascontiguousarray(keep, dtype=np.int32)
+    _check(lib().tlq_partial_trace_dev(ctx, psi_ptr, n, k.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(k),
+                                       rho_ptr, stream_ptr), ctx)
+
+
+def tlq_reduced_density(ctx, circ, theta, keep):
+    """rho_A (complex128 [2^m, 2^m]) of the circuit's output state for one parameter set."""
+    k = np.ascontiguousarray(keep, dtype=np.int32)
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
+    rho = np.zeros((1 << len(k), 1 << len(k)), dtype=np.complex128)
+    _check(lib().tlq_reduced_density(ctx, circ, _dptr(th) if th.size else None,
+                                     k.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(k),
+                                     _dptr(rho.view(np.float64))), ctx)
+    return rho
 
 
 def tlq_profile_enable(ctx, on=True):

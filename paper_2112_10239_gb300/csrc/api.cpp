@@ -229,7 +229,8 @@ size_t dense_workspace_bytes(const PlanEntry& pe, const Circuit& c, int B, bool 
 }
 
 static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const double* theta_dev, int B,
-                            double* energy_dev, double* grad_dev, bool per_gate, void* stream, Workspace* ws) {
+                            double* energy_dev, double* grad_dev, bool per_gate, void* stream, Workspace* ws,
+                            void** state_out = nullptr) {
     const DensePlan& D = *pe.plan->dense;
     const bool grad = grad_dev != nullptr;
     const size_t need = dense_workspace_bytes(pe, c, B, grad, ctx->sm_count);
@@ -261,6 +262,7 @@ static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const
     L.gate_table = ws->take((size_t)B * std::max<size_t>(1, c.gates.size()) * 8);
     L.phase_tab = ws->take((size_t)B * std::max<size_t>(1, D.tab_gate.size()) * 8);
     L.state = ws->take(((size_t)1 << D.n_eff) * 8);
+    if (state_out) *state_out = L.state;
     L.partial = (double*)ws->take(dense_partial_count(D.n_eff) * sizeof(double));
     if (grad) {
         L.lam = ws->take(((size_t)1 << D.n_eff) * 8);
@@ -677,6 +679,159 @@ tlq_status tlq_expectation_grad_dev(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const
     }
     TLQ_TRY(reserve(ctx, work + 4096));
     return run_device(ctx, c, h, theta_dev, B, prec, energy_dev, grad_dev, st, &ctx->ws);
+}
+
+// ---- reduced density operators ----------------------------------------------------------
+
+// Validates keep[0..m) against n qubits and returns it sorted ascending.
+static tlq_status check_keep(int n, const int32_t* keep, int32_t m, std::vector<int32_t>* sorted) {
+    if (!keep) { set_error("keep is NULL"); return TLQ_EINVAL; }
+    if (m < 1 || m > n) { set_error("m must be in [1, n]"); return TLQ_EINVAL; }
+    if (m > kMaxDensityQubits) {
+        set_error("at most " + std::to_string(kMaxDensityQubits) + " kept qubits");
+        return TLQ_EINVAL;
+    }
+    sorted->assign(keep, keep + m);
+    for (int32_t q : *sorted)
+        if (q < 0 || q >= n) { set_error("kept qubit out of range"); return TLQ_EINVAL; }
+    std::sort(sorted->begin(), sorted->end());
+    for (int t = 1; t < m; ++t)
+        if ((*sorted)[t] == (*sorted)[t - 1]) { set_error("kept qubit listed twice"); return TLQ_EINVAL; }
+    return TLQ_OK;
+}
+
+// Kept / traced qubit lists of a state on n <= 31 qubits (keep validated and sorted).
+static QubitMap keep_map(int n, const std::vector<int32_t>& keep) {
+    QubitMap Q{};
+    std::vector<char> in(n, 0);
+    for (int32_t q : keep) in[q] = 1;
+    int a = 0, b = 0;
+    for (int q = 0; q < n && q < 32; ++q) {
+        if (in[q]) Q.kept[a++] = q;
+        else Q.traced[b++] = q;
+    }
+    return Q;
+}
+
+tlq_status tlq_partial_trace_dev(tlq_ctx ctx, const float* psi_dev, int32_t n, const int32_t* keep, int32_t m,
+                                 float* rho_dev, void* cuda_stream) {
+    if (!ctx) { set_error("NULL context"); return TLQ_EINVAL; }
+    if (!psi_dev || !rho_dev) { set_error("NULL device pointer"); return TLQ_EINVAL; }
+    if (n < 1 || n > kDenseMaxQubits) { set_error("n must be in [1, 31]"); return TLQ_EINVAL; }
+    std::vector<int32_t> ks;
+    TLQ_TRY(check_keep(n, keep, m, &ks));
+    if (ctx->host_only()) { set_error("host-only context"); return TLQ_EUNSUPPORTED; }
+    const QubitMap Q = keep_map(n, ks);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TLQ_CUDA(cudaSetDevice(ctx->device));
+    const size_t work = partial_trace_workspace_bytes(n, m, ctx->sm_count);
+    if (ctx->ws.cap < work + 4096) TLQ_CUDA(cudaDeviceSynchronize());
+    TLQ_TRY(reserve(ctx, work + 4096));
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : (cudaStream_t)ctx->stream;
+    if (ctx->profile) TLQ_CUDA(cudaEventRecord((cudaEvent_t)ctx->prof_ev[0], st));
+    int nl = 0;
+    const int rc = launch_partial_trace(psi_dev, n, Q, m, rho_dev, ctx->ws.take(work), ctx->sm_count, ctx->d_err, st, &nl);
+    if (ctx->profile) TLQ_CUDA(cudaEventRecord((cudaEvent_t)ctx->prof_ev[1], st));
+    ctx->last_launches = nl;
+    if (rc != 0) {
+        set_error(std::string("partial trace launch: ") + cudaGetErrorString((cudaError_t)rc));
+        return TLQ_ECUDA;
+    }
+    return TLQ_OK;
+}
+
+tlq_status tlq_reduced_density(tlq_ctx ctx, tlq_circuit c, const double* theta, const int32_t* keep, int32_t m,
+                               double* rho) {
+    if (!ctx || !c) { set_error("NULL handle"); return TLQ_EINVAL; }
+    if (!rho) { set_error("rho is NULL"); return TLQ_EINVAL; }
+    if (!theta && c->n_params > 0) { set_error("theta is NULL"); return TLQ_EINVAL; }
+    std::vector<int32_t> kq;
+    TLQ_TRY(check_keep(c->n, keep, m, &kq));
+    if (m > kMaxDensityQubits - 1) { set_error("at most 14 kept qubits through the host API"); return TLQ_EINVAL; }
+    if (ctx->host_only()) { set_error("host-only context"); return TLQ_EUNSUPPORTED; }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TLQ_CUDA(cudaSetDevice(ctx->device));
+    // the state to trace: the whole circuit (n <= 31), or for a nearest-neighbour circuit the
+    // window of the kept qubits' backward light cone, simulated from |0..0> on its own
+    Circuit* src = c;
+    std::unique_ptr<Circuit> sub;
+    if (c->n > kDenseMaxQubits) {
+        if (!c->nearest_neighbour) {
+            set_error("reduced density of a non-local circuit on more than 31 qubits");
+            return TLQ_EUNSUPPORTED;
+        }
+        int lo = 0, hi = 0;
+        const std::vector<int> gates = light_cone_gates(*c, std::vector<int>(kq.begin(), kq.end()), &lo, &hi);
+        if (hi - lo + 1 > kDenseMaxQubits) {
+            set_error("light cone of the kept qubits wider than 31 qubits");
+            return TLQ_EUNSUPPORTED;
+        }
+        sub.reset(new Circuit());
+        sub->ctx = ctx;
+        sub->n = hi - lo + 1;
+        sub->n_params = c->n_params;
+        for (int g : gates) {
+            tlq_gate G = c->gates[g];
+            G.q0 -= lo;
+            if (G.q1 >= 0) G.q1 -= lo;
+            sub->gates.push_back(G);
+        }
+        plan_circuit_layers(*sub);
+        sub->id = ctx->next_id++;
+        for (int32_t& q : kq) q -= lo;
+        src = sub.get();
+    }
+    Ham empty;
+    empty.ctx = ctx;
+    empty.n = src->n;
+    empty.id = 0;
+    std::shared_ptr<PlanEntry> pe;
+    tlq_status s = get_plan(ctx, src, &empty, &pe);
+    auto drop_sub = [&]() { if (sub) evict_plans(ctx, sub->id, ~(uint64_t)0); };
+    if (s != TLQ_OK) { drop_sub(); return s; }
+    const DensePlan& D = *pe->plan->dense;
+    const QubitMap Q = keep_map(D.n_eff, kq);
+    const size_t P = (size_t)std::max(1, src->n_params);
+    const size_t rho_b = ((size_t)8 << (2 * m));
+    const size_t work = dense_workspace_bytes(*pe, *src, 1, false, ctx->sm_count) +
+                        partial_trace_workspace_bytes(D.n_eff, m, ctx->sm_count) + P * 8 + 8 + rho_b + 8192;
+    if ((s = reserve(ctx, work)) != TLQ_OK || (s = ensure_pinned(ctx, std::max(rho_b, P * 8) + 64)) != TLQ_OK) {
+        drop_sub();
+        return s;
+    }
+    cudaStream_t st = (cudaStream_t)ctx->stream;
+    double* d_theta = (double*)ctx->ws.take(P * 8);
+    double* d_e = (double*)ctx->ws.take(8);
+    float* d_rho = (float*)ctx->ws.take(rho_b);
+    char* hp = (char*)ctx->h_pinned;
+    cudaError_t ce = cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), st);
+    if (ce == cudaSuccess && src->n_params > 0) {
+        std::memcpy(hp, theta, (size_t)src->n_params * 8);
+        ce = cudaMemcpyAsync(d_theta, hp, (size_t)src->n_params * 8, cudaMemcpyHostToDevice, st);
+    }
+    void* state = nullptr;
+    if (ce == cudaSuccess)
+        s = run_dense(ctx, *pe, *src, d_theta, 1, d_e, nullptr, ctx->cfg.fuse_k == 1 || !D.fits_fused, st, &ctx->ws,
+                      &state);
+    if (ce == cudaSuccess && s == TLQ_OK) {
+        const size_t pt = partial_trace_workspace_bytes(D.n_eff, m, ctx->sm_count);
+        int nl = 0;
+        const int rc = launch_partial_trace(state, D.n_eff, Q, m, d_rho, ctx->ws.take(pt), ctx->sm_count, ctx->d_err, st, &nl);
+        ce = (cudaError_t)rc;
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(hp, d_rho, rho_b, cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(hp + rho_b, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    }
+    drop_sub();
+    if (s != TLQ_OK) return s;
+    if (ce != cudaSuccess) { set_error(std::string("reduced density: ") + cudaGetErrorString(ce)); return TLQ_ECUDA; }
+    int32_t kerr = 0;
+    std::memcpy(&kerr, hp + rho_b, sizeof(int32_t));
+    if (kerr != 0) { set_error("kernel error word " + std::to_string(kerr)); return TLQ_EKERNEL; }
+    const float* f = (const float*)hp;
+    const size_t entries = (size_t)2 << (2 * m);
+    for (size_t e = 0; e < entries; ++e) rho[e] = (double)f[e];
+    return TLQ_OK;
 }
 
 tlq_status tlq_plan_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* path, int32_t* lo, int32_t* w,

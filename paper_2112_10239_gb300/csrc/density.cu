@@ -1,0 +1,472 @@
+// Reduced density operators of pure states (TensorLy-Quantum Sec. 2: partial traces of
+// density operators; Sec. 3, Fig. 1 left: full-rank partial traces from n to m qubits).
+//
+// For rho = |psi><psi| and a kept qubit set A (m qubits) with complement B,
+//   rho_A[i][j] = sum_k Psi[i][k] conj(Psi[j][k]),   Psi[i][k] = psi(kept bits i, traced bits k),
+// i.e. rho_A = Psi Psi^dagger with Psi a 2^m x 2^(n-m) matrix: a Hermitian rank-K update.
+// Two kernels:
+//   * psi_gather_kernel lays Psi out row-major (row i contiguous in k) from the state, where
+//     bit t of i is the t-th lowest kept qubit and bit u of k the u-th lowest traced one;
+//   * herk_tile_kernel computes 64 x 64 output tiles of the upper block triangle with 4 x 4
+//     complex register blocks per thread from 16-wide k chunks staged in shared memory, and
+//     writes every entry above the diagonal twice (as computed, and conjugate-transposed below
+//     it) and the diagonal as real numbers, so the output is exactly Hermitian. When the
+//     output has few tiles (small m, long k) the k range is split over CTAs; the splits are
+//     summed in a fixed order by herk_reduce_kernel, so results are deterministic.
+// FP32 products and accumulation (the state's precision), complex64 output.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace tlq {
+
+namespace {
+
+constexpr int kTileR = 64;     // output tile edge
+constexpr int kChunkK = 16;    // k chunk staged per step
+constexpr int kHerkThreads = 256;
+
+// Psi[i * K + k] = psi[x(i, k)], x = deposit(i, keep bits) | deposit(k, traced bits).
+__global__ void psi_gather_kernel(const float2* __restrict__ psi, float2* __restrict__ Psi, int n, int m,
+                                  const __grid_constant__ QubitMap Q) {
+    __shared__ int32_t s_kept[32], s_traced[32];
+    if (threadIdx.x < m) s_kept[threadIdx.x] = Q.kept[threadIdx.x];
+    if (threadIdx.x < n - m) s_traced[threadIdx.x] = Q.traced[threadIdx.x];
+    __syncthreads();
+    const uint64_t N = 1ull << n;
+    const int kb = n - m;
+    for (uint64_t y = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; y < N; y += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = y & ((1ull << kb) - 1);
+        const uint64_t i = y >> kb;
+        uint64_t x = 0;
+        for (int t = 0; t < m; ++t) x |= ((i >> t) & 1ull) << s_kept[t];
+        for (int u = 0; u < kb; ++u) x |= ((k >> u) & 1ull) << s_traced[u];
+        Psi[y] = psi[x];
+    }
+}
+
+// Upper block-triangle tile u -> (bi, bj), bi <= bj: u = bj (bj + 1) / 2 + bi.
+__device__ __forceinline__ void tri_tile(uint32_t u, int& bi, int& bj) {
+    int r = (int)((sqrt(8.0 * (double)u + 1.0) - 1.0) * 0.5);
+    while ((uint64_t)(r + 1) * (uint64_t)(r + 2) / 2 <= u) ++r;
+    while ((uint64_t)r * (uint64_t)(r + 1) / 2 > u) --r;
+    bj = r;
+    bi = (int)(u - (uint32_t)((uint64_t)r * (uint64_t)(r + 1) / 2));
+}
+
+// Stage rows [r0, r0 + 64) x k [k0, k0 + 16) of Psi transposed into s[k][row]; rows >= D and
+// k >= kend read as zero.
+__device__ __forceinline__ void load_chunk(const float2* __restrict__ Psi, int64_t D, int64_t K, int64_t r0,
+                                           int64_t k0, int64_t kend, float2 (&reg)[4], int tid) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int idx = tid + kHerkThreads * e;   // 0 .. 1023 = 64 rows x 16 k
+        const int row = idx >> 4, kk = idx & 15;
+        const int64_t r = r0 + row, k = k0 + kk;
+        reg[e] = (r < D && k < kend) ? Psi[r * K + k] : make_float2(0.f, 0.f);
+    }
+}
+
+__device__ __forceinline__ void store_chunk(float2 (*s)[kTileR + 2], const float2 (&reg)[4], int tid) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int idx = tid + kHerkThreads * e;
+        s[idx & 15][idx >> 4] = reg[e];
+    }
+}
+
+// grid.x = upper tiles, grid.y = k splits. out = rho (splits == 1) or partial + split * D * D.
+__global__ void __launch_bounds__(kHerkThreads) herk_tile_kernel(const float2* __restrict__ Psi, int64_t D,
+                                                                  int64_t K, int64_t k_per_split,
+                                                                  float2* __restrict__ out) {
+    __shared__ __align__(16) float2 sA[kChunkK][kTileR + 2];
+    __shared__ __align__(16) float2 sB[kChunkK][kTileR + 2];
+    int bi, bj;
+    tri_tile(blockIdx.x, bi, bj);
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t i0 = (int64_t)bi * kTileR, j0 = (int64_t)bj * kTileR;
+    const int64_t kbeg = (int64_t)blockIdx.y * k_per_split;
+    const int64_t kend = kbeg + k_per_split < K ? kbeg + k_per_split : K;
+    float2* dst = out + (int64_t)blockIdx.y * (gridDim.y > 1 ? D * D : 0);
+
+    float ar[4][4], ai[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) ar[r][c] = ai[r][c] = 0.f;
+
+    float2 ra[4], rb[4];
+    load_chunk(Psi, D, K, i0, kbeg, kend, ra, tid);
+    load_chunk(Psi, D, K, j0, kbeg, kend, rb, tid);
+    for (int64_t k0 = kbeg; k0 < kend; k0 += kChunkK) {
+        __syncthreads();   // the previous chunk has been consumed
+        store_chunk(sA, ra, tid);
+        store_chunk(sB, rb, tid);
+        __syncthreads();
+        if (k0 + kChunkK < kend) {   // prefetch the next chunk while this one is used
+            load_chunk(Psi, D, K, i0, k0 + kChunkK, kend, ra, tid);
+            load_chunk(Psi, D, K, j0, k0 + kChunkK, kend, rb, tid);
+        }
+#pragma unroll
+        for (int kk = 0; kk < kChunkK; ++kk) {
+            float2 a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = sA[kk][ty * 4 + r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = sB[kk][tx * 4 + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    // a * conj(b)
+                    ar[r][c] = fmaf(a[r].x, b[c].x, fmaf(a[r].y, b[c].y, ar[r][c]));
+                    ai[r][c] = fmaf(a[r].y, b[c].x, fmaf(-a[r].x, b[c].y, ai[r][c]));
+                }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t i = i0 + ty * 4 + r;
+        if (i >= D) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t j = j0 + tx * 4 + c;
+            if (j >= D || j < i) continue;   // the upper triangle; the lower one is its mirror
+            if (j == i) {
+                dst[i * D + i] = make_float2(ar[r][c], 0.f);   // rho is Hermitian: real diagonal
+            } else {
+                dst[i * D + j] = make_float2(ar[r][c], ai[r][c]);
+                dst[j * D + i] = make_float2(ar[r][c], -ai[r][c]);
+            }
+        }
+    }
+}
+
+// rho[e] = sum over splits s = 0, 1, ... of partial[s][e] (FP64 sum in split order).
+__global__ void herk_reduce_kernel(const float2* __restrict__ partial, int splits, int64_t DD,
+                                   float2* __restrict__ rho) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < DD; e += (int64_t)gridDim.x * blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int s = 0; s < splits; ++s) {
+            const float2 v = partial[(int64_t)s * DD + e];
+            re += v.x;
+            im += v.y;
+        }
+        rho[e] = make_float2((float)re, (float)im);
+    }
+}
+
+// ---- tensor-core path (tcgen05, TMEM accumulators) ------------------------------------------
+//
+// rho_A = Psi Psi^dagger in real arithmetic with planar operands (re, im of Psi rows):
+//   Re rho = A_re B_re^T + A_im B_im^T,   Im rho = A_im B_re^T + A_re (-B_im)^T,
+// A = rows i of the output tile, B = rows j. Each FP32 operand x is split into TF32 parts
+// x_hi (x with the low 13 mantissa bits cleared, exact in TF32) and x_lo = x - x_hi; every
+// product is x_hi y_hi + x_hi y_lo + x_lo y_hi (the dropped x_lo y_lo is 2^-20 relative),
+// accumulated in FP32 in tensor memory. One CTA (8 warps) owns a 128 x 128 output tile:
+// Re and Im accumulators take 2 x 128 TMEM columns. The k range is walked in chunks of 8
+// complex values, double-buffered in shared memory: all threads load and split a chunk
+// while the tensor core works on the previous one, and thread 0 issues the 12 MMAs of a
+// chunk (M = N = 128, K = 8, kind::tf32) and commits them to that buffer's mbarrier.
+// Shared-memory operands use the no-swizzle K-major layout: 8-row x 16-byte core matrices,
+// 128 bytes apart along K and 256 bytes apart along M/N (one 4 KB tile per operand part).
+
+constexpr int kTcTile = 128;
+constexpr int kTcThreads = 256;
+constexpr int kTcChunk = 8;                         // complex k per stage (one MMA K-step)
+constexpr int kTcPartBytes = kTcTile * kTcChunk * 4; // 4 KB: 128 rows x 8 TF32
+constexpr int kTcParts = 10;                        // A re/im, B re/im, B -im; each hi and lo
+constexpr int kTcStageBytes = kTcParts * kTcPartBytes;
+constexpr int kTcTmemCols = 2 * kTcTile;            // Re and Im accumulators
+constexpr unsigned long long kTcWaitNs = 1000000000ull;   // bound on every mbarrier wait
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_done(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the given phase of an mbarrier, giving up after kTcWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = gtimer();
+    while (!mbar_done(bar, parity)) {
+        if (gtimer() - t0 > kTcWaitNs) return false;
+        __nanosleep(32);
+    }
+    return true;
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading (K-direction) and stride
+// (M/N-direction) byte offsets of the core matrices, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, M = N = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcTile >> 3) << 17) |
+                              ((uint32_t)(kTcTile >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kTcIdesc), "r"(accumulate)
+        : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes, one lane per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// Split 4 complex values of row `row` (k = 4 * half .. +3 of the chunk) into the operand parts
+// at `base` (re hi, re lo, im hi, im lo [, -im hi, -im lo]); 16-byte stores.
+__device__ __forceinline__ void put_row4(unsigned char* base, int row, int half, const float4& p0, const float4& p1,
+                                         bool with_neg) {
+    const int off = (row >> 3) * 256 + half * 128 + (row & 7) * 16;
+    const float re[4] = {p0.x, p0.z, p1.x, p1.z};
+    const float im[4] = {p0.y, p0.w, p1.y, p1.w};
+    float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        rh[e] = tf32_hi(re[e]);
+        rl[e] = re[e] - rh[e];
+        ih[e] = tf32_hi(im[e]);
+        il[e] = im[e] - ih[e];
+    }
+    *reinterpret_cast<float4*>(base + 0 * kTcPartBytes + off) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+    *reinterpret_cast<float4*>(base + 1 * kTcPartBytes + off) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+    *reinterpret_cast<float4*>(base + 2 * kTcPartBytes + off) = make_float4(ih[0], ih[1], ih[2], ih[3]);
+    *reinterpret_cast<float4*>(base + 3 * kTcPartBytes + off) = make_float4(il[0], il[1], il[2], il[3]);
+    if (with_neg) {
+        *reinterpret_cast<float4*>(base + 4 * kTcPartBytes + off) = make_float4(-ih[0], -ih[1], -ih[2], -ih[3]);
+        *reinterpret_cast<float4*>(base + 5 * kTcPartBytes + off) = make_float4(-il[0], -il[1], -il[2], -il[3]);
+    }
+}
+
+__device__ __forceinline__ void load_rows(const float2* __restrict__ Psi, int64_t D, int64_t K, int64_t r0, int64_t k0,
+                                          int64_t kend, int row, int half, float4& p0, float4& p1) {
+    const int64_t r = r0 + row, k = k0 + 4 * half;
+    p0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    p1 = p0;
+    if (r >= D) return;
+    const float2* src = Psi + r * K + k;
+    if (k + 4 <= kend) {
+        p0 = *reinterpret_cast<const float4*>(src);
+        p1 = *reinterpret_cast<const float4*>(src + 2);
+    } else {
+        float2 v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = (k + e < kend) ? src[e] : make_float2(0.f, 0.f);
+        p0 = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        p1 = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    }
+}
+
+// grid.x = upper 128-tiles, grid.y = k splits; out = rho or partial + split * D * D.
+__global__ void __launch_bounds__(kTcThreads, 2) herk_tc_kernel(const float2* __restrict__ Psi, int64_t D, int64_t K,
+                                                                int64_t k_per_split, float2* __restrict__ out,
+                                                                int32_t* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char* stage0 = tc_smem;                                 // 2 stages x 40 KB
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + 2 * kTcStageBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+    int* s_bad = reinterpret_cast<int*>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int bi, bj;
+    tri_tile(blockIdx.x, bi, bj);
+    const int64_t i0 = (int64_t)bi * kTcTile, j0 = (int64_t)bj * kTcTile;
+    const int64_t kbeg = (int64_t)blockIdx.y * k_per_split;
+    const int64_t kend = kbeg + k_per_split < K ? kbeg + k_per_split : K;
+    const int nchunks = (int)((kend - kbeg + kTcChunk - 1) / kTcChunk);
+    float2* dst = out + (int64_t)blockIdx.y * (gridDim.y > 1 ? D * D : 0);
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_bad = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(kTcTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    const int row = tid >> 1, half = tid & 1;   // this thread's row of A and of B, and k half
+    bool bad = false;
+    for (int c = 0; c < nchunks && !bad; ++c) {
+        const int s = c & 1;
+        unsigned char* st = stage0 + s * kTcStageBytes;
+        if (c >= 2) bad = !mbar_wait(su32(&bars[s]), (uint32_t)(((c >> 1) - 1) & 1));   // MMAs of chunk c-2 done
+        if (__syncthreads_or(bad)) { bad = true; break; }
+        const int64_t k0 = kbeg + (int64_t)c * kTcChunk;
+        float4 a0, a1, b0, b1;
+        load_rows(Psi, D, K, i0, k0, kend, row, half, a0, a1);
+        load_rows(Psi, D, K, j0, k0, kend, row, half, b0, b1);
+        put_row4(st, row, half, a0, a1, false);                  // parts 0-3: A re/im hi/lo
+        put_row4(st + 4 * kTcPartBytes, row, half, b0, b1, true);  // parts 4-9: B re/im, -im
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t b = su32(st);
+            auto d = [&](int part) { return sdesc(b + part * kTcPartBytes, 128, 256); };
+            const uint32_t dr = tmem, di = tmem + kTcTile;
+            const uint32_t acc = c > 0 ? 1u : 0u;
+            // Re: A_re B_re + A_im B_im
+            mma_tf32(dr, d(0), d(4), acc);
+            mma_tf32(dr, d(0), d(5), 1u);
+            mma_tf32(dr, d(1), d(4), 1u);
+            mma_tf32(dr, d(2), d(6), 1u);
+            mma_tf32(dr, d(2), d(7), 1u);
+            mma_tf32(dr, d(3), d(6), 1u);
+            // Im: A_im B_re + A_re (-B_im)
+            mma_tf32(di, d(2), d(4), acc);
+            mma_tf32(di, d(2), d(5), 1u);
+            mma_tf32(di, d(3), d(4), 1u);
+            mma_tf32(di, d(0), d(8), 1u);
+            mma_tf32(di, d(0), d(9), 1u);
+            mma_tf32(di, d(1), d(8), 1u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(&bars[s]))
+                         : "memory");
+        }
+    }
+    if (!bad && nchunks > 0) {
+        const int cl = nchunks - 1;
+        bad = !mbar_wait(su32(&bars[cl & 1]), (uint32_t)((cl >> 1) & 1));   // every MMA of the tile done
+    }
+    bad = __syncthreads_or(bad) != 0;
+    if (!bad && nchunks > 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int q = warp & 3, h = warp >> 2;   // TMEM lanes 32q.., columns 64h..
+        const int64_t i = i0 + 32 * q + lane;
+#pragma unroll 1
+        for (int cc = 0; cc < 4; ++cc) {
+            const int col = 64 * h + 16 * cc;
+            float vr[16], vi[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, vr);
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kTcTile + col), vi);
+            if (i >= D) continue;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int64_t j = j0 + col + e;
+                if (j >= D || j < i) continue;
+                if (j == i) {
+                    dst[i * D + i] = make_float2(vr[e], 0.f);
+                } else {
+                    dst[i * D + j] = make_float2(vr[e], vi[e]);
+                    dst[j * D + i] = make_float2(vr[e], -vi[e]);
+                }
+            }
+        }
+    }
+    if (bad && tid == 0) atomicExch(err, 3);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+}
+
+constexpr size_t kTcSmem = 2 * (size_t)kTcStageBytes + 64;
+
+}  // namespace
+
+// Tile and k-split plan shared by the workspace size and the launch: the tensor-core kernel
+// for outputs of at least one 128-tile (m >= 7), the CUDA-core kernel below that; the k range
+// is split (each split a whole number of chunks) until the launch has ~2 CTAs per SM.
+struct HerkPlan {
+    bool tc;
+    int64_t tiles;
+    int splits;
+    int64_t kps;   // k values per split
+};
+
+static HerkPlan herk_plan(int n, int m, int sm_count) {
+    HerkPlan P;
+    P.tc = m >= 7;
+    const int tile = P.tc ? kTcTile : kTileR;
+    const int chunk = P.tc ? kTcChunk : kChunkK;
+    const int64_t D = 1ll << m, K = 1ll << (n - m);
+    const int64_t T = (D + tile - 1) / tile;
+    P.tiles = T * (T + 1) / 2;
+    int64_t s = 1;
+    while (P.tiles * s < 2ll * sm_count && K / (s * 2) >= 8 * chunk) s *= 2;
+    P.kps = ((K + s - 1) / s + chunk - 1) / chunk * chunk;
+    P.splits = (int)((K + P.kps - 1) / P.kps);
+    return P;
+}
+
+int herk_splits(int n, int m, int sm_count) { return herk_plan(n, m, sm_count).splits; }
+
+size_t partial_trace_workspace_bytes(int n, int m, int sm_count) {
+    const int s = herk_splits(n, m, sm_count);
+    size_t b = ((size_t)8 << n) + 256;
+    if (s > 1) b += (size_t)s * ((size_t)8 << (2 * m)) + 256;
+    return b + 1024;
+}
+
+int launch_partial_trace(const void* psi_v, int n, const QubitMap& Q, int m, void* rho_v, void* workspace,
+                         int sm_count, int32_t* err, void* stream, int* launches) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const float2* psi = (const float2*)psi_v;
+    float2* rho = (float2*)rho_v;
+    const int64_t D = 1ll << m, K = 1ll << (n - m);
+    float2* Psi = (float2*)workspace;
+    const HerkPlan P = herk_plan(n, m, sm_count);
+    float2* partial = P.splits > 1 ? (float2*)((char*)workspace + (((size_t)8 << n) + 255) / 256 * 256) : nullptr;
+    float2* dst = P.splits > 1 ? partial : rho;
+    psi_gather_kernel<<<sm_count * 8, 256, 0, st>>>(psi, Psi, n, m, Q);
+    dim3 grid((unsigned)P.tiles, (unsigned)P.splits);
+    if (P.tc) {
+        cudaError_t e = cudaFuncSetAttribute(herk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+        if (e != cudaSuccess) return (int)e;
+        herk_tc_kernel<<<grid, kTcThreads, kTcSmem, st>>>(Psi, D, K, P.kps, dst, err);
+    } else {
+        herk_tile_kernel<<<grid, kHerkThreads, 0, st>>>(Psi, D, K, P.kps, dst);
+    }
+    int nl = 2;
+    if (P.splits > 1) {
+        herk_reduce_kernel<<<sm_count * 4, 256, 0, st>>>(partial, P.splits, D * D, rho);
+        ++nl;
+    }
+    if (launches) *launches = nl;
+    return (int)cudaGetLastError();
+}
+
+}  // namespace tlq

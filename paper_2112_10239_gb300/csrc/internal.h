@@ -369,4 +369,16 @@ int dense_grid(int n_eff, int sm_count);
 
 int launch_dense(DenseLaunch& L, void* stream);
 
+// Partial trace of a pure state (density.cu): kept[t] = t-th lowest kept qubit, traced[u] =
+// u-th lowest traced qubit.
+constexpr int kMaxDensityQubits = 15;   // largest kept set (a 2^15 x 2^15 complex64 output)
+struct QubitMap { int32_t kept[32]; int32_t traced[32]; };
+int herk_splits(int n, int m, int sm_count);
+size_t partial_trace_workspace_bytes(int n, int m, int sm_count);
+int launch_partial_trace(const void* psi, int n, const QubitMap& Q, int m, void* rho, void* workspace, int sm_count,
+                         int32_t* err, void* stream, int* launches);
+// Gates in the backward light cone of the qubit set S on a circuit's layers (every operator
+// on S); *lo / *hi bound the qubits they touch together with S.
+std::vector<int> light_cone_gates(const Circuit& c, const std::vector<int>& S, int* lo, int* hi);
+
 }  // namespace tlq

@@ -424,6 +424,37 @@ void place(std::vector<ClassBuild>& list, const ClassBuild& proto, F add) {
 
 }  // namespace
 
+std::vector<int> light_cone_gates(const Circuit& c, const std::vector<int>& S0, int* lo, int* hi) {
+    // Walk the layers from last to first. A layer's diagonal gates commute with each other,
+    // so conjugating a general operator on the support S by all of them involves only the
+    // gates that touch S as it stands before the layer: each joins the cone and its other
+    // qubit joins S (partners added here pull in no further gate of the same layer). Then
+    // the layer's rotations on S join. Gates outside commute with the operator and drop out
+    // (the rule of the term cones, for a non-diagonal operator).
+    std::vector<char> in(c.n, 0);
+    std::vector<int> S;
+    for (int q : S0) if (!in[q]) { in[q] = 1; S.push_back(q); }
+    std::vector<int> kept, grow;
+    for (int l = (int)c.layers.size() - 1; l >= 0; --l) {
+        grow.clear();
+        for (int g : c.layers[l].diag) {
+            const tlq_gate& G = c.gates[g];
+            const bool two = G.kind == TLQ_RZZ || G.kind == TLQ_CZ;
+            if (!in[G.q0] && !(two && in[G.q1])) continue;
+            kept.push_back(g);
+            if (two) grow.push_back(in[G.q0] ? G.q1 : G.q0);
+        }
+        for (int q : grow)
+            if (!in[q]) { in[q] = 1; S.push_back(q); }
+        for (int g : c.layers[l].rot)
+            if (in[c.gates[g].q0]) kept.push_back(g);
+    }
+    std::sort(kept.begin(), kept.end());
+    *lo = *std::min_element(S.begin(), S.end());
+    *hi = *std::max_element(S.begin(), S.end());
+    return kept;
+}
+
 std::shared_ptr<DensePlan> make_dense_plan(const Circuit& c, const Ham& h, std::string* err) {
     if (c.n > kDenseMaxQubits) {
         if (err) *err = "dense statevector path needs n <= " + std::to_string(kDenseMaxQubits);

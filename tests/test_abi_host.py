@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2112_10239_gb300 import build as tlq_build
@@ -138,3 +139,37 @@ def test_dense_plan_info(B, hctx):
     n_eff, _, n_x, _ = B.tlq_plan_dense_info(hctx.h, c2.h, h2.h)
     assert n_eff == 13
     assert n_x == sum(1 for _, _, letters in q.terms if set(letters) - {"Z"})
+
+
+def test_partial_trace_argument_checks(B, hctx):
+    # validation happens before any device work: EINVAL for bad kept-qubit lists, then the
+    # host-only context reports EUNSUPPORTED for a valid request
+    import ctypes
+    L = B.lib()
+    ip = ctypes.POINTER(ctypes.c_int32)
+
+    def pt(n, keep):
+        k = np.array(keep, dtype=np.int32)
+        return L.tlq_partial_trace_dev(hctx.h, ctypes.c_void_p(16), n, k.ctypes.data_as(ip), len(keep),
+                                       ctypes.c_void_p(16), None)
+
+    assert pt(10, [0, 10]) == B.TLQ_EINVAL          # out of range
+    assert pt(10, [3, 3]) == B.TLQ_EINVAL           # repeated
+    assert pt(10, []) == B.TLQ_EINVAL               # m = 0
+    assert pt(32, [0]) == B.TLQ_EINVAL              # n > 31
+    assert pt(20, list(range(16))) == B.TLQ_EINVAL  # m > 15
+    assert pt(10, [7, 2]) == B.TLQ_EUNSUPPORTED     # valid; host-only context
+    p = W.tfim_problem(500, 4, 1, seed=6)
+    c, h = hctx.problem(p)
+    th = np.ascontiguousarray(p.theta[0])
+    rho = np.zeros(2 * 64)
+    dp = ctypes.POINTER(ctypes.c_double)
+
+    def rd(keep):
+        k = np.array(keep, dtype=np.int32)
+        return L.tlq_reduced_density(hctx.h, c.h, th.ctypes.data_as(dp), k.ctypes.data_as(ip), len(keep),
+                                     rho.ctypes.data_as(dp))
+
+    assert rd([499, 500]) == B.TLQ_EINVAL
+    assert rd(list(range(15))) == B.TLQ_EINVAL      # the host API returns at most 14 kept qubits
+    assert rd([250, 251, 253]) == B.TLQ_EUNSUPPORTED
