@@ -407,7 +407,7 @@ def extra_workloads(B, dev, local, flush, peaks):
     return out
 
 
-def partial_trace_workloads(B, dev, local, flush, peaks, n=20, ms=(14, 10), steps=10):
+def partial_trace_workloads(B, dev, local, flush, peaks, n=20, ms=(14, 10), steps=10, warmup=3, with_cpu=True):
     """Device time of tlq_partial_trace_dev on a seeded random n-qubit state, and the oracle
     (numpy: one reshape/transpose and one complex128 matrix product) on the host."""
     import torch
@@ -420,11 +420,12 @@ def partial_trace_workloads(B, dev, local, flush, peaks, n=20, ms=(14, 10), step
     out = {}
     with B.Context(device=local) as ctx:
         B.tlq_profile_enable(ctx.h, True)
-        stream = torch.cuda.current_stream(dev)
+        stream = torch.cuda.Stream(dev)   # a real handle: the events and the library share it
+        torch.cuda.set_stream(stream)
         for m in ms:
             keep = list(range(n - m, n)) if m == ms[0] else list(range(m))
             rho_d = torch.empty(2 * 4 ** m, dtype=torch.float32, device=dev)
-            for _ in range(3):
+            for _ in range(max(1, warmup)):
                 B.tlq_partial_trace_dev(ctx.h, psi_d.data_ptr(), n, keep, rho_d.data_ptr(), stream.cuda_stream)
             torch.cuda.synchronize()
             t, kt = [], []
@@ -439,21 +440,42 @@ def partial_trace_workloads(B, dev, local, flush, peaks, n=20, ms=(14, 10), step
                 t.append(a.elapsed_time(b))
                 kt.append(kms)
             D, K = 2 ** m, 2 ** (n - m)
-            flops = 8.0 * D * (D + 1) / 2 * K      # Hermitian half of rho = Psi Psi^dagger
+            flops = 8.0 * D * (D + 1) / 2 * K      # Hermitian half of rho = Psi Psi^dagger (complex MACs x 8)
             kms = float(np.median(kt))
-            t0 = time.perf_counter()
-            density.reduced_density(psi, n, keep)
-            cpu_s = time.perf_counter() - t0
+            cpu_s = None
+            if with_cpu:
+                t0 = time.perf_counter()
+                density.reduced_density(psi, n, keep)
+                cpu_s = time.perf_counter() - t0
             del rho_d
+            hbm_bytes = 8 * D * D + 3 * 8 * 2 ** n     # rho written; psi read, Psi written and read
+            hbm_peak = float(peaks["hbm_gbs"])
+            if m >= 7:
+                # tensor cores: per 128 x 128 upper tile and 8 complex k, 12 TF32 MMAs of 128 x 128 x 8
+                T = (D + 127) // 128
+                tc_flops = T * (T + 1) // 2 * (K / 8) * 12 * 2 * 128 * 128 * 8
+                tf32_peak = float(peaks["bf16_tflops"]) * 1.1 / 2.25   # nominal TF32 / BF16 dense ratio
+                hbm_floor, tc_floor = hbm_bytes / (hbm_peak * 1e9), tc_flops / (tf32_peak * 1e12)
+                if hbm_floor >= tc_floor:
+                    roof = {"bound": "hbm", "achieved": hbm_bytes / (kms * 1e-3) / 1e9, "peak": hbm_peak,
+                            "unit": "GB/s", "frac": hbm_bytes / (kms * 1e-3) / 1e9 / hbm_peak}
+                else:
+                    roof = {"bound": "tensor", "achieved": tc_flops / (kms * 1e-3) / 1e12, "peak": tf32_peak,
+                            "unit": "TFLOP/s", "frac": tc_flops / (kms * 1e-3) / 1e12 / tf32_peak,
+                            "peak_basis": "measured bf16 dense x 1.1/2.25 (nominal TF32/BF16)"}
+                roof.update({"kernel": "herk_tc_kernel (tcgen05 kind::tf32, TMEM accumulators)",
+                             "tensor_tflops_executed": tc_flops / (kms * 1e-3) / 1e12,
+                             "hbm_gbs": hbm_bytes / (kms * 1e-3) / 1e9})
+            else:
+                roof = {"bound": "alu", "achieved": flops / (kms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": flops / (kms * 1e-3) / 1e12 / peak, "kernel": "herk_tile_kernel (FP32)"}
+            roof.update({"kernel_ms": kms, "traffic": None, "hbm_bytes": hbm_bytes, "algorithmic_flops": flops})
             out[f"partial_trace_n{n}_m{m}"] = {
                 "value": 1e3 / float(np.median(t)), "unit": "traces/s", "ms": float(np.median(t)), "launches": nl,
-                "keep": f"qubits {keep[0]}..{keep[-1]}",
-                "roofline": {"bound": "alu", "achieved": flops / (kms * 1e-3) / 1e12, "peak": peak,
-                             "unit": "TFLOP/s", "frac": flops / (kms * 1e-3) / 1e12 / peak, "kernel_ms": kms,
-                             "output_bytes": 8 * D * D,
-                             "output_write_floor_ms": 8 * D * D / (float(peaks["hbm_gbs"]) * 1e9) * 1e3},
-                "cpu_baseline": {"value": 1.0 / cpu_s, "unit": "traces/s", "kind": "oracle",
-                                 "cores": len(os.sched_getaffinity(0)), "sample": "one full trace (numpy complex128)"}}
+                "keep": f"qubits {keep[0]}..{keep[-1]}", "roofline": roof,
+                "cpu_baseline": None if cpu_s is None else {
+                    "value": 1.0 / cpu_s, "unit": "traces/s", "kind": "oracle", "cores": len(os.sched_getaffinity(0)),
+                    "sample": "one full trace (numpy complex128)"}}
     return out
 
 
@@ -476,6 +498,29 @@ def main():
     if world > 1:
         dist.barrier()
     from paper_2112_10239_gb300 import binding as B
+
+    pt = re.fullmatch(r"partial_trace_n(\d+)_m(\d+)", args.workload)
+    if pt:   # the partial trace alone (device time of tlq_partial_trace_dev), one replica per rank
+        n, m = int(pt.group(1)), int(pt.group(2))
+        if not 1 <= m <= min(n, 15) or n > 31:
+            raise SystemExit("partial_trace workloads take 1 <= m <= min(n, 15), n <= 31")
+        dev = torch.device("cuda", local)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        peaks, peak_kind = measured_peaks()
+        res = partial_trace_workloads(B, dev, local, flush, peaks, n=n, ms=(m,), steps=args.steps,
+                                      warmup=args.warmup, with_cpu=not args.no_extras)
+        r = res[f"partial_trace_n{n}_m{m}"]
+        if rank == 0:
+            print(json.dumps({"metric": "partial traces/sec", "value": world * r["value"], "unit": "traces/s",
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                              "data": "synthetic", "config": {"workload": args.workload, "n": n, "m": m,
+                                                              "keep": r["keep"], "l2": "flushed between steps"},
+                              "gpu_launches": r["launches"] * args.steps, "roofline": r["roofline"],
+                              "peak_source": peak_kind, "cpu_baseline": r.get("cpu_baseline")}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     prob = workload(args.workload)
     ctx = B.Context(device=local)

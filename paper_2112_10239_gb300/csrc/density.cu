@@ -171,7 +171,9 @@ __global__ void herk_reduce_kernel(const float2* __restrict__ partial, int split
 // Re and Im accumulators take 2 x 128 TMEM columns. The k range is walked in chunks of 8
 // complex values, double-buffered in shared memory: all threads load and split a chunk
 // while the tensor core works on the previous one, and thread 0 issues the 12 MMAs of a
-// chunk (M = N = 128, K = 8, kind::tf32) and commits them to that buffer's mbarrier.
+// chunk (M = N = 128, K = 8, kind::tf32) and commits them to that buffer's mbarrier; the
+// global loads of the following chunk are issued right after, so their latency overlaps the
+// tensor core's work.
 // Shared-memory operands use the no-swizzle K-major layout: 8-row x 16-byte core matrices,
 // 128 bytes apart along K and 256 bytes apart along M/N (one 4 KB tile per operand part).
 
@@ -291,6 +293,55 @@ __device__ __forceinline__ void load_rows(const float2* __restrict__ Psi, int64_
     }
 }
 
+// One chunk of the tile's k loop: wait until the MMAs that last read this stage are done,
+// split the chunk held in registers into the stage, issue its 12 MMAs (thread 0), then load
+// the chunk two ahead into the same registers. Returns false when a wait gave up.
+__device__ __forceinline__ bool tc_chunk(int c, int nchunks, unsigned char* stage0, uint64_t* bars, uint32_t tmem,
+                                         const float2* __restrict__ Psi, int64_t D, int64_t K, int64_t i0,
+                                         int64_t j0, int64_t kbeg, int64_t kend, int row, int half, int tid,
+                                         float4& a0, float4& a1, float4& b0, float4& b1) {
+    const int s = c & 1;
+    unsigned char* st = stage0 + s * kTcStageBytes;
+    bool bad = false;
+    if (c >= 2) bad = !mbar_wait(su32(&bars[s]), (uint32_t)(((c >> 1) - 1) & 1));   // MMAs of chunk c-2 done
+    if (__syncthreads_or(bad)) return false;
+    put_row4(st, row, half, a0, a1, false);                    // parts 0-3: A re/im hi/lo
+    put_row4(st + 4 * kTcPartBytes, row, half, b0, b1, true);  // parts 4-9: B re/im, -im
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t b = su32(st);
+        auto d = [&](int part) { return sdesc(b + part * kTcPartBytes, 128, 256); };
+        const uint32_t dr = tmem, di = tmem + kTcTile;
+        const uint32_t acc = c > 0 ? 1u : 0u;
+        // Re: A_re B_re + A_im B_im
+        mma_tf32(dr, d(0), d(4), acc);
+        mma_tf32(dr, d(0), d(5), 1u);
+        mma_tf32(dr, d(1), d(4), 1u);
+        mma_tf32(dr, d(2), d(6), 1u);
+        mma_tf32(dr, d(2), d(7), 1u);
+        mma_tf32(dr, d(3), d(6), 1u);
+        // Im: A_im B_re + A_re (-B_im)
+        mma_tf32(di, d(2), d(4), acc);
+        mma_tf32(di, d(2), d(5), 1u);
+        mma_tf32(di, d(3), d(4), 1u);
+        mma_tf32(di, d(0), d(8), 1u);
+        mma_tf32(di, d(0), d(9), 1u);
+        mma_tf32(di, d(1), d(8), 1u);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&bars[s]))
+                     : "memory");
+    }
+    if (c + 2 < nchunks) {
+        const int64_t k2 = kbeg + (int64_t)(c + 2) * kTcChunk;
+        load_rows(Psi, D, K, i0, k2, kend, row, half, a0, a1);
+        load_rows(Psi, D, K, j0, k2, kend, row, half, b0, b1);
+    }
+    return true;
+}
+
+constexpr int kTcStagePitch = 64 + 1;   // complex per staged output row (64 columns + 1 pad)
+
 // grid.x = upper 128-tiles, grid.y = k splits; out = rho or partial + split * D * D.
 __global__ void __launch_bounds__(kTcThreads, 2) herk_tc_kernel(const float2* __restrict__ Psi, int64_t D, int64_t K,
                                                                 int64_t k_per_split, float2* __restrict__ out,
@@ -299,7 +350,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) herk_tc_kernel(const float2* __
     unsigned char* stage0 = tc_smem;                                 // 2 stages x 40 KB
     uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + 2 * kTcStageBytes);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
-    int* s_bad = reinterpret_cast<int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int bi, bj;
@@ -314,7 +364,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) herk_tc_kernel(const float2* __
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[0])) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *s_bad = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
@@ -328,43 +377,27 @@ __global__ void __launch_bounds__(kTcThreads, 2) herk_tc_kernel(const float2* __
     const uint32_t tmem = *tmem_slot;
 
     const int row = tid >> 1, half = tid & 1;   // this thread's row of A and of B, and k half
+    // chunks c (even) and c + 1 (odd) in two register sets, each refilled two chunks ahead
+    float4 a0, a1, b0, b1, e0, e1, f0, f1;
+    if (nchunks > 0) {
+        load_rows(Psi, D, K, i0, kbeg, kend, row, half, a0, a1);
+        load_rows(Psi, D, K, j0, kbeg, kend, row, half, b0, b1);
+    }
+    if (nchunks > 1) {
+        load_rows(Psi, D, K, i0, kbeg + kTcChunk, kend, row, half, e0, e1);
+        load_rows(Psi, D, K, j0, kbeg + kTcChunk, kend, row, half, f0, f1);
+    }
     bool bad = false;
-    for (int c = 0; c < nchunks && !bad; ++c) {
-        const int s = c & 1;
-        unsigned char* st = stage0 + s * kTcStageBytes;
-        if (c >= 2) bad = !mbar_wait(su32(&bars[s]), (uint32_t)(((c >> 1) - 1) & 1));   // MMAs of chunk c-2 done
-        if (__syncthreads_or(bad)) { bad = true; break; }
-        const int64_t k0 = kbeg + (int64_t)c * kTcChunk;
-        float4 a0, a1, b0, b1;
-        load_rows(Psi, D, K, i0, k0, kend, row, half, a0, a1);
-        load_rows(Psi, D, K, j0, k0, kend, row, half, b0, b1);
-        put_row4(st, row, half, a0, a1, false);                  // parts 0-3: A re/im hi/lo
-        put_row4(st + 4 * kTcPartBytes, row, half, b0, b1, true);  // parts 4-9: B re/im, -im
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t b = su32(st);
-            auto d = [&](int part) { return sdesc(b + part * kTcPartBytes, 128, 256); };
-            const uint32_t dr = tmem, di = tmem + kTcTile;
-            const uint32_t acc = c > 0 ? 1u : 0u;
-            // Re: A_re B_re + A_im B_im
-            mma_tf32(dr, d(0), d(4), acc);
-            mma_tf32(dr, d(0), d(5), 1u);
-            mma_tf32(dr, d(1), d(4), 1u);
-            mma_tf32(dr, d(2), d(6), 1u);
-            mma_tf32(dr, d(2), d(7), 1u);
-            mma_tf32(dr, d(3), d(6), 1u);
-            // Im: A_im B_re + A_re (-B_im)
-            mma_tf32(di, d(2), d(4), acc);
-            mma_tf32(di, d(2), d(5), 1u);
-            mma_tf32(di, d(3), d(4), 1u);
-            mma_tf32(di, d(0), d(8), 1u);
-            mma_tf32(di, d(0), d(9), 1u);
-            mma_tf32(di, d(1), d(8), 1u);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             su32(&bars[s]))
-                         : "memory");
+    for (int c = 0; c < nchunks; c += 2) {
+        if (!tc_chunk(c, nchunks, stage0, bars, tmem, Psi, D, K, i0, j0, kbeg, kend, row, half, tid, a0, a1, b0, b1)) {
+            bad = true;
+            break;
+        }
+        if (c + 1 < nchunks &&
+            !tc_chunk(c + 1, nchunks, stage0, bars, tmem, Psi, D, K, i0, j0, kbeg, kend, row, half, tid, e0, e1, f0,
+                      f1)) {
+            bad = true;
+            break;
         }
     }
     if (!bad && nchunks > 0) {
@@ -373,27 +406,45 @@ __global__ void __launch_bounds__(kTcThreads, 2) herk_tc_kernel(const float2* __
     }
     bad = __syncthreads_or(bad) != 0;
     if (!bad && nchunks > 0) {
+        // Epilogue through shared memory (the stages are free now), one 128 x 64 half of the
+        // tile at a time: TMEM -> staged rows, then coalesced row writes of the entries on or
+        // above the diagonal and coalesced writes of their conjugate mirrors (rows of rho^T).
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int q = warp & 3, h = warp >> 2;   // TMEM lanes 32q.., columns 64h..
-        const int64_t i = i0 + 32 * q + lane;
+        float2* S = reinterpret_cast<float2*>(tc_smem);   // [128][kTcStagePitch]
+        const int q = warp & 3, hh = warp >> 2;          // TMEM lanes 32q.., 32-column quarter hh
 #pragma unroll 1
-        for (int cc = 0; cc < 4; ++cc) {
-            const int col = 64 * h + 16 * cc;
-            float vr[16], vi[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, vr);
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kTcTile + col), vi);
-            if (i >= D) continue;
+        for (int h2 = 0; h2 < 2; ++h2) {
+#pragma unroll 1
+            for (int cc = 0; cc < 2; ++cc) {
+                const int col = 64 * h2 + 32 * hh + 16 * cc;   // tile column of this load
+                float vr[16], vi[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, vr);
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kTcTile + col), vi);
+                float2* srow = S + (32 * q + lane) * kTcStagePitch + (col - 64 * h2);
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int64_t j = j0 + col + e;
-                if (j >= D || j < i) continue;
-                if (j == i) {
-                    dst[i * D + i] = make_float2(vr[e], 0.f);
-                } else {
-                    dst[i * D + j] = make_float2(vr[e], vi[e]);
-                    dst[j * D + i] = make_float2(vr[e], -vi[e]);
-                }
+                for (int e = 0; e < 16; ++e) srow[e] = make_float2(vr[e], vi[e]);
             }
+            __syncthreads();
+            // rows: entry (i, j) for j >= i (the diagonal as a real number)
+#pragma unroll 4
+            for (int t = tid; t < kTcTile * 64; t += kTcThreads) {
+                const int r = t >> 6, cj = t & 63;
+                const int64_t i = i0 + r, j = j0 + 64 * h2 + cj;
+                if (i >= D || j >= D || j < i) continue;
+                float2 v = S[r * kTcStagePitch + cj];
+                if (j == i) v.y = 0.f;
+                dst[i * D + j] = v;
+            }
+            // mirrors: entry (j, i) = conj(i, j) for j > i, written along rows j
+#pragma unroll 4
+            for (int t = tid; t < kTcTile * 64; t += kTcThreads) {
+                const int cj = t >> 7, r = t & 127;
+                const int64_t i = i0 + r, j = j0 + 64 * h2 + cj;
+                if (i >= D || j >= D || j <= i) continue;
+                const float2 v = S[r * kTcStagePitch + cj];
+                dst[j * D + i] = make_float2(v.x, -v.y);
+            }
+            __syncthreads();
         }
     }
     if (bad && tid == 0) atomicExch(err, 3);
