@@ -242,7 +242,7 @@ tlq_status tlq_plan_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* path, i
 tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* ncones, int32_t* nrot, int32_t* ndiag,
                                int32_t* npdiag, int32_t* weff, int32_t* wtrue, int32_t* nterms);
 
-/* Dense statevector plan of (c, h): the state's qubit count *n_eff (n, at least 13), the
+/* Dense statevector plan of (c, h): the state's qubit count *n_eff (n, at least 12), the
  * number of streaming passes *n_passes one forward evaluation makes over the state (the
  * adjoint makes as many again, in reverse), the number of Pauli strings with X/Y letters
  * *n_xterms measured by separate sweeps, and *fused = 1 when the fused passes are used

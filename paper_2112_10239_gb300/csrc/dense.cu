@@ -4,10 +4,10 @@
 // this file is that representation, tuned for HBM streaming.
 //
 // The 2^n complex64 state lives in HBM. Each layer (rotations, then commuting diagonal
-// gates) is applied in passes over tiles of 2^13 amplitudes staged in shared memory:
-//   * a low tile is 2^13 contiguous amplitudes (qubits 0..12);
+// gates) is applied in passes over tiles of 2^12 amplitudes staged in shared memory:
+//   * a low tile is 2^12 contiguous amplitudes (qubits 0..11);
 //   * a strided tile keeps qubits 0..3 (16 contiguous amplitudes = 128 bytes per row) and
-//     9 higher qubits a..a+8 as its 512 rows.
+//     8 higher qubits a..a+7 as its 256 rows.
 // Inside a tile the rotations on the tile's qubits run as 16-amplitude register passes
 // (gates.cuh). The layer's diagonal gates are applied in the layer's last pass: RZ/RZZ gates
 // sharing one angle form a class whose phase exp(-i a/2 (N - 2c)) depends only on the count
@@ -26,8 +26,8 @@ namespace tlq {
 
 namespace {
 
-constexpr int kTile = 1 << kDenseTileBits;        // 8192 amplitudes
-constexpr int kThreads = 512;                     // 16 amplitudes per thread per register pass
+constexpr int kTile = 1 << kDenseTileBits;        // 4096 amplitudes
+constexpr int kThreads = kTile / 16;                // 16 amplitudes per thread per register pass
 constexpr int kMaxLayerClasses = kDenseMaxLayerClasses;
 constexpr int kMaxDistWords = kDenseMaxDistWords;  // (d, mask) int pairs staged in shared memory
 constexpr int kMaxTab = kDenseMaxTab;              // phase-table entries staged per layer
@@ -150,9 +150,9 @@ __device__ __forceinline__ int split_count(const DensePassClassDev& pc, int cnt0
 // Persistent pass kernel: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // with two shared-memory tile buffers; the cp.async copy of the next tile runs while the
 // current one is processed. The last register pass writes its 16 amplitudes straight to HBM.
-__global__ void __launch_bounds__(kThreads, 1) dense_pass_kernel(const __grid_constant__ PassArgs A) {
+__global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_constant__ PassArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float2* bufs = reinterpret_cast<float2*>(smem_raw);                              // 2 x padded_amps(13)
+    float2* bufs = reinterpret_cast<float2*>(smem_raw);                              // 2 x padded_amps(12)
     float2* s_tab = bufs + 2 * padded_amps(kDenseTileBits);                          // kMaxTab
     int32_t* s_dist = reinterpret_cast<int32_t*>(s_tab + kMaxTab);                   // kMaxDistWords
     DenseClassDev* s_cls = reinterpret_cast<DenseClassDev*>(s_dist + kMaxDistWords); // kMaxLayerClasses
@@ -337,11 +337,11 @@ __device__ __forceinline__ void adjoint_bit(const AdjArgs& A, int g, float2 (&v)
     if (lane == 0) acc[4 * g + K] += (double)gk;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) dense_adjoint_kernel(const __grid_constant__ AdjArgs A) {
+__global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid_constant__ AdjArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float2* bpsi = reinterpret_cast<float2*>(smem_raw);                               // padded_amps(13)
-    float2* blam = bpsi + padded_amps(kDenseTileBits);                                // padded_amps(13)
-    double* s_gacc = reinterpret_cast<double*>(blam + padded_amps(kDenseTileBits));   // [16 warps][slots]
+    float2* bpsi = reinterpret_cast<float2*>(smem_raw);                               // padded_amps(12)
+    float2* blam = bpsi + padded_amps(kDenseTileBits);                                // padded_amps(12)
+    double* s_gacc = reinterpret_cast<double*>(blam + padded_amps(kDenseTileBits));   // [warps][slots]
     float2* s_tab = reinterpret_cast<float2*>(s_gacc + (kThreads / 32) * kDenseAdjSlots);
     int32_t* s_dist = reinterpret_cast<int32_t*>(s_tab + kMaxTab);
     DenseClassDev* s_cls = reinterpret_cast<DenseClassDev*>(s_dist + kMaxDistWords);
@@ -667,7 +667,7 @@ size_t dense_partial_count(int n_eff) {
 
 int dense_grid(int n_eff, int sm_count) {
     const int ntiles = 1 << (n_eff - kDenseTileBits);
-    return ntiles < sm_count ? ntiles : sm_count;
+    return ntiles < 2 * sm_count ? ntiles : 2 * sm_count;   // two CTAs per SM
 }
 
 namespace {

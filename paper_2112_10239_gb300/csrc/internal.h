@@ -69,13 +69,13 @@ constexpr int kCtaThreads = 512;
 constexpr int kMaxPassSlots = 4 + 2 * 20;  // gradient values per adjoint pass: 4 rotations + RZ/pair per qubit
 
 // Dense statevector path (circuits with non-adjacent two-qubit gates): the 2^n state lives
-// in HBM and is processed in passes over tiles of 2^13 amplitudes. A "low" tile is 2^13
-// contiguous amplitudes (qubits 0..12); a "strided" tile keeps qubits 0..3 (16 contiguous
-// amplitudes, 128 bytes) and 9 higher qubits a..a+8. Inside a tile, rotations run as
-// 16-amplitude register passes; the diagonal gates of a layer are grouped into angle
-// classes and applied from a phase table indexed by a popcount.
-constexpr int kDenseTileBits = 13;
-constexpr int kDenseStridedBits = 9;
+// in HBM and is processed in passes over tiles of 2^12 amplitudes (256 threads; two CTAs
+// share an SM). A "low" tile is 2^12 contiguous amplitudes (qubits 0..11); a "strided" tile
+// keeps qubits 0..3 (16 contiguous amplitudes, 128 bytes) and 8 higher qubits a..a+7.
+// Inside a tile, rotations run as 16-amplitude register passes; the diagonal gates of a
+// layer are grouped into angle classes and applied from a phase table indexed by a popcount.
+constexpr int kDenseTileBits = 12;
+constexpr int kDenseStridedBits = 8;
 constexpr int kDenseMaxQubits = 31;
 constexpr int kDenseMaxLayerClasses = 48;  // per layer (+ energy classes)
 constexpr int kDenseMaxDistWords = 512;
