@@ -213,7 +213,7 @@ def cpu_baseline(prob, budget_s=12.0):
                       f"+ adjoint), {dt:.1f} s wall"}
 
 
-def serving_replay(B, device, count, rate, seed=4):
+def serving_replay(B, device, count, rate, seed=4, plain_path=True):
     """Replay a Poisson request stream (n ~ U[16,400], L ~ U[2,8], h ~ U[0.5,1.5], 30% with
     gradient) open-loop through tlq_submit/tlq_poll, and the same arrivals served one at a
     time through the synchronous calls (the plain path). Circuits are created once per
@@ -269,6 +269,8 @@ def serving_replay(B, device, count, rate, seed=4):
                "mean_batch": mean_batch, "completed": n_done}
     ctx.close()
 
+    if not plain_path:
+        return {"requests": count, "rate_per_s": rate, "batched": batched}
     # plain path: one request at a time through the synchronous calls, same arrivals
     ctx = B.Context(device=device)
     circ, hams = prepare(ctx)
@@ -404,6 +406,12 @@ def extra_workloads(B, dev, local, flush, peaks):
     out.update(partial_trace_workloads(B, dev, local, flush, peaks))
     # serving: Poisson arrivals, continuous batching vs one request at a time
     out["serving"] = serving_replay(B, local, 2000, 2000.0)
+    # offered-rate sweep of the batched server (below, near and above its capacity)
+    sweep = []
+    for rate, count in ((300.0, 600), (1000.0, 1500), (5000.0, 3000)):
+        r = serving_replay(B, local, count, rate, seed=5, plain_path=False)
+        sweep.append({"rate_per_s": rate, "requests": count, **r["batched"]})
+    out["serving_sweep"] = sweep
     return out
 
 
