@@ -283,9 +283,9 @@ __device__ void pass_fwd(T2* psi, int s, unsigned m, bool diag, const Team& tm, 
 // in `m`, emit Im<lam|G|psi> and un-apply it from psi and lam. Per-warp partial sums go to
 // red[slot * nw + warp]: slots 0..3 rotations (register bit), 4.. diagonal gates in program
 // order.
-template <typename real, typename T2>
-__device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, bool diag, const Team& tm, const TeamMem<T2>& M,
-                         int par, real* red) {
+template <typename real, typename T2, bool DIAG>
+__device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, const Team& tm, const TeamMem<T2>& M, int par,
+                         real* red) {
     const int W = M.W;
     const T2* cs = info_cs(M, par);
     const int* kinds = info_kinds(M, par);
@@ -312,7 +312,7 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, bool diag, const T
         T2 p[16], l[16];
         load16(p, pp, stride);
         load16(l, lp, stride);
-        if (diag) {
+        if constexpr (DIAG) {
             // w_x = Im(conj(lam_x) psi_x); dE/da is sum_x z_q(x) w_x for RZ on q and
             // sum_x z_q0(x) z_q1(x) w_x for RZZ on (q0, q1 = q0 + 1).
             real S = 0, Sk0 = 0, Sk1 = 0, Sk2 = 0, Sk3 = 0, Sp0 = 0, Sp1 = 0, Sp2 = 0;
@@ -365,22 +365,27 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, bool diag, const T
                 l[j] = cmul(l[j], ph);
             }
         }
-        real g0 = 0, g1 = 0, g2 = 0, g3 = 0;
-        if (kd[0] >= 0) g0 = adjoint_rot<0, T2, real>(p, l, kd[0], c[0], sn[0]);
-        if (kd[1] >= 0) g1 = adjoint_rot<1, T2, real>(p, l, kd[1], c[1], sn[1]);
-        if (kd[2] >= 0) g2 = adjoint_rot<2, T2, real>(p, l, kd[2], c[2], sn[2]);
-        if (kd[3] >= 0) g3 = adjoint_rot<3, T2, real>(p, l, kd[3], c[3], sn[3]);
-        store16(p, pp, stride);
-        store16(l, lp, stride);
-        const real gk[4] = {g0, g1, g2, g3};
+        if constexpr (!DIAG) {
+            real g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+            if (kd[0] >= 0) g0 = adjoint_rot<0, T2, real>(p, l, kd[0], c[0], sn[0]);
+            if (kd[1] >= 0) g1 = adjoint_rot<1, T2, real>(p, l, kd[1], c[1], sn[1]);
+            if (kd[2] >= 0) g2 = adjoint_rot<2, T2, real>(p, l, kd[2], c[2], sn[2]);
+            if (kd[3] >= 0) g3 = adjoint_rot<3, T2, real>(p, l, kd[3], c[3], sn[3]);
+            store16(p, pp, stride);
+            store16(l, lp, stride);
+            const real gk[4] = {g0, g1, g2, g3};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (kd[k] < 0) continue;
-            const real val = team_warp_sum(gk[k], tm);
-            if (leader) {
-                real* dst = red + k * nw + warp;
-                *dst = first ? val : *dst + val;
+            for (int k = 0; k < 4; ++k) {
+                if (kd[k] < 0) continue;
+                const real val = team_warp_sum(gk[k], tm);
+                if (leader) {
+                    real* dst = red + k * nw + warp;
+                    *dst = first ? val : *dst + val;
+                }
             }
+        } else {
+            store16(p, pp, stride);
+            store16(l, lp, stride);
         }
         first = false;
     }
@@ -534,28 +539,25 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
         const int par = li & 1;
         unsigned todo = (unsigned)lp[1];
         stage_layer<real, T2>(lp, GT, tm, M, par, true);
-        bool first = true;
-        while (todo || (first && ndiag > 0)) {
-            int s;
-            unsigned m;
-            if (todo) {
-                const int bt = 31 - __clz(todo);
-                s = bt - 3;
-                if (s < 4) s = bt >= 4 ? 4 : 0;
-                if (s > W - 4) s = W - 4;
-                m = (todo >> s) & 15u;
-                todo &= ~(15u << s);
-            } else {
-                s = W - 4;
-                m = 0;
-            }
+        if (ndiag > 0) {   // the layer's diagonal first: its gradients, then its conjugate phase
             real* rb = red + rpar * kMaxPassSlots * nw;
-            const bool dpass = first && ndiag > 0;
-            pass_bwd<real, T2>(M.psi, M.lam, s, m, dpass, tm, M, par, rb);
+            pass_bwd<real, T2, true>(M.psi, M.lam, W - 4, 0u, tm, M, par, rb);
             tm.sync();
-            flush_pass<real, T2>(rb, nw, m, s, M, par, dpass, gdst, tm);
+            flush_pass<real, T2>(rb, nw, 0u, W - 4, M, par, true, gdst, tm);
             rpar ^= 1;
-            first = false;
+        }
+        while (todo) {
+            const int bt = 31 - __clz(todo);
+            int s = bt - 3;
+            if (s < 4) s = bt >= 4 ? 4 : 0;
+            if (s > W - 4) s = W - 4;
+            const unsigned m = (todo >> s) & 15u;
+            todo &= ~(15u << s);
+            real* rb = red + rpar * kMaxPassSlots * nw;
+            pass_bwd<real, T2, false>(M.psi, M.lam, s, m, tm, M, par, rb);
+            tm.sync();
+            flush_pass<real, T2>(rb, nw, m, s, M, par, false, gdst, tm);
+            rpar ^= 1;
         }
     }
 }
