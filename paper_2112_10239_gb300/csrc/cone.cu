@@ -39,7 +39,7 @@ namespace tlq {
 // double-buffered per-warp gradient partials.
 
 struct TeamLayout {
-    int psi, lam, tab, info, red, bytes;
+    int psi, lam, tab, info, fac, red, bytes;
     int tab1, tab2;     // entry offsets of chunk tables 1 and 2
     int tab_entries;    // total table entries (unpadded) built per layer
 };
@@ -66,6 +66,9 @@ __host__ __device__ inline TeamLayout team_layout(int W, int tt, int real_bytes,
     off = (off + 15) & ~15;
     L.info = off;
     off += 2 * info_bytes(real_bytes);
+    L.fac = off;   // per-qubit diagonal factors of the layer being staged (info_fac): 2 x 32 complex + 32 kinds
+    off += 64 * r2 + 32 * 4;
+    off = (off + 15) & ~15;
     L.red = off;
     off += 2 * kMaxPassSlots * nwarps_of(tt) * real_bytes;
     L.bytes = (off + 15) & ~15;
@@ -143,7 +146,7 @@ struct TeamMem {
     T2* psi;
     T2* lam;
     T2* tab;
-    unsigned char* info;   // two buffers of info_bytes
+    unsigned char* info;   // two buffers of info_bytes, then the per-qubit factor staging area
     void* red;
     int tab1, tab2, tab_entries, W;
 };
@@ -168,11 +171,18 @@ template <typename T2>
 __device__ __forceinline__ int* info_pslot(const TeamMem<T2>& M, int par) {
     return info_kinds(M, par) + 96;
 }
+// The factor staging area follows the two info buffers (TeamLayout::fac).
+template <typename T2>
+__device__ __forceinline__ T2* info_fac(const TeamMem<T2>& M) {
+    return reinterpret_cast<T2*>(M.info + 2 * info_bytes((int)sizeof(T2) / 2));
+}
 
 // Stage one layer from its per-qubit records: rotation parameters and gradient slots into
 // info buffer `par`, and the diagonal phase table (conjugated for the adjoint direction).
 // A table entry is the product of the RZ factors of its chunk's qubits and the RZZ/CZ
-// factors of the pairs whose upper qubit lies in the chunk. Ends with a team barrier.
+// factors of the pairs whose upper qubit lies in the chunk; those factors are first staged
+// per qubit in shared memory (one global read each), then every entry is built from them.
+// Ends with a team barrier.
 template <typename real, typename T2>
 __device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, const TeamMem<T2>& M, int par,
                             bool conj_phase) {
@@ -184,6 +194,12 @@ __device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, con
     int* pslot = info_pslot(M, par);
     const int has_diag = lp[0];
     const int32_t* R = lp + kLayerHeader;
+    T2* fz = info_fac(M);                                 // RZ on q: (cos, sin) of a/2, or (1, 0)
+    T2* fp = fz + 32;                                     // RZZ on (q - 1, q): (cos, sin), or (1, 0)
+    int* fpk = reinterpret_cast<int*>(fz + 64);           // kind of the (q - 1, q) gate, -1 none
+    T2 one;
+    one.x = 1;
+    one.y = 0;
     for (int j = tm.tid; j < W; j += tm.tt) {
         const int32_t* r = R + j * kRecWords;
         const int rg = r[0];
@@ -192,8 +208,23 @@ __device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, con
         rslot[j] = (r[1] >> 8) - 1;
         zslot[j] = r[3];
         pslot[j] = (r[5] >> 8) - 1;
+        if (has_diag) {
+            fz[j] = r[2] >= 0 ? GT[r[2]] : one;
+            int pk = -1;
+            T2 pf = one;
+            if (j > 0) {
+                const int32_t* rp = r - kRecWords;   // the pair (j - 1, j) sits in record j - 1
+                if (rp[4] >= 0) {
+                    pk = rp[5] & 255;
+                    if (pk != TLQ_CZ) pf = GT[rp[4]];
+                }
+            }
+            fpk[j] = pk;
+            fp[j] = pf;
+        }
     }
     if (has_diag) {
+        tm.sync();   // the per-qubit factors are staged
         const int b1 = (W - 7) < 7 ? (W - 7) : 7;
         for (int e = tm.tid; e < M.tab_entries; e += tm.tt) {
             int lo, bc, idx, slot;
@@ -211,26 +242,21 @@ __device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, con
             for (int k = 0; k < bc; ++k) {
                 const int q = lo + k;
                 const int bq = (idx >> k) & 1;
-                const int32_t* r = R + q * kRecWords;
-                if (r[2] >= 0) {   // RZ(a) on q: e^{-ia/2} for bit 0, e^{+ia/2} for bit 1
-                    const T2 g = GT[r[2]];
-                    T2 f;
-                    f.x = g.x;
-                    f.y = bq ? g.y : -g.y;
-                    ph = cmul(ph, f);
-                }
+                const T2 g = fz[q];
+                // RZ(a) on q: e^{-ia/2} for bit 0, e^{+ia/2} for bit 1 (identity when absent)
+                T2 f;
+                f.x = g.x;
+                f.y = bq ? g.y : -g.y;
+                ph = cmul(ph, f);
                 if (q > 0) {
-                    const int32_t* rp = r - kRecWords;   // pair (q - 1, q)
-                    if (rp[4] >= 0) {
-                        if ((rp[5] & 255) == TLQ_CZ) {
-                            if (prev & bq) { ph.x = -ph.x; ph.y = -ph.y; }
-                        } else {
-                            const T2 g = GT[rp[4]];
-                            T2 f;
-                            f.x = g.x;
-                            f.y = (prev ^ bq) ? g.y : -g.y;
-                            ph = cmul(ph, f);
-                        }
+                    const int pk = fpk[q];
+                    if (pk == TLQ_CZ) {
+                        if (prev & bq) { ph.x = -ph.x; ph.y = -ph.y; }
+                    } else if (pk >= 0) {   // RZZ: e^{-ia/2} for equal bits, e^{+ia/2} otherwise
+                        const T2 h = fp[q];
+                        f.x = h.x;
+                        f.y = (prev ^ bq) ? h.y : -h.y;
+                        ph = cmul(ph, f);
                     }
                 }
                 prev = bq;
@@ -626,12 +652,22 @@ struct Neumaier {
     __device__ double value() const { return s + c; }
 };
 
+// E_b = sum_t c_t e_{t,b}: one warp per set; lane l sums the terms t = l, l + 32, ... with a
+// compensated sum (coalesced reads), then lane 0 adds the 32 partials in lane order. The
+// order is fixed, so the result does not depend on the launch.
 __global__ void energy_reduce_kernel(const double* e_part, const double* coeff, int T, int B, double* energy) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (b >= B) return;
     Neumaier acc;
-    for (int t = 0; t < T; ++t) acc.add(coeff[t] * e_part[(size_t)b * T + t]);
-    energy[b] = acc.value();
+    for (int t = lane; t < T; t += 32) acc.add(coeff[t] * e_part[(size_t)b * T + t]);
+    double mine = acc.value();
+    Neumaier tot;
+    for (int l = 0; l < 32; ++l) {
+        const double v = __shfl_sync(0xffffffffu, mine, l);
+        if (lane == 0) tot.add(v);
+    }
+    if (lane == 0) energy[b] = tot.value();
 }
 
 __global__ void grad_reduce_kernel(const double* g_part, const int32_t* off, const int32_t* idx, const int32_t* term,
@@ -730,7 +766,7 @@ int launch_cone(ConeLaunch& L, void* stream) {
     }
     if (rc) return rc;
     if (L.ev_end && (e = cudaEventRecord((cudaEvent_t)L.ev_end, st)) != cudaSuccess) return (int)e;
-    energy_reduce_kernel<<<(L.B + 127) / 128, 128, 0, st>>>(L.e_part, L.term_coeff, L.n_terms, L.B, L.energy);
+    energy_reduce_kernel<<<(L.B + 3) / 4, 128, 0, st>>>(L.e_part, L.term_coeff, L.n_terms, L.B, L.energy);
     if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     if (grad) {
         const long long n = (long long)L.B * L.n_params;
@@ -758,13 +794,22 @@ __global__ void batch_gate_table_kernel(const SetRec* sets, typename R2<real>::T
     out[R.gt_off + g] = v;
 }
 
+// Same summation order as energy_reduce_kernel (warp per set, lanes over terms, partials in
+// lane order), so a set's energy is bit-identical served or computed synchronously.
 __global__ void batch_energy_kernel(const SetRec* sets, int n_sets, const double* e_part) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (b >= n_sets) return;
     const SetRec& R = sets[b];
     Neumaier acc;
-    for (int t = 0; t < R.n_terms; ++t) acc.add(R.term_coeff[t] * e_part[R.e_off + t]);
-    *R.energy = acc.value();
+    for (int t = lane; t < R.n_terms; t += 32) acc.add(R.term_coeff[t] * e_part[R.e_off + t]);
+    const double mine = acc.value();
+    Neumaier tot;
+    for (int l = 0; l < 32; ++l) {
+        const double v = __shfl_sync(0xffffffffu, mine, l);
+        if (lane == 0) tot.add(v);
+    }
+    if (lane == 0) *R.energy = tot.value();
 }
 
 __global__ void batch_grad_kernel(const SetRec* sets, const double* g_part) {
@@ -829,7 +874,7 @@ int launch_cone_batch(BatchLaunch& L, void* stream) {
     if ((e = cudaMemsetAsync(L.counters, 0, 4 * sizeof(int32_t), st)) != cudaSuccess) return (int)e;
     const int rc = L.fp64 ? launch_batch_all<double>(L, st) : launch_batch_all<float>(L, st);
     if (rc) return rc;
-    batch_energy_kernel<<<(L.n_sets + 127) / 128, 128, 0, st>>>(L.sets, L.n_sets, L.e_part);
+    batch_energy_kernel<<<(L.n_sets + 3) / 4, 128, 0, st>>>(L.sets, L.n_sets, L.e_part);
     if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     if (L.max_params > 0 && L.range[4] > L.range[2]) {
         const dim3 gg((L.max_params + 255) / 256, L.n_sets);
