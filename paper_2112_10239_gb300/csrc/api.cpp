@@ -144,7 +144,7 @@ tlq_status ensure_worklist(Context* ctx, PlanEntry& pe, const Circuit& c, int B,
         int nteams = std::min(kCtaThreads / tt, smax / tb);
         bool global = (W > kMaxSmemConeW) || nteams < 1;
         if (global) {
-            tt = kCtaThreads;
+            tt = kGlobalCtaThreads;
             tb = team_bytes_host(W, tt, fp64, grad, false);
             nteams = 1;
         }
@@ -195,7 +195,7 @@ static size_t global_slot_bytes(int W, bool fp64, bool grad) {
 
 static int global_grid(const PlanEntry& pe, int sm_count) {
     const int ng = pe.n_chunks - pe.n_chunks_smem;
-    return std::max(0, std::min(ng, sm_count));
+    return std::max(0, std::min(ng, kGlobalCtasPerSm * sm_count));
 }
 
 size_t cone_workspace_bytes(const PlanEntry& pe, const Circuit& c, int B, bool fp64, bool grad, int g_grid) {
@@ -611,7 +611,7 @@ static tlq_status sync_call(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double*
     size_t work = 0;
     if (pe->plan->path == TLQ_PATH_CONE && ctx->cfg.fuse_k != 1) {
         TLQ_TRY(ensure_worklist(ctx, *pe, *c, B, fp64, want_grad));
-        work = cone_workspace_bytes(*pe, *c, B, fp64, want_grad, std::max(0, std::min(pe->n_chunks - pe->n_chunks_smem, ctx->sm_count)));
+        work = cone_workspace_bytes(*pe, *c, B, fp64, want_grad, global_grid(*pe, ctx->sm_count));
     } else if (pe->plan->dense) {
         work = dense_workspace_bytes(*pe, *c, B, want_grad, ctx->sm_count);
     }
@@ -668,7 +668,7 @@ tlq_status tlq_expectation_grad_dev(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const
     if (pe->plan->path == TLQ_PATH_CONE && ctx->cfg.fuse_k != 1) {
         TLQ_TRY(ensure_worklist(ctx, *pe, *c, B, fp64, grad_dev != nullptr));
         work = cone_workspace_bytes(*pe, *c, B, fp64, grad_dev != nullptr,
-                                    std::max(0, std::min(pe->n_chunks - pe->n_chunks_smem, ctx->sm_count)));
+                                    global_grid(*pe, ctx->sm_count));
     } else if (pe->plan->dense) {
         work = dense_workspace_bytes(*pe, *c, B, grad_dev != nullptr, ctx->sm_count);
     }

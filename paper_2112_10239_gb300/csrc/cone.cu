@@ -589,7 +589,8 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
 }
 
 template <typename real, bool GRAD, bool GLOBAL>
-__global__ void __launch_bounds__(kCtaThreads, 1) cone_kernel(ConeArgs A) {
+__global__ void __launch_bounds__(GLOBAL ? kGlobalCtaThreads : kCtaThreads, GLOBAL ? kGlobalCtasPerSm : 1)
+cone_kernel(ConeArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_chunk;
     for (;;) {
@@ -711,7 +712,7 @@ static int launch_cone_t(const ConeLaunch& L, cudaStream_t st, int begin, int en
     A.sets = nullptr;
     const int n = end - begin;
     if (grid > n) grid = n;
-    kern<<<grid, kCtaThreads, smem, st>>>(A);
+    kern<<<grid, GLOBAL ? kGlobalCtaThreads : kCtaThreads, smem, st>>>(A);
     return (int)cudaGetLastError();
 }
 
@@ -845,7 +846,7 @@ static int launch_batch_t(const BatchLaunch& L, cudaStream_t st, int begin, int 
     const int n = end - begin;
     if (grid > n) grid = n;
     if (grid < 1) grid = 1;
-    kern<<<grid, kCtaThreads, smem, st>>>(A);
+    kern<<<grid, GLOBAL ? kGlobalCtaThreads : kCtaThreads, smem, st>>>(A);
     return (int)cudaGetLastError();
 }
 

@@ -66,6 +66,11 @@ constexpr int kMaxGroupTerms = 8;  // terms measured on one shared window
 constexpr int kMaxSmemConeW = 14;  // widest cone kept in shared memory (when it fits: FP32 forward at 14)
 constexpr int kMaxConeW = 20;      // widest cone on the cone path (global-memory tier)
 constexpr int kCtaThreads = 512;
+// Global-memory tier: one window per CTA of kGlobalCtaThreads, kGlobalCtasPerSm CTAs per SM,
+// each with its own state slot in HBM/L2. (Two 256-thread CTAs per SM measured 9 % slower on
+// 15- and 17-qubit windows than one 512-thread CTA: twice the blocks per thread per pass.)
+constexpr int kGlobalCtaThreads = 512;
+constexpr int kGlobalCtasPerSm = 1;
 constexpr int kMaxPassSlots = 4 + 2 * 20;  // gradient values per adjoint pass: 4 rotations + RZ/pair per qubit
 
 // Dense statevector path (circuits with non-adjacent two-qubit gates): the 2^n state lives

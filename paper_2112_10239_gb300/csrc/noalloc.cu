@@ -117,7 +117,7 @@ void build_host_worklist(HostPlan& hp, int B, bool grad, int smax) {
         int nteams = std::min(kCtaThreads / tt, smax / tb);
         const bool global = (W > kMaxSmemConeW) || nteams < 1;
         if (global) {
-            tt = kCtaThreads;
+            tt = kGlobalCtaThreads;
             tb = team_bytes_host(W, tt, false, grad, false);
             nteams = 1;
         }
@@ -213,7 +213,7 @@ extern "C" tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tl
     const int T = (int)P.term_coeff.size();
     const int S = std::max<int32_t>(1, P.n_slots);
     const int n_glob = (int)hp->chunks.size() - hp->n_chunks_smem;
-    const int g_grid = std::max(0, std::min(n_glob, C->sm_count));
+    const int g_grid = std::max(0, std::min(n_glob, kGlobalCtasPerSm * C->sm_count));
     const size_t amps = hp->g_maxW > 0 ? ((size_t)1 << hp->g_maxW) + ((size_t)1 << (hp->g_maxW - 3)) : 0;
     const size_t gslot = ((amps * 8 * (grad ? 2 : 1)) + 255) & ~(size_t)255;
 

@@ -242,7 +242,7 @@ bool Scheduler::launch(Slot& sl, std::vector<ServeRequest*>& batch) {
             int nteams = std::min(kCtaThreads / tt, smax / tb);
             const bool global = (W > kMaxSmemConeW) || nteams < 1;
             if (global) {
-                tt = kCtaThreads;
+                tt = kGlobalCtaThreads;
                 tb = team_bytes_host(W, tt, fp64, gr == 1, false);
                 nteams = 1;
             }
@@ -274,7 +274,7 @@ bool Scheduler::launch(Slot& sl, std::vector<ServeRequest*>& batch) {
         n_glob_max = std::max(n_glob_max, (int)gl.size());
     }
     L.range[4] = (int32_t)chunks.size();
-    const int g_grid = std::min(n_glob_max, ctx->sm_count);
+    const int g_grid = std::min(n_glob_max, kGlobalCtasPerSm * ctx->sm_count);
     const size_t gslot = g_maxW > 0 ? global_slot(g_maxW, fp64, g_grad) : 0;
 
     // ---- layout ----

@@ -165,3 +165,18 @@ def test_width14_forward_in_shared_memory(tlq):
     E, _ = _run(tlq, prob, grad=False)
     Er, _ = _oracle(prob, prob.theta, grad=False)
     check_energy(E, Er)
+
+
+def test_global_tier_many_windows_batch_invariant(tlq):
+    # n=60, L=7: about 30 windows of 15 qubits per set on the global-memory tier. A 12-set batch
+    # has more of them than CTAs (two per SM), so CTAs take several windows in turn; each set
+    # must still equal its own single-set call bit for bit. (Correctness of the tier itself
+    # against the oracle: test_wide_cones_global_tier.)
+    prob = W.tfim_problem(60, 7, 12, seed=21, h_range=(0.5, 1.5))
+    E, g = _run(tlq, prob)
+    for b in (0, 5, 11):
+        one = W.Problem(prob.n, prob.gates, prob.n_params, prob.terms, prob.theta[b:b + 1])
+        E1, g1 = _run(tlq, one)
+        assert E1[0] == E[b]
+        assert np.array_equal(g1[0], g[b])
+    assert np.all(np.isfinite(E)) and np.all(np.isfinite(g))
