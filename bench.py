@@ -362,6 +362,8 @@ def extra_workloads(B, dev, local, flush, peaks):
                          "frac": flops / (kms * 1e-3) / 1e12 / peak, "kernel_ms": kms}}
         c.close()
         h.close()
+    # n=8, L=2, one set: latency of the synchronous call (launch-bound; no roofline)
+    out["tfim_n8_L2_B1_latency"] = latency_n8(B, local)
     # n=28 QAOA on a 3-regular graph (dense statevector): energy and energy + gradient, fused
     # passes vs the plain per-gate sweeps
     prob = W.qaoa_n28_p4()
@@ -413,6 +415,39 @@ def extra_workloads(B, dev, local, flush, peaks):
         sweep.append({"rate_per_s": rate, "requests": count, **r["batched"]})
     out["serving_sweep"] = sweep
     return out
+
+
+def latency_n8(B, local, calls=10000):
+    """n=8, L=2, one parameter set, energy only: a launch-bound call, reported as latency.
+    GPU: the synchronous host-pointer call (H2D of the angles, kernels, D2H of the energy) timed
+    with the host clock per call. CPU: the oracle's plain statevector energy per call."""
+    from oracle import dense
+    from paper_2112_10239_gb300 import workloads as W
+    prob = W.tfim_n8_L2()
+    th = np.ascontiguousarray(prob.theta)
+
+    def pct(v):
+        v = sorted(v)
+        return {"p50_us": 1e6 * v[len(v) // 2], "p99_us": 1e6 * v[min(len(v) - 1, int(math.ceil(0.99 * len(v))) - 1)]}
+
+    with B.Context(device=local) as ctx:
+        c, h = ctx.problem(prob)
+        for _ in range(100):
+            B.tlq_expectation(ctx.h, c.h, h.h, th)
+        t = []
+        for _ in range(calls):
+            t0 = time.perf_counter()
+            B.tlq_expectation(ctx.h, c.h, h.h, th)
+            t.append(time.perf_counter() - t0)
+        c.close()
+        h.close()
+    cpu = []
+    for _ in range(calls // 10):
+        t0 = time.perf_counter()
+        dense.energy(prob.n, prob.gates, prob.terms, prob.theta[0])
+        cpu.append(time.perf_counter() - t0)
+    return {"workload": "tfim_n8_L2_B1 (energy)", "calls": calls, "gpu": pct(t),
+            "cpu_oracle": {**pct(cpu), "calls": len(cpu)}}
 
 
 def partial_trace_workloads(B, dev, local, flush, peaks, n=20, ms=(14, 10), steps=10, warmup=3, with_cpu=True):

@@ -444,7 +444,9 @@ __device__ void flush_pass(const real* red, int nw, unsigned m, int s, const Tea
 
 // <psi|P_t|psi> for every term t measured on this window, written to e_out[term]; when
 // GRAD also lam = sum_t c_t P_t psi (the term coefficients folded into the adjoint).
-// Ends with a team barrier.
+// One pass over the window for all its terms (at most kMaxGroupTerms): each block of 16
+// amplitudes is read once, lam is accumulated in registers and written once, and each term
+// keeps its own partial sum. Ends with a team barrier.
 template <typename real, typename T2, bool GRAD>
 __device__ void measure(const TeamMem<T2>& M, const MeasDev* mt, int nmt, const double* coeff, double* e_out,
                         const Team& tm, real* red) {
@@ -453,44 +455,57 @@ __device__ void measure(const TeamMem<T2>& M, const MeasDev* mt, int nmt, const 
     const int nw = nwarps_of(tm.tt);
     const int warp = tm.tt >= 32 ? (tm.tid >> 5) : 0;
     const bool leader = tm.tt >= 32 ? ((tm.tid & 31) == 0) : (tm.tid == 0);
-    for (int k = 0; k < nmt; ++k) {
-        const MeasDev md = mt[k];
-        T2 f0;   // (-i)^ny
-        const int ny = md.ny & 3;
-        f0.x = ny == 0 ? 1 : ny == 2 ? -1 : 0;
-        f0.y = ny == 1 ? -1 : ny == 3 ? 1 : 0;
-        const real ck = GRAD ? (real)coeff[md.term] : (real)0;
-        real acc = 0;
-        for (int o = tm.tid; o < nout; o += tm.tt) {
-            const int x0 = o << 4;
-            T2 a[16];
-            load16(a, M.psi + pad16(x0), 1);
-            T2 lv[16];
-            if (GRAD && k > 0) load16(lv, M.lam + pad16(x0), 1);
+    real acc[kMaxGroupTerms];
+#pragma unroll
+    for (int k = 0; k < kMaxGroupTerms; ++k) acc[k] = 0;
+    for (int o = tm.tid; o < nout; o += tm.tt) {
+        const int x0 = o << 4;
+        T2 a[16];
+        load16(a, M.psi + pad16(x0), 1);
+        T2 lv[16];
+        if (GRAD) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) lv[j].x = lv[j].y = 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kMaxGroupTerms; ++k) {
+            if (k >= nmt) break;
+            const MeasDev md = mt[k];
+            T2 f0;   // (-i)^ny
+            const int ny = md.ny & 3;
+            f0.x = ny == 0 ? 1 : ny == 2 ? -1 : 0;
+            f0.y = ny == 1 ? -1 : ny == 3 ? 1 : 0;
+            const real ck = GRAD ? (real)coeff[md.term] : (real)0;
+            real sk = 0;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int x = x0 | j;
                 const T2 v = M.psi[pad16(x ^ (int)md.flip)];
                 T2 t = cmul(f0, v);
                 if (__popc((unsigned)x & md.zy) & 1) { t.x = -t.x; t.y = -t.y; }
-                acc += a[j].x * t.x + a[j].y * t.y;
+                sk += a[j].x * t.x + a[j].y * t.y;
                 if (GRAD) {
-                    if (k == 0) { lv[j].x = ck * t.x; lv[j].y = ck * t.y; }
-                    else { lv[j].x += ck * t.x; lv[j].y += ck * t.y; }
+                    lv[j].x += ck * t.x;
+                    lv[j].y += ck * t.y;
                 }
             }
-            if (GRAD) store16(lv, M.lam + pad16(x0), 1);
+            acc[k] += sk;
         }
-        acc = team_warp_sum(acc, tm);
-        if (leader) red[warp] = acc;
-        tm.sync();
-        if (tm.tid == 0) {
-            real e = 0;
-            for (int w = 0; w < nw; ++w) e += red[w];
-            e_out[md.term] = (double)e;
-        }
-        tm.sync();
+        if (GRAD) store16(lv, M.lam + pad16(x0), 1);
     }
+#pragma unroll
+    for (int k = 0; k < kMaxGroupTerms; ++k) {
+        if (k >= nmt) break;
+        const real v = team_warp_sum(acc[k], tm);
+        if (leader) red[k * nw + warp] = v;
+    }
+    tm.sync();
+    for (int k = tm.tid; k < nmt; k += tm.tt) {
+        real e = 0;
+        for (int w = 0; w < nw; ++w) e += red[k * nw + w];
+        e_out[mt[k].term] = (double)e;
+    }
+    tm.sync();
 }
 
 template <typename real, bool GRAD, bool GLOBAL>
