@@ -309,7 +309,7 @@ __device__ void pass_fwd(T2* psi, int s, unsigned m, bool diag, const Team& tm, 
 // in `m`, emit Im<lam|G|psi> and un-apply it from psi and lam. Per-warp partial sums go to
 // red[slot * nw + warp]: slots 0..3 rotations (register bit), 4.. diagonal gates in program
 // order.
-template <typename real, typename T2, bool DIAG>
+template <typename real, typename T2, bool DIAG, bool FINAL = false>
 __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, const Team& tm, const TeamMem<T2>& M, int par,
                          real* red) {
     const int W = M.W;
@@ -393,12 +393,21 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, const Team& tm, co
         }
         if constexpr (!DIAG) {
             real g0 = 0, g1 = 0, g2 = 0, g3 = 0;
-            if (kd[0] >= 0) g0 = adjoint_rot<0, T2, real>(p, l, kd[0], c[0], sn[0]);
-            if (kd[1] >= 0) g1 = adjoint_rot<1, T2, real>(p, l, kd[1], c[1], sn[1]);
-            if (kd[2] >= 0) g2 = adjoint_rot<2, T2, real>(p, l, kd[2], c[2], sn[2]);
-            if (kd[3] >= 0) g3 = adjoint_rot<3, T2, real>(p, l, kd[3], c[3], sn[3]);
-            store16(p, pp, stride);
-            store16(l, lp, stride);
+            if constexpr (FINAL) {
+                // layer 0: the states are not needed afterwards, and its rotations commute, so
+                // every gradient is taken at this state with nothing un-applied or stored
+                if (kd[0] >= 0) g0 = kd[0] == TLQ_RY ? grad_y<0, T2, real>(p, l) : grad_x<0, T2, real>(p, l);
+                if (kd[1] >= 0) g1 = kd[1] == TLQ_RY ? grad_y<1, T2, real>(p, l) : grad_x<1, T2, real>(p, l);
+                if (kd[2] >= 0) g2 = kd[2] == TLQ_RY ? grad_y<2, T2, real>(p, l) : grad_x<2, T2, real>(p, l);
+                if (kd[3] >= 0) g3 = kd[3] == TLQ_RY ? grad_y<3, T2, real>(p, l) : grad_x<3, T2, real>(p, l);
+            } else {
+                if (kd[0] >= 0) g0 = adjoint_rot<0, T2, real>(p, l, kd[0], c[0], sn[0]);
+                if (kd[1] >= 0) g1 = adjoint_rot<1, T2, real>(p, l, kd[1], c[1], sn[1]);
+                if (kd[2] >= 0) g2 = adjoint_rot<2, T2, real>(p, l, kd[2], c[2], sn[2]);
+                if (kd[3] >= 0) g3 = adjoint_rot<3, T2, real>(p, l, kd[3], c[3], sn[3]);
+                store16(p, pp, stride);
+                store16(l, lp, stride);
+            }
             const real gk[4] = {g0, g1, g2, g3};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -439,6 +448,60 @@ __device__ void flush_pass(const real* red, int nw, unsigned m, int s, const Tea
         real acc = 0;
         for (int w = 0; w < nw; ++w) acc += red[t * nw + w];
         gdst[slot] = (double)acc;
+    }
+}
+
+// The window state after layer 0's rotations (staged in info buffer `par`), from |0..0>:
+// single-qubit rotations on |0> give a product state, amplitude(x) = prod_j f_j(x_j) with
+// f_j(0) = cos(a_j/2) and f_j(1) = sin(a_j/2) (RY) or -i sin(a_j/2) (RX); qubits without a live
+// rotation contribute 1 for bit 0 and 0 for bit 1. Each thread writes 16 contiguous
+// amplitudes: the product over its fixed high bits times the 16 products over the low four
+// bits (built by doubling), then layer 0's diagonal phase when `diag`. Replaces the register
+// passes of layer 0 (and its diagonal pass) in the forward sweep.
+template <typename real, typename T2>
+__device__ void init_product_state(const TeamMem<T2>& M, unsigned live, bool diag, const Team& tm, int par) {
+    const int W = M.W;
+    const T2* cs = info_cs(M, par);
+    const int* kinds = info_kinds(M, par);
+    auto factor = [&](int j, int bit) {
+        T2 f;
+        const bool rot = ((live >> j) & 1u) && kinds[j] >= 0;
+        if (!rot) {
+            f.x = bit ? 0 : 1;
+            f.y = 0;
+        } else if (bit == 0) {
+            f.x = cs[j].x;
+            f.y = 0;
+        } else if (kinds[j] == TLQ_RY) {
+            f.x = cs[j].y;
+            f.y = 0;
+        } else {   // RX
+            f.x = 0;
+            f.y = -cs[j].y;
+        }
+        return f;
+    };
+    const int nout = 1 << (W - 4);
+    for (int o = tm.tid; o < nout; o += tm.tt) {
+        const int base = o << 4;
+        T2 v[16];
+        v[0].x = 1;
+        v[0].y = 0;
+        for (int j = 4; j < W; ++j) v[0] = cmul(v[0], factor(j, (base >> j) & 1));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const T2 f0 = factor(k, 0), f1 = factor(k, 1);
+#pragma unroll
+            for (int j = 0; j < (1 << k); ++j) {
+                v[j | (1 << k)] = cmul(v[j], f1);
+                v[j] = cmul(v[j], f0);
+            }
+        }
+        if (diag) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = cmul(v[j], phase_of(M.tab, M.tab1, M.tab2, W, base | j));
+        }
+        store16(v, M.psi + pad16(base), 1);
     }
 }
 
@@ -533,19 +596,24 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
     const T2* GT = reinterpret_cast<const T2*>(A.gate_table) + (R ? (size_t)R->gt_off : (size_t)b * A.n_gates);
     real* red = reinterpret_cast<real*>(M.red);
     const int nw = nwarps_of(tm.tt);
-    // |0...0>
-    for (int x = tm.tid; x < padded_amps(W); x += tm.tt) {
-        T2 z;
-        z.x = x == 0 ? 1 : 0;
-        z.y = 0;
-        M.psi[x] = z;   // pad16(0) == 0
-    }
     const int32_t* prog = (R ? R->prog : A.prog) + cd.prog_off;
     const int nl = prog[0];
     const int32_t* lofs = prog + 1;
     const int32_t* body = prog + 1 + nl;
+    if (nl > 0) {   // layer 0 acts on |0..0>: write its product state (and phase) directly
+        const int32_t* lp = body + lofs[0];
+        stage_layer<real, T2>(lp, GT, tm, M, 0, false);
+        init_product_state<real, T2>(M, (unsigned)lp[1], lp[0] > 0, tm, 0);
+    } else {        // |0...0>
+        for (int x = tm.tid; x < padded_amps(W); x += tm.tt) {
+            T2 z;
+            z.x = x == 0 ? 1 : 0;
+            z.y = 0;
+            M.psi[x] = z;   // pad16(0) == 0
+        }
+    }
     tm.sync();
-    for (int li = 0; li < nl; ++li) {
+    for (int li = 1; li < nl; ++li) {
         const int32_t* lp = body + lofs[li];
         const int ndiag = lp[0];
         const int par = li & 1;
@@ -595,7 +663,8 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
             const unsigned m = (todo >> s) & 15u;
             todo &= ~(15u << s);
             real* rb = red + rpar * kMaxPassSlots * nw;
-            pass_bwd<real, T2, false>(M.psi, M.lam, s, m, tm, M, par, rb);
+            if (li == 0) pass_bwd<real, T2, false, true>(M.psi, M.lam, s, m, tm, M, par, rb);
+            else pass_bwd<real, T2, false>(M.psi, M.lam, s, m, tm, M, par, rb);
             tm.sync();
             flush_pass<real, T2>(rb, nw, m, s, M, par, false, gdst, tm);
             rpar ^= 1;
