@@ -613,7 +613,9 @@ def main():
         total_s = float(t.item())
     value = world * Bsz * args.steps / total_s
 
-    # end to end through the host-pointer API (H2D of theta and D2H of energy + gradient inside)
+    # end to end through the host-pointer API (H2D of theta and D2H of energy + gradient inside);
+    # kernel profiling off, as for any caller (it records events around single kernels)
+    B.tlq_profile_enable(ctx.h, False)
     theta_h = np.ascontiguousarray(prob.theta)
     for _ in range(3):
         B.tlq_expectation_grad(ctx.h, c.h, h.h, theta_h)

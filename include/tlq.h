@@ -121,7 +121,10 @@ tlq_status tlq_hamiltonian_create(tlq_ctx ctx, int32_t n_qubits, const tlq_term*
 tlq_status tlq_hamiltonian_destroy(tlq_ham h);
 
 /* Forward pass (Sec. 3, <H>): energy[b] = <psi(theta_b)| H |psi(theta_b)> for b < B.
- * theta: host, row-major [B][n_params] FP64. energy: host [B] FP64. Synchronous.
+ * theta: host, row-major [B][n_params] FP64. energy: host [B] FP64. Synchronous. The device
+ * work of a call (input copy, kernels, output copies) is captured once as a CUDA graph per
+ * (circuit, Hamiltonian, B, precision, gradient or not) and replayed by later calls with the
+ * same key, unless kernel profiling is enabled.
  * EINVAL: B <= 0, null pointers, circuit/Hamiltonian qubit counts differ.
  * ENOMEM: the call's workspace exceeds the context's budget. */
 tlq_status tlq_expectation(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta, int32_t B,

@@ -25,6 +25,7 @@ const char* get_error() { return t_err.c_str(); }
     } while (0)
 
 PlanEntry::~PlanEntry() {
+    if (graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)graph_exec);
     cudaFree(d_cones);
     cudaFree(d_meas);
     cudaFree(d_prog);
@@ -597,6 +598,27 @@ static tlq_status check_pair(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t B, t
     return TLQ_OK;
 }
 
+// Enqueue the synchronous call's device work on `st`: clear the error word, copy the angles
+// from the pinned staging buffer, run the path, copy energies (gradients) and the error word
+// back into the staging buffer.
+static tlq_status sync_enqueue(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t B, tlq_precision prec, bool want_grad,
+                               cudaStream_t st, size_t th_b, size_t e_b, size_t g_b) {
+    ctx->ws.used = 0;
+    double* d_theta = (double*)ctx->ws.take(th_b);
+    double* d_e = (double*)ctx->ws.take(e_b);
+    double* d_g = want_grad ? (double*)ctx->ws.take(g_b) : nullptr;
+    char* hp = (char*)ctx->h_pinned;
+    TLQ_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), st));
+    if (c->n_params > 0)
+        TLQ_CUDA(cudaMemcpyAsync(d_theta, hp, (size_t)B * c->n_params * sizeof(double), cudaMemcpyHostToDevice, st));
+    TLQ_TRY(run_device(ctx, c, h, d_theta, B, prec, d_e, d_g, st, &ctx->ws));
+    TLQ_CUDA(cudaMemcpyAsync(hp + th_b, d_e, e_b, cudaMemcpyDeviceToHost, st));
+    if (want_grad)
+        TLQ_CUDA(cudaMemcpyAsync(hp + th_b + e_b, d_g, (size_t)B * c->n_params * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TLQ_CUDA(cudaMemcpyAsync(hp + th_b + e_b + g_b, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    return TLQ_OK;
+}
+
 static tlq_status sync_call(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta, int32_t B, tlq_precision prec,
                             double* energy, double* grad) {
     TLQ_TRY(check_pair(ctx, c, h, B, prec));
@@ -622,19 +644,47 @@ static tlq_status sync_call(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double*
     TLQ_TRY(reserve(ctx, work + th_b + e_b + g_b + 4096));
     TLQ_TRY(ensure_pinned(ctx, th_b + e_b + g_b + 64));
     cudaStream_t st = (cudaStream_t)ctx->stream;
-    double* d_theta = (double*)ctx->ws.take(th_b);
-    double* d_e = (double*)ctx->ws.take(e_b);
-    double* d_g = want_grad ? (double*)ctx->ws.take(g_b) : nullptr;
     char* hp = (char*)ctx->h_pinned;
     if (c->n_params > 0) std::memcpy(hp, theta, (size_t)B * c->n_params * sizeof(double));
-    TLQ_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), st));
-    if (c->n_params > 0) TLQ_CUDA(cudaMemcpyAsync(d_theta, hp, (size_t)B * c->n_params * sizeof(double), cudaMemcpyHostToDevice, st));
-    TLQ_TRY(run_device(ctx, c, h, d_theta, B, prec, d_e, d_g, st, &ctx->ws));
-    int32_t* h_err = (int32_t*)(hp + th_b + e_b + g_b);
-    TLQ_CUDA(cudaMemcpyAsync(hp + th_b, d_e, e_b, cudaMemcpyDeviceToHost, st));
-    if (want_grad) TLQ_CUDA(cudaMemcpyAsync(hp + th_b + e_b, d_g, (size_t)B * c->n_params * sizeof(double), cudaMemcpyDeviceToHost, st));
-    TLQ_CUDA(cudaMemcpyAsync(h_err, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    // The device work is a fixed launch sequence for a given plan, batch size, precision and
+    // buffers: capture it once as a CUDA graph and replay it (one launch instead of about ten
+    // runtime calls). Profiling records events around single kernels, so it runs uncaptured;
+    // a capture that fails also falls back to direct launches.
+    PlanEntry::GraphKey key;
+    key.B = B;
+    key.prec = (int)prec;
+    key.grad = want_grad ? 1 : 0;
+    key.fuse_k = ctx->cfg.fuse_k;
+    key.ws_base = ctx->ws.base;
+    key.ws_cap = ctx->ws.cap;
+    key.pinned = ctx->h_pinned;
+    key.pinned_cap = ctx->h_pinned_cap;
+    bool launched = false;
+    if (!ctx->profile) {
+        if (!(pe->graph_exec && pe->graph_key == key)) {
+            if (pe->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)pe->graph_exec);
+            pe->graph_exec = nullptr;
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const tlq_status s = sync_enqueue(ctx, c, h, B, prec, want_grad, st, th_b, e_b, g_b);
+                const cudaError_t ce = cudaStreamEndCapture(st, &g);
+                cudaGraphExec_t ex = nullptr;
+                if (s == TLQ_OK && ce == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+                    pe->graph_exec = ex;
+                    pe->graph_key = key;
+                }
+                if (g) cudaGraphDestroy(g);
+            }
+            cudaGetLastError();   // a failed capture leaves nothing behind: run uncaptured below
+        }
+        if (pe->graph_exec) {
+            TLQ_CUDA(cudaGraphLaunch((cudaGraphExec_t)pe->graph_exec, st));
+            launched = true;
+        }
+    }
+    if (!launched) TLQ_TRY(sync_enqueue(ctx, c, h, B, prec, want_grad, st, th_b, e_b, g_b));
     TLQ_CUDA(cudaStreamSynchronize(st));
+    const int32_t* h_err = (const int32_t*)(hp + th_b + e_b + g_b);
     if (*h_err != 0) {
         set_error("kernel error word " + std::to_string(*h_err));
         return TLQ_EKERNEL;

@@ -49,6 +49,20 @@ struct PlanEntry {
     int n_chunks_smem = 0, n_chunks = 0;
     int smem_bytes = 0, gsmem_bytes = 0, g_maxW = 0;
     size_t device_bytes = 0;
+    // CUDA graph of the synchronous call's device work (input copy, kernels, output copies),
+    // replayed while the key below is unchanged; see sync_call in api.cpp
+    void* graph_exec = nullptr;   // cudaGraphExec_t
+    struct GraphKey {
+        int B = -1, prec = -1, grad = -1, fuse_k = -1;
+        void* ws_base = nullptr;
+        size_t ws_cap = 0;
+        void* pinned = nullptr;
+        size_t pinned_cap = 0;
+        bool operator==(const GraphKey& o) const {
+            return B == o.B && prec == o.prec && grad == o.grad && fuse_k == o.fuse_k && ws_base == o.ws_base &&
+                   ws_cap == o.ws_cap && pinned == o.pinned && pinned_cap == o.pinned_cap;
+        }
+    } graph_key;
     ~PlanEntry();
 };
 
