@@ -180,3 +180,21 @@ def test_global_tier_many_windows_batch_invariant(tlq):
         assert E1[0] == E[b]
         assert np.array_equal(g1[0], g[b])
     assert np.all(np.isfinite(E)) and np.all(np.isfinite(g))
+
+
+def test_widest_cones_L9(tlq):
+    # L=9: X windows of 2L+1 = 19 qubits (the cone path takes up to 20), on the global tier,
+    # against the full-chain oracle at n=22 (energy and gradient)
+    from paper_2112_10239_gb300 import binding as B
+    prob = W.tfim_problem(22, 9, 1, seed=17, h_range=(0.5, 1.5))
+    c, h = tlq.problem(prob)
+    try:
+        _, _, _, weff, _, _ = B.tlq_plan_cone_stats(tlq.h, c.h, h.h, len(prob.terms))
+    finally:
+        c.close()
+        h.close()
+    assert max(weff) == 19
+    E, g = _run(tlq, prob)
+    Er, gr = _oracle(prob, prob.theta)
+    check_energy(E, Er)
+    check_grad(g, gr)

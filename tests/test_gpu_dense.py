@@ -246,3 +246,14 @@ def test_dense_fp64_reports_unsupported(tlq):
     finally:
         c.close()
         h.close()
+
+
+def test_dense_largest_state_n31(tlq):
+    # n=31, the largest dense state (2^31 complex64 = 16 GiB): QAOA p=1 on a 3-regular graph
+    # has the closed form E = |edges| cos^2(beta) from |0..0> (the RZZ layer is a global phase);
+    # n=31 is odd, so the graph is built on 30 vertices and qubit 30 stays idle but simulated
+    one = W.qaoa_problem(30, 1, 2, seed=4)
+    m = len(one.meta["edges"])
+    prob = W.Problem(n=31, gates=one.gates, n_params=one.n_params, terms=one.terms, theta=one.theta)
+    E, _ = _energy(tlq, prob)
+    check_energy(E, [m * math.cos(b) ** 2 for b in one.theta[:, 1]])
