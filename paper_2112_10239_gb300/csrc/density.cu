@@ -14,10 +14,12 @@
 //     output has few tiles (small m, long k) the k range is split over CTAs; the splits are
 //     summed in a fixed order by herk_reduce_kernel, so results are deterministic.
 // FP32 products and accumulation (the state's precision), complex64 output.
+#include <cuda.h>   // CUtensorMap and its enums (the encoder is fetched through the runtime)
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "internal.h"
 
@@ -345,7 +347,10 @@ constexpr int kTcStagePitch = 64 + 1;   // complex per staged output row (64 col
 // grid.x = upper 128-tiles, grid.y = k splits; out = rho or partial + split * D * D.
 __global__ void __launch_bounds__(kTcThreads, 2) herk_tc_kernel(const float2* __restrict__ Psi, int64_t D, int64_t K,
                                                                 int64_t k_per_split, float2* __restrict__ out,
-                                                                int32_t* __restrict__ err) {
+                                                                int32_t* __restrict__ err,
+                                                                const __grid_constant__ CUtensorMap tm_rows,
+                                                                const __grid_constant__ CUtensorMap tm_mirror,
+                                                                int use_tma) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char* stage0 = tc_smem;                                 // 2 stages x 40 KB
     uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + 2 * kTcStageBytes);
@@ -405,7 +410,61 @@ __global__ void __launch_bounds__(kTcThreads, 2) herk_tc_kernel(const float2* __
         bad = !mbar_wait(su32(&bars[cl & 1]), (uint32_t)((cl >> 1) & 1));   // every MMA of the tile done
     }
     bad = __syncthreads_or(bad) != 0;
-    if (!bad && nchunks > 0) {
+    if (!bad && nchunks > 0 && use_tma && bi != bj) {
+        // Off-diagonal tile, TMA epilogue: per quarter of 32 columns, the TMEM values are staged
+        // as 128-byte-swizzled boxes (16 complex wide) -- two boxes of 128 rows for rho[i][j]
+        // and eight boxes of 32 rows for the mirror rho[j][i] = conj -- and written by tensor
+        // stores issued by one thread; the next quarter waits until the boxes have been read.
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char* box_rows = tc_smem;                  // 2 x 16 KB (128 rows x 128 B)
+        unsigned char* box_mirror = tc_smem + 32768;        // 8 x 4 KB (32 rows x 128 B)
+        const int q = warp & 3, hh = warp >> 2;            // TMEM lanes 32q.., 16-column group hh
+        const int r = 32 * q + lane;                       // this thread's row of the tile
+#pragma unroll 1
+        for (int qq = 0; qq < 4; ++qq) {
+            const int col = 32 * qq + 16 * hh;             // tile column of this thread's 16 values
+            float vr[16], vi[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, vr);
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kTcTile + col), vi);
+            // rows: box hh, row r, 16-byte chunk c (two complex) at chunk c ^ (r & 7)
+            unsigned char* rb = box_rows + hh * 16384 + r * 128;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                *reinterpret_cast<float4*>(rb + ((c ^ (r & 7)) << 4)) =
+                    make_float4(vr[2 * c], vi[2 * c], vr[2 * c + 1], vi[2 * c + 1]);
+            // mirror: box r / 16, row jl = 16 hh + e (32 rows per box), complex r % 16
+            unsigned char* mb = box_mirror + (r >> 4) * 4096;
+            const int ci = r & 15;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int jl = 16 * hh + e;
+                *reinterpret_cast<float2*>(mb + jl * 128 + ((((ci >> 1) ^ (jl & 7))) << 4) + ((ci & 1) << 3)) =
+                    make_float2(vr[e], -vi[e]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                const uint64_t mr = reinterpret_cast<uint64_t>(&tm_rows);
+                const uint64_t mm = reinterpret_cast<uint64_t>(&tm_mirror);
+                for (int b = 0; b < 2; ++b) {
+                    const int x = (int)(2 * (j0 + 32 * qq + 16 * b)), y = (int)i0;
+                    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(mr),
+                                 "r"(x), "r"(y), "r"(su32(box_rows + b * 16384))
+                                 : "memory");
+                }
+                for (int b = 0; b < 8; ++b) {
+                    const int x = (int)(2 * (i0 + 16 * b)), y = (int)(j0 + 32 * qq);
+                    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(mm),
+                                 "r"(x), "r"(y), "r"(su32(box_mirror + b * 4096))
+                                 : "memory");
+                }
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // boxes may be rewritten
+            }
+            __syncthreads();
+        }
+        if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // stores complete
+    } else if (!bad && nchunks > 0) {
         // Epilogue through shared memory (the stages are free now), one 128 x 64 half of the
         // tile at a time: TMEM -> staged rows, then coalesced row writes of the entries on or
         // above the diagonal and coalesced writes of their conjugate mirrors (rows of rho^T).
@@ -458,6 +517,42 @@ constexpr size_t kTcSmem = 2 * (size_t)kTcStageBytes + 64;
 
 }  // namespace
 
+// Tensor maps of rho (D x D complex64, viewed as float32 [D][2D]) for the TMA epilogue:
+// boxes 32 floats (16 complex, 128 bytes) wide, 128 rows (rho[i][j]) or 32 rows (mirrors),
+// 128-byte swizzle. The encoder is fetched from the driver through the runtime, so the
+// library does not link libcuda. False (no TMA) when rho is not 16-byte aligned or the
+// encoder is unavailable.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static bool encode_rho_maps(float2* rho, int64_t D, CUtensorMap* rows, CUtensorMap* mirror) {
+    if ((reinterpret_cast<uintptr_t>(rho) & 15u) != 0) return false;
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {   // looked up once (thread-safe)
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const bool ok = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                            cudaSuccess &&
+                        q == cudaDriverEntryPointSuccess;
+        cudaGetLastError();
+        return ok ? reinterpret_cast<EncodeTiledFn>(f) : nullptr;
+    }();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * D), (cuuint64_t)D};
+    const cuuint64_t strides[1] = {(cuuint64_t)(8 * D)};
+    const cuuint32_t estr[2] = {1, 1};
+    const cuuint32_t box_rows[2] = {32, (cuuint32_t)kTcTile};
+    const cuuint32_t box_mirror[2] = {32, 32};
+    if (fn(rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, rho, dims, strides, box_rows, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (fn(mirror, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, rho, dims, strides, box_mirror, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    return true;
+}
+
 // Tile and k-split plan shared by the workspace size and the launch: the tensor-core kernel
 // for outputs of at least one 128-tile (m >= 7), the CUDA-core kernel below that; the k range
 // is split (each split a whole number of chunks) until the launch has ~2 CTAs per SM.
@@ -507,7 +602,11 @@ int launch_partial_trace(const void* psi_v, int n, const QubitMap& Q, int m, voi
     if (P.tc) {
         cudaError_t e = cudaFuncSetAttribute(herk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
         if (e != cudaSuccess) return (int)e;
-        herk_tc_kernel<<<grid, kTcThreads, kTcSmem, st>>>(Psi, D, K, P.kps, dst, err);
+        CUtensorMap tm_rows, tm_mirror;
+        std::memset(&tm_rows, 0, sizeof(tm_rows));
+        std::memset(&tm_mirror, 0, sizeof(tm_mirror));
+        const int use_tma = P.splits == 1 && encode_rho_maps(rho, D, &tm_rows, &tm_mirror) ? 1 : 0;
+        herk_tc_kernel<<<grid, kTcThreads, kTcSmem, st>>>(Psi, D, K, P.kps, dst, err, tm_rows, tm_mirror, use_tma);
     } else {
         herk_tile_kernel<<<grid, kHerkThreads, 0, st>>>(Psi, D, K, P.kps, dst);
     }
