@@ -249,6 +249,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
 }
 
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes, one lane per thread.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[e]);
+}
+
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 // Split 4 complex values of row `row` (k = 4 * half .. +3 of the chunk) into the operand parts
@@ -411,57 +424,56 @@ __global__ void __launch_bounds__(kTcThreads, 2) herk_tc_kernel(const float2* __
     }
     bad = __syncthreads_or(bad) != 0;
     if (!bad && nchunks > 0 && use_tma && bi != bj) {
-        // Off-diagonal tile, TMA epilogue: per quarter of 32 columns, the TMEM values are staged
-        // as 128-byte-swizzled boxes (16 complex wide) -- two boxes of 128 rows for rho[i][j]
-        // and eight boxes of 32 rows for the mirror rho[j][i] = conj -- and written by tensor
-        // stores issued by one thread; the next quarter waits until the boxes have been read.
+        // Off-diagonal tile, TMA epilogue in 8 steps of 16 columns, double-buffered: a step's
+        // TMEM values are staged as 128-byte-swizzled boxes (16 complex wide) -- one box of 128
+        // rows for rho[i][j] and eight boxes of 16 rows for the mirror rho[j][i] = conj -- and
+        // written by tensor stores that one thread issues; staging the next step overlaps them,
+        // and a buffer is restaged only after the stores that read it are done.
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        unsigned char* box_rows = tc_smem;                  // 2 x 16 KB (128 rows x 128 B)
-        unsigned char* box_mirror = tc_smem + 32768;        // 8 x 4 KB (32 rows x 128 B)
-        const int q = warp & 3, hh = warp >> 2;            // TMEM lanes 32q.., 16-column group hh
+        const int q = warp & 3, hh = warp >> 2;            // TMEM lanes 32q.., 8-column half hh
         const int r = 32 * q + lane;                       // this thread's row of the tile
+        const int ci = r & 15;
+        const uint64_t mr = reinterpret_cast<uint64_t>(&tm_rows);
+        const uint64_t mm = reinterpret_cast<uint64_t>(&tm_mirror);
 #pragma unroll 1
-        for (int qq = 0; qq < 4; ++qq) {
-            const int col = 32 * qq + 16 * hh;             // tile column of this thread's 16 values
-            float vr[16], vi[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, vr);
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kTcTile + col), vi);
-            // rows: box hh, row r, 16-byte chunk c (two complex) at chunk c ^ (r & 7)
-            unsigned char* rb = box_rows + hh * 16384 + r * 128;
+        for (int st = 0; st < kTcTile / 16; ++st) {
+            unsigned char* buf = tc_smem + (st & 1) * 32768;   // [16 KB rows box][8 x 2 KB mirror boxes]
+            if (tid == 0 && st >= 2) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            __syncthreads();   // this buffer's previous stores have read it
+            const int col = 16 * st + 8 * hh;              // tile column of this thread's 8 values
+            float vr[8], vi[8];
+            tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, vr);
+            tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kTcTile + col), vi);
+            // rows: row r, 16-byte chunk c (two complex) at chunk c ^ (r & 7); this thread has
+            // chunks 4 hh .. 4 hh + 3 of the row
+            unsigned char* rb = buf + r * 128;
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                *reinterpret_cast<float4*>(rb + ((c ^ (r & 7)) << 4)) =
+            for (int c = 0; c < 4; ++c) {
+                const int cc = 4 * hh + c;
+                *reinterpret_cast<float4*>(rb + ((cc ^ (r & 7)) << 4)) =
                     make_float4(vr[2 * c], vi[2 * c], vr[2 * c + 1], vi[2 * c + 1]);
-            // mirror: box r / 16, row jl = 16 hh + e (32 rows per box), complex r % 16
-            unsigned char* mb = box_mirror + (r >> 4) * 4096;
-            const int ci = r & 15;
+            }
+            // mirror: box r / 16 (16 rows x 128 B), row jl = 8 hh + e, complex r % 16
+            unsigned char* mb = buf + 16384 + (r >> 4) * 2048;
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int jl = 16 * hh + e;
+            for (int e = 0; e < 8; ++e) {
+                const int jl = 8 * hh + e;
                 *reinterpret_cast<float2*>(mb + jl * 128 + ((((ci >> 1) ^ (jl & 7))) << 4) + ((ci & 1) << 3)) =
                     make_float2(vr[e], -vi[e]);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (tid == 0) {
-                const uint64_t mr = reinterpret_cast<uint64_t>(&tm_rows);
-                const uint64_t mm = reinterpret_cast<uint64_t>(&tm_mirror);
-                for (int b = 0; b < 2; ++b) {
-                    const int x = (int)(2 * (j0 + 32 * qq + 16 * b)), y = (int)i0;
-                    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(mr),
-                                 "r"(x), "r"(y), "r"(su32(box_rows + b * 16384))
-                                 : "memory");
-                }
-                for (int b = 0; b < 8; ++b) {
-                    const int x = (int)(2 * (i0 + 16 * b)), y = (int)(j0 + 32 * qq);
+                asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(mr),
+                             "r"((int)(2 * (j0 + 16 * st))), "r"((int)i0), "r"(su32(buf))
+                             : "memory");
+                for (int b = 0; b < 8; ++b)
                     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(mm),
-                                 "r"(x), "r"(y), "r"(su32(box_mirror + b * 4096))
+                                 "r"((int)(2 * (i0 + 16 * b))), "r"((int)(j0 + 16 * st)),
+                                 "r"(su32(buf + 16384 + b * 2048))
                                  : "memory");
-                }
                 asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // boxes may be rewritten
             }
-            __syncthreads();
         }
         if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // stores complete
     } else if (!bad && nchunks > 0) {
@@ -518,7 +530,7 @@ constexpr size_t kTcSmem = 2 * (size_t)kTcStageBytes + 64;
 }  // namespace
 
 // Tensor maps of rho (D x D complex64, viewed as float32 [D][2D]) for the TMA epilogue:
-// boxes 32 floats (16 complex, 128 bytes) wide, 128 rows (rho[i][j]) or 32 rows (mirrors),
+// boxes 32 floats (16 complex, 128 bytes) wide, 128 rows (rho[i][j]) or 16 rows (mirrors),
 // 128-byte swizzle. The encoder is fetched from the driver through the runtime, so the
 // library does not link libcuda. False (no TMA) when rho is not 16-byte aligned or the
 // encoder is unavailable.
@@ -542,7 +554,7 @@ static bool encode_rho_maps(float2* rho, int64_t D, CUtensorMap* rows, CUtensorM
     const cuuint64_t strides[1] = {(cuuint64_t)(8 * D)};
     const cuuint32_t estr[2] = {1, 1};
     const cuuint32_t box_rows[2] = {32, (cuuint32_t)kTcTile};
-    const cuuint32_t box_mirror[2] = {32, 32};
+    const cuuint32_t box_mirror[2] = {32, 16};
     if (fn(rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, rho, dims, strides, box_rows, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
