@@ -298,18 +298,19 @@ def serving_replay(B, device, count, rate, seed=4, plain_path=True):
 
 def dense_bytes(B, ctx, c, h, grad):
     """HBM bytes one evaluation of the dense pass sequence moves (the pass schedule's own
-    traffic): every forward pass reads and writes the 2^n complex64 state; with the gradient
-    the final pass also writes lam = H psi, each reverse pass reads and writes psi and lam
-    (the last one only reads), and X/Y strings add a gather sweep that reads psi and lam
-    and writes lam."""
-    n_eff, passes, n_x, _ = B.tlq_plan_dense_info(ctx.h, c.h, h.h)
+    traffic): the start state (layer 0's product state, or |0..0>) is written once, then
+    every forward pass reads and writes the 2^n complex64 state; with the gradient the final
+    pass also writes lam = H psi, each reverse pass reads and writes psi and lam (the last one
+    only reads), and X/Y strings add a gather sweep that reads psi and lam and writes lam.
+    Returns (bytes, forward passes)."""
+    n_eff, passes, n_fwd, n_x, _ = B.tlq_plan_dense_info(ctx.h, c.h, h.h)
     S = 8 * (1 << n_eff)
-    total = passes * 2 * S
+    total = S + n_fwd * 2 * S                   # write of the start state, then the forward passes
     if grad:
         total += S + max(0, passes - 1) * 4 * S + (2 * S if passes > 0 else 0)
         if n_x:
             total += 3 * S
-    return total, passes
+    return total, n_fwd
 
 
 def device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3):

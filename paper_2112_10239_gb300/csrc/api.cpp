@@ -46,6 +46,7 @@ PlanEntry::~PlanEntry() {
     cudaFree(d_dallterms);
     cudaFree(d_dadj_off);
     cudaFree(d_dadj_idx);
+    cudaFree(d_dinit_pcd);
     cudaFree(d_items);
     cudaFree(d_chunks);
 }
@@ -104,6 +105,7 @@ tlq_status get_plan(Context* ctx, Circuit* c, Ham* h, std::shared_ptr<PlanEntry>
             TLQ_TRY(upload(D.all_terms, &pe->d_dallterms, &bytes));
             TLQ_TRY(upload(D.adj_off, &pe->d_dadj_off, &bytes));
             TLQ_TRY(upload(D.adj_idx, &pe->d_dadj_idx, &bytes));
+            TLQ_TRY(upload(D.init_pcd, &pe->d_dinit_pcd, &bytes));
         }
         pe->device_bytes = bytes;
         ctx->held += bytes;
@@ -280,6 +282,13 @@ static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const
     L.sm_count = ctx->sm_count;
     L.host_gates = c.gates.data();
     L.host_passes = D.passes.data();
+    L.product_init = D.product_init;
+    L.host_fwd_passes = D.fwd_passes.data();
+    L.n_fwd_passes = (int32_t)D.fwd_passes.size();
+    L.host_init_gate = D.init_gate.data();
+    L.init_class_off = D.init_class_off;
+    L.init_nclass = D.init_nclass;
+    L.init_pcd = pe.d_dinit_pcd;
     L.host_xterms = D.xterms.data();
     L.host_all_terms = D.all_terms.data();
     L.n_all_terms = (int32_t)D.all_terms.size();
@@ -929,7 +938,7 @@ tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n
 }
 
 tlq_status tlq_plan_dense_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n_eff, int32_t* n_passes,
-                               int32_t* n_xterms, int32_t* fused) {
+                               int32_t* n_fwd_passes, int32_t* n_xterms, int32_t* fused) {
     if (!ctx || !c || !h) { set_error("NULL handle"); return TLQ_EINVAL; }
     if (c->n != h->n) { set_error("circuit and Hamiltonian qubit counts differ"); return TLQ_EINVAL; }
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -939,6 +948,7 @@ tlq_status tlq_plan_dense_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n
     const DensePlan& D = *pe->plan->dense;
     if (n_eff) *n_eff = D.n_eff;
     if (n_passes) *n_passes = (int32_t)D.passes.size();
+    if (n_fwd_passes) *n_fwd_passes = D.product_init ? (int32_t)D.fwd_passes.size() : (int32_t)D.passes.size();
     if (n_xterms) *n_xterms = (int32_t)D.xterms.size();
     if (fused) *fused = D.fits_fused ? 1 : 0;
     return TLQ_OK;

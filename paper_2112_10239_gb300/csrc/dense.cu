@@ -653,6 +653,62 @@ __global__ void __launch_bounds__(kMeasThreads) pergate_grad_kernel(const float2
     }
 }
 
+// The state after layer 0 from |0..0> (layer 0 acts on |0..0>): single-qubit rotations give a
+// product state, amplitude(x) = prod_q f_q(x_q) with f_q(0) = cos(a_q/2) and f_q(1) = sin(a_q/2)
+// (RY) or -i sin(a_q/2) (RX), 1 and 0 for a qubit without a rotation; then layer 0's diagonal
+// classes (phase exp(-i a/2 (N - 2c)) from the phase table, or the CZ sign (-1)^c). Each
+// thread writes 16 consecutive amplitudes: the product over bits 4.. once, the low four bits
+// by doubling. Replaces the layer-0 passes of the forward sweep.
+struct InitGates { int32_t gate[32]; };
+
+__device__ __forceinline__ float2 init_factor(const InitGates& I, const tlq_gate* gates, const float2* GT, int q,
+                                              int bit) {
+    const int g = I.gate[q];
+    if (g < 0) return make_float2(bit ? 0.f : 1.f, 0.f);
+    const float2 cs = GT[g];
+    if (!bit) return make_float2(cs.x, 0.f);
+    return gates[g].kind == TLQ_RY ? make_float2(cs.y, 0.f) : make_float2(0.f, -cs.y);
+}
+
+__global__ void dense_product_init_kernel(float2* psi, int n_eff, const __grid_constant__ InitGates I,
+                                          const tlq_gate* gates, const float2* GT, const DenseClassDev* classes,
+                                          int cls_off, int ncls, const DensePassClassDev* pcd, const int32_t* dists,
+                                          const float2* ptab) {
+    const uint64_t nblk = 1ull << (n_eff - 4);
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nblk; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t x0 = (uint32_t)(t << 4);
+        float2 v[16];
+        v[0] = make_float2(1.f, 0.f);
+        for (int q = 4; q < n_eff; ++q) v[0] = cmul(v[0], init_factor(I, gates, GT, q, (x0 >> q) & 1u));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 f0 = init_factor(I, gates, GT, k, 0), f1 = init_factor(I, gates, GT, k, 1);
+#pragma unroll
+            for (int j = 0; j < (1 << k); ++j) {
+                v[j | (1 << k)] = cmul(v[j], f1);
+                v[j] = cmul(v[j], f0);
+            }
+        }
+        // layer 0's diagonal from split counts over bits 0..3 (one full count per class)
+        for (int ci = 0; ci < ncls; ++ci) {
+            const DenseClassDev C = classes[cls_off + ci];
+            const DensePassClassDev pc = pcd[ci];
+            const int cnt0 = class_count(C, dists + 2 * C.dist_off, x0);
+            int Ak[4];
+            split_deltas(C, pc, x0, Ak);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int cnt = split_count(pc, cnt0, Ak, j);
+                if (C.kind == 0) v[j] = cmul(v[j], ptab[C.tab_off + cnt]);
+                else if (cnt & 1) v[j] = make_float2(-v[j].x, -v[j].y);
+            }
+        }
+        float4* out = reinterpret_cast<float4*>(psi + x0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) out[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+    }
+}
+
 __global__ void init_state_kernel(float2* psi, uint64_t N) {
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x)
         psi[x] = make_float2(x == 0 ? 1.f : 0.f, 0.f);
@@ -751,9 +807,18 @@ int launch_dense(DenseLaunch& L, void* stream) {
                                                                                  L.tab_entries, th, PT);
             ++launches;
         }
-        init_state_kernel<<<grid_sweep, 256, 0, st>>>(psi, N);
-        ++launches;
         if (b == 0 && L.ev_begin && (e = cudaEventRecord((cudaEvent_t)L.ev_begin, st)) != cudaSuccess) return (int)e;
+        const bool product_init = !L.per_gate && L.product_init;
+        if (product_init) {   // the state after layer 0, written directly
+            InitGates I;
+            for (int q = 0; q < 32; ++q) I.gate[q] = q < L.n_eff ? L.host_init_gate[q] : -1;
+            dense_product_init_kernel<<<grid_sweep, 256, 0, st>>>(psi, L.n_eff, I, L.gates, GT, L.classes,
+                                                                  L.init_class_off, L.init_nclass, L.init_pcd,
+                                                                  L.dists, PT);
+        } else {
+            init_state_kernel<<<grid_sweep, 256, 0, st>>>(psi, N);
+        }
+        ++launches;
         double* eout = L.energy + b;
         if ((e = cudaMemsetAsync(eout, 0, sizeof(double), st)) != cudaSuccess) return (int)e;
         if (L.per_gate) {
@@ -780,8 +845,10 @@ int launch_dense(DenseLaunch& L, void* stream) {
             A.lam = nullptr;
             const int grid = dense_grid(L.n_eff, L.sm_count);
             bool measured = false;
-            for (int p = 0; p < L.n_passes; ++p) {
-                A.pass = L.host_passes[p];
+            const DensePassDev* fwd = product_init ? L.host_fwd_passes : L.host_passes;
+            const int n_fwd = product_init ? L.n_fwd_passes : L.n_passes;
+            for (int p = 0; p < n_fwd; ++p) {
+                A.pass = fwd[p];
                 if (gout) {
                     A.pass.store = 1;   // the adjoint starts from the final state in HBM
                     if (A.pass.measure_group >= 0) A.lam = lam;

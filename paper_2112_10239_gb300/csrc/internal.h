@@ -156,6 +156,15 @@ struct DensePlan {
     std::vector<DenseXTermDev> all_terms;   // every term (plain per-gate path measures them one by one)
     std::vector<DensePassClassDev> pcd;     // per (pass, group, class): split counts
     std::vector<int32_t> stage;             // per pass: classes staged in shared memory
+    // Product-state start (two or more layers): the forward writes layer 0's result directly --
+    // the init_gate rotations (per qubit, -1 none) on |0..0> times layer 0's diagonal classes
+    // [init_class_off, +init_nclass) with split counts init_pcd over bits 0..3 -- and then runs
+    // fwd_passes (layers 1..); the adjoint walks `passes` (all layers) in reverse.
+    bool product_init = false;
+    std::vector<DensePassDev> fwd_passes;
+    std::vector<int32_t> init_gate;
+    int32_t init_class_off = 0, init_nclass = 0;
+    std::vector<DensePassClassDev> init_pcd;
     // adjoint: for parameter p, entries adj_idx[adj_off[p] .. adj_off[p+1]) are the
     // (pass * kDenseAdjSlots + slot) gradient slots that carry it, in a fixed order
     std::vector<int32_t> adj_off;
@@ -352,6 +361,12 @@ struct DenseLaunch {
     double* partial = nullptr;            // per-CTA / per-block partial sums
     double* xpart = nullptr;              // [n_xterms] per set
     int32_t* err = nullptr;               // kernel error word
+    bool product_init = false;            // DensePlan::product_init
+    const DensePassDev* host_fwd_passes = nullptr;   // DensePlan::fwd_passes
+    int32_t n_fwd_passes = 0;
+    const int32_t* host_init_gate = nullptr;   // DensePlan::init_gate (n_eff entries)
+    int32_t init_class_off = 0, init_nclass = 0;
+    const DensePassClassDev* init_pcd = nullptr;   // device copy of DensePlan::init_pcd
     void* lam = nullptr;                  // gradient mode: 2^n_eff float2 adjoint state
     double* gpart = nullptr;              // gradient mode: [n_passes][kDenseAdjSlots][grid] partials
     // outputs

@@ -573,145 +573,171 @@ std::shared_ptr<DensePlan> make_dense_plan(const Circuit& c, const Ham& h, std::
         return (q >= a && q < a + kDenseStridedBits) ? 4 + q - a : -1;
     };
     struct GroupDiag { int pass, group, layer; };     // diagonal (or energy: layer = -1) after a group
-    std::vector<GroupDiag> gdiag;
-    std::vector<int> pend;                            // pending rotation gates of layer l
-    int l = 0;
-    auto load_layer = [&]() {
-        pend.clear();
-        if (l < L) pend = c.layers[l].rot;
-    };
-    load_layer();
-    while (l < L) {
-        // choose the pattern with the most pending rotations
-        int best = -1, bestn = -1;
-        for (int pat = -1; pat < (int)chunk_a.size(); ++pat) {
-            int cnt = 0;
-            for (int g : pend) cnt += local_of(pat, c.gates[g].q0) >= 0;
-            if (cnt > bestn) { bestn = cnt; best = pat; }
-        }
-        DensePassDev pass = blank(best >= 0, best >= 0 ? chunk_a[best] : 0);
-        const int pi = (int)D->passes.size();
-        for (;;) {
-            // rotations of layer l on this tile
-            uint32_t bits = 0;
-            int gate_at[16];
-            for (int k = 0; k < 16; ++k) gate_at[k] = -1;
-            std::vector<int> rest;
-            for (int g : pend) {
-                const int lb = local_of(best, c.gates[g].q0);
-                if (lb >= 0 && !((bits >> lb) & 1)) { bits |= 1u << lb; gate_at[lb] = g; }
-                else rest.push_back(g);
+    // Greedy schedule of layers [l0, l1) into `out` (pass indices in gdiag are into `out`).
+    auto schedule = [&](int l0, int l1, std::vector<DensePassDev>& out, std::vector<GroupDiag>& gdiag) {
+        std::vector<int> pend;                        // pending rotation gates of layer l
+        int l = l0;
+        auto load_layer = [&]() {
+            pend.clear();
+            if (l < l1) pend = c.layers[l].rot;
+        };
+        load_layer();
+        while (l < l1) {
+            // choose the pattern with the most pending rotations
+            int best = -1, bestn = -1;
+            for (int pat = -1; pat < (int)chunk_a.size(); ++pat) {
+                int cnt = 0;
+                for (int g : pend) cnt += local_of(pat, c.gates[g].q0) >= 0;
+                if (cnt > bestn) { bestn = cnt; best = pat; }
             }
-            int need = 0;
-            for (uint32_t b2 = bits; b2;) {
-                const int b = __builtin_ctz(b2);
-                const int s = b < 4 ? 0 : std::min(b, kDenseTileBits - 4);
-                b2 &= ~(15u << s);
-                ++need;
+            DensePassDev pass = blank(best >= 0, best >= 0 ? chunk_a[best] : 0);
+            const int pi = (int)out.size();
+            for (;;) {
+                // rotations of layer l on this tile
+                uint32_t bits = 0;
+                int gate_at[16];
+                for (int k = 0; k < 16; ++k) gate_at[k] = -1;
+                std::vector<int> rest;
+                for (int g : pend) {
+                    const int lb = local_of(best, c.gates[g].q0);
+                    if (lb >= 0 && !((bits >> lb) & 1)) { bits |= 1u << lb; gate_at[lb] = g; }
+                    else rest.push_back(g);
+                }
+                int need = 0;
+                for (uint32_t b2 = bits; b2;) {
+                    const int b = __builtin_ctz(b2);
+                    const int s = b < 4 ? 0 : std::min(b, kDenseTileBits - 4);
+                    b2 &= ~(15u << s);
+                    ++need;
+                }
+                const bool completes = rest.empty();
+                if (pass.ngroups + std::max(need, completes ? 1 : 0) > kDenseMaxGroups) break;
+                while (bits) {
+                    const int b = __builtin_ctz(bits);
+                    const int s = b < 4 ? 0 : std::min(b, kDenseTileBits - 4);
+                    const int gi = pass.ngroups++;
+                    pass.group_s[gi] = s;
+                    pass.group_mask[gi] = (bits >> s) & 15u;
+                    for (int k = 0; k < 4; ++k)
+                        if ((pass.group_mask[gi] >> k) & 1) pass.gate[gi][k] = gate_at[s + k];
+                    bits &= ~(15u << s);
+                }
+                pend = rest;
+                if (!completes) break;
+                // layer l done on the whole state: its diagonal follows the last group
+                if (pass.ngroups == 0) {
+                    pass.group_s[0] = kDenseTileBits - 4;
+                    pass.group_mask[0] = 0;
+                    pass.ngroups = 1;
+                }
+                if (!c.layers[l].diag.empty()) gdiag.push_back({pi, pass.ngroups - 1, l});
+                ++l;
+                load_layer();
+                if (l >= l1) break;
+                if (pass.ngroups >= kDenseMaxGroups) break;
             }
-            const bool completes = rest.empty();
-            if (pass.ngroups + std::max(need, completes ? 1 : 0) > kDenseMaxGroups) break;
-            while (bits) {
-                const int b = __builtin_ctz(bits);
-                const int s = b < 4 ? 0 : std::min(b, kDenseTileBits - 4);
-                const int gi = pass.ngroups++;
-                pass.group_s[gi] = s;
-                pass.group_mask[gi] = (bits >> s) & 15u;
-                for (int k = 0; k < 4; ++k)
-                    if ((pass.group_mask[gi] >> k) & 1) pass.gate[gi][k] = gate_at[s + k];
-                bits &= ~(15u << s);
-            }
-            pend = rest;
-            if (!completes) break;
-            // layer l done on the whole state: its diagonal follows the last group
-            if (pass.ngroups == 0) {
+            if (pass.ngroups == 0) {   // nothing fit (cannot happen with 8 groups) -- keep the loop finite
                 pass.group_s[0] = kDenseTileBits - 4;
                 pass.group_mask[0] = 0;
                 pass.ngroups = 1;
             }
-            if (!c.layers[l].diag.empty()) gdiag.push_back({pi, pass.ngroups - 1, l});
-            ++l;
-            load_layer();
-            if (l >= L) break;
-            if (pass.ngroups >= kDenseMaxGroups) break;
+            out.push_back(pass);
         }
-        if (pass.ngroups == 0) {   // nothing fit (cannot happen with 8 groups) -- keep the loop finite
-            pass.group_s[0] = kDenseTileBits - 4;
-            pass.group_mask[0] = 0;
-            pass.ngroups = 1;
-        }
-        D->passes.push_back(pass);
-    }
-    const bool want_energy = D->energy_nclass > 0 || !D->zterms.empty();
-    if (want_energy) {
-        if (D->passes.empty()) {
-            DensePassDev p = blank(0, 0);
-            p.ngroups = 1;
-            p.group_s[0] = kDenseTileBits - 4;
-            p.store = 0;
-            D->passes.push_back(p);
-        }
-        gdiag.push_back({(int)D->passes.size() - 1, D->passes.back().ngroups - 1, -1});
-        D->passes.back().measure_group = D->passes.back().ngroups - 1;
-    }
-    // stage lists and split counts: per pass, the classes of every group that evaluates some
-    for (int pi = 0; pi < (int)D->passes.size(); ++pi) {
-        DensePassDev& pass = D->passes[pi];
-        pass.stage_off = (int32_t)D->stage.size();
-        for (const GroupDiag& gd : gdiag) {
-            if (gd.pass != pi) continue;
-            const int gi = gd.group;
-            int first_cls, ncls;
-            if (gd.layer >= 0) {
-                first_cls = D->layers[gd.layer].class_off;
-                ncls = D->layers[gd.layer].nclass;
-            } else {
-                first_cls = D->energy_class_off;
-                ncls = D->energy_nclass;
-            }
-            if (pass.group_ncls[gi] == 0) {
-                pass.group_cls[gi] = (int32_t)D->stage.size() - pass.stage_off;
-                pass.group_pcd[gi] = (int32_t)D->pcd.size();
-            }
-            pass.group_ncls[gi] += ncls;
-            const int s = pass.group_s[gi];
-            int gbit[4];
-            for (int k = 0; k < 4; ++k) {
-                const int local = s + k;
-                gbit[k] = pass.strided ? (local < 4 ? local : pass.a + local - 4) : local;
-            }
-            auto kof = [&](int q) { for (int k = 0; k < 4; ++k) if (gbit[k] == q) return k; return -1; };
-            for (int ci = first_cls; ci < first_cls + ncls; ++ci) {
-                const DenseClassDev& cl = D->classes[ci];
-                D->stage.push_back(ci);
-                DensePassClassDev pc{};
-                uint32_t cnt[16] = {0};
-                for (int k = 0; k < cl.ndist; ++k) {
-                    const int d = D->dists[2 * (cl.dist_off + k)];
-                    const uint32_t M = (uint32_t)D->dists[2 * (cl.dist_off + k) + 1];
-                    for (int u = 0; u < 32; ++u) {
-                        if (!((M >> u) & 1)) continue;
-                        const int v = u + d;
-                        const int ku = kof(u), kv = kof(v);
-                        if (ku >= 0 && kv >= 0) {
-                            for (int jj = 0; jj < 16; ++jj) {
-                                const int bu = (jj >> ku) & 1, bv = (jj >> kv) & 1;
-                                cnt[jj] += cl.kind == 1 ? (bu & bv) : (bu ^ bv);
-                            }
-                        } else if (ku >= 0) {
-                            pc.N[ku] |= 1u << v;
-                        } else if (kv >= 0) {
-                            pc.N[kv] |= 1u << u;
-                        }
+    };
+    // Split counts of class `cl` over register bits gbit[0..3] (global qubits; see
+    // DensePassClassDev): partners outside the bits per bit, in-group counts C[j].
+    auto split_counts = [&](const DenseClassDev& cl, const int (&gbit)[4]) {
+        auto kof = [&](int q) { for (int k = 0; k < 4; ++k) if (gbit[k] == q) return k; return -1; };
+        DensePassClassDev pc{};
+        uint32_t cnt[16] = {0};
+        for (int k = 0; k < cl.ndist; ++k) {
+            const int d = D->dists[2 * (cl.dist_off + k)];
+            const uint32_t M = (uint32_t)D->dists[2 * (cl.dist_off + k) + 1];
+            for (int u = 0; u < 32; ++u) {
+                if (!((M >> u) & 1)) continue;
+                const int v = u + d;
+                const int ku = kof(u), kv = kof(v);
+                if (ku >= 0 && kv >= 0) {
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int bu = (jj >> ku) & 1, bv = (jj >> kv) & 1;
+                        cnt[jj] += cl.kind == 1 ? (bu & bv) : (bu ^ bv);
                     }
+                } else if (ku >= 0) {
+                    pc.N[ku] |= 1u << v;
+                } else if (kv >= 0) {
+                    pc.N[kv] |= 1u << u;
                 }
-                for (int k = 0; k < 4; ++k)
-                    if ((cl.single >> gbit[k]) & 1) pc.single |= 1u << k;
-                for (int jj = 0; jj < 16; ++jj) pc.C[jj >> 2] |= cnt[jj] << (8 * (jj & 3));
-                D->pcd.push_back(pc);
             }
         }
-        pass.nstage = (int32_t)D->stage.size() - pass.stage_off;
+        for (int k = 0; k < 4; ++k)
+            if ((cl.single >> gbit[k]) & 1) pc.single |= 1u << k;
+        for (int jj = 0; jj < 16; ++jj) pc.C[jj >> 2] |= cnt[jj] << (8 * (jj & 3));
+        return pc;
+    };
+    // The energy after the last pass of P, then per pass the staged classes of every group
+    // that evaluates some, with their split counts (shared pools D->stage and D->pcd).
+    const bool want_energy = D->energy_nclass > 0 || !D->zterms.empty();
+    auto finalize = [&](std::vector<DensePassDev>& P, std::vector<GroupDiag>& gdiag) {
+        if (want_energy) {
+            if (P.empty()) {
+                DensePassDev p = blank(0, 0);
+                p.ngroups = 1;
+                p.group_s[0] = kDenseTileBits - 4;
+                p.store = 0;
+                P.push_back(p);
+            }
+            gdiag.push_back({(int)P.size() - 1, P.back().ngroups - 1, -1});
+            P.back().measure_group = P.back().ngroups - 1;
+        }
+        for (int pi = 0; pi < (int)P.size(); ++pi) {
+            DensePassDev& pass = P[pi];
+            pass.stage_off = (int32_t)D->stage.size();
+            for (const GroupDiag& gd : gdiag) {
+                if (gd.pass != pi) continue;
+                const int gi = gd.group;
+                int first_cls, ncls;
+                if (gd.layer >= 0) {
+                    first_cls = D->layers[gd.layer].class_off;
+                    ncls = D->layers[gd.layer].nclass;
+                } else {
+                    first_cls = D->energy_class_off;
+                    ncls = D->energy_nclass;
+                }
+                if (pass.group_ncls[gi] == 0) {
+                    pass.group_cls[gi] = (int32_t)D->stage.size() - pass.stage_off;
+                    pass.group_pcd[gi] = (int32_t)D->pcd.size();
+                }
+                pass.group_ncls[gi] += ncls;
+                const int s = pass.group_s[gi];
+                int gbit[4];
+                for (int k = 0; k < 4; ++k) {
+                    const int local = s + k;
+                    gbit[k] = pass.strided ? (local < 4 ? local : pass.a + local - 4) : local;
+                }
+                for (int ci = first_cls; ci < first_cls + ncls; ++ci) {
+                    D->stage.push_back(ci);
+                    D->pcd.push_back(split_counts(D->classes[ci], gbit));
+                }
+            }
+            pass.nstage = (int32_t)D->stage.size() - pass.stage_off;
+        }
+    };
+    // The full schedule (used by the adjoint, and by the forward from |0..0>) and, for two or
+    // more layers, a forward schedule of layers 1.. that starts from layer 0's product state.
+    std::vector<GroupDiag> gd_all, gd_fwd;
+    D->init_gate.assign(n_eff, -1);
+    schedule(0, L, D->passes, gd_all);
+    finalize(D->passes, gd_all);
+    D->product_init = L >= 2;
+    if (D->product_init) {
+        schedule(1, L, D->fwd_passes, gd_fwd);
+        finalize(D->fwd_passes, gd_fwd);
+        for (int g : c.layers[0].rot) D->init_gate[c.gates[g].q0] = g;
+        D->init_class_off = D->layers[0].class_off;
+        D->init_nclass = D->layers[0].nclass;
+        const int gbit0[4] = {0, 1, 2, 3};
+        for (int ci = D->init_class_off; ci < D->init_class_off + D->init_nclass; ++ci)
+            D->init_pcd.push_back(split_counts(D->classes[ci], gbit0));
     }
     // adjoint slots: rotation k of group g -> 4g + k; staged class ci (kind 0, a parameter) ->
     // 4 * kDenseMaxGroups + ci; collected per parameter with a counting sort (pass-major order)
@@ -739,7 +765,9 @@ std::shared_ptr<DensePlan> make_dense_plan(const Circuit& c, const Ham& h, std::
         for (auto& e : ent) D->adj_idx[fill[e.first]++] = e.second;
     }
     // shared-memory capacity of the pass kernel
-    for (const DensePassDev& pass : D->passes) {
+    std::vector<DensePassDev> all_passes = D->passes;
+    all_passes.insert(all_passes.end(), D->fwd_passes.begin(), D->fwd_passes.end());
+    for (const DensePassDev& pass : all_passes) {
         int words = 0, tab = 0;
         for (int k = 0; k < pass.nstage; ++k) {
             const DenseClassDev& cl = D->classes[D->stage[pass.stage_off + k]];

@@ -40,6 +40,7 @@ struct PlanEntry {
     DenseXTermDev* d_dallterms = nullptr;
     int32_t* d_dadj_off = nullptr;
     int32_t* d_dadj_idx = nullptr;
+    DensePassClassDev* d_dinit_pcd = nullptr;
     // work list cache (keyed by batch size and precision)
     int wl_B = -1;
     bool wl_fp64 = false;
