@@ -300,14 +300,15 @@ def dense_bytes(B, ctx, c, h, grad):
     """HBM bytes one evaluation of the dense pass sequence moves (the pass schedule's own
     traffic): the start state (layer 0's product state, or |0..0>) is written once, then
     every forward pass reads and writes the 2^n complex64 state; with the gradient the final
-    pass also writes lam = H psi, each reverse pass reads and writes psi and lam (the last one
-    only reads), and X/Y strings add a gather sweep that reads psi and lam and writes lam.
+    pass also writes lam = H psi, each reverse pass reads psi and lam and writes both back
+    unless nothing after it needs them, and X/Y strings add a gather sweep that reads psi and
+    lam and writes lam.
     Returns (bytes, forward passes)."""
-    n_eff, passes, n_fwd, n_x, _ = B.tlq_plan_dense_info(ctx.h, c.h, h.h)
+    n_eff, passes, n_fwd, n_rev_store, n_x, _ = B.tlq_plan_dense_info(ctx.h, c.h, h.h)
     S = 8 * (1 << n_eff)
     total = S + n_fwd * 2 * S                   # write of the start state, then the forward passes
-    if grad:
-        total += S + max(0, passes - 1) * 4 * S + (2 * S if passes > 0 else 0)
+    if grad:                                    # lambda written; reverse passes read (and some write) both
+        total += S + passes * 2 * S + n_rev_store * 2 * S
         if n_x:
             total += 3 * S
     return total, n_fwd

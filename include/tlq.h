@@ -249,13 +249,15 @@ tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n
  * number of streaming passes *n_passes the adjoint makes over the state (in reverse); the
  * number *n_fwd_passes the forward makes -- with two or more layers the forward first writes
  * layer 0's result directly (one write of the state, layer 0 acting on |0..0>) and then runs
- * a schedule of the remaining layers; the number of Pauli strings with X/Y letters *n_xterms
+ * a schedule of the remaining layers; the number of reverse passes *n_rev_store that write psi
+ * and lambda back (the others only read: the first pass, and passes that only give layer 0's
+ * rotation gradients); the number of Pauli strings with X/Y letters *n_xterms
  * measured by separate sweeps; and *fused = 1 when the fused passes are used (0: the plan's
  * staged data exceed the pass kernel's shared memory and the plain per-gate sweeps run
  * instead). Any out pointer may be NULL. TLQ_EUNSUPPORTED when (c, h) has no dense plan (more
  * than 31 qubits). */
 tlq_status tlq_plan_dense_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n_eff, int32_t* n_passes,
-                               int32_t* n_fwd_passes, int32_t* n_xterms, int32_t* fused);
+                               int32_t* n_fwd_passes, int32_t* n_rev_store, int32_t* n_xterms, int32_t* fused);
 
 /* Kernel timing for benchmarks. While enabled, every compute call records CUDA events
  * around its dominant kernel (the batched cone kernel, or the dense pass sequence) on the

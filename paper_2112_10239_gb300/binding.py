@@ -81,7 +81,7 @@ def lib():
         L.tlq_last_error.restype = ctypes.c_char_p
         L.tlq_plan_info.argtypes = [vp, vp, vp, ip, ip, ip, ip]
         L.tlq_plan_cone_stats.argtypes = [vp, vp, vp, ip, ip, ip, ip, ip, ip, ip]
-        L.tlq_plan_dense_info.argtypes = [vp, vp, vp, ip, ip, ip, ip, ip]
+        L.tlq_plan_dense_info.argtypes = [vp, vp, vp, ip, ip, ip, ip, ip, ip]
         L.tlq_partial_trace_dev.argtypes = [vp, vp, ctypes.c_int32, ip, ctypes.c_int32, vp, vp]
         L.tlq_reduced_density.argtypes = [vp, vp, dp, ip, ctypes.c_int32, dp]
         L.tlq_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -255,8 +255,8 @@ def tlq_plan_cone_stats(ctx, circ, ham, n_terms):
 
 
 def tlq_plan_dense_info(ctx, circ, ham):
-    """(n_eff, n_passes, n_fwd_passes, n_xterms, fused) of the dense statevector plan."""
-    v = [ctypes.c_int32() for _ in range(5)]
+    """(n_eff, n_passes, n_fwd_passes, n_rev_store, n_xterms, fused) of the dense plan."""
+    v = [ctypes.c_int32() for _ in range(6)]
     _check(lib().tlq_plan_dense_info(ctx, circ, ham, *[ctypes.byref(x) for x in v]), ctx)
     return tuple(x.value for x in v)
 

@@ -284,6 +284,7 @@ static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const
     L.host_passes = D.passes.data();
     L.product_init = D.product_init;
     L.host_fwd_passes = D.fwd_passes.data();
+    L.host_rev_store = D.rev_store.data();
     L.n_fwd_passes = (int32_t)D.fwd_passes.size();
     L.host_init_gate = D.init_gate.data();
     L.init_class_off = D.init_class_off;
@@ -938,7 +939,7 @@ tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n
 }
 
 tlq_status tlq_plan_dense_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n_eff, int32_t* n_passes,
-                               int32_t* n_fwd_passes, int32_t* n_xterms, int32_t* fused) {
+                               int32_t* n_fwd_passes, int32_t* n_rev_store, int32_t* n_xterms, int32_t* fused) {
     if (!ctx || !c || !h) { set_error("NULL handle"); return TLQ_EINVAL; }
     if (c->n != h->n) { set_error("circuit and Hamiltonian qubit counts differ"); return TLQ_EINVAL; }
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -949,6 +950,11 @@ tlq_status tlq_plan_dense_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n
     if (n_eff) *n_eff = D.n_eff;
     if (n_passes) *n_passes = (int32_t)D.passes.size();
     if (n_fwd_passes) *n_fwd_passes = D.product_init ? (int32_t)D.fwd_passes.size() : (int32_t)D.passes.size();
+    if (n_rev_store) {
+        int32_t k = 0;
+        for (int32_t v : D.rev_store) k += v;
+        *n_rev_store = k;
+    }
     if (n_xterms) *n_xterms = (int32_t)D.xterms.size();
     if (fused) *fused = D.fits_fused ? 1 : 0;
     return TLQ_OK;

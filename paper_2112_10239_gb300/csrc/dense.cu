@@ -337,6 +337,16 @@ __device__ __forceinline__ void adjoint_bit(const AdjArgs& A, int g, float2 (&v)
     if (lane == 0) acc[4 * g + K] += (double)gk;
 }
 
+// Layer-0 rotation on register bit K: gradient only (see DensePassDev::group_rot0).
+template <int K>
+__device__ __forceinline__ void gradient_bit(const AdjArgs& A, int g, const float2 (&v)[16], const float2 (&u)[16],
+                                             double* acc, int lane) {
+    const int gate = A.pass.gate[g][K];
+    float gk = A.gates[gate].kind == TLQ_RY ? grad_y<K, float2, float>(v, u) : grad_x<K, float2, float>(v, u);
+    gk = warp_sum(gk);
+    if (lane == 0) acc[4 * g + K] += (double)gk;
+}
+
 __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid_constant__ AdjArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2* bpsi = reinterpret_cast<float2*>(smem_raw);                               // padded_amps(12)
@@ -417,12 +427,20 @@ __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid
                     }
                 }
             }
-            // the group's rotations: gradient, then the inverse rotation on both states
+            // the group's rotations: gradient, then the inverse rotation on both states; layer 0's
+            // rotations commute and nothing after them needs the state, so they only give gradients
             const unsigned m = P.group_mask[g];
-            if (m & 1u) adjoint_bit<0>(A, g, v, u, acc, lane);
-            if (m & 2u) adjoint_bit<1>(A, g, v, u, acc, lane);
-            if (m & 4u) adjoint_bit<2>(A, g, v, u, acc, lane);
-            if (m & 8u) adjoint_bit<3>(A, g, v, u, acc, lane);
+            if ((P.group_rot0 >> g) & 1u) {
+                if (m & 1u) gradient_bit<0>(A, g, v, u, acc, lane);
+                if (m & 2u) gradient_bit<1>(A, g, v, u, acc, lane);
+                if (m & 4u) gradient_bit<2>(A, g, v, u, acc, lane);
+                if (m & 8u) gradient_bit<3>(A, g, v, u, acc, lane);
+            } else {
+                if (m & 1u) adjoint_bit<0>(A, g, v, u, acc, lane);
+                if (m & 2u) adjoint_bit<1>(A, g, v, u, acc, lane);
+                if (m & 4u) adjoint_bit<2>(A, g, v, u, acc, lane);
+                if (m & 8u) adjoint_bit<3>(A, g, v, u, acc, lane);
+            }
             if (g > 0) {
                 store16(v, bpsi + pad16(base), stride);
                 store16(u, blam + pad16(base), stride);
@@ -670,19 +688,50 @@ __device__ __forceinline__ float2 init_factor(const InitGates& I, const tlq_gate
     return gates[g].kind == TLQ_RY ? make_float2(cs.y, 0.f) : make_float2(0.f, -cs.y);
 }
 
-__global__ void dense_product_init_kernel(float2* psi, int n_eff, const __grid_constant__ InitGates I,
-                                          const tlq_gate* gates, const float2* GT, const DenseClassDev* classes,
-                                          int cls_off, int ncls, const DensePassClassDev* pcd, const int32_t* dists,
-                                          const float2* ptab) {
+__global__ void __launch_bounds__(256) dense_product_init_kernel(float2* psi, int n_eff,
+                                                                  const __grid_constant__ InitGates I,
+                                                                  const tlq_gate* gates, const float2* GT,
+                                                                  const DenseClassDev* classes, int cls_off, int ncls,
+                                                                  const DensePassClassDev* pcd, const int32_t* dists,
+                                                                  const float2* ptab) {
+    // per-qubit factors and layer 0's classes, staged once per block
+    __shared__ float2 s_f[32][2];
+    __shared__ DenseClassDev s_cls[kMaxLayerClasses];
+    __shared__ DensePassClassDev s_pcd[kMaxLayerClasses];
+    __shared__ int32_t s_dist[kMaxDistWords];
+    __shared__ int32_t s_woff[kMaxLayerClasses];
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        s_f[tid][0] = tid < n_eff ? init_factor(I, gates, GT, tid, 0) : make_float2(1.f, 0.f);
+        s_f[tid][1] = tid < n_eff ? init_factor(I, gates, GT, tid, 1) : make_float2(0.f, 0.f);
+    }
+    const int nc = ncls < kMaxLayerClasses ? ncls : kMaxLayerClasses;
+    if (tid < nc) {
+        s_cls[tid] = classes[cls_off + tid];
+        s_pcd[tid] = pcd[tid];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int w = 0;
+        for (int c = 0; c < nc; ++c) {
+            s_woff[c] = w;
+            w += 2 * s_cls[c].ndist;
+        }
+    }
+    __syncthreads();
+    for (int c = 0; c < nc; ++c)
+        for (int k = tid; k < 2 * s_cls[c].ndist; k += blockDim.x)
+            if (s_woff[c] + k < kMaxDistWords) s_dist[s_woff[c] + k] = dists[2 * s_cls[c].dist_off + k];
+    __syncthreads();
     const uint64_t nblk = 1ull << (n_eff - 4);
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nblk; t += (uint64_t)gridDim.x * blockDim.x) {
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + tid; t < nblk; t += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t x0 = (uint32_t)(t << 4);
         float2 v[16];
         v[0] = make_float2(1.f, 0.f);
-        for (int q = 4; q < n_eff; ++q) v[0] = cmul(v[0], init_factor(I, gates, GT, q, (x0 >> q) & 1u));
+        for (int q = 4; q < n_eff; ++q) v[0] = cmul(v[0], s_f[q][(x0 >> q) & 1u]);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float2 f0 = init_factor(I, gates, GT, k, 0), f1 = init_factor(I, gates, GT, k, 1);
+            const float2 f0 = s_f[k][0], f1 = s_f[k][1];
 #pragma unroll
             for (int j = 0; j < (1 << k); ++j) {
                 v[j | (1 << k)] = cmul(v[j], f1);
@@ -690,10 +739,10 @@ __global__ void dense_product_init_kernel(float2* psi, int n_eff, const __grid_c
             }
         }
         // layer 0's diagonal from split counts over bits 0..3 (one full count per class)
-        for (int ci = 0; ci < ncls; ++ci) {
-            const DenseClassDev C = classes[cls_off + ci];
-            const DensePassClassDev pc = pcd[ci];
-            const int cnt0 = class_count(C, dists + 2 * C.dist_off, x0);
+        for (int ci = 0; ci < nc; ++ci) {
+            const DenseClassDev& C = s_cls[ci];
+            const DensePassClassDev& pc = s_pcd[ci];
+            const int cnt0 = class_count(C, s_dist + s_woff[ci], x0);
             int Ak[4];
             split_deltas(C, pc, x0, Ak);
 #pragma unroll
@@ -886,7 +935,7 @@ int launch_dense(DenseLaunch& L, void* stream) {
                 R.n_eff = L.n_eff;
                 for (int p = L.n_passes - 1; p >= 0; --p) {
                     R.pass = L.host_passes[p];
-                    R.pass.store = p > 0;   // the first pass's inputs are not needed again
+                    R.pass.store = L.host_rev_store[p];   // see DensePlan::rev_store
                     R.gpart = L.gpart + (size_t)p * kDenseAdjSlots * grid;
                     dense_adjoint_kernel<<<grid, kThreads, asmem, st>>>(R);
                     ++launches;

@@ -101,7 +101,8 @@ struct DensePassDev {
     int32_t nstage;                       // classes staged in shared memory for this pass
     int32_t stage_off;                    // their indices in DensePlan::stage
     int32_t measure_group;                // group after which the energy is accumulated (-1 none)
-    int32_t pad;
+    uint32_t group_rot0;                  // bit g: group g rotates layer 0 (the adjoint needs only
+                                          // their gradients: nothing after them uses the state)
     int32_t group_s[kDenseMaxGroups];     // local start bit of each register pass
     uint32_t group_mask[kDenseMaxGroups]; // register bits carrying a rotation
     int32_t group_cls[kDenseMaxGroups];   // first staged class evaluated after the group's rotations
@@ -162,6 +163,9 @@ struct DensePlan {
     // fwd_passes (layers 1..); the adjoint walks `passes` (all layers) in reverse.
     bool product_init = false;
     std::vector<DensePassDev> fwd_passes;
+    // per pass of `passes`: 1 when its reverse (adjoint) pass writes psi and lambda back -- not
+    // the first pass, nor a pass that only gives layer 0's rotation gradients
+    std::vector<int32_t> rev_store;
     std::vector<int32_t> init_gate;
     int32_t init_class_off = 0, init_nclass = 0;
     std::vector<DensePassClassDev> init_pcd;
@@ -363,6 +367,7 @@ struct DenseLaunch {
     int32_t* err = nullptr;               // kernel error word
     bool product_init = false;            // DensePlan::product_init
     const DensePassDev* host_fwd_passes = nullptr;   // DensePlan::fwd_passes
+    const int32_t* host_rev_store = nullptr;          // DensePlan::rev_store
     int32_t n_fwd_passes = 0;
     const int32_t* host_init_gate = nullptr;   // DensePlan::init_gate (n_eff entries)
     int32_t init_class_off = 0, init_nclass = 0;

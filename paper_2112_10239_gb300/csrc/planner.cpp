@@ -545,7 +545,7 @@ std::shared_ptr<DensePlan> make_dense_plan(const Circuit& c, const Ham& h, std::
         for (auto& cb : kv.second) emit_class(*D, cb);
     D->energy_nclass = (int32_t)D->classes.size() - D->energy_class_off;
 
-    // Pass schedule. Tile patterns: the low tile (qubits 0..12) and strided tiles covering 9
+    // Pass schedule. Tile patterns: the low tile (qubits 0..11) and strided tiles covering 8
     // higher qubits each. Greedy: each pass takes the pattern covering the most pending
     // rotations of the current layer; when a pass completes a layer it applies the layer's
     // diagonal right there and continues with the next layer's rotations on the same tile.
@@ -616,6 +616,7 @@ std::shared_ptr<DensePlan> make_dense_plan(const Circuit& c, const Ham& h, std::
                     const int b = __builtin_ctz(bits);
                     const int s = b < 4 ? 0 : std::min(b, kDenseTileBits - 4);
                     const int gi = pass.ngroups++;
+                    if (l == 0) pass.group_rot0 |= 1u << gi;
                     pass.group_s[gi] = s;
                     pass.group_mask[gi] = (bits >> s) & 15u;
                     for (int k = 0; k < 4; ++k)
@@ -728,6 +729,13 @@ std::shared_ptr<DensePlan> make_dense_plan(const Circuit& c, const Ham& h, std::
     D->init_gate.assign(n_eff, -1);
     schedule(0, L, D->passes, gd_all);
     finalize(D->passes, gd_all);
+    D->rev_store.assign(D->passes.size(), 0);
+    for (size_t p = 1; p < D->passes.size(); ++p) {
+        const DensePassDev& ps = D->passes[p];
+        bool rot0_only = ps.group_rot0 == (1u << ps.ngroups) - 1u;
+        for (int g = 0; g < ps.ngroups; ++g) rot0_only &= ps.group_ncls[g] == 0;
+        D->rev_store[p] = rot0_only ? 0 : 1;
+    }
     D->product_init = L >= 2;
     if (D->product_init) {
         schedule(1, L, D->fwd_passes, gd_fwd);

@@ -130,14 +130,15 @@ def test_dense_plan_info(B, hctx):
     # layer's RX touches all 28 qubits: a low tile (0..11) and two strided tiles (12..19, 20..27)
     p = W.qaoa_n28_p4()
     c, h = hctx.problem(p)
-    n_eff, n_passes, n_fwd, n_x, fused = B.tlq_plan_dense_info(hctx.h, c.h, h.h)
+    n_eff, n_passes, n_fwd, n_rev_store, n_x, fused = B.tlq_plan_dense_info(hctx.h, c.h, h.h)
     assert (n_eff, n_x, fused) == (28, 0, 1)
     assert 4 <= n_passes <= 12          # at least one pass per layer, at most three
     assert 3 <= n_fwd < n_passes        # layers 1..3 after the product-state start
+    assert n_rev_store <= n_passes - 2  # the first pass and layer-0-only passes write nothing
     # small circuits keep a 12-qubit state (one tile); X/Y strings are measured separately
     q = W.random_nonlocal_problem(6, 2, 1, seed=1)
     c2, h2 = hctx.problem(q)
-    n_eff, _, _, n_x, _ = B.tlq_plan_dense_info(hctx.h, c2.h, h2.h)
+    n_eff, _, _, _, n_x, _ = B.tlq_plan_dense_info(hctx.h, c2.h, h2.h)
     assert n_eff == 12
     assert n_x == sum(1 for _, _, letters in q.terms if set(letters) - {"Z"})
 
