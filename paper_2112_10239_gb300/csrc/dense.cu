@@ -15,9 +15,13 @@
 // per-layer table; CZ gates contribute (-1)^(count of 11 pairs). The energy of Z/ZZ terms is
 // accumulated in the final pass from the same counts; X/Y terms are measured by a separate
 // streaming kernel. Reductions run in a fixed order, so results are deterministic.
+// Layer 0 acts on |0..0>, so the forward starts from its product state written in one kernel
+// and streams the remaining layers; the gradient's reverse passes (the adjoint) walk the
+// fused schedule of all layers.
 //
-// The plain per-gate path (one full-state sweep per gate, per-term measurement sweeps) is
-// kept as the baseline the fused passes are compared against.
+// The plain per-gate path (one full-state sweep per gate, per-term measurement sweeps, and
+// for the gradient one sweep per gate and state) is kept as the baseline the fused passes are
+// compared against.
 #include "gates.cuh"
 
 #include <cstdio>

@@ -4,16 +4,18 @@
 // For rho = |psi><psi| and a kept qubit set A (m qubits) with complement B,
 //   rho_A[i][j] = sum_k Psi[i][k] conj(Psi[j][k]),   Psi[i][k] = psi(kept bits i, traced bits k),
 // i.e. rho_A = Psi Psi^dagger with Psi a 2^m x 2^(n-m) matrix: a Hermitian rank-K update.
-// Two kernels:
+// Kernels:
 //   * psi_gather_kernel lays Psi out row-major (row i contiguous in k) from the state, where
 //     bit t of i is the t-th lowest kept qubit and bit u of k the u-th lowest traced one;
-//   * herk_tile_kernel computes 64 x 64 output tiles of the upper block triangle with 4 x 4
-//     complex register blocks per thread from 16-wide k chunks staged in shared memory, and
-//     writes every entry above the diagonal twice (as computed, and conjugate-transposed below
-//     it) and the diagonal as real numbers, so the output is exactly Hermitian. When the
-//     output has few tiles (small m, long k) the k range is split over CTAs; the splits are
-//     summed in a fixed order by herk_reduce_kernel, so results are deterministic.
-// FP32 products and accumulation (the state's precision), complex64 output.
+//   * herk_tc_kernel (m >= 7) computes 128 x 128 tiles of the upper block triangle on the
+//     tensor cores (tcgen05, TF32 high/low split, FP32 accumulators in tensor memory) and
+//     writes off-diagonal tiles and their conjugate mirrors with TMA tensor stores;
+//   * herk_tile_kernel (m < 7) computes 64 x 64 tiles on FP32 CUDA cores with 4 x 4 complex
+//     register blocks per thread from 16-wide k chunks staged in shared memory.
+// Entries above the diagonal are written twice (as computed, and conjugate-transposed below
+// it) and the diagonal as real numbers, so the output is exactly Hermitian. When the output
+// has few tiles (small m, long k) the k range is split over CTAs; the splits are summed in a
+// fixed order by herk_reduce_kernel, so results are deterministic. Complex64 output.
 #include <cuda.h>   // CUtensorMap and its enums (the encoder is fetched through the runtime)
 #include <cuda_runtime.h>
 
