@@ -149,7 +149,7 @@ def algorithmic_flops(B_mod, ctx, c, h, prob, grad=True):
     Padding to the kernel's minimum width is not counted.
     """
     n_terms = len(prob.terms)
-    nrot, ndiag, npdiag, _, w, nterms = B_mod.tlq_plan_cone_stats(ctx.h, c.h, h.h, n_terms)
+    nrot, ndiag, npdiag, _, w, nterms, _ = B_mod.tlq_plan_cone_stats(ctx.h, c.h, h.h, n_terms)
     A = np.power(2.0, w.astype(np.float64))
     f = A * (6 * nrot + 6 * ndiag + 8 * nterms)
     if grad:

@@ -238,12 +238,15 @@ tlq_status tlq_plan_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* path, i
 /* Work-cone statistics for (c, h) on the cone path. Terms whose causal cone lies inside
  * another term's window are measured on that window, so the plan has *ncones <= n_terms
  * work cones. For cone k: rotations nrot[k], diagonal layers ndiag[k] and parametrised
- * diagonal gates npdiag[k] it simulates, the width weff[k] the kernel runs (padded to at
- * least 8 qubits), its true width wtrue[k] and the number of terms nterms[k] measured on it.
- * Arrays must hold n_terms entries; any pointer may be NULL. Used to count the algorithmic
- * work of a call. TLQ_EUNSUPPORTED on the dense path. */
+ * diagonal gates npdiag[k] it simulates, the width weff[k] of its window (padded to at
+ * least 8 qubits), its true width wtrue[k], the number of terms nterms[k] measured on it,
+ * and split[k] = 1 when the kernel runs it as two independent branches of weff[k] - 1 qubits
+ * (the window's top qubit carries gates of the first layer only and no measured term, so the
+ * states with that qubit 0 and 1 never mix; their energies and gradients add up). Arrays
+ * must hold n_terms entries; any pointer may be NULL. Used to count the algorithmic work of a
+ * call. TLQ_EUNSUPPORTED on the dense path. */
 tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* ncones, int32_t* nrot, int32_t* ndiag,
-                               int32_t* npdiag, int32_t* weff, int32_t* wtrue, int32_t* nterms);
+                               int32_t* npdiag, int32_t* weff, int32_t* wtrue, int32_t* nterms, int32_t* split);
 
 /* Dense statevector plan of (c, h): the state's qubit count *n_eff (n, at least 12); the
  * number of streaming passes *n_passes the adjoint makes over the state (in reverse); the

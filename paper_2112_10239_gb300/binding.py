@@ -80,7 +80,7 @@ def lib():
         L.tlq_last_error.argtypes = [vp]
         L.tlq_last_error.restype = ctypes.c_char_p
         L.tlq_plan_info.argtypes = [vp, vp, vp, ip, ip, ip, ip]
-        L.tlq_plan_cone_stats.argtypes = [vp, vp, vp, ip, ip, ip, ip, ip, ip, ip]
+        L.tlq_plan_cone_stats.argtypes = [vp, vp, vp, ip, ip, ip, ip, ip, ip, ip, ip]
         L.tlq_plan_dense_info.argtypes = [vp, vp, vp, ip, ip, ip, ip, ip, ip]
         L.tlq_partial_trace_dev.argtypes = [vp, vp, ctypes.c_int32, ip, ctypes.c_int32, vp, vp]
         L.tlq_reduced_density.argtypes = [vp, vp, dp, ip, ctypes.c_int32, dp]
@@ -246,10 +246,10 @@ def tlq_plan_info(ctx, circ, ham, n_terms):
 
 
 def tlq_plan_cone_stats(ctx, circ, ham, n_terms):
-    """Per work cone: (nrot, ndiag, npdiag, weff, wtrue, nterms), arrays of length ncones."""
+    """Per work cone: (nrot, ndiag, npdiag, weff, wtrue, nterms, split), arrays of length ncones."""
     ip = ctypes.POINTER(ctypes.c_int32)
     nc = ctypes.c_int32()
-    out = [np.zeros(max(1, n_terms), dtype=np.int32) for _ in range(6)]
+    out = [np.zeros(max(1, n_terms), dtype=np.int32) for _ in range(7)]
     _check(lib().tlq_plan_cone_stats(ctx, circ, ham, ctypes.byref(nc), *[a.ctypes.data_as(ip) for a in out]), ctx)
     return tuple(a[:nc.value] for a in out)
 

@@ -115,8 +115,6 @@ tlq_status get_plan(Context* ctx, Circuit* c, Ham* h, std::shared_ptr<PlanEntry>
     return TLQ_OK;
 }
 
-int team_bytes_host(int W, int tt, bool fp64, bool grad, bool smem_state);
-
 static int smem_optin(int device) {
     int v = 0;
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -128,48 +126,15 @@ tlq_status ensure_worklist(Context* ctx, PlanEntry& pe, const Circuit& c, int B,
     if (pe.wl_B == B && pe.wl_fp64 == fp64 && pe.wl_grad == grad) return TLQ_OK;
     const Plan& P = *pe.plan;
     const int T = (int)P.cones.size();
-    std::vector<int> order(T);
-    for (int t = 0; t < T; ++t) order[t] = t;
-    // widest first; within a width, chain order (measured faster than longest-first by
-    // estimated work on the n=20 batch, and equal on the n=500 batch)
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P.cones[a].W > P.cones[b].W; });
-    const int smax = smem_optin(ctx->device);
+    std::vector<WorkItem> its;
+    its.reserve((size_t)T * B * 2);
+    for (int t = 0; t < T; ++t)
+        for (int b = 0; b < B; ++b) push_cone_items(P, t, b, grad, its);
     std::vector<int32_t> items;
-    std::vector<ChunkDev> smem_chunks, glob_chunks;
-    int smem_bytes = 0, gsmem_bytes = 0, g_maxW = 0;
-    size_t k = 0;
-    while (k < order.size()) {
-        const int W = P.cones[order[k]].W;
-        size_t k2 = k;
-        while (k2 < order.size() && P.cones[order[k2]].W == W) ++k2;
-        int tt = std::min(kCtaThreads, 1 << (W - 4));
-        int tb = team_bytes_host(W, tt, fp64, grad, true);
-        int nteams = std::min(kCtaThreads / tt, smax / tb);
-        bool global = (W > kMaxSmemConeW) || nteams < 1;
-        if (global) {
-            tt = kGlobalCtaThreads;
-            tb = team_bytes_host(W, tt, fp64, grad, false);
-            nteams = 1;
-        }
-        const int first_item = (int)items.size() / 2;
-        for (size_t i = k; i < k2; ++i)
-            for (int b = 0; b < B; ++b) { items.push_back(order[i]); items.push_back(b); }
-        const int nit = (int)items.size() / 2 - first_item;
-        for (int f = 0; f < nit; f += nteams) {
-            ChunkDev ch{};
-            ch.W = W;
-            ch.first = first_item + f;
-            ch.count = std::min(nteams, nit - f);
-            ch.tt = tt;
-            ch.team_bytes = tb;
-            (global ? glob_chunks : smem_chunks).push_back(ch);
-        }
-        if (global) { gsmem_bytes = std::max(gsmem_bytes, tb); g_maxW = std::max(g_maxW, W); }
-        else smem_bytes = std::max(smem_bytes, nteams * tb);
-        k = k2;
-    }
-    std::vector<ChunkDev> chunks = smem_chunks;
-    chunks.insert(chunks.end(), glob_chunks.begin(), glob_chunks.end());
+    ChunkSet cs;
+    build_chunks(its, fp64, grad, smem_optin(ctx->device), items, cs);
+    std::vector<ChunkDev> chunks = cs.smem;
+    chunks.insert(chunks.end(), cs.glob.begin(), cs.glob.end());
     cudaFree(pe.d_items);
     cudaFree(pe.d_chunks);
     pe.d_items = nullptr;
@@ -177,11 +142,13 @@ tlq_status ensure_worklist(Context* ctx, PlanEntry& pe, const Circuit& c, int B,
     size_t bytes = 0;
     TLQ_TRY(upload(items, &pe.d_items, &bytes));
     TLQ_TRY(upload(chunks, &pe.d_chunks, &bytes));
-    pe.n_chunks_smem = (int)smem_chunks.size();
+    pe.n_chunks_smem = (int)cs.smem.size();
     pe.n_chunks = (int)chunks.size();
-    pe.smem_bytes = smem_bytes;
-    pe.gsmem_bytes = gsmem_bytes;
-    pe.g_maxW = g_maxW;
+    pe.smem_bytes = cs.smem_bytes;
+    pe.smem_threads = cs.smem_threads;
+    pe.gsmem_bytes = cs.gsmem_bytes;
+    pe.g_maxW = cs.g_maxW;
+    pe.accum = cs.accum;
     pe.wl_B = B;
     pe.wl_fp64 = fp64;
     pe.wl_grad = grad;
@@ -350,6 +317,8 @@ tlq_status run_device(Context* ctx, Circuit* c, Ham* h, const double* theta_dev,
     L.n_chunks_smem = pe->n_chunks_smem;
     L.n_chunks = pe->n_chunks;
     L.smem_bytes = pe->smem_bytes;
+    L.smem_threads = pe->smem_threads;
+    L.accum = pe->accum;
     L.gsmem_bytes = pe->gsmem_bytes;
     L.g_maxW = pe->g_maxW;
     const size_t r2 = fp64 ? 16 : 8;
@@ -918,7 +887,7 @@ tlq_status tlq_plan_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* path, i
 extern "C" {
 
 tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* ncones, int32_t* nrot, int32_t* ndiag,
-                               int32_t* npdiag, int32_t* weff, int32_t* wtrue, int32_t* nterms) {
+                               int32_t* npdiag, int32_t* weff, int32_t* wtrue, int32_t* nterms, int32_t* split) {
     if (!ctx || !c || !h) { set_error("NULL handle"); return TLQ_EINVAL; }
     if (c->n != h->n) { set_error("circuit and Hamiltonian qubit counts differ"); return TLQ_EINVAL; }
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -934,6 +903,7 @@ tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n
         if (weff) weff[t] = P.cones[t].W;
         if (wtrue) wtrue[t] = P.group_wtrue[t];
         if (nterms) nterms[t] = P.cones[t].nmterms;
+        if (split) split[t] = P.cones[t].split;
     }
     return TLQ_OK;
 }

@@ -37,6 +37,13 @@ namespace tlq {
 // bit 6; chunk 2: bits 14.. plus crossing bit 13), two layer-info buffers (rotation
 // (c, s), kind and gradient slot per window qubit; alternating by layer) and the
 // double-buffered per-warp gradient partials.
+//
+// A team may hold half a window: when the window's top qubit carries gates of layer 0 only
+// and no measured term, the state is the sum of two branches (top bit 0 and 1) that no
+// later gate mixes and no term connects, so each branch is an independent item of W - 1
+// qubits (`W` below is the state width) whose energies and gradients add up to the
+// window's. Tables and layer records still cover the whole window (`Wt` qubits); the
+// branch's top bit enters every phase lookup as the constant `hi`.
 
 struct TeamLayout {
     int psi, lam, tab, info, fac, red, bytes;
@@ -47,7 +54,7 @@ struct TeamLayout {
 __host__ __device__ inline int nwarps_of(int tt) { return tt >= 32 ? tt / 32 : 1; }
 __host__ __device__ inline int info_bytes(int real_bytes) { return 32 * 2 * real_bytes + 4 * 32 * 4; }
 
-__host__ __device__ inline TeamLayout team_layout(int W, int tt, int real_bytes, bool grad, bool smem_state) {
+__host__ __device__ inline TeamLayout team_layout(int W, int Wt, int tt, int real_bytes, bool grad, bool smem_state) {
     TeamLayout L{};
     const int r2 = 2 * real_bytes;
     int off = 0;
@@ -55,8 +62,8 @@ __host__ __device__ inline TeamLayout team_layout(int W, int tt, int real_bytes,
     if (smem_state) off += padded_amps(W) * r2;
     L.lam = off;
     if (smem_state && grad) off += padded_amps(W) * r2;
-    const int b1 = (W - 7) < 7 ? (W - 7) : 7;
-    const int b2 = W > 14 ? W - 14 : 0;
+    const int b1 = (Wt - 7) < 7 ? (Wt - 7) : 7;
+    const int b2 = Wt > 14 ? Wt - 14 : 0;
     L.tab1 = 136;
     L.tab2 = L.tab1 + (1 << (b1 + 1));
     const int slots = L.tab2 + (b2 > 0 ? (1 << (b2 + 1)) : 0);
@@ -148,7 +155,10 @@ struct TeamMem {
     T2* tab;
     unsigned char* info;   // two buffers of info_bytes, then the per-qubit factor staging area
     void* red;
-    int tab1, tab2, tab_entries, W;
+    int tab1, tab2, tab_entries;
+    int W;                 // qubits of the state held (the window, or its branch)
+    int Wt;                // qubits of the window (tables, layer records)
+    int hi;                // index bits above the state: the branch's top bit (0 for a whole window)
 };
 
 template <typename T2>
@@ -186,7 +196,7 @@ __device__ __forceinline__ T2* info_fac(const TeamMem<T2>& M) {
 template <typename real, typename T2>
 __device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, const TeamMem<T2>& M, int par,
                             bool conj_phase) {
-    const int W = M.W;
+    const int W = M.Wt;
     T2* cs = info_cs(M, par);
     int* kinds = info_kinds(M, par);
     int* rslot = info_rslot(M, par);
@@ -297,8 +307,9 @@ __device__ void pass_fwd(T2* psi, int s, unsigned m, bool diag, const Team& tm, 
         if (kd[2] >= 0) apply_rot<2>(v, kd[2], c[2], sn[2]);
         if (kd[3] >= 0) apply_rot<3>(v, kd[3], c[3], sn[3]);
         if (diag) {
+            const int xb = base | M.hi;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = cmul(v[j], phase_of(M.tab, M.tab1, M.tab2, W, base | (j << s)));
+            for (int j = 0; j < 16; ++j) v[j] = cmul(v[j], phase_of(M.tab, M.tab1, M.tab2, M.Wt, xb | (j << s)));
         }
         store16(v, p, stride);
     }
@@ -356,13 +367,14 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, const Team& tm, co
             }
             const int* zslot = info_zslot(M, par);
             const int* pslot = info_pslot(M, par);
-            for (int j0 = 0; j0 < W; ++j0) {
+            const int xb = base | M.hi;   // the index bits outside the register bits
+            for (int j0 = 0; j0 < M.Wt; ++j0) {
                 const int k0 = j0 - s;
                 const bool in0 = (unsigned)k0 < 4u;
                 if (zslot[j0] >= 0) {
                     real val;
                     if (in0) val = k0 == 0 ? Sk0 : k0 == 1 ? Sk1 : k0 == 2 ? Sk2 : Sk3;
-                    else val = ((base >> j0) & 1) ? -S : S;
+                    else val = ((xb >> j0) & 1) ? -S : S;
                     val = team_warp_sum(val, tm);
                     if (leader) {
                         real* dst = red + (4 + 2 * j0) * nw + warp;
@@ -374,9 +386,9 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, const Team& tm, co
                     const bool in1 = (unsigned)(j1 - s) < 4u;
                     real val;
                     if (in0 && in1) val = k0 == 0 ? Sp0 : k0 == 1 ? Sp1 : Sp2;
-                    else if (in0) val = ((base >> j1) & 1) ? -Sk3 : Sk3;   // j0 = s + 3
-                    else if (in1) val = ((base >> j0) & 1) ? -Sk0 : Sk0;   // j1 = s
-                    else val = (((base >> j0) ^ (base >> j1)) & 1) ? -S : S;
+                    else if (in0) val = ((xb >> j1) & 1) ? -Sk3 : Sk3;   // j0 = s + 3
+                    else if (in1) val = ((xb >> j0) & 1) ? -Sk0 : Sk0;   // j1 = s
+                    else val = (((xb >> j0) ^ (xb >> j1)) & 1) ? -S : S;
                     val = team_warp_sum(val, tm);
                     if (leader) {
                         real* dst = red + (5 + 2 * j0) * nw + warp;
@@ -386,7 +398,7 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, const Team& tm, co
             }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const T2 ph = phase_of(M.tab, M.tab1, M.tab2, W, base | (j << s));   // conjugated table
+                const T2 ph = phase_of(M.tab, M.tab1, M.tab2, M.Wt, xb | (j << s));   // conjugated table
                 p[j] = cmul(p[j], ph);
                 l[j] = cmul(l[j], ph);
             }
@@ -434,7 +446,7 @@ __device__ void flush_pass(const real* red, int nw, unsigned m, int s, const Tea
     const int* rslot = info_rslot(M, par);
     const int* zslot = info_zslot(M, par);
     const int* pslot = info_pslot(M, par);
-    const int nred = diag ? 4 + 2 * M.W : 4;
+    const int nred = diag ? 4 + 2 * M.Wt : 4;
     for (int t = tm.tid; t < nred; t += tm.tt) {
         int slot;
         if (t < 4) {
@@ -447,91 +459,154 @@ __device__ void flush_pass(const real* red, int nw, unsigned m, int s, const Tea
         if (slot < 0) continue;
         real acc = 0;
         for (int w = 0; w < nw; ++w) acc += red[t * nw + w];
-        gdst[slot] = (double)acc;
+        // a branch adds its share onto zeroed slots: two addends, so the order does not matter
+        if (M.Wt > M.W) atomicAdd(gdst + slot, (double)acc);
+        else gdst[slot] = (double)acc;
     }
 }
 
-// The window state after layer 0's rotations (staged in info buffer `par`), from |0..0>:
-// single-qubit rotations on |0> give a product state, amplitude(x) = prod_j f_j(x_j) with
-// f_j(0) = cos(a_j/2) and f_j(1) = sin(a_j/2) (RY) or -i sin(a_j/2) (RX); qubits without a live
-// rotation contribute 1 for bit 0 and 0 for bit 1. Each thread writes 16 contiguous
-// amplitudes: the product over its fixed high bits times the 16 products over the low four
-// bits (built by doubling), then layer 0's diagonal phase when `diag`. Replaces the register
-// passes of layer 0 (and its diagonal pass) in the forward sweep.
+// Factor of window qubit j with bit value `bit` in the product state that layer 0's
+// rotations make from |0..0> (staged in info buffer `par`): f_j(0) = cos(a_j/2) and
+// f_j(1) = sin(a_j/2) (RY) or -i sin(a_j/2) (RX); a qubit without a live rotation gives 1
+// for bit 0 and 0 for bit 1.
+template <typename T2>
+__device__ __forceinline__ T2 init_factor(const T2* cs, const int* kinds, unsigned live, int j, int bit) {
+    T2 f;
+    const bool rot = ((live >> j) & 1u) && kinds[j] >= 0;
+    if (!rot) {
+        f.x = bit ? 0 : 1;
+        f.y = 0;
+    } else if (bit == 0) {
+        f.x = cs[j].x;
+        f.y = 0;
+    } else if (kinds[j] == TLQ_RY) {
+        f.x = cs[j].y;
+        f.y = 0;
+    } else {   // RX
+        f.x = 0;
+        f.y = -cs[j].y;
+    }
+    return f;
+}
+
+// The 16 amplitudes x = base | j (j < 16) of the product state over the state's qubits,
+// prod_{q < M.W} f_q(x_q): the product over the fixed high bits times the 16 products over
+// the low four bits (built by doubling).
+template <typename T2>
+__device__ __forceinline__ void product16(const T2* cs, const int* kinds, int W, unsigned live, int base,
+                                          T2 (&v)[16]) {
+    v[0].x = 1;
+    v[0].y = 0;
+    for (int j = 4; j < W; ++j) v[0] = cmul(v[0], init_factor(cs, kinds, live, j, (base >> j) & 1));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T2 f0 = init_factor(cs, kinds, live, k, 0), f1 = init_factor(cs, kinds, live, k, 1);
+#pragma unroll
+        for (int j = 0; j < (1 << k); ++j) {
+            v[j | (1 << k)] = cmul(v[j], f1);
+            v[j] = cmul(v[j], f0);
+        }
+    }
+}
+
+// The window state after layer 0 (staged in info buffer `par`), from |0..0>: the product
+// state of its rotations, times the branch's top-qubit factor for half a window, then
+// layer 0's diagonal phase when `diag`. Each thread writes 16 contiguous amplitudes.
+// Replaces the register passes of layer 0 (and its diagonal pass) in the forward sweep.
 template <typename real, typename T2>
 __device__ void init_product_state(const TeamMem<T2>& M, unsigned live, bool diag, const Team& tm, int par) {
     const int W = M.W;
+    const int nout = 1 << (W - 4);
     const T2* cs = info_cs(M, par);
     const int* kinds = info_kinds(M, par);
-    auto factor = [&](int j, int bit) {
-        T2 f;
-        const bool rot = ((live >> j) & 1u) && kinds[j] >= 0;
-        if (!rot) {
-            f.x = bit ? 0 : 1;
-            f.y = 0;
-        } else if (bit == 0) {
-            f.x = cs[j].x;
-            f.y = 0;
-        } else if (kinds[j] == TLQ_RY) {
-            f.x = cs[j].y;
-            f.y = 0;
-        } else {   // RX
-            f.x = 0;
-            f.y = -cs[j].y;
-        }
-        return f;
-    };
-    const int nout = 1 << (W - 4);
+    T2 top;
+    top.x = 1;
+    top.y = 0;
+    if (M.Wt > W) top = init_factor(cs, kinds, live, W, (M.hi >> W) & 1);
     for (int o = tm.tid; o < nout; o += tm.tt) {
         const int base = o << 4;
         T2 v[16];
-        v[0].x = 1;
-        v[0].y = 0;
-        for (int j = 4; j < W; ++j) v[0] = cmul(v[0], factor(j, (base >> j) & 1));
+        product16(cs, kinds, W, live, base, v);
+        if (M.Wt > W) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const T2 f0 = factor(k, 0), f1 = factor(k, 1);
-#pragma unroll
-            for (int j = 0; j < (1 << k); ++j) {
-                v[j | (1 << k)] = cmul(v[j], f1);
-                v[j] = cmul(v[j], f0);
-            }
+            for (int j = 0; j < 16; ++j) v[j] = cmul(v[j], top);
         }
         if (diag) {
+            const int xb = base | M.hi;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = cmul(v[j], phase_of(M.tab, M.tab1, M.tab2, W, base | j));
+            for (int j = 0; j < 16; ++j) v[j] = cmul(v[j], phase_of(M.tab, M.tab1, M.tab2, M.Wt, xb | j));
         }
         store16(v, M.psi + pad16(base), 1);
     }
 }
 
-// <psi|P_t|psi> for every term t measured on this window, written to e_out[term]; when
-// GRAD also lam = sum_t c_t P_t psi (the term coefficients folded into the adjoint).
-// One pass over the window for all its terms (at most kMaxGroupTerms): each block of 16
-// amplitudes is read once, lam is accumulated in registers and written once, and each term
-// keeps its own partial sum. Ends with a team barrier.
-template <typename real, typename T2, bool GRAD>
-__device__ void measure(const TeamMem<T2>& M, const MeasDev* mt, int nmt, const double* coeff, double* e_out,
-                        const Team& tm, real* red) {
+// Gradient of layer 0's rotation on the top qubit of a branch (bit value h): Im<lam|G|psi>
+// pairs amplitudes of the two branches, and this branch holds only lam and psi with top bit
+// h. At this point (layer 0's diagonal un-applied) psi is the product state of layer 0's
+// rotations, so the other branch's amplitude is known exactly: f_top(1 - h) times the
+// product over the state's qubits. The branch adds its half of the pair sums:
+// RY, G = Y: h = 0 gives -Re(conj(l0) p1), h = 1 gives +Re(conj(l1) p0);
+// RX, G = X: Im(conj(l_h) p_{1-h}) for either h.
+// Per-warp partial sums go to red[warp]. Ends without a barrier.
+template <typename real, typename T2>
+__device__ void top_rotation_grad(const TeamMem<T2>& M, unsigned live, int par, const Team& tm, real* red) {
+    const int W = M.W;
+    const int h = (M.hi >> W) & 1;
+    const int nout = 1 << (W - 4);
+    const T2* cs = info_cs(M, par);
+    const int* kinds = info_kinds(M, par);
+    const int kind = kinds[W];
+    const T2 f = init_factor(cs, kinds, live, W, 1 - h);   // the other branch's top factor
+    const int warp = tm.tt >= 32 ? (tm.tid >> 5) : 0;
+    const bool leader = tm.tt >= 32 ? ((tm.tid & 31) == 0) : (tm.tid == 0);
+    real acc = 0;
+    for (int o = tm.tid; o < nout; o += tm.tt) {
+        const int base = o << 4;
+        T2 u[16], l[16];
+        product16(cs, kinds, W, live, base, u);
+        load16(l, M.lam + pad16(base), 1);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const T2 q = cmul(f, u[j]);   // psi of the paired amplitude in the other branch
+            if (kind == TLQ_RY) acc += (h ? (real)1 : (real)-1) * (l[j].x * q.x + l[j].y * q.y);
+            else acc += l[j].x * q.y - l[j].y * q.x;
+        }
+    }
+    acc = team_warp_sum(acc, tm);
+    if (leader) red[warp] = acc;
+}
+
+// One pass over the window for up to kMeasBatch terms: per-warp partial sums of
+// <psi|P_t|psi> go to red[k * nw + warp]; when GRAD, lam += sum_t c_t P_t psi over these
+// terms (lam starts at zero unless ADD, in which case each thread reads back the values it
+// wrote in the previous batch). Each block of 16 amplitudes is read once per pass.
+constexpr int kMeasBatch = 8;
+template <typename real, typename T2, bool GRAD, bool ADD>
+__device__ void measure_batch(const TeamMem<T2>& M, const MeasDev* mt, int nmt, const double* coeff, const Team& tm,
+                              real* red) {
     const int W = M.W;
     const int nout = 1 << (W - 4);
     const int nw = nwarps_of(tm.tt);
     const int warp = tm.tt >= 32 ? (tm.tid >> 5) : 0;
     const bool leader = tm.tt >= 32 ? ((tm.tid & 31) == 0) : (tm.tid == 0);
-    real acc[kMaxGroupTerms];
+    real acc[kMeasBatch];
 #pragma unroll
-    for (int k = 0; k < kMaxGroupTerms; ++k) acc[k] = 0;
+    for (int k = 0; k < kMeasBatch; ++k) acc[k] = 0;
     for (int o = tm.tid; o < nout; o += tm.tt) {
         const int x0 = o << 4;
         T2 a[16];
         load16(a, M.psi + pad16(x0), 1);
         T2 lv[16];
         if (GRAD) {
+            if (ADD) {
+                load16(lv, M.lam + pad16(x0), 1);
+            } else {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) lv[j].x = lv[j].y = 0;
+                for (int j = 0; j < 16; ++j) lv[j].x = lv[j].y = 0;
+            }
         }
 #pragma unroll
-        for (int k = 0; k < kMaxGroupTerms; ++k) {
+        for (int k = 0; k < kMeasBatch; ++k) {
             if (k >= nmt) break;
             const MeasDev md = mt[k];
             T2 f0;   // (-i)^ny
@@ -557,26 +632,48 @@ __device__ void measure(const TeamMem<T2>& M, const MeasDev* mt, int nmt, const 
         if (GRAD) store16(lv, M.lam + pad16(x0), 1);
     }
 #pragma unroll
-    for (int k = 0; k < kMaxGroupTerms; ++k) {
+    for (int k = 0; k < kMeasBatch; ++k) {
         if (k >= nmt) break;
         const real v = team_warp_sum(acc[k], tm);
         if (leader) red[k * nw + warp] = v;
     }
+}
+
+// <psi|P_t|psi> for every term t measured on this window, written to e_out[term] (added for
+// a branch); when GRAD also lam = sum_t c_t P_t psi (the term coefficients folded into the
+// adjoint). Terms go kMeasBatch per pass over the window (at most kMaxGroupTerms in all).
+// Ends with a team barrier.
+template <typename real, typename T2, bool GRAD>
+__device__ void measure(const TeamMem<T2>& M, const MeasDev* mt, int nmt, const double* coeff, double* e_out,
+                        const Team& tm, real* red) {
+    const int nw = nwarps_of(tm.tt);
+    measure_batch<real, T2, GRAD, false>(M, mt, nmt < kMeasBatch ? nmt : kMeasBatch, coeff, tm, red);
+    for (int k0 = kMeasBatch; k0 < nmt; k0 += kMeasBatch)
+        measure_batch<real, T2, GRAD, true>(M, mt + k0, nmt - k0 < kMeasBatch ? nmt - k0 : kMeasBatch, coeff, tm,
+                                            red + k0 * nw);
     tm.sync();
     for (int k = tm.tid; k < nmt; k += tm.tt) {
         real e = 0;
         for (int w = 0; w < nw; ++w) e += red[k * nw + w];
-        e_out[mt[k].term] = (double)e;
+        if (M.Wt > M.W) atomicAdd(e_out + mt[k].term, (double)e);   // a branch: two addends onto zero
+        else e_out[mt[k].term] = (double)e;
     }
     tm.sync();
 }
 
+// One (cone, set) item: the whole window (half = 0), or the branch with the window's top
+// bit half - 1 (W = the window's width - 1). Ends with a team barrier.
 template <typename real, bool GRAD, bool GLOBAL>
-__device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm, unsigned char* tb, int W) {
+__device__ void run_cone(const ConeArgs& A, int cone_idx, int half, int b, const Team& tm, unsigned char* tb, int W,
+                         int team_bytes) {
     using T2 = typename R2<real>::T;
     const SetRec* R = A.sets ? A.sets + b : nullptr;
     const ConeDev cd = R ? R->cones[cone_idx] : A.cones[cone_idx];
-    const TeamLayout TL = team_layout(W, tm.tt, (int)sizeof(real), GRAD, !GLOBAL);
+    const TeamLayout TL = team_layout(W, cd.W, tm.tt, (int)sizeof(real), GRAD, !GLOBAL);
+    if (half > 2 || cd.W != W + (half ? 1 : 0) || TL.bytes > team_bytes || (half && (R ? R->prog : A.prog)[cd.prog_off] < 1)) {
+        if (tm.tid == 0) atomicOr(A.err, 1);
+        return;
+    }
     TeamMem<T2> M;
     if (GLOBAL) {
         unsigned char* g = reinterpret_cast<unsigned char*>(A.gscratch) + (size_t)blockIdx.x * A.gscratch_slot;
@@ -593,6 +690,8 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
     M.tab2 = TL.tab2;
     M.tab_entries = TL.tab_entries;
     M.W = W;
+    M.Wt = cd.W;
+    M.hi = half ? (half - 1) << W : 0;
     const T2* GT = reinterpret_cast<const T2*>(A.gate_table) + (R ? (size_t)R->gt_off : (size_t)b * A.n_gates);
     real* red = reinterpret_cast<real*>(M.red);
     const int nw = nwarps_of(tm.tt);
@@ -618,6 +717,10 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
         const int ndiag = lp[0];
         const int par = li & 1;
         unsigned todo = (unsigned)lp[1];
+        if (todo >> W) {   // a branch's top qubit has gates of layer 0 only
+            if (tm.tid == 0) atomicOr(A.err, 1);
+            return;
+        }
         stage_layer<real, T2>(lp, GT, tm, M, par, false);
         bool first = true;
         while (todo || (first && ndiag > 0)) {
@@ -655,6 +758,18 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int b, const Team& tm,
             flush_pass<real, T2>(rb, nw, 0u, W - 4, M, par, true, gdst, tm);
             rpar ^= 1;
         }
+        if (li == 0 && ((todo >> W) & 1u)) {   // a branch: layer 0's rotation on the window's top qubit
+            real* rb = red + rpar * kMaxPassSlots * nw;
+            top_rotation_grad<real, T2>(M, (unsigned)lp[1], par, tm, rb);
+            tm.sync();
+            flush_pass<real, T2>(rb, nw, 1u, W, M, par, false, gdst, tm);
+            rpar ^= 1;
+            todo &= ~(1u << W);
+        }
+        if (todo >> W) {
+            if (tm.tid == 0) atomicOr(A.err, 1);
+            return;
+        }
         while (todo) {
             const int bt = 31 - __clz(todo);
             int s = bt - 3;
@@ -686,7 +801,7 @@ cone_kernel(ConeArgs A) {
         const ChunkDev ch = A.chunks[c];
         const int tt = ch.tt;
         const int team = threadIdx.x / tt;
-        if (ch.W < kMinConeW || ch.W > kMaxConeW || tt < 16 || tt > kCtaThreads ||
+        if (ch.W < kMinConeW || ch.W > kMaxConeW || tt < 16 || tt > (int)blockDim.x || ch.count > (int)blockDim.x / tt ||
             (!GLOBAL && ((1 << (ch.W - 4)) < kCtaThreads ? (1 << (ch.W - 4)) : kCtaThreads) != tt)) {
             if (threadIdx.x == 0) atomicOr(A.err, 1);
             continue;
@@ -699,8 +814,9 @@ cone_kernel(ConeArgs A) {
             const int lane = threadIdx.x & 31;
             tm.mask = tt >= 32 ? 0xffffffffu : (((1u << tt) - 1u) << (lane & ~(tt - 1)));
             const int item = ch.first + team;
-            const int cone = A.items[2 * item], b = A.items[2 * item + 1];
-            run_cone<real, GRAD, GLOBAL>(A, cone, b, tm, smem + (size_t)team * ch.team_bytes, ch.W);
+            const int cw = A.items[2 * item], b = A.items[2 * item + 1];
+            run_cone<real, GRAD, GLOBAL>(A, cw & kItemConeMask, (cw >> kItemHalfShift) & 3, b, tm,
+                                         smem + (size_t)team * ch.team_bytes, ch.W, ch.team_bytes);
         }
         __syncthreads();
     }
@@ -769,7 +885,7 @@ __global__ void grad_reduce_kernel(const double* g_part, const int32_t* off, con
 
 template <typename real, bool GRAD, bool GLOBAL>
 static int launch_cone_t(const ConeLaunch& L, cudaStream_t st, int begin, int end, int smem, int grid,
-                         int32_t* counter) {
+                         int32_t* counter, int threads) {
     if (end <= begin) return 0;
     auto kern = cone_kernel<real, GRAD, GLOBAL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -796,26 +912,26 @@ static int launch_cone_t(const ConeLaunch& L, cudaStream_t st, int begin, int en
     A.sets = nullptr;
     const int n = end - begin;
     if (grid > n) grid = n;
-    kern<<<grid, GLOBAL ? kGlobalCtaThreads : kCtaThreads, smem, st>>>(A);
+    kern<<<grid, GLOBAL ? kGlobalCtaThreads : threads, smem, st>>>(A);
     return (int)cudaGetLastError();
 }
 
-int cone_smem_grid(bool fp64, bool grad, int smem_bytes, int sm_count) {
+int cone_smem_grid(bool fp64, bool grad, int smem_bytes, int sm_count, int threads) {
     int per_sm = 0;
     cudaError_t e;
     if (fp64) {
-        e = grad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cone_kernel<double, true, false>, kCtaThreads, smem_bytes)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cone_kernel<double, false, false>, kCtaThreads, smem_bytes);
+        e = grad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cone_kernel<double, true, false>, threads, smem_bytes)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cone_kernel<double, false, false>, threads, smem_bytes);
     } else {
-        e = grad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cone_kernel<float, true, false>, kCtaThreads, smem_bytes)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cone_kernel<float, false, false>, kCtaThreads, smem_bytes);
+        e = grad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cone_kernel<float, true, false>, threads, smem_bytes)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cone_kernel<float, false, false>, threads, smem_bytes);
     }
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     return per_sm * sm_count;
 }
 
-int team_bytes_host(int W, int tt, bool fp64, bool grad, bool smem_state) {
-    return team_layout(W, tt, fp64 ? 8 : 4, grad, smem_state).bytes;
+int team_bytes_host(int W, int Wt, int tt, bool fp64, bool grad, bool smem_state) {
+    return team_layout(W, Wt, tt, fp64 ? 8 : 4, grad, smem_state).bytes;
 }
 
 int launch_cone(ConeLaunch& L, void* stream) {
@@ -832,22 +948,27 @@ int launch_cone(ConeLaunch& L, void* stream) {
         if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     }
     if ((e = cudaMemsetAsync(L.counters, 0, 2 * sizeof(int32_t), st)) != cudaSuccess) return (int)e;
+    if (L.accum) {   // branch items add their shares
+        if ((e = cudaMemsetAsync(L.e_part, 0, (size_t)L.B * L.n_terms * sizeof(double), st)) != cudaSuccess) return (int)e;
+        if (grad && (e = cudaMemsetAsync(L.g_part, 0, (size_t)L.B * L.n_slots * sizeof(double), st)) != cudaSuccess)
+            return (int)e;
+    }
     L.launches = 1 + (L.n_chunks_smem > 0) + (L.n_chunks > L.n_chunks_smem) + 1 + (grad ? 1 : 0);
+    const int smem_grid = cone_smem_grid(L.fp64, grad, L.smem_bytes, L.sm_count, L.smem_threads);
     if (L.ev_begin && (e = cudaEventRecord((cudaEvent_t)L.ev_begin, st)) != cudaSuccess) return (int)e;
     int rc;
-    const int smem_grid = cone_smem_grid(L.fp64, grad, L.smem_bytes, L.sm_count);
     if (L.fp64) {
-        rc = grad ? launch_cone_t<double, true, false>(L, st, 0, L.n_chunks_smem, L.smem_bytes, smem_grid, L.counters)
-                  : launch_cone_t<double, false, false>(L, st, 0, L.n_chunks_smem, L.smem_bytes, smem_grid, L.counters);
+        rc = grad ? launch_cone_t<double, true, false>(L, st, 0, L.n_chunks_smem, L.smem_bytes, smem_grid, L.counters, L.smem_threads)
+                  : launch_cone_t<double, false, false>(L, st, 0, L.n_chunks_smem, L.smem_bytes, smem_grid, L.counters, L.smem_threads);
         if (rc) return rc;
-        rc = grad ? launch_cone_t<double, true, true>(L, st, L.n_chunks_smem, L.n_chunks, L.gsmem_bytes, L.g_grid, L.counters + 1)
-                  : launch_cone_t<double, false, true>(L, st, L.n_chunks_smem, L.n_chunks, L.gsmem_bytes, L.g_grid, L.counters + 1);
+        rc = grad ? launch_cone_t<double, true, true>(L, st, L.n_chunks_smem, L.n_chunks, L.gsmem_bytes, L.g_grid, L.counters + 1, kGlobalCtaThreads)
+                  : launch_cone_t<double, false, true>(L, st, L.n_chunks_smem, L.n_chunks, L.gsmem_bytes, L.g_grid, L.counters + 1, kGlobalCtaThreads);
     } else {
-        rc = grad ? launch_cone_t<float, true, false>(L, st, 0, L.n_chunks_smem, L.smem_bytes, smem_grid, L.counters)
-                  : launch_cone_t<float, false, false>(L, st, 0, L.n_chunks_smem, L.smem_bytes, smem_grid, L.counters);
+        rc = grad ? launch_cone_t<float, true, false>(L, st, 0, L.n_chunks_smem, L.smem_bytes, smem_grid, L.counters, L.smem_threads)
+                  : launch_cone_t<float, false, false>(L, st, 0, L.n_chunks_smem, L.smem_bytes, smem_grid, L.counters, L.smem_threads);
         if (rc) return rc;
-        rc = grad ? launch_cone_t<float, true, true>(L, st, L.n_chunks_smem, L.n_chunks, L.gsmem_bytes, L.g_grid, L.counters + 1)
-                  : launch_cone_t<float, false, true>(L, st, L.n_chunks_smem, L.n_chunks, L.gsmem_bytes, L.g_grid, L.counters + 1);
+        rc = grad ? launch_cone_t<float, true, true>(L, st, L.n_chunks_smem, L.n_chunks, L.gsmem_bytes, L.g_grid, L.counters + 1, kGlobalCtaThreads)
+                  : launch_cone_t<float, false, true>(L, st, L.n_chunks_smem, L.n_chunks, L.gsmem_bytes, L.g_grid, L.counters + 1, kGlobalCtaThreads);
     }
     if (rc) return rc;
     if (L.ev_end && (e = cudaEventRecord((cudaEvent_t)L.ev_end, st)) != cudaSuccess) return (int)e;
@@ -909,7 +1030,7 @@ __global__ void batch_grad_kernel(const SetRec* sets, const double* g_part) {
 
 template <typename real, bool GRAD, bool GLOBAL>
 static int launch_batch_t(const BatchLaunch& L, cudaStream_t st, int begin, int end, int smem, int grid,
-                          int32_t* counter) {
+                          int32_t* counter, int threads) {
     if (end <= begin) return 0;
     auto kern = cone_kernel<real, GRAD, GLOBAL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -930,19 +1051,29 @@ static int launch_batch_t(const BatchLaunch& L, cudaStream_t st, int begin, int 
     const int n = end - begin;
     if (grid > n) grid = n;
     if (grid < 1) grid = 1;
-    kern<<<grid, GLOBAL ? kGlobalCtaThreads : kCtaThreads, smem, st>>>(A);
+    kern<<<grid, GLOBAL ? kGlobalCtaThreads : threads, smem, st>>>(A);
     return (int)cudaGetLastError();
 }
 
 template <typename real>
 static int launch_batch_all(BatchLaunch& L, cudaStream_t st) {
     int rc;
-    const int g0 = cone_smem_grid(sizeof(real) == 8, false, L.smem_bytes[0] > 0 ? L.smem_bytes[0] : 1024, L.sm_count);
-    const int g1 = cone_smem_grid(sizeof(real) == 8, true, L.smem_bytes[1] > 0 ? L.smem_bytes[1] : 1024, L.sm_count);
-    if ((rc = launch_batch_t<real, false, false>(L, st, L.range[0], L.range[1], L.smem_bytes[0], g0, L.counters + 0))) return rc;
-    if ((rc = launch_batch_t<real, false, true>(L, st, L.range[1], L.range[2], L.gsmem_bytes[0], L.g_grid, L.counters + 1))) return rc;
-    if ((rc = launch_batch_t<real, true, false>(L, st, L.range[2], L.range[3], L.smem_bytes[1], g1, L.counters + 2))) return rc;
-    if ((rc = launch_batch_t<real, true, true>(L, st, L.range[3], L.range[4], L.gsmem_bytes[1], L.g_grid, L.counters + 3))) return rc;
+    const int g0 = cone_smem_grid(sizeof(real) == 8, false, L.smem_bytes[0] > 0 ? L.smem_bytes[0] : 1024, L.sm_count,
+                                  L.smem_threads[0]);
+    const int g1 = cone_smem_grid(sizeof(real) == 8, true, L.smem_bytes[1] > 0 ? L.smem_bytes[1] : 1024, L.sm_count,
+                                  L.smem_threads[1]);
+    if ((rc = launch_batch_t<real, false, false>(L, st, L.range[0], L.range[1], L.smem_bytes[0], g0, L.counters + 0,
+                                                 L.smem_threads[0])))
+        return rc;
+    if ((rc = launch_batch_t<real, false, true>(L, st, L.range[1], L.range[2], L.gsmem_bytes[0], L.g_grid, L.counters + 1,
+                                                kGlobalCtaThreads)))
+        return rc;
+    if ((rc = launch_batch_t<real, true, false>(L, st, L.range[2], L.range[3], L.smem_bytes[1], g1, L.counters + 2,
+                                                L.smem_threads[1])))
+        return rc;
+    if ((rc = launch_batch_t<real, true, true>(L, st, L.range[3], L.range[4], L.gsmem_bytes[1], L.g_grid, L.counters + 3,
+                                               kGlobalCtaThreads)))
+        return rc;
     for (int k = 0; k < 4; ++k) L.launches += L.range[k + 1] > L.range[k];
     return 0;
 }
@@ -957,6 +1088,10 @@ int launch_cone_batch(BatchLaunch& L, void* stream) {
     else batch_gate_table_kernel<float><<<gk, 256, 0, st>>>(L.sets, (float2*)L.gate_table);
     if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     if ((e = cudaMemsetAsync(L.counters, 0, 4 * sizeof(int32_t), st)) != cudaSuccess) return (int)e;
+    if (L.accum) {   // branch items add their shares
+        if (L.e_count && (e = cudaMemsetAsync(L.e_part, 0, L.e_count * sizeof(double), st)) != cudaSuccess) return (int)e;
+        if (L.g_count && (e = cudaMemsetAsync(L.g_part, 0, L.g_count * sizeof(double), st)) != cudaSuccess) return (int)e;
+    }
     const int rc = L.fp64 ? launch_batch_all<double>(L, st) : launch_batch_all<float>(L, st);
     if (rc) return rc;
     batch_energy_kernel<<<(L.n_sets + 3) / 4, 128, 0, st>>>(L.sets, L.n_sets, L.e_part);

@@ -29,8 +29,16 @@ struct ConeDev {
     int32_t nslots;     // gradient slots of this cone
     int32_t mterm_off;  // first of this cone's measured terms in the MeasDev array
     int32_t nmterms;    // terms measured on this window
-    int32_t pad[2];
+    int32_t split;      // 1: run as two branches of W - 1 qubits (the top qubit has gates of
+                        // layer 0 only and no measured term); 0: one item of W qubits
+    int32_t pad;
 };
+
+// Work-list items are (cone word, set) pairs; the cone word carries the branch:
+// cone | half << kItemHalfShift, half 0 = the whole window, 1 / 2 = top bit 0 / 1.
+constexpr int kItemHalfShift = 28;
+constexpr int32_t kItemConeMask = (1 << kItemHalfShift) - 1;
+constexpr int kSplitMinW = 13;     // windows at least this wide are split when they can be
 
 // A term measured on a cone's window: P = (-i)^ny (-1)^popc(x & zy) X^flip.
 struct MeasDev {
@@ -62,7 +70,7 @@ struct ChunkDev {
 constexpr int kRecWords = 6;
 constexpr int kLayerHeader = 4;
 constexpr int kMinConeW = 8;       // narrower cones are padded to this width
-constexpr int kMaxGroupTerms = 8;  // terms measured on one shared window
+constexpr int kMaxGroupTerms = 16; // terms measured on one shared window
 constexpr int kMaxSmemConeW = 14;  // widest cone kept in shared memory (when it fits: FP32 forward at 14)
 constexpr int kMaxConeW = 20;      // widest cone on the cone path (global-memory tier)
 constexpr int kCtaThreads = 512;
@@ -269,8 +277,11 @@ struct ConeLaunch {
     int32_t n_chunks_smem = 0;            // chunks [0, n_chunks_smem) use shared memory
     int32_t n_chunks = 0;                 // chunks [n_chunks_smem, n_chunks) use global memory
     int32_t smem_bytes = 0;               // dynamic shared memory for the shared tier
+    int32_t smem_threads = kCtaThreads;   // CTA size of the shared tier
     int32_t gsmem_bytes = 0;              // dynamic shared memory for the global tier
     int32_t g_maxW = 0;                   // widest cone of the global tier
+    bool accum = false;                   // branch items: partial energies and slots are added
+                                          // (zeroed by the launcher)
     // workspace
     void* gate_table = nullptr;           // [B][n_gates] real2
     double* e_part = nullptr;             // [B][n_terms]
@@ -291,6 +302,33 @@ struct ConeLaunch {
 };
 
 int launch_cone(ConeLaunch& L, void* stream);
+
+// ---- work lists (planner.cpp) ----
+// One work item before chunking: the cone word (cone | half << kItemHalfShift), the set, the
+// state width W, the window width Wt (W + 1 for a branch) and the estimated amplitude visits.
+struct WorkItem {
+    int32_t cone, set, W, Wt;
+    double work;
+};
+// Chunks of one launch group (shared and global tier) and what their launches need.
+struct ChunkSet {
+    std::vector<ChunkDev> smem, glob;
+    int smem_bytes = 0, smem_threads = kCtaThreads, gsmem_bytes = 0, g_maxW = 0;
+    bool accum = false;   // branch items present
+};
+// Amplitude visits of one (cone, set) item as the cone kernel schedules its register passes:
+// the layer-0 product state, one pass per 4-bit group of live rotations per later layer (the
+// diagonal folded into the last), the measurement, and in the adjoint the diagonal pass plus
+// the rotation passes of every layer over both states.
+double cone_visits(const Plan& P, int cone, bool grad);
+// The items of one (cone, set): the whole window, or its two branches when the cone splits.
+void push_cone_items(const Plan& P, int cone, int set, bool grad, std::vector<WorkItem>& out);
+// Sorts `its` (widest state first, then most work first), appends the (cone word, set) pairs
+// to `items` and fills `cs` with the chunks of each width class: teams of 2^(W-4) threads as
+// many as fit a CTA in the shared tier, one 512-thread team per CTA in the global tier.
+void build_chunks(std::vector<WorkItem>& its, bool fp64, bool grad, int smax, std::vector<int32_t>& items,
+                  ChunkSet& cs);
+int team_bytes_host(int W, int Wt, int tt, bool fp64, bool grad, bool smem_state);
 
 // One parameter set of a serving batch: where its plan, angles, partial sums and outputs
 // live. Sets of different circuits share one launch through these records.
@@ -318,7 +356,10 @@ struct BatchLaunch {
     // chunk ranges: forward-only smem, forward-only global, gradient smem, gradient global
     int32_t range[5] = {0, 0, 0, 0, 0};
     int32_t smem_bytes[2] = {0, 0};   // shared tier: forward, gradient
+    int32_t smem_threads[2] = {kCtaThreads, kCtaThreads};   // shared tier CTA sizes
     int32_t gsmem_bytes[2] = {0, 0};  // global tier: forward, gradient
+    size_t e_count = 0, g_count = 0;  // doubles in e_part / g_part (zeroed when `accum`)
+    bool accum = false;               // branch items present
     void* gate_table = nullptr;
     double* e_part = nullptr;
     double* g_part = nullptr;
@@ -332,7 +373,7 @@ struct BatchLaunch {
     int launches = 0;
 };
 int launch_cone_batch(BatchLaunch& L, void* stream);
-int cone_smem_grid(bool fp64, bool grad, int smem_bytes, int sm_count);
+int cone_smem_grid(bool fp64, bool grad, int smem_bytes, int sm_count, int threads);
 
 struct DenseLaunch {
     int n_eff = 0;

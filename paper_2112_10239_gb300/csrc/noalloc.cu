@@ -29,7 +29,6 @@ constexpr size_t kStaticScratchBytes = (size_t)16 << 20;   // 16 MiB
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-int team_bytes_host(int W, int tt, bool fp64, bool grad, bool smem_state);
 
 namespace {
 
@@ -65,7 +64,8 @@ struct HostPlan {
     bool grad = false;
     std::vector<int32_t> items;
     std::vector<ChunkDev> chunks;
-    int n_chunks_smem = 0, smem_bytes = 0, gsmem_bytes = 0, g_maxW = 0;
+    int n_chunks_smem = 0, smem_bytes = 0, smem_threads = kCtaThreads, gsmem_bytes = 0, g_maxW = 0;
+    bool accum = false;
 };
 std::vector<std::unique_ptr<HostPlan>> g_plans;   // small LRU, guarded by g_mu
 
@@ -100,47 +100,20 @@ void fingerprint(const Context* ctx, const Circuit& c, const Ham& h, uint64_t ou
 
 void build_host_worklist(HostPlan& hp, int B, bool grad, int smax) {
     const Plan& P = *hp.plan;
-    const int T = (int)P.cones.size();
-    std::vector<int> order(T);
-    for (int t = 0; t < T; ++t) order[t] = t;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P.cones[a].W > P.cones[b].W; });
+    std::vector<WorkItem> its;
+    for (int t = 0; t < (int)P.cones.size(); ++t)
+        for (int b = 0; b < B; ++b) push_cone_items(P, t, b, grad, its);
     hp.items.clear();
-    std::vector<ChunkDev> sm, gl;
-    hp.smem_bytes = hp.gsmem_bytes = hp.g_maxW = 0;
-    size_t k = 0;
-    while (k < order.size()) {
-        const int W = P.cones[order[k]].W;
-        size_t k2 = k;
-        while (k2 < order.size() && P.cones[order[k2]].W == W) ++k2;
-        int tt = std::min(kCtaThreads, 1 << (W - 4));
-        int tb = team_bytes_host(W, tt, false, grad, true);
-        int nteams = std::min(kCtaThreads / tt, smax / tb);
-        const bool global = (W > kMaxSmemConeW) || nteams < 1;
-        if (global) {
-            tt = kGlobalCtaThreads;
-            tb = team_bytes_host(W, tt, false, grad, false);
-            nteams = 1;
-        }
-        const int first = (int)hp.items.size() / 2;
-        for (size_t i = k; i < k2; ++i)
-            for (int b = 0; b < B; ++b) { hp.items.push_back(order[i]); hp.items.push_back(b); }
-        const int nit = (int)hp.items.size() / 2 - first;
-        for (int f = 0; f < nit; f += nteams) {
-            ChunkDev ch{};
-            ch.W = W;
-            ch.first = first + f;
-            ch.count = std::min(nteams, nit - f);
-            ch.tt = tt;
-            ch.team_bytes = tb;
-            (global ? gl : sm).push_back(ch);
-        }
-        if (global) { hp.gsmem_bytes = std::max(hp.gsmem_bytes, tb); hp.g_maxW = std::max(hp.g_maxW, W); }
-        else hp.smem_bytes = std::max(hp.smem_bytes, nteams * tb);
-        k = k2;
-    }
-    hp.chunks = sm;
-    hp.chunks.insert(hp.chunks.end(), gl.begin(), gl.end());
-    hp.n_chunks_smem = (int)sm.size();
+    ChunkSet cs;
+    build_chunks(its, false, grad, smax, hp.items, cs);
+    hp.chunks = cs.smem;
+    hp.chunks.insert(hp.chunks.end(), cs.glob.begin(), cs.glob.end());
+    hp.n_chunks_smem = (int)cs.smem.size();
+    hp.smem_bytes = cs.smem_bytes;
+    hp.smem_threads = cs.smem_threads;
+    hp.gsmem_bytes = cs.gsmem_bytes;
+    hp.g_maxW = cs.g_maxW;
+    hp.accum = cs.accum;
     hp.B = B;
     hp.grad = grad;
 }
@@ -277,6 +250,8 @@ extern "C" tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tl
     L.n_chunks_smem = hp->n_chunks_smem;
     L.n_chunks = (int)hp->chunks.size();
     L.smem_bytes = hp->smem_bytes;
+    L.smem_threads = hp->smem_threads;
+    L.accum = hp->accum;
     L.gsmem_bytes = hp->gsmem_bytes;
     L.g_maxW = hp->g_maxW;
     L.gate_table = d_gt;

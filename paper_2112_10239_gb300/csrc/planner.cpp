@@ -213,6 +213,28 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
         const int lo = glo[t];
         const int W = std::max(ghi[t] - glo[t] + 1, kMinConeW);
         P->group_wtrue[t] = ghi[t] - glo[t] + 1;
+        // A wide window whose top qubit is busy after the first layer (or measured) but whose
+        // bottom qubit is free is laid out mirrored (window qubit j = chain qubit hi - j), so
+        // that the free end is the top and the window can run as two branches (see below).
+        bool mirror = false;
+        if (W >= kSplitMinW && P->group_wtrue[t] == W && !kept.empty()) {
+            const int l0 = ix.layer_of[kept.front()];
+            auto end_free = [&](int q) {
+                for (int m : members[t])
+                    for (int site : h.terms[m].sites)
+                        if (site == q) return false;
+                for (int g : kept) {
+                    const tlq_gate& G = c.gates[g];
+                    const bool touches = G.q0 == q || (is_two(G.kind) && G.q1 == q);
+                    if (touches && ix.layer_of[g] != l0) return false;
+                }
+                return true;
+            };
+            mirror = !end_free(ghi[t]) && end_free(lo);
+        }
+        const int top_q = lo + W - 1;
+        auto pos1 = [&](int q) { return mirror ? top_q - q : q - lo; };                  // window qubit of q
+        auto pos2 = [&](int a, int b) { return mirror ? top_q - std::max(a, b) : std::min(a, b) - lo; };   // of pair (a, a+1)
         // Emit the program in forward layer order: per layer a header and one fixed record
         // per window qubit (see internal.h). A layer whose cone gates put two RZ on one
         // qubit or two two-qubit gates on one pair is split into several layers (the
@@ -240,7 +262,7 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                 if (ix.is_rot[g]) continue;
                 const tlq_gate& G = c.gates[g];
                 const bool two = is_two(G.kind);
-                const uint32_t bit = 1u << (std::min(G.q0, two ? G.q1 : G.q0) - lo);
+                const uint32_t bit = 1u << (two ? pos2(G.q0, G.q1) : pos1(G.q0));
                 int part = 0;
                 while (part < nparts && ((two ? pmask[part] : zmask[part]) & bit)) ++part;
                 if (part == nparts) {
@@ -265,7 +287,7 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                     for (size_t k = kp; k < kp2; ++k) {
                         const int g = kept[k];
                         if (!ix.is_rot[g]) continue;
-                        const int jj = c.gates[g].q0 - lo;
+                        const int jj = pos1(c.gates[g].q0);
                         rec[(size_t)jj * kRecWords + 0] = g;
                         live |= 1u << jj;
                     }
@@ -275,7 +297,7 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
                     if (dp.second != part) continue;
                     const tlq_gate& G = c.gates[dp.first];
                     const bool two = is_two(G.kind);
-                    const int jj = std::min(G.q0, two ? G.q1 : G.q0) - lo;
+                    const int jj = two ? pos2(G.q0, G.q1) : pos1(G.q0);
                     rec[(size_t)jj * kRecWords + (two ? 4 : 2)] = dp.first;
                     any_diag = true;
                 }
@@ -331,13 +353,31 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
             MeasDev md{};
             md.term = m;
             for (size_t q = 0; q < term.sites.size(); ++q) {
-                const uint32_t bit = 1u << (term.sites[q] - lo);
+                const uint32_t bit = 1u << pos1(term.sites[q]);
                 const char ch = term.letters[q];
                 if (ch == 'X' || ch == 'Y') md.flip |= bit;
                 if (ch == 'Y' || ch == 'Z') md.zy |= bit;
                 if (ch == 'Y') ++md.ny;
             }
             P->meas.push_back(md);
+        }
+        // Two branches of W - 1 qubits instead of one window when the window is real (no
+        // padding), wide, its top qubit has gates of program layer 0 only and no measured
+        // term touches it: the branches with top bit 0 and 1 are then independent items.
+        cd.split = 0;
+        if (W >= kSplitMinW && P->group_wtrue[t] == W && nlayers >= 1) {
+            const int top = W - 1;
+            bool ok = true;
+            for (int m = cd.mterm_off; m < cd.mterm_off + cd.nmterms; ++m)
+                if (((P->meas[m].flip | P->meas[m].zy) >> top) & 1u) ok = false;
+            for (int li = 1; li < nlayers && ok; ++li) {
+                const int32_t* lp = body.data() + layer_off[li];
+                const int32_t* rec = lp + kLayerHeader;
+                if (((uint32_t)lp[1] >> top) & 1u) ok = false;                 // rotation on top
+                if (rec[top * kRecWords + 2] >= 0) ok = false;                 // RZ on top
+                if (rec[(top - 1) * kRecWords + 4] >= 0) ok = false;           // pair (top - 1, top)
+            }
+            cd.split = ok ? 1 : 0;
         }
         P->cones[t] = cd;
     }
@@ -360,6 +400,129 @@ std::shared_ptr<Plan> make_plan(const Circuit& c, const Ham& h, std::string* err
     return P;
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Work lists of the cone kernel.
+// ---------------------------------------------------------------------------------------
+
+double cone_visits(const Plan& P, int cone, bool grad) {
+    const ConeDev& cd = P.cones[cone];
+    const int W = cd.W;
+    const int32_t* prog = P.prog.data() + cd.prog_off;
+    const int nl = prog[0];
+    const int32_t* body = prog + 1 + nl;
+    double passes = 1 + 1;   // layer 0 (or the |0..0> start) and the measurement
+    for (int li = 0; li < nl; ++li) {
+        const int32_t* lp = body + prog[1 + li];
+        const bool diag = lp[0] > 0;
+        const unsigned live = (unsigned)lp[1];
+        if (li > 0) {
+            unsigned todo = live;
+            int n = 0;
+            while (todo) {
+                const int bt = __builtin_ctz(todo);
+                const int sh = bt < 4 ? 0 : std::min(bt, W - 4);
+                todo &= ~(15u << sh);
+                ++n;
+            }
+            passes += std::max(n, diag ? 1 : 0);
+        }
+        if (grad) {
+            unsigned todo = live;
+            int n = diag ? 1 : 0;
+            while (todo) {
+                const int bt = 31 - __builtin_clz(todo);
+                int sh = bt - 3;
+                if (sh < 4) sh = bt >= 4 ? 4 : 0;
+                if (sh > W - 4) sh = W - 4;
+                todo &= ~(15u << sh);
+                ++n;
+            }
+            passes += 2.0 * n;
+        }
+    }
+    return passes * (double)(1u << W);
+}
+
+void push_cone_items(const Plan& P, int cone, int set, bool grad, std::vector<WorkItem>& out) {
+    const ConeDev& cd = P.cones[cone];
+    const double w = cone_visits(P, cone, grad);
+    if (cd.split) {
+        out.push_back({cone | (1 << kItemHalfShift), set, cd.W - 1, cd.W, 0.5 * w});
+        out.push_back({cone | (2 << kItemHalfShift), set, cd.W - 1, cd.W, 0.5 * w});
+    } else {
+        out.push_back({cone, set, cd.W, cd.W, w});
+    }
+}
+
+void build_chunks(std::vector<WorkItem>& its, bool fp64, bool grad, int smax, std::vector<int32_t>& items,
+                  ChunkSet& cs) {
+    // widest state first; within a width the most amplitude visits first, so that the items
+    // left for the last round of a width class are its cheapest
+    std::stable_sort(its.begin(), its.end(), [](const WorkItem& a, const WorkItem& b) {
+        if (a.W != b.W) return a.W > b.W;
+        return a.work > b.work;
+    });
+    struct Class {
+        size_t k, k2;
+        int W, tt, tb;
+        bool global;
+    };
+    std::vector<Class> cls;
+    int max_tt = 0;
+    for (size_t k = 0; k < its.size();) {
+        Class c{};
+        c.k = k;
+        c.W = its[k].W;
+        int wt = c.W;   // widest window of the class (tables of branch items cover the whole window)
+        size_t k2 = k;
+        while (k2 < its.size() && its[k2].W == c.W) {
+            wt = std::max(wt, its[k2].Wt);
+            ++k2;
+        }
+        c.k2 = k2;
+        c.tt = std::min(kCtaThreads, 1 << (c.W - 4));
+        c.tb = team_bytes_host(c.W, wt, c.tt, fp64, grad, true);
+        c.global = c.W > kMaxSmemConeW || c.tb > smax;
+        if (c.global) {
+            c.tt = kGlobalCtaThreads;
+            c.tb = team_bytes_host(c.W, wt, c.tt, fp64, grad, false);
+        } else {
+            max_tt = std::max(max_tt, c.tt);
+        }
+        cls.push_back(c);
+        k = k2;
+    }
+    // Shared-tier CTAs of 256 threads when the widest teams have 256: two CTAs per SM with one
+    // such team each take their items independently (finer load balance at the end of a
+    // launch); 512 threads otherwise.
+    cs.smem_threads = max_tt == 256 ? 256 : kCtaThreads;
+    for (const Class& c : cls) {
+        const int nteams = c.global ? 1 : std::max(1, std::min(cs.smem_threads / c.tt, smax / c.tb));
+        const int first = (int)items.size() / 2;
+        for (size_t i = c.k; i < c.k2; ++i) {
+            items.push_back(its[i].cone);
+            items.push_back(its[i].set);
+            if (its[i].Wt > its[i].W) cs.accum = true;
+        }
+        const int nit = (int)(c.k2 - c.k);
+        for (int f = 0; f < nit; f += nteams) {
+            ChunkDev ch{};
+            ch.W = c.W;
+            ch.first = first + f;
+            ch.count = std::min(nteams, nit - f);
+            ch.tt = c.tt;
+            ch.team_bytes = c.tb;
+            (c.global ? cs.glob : cs.smem).push_back(ch);
+        }
+        if (c.global) {
+            cs.gsmem_bytes = std::max(cs.gsmem_bytes, c.tb);
+            cs.g_maxW = std::max(cs.g_maxW, c.W);
+        } else {
+            cs.smem_bytes = std::max(cs.smem_bytes, nteams * c.tb);
+        }
+    }
+}
 
 // ---------------------------------------------------------------------------------------
 // Dense statevector plan.

@@ -49,6 +49,8 @@ struct PlanEntry {
     ChunkDev* d_chunks = nullptr;
     int n_chunks_smem = 0, n_chunks = 0;
     int smem_bytes = 0, gsmem_bytes = 0, g_maxW = 0;
+    int smem_threads = 512;   // CTA size of the shared tier
+    bool accum = false;       // branch items: the launcher zeroes the partial sums
     size_t device_bytes = 0;
     // CUDA graph of the synchronous call's device work (input copy, kernels, output copies),
     // replayed while the key below is unchanged; see sync_call in api.cpp

@@ -28,8 +28,6 @@
 
 namespace tlq {
 
-int team_bytes_host(int W, int tt, bool fp64, bool grad, bool smem_state);
-
 namespace {
 
 double now_s() {
@@ -170,10 +168,6 @@ namespace tlq {
 
 namespace {
 
-struct ItemRec {
-    int32_t W, cone, set;
-};
-
 size_t global_slot(int W, bool fp64, bool grad) {
     const size_t amps = ((size_t)1 << W) + ((size_t)1 << (W - 3));
     return al(amps * (fp64 ? 16 : 8) * (grad ? 2 : 1));
@@ -196,7 +190,7 @@ size_t Scheduler::request_bytes(const ServeRequest& r) const {
          al(P.prog.size() * 4) + al(T * 8);
     s += al((P.pmap_off.size()) * 4) + 2 * al(std::max<size_t>(1, E) * 4);
     s += al((size_t)r.B * std::max(1, r.n_params) * 8);                      // theta
-    s += (size_t)r.B * (sizeof(SetRec) + T * 8 + sizeof(ChunkDev));           // records, items, chunks
+    s += (size_t)r.B * (sizeof(SetRec) + P.cones.size() * (16 + 2 * sizeof(ChunkDev)));   // records, items, chunks
     s += (size_t)r.B * 8 + (r.grad ? (size_t)r.B * r.n_params * 8 : 0);       // outputs
     s += al((size_t)r.B * std::max<size_t>(1, G) * r2) + al((size_t)r.B * T * 8);
     if (r.grad) s += al((size_t)r.B * std::max<int32_t>(1, P.n_slots) * 8);
@@ -214,13 +208,13 @@ bool Scheduler::launch(Slot& sl, std::vector<ServeRequest*>& batch) {
     }
     // ---- work list: (grad, tier, W desc) groups, chunked per width class ----
     const int smax = smem_optin_dev(ctx->device);
-    std::vector<ItemRec> its[2];
+    std::vector<WorkItem> its[2];
     {
         int gs = 0;
         for (ServeRequest* r : batch) {
             const Plan& P = *r->plan;
             for (int b = 0; b < r->B; ++b, ++gs)
-                for (size_t t = 0; t < P.cones.size(); ++t) its[r->grad ? 1 : 0].push_back({P.cones[t].W, (int32_t)t, gs});
+                for (size_t t = 0; t < P.cones.size(); ++t) push_cone_items(P, (int)t, gs, r->grad, its[r->grad ? 1 : 0]);
         }
     }
     std::vector<int32_t> items;
@@ -230,48 +224,21 @@ bool Scheduler::launch(Slot& sl, std::vector<ServeRequest*>& batch) {
     bool g_grad = false;
     int n_glob_max = 0;
     for (int gr = 0; gr < 2; ++gr) {
-        std::stable_sort(its[gr].begin(), its[gr].end(), [](const ItemRec& a, const ItemRec& b) { return a.W > b.W; });
-        std::vector<ChunkDev> sm, gl;
-        size_t k = 0;
-        while (k < its[gr].size()) {
-            const int W = its[gr][k].W;
-            size_t k2 = k;
-            while (k2 < its[gr].size() && its[gr][k2].W == W) ++k2;
-            int tt = std::min(kCtaThreads, 1 << (W - 4));
-            int tb = team_bytes_host(W, tt, fp64, gr == 1, true);
-            int nteams = std::min(kCtaThreads / tt, smax / tb);
-            const bool global = (W > kMaxSmemConeW) || nteams < 1;
-            if (global) {
-                tt = kGlobalCtaThreads;
-                tb = team_bytes_host(W, tt, fp64, gr == 1, false);
-                nteams = 1;
-            }
-            const int first = (int)items.size() / 2;
-            for (size_t i = k; i < k2; ++i) { items.push_back(its[gr][i].cone); items.push_back(its[gr][i].set); }
-            const int nit = (int)(k2 - k);
-            for (int f = 0; f < nit; f += nteams) {
-                ChunkDev ch{};
-                ch.W = W;
-                ch.first = first + f;
-                ch.count = std::min(nteams, nit - f);
-                ch.tt = tt;
-                ch.team_bytes = tb;
-                (global ? gl : sm).push_back(ch);
-            }
-            if (global) {
-                L.gsmem_bytes[gr] = std::max(L.gsmem_bytes[gr], tb);
-                g_maxW = std::max(g_maxW, W);
-                g_grad |= gr == 1;
-            } else {
-                L.smem_bytes[gr] = std::max(L.smem_bytes[gr], nteams * tb);
-            }
-            k = k2;
+        ChunkSet cs;
+        build_chunks(its[gr], fp64, gr == 1, smax, items, cs);
+        L.smem_bytes[gr] = cs.smem_bytes;
+        L.smem_threads[gr] = cs.smem_threads;
+        L.gsmem_bytes[gr] = cs.gsmem_bytes;
+        L.accum |= cs.accum;
+        if (!cs.glob.empty()) {
+            g_maxW = std::max(g_maxW, cs.g_maxW);
+            g_grad |= gr == 1;
         }
         L.range[2 * gr] = (int32_t)chunks.size();
-        chunks.insert(chunks.end(), sm.begin(), sm.end());
+        chunks.insert(chunks.end(), cs.smem.begin(), cs.smem.end());
         L.range[2 * gr + 1] = (int32_t)chunks.size();
-        chunks.insert(chunks.end(), gl.begin(), gl.end());
-        n_glob_max = std::max(n_glob_max, (int)gl.size());
+        chunks.insert(chunks.end(), cs.glob.begin(), cs.glob.end());
+        n_glob_max = std::max(n_glob_max, (int)cs.glob.size());
     }
     L.range[4] = (int32_t)chunks.size();
     const int g_grid = std::min(n_glob_max, kGlobalCtasPerSm * ctx->sm_count);
@@ -396,6 +363,8 @@ bool Scheduler::launch(Slot& sl, std::vector<ServeRequest*>& batch) {
     L.gate_table = D + o_gt;
     L.e_part = (double*)(D + o_e);
     L.g_part = (double*)(D + o_g);
+    L.e_count = e_total;
+    L.g_count = g_total;
     L.gscratch = g_grid > 0 ? D + o_gs : nullptr;
     L.gscratch_slot = gslot;
     L.g_grid = g_grid;

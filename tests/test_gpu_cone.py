@@ -59,6 +59,49 @@ def test_random_local_circuits(tlq, seed, prec):
     check_grad(g, gr, prec)
 
 
+@pytest.mark.parametrize("n,L,seed", [(16, 7, 40), (18, 8, 45), (20, 8, 42)])
+@pytest.mark.parametrize("prec", [0, 2])
+def test_split_windows_random_local(tlq, n, L, seed, prec):
+    # windows of 13 to 16 qubits whose end qubit carries only first-layer gates run as two
+    # branches (in shared memory, or on the global tier from 15 up); the first layer draws RX
+    # or RY per qubit and RZ / RZZ / CZ at random, so the branch's top rotation gradient (both
+    # kinds) and its diagonal terms are exercised, and windows are mirrored where only the
+    # bottom end is free
+    from paper_2112_10239_gb300 import binding as B
+    prob = W.random_local_problem(n, L, 2, seed)
+    c, h = tlq.problem(prob)
+    try:
+        split = B.tlq_plan_cone_stats(tlq.h, c.h, h.h, len(prob.terms))[6]
+    finally:
+        c.close()
+        h.close()
+    assert split.sum() > 0
+    E, g = _run(tlq, prob, prec=prec)
+    Er, gr = _oracle(prob, prob.theta)
+    check_energy(E, Er, prec)
+    check_grad(g, gr, prec)
+    Ee, _ = _run(tlq, prob, prec=prec, grad=False)
+    check_energy(Ee, Er, prec)
+
+
+def test_split_windows_tfim_counts(tlq):
+    # n=20, L=6: all eight 13-qubit windows split (the last one laid out mirrored: its top end
+    # is the end of the chain, which carries terms); the oracle checks energy and gradient
+    from paper_2112_10239_gb300 import binding as B
+    prob = W.tfim_n20_L6_B64(B=2)
+    c, h = tlq.problem(prob)
+    try:
+        _, _, _, weff, _, _, split = B.tlq_plan_cone_stats(tlq.h, c.h, h.h, len(prob.terms))
+    finally:
+        c.close()
+        h.close()
+    assert list(weff) == [13] * 8 and split.sum() == 8
+    E, g = _run(tlq, prob)
+    Er, gr = _oracle(prob, prob.theta)
+    check_energy(E, Er)
+    check_grad(g, gr)
+
+
 @pytest.mark.parametrize("n,L,B", [(1, 1, 2), (2, 3, 1), (5, 2, 5), (9, 4, 3), (12, 5, 2)])
 def test_tfim_small_and_degenerate(tlq, n, L, B):
     prob = W.tfim_problem(n, L, B, seed=n * 10 + L, h_range=(0.5, 1.5))
@@ -153,12 +196,12 @@ def test_repeated_calls_identical(tlq):
 
 def test_width14_forward_in_shared_memory(tlq):
     # L=7 with ZZ terms only, energies only: every window is 14 wide and runs in shared
-    # memory with two amplitude blocks per thread.
+    # memory (whole, or as two 13-qubit branches where the top qubit allows it).
     from paper_2112_10239_gb300 import binding as B
     p = W.tfim_problem(22, 7, 3, seed=8, h_range=(0.5, 1.5))
     prob = W.Problem(p.n, p.gates, p.n_params, [t for t in p.terms if t[2] == "ZZ"], p.theta)
     c, h = tlq.problem(prob)
-    _, _, _, weff, _, _ = B.tlq_plan_cone_stats(tlq.h, c.h, h.h, len(prob.terms))
+    _, _, _, weff, _, _, _ = B.tlq_plan_cone_stats(tlq.h, c.h, h.h, len(prob.terms))
     c.close()
     h.close()
     assert max(weff) == 14
@@ -189,7 +232,7 @@ def test_widest_cones_L9(tlq):
     prob = W.tfim_problem(22, 9, 1, seed=17, h_range=(0.5, 1.5))
     c, h = tlq.problem(prob)
     try:
-        _, _, _, weff, _, _ = B.tlq_plan_cone_stats(tlq.h, c.h, h.h, len(prob.terms))
+        _, _, _, weff, _, _, _ = B.tlq_plan_cone_stats(tlq.h, c.h, h.h, len(prob.terms))
     finally:
         c.close()
         h.close()

@@ -53,6 +53,35 @@ def test_single_request_equals_sync_call(tlq):
         hd.close()
 
 
+def test_split_windows_served_equal_sync(tlq):
+    # depth 6 and 7: 13- and 15-qubit windows run as two branches each; served alone and
+    # together (energy-only and gradient requests), the results equal the synchronous calls
+    from paper_2112_10239_gb300 import binding as B
+    probs = [W.tfim_problem(24, 6, 2, seed=31, h_range=(0.5, 1.5)),
+             W.tfim_problem(20, 7, 1, seed=32, h_range=(0.5, 1.5)),
+             W.tfim_problem(17, 6, 3, seed=33, h_range=(0.5, 1.5))]
+    grads = [True, True, False]
+    handles = [tlq.problem(p) for p in probs]
+    for p, hd in zip(probs, handles):
+        split = B.tlq_plan_cone_stats(tlq.h, hd[0].h, hd[1].h, len(p.terms))[6]
+        assert split.sum() > 0
+    pending = [_submit(B, tlq, hd, p, g) for p, g, hd in zip(probs, grads, handles)]
+    for t, _ in pending:
+        _wait(B, tlq, t)
+    for p, g, hd, (_, (th, E, G)) in zip(probs, grads, handles, pending):
+        if g:
+            Es, Gs = B.tlq_expectation_grad(tlq.h, hd[0].h, hd[1].h, p.theta)
+            assert np.array_equal(E, Es) and np.array_equal(G, Gs)
+        else:
+            Es = B.tlq_expectation(tlq.h, hd[0].h, hd[1].h, p.theta)
+            assert np.array_equal(E, Es)
+        Er = [dense.energy(p.n, p.gates, p.terms, t) for t in p.theta]
+        check_energy(E, Er)
+    for hd in handles:
+        for x in hd:
+            x.close()
+
+
 def test_alone_and_in_mix_identical(tlq):
     from paper_2112_10239_gb300 import binding as B
     reqs = _requests(40, seed=3)
