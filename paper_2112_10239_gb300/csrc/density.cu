@@ -7,9 +7,12 @@
 // Kernels:
 //   * psi_gather_kernel lays Psi out row-major (row i contiguous in k) from the state, where
 //     bit t of i is the t-th lowest kept qubit and bit u of k the u-th lowest traced one;
-//   * herk_tc_kernel (m >= 7) computes 128 x 128 tiles of the upper block triangle on the
-//     tensor cores (tcgen05, TF32 high/low split, FP32 accumulators in tensor memory) and
-//     writes off-diagonal tiles and their conjugate mirrors with TMA tensor stores;
+//   * herk_ws_kernel (m >= 7 with at least one whole tile per SM) computes 128 x 128 tiles of
+//     the upper block triangle on the tensor cores (tcgen05, TF32 high/low split, FP32
+//     accumulators in tensor memory): persistent CTAs with producer, MMA and epilogue warps,
+//     two accumulator sets, TMA tensor stores of off-diagonal tiles and their conjugate mirrors;
+//   * herk_tc_kernel (m >= 7, fewer tiles: k split over CTAs) does the same arithmetic one
+//     tile per CTA, all warps taking turns at loading and storing;
 //   * herk_tile_kernel (m < 7) computes 64 x 64 tiles on FP32 CUDA cores with 4 x 4 complex
 //     register blocks per thread from 16-wide k chunks staged in shared memory.
 // Entries above the diagonal are written twice (as computed, and conjugate-transposed below
@@ -54,7 +57,7 @@ __global__ void psi_gather_kernel(const float2* __restrict__ psi, float2* __rest
 
 // Upper block-triangle tile u -> (bi, bj), bi <= bj: u = bj (bj + 1) / 2 + bi.
 __device__ __forceinline__ void tri_tile(uint32_t u, int& bi, int& bj) {
-    int r = (int)((sqrt(8.0 * (double)u + 1.0) - 1.0) * 0.5);
+    int r = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);   // within one of the root; fixed below
     while ((uint64_t)(r + 1) * (uint64_t)(r + 2) / 2 <= u) ++r;
     while ((uint64_t)r * (uint64_t)(r + 1) / 2 > u) --r;
     bj = r;
@@ -171,21 +174,28 @@ __global__ void herk_reduce_kernel(const float2* __restrict__ partial, int split
 // A = rows i of the output tile, B = rows j. Each FP32 operand x is split into TF32 parts
 // x_hi (x with the low 13 mantissa bits cleared, exact in TF32) and x_lo = x - x_hi; every
 // product is x_hi y_hi + x_hi y_lo + x_lo y_hi (the dropped x_lo y_lo is 2^-20 relative),
-// accumulated in FP32 in tensor memory. One CTA (8 warps) owns a 128 x 128 output tile:
-// Re and Im accumulators take 2 x 128 TMEM columns. The k range is walked in chunks of 8
-// complex values, double-buffered in shared memory: all threads load and split a chunk
-// while the tensor core works on the previous one, and thread 0 issues the 12 MMAs of a
-// chunk (M = N = 128, K = 8, kind::tf32) and commits them to that buffer's mbarrier; the
-// global loads of the following chunk are issued right after, so their latency overlaps the
-// tensor core's work.
+// accumulated in FP32 in tensor memory: Re in TMEM columns 0..127 of the accumulator, Im in
+// 128..255. The twelve products of a chunk go as six MMAs of N = 256 (M = 128, K = 8,
+// kind::tf32): an A part times a stack of two B parts [X; Y] adds A X^T to Re and A Y^T to Im.
+// The B parts are laid out as [B_im hi][B_re hi][-B_im hi] [B_im lo][B_re lo][-B_im lo], so
+// every stack needed is two neighbouring parts:
+//   A_re hi x [B_re hi; -B_im hi],  A_re hi x [B_re lo; -B_im lo],  A_re lo x [B_re hi; -B_im hi],
+//   A_im hi x [B_im hi;  B_re hi],  A_im hi x [B_im lo;  B_re lo],  A_im lo x [B_im hi;  B_re hi].
 // Shared-memory operands use the no-swizzle K-major layout: 8-row x 16-byte core matrices,
-// 128 bytes apart along K and 256 bytes apart along M/N (one 4 KB tile per operand part).
+// 128 bytes apart along K and 256 bytes apart along M/N (one 4 KB tile per operand part, a
+// 256-row stack spanning two neighbouring parts).
+//
+// herk_tc_kernel: one CTA (8 warps) owns a 128 x 128 output tile. The k range is walked in
+// chunks of 8 complex values, double-buffered in shared memory: all threads load and split a
+// chunk while the tensor core works on the previous one, and thread 0 issues the chunk's MMAs
+// and commits them to that buffer's mbarrier; the global loads of the following chunk are
+// issued right after, so their latency overlaps the tensor core's work.
 
 constexpr int kTcTile = 128;
 constexpr int kTcThreads = 256;
 constexpr int kTcChunk = 8;                         // complex k per stage (one MMA K-step)
 constexpr int kTcPartBytes = kTcTile * kTcChunk * 4; // 4 KB: 128 rows x 8 TF32
-constexpr int kTcParts = 10;                        // A re/im, B re/im, B -im; each hi and lo
+constexpr int kTcParts = 10;                        // A: re/im hi/lo; B: im, re, -im, each hi and lo
 constexpr int kTcStageBytes = kTcParts * kTcPartBytes;
 constexpr int kTcTmemCols = 2 * kTcTile;            // Re and Im accumulators
 constexpr unsigned long long kTcWaitNs = 1000000000ull;   // bound on every mbarrier wait
@@ -225,8 +235,8 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-// Instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, M = N = 128.
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcTile >> 3) << 17) |
+// Instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, M = 128, N = 256.
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)((2 * kTcTile) >> 3) << 17) |
                               ((uint32_t)(kTcTile >> 4) << 24);
 
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
@@ -267,9 +277,10 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 // Split 4 complex values of row `row` (k = 4 * half .. +3 of the chunk) into the operand parts
-// at `base` (re hi, re lo, im hi, im lo [, -im hi, -im lo]); 16-byte stores.
+// at `base`: A side (re hi, re lo, im hi, im lo), or B side (im hi, re hi, -im hi, im lo,
+// re lo, -im lo); 16-byte stores.
 __device__ __forceinline__ void put_row4(unsigned char* base, int row, int half, const float4& p0, const float4& p1,
-                                         bool with_neg) {
+                                         bool b_side) {
     const int off = (row >> 3) * 256 + half * 128 + (row & 7) * 16;
     const float re[4] = {p0.x, p0.z, p1.x, p1.z};
     const float im[4] = {p0.y, p0.w, p1.y, p1.w};
@@ -281,14 +292,32 @@ __device__ __forceinline__ void put_row4(unsigned char* base, int row, int half,
         ih[e] = tf32_hi(im[e]);
         il[e] = im[e] - ih[e];
     }
-    *reinterpret_cast<float4*>(base + 0 * kTcPartBytes + off) = make_float4(rh[0], rh[1], rh[2], rh[3]);
-    *reinterpret_cast<float4*>(base + 1 * kTcPartBytes + off) = make_float4(rl[0], rl[1], rl[2], rl[3]);
-    *reinterpret_cast<float4*>(base + 2 * kTcPartBytes + off) = make_float4(ih[0], ih[1], ih[2], ih[3]);
-    *reinterpret_cast<float4*>(base + 3 * kTcPartBytes + off) = make_float4(il[0], il[1], il[2], il[3]);
-    if (with_neg) {
-        *reinterpret_cast<float4*>(base + 4 * kTcPartBytes + off) = make_float4(-ih[0], -ih[1], -ih[2], -ih[3]);
+    if (!b_side) {
+        *reinterpret_cast<float4*>(base + 0 * kTcPartBytes + off) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+        *reinterpret_cast<float4*>(base + 1 * kTcPartBytes + off) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+        *reinterpret_cast<float4*>(base + 2 * kTcPartBytes + off) = make_float4(ih[0], ih[1], ih[2], ih[3]);
+        *reinterpret_cast<float4*>(base + 3 * kTcPartBytes + off) = make_float4(il[0], il[1], il[2], il[3]);
+    } else {
+        *reinterpret_cast<float4*>(base + 0 * kTcPartBytes + off) = make_float4(ih[0], ih[1], ih[2], ih[3]);
+        *reinterpret_cast<float4*>(base + 1 * kTcPartBytes + off) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+        *reinterpret_cast<float4*>(base + 2 * kTcPartBytes + off) = make_float4(-ih[0], -ih[1], -ih[2], -ih[3]);
+        *reinterpret_cast<float4*>(base + 3 * kTcPartBytes + off) = make_float4(il[0], il[1], il[2], il[3]);
+        *reinterpret_cast<float4*>(base + 4 * kTcPartBytes + off) = make_float4(rl[0], rl[1], rl[2], rl[3]);
         *reinterpret_cast<float4*>(base + 5 * kTcPartBytes + off) = make_float4(-il[0], -il[1], -il[2], -il[3]);
     }
+}
+
+// The six MMAs of one staged chunk (parts at shared address `st`) into the accumulator at TMEM
+// column `d` (Re at d, Im at d + 128); `acc` = 0 starts a new tile.
+__device__ __forceinline__ void issue_chunk(uint32_t d, uint32_t st, uint32_t acc) {
+    const uint64_t a0 = sdesc(st, 128, 256);   // part 0; part p is + p * kTcPartBytes / 16
+    auto dp = [&](int part) { return a0 + (uint64_t)(part * (kTcPartBytes >> 4)); };
+    mma_tf32(d, dp(0), dp(5), acc);   // A_re hi x [B_re hi; -B_im hi]
+    mma_tf32(d, dp(0), dp(8), 1u);    // A_re hi x [B_re lo; -B_im lo]
+    mma_tf32(d, dp(1), dp(5), 1u);    // A_re lo x [B_re hi; -B_im hi]
+    mma_tf32(d, dp(2), dp(4), 1u);    // A_im hi x [B_im hi;  B_re hi]
+    mma_tf32(d, dp(2), dp(7), 1u);    // A_im hi x [B_im lo;  B_re lo]
+    mma_tf32(d, dp(3), dp(4), 1u);    // A_im lo x [B_im hi;  B_re hi]
 }
 
 __device__ __forceinline__ void load_rows(const float2* __restrict__ Psi, int64_t D, int64_t K, int64_t r0, int64_t k0,
@@ -323,29 +352,12 @@ __device__ __forceinline__ bool tc_chunk(int c, int nchunks, unsigned char* stag
     if (c >= 2) bad = !mbar_wait(su32(&bars[s]), (uint32_t)(((c >> 1) - 1) & 1));   // MMAs of chunk c-2 done
     if (__syncthreads_or(bad)) return false;
     put_row4(st, row, half, a0, a1, false);                    // parts 0-3: A re/im hi/lo
-    put_row4(st + 4 * kTcPartBytes, row, half, b0, b1, true);  // parts 4-9: B re/im, -im
+    put_row4(st + 4 * kTcPartBytes, row, half, b0, b1, true);  // parts 4-9: B im, re, -im
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t b = su32(st);
-        auto d = [&](int part) { return sdesc(b + part * kTcPartBytes, 128, 256); };
-        const uint32_t dr = tmem, di = tmem + kTcTile;
-        const uint32_t acc = c > 0 ? 1u : 0u;
-        // Re: A_re B_re + A_im B_im
-        mma_tf32(dr, d(0), d(4), acc);
-        mma_tf32(dr, d(0), d(5), 1u);
-        mma_tf32(dr, d(1), d(4), 1u);
-        mma_tf32(dr, d(2), d(6), 1u);
-        mma_tf32(dr, d(2), d(7), 1u);
-        mma_tf32(dr, d(3), d(6), 1u);
-        // Im: A_im B_re + A_re (-B_im)
-        mma_tf32(di, d(2), d(4), acc);
-        mma_tf32(di, d(2), d(5), 1u);
-        mma_tf32(di, d(3), d(4), 1u);
-        mma_tf32(di, d(0), d(8), 1u);
-        mma_tf32(di, d(0), d(9), 1u);
-        mma_tf32(di, d(1), d(8), 1u);
+        issue_chunk(tmem, su32(st), c > 0 ? 1u : 0u);
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&bars[s]))
                      : "memory");
     }
@@ -529,6 +541,296 @@ __global__ void __launch_bounds__(kTcThreads, 2) herk_tc_kernel(const float2* __
 
 constexpr size_t kTcSmem = 2 * (size_t)kTcStageBytes + 64;
 
+// ---- persistent warp-specialised tensor-core path -------------------------------------------
+//
+// The arithmetic of herk_tc_kernel (TF32 hi/lo planes, 12 MMAs per 8-complex chunk into Re/Im
+// accumulators), organised so that operand loads, tensor-core work and output stores overlap.
+// One CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ... with three roles:
+//   * 8 producer warps: half an A row and half a B row (4 complex each) per thread, loaded
+//     kWsAhead chunks ahead into registers, split into the TF32 planes of a shared-memory stage
+//     (kWsStages stages) and announced on the stage's "full" mbarrier;
+//   * 1 MMA warp: one thread waits for a full stage, issues its 12 MMAs into one of two TMEM
+//     accumulator sets (tiles alternate between them), commits them to the stage's "empty"
+//     mbarrier, and after a tile's last chunk commits to the set's "ready" mbarrier;
+//   * 4 epilogue warps (TMEM lane quadrants 0-3, one tile row per thread): wait for a ready set,
+//     read it 16 columns at a time, hand it back ("freed" mbarrier) after the last read, and
+//     stage the values as 128-byte-swizzled boxes for TMA tensor stores (two staging buffers),
+//     as herk_tc_kernel does; diagonal tiles are written from registers (upper triangle, its
+//     conjugate mirror, real diagonal) so the output stays exactly Hermitian.
+// Every wait is bounded (kTcWaitNs): a role that gives up raises the abort flag and the error
+// word, the others stop at their next wait, and all threads meet at the end, after the MMA
+// thread has waited for its last MMAs, to release tensor memory.
+constexpr int kWsStages = 3;
+constexpr int kWsAhead = 3;                        // chunks in flight per producer thread
+constexpr int kWsProd = 256;                       // producer threads (warps 4-11)
+constexpr int kWsMmaWarp = 12;
+constexpr int kWsThreads = 13 * 32;                // warps 0-3 epilogue, 4-11 producers, 12 MMA
+constexpr int kWsEpiBytes = 32768;                 // one staging buffer: rows box + 8 mirror boxes
+constexpr int kWsTmemCols = 2 * kTcTmemCols;       // two accumulator sets
+constexpr size_t kWsBarOff = (size_t)kWsStages * kTcStageBytes + 2 * kWsEpiBytes;
+constexpr size_t kWsSmem = kWsBarOff + 256;
+
+struct WsBars {
+    uint64_t full[kWsStages], empty[kWsStages], ready[2], freed[2], done;
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+
+// One potentially blocking test of an mbarrier phase: the hardware suspends the thread until
+// the phase completes or a short system time limit passes.
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the given phase of an mbarrier; false when another role aborted or after kTcWaitNs
+// (then this thread raises the abort flag).
+__device__ __forceinline__ bool ws_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (!mbar_try(bar, parity)) {
+        if (*abort) return false;
+        if (gtimer() - t0 > kTcWaitNs) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// OR of `v` over the 128 epilogue threads (named barrier 1): they leave their loop together,
+// so none is left waiting at a barrier the others no longer reach.
+__device__ __forceinline__ bool epi_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(kWsThreads, 1) herk_ws_kernel(const float2* __restrict__ Psi, int64_t D, int64_t K,
+                                                                int64_t tiles, float2* __restrict__ rho,
+                                                                int32_t* __restrict__ err,
+                                                                const __grid_constant__ CUtensorMap tm_rows,
+                                                                const __grid_constant__ CUtensorMap tm_mirror) {
+    extern __shared__ __align__(1024) unsigned char ws_smem[];
+    unsigned char* stage0 = ws_smem;
+    unsigned char* epi0 = ws_smem + (size_t)kWsStages * kTcStageBytes;
+    WsBars* B = reinterpret_cast<WsBars*>(ws_smem + kWsBarOff);
+    volatile int* abort = &B->abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nch = (int)(K / kTcChunk);                       // chunks per tile
+    const int64_t nloc = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;   // this CTA's tiles
+    const int64_t G = nloc * nch;                              // this CTA's chunks
+
+    if (tid == 0) {
+        for (int s = 0; s < kWsStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&B->full[s])), "r"(kWsProd) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&B->empty[s])) : "memory");
+        }
+        for (int a = 0; a < 2; ++a) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&B->ready[a])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(su32(&B->freed[a])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&B->done)) : "memory");
+        B->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kWsMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&B->tmem)),
+                     "r"(kWsTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = B->tmem;
+
+    if (warp >= 4 && warp < kWsMmaWarp) {
+        // ---- producers: k half `half` of row `row` of A (tile rows i0..) and of B (rows j0..) ----
+        const int pt = tid - 128, row = pt >> 1, half = pt & 1;
+        float4 pa[kWsAhead][2], pb[kWsAhead][2];
+        // chunks are fetched in order: the next one is chunk f_c of this CTA's tile f_lt, whose
+        // block coordinates are (f_bi, f_bj)
+        int64_t f_lt = 0;
+        int f_c = 0, f_bi = 0, f_bj = 0;
+        if (nloc > 0) tri_tile((uint32_t)blockIdx.x, f_bi, f_bj);
+        auto fetch = [&](float4 (&a)[2], float4 (&b)[2]) {
+            const int bi = f_bi, bj = f_bj;
+            const int64_t k = (int64_t)f_c * kTcChunk + 4 * half;
+            const float4* sa = reinterpret_cast<const float4*>(Psi + ((int64_t)bi * kTcTile + row) * K + k);
+            const float4* sb = reinterpret_cast<const float4*>(Psi + ((int64_t)bj * kTcTile + row) * K + k);
+            a[0] = sa[0];
+            a[1] = sa[1];
+            b[0] = sb[0];
+            b[1] = sb[1];
+            if (++f_c == nch) {
+                f_c = 0;
+                if (++f_lt < nloc) tri_tile((uint32_t)(blockIdx.x + f_lt * gridDim.x), f_bi, f_bj);
+            }
+        };
+        auto put = [&](int64_t g, const float4 (&a)[2], const float4 (&b)[2]) -> bool {
+            const int s = (int)(g % kWsStages);
+            const uint32_t ph = (uint32_t)((g / kWsStages) & 1);
+            if (!ws_wait(su32(&B->empty[s]), ph ^ 1u, abort)) return false;   // its last MMAs are done
+            unsigned char* st = stage0 + (size_t)s * kTcStageBytes;
+            put_row4(st, row, half, a[0], a[1], false);
+            put_row4(st + 4 * kTcPartBytes, row, half, b[0], b[1], true);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(su32(&B->full[s]));
+            return true;
+        };
+#pragma unroll
+        for (int e = 0; e < kWsAhead; ++e)
+            if (e < G) fetch(pa[e], pb[e]);
+        bool ok = true;
+        for (int64_t g0 = 0; g0 < G && ok; g0 += kWsAhead) {
+#pragma unroll
+            for (int e = 0; e < kWsAhead; ++e) {
+                const int64_t g = g0 + e;
+                if (g >= G) break;
+                if (!put(g, pa[e], pb[e])) {
+                    ok = false;
+                    break;
+                }
+                if (g + kWsAhead < G) fetch(pa[e], pb[e]);
+            }
+        }
+    } else if (warp == kWsMmaWarp) {
+        // ---- MMA issue: one thread ----
+        if (lane == 0) {
+            for (int64_t lt = 0; lt < nloc; ++lt) {
+                const int a = (int)(lt & 1);
+                if (!ws_wait(su32(&B->freed[a]), (uint32_t)(((lt >> 1) & 1) ^ 1), abort)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dr = tmem + (uint32_t)(a * kTcTmemCols);
+                bool ok = true;
+                for (int c = 0; c < nch; ++c) {
+                    const int64_t g = lt * nch + c;
+                    const int s = (int)(g % kWsStages);
+                    if (!ws_wait(su32(&B->full[s]), (uint32_t)((g / kWsStages) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    issue_chunk(dr, su32(stage0 + (size_t)s * kTcStageBytes), c > 0 ? 1u : 0u);
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     su32(&B->empty[s]))
+                                 : "memory");
+                }
+                if (!ok) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 su32(&B->ready[a]))
+                             : "memory");
+            }
+            // every MMA issued so far has completed once this commit arrives
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(&B->done))
+                         : "memory");
+            const uint64_t t0 = gtimer();
+            while (!mbar_done(su32(&B->done), 0u) && gtimer() - t0 <= kTcWaitNs) __nanosleep(32);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32w.., this thread's tile row r ----
+        const int r = tid;
+        const int ci = r & 15;
+        const uint64_t mr = reinterpret_cast<uint64_t>(&tm_rows);
+        const uint64_t mm = reinterpret_cast<uint64_t>(&tm_mirror);
+        int64_t q = 0;   // staging steps issued (buffer q & 1)
+        for (int64_t lt = 0; lt < nloc; ++lt) {
+            const int a = (int)(lt & 1);
+            const bool ok = ws_wait(su32(&B->ready[a]), (uint32_t)((lt >> 1) & 1), abort);
+            if (epi_any(!ok)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int bi, bj;
+            tri_tile((uint32_t)(blockIdx.x + lt * gridDim.x), bi, bj);
+            const int64_t i0 = (int64_t)bi * kTcTile, j0 = (int64_t)bj * kTcTile;
+            const uint32_t tr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * kTcTmemCols);
+            for (int st = 0; st < kTcTile / 16; ++st) {
+                float vr[16], vi[16];
+                if (bi != bj) {
+                    unsigned char* buf = epi0 + (q & 1) * kWsEpiBytes;
+                    if (r == 0 && q >= 2) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    asm volatile("bar.sync 1, 128;" ::: "memory");   // this buffer's previous stores have read it
+                    tmem_ld16(tr + (uint32_t)(16 * st), vr);
+                    tmem_ld16(tr + (uint32_t)(kTcTile + 16 * st), vi);
+                    if (st == kTcTile / 16 - 1) {   // the accumulator set is free for the tile after next
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        mbar_arrive(su32(&B->freed[a]));
+                    }
+                    // rows box: row r, 16-byte chunk c (two complex) at chunk c ^ (r & 7)
+                    unsigned char* rb = buf + r * 128;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        *reinterpret_cast<float4*>(rb + ((c ^ (r & 7)) << 4)) =
+                            make_float4(vr[2 * c], vi[2 * c], vr[2 * c + 1], vi[2 * c + 1]);
+                    // mirror boxes: box r / 16 (16 rows x 128 B), row e, complex r % 16
+                    unsigned char* mb = buf + 16384 + (r >> 4) * 2048;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        *reinterpret_cast<float2*>(mb + e * 128 + ((((ci >> 1) ^ (e & 7))) << 4) + ((ci & 1) << 3)) =
+                            make_float2(vr[e], -vi[e]);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    if (r == 0) {
+                        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(mr),
+                                     "r"((int)(2 * (j0 + 16 * st))), "r"((int)i0), "r"(su32(buf))
+                                     : "memory");
+                        for (int bx = 0; bx < 8; ++bx)
+                            asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(mm),
+                                         "r"((int)(2 * (i0 + 16 * bx))), "r"((int)(j0 + 16 * st)),
+                                         "r"(su32(buf + 16384 + bx * 2048))
+                                         : "memory");
+                        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    }
+                    ++q;
+                } else {
+                    // diagonal tile: entries (i, j) with j >= i from registers, their mirrors, a
+                    // real diagonal
+                    tmem_ld16(tr + (uint32_t)(16 * st), vr);
+                    tmem_ld16(tr + (uint32_t)(kTcTile + 16 * st), vi);
+                    if (st == kTcTile / 16 - 1) {
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        mbar_arrive(su32(&B->freed[a]));
+                    }
+                    const int64_t i = i0 + r;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int cj = 16 * st + e;
+                        const int64_t j = j0 + cj;
+                        if (cj > r) {
+                            rho[i * D + j] = make_float2(vr[e], vi[e]);
+                            rho[j * D + i] = make_float2(vr[e], -vi[e]);
+                        } else if (cj == r) {
+                            rho[i * D + i] = make_float2(vr[e], 0.f);
+                        }
+                    }
+                }
+            }
+        }
+        if (r == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // stores complete
+    }
+    if (tid == 0 && *abort) atomicExch(err, 3);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && *abort) atomicExch(err, 3);
+    if (warp == kWsMmaWarp)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWsTmemCols) : "memory");
+}
+
 }  // namespace
 
 // Tensor maps of rho (D x D complex64, viewed as float32 [D][2D]) for the TMA epilogue:
@@ -620,7 +922,15 @@ int launch_partial_trace(const void* psi_v, int n, const QubitMap& Q, int m, voi
         std::memset(&tm_rows, 0, sizeof(tm_rows));
         std::memset(&tm_mirror, 0, sizeof(tm_mirror));
         const int use_tma = P.splits == 1 && encode_rho_maps(rho, D, &tm_rows, &tm_mirror) ? 1 : 0;
-        herk_tc_kernel<<<grid, kTcThreads, kTcSmem, st>>>(Psi, D, K, P.kps, dst, err, tm_rows, tm_mirror, use_tma);
+        if (use_tma && n - m >= 3 && P.tiles >= sm_count) {
+            // enough whole tiles for every SM: the persistent warp-specialised kernel
+            e = cudaFuncSetAttribute(herk_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
+            if (e != cudaSuccess) return (int)e;
+            const unsigned g = (unsigned)(P.tiles < sm_count ? P.tiles : sm_count);
+            herk_ws_kernel<<<g, kWsThreads, kWsSmem, st>>>(Psi, D, K, P.tiles, rho, err, tm_rows, tm_mirror);
+        } else {
+            herk_tc_kernel<<<grid, kTcThreads, kTcSmem, st>>>(Psi, D, K, P.kps, dst, err, tm_rows, tm_mirror, use_tma);
+        }
     } else {
         herk_tile_kernel<<<grid, kHerkThreads, 0, st>>>(Psi, D, K, P.kps, dst);
     }

@@ -34,10 +34,13 @@ def _trace_dev(tlq, psi, n, keep):
 
 @pytest.mark.parametrize("n,keep", [(1, [0]), (2, [1]), (3, [0, 2]), (6, [5, 1, 3]), (9, list(range(9))),
                                     (10, [0, 1, 2, 3, 4]), (12, [11, 3, 7, 0, 5, 9, 2]), (14, [2, 4, 6, 8, 10, 12, 13]),
-                                    (16, [0]), (20, [19, 18]), (13, list(range(13)))])
+                                    (16, [0]), (20, [19, 18]), (13, list(range(13))),
+                                    (16, [15, 0, 2, 3, 5, 6, 8, 9, 11, 12, 13, 14]), (15, list(range(3, 15)))])
 def test_partial_trace_random_states(tlq, n, keep):
     # ragged and degenerate shapes: m = n (pure rho), m = 1 with long k (split k range),
-    # scattered kept qubits, outputs smaller than one 64 x 64 tile and spanning many tiles
+    # scattered kept qubits, outputs smaller than one 64 x 64 tile and spanning many tiles;
+    # m = 12 with k = 16 and k = 8 (one chunk per tile) run the persistent warp-specialised
+    # kernel (528 tiles of 128 x 128)
     psi = _random_state(n, seed=n * 31 + len(keep))
     rho = _trace_dev(tlq, psi, n, keep)
     ref = density.reduced_density(psi.astype(np.complex64).astype(np.complex128), n, keep)
