@@ -549,22 +549,24 @@ constexpr size_t kTcSmem = 2 * (size_t)kTcStageBytes + 64;
 //   * 8 producer warps: half an A row and half a B row (4 complex each) per thread, loaded
 //     kWsAhead chunks ahead into registers, split into the TF32 planes of a shared-memory stage
 //     (kWsStages stages) and announced on the stage's "full" mbarrier;
-//   * 1 MMA warp: one thread waits for a full stage, issues its 12 MMAs into one of two TMEM
+//   * 1 MMA warp: one thread waits for a full stage, issues its six MMAs into one of two TMEM
 //     accumulator sets (tiles alternate between them), commits them to the stage's "empty"
 //     mbarrier, and after a tile's last chunk commits to the set's "ready" mbarrier;
-//   * 4 epilogue warps (TMEM lane quadrants 0-3, one tile row per thread): wait for a ready set,
-//     read it 16 columns at a time, hand it back ("freed" mbarrier) after the last read, and
-//     stage the values as 128-byte-swizzled boxes for TMA tensor stores (two staging buffers),
-//     as herk_tc_kernel does; diagonal tiles are written from registers (upper triangle, its
-//     conjugate mirror, real diagonal) so the output stays exactly Hermitian.
+//   * 8 epilogue warps (warp w: TMEM lane quadrant w % 4, i.e. one tile row per thread, and the
+//     8-column half w / 4 of each 16-column step): wait for a ready set, read it, hand it back
+//     ("freed" mbarrier) after the last read, and stage the values as 128-byte-swizzled boxes
+//     for TMA tensor stores (two staging buffers), as herk_tc_kernel does; diagonal tiles are
+//     written from registers (upper triangle, its conjugate mirror, real diagonal) so the output
+//     stays exactly Hermitian.
 // Every wait is bounded (kTcWaitNs): a role that gives up raises the abort flag and the error
 // word, the others stop at their next wait, and all threads meet at the end, after the MMA
 // thread has waited for its last MMAs, to release tensor memory.
 constexpr int kWsStages = 3;
 constexpr int kWsAhead = 3;                        // chunks in flight per producer thread
-constexpr int kWsProd = 256;                       // producer threads (warps 4-11)
-constexpr int kWsMmaWarp = 12;
-constexpr int kWsThreads = 13 * 32;                // warps 0-3 epilogue, 4-11 producers, 12 MMA
+constexpr int kWsEpi = 256;                        // epilogue threads (warps 0-7)
+constexpr int kWsProd = 256;                       // producer threads (warps 8-15)
+constexpr int kWsMmaWarp = 16;
+constexpr int kWsThreads = 17 * 32;
 constexpr int kWsEpiBytes = 32768;                 // one staging buffer: rows box + 8 mirror boxes
 constexpr int kWsTmemCols = 2 * kTcTmemCols;       // two accumulator sets
 constexpr size_t kWsBarOff = (size_t)kWsStages * kTcStageBytes + 2 * kWsEpiBytes;
@@ -612,7 +614,7 @@ __device__ __forceinline__ bool ws_wait(uint32_t bar, uint32_t parity, volatile 
 __device__ __forceinline__ bool epi_any(bool v) {
     uint32_t r;
     asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.or.pred q, 1, 256, p;\n selp.u32 %0, 1, 0, q;\n}\n"
         : "=r"(r)
         : "r"((uint32_t)v)
         : "memory");
@@ -641,7 +643,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) herk_ws_kernel(const float2* __
         }
         for (int a = 0; a < 2; ++a) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&B->ready[a])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(su32(&B->freed[a])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&B->freed[a])), "r"(kWsEpi) : "memory");
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&B->done)) : "memory");
         B->abort = 0;
@@ -658,9 +660,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) herk_ws_kernel(const float2* __
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = B->tmem;
 
-    if (warp >= 4 && warp < kWsMmaWarp) {
+    if (warp >= kWsEpi / 32 && warp < kWsMmaWarp) {
         // ---- producers: k half `half` of row `row` of A (tile rows i0..) and of B (rows j0..) ----
-        const int pt = tid - 128, row = pt >> 1, half = pt & 1;
+        const int pt = tid - kWsEpi, row = pt >> 1, half = pt & 1;
         float4 pa[kWsAhead][2], pb[kWsAhead][2];
         // chunks are fetched in order: the next one is chunk f_c of this CTA's tile f_lt, whose
         // block coordinates are (f_bi, f_bj)
@@ -744,8 +746,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) herk_ws_kernel(const float2* __
         }
         __syncwarp();
     } else {
-        // ---- epilogue: warp w reads TMEM lanes 32w.., this thread's tile row r ----
-        const int r = tid;
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4).. (its thread's tile row r) and the
+        // 8-column half w / 4 of each 16-column step ----
+        const int q4 = warp & 3, hh = warp >> 2;
+        const int r = 32 * q4 + lane;
         const int ci = r & 15;
         const uint64_t mr = reinterpret_cast<uint64_t>(&tm_rows);
         const uint64_t mm = reinterpret_cast<uint64_t>(&tm_mirror);
@@ -758,34 +762,40 @@ __global__ void __launch_bounds__(kWsThreads, 1) herk_ws_kernel(const float2* __
             int bi, bj;
             tri_tile((uint32_t)(blockIdx.x + lt * gridDim.x), bi, bj);
             const int64_t i0 = (int64_t)bi * kTcTile, j0 = (int64_t)bj * kTcTile;
-            const uint32_t tr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * kTcTmemCols);
+            const uint32_t tr = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(a * kTcTmemCols);
             for (int st = 0; st < kTcTile / 16; ++st) {
-                float vr[16], vi[16];
+                const int col = 16 * st + 8 * hh;   // tile column of this thread's 8 values
+                float vr[8], vi[8];
                 if (bi != bj) {
                     unsigned char* buf = epi0 + (q & 1) * kWsEpiBytes;
-                    if (r == 0 && q >= 2) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-                    asm volatile("bar.sync 1, 128;" ::: "memory");   // this buffer's previous stores have read it
-                    tmem_ld16(tr + (uint32_t)(16 * st), vr);
-                    tmem_ld16(tr + (uint32_t)(kTcTile + 16 * st), vi);
+                    if (tid == 0 && q >= 2) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    asm volatile("bar.sync 1, 256;" ::: "memory");   // this buffer's previous stores have read it
+                    tmem_ld8(tr + (uint32_t)col, vr);
+                    tmem_ld8(tr + (uint32_t)(kTcTile + col), vi);
                     if (st == kTcTile / 16 - 1) {   // the accumulator set is free for the tile after next
                         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                         mbar_arrive(su32(&B->freed[a]));
                     }
-                    // rows box: row r, 16-byte chunk c (two complex) at chunk c ^ (r & 7)
+                    // rows box: row r, 16-byte chunk cc (two complex) at chunk cc ^ (r & 7); this
+                    // thread has chunks 4 hh .. 4 hh + 3
                     unsigned char* rb = buf + r * 128;
 #pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        *reinterpret_cast<float4*>(rb + ((c ^ (r & 7)) << 4)) =
+                    for (int c = 0; c < 4; ++c) {
+                        const int cc = 4 * hh + c;
+                        *reinterpret_cast<float4*>(rb + ((cc ^ (r & 7)) << 4)) =
                             make_float4(vr[2 * c], vi[2 * c], vr[2 * c + 1], vi[2 * c + 1]);
-                    // mirror boxes: box r / 16 (16 rows x 128 B), row e, complex r % 16
+                    }
+                    // mirror boxes: box r / 16 (16 rows x 128 B), row jl = 8 hh + e, complex r % 16
                     unsigned char* mb = buf + 16384 + (r >> 4) * 2048;
 #pragma unroll
-                    for (int e = 0; e < 16; ++e)
-                        *reinterpret_cast<float2*>(mb + e * 128 + ((((ci >> 1) ^ (e & 7))) << 4) + ((ci & 1) << 3)) =
+                    for (int e = 0; e < 8; ++e) {
+                        const int jl = 8 * hh + e;
+                        *reinterpret_cast<float2*>(mb + jl * 128 + ((((ci >> 1) ^ (jl & 7))) << 4) + ((ci & 1) << 3)) =
                             make_float2(vr[e], -vi[e]);
+                    }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
-                    if (r == 0) {
+                    asm volatile("bar.sync 1, 256;" ::: "memory");
+                    if (tid == 0) {
                         asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(mr),
                                      "r"((int)(2 * (j0 + 16 * st))), "r"((int)i0), "r"(su32(buf))
                                      : "memory");
@@ -800,16 +810,16 @@ __global__ void __launch_bounds__(kWsThreads, 1) herk_ws_kernel(const float2* __
                 } else {
                     // diagonal tile: entries (i, j) with j >= i from registers, their mirrors, a
                     // real diagonal
-                    tmem_ld16(tr + (uint32_t)(16 * st), vr);
-                    tmem_ld16(tr + (uint32_t)(kTcTile + 16 * st), vi);
+                    tmem_ld8(tr + (uint32_t)col, vr);
+                    tmem_ld8(tr + (uint32_t)(kTcTile + col), vi);
                     if (st == kTcTile / 16 - 1) {
                         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                         mbar_arrive(su32(&B->freed[a]));
                     }
                     const int64_t i = i0 + r;
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int cj = 16 * st + e;
+                    for (int e = 0; e < 8; ++e) {
+                        const int cj = col + e;
                         const int64_t j = j0 + cj;
                         if (cj > r) {
                             rho[i * D + j] = make_float2(vr[e], vi[e]);
@@ -821,7 +831,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) herk_ws_kernel(const float2* __
                 }
             }
         }
-        if (r == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // stores complete
+        if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // stores complete
     }
     if (tid == 0 && *abort) atomicExch(err, 3);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
