@@ -496,9 +496,10 @@ def partial_trace_workloads(B, dev, local, flush, peaks, n=20, ms=(14, 10), step
             hbm_bytes = 8 * D * D + 3 * 8 * 2 ** n     # rho written; psi read, Psi written and read
             hbm_peak = float(peaks["hbm_gbs"])
             if m >= 7:
-                # tensor cores: per 128 x 128 upper tile and 8 complex k, 12 TF32 MMAs of 128 x 128 x 8
+                # tensor cores: per 128 x 128 upper tile and 8 complex k, six TF32 MMAs of 128 x 256 x 8
                 T = (D + 127) // 128
-                tc_flops = T * (T + 1) // 2 * (K / 8) * 12 * 2 * 128 * 128 * 8
+                tc_flops = T * (T + 1) // 2 * (K / 8) * 6 * 2 * 128 * 256 * 8
+                ws = T * (T + 1) // 2 >= torch.cuda.get_device_properties(0).multi_processor_count and n - m >= 3
                 tf32_peak = float(peaks["bf16_tflops"]) * 1.1 / 2.25   # nominal TF32 / BF16 dense ratio
                 hbm_floor, tc_floor = hbm_bytes / (hbm_peak * 1e9), tc_flops / (tf32_peak * 1e12)
                 if hbm_floor >= tc_floor:
@@ -508,7 +509,8 @@ def partial_trace_workloads(B, dev, local, flush, peaks, n=20, ms=(14, 10), step
                     roof = {"bound": "tensor", "achieved": tc_flops / (kms * 1e-3) / 1e12, "peak": tf32_peak,
                             "unit": "TFLOP/s", "frac": tc_flops / (kms * 1e-3) / 1e12 / tf32_peak,
                             "peak_basis": "measured bf16 dense x 1.1/2.25 (nominal TF32/BF16)"}
-                roof.update({"kernel": "herk_tc_kernel (tcgen05 kind::tf32, TMEM accumulators)",
+                roof.update({"kernel": ("herk_ws_kernel (persistent, warp-specialised" if ws else
+                                        "herk_tc_kernel (split k") + "; tcgen05 kind::tf32, TMEM accumulators)",
                              "tensor_tflops_executed": tc_flops / (kms * 1e-3) / 1e12,
                              "hbm_gbs": hbm_bytes / (kms * 1e-3) / 1e9})
             else:
