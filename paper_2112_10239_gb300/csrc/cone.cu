@@ -111,6 +111,24 @@ __device__ __forceinline__ real team_warp_sum(real v, const Team& tm) {
     return v;
 }
 
+// Warp sums of four values at once (a transposing reduction: 6 shuffles instead of 4 x 5).
+// Lane l receives the sum over the warp of value (l >> 3) & 3.
+template <typename real>
+__device__ __forceinline__ real warp_sum4(real a0, real a1, real a2, real a3, int lane) {
+    const bool u = (lane & 16) != 0;
+    real k0 = u ? a2 : a0, k1 = u ? a3 : a1;   // kept: values 2u and 2u + 1
+    const real s0 = u ? a0 : a2, s1 = u ? a1 : a3;
+    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+    const bool v = (lane & 8) != 0;
+    real k = v ? k1 : k0;                      // value 2u + v
+    k += __shfl_xor_sync(0xffffffffu, v ? k0 : k1, 8);
+    k += __shfl_xor_sync(0xffffffffu, k, 4);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    return k;
+}
+
 // Diagonal phase of window index x: the product of the chunk-table entries.
 template <typename T2>
 __device__ __forceinline__ T2 phase_of(const T2* tab, int tab1, int tab2, int W, int x) {
@@ -420,14 +438,25 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, const Team& tm, co
                 store16(p, pp, stride);
                 store16(l, lp, stride);
             }
-            const real gk[4] = {g0, g1, g2, g3};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (kd[k] < 0) continue;
-                const real val = team_warp_sum(gk[k], tm);
-                if (leader) {
+            if (tm.tt >= 32) {
+                const int lane = tm.tid & 31;
+                const real val = warp_sum4(g0, g1, g2, g3, lane);   // value k = (lane >> 3) & 3
+                const int k = (lane >> 3) & 3;
+                const int kdk = k == 0 ? kd[0] : k == 1 ? kd[1] : k == 2 ? kd[2] : kd[3];
+                if ((lane & 7) == 0 && kdk >= 0) {
                     real* dst = red + k * nw + warp;
                     *dst = first ? val : *dst + val;
+                }
+            } else {
+                const real gk[4] = {g0, g1, g2, g3};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (kd[k] < 0) continue;
+                    const real val = team_warp_sum(gk[k], tm);
+                    if (leader) {
+                        real* dst = red + k * nw + warp;
+                        *dst = first ? val : *dst + val;
+                    }
                 }
             }
         } else {
