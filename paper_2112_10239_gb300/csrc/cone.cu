@@ -19,7 +19,7 @@
 //                           optionally multiplies by the layer's diagonal phase, and
 //                           stores them back. The adjoint walks the layers backwards with
 //                           psi and lambda = P psi, emitting Im<lambda|G|psi> per gate.
-//   energy_reduce / grad_reduce (K5) fixed-order Neumaier sums over terms in FP64, so a
+//   reduce_kernel      (K5) energies and gradients in one launch: fixed-order Neumaier sums in FP64, so a
 //                           result does not depend on batching or scheduling.
 #include "internal.h"
 
@@ -885,29 +885,52 @@ struct Neumaier {
 // E_b = sum_t c_t e_{t,b}: one warp per set; lane l sums the terms t = l, l + 32, ... with a
 // compensated sum (coalesced reads), then lane 0 adds the 32 partials in lane order. The
 // order is fixed, so the result does not depend on the launch.
-__global__ void energy_reduce_kernel(const double* e_part, const double* coeff, int T, int B, double* energy) {
-    const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (b >= B) return;
+__device__ __forceinline__ void energy_warp(const double* e, const double* coeff, int T, int lane, double* out) {
     Neumaier acc;
-    for (int t = lane; t < T; t += 32) acc.add(coeff[t] * e_part[(size_t)b * T + t]);
-    double mine = acc.value();
+    for (int t = lane; t < T; t += 32) acc.add(coeff[t] * e[t]);
+    const double mine = acc.value();
     Neumaier tot;
     for (int l = 0; l < 32; ++l) {
         const double v = __shfl_sync(0xffffffffu, mine, l);
         if (lane == 0) tot.add(v);
     }
-    if (lane == 0) energy[b] = tot.value();
+    if (lane == 0) *out = tot.value();
 }
 
-__global__ void grad_reduce_kernel(const double* g_part, const int32_t* off, const int32_t* idx, const int32_t* term,
-                                   const double* coeff, int P, int S, int B, double* grad) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// g_p = sum over the slots k of parameter p of c_term(k) g_slot(k), compensated, in slot order;
+// the slots are loaded eight at a time before they are added, so their latencies overlap.
+__device__ __forceinline__ double grad_slots(const double* g, const int32_t* idx, const int32_t* term,
+                                             const double* coeff, int k0, int k1) {
+    Neumaier acc;
+    for (int k = k0; k < k1; k += 8) {
+        double v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            if (k + e < k1) {
+                const int t = term[k + e];
+                v[e] = (t >= 0 ? coeff[t] : 1.0) * g[idx[k + e]];
+            }
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            if (k + e < k1) acc.add(v[e]);
+    }
+    return acc.value();
+}
+
+// Energies and gradients of a launch in one kernel: blocks [0, eb) hold one warp per set for
+// the energies, the others one thread per (set, parameter) for the gradients (P = 0: none).
+__global__ void reduce_kernel(const double* e_part, const double* coeff, int T, int B, double* energy, int eb,
+                              const double* g_part, const int32_t* off, const int32_t* idx, const int32_t* term,
+                              int P, int S, double* grad) {
+    if ((int)blockIdx.x < eb) {
+        const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+        if (b < B) energy_warp(e_part + (size_t)b * T, coeff, T, threadIdx.x & 31, energy + b);
+        return;
+    }
+    const long long i = (long long)(blockIdx.x - eb) * blockDim.x + threadIdx.x;
     if (i >= (long long)B * P) return;
     const int b = (int)(i / P), p = (int)(i % P);
-    Neumaier acc;
-    for (int k = off[p]; k < off[p + 1]; ++k) acc.add((term[k] >= 0 ? coeff[term[k]] : 1.0) * g_part[(size_t)b * S + idx[k]]);
-    grad[i] = acc.value();
+    grad[i] = grad_slots(g_part + (size_t)b * S, idx, term, coeff, off[p], off[p + 1]);
 }
 
 // ---- launchers -----------------------------------------------------------------------------
@@ -982,7 +1005,7 @@ int launch_cone(ConeLaunch& L, void* stream) {
         if (grad && (e = cudaMemsetAsync(L.g_part, 0, (size_t)L.B * L.n_slots * sizeof(double), st)) != cudaSuccess)
             return (int)e;
     }
-    L.launches = 1 + (L.n_chunks_smem > 0) + (L.n_chunks > L.n_chunks_smem) + 1 + (grad ? 1 : 0);
+    L.launches = 1 + (L.n_chunks_smem > 0) + (L.n_chunks > L.n_chunks_smem) + 1;
     const int smem_grid = cone_smem_grid(L.fp64, grad, L.smem_bytes, L.sm_count, L.smem_threads);
     if (L.ev_begin && (e = cudaEventRecord((cudaEvent_t)L.ev_begin, st)) != cudaSuccess) return (int)e;
     int rc;
@@ -1001,12 +1024,13 @@ int launch_cone(ConeLaunch& L, void* stream) {
     }
     if (rc) return rc;
     if (L.ev_end && (e = cudaEventRecord((cudaEvent_t)L.ev_end, st)) != cudaSuccess) return (int)e;
-    energy_reduce_kernel<<<(L.B + 3) / 4, 128, 0, st>>>(L.e_part, L.term_coeff, L.n_terms, L.B, L.energy);
-    if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
-    if (grad) {
-        const long long n = (long long)L.B * L.n_params;
-        grad_reduce_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(L.g_part, L.pmap_off, L.pmap_idx, L.pmap_term, L.term_coeff,
-                                                                   L.n_params, L.n_slots, L.B, L.grad);
+    {
+        const int eb = (L.B + 7) / 8;   // 8 warps per block
+        const int P = grad ? L.n_params : 0;
+        const long long n = (long long)L.B * P;
+        const int gb = (int)((n + 255) / 256);
+        reduce_kernel<<<eb + gb, 256, 0, st>>>(L.e_part, L.term_coeff, L.n_terms, L.B, L.energy, eb, L.g_part,
+                                               L.pmap_off, L.pmap_idx, L.pmap_term, P, L.n_slots, L.grad);
         if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     }
     return 0;
@@ -1029,32 +1053,26 @@ __global__ void batch_gate_table_kernel(const SetRec* sets, typename R2<real>::T
     out[R.gt_off + g] = v;
 }
 
-// Same summation order as energy_reduce_kernel (warp per set, lanes over terms, partials in
-// lane order), so a set's energy is bit-identical served or computed synchronously.
-__global__ void batch_energy_kernel(const SetRec* sets, int n_sets, const double* e_part) {
-    const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
+// The serving batch's energies and gradients in one kernel, in the summation orders of
+// reduce_kernel, so a set's results are bit-identical served or computed synchronously:
+// blocks [0, eb) hold one warp per set, the others cover (set, parameter) pairs, gx blocks of
+// 256 parameters per set.
+__global__ void batch_reduce_kernel(const SetRec* sets, int n_sets, const double* e_part, const double* g_part,
+                                    int eb, int gx) {
+    if ((int)blockIdx.x < eb) {
+        const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+        if (b >= n_sets) return;
+        const SetRec& R = sets[b];
+        energy_warp(e_part + R.e_off, R.term_coeff, R.n_terms, threadIdx.x & 31, R.energy);
+        return;
+    }
+    const int q = (int)blockIdx.x - eb;
+    const int b = q / gx;
     if (b >= n_sets) return;
     const SetRec& R = sets[b];
-    Neumaier acc;
-    for (int t = lane; t < R.n_terms; t += 32) acc.add(R.term_coeff[t] * e_part[R.e_off + t]);
-    const double mine = acc.value();
-    Neumaier tot;
-    for (int l = 0; l < 32; ++l) {
-        const double v = __shfl_sync(0xffffffffu, mine, l);
-        if (lane == 0) tot.add(v);
-    }
-    if (lane == 0) *R.energy = tot.value();
-}
-
-__global__ void batch_grad_kernel(const SetRec* sets, const double* g_part) {
-    const SetRec& R = sets[blockIdx.y];
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = (q - b * gx) * blockDim.x + threadIdx.x;
     if (!R.grad || p >= R.n_params) return;
-    Neumaier acc;
-    for (int k = R.pmap_off[p]; k < R.pmap_off[p + 1]; ++k)
-        acc.add((R.pmap_term[k] >= 0 ? R.term_coeff[R.pmap_term[k]] : 1.0) * g_part[R.g_off + R.pmap_idx[k]]);
-    R.grad[p] = acc.value();
+    R.grad[p] = grad_slots(g_part + R.g_off, R.pmap_idx, R.pmap_term, R.term_coeff, R.pmap_off[p], R.pmap_off[p + 1]);
 }
 
 template <typename real, bool GRAD, bool GLOBAL>
@@ -1123,13 +1141,11 @@ int launch_cone_batch(BatchLaunch& L, void* stream) {
     }
     const int rc = L.fp64 ? launch_batch_all<double>(L, st) : launch_batch_all<float>(L, st);
     if (rc) return rc;
-    batch_energy_kernel<<<(L.n_sets + 3) / 4, 128, 0, st>>>(L.sets, L.n_sets, L.e_part);
-    if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
-    if (L.max_params > 0 && L.range[4] > L.range[2]) {
-        const dim3 gg((L.max_params + 255) / 256, L.n_sets);
-        batch_grad_kernel<<<gg, 256, 0, st>>>(L.sets, L.g_part);
+    {
+        const int eb = (L.n_sets + 7) / 8;   // 8 warps per block
+        const int gx = (L.max_params > 0 && L.range[4] > L.range[2]) ? (L.max_params + 255) / 256 : 0;
+        batch_reduce_kernel<<<eb + gx * L.n_sets, 256, 0, st>>>(L.sets, L.n_sets, L.e_part, L.g_part, eb, gx);
         if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
-        ++L.launches;
     }
     L.launches += 2;
     return 0;
