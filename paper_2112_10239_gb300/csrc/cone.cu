@@ -853,10 +853,17 @@ cone_kernel(ConeArgs A) {
 
 // ---- K0: gate tables ---------------------------------------------------------------------
 
+// The same launch zeroes the cone kernel's work counters and, when window branches add into
+// them, the partial energies and gradient slots (z0[0..n0), z1[0..n1)).
 template <typename real>
 __global__ void gate_table_kernel(const tlq_gate* gates, int n_gates, const double* theta, int n_params, int B,
-                                  typename R2<real>::T* out) {
+                                  typename R2<real>::T* out, int32_t* counters, double* z0, long long n0, double* z1,
+                                  long long n1) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    if (i < 2) counters[i] = 0;
+    for (long long k = i; k < n0; k += nth) z0[k] = 0.0;
+    for (long long k = i; k < n1; k += nth) z1[k] = 0.0;
     if (i >= (long long)B * n_gates) return;
     const int b = (int)(i / n_gates), g = (int)(i % n_gates);
     const tlq_gate G = gates[g];
@@ -990,20 +997,20 @@ int launch_cone(ConeLaunch& L, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     const bool grad = L.grad != nullptr;
     cudaError_t e;
-    // K0
+    // K0 (also zeroes the work counters and, for branch items, the partial sums they add into)
     {
         const long long n = (long long)L.B * L.n_gates;
         const int thr = 256;
-        const int blocks = (int)((n + thr - 1) / thr);
-        if (L.fp64) gate_table_kernel<double><<<blocks, thr, 0, st>>>(L.gates, L.n_gates, L.theta, L.n_params, L.B, (double2*)L.gate_table);
-        else gate_table_kernel<float><<<blocks, thr, 0, st>>>(L.gates, L.n_gates, L.theta, L.n_params, L.B, (float2*)L.gate_table);
+        const int blocks = (int)((n + thr - 1) / thr) > 0 ? (int)((n + thr - 1) / thr) : 1;
+        const long long n0 = L.accum ? (long long)L.B * L.n_terms : 0;
+        const long long n1 = L.accum && grad ? (long long)L.B * L.n_slots : 0;
+        if (L.fp64)
+            gate_table_kernel<double><<<blocks, thr, 0, st>>>(L.gates, L.n_gates, L.theta, L.n_params, L.B,
+                                                              (double2*)L.gate_table, L.counters, L.e_part, n0, L.g_part, n1);
+        else
+            gate_table_kernel<float><<<blocks, thr, 0, st>>>(L.gates, L.n_gates, L.theta, L.n_params, L.B,
+                                                             (float2*)L.gate_table, L.counters, L.e_part, n0, L.g_part, n1);
         if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
-    }
-    if ((e = cudaMemsetAsync(L.counters, 0, 2 * sizeof(int32_t), st)) != cudaSuccess) return (int)e;
-    if (L.accum) {   // branch items add their shares
-        if ((e = cudaMemsetAsync(L.e_part, 0, (size_t)L.B * L.n_terms * sizeof(double), st)) != cudaSuccess) return (int)e;
-        if (grad && (e = cudaMemsetAsync(L.g_part, 0, (size_t)L.B * L.n_slots * sizeof(double), st)) != cudaSuccess)
-            return (int)e;
     }
     L.launches = 1 + (L.n_chunks_smem > 0) + (L.n_chunks > L.n_chunks_smem) + 1;
     const int smem_grid = cone_smem_grid(L.fp64, grad, L.smem_bytes, L.sm_count, L.smem_threads);
@@ -1038,8 +1045,16 @@ int launch_cone(ConeLaunch& L, void* stream) {
 
 // ---- serving batches: per-set records --------------------------------------------------------
 
+// Also zeroes the batch's four work counters and, when window branches add into them, its
+// partial energies and gradient slots (z0[0..n0), z1[0..n1)).
 template <typename real>
-__global__ void batch_gate_table_kernel(const SetRec* sets, typename R2<real>::T* out) {
+__global__ void batch_gate_table_kernel(const SetRec* sets, typename R2<real>::T* out, int32_t* counters, double* z0,
+                                        long long n0, double* z1, long long n1) {
+    const long long t = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+    const long long nth = (long long)gridDim.x * gridDim.y * blockDim.x;
+    if (t < 4) counters[t] = 0;
+    for (long long k = t; k < n0; k += nth) z0[k] = 0.0;
+    for (long long k = t; k < n1; k += nth) z1[k] = 0.0;
     const SetRec& R = sets[blockIdx.y];
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= R.n_gates) return;
@@ -1131,14 +1146,15 @@ int launch_cone_batch(BatchLaunch& L, void* stream) {
     L.launches = 0;
     if (L.n_sets <= 0) return 0;
     const dim3 gk((L.max_gates + 255) / 256 > 0 ? (L.max_gates + 255) / 256 : 1, L.n_sets);
-    if (L.fp64) batch_gate_table_kernel<double><<<gk, 256, 0, st>>>(L.sets, (double2*)L.gate_table);
-    else batch_gate_table_kernel<float><<<gk, 256, 0, st>>>(L.sets, (float2*)L.gate_table);
+    // the gate tables, the work counters and (branch items add their shares) the partial sums
+    const long long n0 = L.accum ? (long long)L.e_count : 0, n1 = L.accum ? (long long)L.g_count : 0;
+    if (L.fp64)
+        batch_gate_table_kernel<double><<<gk, 256, 0, st>>>(L.sets, (double2*)L.gate_table, L.counters, L.e_part, n0,
+                                                            L.g_part, n1);
+    else
+        batch_gate_table_kernel<float><<<gk, 256, 0, st>>>(L.sets, (float2*)L.gate_table, L.counters, L.e_part, n0,
+                                                           L.g_part, n1);
     if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
-    if ((e = cudaMemsetAsync(L.counters, 0, 4 * sizeof(int32_t), st)) != cudaSuccess) return (int)e;
-    if (L.accum) {   // branch items add their shares
-        if (L.e_count && (e = cudaMemsetAsync(L.e_part, 0, L.e_count * sizeof(double), st)) != cudaSuccess) return (int)e;
-        if (L.g_count && (e = cudaMemsetAsync(L.g_part, 0, L.g_count * sizeof(double), st)) != cudaSuccess) return (int)e;
-    }
     const int rc = L.fp64 ? launch_batch_all<double>(L, st) : launch_batch_all<float>(L, st);
     if (rc) return rc;
     {
