@@ -73,8 +73,8 @@ __host__ __device__ inline TeamLayout team_layout(int W, int Wt, int tt, int rea
     off = (off + 15) & ~15;
     L.info = off;
     off += 2 * info_bytes(real_bytes);
-    L.fac = off;   // per-qubit diagonal factors of the layer being staged (info_fac): 2 x 32 complex + 32 kinds
-    off += 64 * r2 + 32 * 4;
+    L.fac = off;   // per-qubit diagonal factors of the layer being staged (info_fac): 32 x 4 complex
+    off += 128 * r2;
     off = (off + 15) & ~15;
     L.red = off;
     off += 2 * kMaxPassSlots * nwarps_of(tt) * real_bytes;
@@ -207,10 +207,11 @@ __device__ __forceinline__ T2* info_fac(const TeamMem<T2>& M) {
 
 // Stage one layer from its per-qubit records: rotation parameters and gradient slots into
 // info buffer `par`, and the diagonal phase table (conjugated for the adjoint direction).
-// A table entry is the product of the RZ factors of its chunk's qubits and the RZZ/CZ
-// factors of the pairs whose upper qubit lies in the chunk; those factors are first staged
-// per qubit in shared memory (one global read each), then every entry is built from them.
-// Ends with a team barrier.
+// A table entry is the product, over its chunk's qubits q, of the RZ factor of q and the
+// RZZ/CZ factor of the pair (q - 1, q) (q - 1 is the chunk's crossing bit for its first
+// qubit). Those two factors depend only on the bits of q - 1 and q, so they are first staged
+// per qubit as h_q(prev, bit) (one global read of the layer's records each), and an entry
+// costs one complex multiply per qubit. Ends with a team barrier.
 template <typename real, typename T2>
 __device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, const TeamMem<T2>& M, int par,
                             bool conj_phase) {
@@ -222,9 +223,7 @@ __device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, con
     int* pslot = info_pslot(M, par);
     const int has_diag = lp[0];
     const int32_t* R = lp + kLayerHeader;
-    T2* fz = info_fac(M);                                 // RZ on q: (cos, sin) of a/2, or (1, 0)
-    T2* fp = fz + 32;                                     // RZZ on (q - 1, q): (cos, sin), or (1, 0)
-    int* fpk = reinterpret_cast<int*>(fz + 64);           // kind of the (q - 1, q) gate, -1 none
+    T2* hq = info_fac(M);   // hq[4 q + 2 prev + bit]
     T2 one;
     one.x = 1;
     one.y = 0;
@@ -237,18 +236,33 @@ __device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, con
         zslot[j] = r[3];
         pslot[j] = (r[5] >> 8) - 1;
         if (has_diag) {
-            fz[j] = r[2] >= 0 ? GT[r[2]] : one;
-            int pk = -1;
+            const T2 g = r[2] >= 0 ? GT[r[2]] : one;   // RZ on j: (cos, sin) of a/2
+            int pk = -1;                                // the (j - 1, j) gate sits in record j - 1
             T2 pf = one;
             if (j > 0) {
-                const int32_t* rp = r - kRecWords;   // the pair (j - 1, j) sits in record j - 1
+                const int32_t* rp = r - kRecWords;
                 if (rp[4] >= 0) {
                     pk = rp[5] & 255;
                     if (pk != TLQ_CZ) pf = GT[rp[4]];
                 }
             }
-            fpk[j] = pk;
-            fp[j] = pf;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int prev = e >> 1, bq = e & 1;
+                // RZ(a): e^{-ia/2} for bit 0, e^{+ia/2} for bit 1 (identity when absent)
+                T2 f;
+                f.x = g.x;
+                f.y = bq ? g.y : -g.y;
+                if (pk == TLQ_CZ) {
+                    if (prev & bq) { f.x = -f.x; f.y = -f.y; }
+                } else if (pk >= 0) {   // RZZ: e^{-ia/2} for equal bits, e^{+ia/2} otherwise
+                    T2 h;
+                    h.x = pf.x;
+                    h.y = (prev ^ bq) ? pf.y : -pf.y;
+                    f = cmul(f, h);
+                }
+                hq[4 * j + e] = f;
+            }
         }
     }
     if (has_diag) {
@@ -263,30 +277,12 @@ __device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, con
             } else {
                 lo = 14; bc = W - 14; idx = e - 128 - (2 << b1); slot = M.tab2 + idx;
             }
-            T2 ph;
-            ph.x = 1;
-            ph.y = 0;
             int prev = lo > 0 ? (idx >> bc) & 1 : 0;   // bit of qubit lo - 1 (crossing bit)
-            for (int k = 0; k < bc; ++k) {
-                const int q = lo + k;
+            T2 ph = hq[4 * lo + 2 * prev + (idx & 1)];
+            prev = idx & 1;
+            for (int k = 1; k < bc; ++k) {
                 const int bq = (idx >> k) & 1;
-                const T2 g = fz[q];
-                // RZ(a) on q: e^{-ia/2} for bit 0, e^{+ia/2} for bit 1 (identity when absent)
-                T2 f;
-                f.x = g.x;
-                f.y = bq ? g.y : -g.y;
-                ph = cmul(ph, f);
-                if (q > 0) {
-                    const int pk = fpk[q];
-                    if (pk == TLQ_CZ) {
-                        if (prev & bq) { ph.x = -ph.x; ph.y = -ph.y; }
-                    } else if (pk >= 0) {   // RZZ: e^{-ia/2} for equal bits, e^{+ia/2} otherwise
-                        const T2 h = fp[q];
-                        f.x = h.x;
-                        f.y = (prev ^ bq) ? h.y : -h.y;
-                        ph = cmul(ph, f);
-                    }
-                }
+                ph = cmul(ph, hq[4 * (lo + k) + 2 * prev + bq]);
                 prev = bq;
             }
             if (conj_phase) ph.y = -ph.y;
