@@ -278,6 +278,20 @@ tlq_status run_device(Context* ctx, Circuit* c, Ham* h, const double* theta_dev,
     const bool fp64 = prec == TLQ_FP64_REF;
     const bool grad = grad_dev != nullptr;
     const bool plain = ctx->cfg.fuse_k == 1;
+    if (!grad && !fp64 && !plain && P.dense &&
+        tiny_fits(c->n, (int)c->gates.size(), (int)P.dense->all_terms.size())) {
+        // a small circuit, energies only: one CTA per set with the whole state (tiny.cu)
+        if (ctx->profile) TLQ_CUDA(cudaEventRecord((cudaEvent_t)ctx->prof_ev[0], (cudaStream_t)stream));
+        const int rc = launch_tiny_energy(pe->d_gates, (int)c->gates.size(), theta_dev, c->n_params, c->n,
+                                          pe->d_dallterms, (int)P.dense->all_terms.size(), B, energy_dev, stream);
+        if (ctx->profile) TLQ_CUDA(cudaEventRecord((cudaEvent_t)ctx->prof_ev[1], (cudaStream_t)stream));
+        ctx->last_launches = 1;
+        if (rc != 0) {
+            set_error(std::string("tiny launch: ") + cudaGetErrorString((cudaError_t)rc));
+            return TLQ_ECUDA;
+        }
+        return TLQ_OK;
+    }
     if (P.path != TLQ_PATH_CONE || plain) {
         if (!P.dense) {
             set_error("no dense statevector plan for this request (n > " + std::to_string(kDenseMaxQubits) + ")");

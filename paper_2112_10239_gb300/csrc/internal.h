@@ -303,6 +303,15 @@ struct ConeLaunch {
 
 int launch_cone(ConeLaunch& L, void* stream);
 
+// ---- small circuits (tiny.cu) ----
+// Energies of circuits of at most kTinyMaxQubits qubits: one CTA per parameter set holds the
+// whole state in shared memory and applies the gates in circuit order (FP32), then measures
+// every term (terms as in DensePlan::all_terms) and sums them in FP64 in term order.
+constexpr int kTinyMaxQubits = 10;
+bool tiny_fits(int n, int n_gates, int n_terms);
+int launch_tiny_energy(const tlq_gate* gates, int n_gates, const double* theta, int n_params, int n,
+                       const DenseXTermDev* terms, int n_terms, int B, double* energy, void* stream);
+
 // ---- work lists (planner.cpp) ----
 // One work item before chunking: the cone word (cone | half << kItemHalfShift), the set, the
 // state width W, the window width Wt (W + 1 for a branch) and the estimated amplitude visits.

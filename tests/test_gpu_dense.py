@@ -156,9 +156,13 @@ def test_qaoa_gradient_vs_oracle(tlq, n, p, seed):
     Er, gr = _oracle_grad(prob, prob.theta)
     check_energy(E, Er)
     check_grad(g, gr)
-    # the energy of the gradient call equals the energy-only call
+    # the energy of the gradient call equals the energy-only call (bit for bit on the dense
+    # path; up to rounding below 11 qubits, where energy-only calls run the small-circuit kernel)
     E2, _ = _energy(tlq, prob)
-    assert np.array_equal(E, E2)
+    if n > 10:
+        assert np.array_equal(E, E2)
+    else:
+        check_energy(E2, E)
 
 
 def test_qaoa_n24_gradient_vs_oracle(tlq):
