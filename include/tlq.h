@@ -124,7 +124,9 @@ tlq_status tlq_hamiltonian_destroy(tlq_ham h);
  * theta: host, row-major [B][n_params] FP64. energy: host [B] FP64. Synchronous. The device
  * work of a call (input copy, kernels, output copies) is captured once as a CUDA graph per
  * (circuit, Hamiltonian, B, precision, gradient or not) and replayed by later calls with the
- * same key, unless kernel profiling is enabled.
+ * same key, unless kernel profiling is enabled. Circuits of at most 10 qubits (FP32) are
+ * evaluated by one small kernel that applies the gates in order to the whole state; their
+ * energies agree with tlq_expectation_grad's to rounding, not bit for bit.
  * EINVAL: B <= 0, null pointers, circuit/Hamiltonian qubit counts differ.
  * ENOMEM: the call's workspace exceeds the context's budget. */
 tlq_status tlq_expectation(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta, int32_t B,
