@@ -382,6 +382,63 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, const Team& tm, co
             const int* zslot = info_zslot(M, par);
             const int* pslot = info_pslot(M, par);
             const int xb = base | M.hi;   // the index bits outside the register bits
+            if (tm.tt >= 32) {
+                // Whole warps (W >= 9, so s >= 5: window bits 0..4 are the lane bits, the bits
+                // from 5 up to s - 1 and above the register bits are the same across the warp).
+                // A Walsh transform of S over the lanes gives every sign pattern of the lane
+                // bits at once: lane m holds F[m] = sum_l (-1)^popc(l & m) S_l, so the sum for an
+                // RZ on lane bit j is F[2^j], for a pair of lane bits F[2^j0 + 2^j1], and for
+                // uniform bits F[0] with the warp's sign. The register-bit sums are reduced four
+                // at a time. Each slot is written by the lane that holds its value.
+                const int lane = tm.tid & 31;
+                real F = S;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const real o2 = __shfl_xor_sync(0xffffffffu, F, off);
+                    F = (lane & off) ? (o2 - F) : (F + o2);
+                }
+                const real sk = warp_sum4(Sk0, Sk1, Sk2, Sk3, lane);   // lane 8 k: sum of Sk_k
+                bool pin = false;                                      // RZZ inside the register block
+                for (int j0 = s; j0 < s + 3; ++j0) pin |= pslot[j0] >= 0;
+                const real sp = pin ? warp_sum4(Sp0, Sp1, Sp2, (real)0, lane) : (real)0;
+                auto put = [&](int t, int owner, real val) {
+                    if (lane == owner) {
+                        real* dst = red + t * nw + warp;
+                        *dst = first ? val : *dst + val;
+                    }
+                };
+                for (int j0 = 0; j0 < M.Wt; ++j0) {
+                    const int k0 = j0 - s;
+                    const bool in0 = (unsigned)k0 < 4u;
+                    if (zslot[j0] >= 0) {
+                        if (in0) put(4 + 2 * j0, 8 * k0, sk);
+                        else if (j0 < 5) put(4 + 2 * j0, 1 << j0, F);
+                        else put(4 + 2 * j0, 0, ((xb >> j0) & 1) ? -F : F);
+                    }
+                    if (pslot[j0] >= 0) {   // RZZ on (j0, j0 + 1)
+                        const int j1 = j0 + 1;
+                        const bool in1 = (unsigned)(j1 - s) < 4u;
+                        if (in0 && in1) {
+                            put(5 + 2 * j0, 8 * k0, sp);
+                        } else if (in0) {   // j0 = s + 3, j1 above the block: the same across the warp
+                            put(5 + 2 * j0, 24, ((xb >> j1) & 1) ? -sk : sk);
+                        } else if (in1) {   // j1 = s, j0 = s - 1
+                            if (j0 < 5) {   // a lane bit (s = 5): signed sum of Sk0 over the warp
+                                const real v = team_warp_sum(((xb >> j0) & 1) ? -Sk0 : Sk0, tm);
+                                put(5 + 2 * j0, 0, v);
+                            } else {
+                                put(5 + 2 * j0, 0, ((xb >> j0) & 1) ? -sk : sk);
+                            }
+                        } else if (j1 < 5) {
+                            put(5 + 2 * j0, (1 << j0) | (1 << j1), F);
+                        } else if (j0 < 5) {   // j0 = 4, j1 = 5
+                            put(5 + 2 * j0, 16, ((xb >> j1) & 1) ? -F : F);
+                        } else {
+                            put(5 + 2 * j0, 0, (((xb >> j0) ^ (xb >> j1)) & 1) ? -F : F);
+                        }
+                    }
+                }
+            } else
             for (int j0 = 0; j0 < M.Wt; ++j0) {
                 const int k0 = j0 - s;
                 const bool in0 = (unsigned)k0 < 4u;
