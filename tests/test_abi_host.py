@@ -118,6 +118,31 @@ def test_planner_window_inside_oracle_window(B, hctx):
         assert ng[t] <= len(keep)
 
 
+@pytest.mark.parametrize("n,L,n_split", [(20, 6, 8), (500, 4, 0), (100, 7, 86), (100, 8, 84)])
+def test_planner_window_branches(B, hctx, n, L, n_split):
+    # Windows of 13 or more qubits whose end qubit carries only first-layer gates and no term
+    # run as two branches; in the brick-wall Ising circuits that is every wide window (the
+    # clipped one at the chain's top end laid out mirrored). Each window measures at most 16
+    # terms and every term exactly once.
+    p = W.tfim_problem(n, L, 1, seed=0)
+    c, h = hctx.problem(p)
+    nrot, ndiag, npdiag, weff, wtrue, nterms, split = B.tlq_plan_cone_stats(hctx.h, c.h, h.h, len(p.terms))
+    assert int(split.sum()) == n_split
+    assert np.all(split[weff < 13] == 0) and np.all(split[weff >= 13] == 1)
+    assert np.all(wtrue[split == 1] == weff[split == 1])
+    assert nterms.max() <= 16 and int(nterms.sum()) == len(p.terms)
+
+
+def test_planner_no_branches_when_both_ends_are_measured(B, hctx):
+    # an X X term on both ends of a 13-qubit chain: the whole-chain window has terms on its
+    # top and bottom qubit, so it cannot be split either way
+    p = W.tfim_problem(13, 6, 1, seed=0)
+    p = W.Problem(p.n, p.gates, p.n_params, p.terms + [(0.7, (0, 12), "XX")], p.theta)
+    c, h = hctx.problem(p)
+    weff, split = B.tlq_plan_cone_stats(hctx.h, c.h, h.h, len(p.terms))[3::3]
+    assert 13 in list(weff) and int(split.sum()) == 0
+
+
 def test_non_local_circuit_goes_dense(B, hctx):
     p = W.qaoa_problem(10, 2, 1, seed=0)
     c, h = hctx.problem(p)
