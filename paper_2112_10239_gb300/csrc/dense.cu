@@ -704,6 +704,9 @@ __global__ void __launch_bounds__(256) dense_product_init_kernel(float2* psi, in
     __shared__ DensePassClassDev s_pcd[kMaxLayerClasses];
     __shared__ int32_t s_dist[kMaxDistWords];
     __shared__ int32_t s_woff[kMaxLayerClasses];
+    __shared__ int32_t s_toff[kMaxLayerClasses];
+    __shared__ float2 s_tab[kMaxTab];
+    __shared__ int s_staged;
     const int tid = threadIdx.x;
     if (tid < 32) {
         s_f[tid][0] = tid < n_eff ? init_factor(I, gates, GT, tid, 0) : make_float2(1.f, 0.f);
@@ -716,16 +719,22 @@ __global__ void __launch_bounds__(256) dense_product_init_kernel(float2* psi, in
     }
     __syncthreads();
     if (tid == 0) {
-        int w = 0;
+        int w = 0, t = 0;
         for (int c = 0; c < nc; ++c) {
             s_woff[c] = w;
             w += 2 * s_cls[c].ndist;
+            s_toff[c] = t;
+            t += s_cls[c].kind == 0 ? s_cls[c].nterms + 1 : 0;
         }
+        s_staged = t <= kMaxTab;   // the phase tables fit: read them from shared memory
     }
     __syncthreads();
-    for (int c = 0; c < nc; ++c)
+    for (int c = 0; c < nc; ++c) {
         for (int k = tid; k < 2 * s_cls[c].ndist; k += blockDim.x)
             if (s_woff[c] + k < kMaxDistWords) s_dist[s_woff[c] + k] = dists[2 * s_cls[c].dist_off + k];
+        if (s_staged && s_cls[c].kind == 0)
+            for (int e = tid; e <= s_cls[c].nterms; e += blockDim.x) s_tab[s_toff[c] + e] = ptab[s_cls[c].tab_off + e];
+    }
     __syncthreads();
     const uint64_t nblk = 1ull << (n_eff - 4);
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + tid; t < nblk; t += (uint64_t)gridDim.x * blockDim.x) {
@@ -749,10 +758,11 @@ __global__ void __launch_bounds__(256) dense_product_init_kernel(float2* psi, in
             const int cnt0 = class_count(C, s_dist + s_woff[ci], x0);
             int Ak[4];
             split_deltas(C, pc, x0, Ak);
+            const float2* tab = s_staged ? s_tab + s_toff[ci] : ptab + C.tab_off;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int cnt = split_count(pc, cnt0, Ak, j);
-                if (C.kind == 0) v[j] = cmul(v[j], ptab[C.tab_off + cnt]);
+                if (C.kind == 0) v[j] = cmul(v[j], tab[cnt]);
                 else if (cnt & 1) v[j] = make_float2(-v[j].x, -v[j].y);
             }
         }
