@@ -357,3 +357,55 @@ def test_partial_trace_properties_and_pauli_expectations(seed):
     # keeping every qubit gives the pure density operator itself
     full = density.reduced_density(psi, prob.n, range(prob.n))
     assert np.max(np.abs(full - np.outer(psi, psi.conj()))) < 1e-15
+
+
+@pytest.mark.parametrize("seed,top_kind,pair_kind", [(0, RY, CZ), (1, RX, RZZ), (2, RY, RZZ), (3, RX, CZ)])
+def test_window_branch_decomposition(seed, top_kind, pair_kind):
+    # The CUDA cone kernel splits a window whose top qubit t carries gates of the first layer
+    # only and no measured term into the branches t = 0 and t = 1. Check the mathematics it
+    # relies on with the oracle alone: with p_h the weight |f_t(h)|^2 of the top qubit's
+    # first-layer rotation (cos^2 a/2, sin^2 a/2) and E_h the energy of the (W-1)-qubit circuit
+    # whose pair gate (t-1, t) is replaced by its action at t = h (CZ: Z on t-1 for h = 1;
+    # RZZ(g): RZ((-1)^h g) on t-1), E = p_0 E_0 + p_1 E_1, and dE/da = sin(a)/2 (E_1 - E_0).
+    rng = np.random.default_rng(seed)
+    n, t = 9, 8
+    gates, P = [], 0
+    for q in range(n):   # first layer: rotations on every qubit, RZ, pairs (including (t-1, t))
+        gates.append((top_kind if q == t else int(rng.choice([RX, RY])), q, -1, P, 0.0))
+        P += 1
+    for q in range(n):
+        gates.append((RZ, q, -1, P, 0.0))
+        P += 1
+    for q in range(n - 1):
+        kind = pair_kind if q == t - 1 else int(rng.choice([CZ, RZZ]))
+        gates.append((kind, q, q + 1, P if kind == RZZ else -1, 0.0))
+        P += kind == RZZ
+    rest = []
+    for _ in range(3):   # later layers never touch t
+        for q in range(t):
+            rest.append((int(rng.choice([RX, RY])), q, -1, P, 0.0))
+            P += 1
+        for q in range(t - 1):
+            rest.append((RZZ, q, q + 1, P, 0.0))
+            P += 1
+    terms = [(float(rng.uniform(-1, 1)), (q,), "XYZ"[int(rng.integers(3))]) for q in range(t)]
+    terms += [(float(rng.uniform(-1, 1)), (q, q + 1), "ZZ") for q in range(t - 1)]
+    theta = rng.uniform(0, 2 * math.pi, size=P)
+    full = gates + rest
+    E, g = dense.grad_adjoint(n, full, terms, theta, P)
+    a_idx = next(G[3] for G in gates if G[1] == t and G[0] in (RX, RY))
+    a = theta[a_idx]
+    pair = next(G for G in gates if G[0] in (CZ, RZZ) and G[1] == t - 1)
+    Eh = []
+    for h in (0, 1):
+        # the branch circuit on qubits 0..t-1: gates not touching t, the pair gate at t = h
+        br = [G for G in gates if G[1] != t and not (G[0] in (CZ, RZZ) and G[2] == t)]
+        if pair[0] == CZ:
+            if h == 1:
+                br.append((RZ, t - 1, -1, -1, math.pi))   # Z on t-1 up to a global phase
+        else:
+            br.append((RZ, t - 1, -1, -1, (-1) ** h * theta[pair[3]]))
+        Eh.append(dense.energy(t, br + rest, terms, theta))
+    p0, p1 = math.cos(a / 2) ** 2, math.sin(a / 2) ** 2
+    assert abs(E - (p0 * Eh[0] + p1 * Eh[1])) <= 1e-12
+    assert abs(g[a_idx] - 0.5 * math.sin(a) * (Eh[1] - Eh[0])) <= 1e-10
