@@ -881,7 +881,10 @@ static bool encode_rho_maps(float2* rho, int64_t D, CUtensorMap* rows, CUtensorM
 
 // Tile and k-split plan shared by the workspace size and the launch: the tensor-core kernel
 // for outputs of at least one 128-tile (m >= 7), the CUDA-core kernel below that; the k range
-// is split (each split a whole number of chunks) until the launch has ~2 CTAs per SM.
+// is split (each split a whole number of chunks) while the launch still fits one wave (one CTA
+// per SM for the tensor-core kernel, two for the CUDA-core one): every split adds a full
+// partial output to write and sum. Long k ranges (>= 256 chunks a split) split further, up to
+// two tensor-core CTAs per SM, whose epilogues then overlap the other CTA's MMAs.
 struct HerkPlan {
     bool tc;
     int64_t tiles;
@@ -898,7 +901,10 @@ static HerkPlan herk_plan(int n, int m, int sm_count) {
     const int64_t T = (D + tile - 1) / tile;
     P.tiles = T * (T + 1) / 2;
     int64_t s = 1;
-    while (P.tiles * s < 2ll * sm_count && K / (s * 2) >= 8 * chunk) s *= 2;
+    const int64_t wave = P.tc ? sm_count : 2ll * sm_count;
+    while (K / (s * 2) >= 8 * chunk &&
+           (P.tiles * s * 2 <= wave || (P.tc && P.tiles * s < 2ll * sm_count && K / (s * 2) >= 256 * chunk)))
+        s *= 2;
     P.kps = ((K + s - 1) / s + chunk - 1) / chunk * chunk;
     P.splits = (int)((K + P.kps - 1) / P.kps);
     return P;
