@@ -36,6 +36,15 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant kernel,
+# taken from one ncu capture of that kernel on that workload (summaries in profiles/). Workloads
+# without an entry report null; an entry is removed when its kernel changes after the capture.
+NCU_TRAFFIC = {
+    ("tfim_n20_L6_B64", "cone_kernel"): 854016.0 + 0.0,
+    ("tfim_n500_L4_B256", "cone_kernel"): 10291712.0 + 632832.0,
+    ("partial_trace_n20_m13", "herk_ws_kernel"): 8826624.0 + 475120128.0,
+}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -516,7 +525,9 @@ def partial_trace_workloads(B, dev, local, flush, peaks, n=20, ms=(14, 10), step
             else:
                 roof = {"bound": "alu", "achieved": flops / (kms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                         "frac": flops / (kms * 1e-3) / 1e12 / peak, "kernel": "herk_tile_kernel (FP32)"}
-            roof.update({"kernel_ms": kms, "traffic": None, "hbm_bytes": hbm_bytes, "algorithmic_flops": flops})
+            kname = roof["kernel"].split(" ")[0]
+            roof.update({"kernel_ms": kms, "traffic": NCU_TRAFFIC.get((f"partial_trace_n{n}_m{m}", kname)),
+                         "hbm_bytes": hbm_bytes, "algorithmic_flops": flops})
             out[f"partial_trace_n{n}_m{m}"] = {
                 "value": 1e3 / float(np.median(t)), "unit": "traces/s", "ms": float(np.median(t)), "launches": nl,
                 "keep": f"qubits {keep[0]}..{keep[-1]}", "roofline": roof,
@@ -649,7 +660,7 @@ def main():
         flops = algorithmic_flops(B, ctx, c, h, prob, grad=True)
         achieved = flops / (kern_mean_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tflops, "traffic": None,
+                    "frac": achieved / peak_tflops, "traffic": NCU_TRAFFIC.get((args.workload, "cone_kernel")),
                     "kernel": "cone_kernel<float,grad> (batched causal cones + adjoint)",
                     "kernel_ms": kern_mean_ms, "algorithmic_flops": flops,
                     "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x {sm_max:.0f} MHz"}
