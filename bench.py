@@ -323,8 +323,9 @@ def dense_bytes(B, ctx, c, h, grad):
     return total, n_fwd
 
 
-def device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3):
-    """Time `steps` device-pointer calls (inputs resident, L2 flushed between steps)."""
+def device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3, mps=False):
+    """Time `steps` device-pointer calls (inputs resident, L2 flushed between steps); mps=True
+    times the exact MPS route (tlq_mps_expectation_grad_dev) instead of the default path."""
     import torch
     Bsz, P = prob.theta.shape
     stream = torch.cuda.current_stream(dev)
@@ -332,9 +333,11 @@ def device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3):
     E_d = torch.empty(Bsz, dtype=torch.float64, device=dev)
     G_d = torch.empty(Bsz, P, dtype=torch.float64, device=dev) if grad else None
 
+    call = B.tlq_mps_expectation_grad_dev if mps else B.tlq_expectation_grad_dev
+
     def step():
-        B.tlq_expectation_grad_dev(ctx.h, c.h, h.h, theta_d.data_ptr(), Bsz, B.TLQ_FP32, E_d.data_ptr(),
-                                   G_d.data_ptr() if grad else None, stream.cuda_stream)
+        call(ctx.h, c.h, h.h, theta_d.data_ptr(), Bsz, B.TLQ_FP32, E_d.data_ptr(),
+             G_d.data_ptr() if grad else None, stream.cuda_stream)
 
     for _ in range(warmup):
         step()
@@ -352,6 +355,28 @@ def device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3):
         b.synchronize()
         step_ms.append(a.elapsed_time(b))
     return float(np.median(step_ms)), float(np.median(kern_ms)), launches
+
+
+def mps_workload(B, dev, local, flush, peaks, name, steps=5, warmup=3):
+    """The exact MPS route (energy + gradient) on an Ising workload: device time of its five
+    kernels, FP32 roofline from the plan's contraction flops, and the cone path beside it."""
+    prob = workload(name)
+    with B.Context(device=local) as ctx:
+        c, h = ctx.problem(prob)
+        B.tlq_profile_enable(ctx.h, True)
+        bits, elems, _, fl = B.tlq_plan_mps_info(ctx.h, c.h, h.h)
+        ms, kms, nl = device_steps(B, ctx, c, h, prob, True, steps, dev, flush, warmup=warmup, mps=True)
+        cone_ms, _, _ = device_steps(B, ctx, c, h, prob, True, steps, dev, flush, warmup=warmup)
+        c.close()
+        h.close()
+    peak = 152 * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    flops = fl * prob.B
+    return {"value": prob.B / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "launches": nl,
+            "bond_dimension": 2 ** bits, "elems_per_set": elems, "cone_path_ms_per_step": cone_ms,
+            "roofline": {"bound": "alu", "achieved": flops / (kms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / (kms * 1e-3) / 1e12 / peak, "kernel_ms": kms, "algorithmic_flops": flops,
+                         "kernel": "mps_table/build/sweep/site/reduce kernels (complex64 contractions)",
+                         "traffic": None}}
 
 
 def extra_workloads(B, dev, local, flush, peaks):
@@ -373,6 +398,9 @@ def extra_workloads(B, dev, local, flush, peaks):
                          "frac": flops / (kms * 1e-3) / 1e12 / peak, "kernel_ms": kms}}
         c.close()
         h.close()
+    # the exact MPS route on the two Ising batches (bond dimension 16 and 64), beside the cone path
+    for name in ("tfim_n500_L4_B256", "tfim_n20_L6_B64"):
+        out["mps_" + name] = mps_workload(B, dev, local, flush, peaks, name, steps=3)
     # n=8, L=2, one set: latency of the synchronous call (launch-bound; no roofline)
     out["tfim_n8_L2_B1_latency"] = latency_n8(B, local)
     # n=28 QAOA on a 3-regular graph (dense statevector): energy and energy + gradient, fused
@@ -556,6 +584,28 @@ def main():
     if world > 1:
         dist.barrier()
     from paper_2112_10239_gb300 import binding as B
+
+    if args.workload.startswith("mps_"):   # the exact MPS route alone, one replica per rank
+        dev = torch.device("cuda", local)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        peaks, peak_kind = measured_peaks()
+        r = mps_workload(B, dev, local, flush, peaks, args.workload[4:], steps=args.steps,
+                         warmup=max(3, args.warmup))
+        if rank == 0:
+            prob = workload(args.workload[4:])
+            print(json.dumps({"metric": METRIC, "value": world * r["value"], "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                              "data": "synthetic", "config": {"workload": args.workload, "n": prob.n,
+                                                              "L": prob.meta.get("L"), "B": prob.B,
+                                                              "route": "exact MPS", "l2": "flushed between steps"},
+                              "gpu_launches": r["launches"] * args.steps, "roofline": r["roofline"],
+                              "bond_dimension": r["bond_dimension"],
+                              "cone_path_ms_per_step": r["cone_path_ms_per_step"], "peak_source": peak_kind}),
+                  flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     pt = re.fullmatch(r"partial_trace_n(\d+)_m(\d+)", args.workload)
     if pt:   # the partial trace alone (device time of tlq_partial_trace_dev), one replica per rank

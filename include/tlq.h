@@ -229,6 +229,40 @@ tlq_status tlq_partial_trace_dev(tlq_ctx ctx, const float* psi_dev, int32_t n, c
 tlq_status tlq_reduced_density(tlq_ctx ctx, tlq_circuit c, const double* theta, const int32_t* keep, int32_t m,
                                double* rho);
 
+/* Exact matrix-product-state (tensor-train) route (Sec. 2: MPS / tensor-train factorized
+ * representations; Sec. 1: contraction of factorized tensors; Sec. 3: <H> and its full
+ * gradient), for chain circuits: every RZZ / CZ acts on neighbours (q, q+1). Each such gate is
+ * split exactly into two products of single-site operators, so the bond between q and q+1
+ * carries one bit per two-qubit gate on that pair: bond dimension 2^(gates on the pair), no
+ * truncation, result exact up to rounding. The energies E[b] and, when grad is not NULL, the
+ * gradients grad[b][p] are those of tlq_expectation_grad (same definitions, same layouts:
+ * theta [B][n_params], energy [B], grad [B][n_params], row-major FP64), computed from the MPS
+ * by left and right environment sweeps and one pass per site. The Hamiltonian's terms may
+ * span any sites (a term costs one transfer per site of its span). Precision: TLQ_FP32 (and
+ * TLQ_MIXED_TC) keep site tensors and environments in complex64, TLQ_FP64_REF in complex128;
+ * the term and gradient sums are FP64 in a fixed order (results are deterministic).
+ * tlq_mps_expectation_grad_dev: device pointers, work enqueued on cuda_stream (NULL = the
+ * context's stream) without synchronising; tlq_mps_expectation_grad: host pointers,
+ * synchronous. Workspace from the context: about B * elems_per_set complex entries (see
+ * tlq_plan_mps_info) plus per-set tables.
+ * EINVAL: NULL handles or pointers, B <= 0, qubit counts that differ, n * B >= 2^31.
+ * EUNSUPPORTED: a two-qubit gate on non-neighbouring qubits, more than 6 two-qubit gates on
+ * one pair (5 in FP64), more than 48 gates on one qubit, more than 32 terms covering one qubit.
+ * ENOMEM: the workspace exceeds the context's memory budget. */
+tlq_status tlq_mps_expectation_grad_dev(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta_dev, int32_t B,
+                                        tlq_precision prec, double* energy_dev, double* grad_dev, void* cuda_stream);
+tlq_status tlq_mps_expectation_grad(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta, int32_t B,
+                                    tlq_precision prec, double* energy, double* grad);
+
+/* MPS plan of (c, h): the largest bond's bit count *max_bond_bits (bond dimension
+ * 2^max_bond_bits), the complex entries one parameter set's site tensors, environments and
+ * term chains take (*elems_per_set), and the contraction flops per parameter set of an
+ * energy-only call (*flops_energy) and of an energy + gradient call (*flops_grad), 8 per
+ * complex multiply-add of the environment transfers and site contractions. Any pointer may be
+ * NULL. Works on host-only contexts; EUNSUPPORTED as for tlq_mps_expectation_grad. */
+tlq_status tlq_plan_mps_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* max_bond_bits, int64_t* elems_per_set,
+                             double* flops_energy, double* flops_grad);
+
 typedef enum { TLQ_PATH_CONE = 0, TLQ_PATH_DENSE = 1 } tlq_path;
 
 /* Plan summary for (c, h): the chosen path; for the cone path, per term t < n_terms the

@@ -28,7 +28,8 @@ SYMBOLS = ["tlq_init", "tlq_destroy", "tlq_circuit_create", "tlq_circuit_destroy
            "tlq_expectation_grad", "tlq_expectation_grad_dev", "tlq_submit", "tlq_poll",
            "tlq_last_error", "tlq_plan_info", "tlq_plan_cone_stats", "tlq_profile_enable",
            "tlq_profile_last", "tlq_serving_stats", "tlq_version", "tlq_expectation_grad_static",
-           "tlq_plan_dense_info", "tlq_partial_trace_dev", "tlq_reduced_density"]
+           "tlq_plan_dense_info", "tlq_partial_trace_dev", "tlq_reduced_density",
+           "tlq_mps_expectation_grad", "tlq_mps_expectation_grad_dev", "tlq_plan_mps_info"]
 
 
 class tlq_gate(ctypes.Structure):
@@ -84,6 +85,9 @@ def lib():
         L.tlq_plan_dense_info.argtypes = [vp, vp, vp, ip, ip, ip, ip, ip, ip]
         L.tlq_partial_trace_dev.argtypes = [vp, vp, ctypes.c_int32, ip, ctypes.c_int32, vp, vp]
         L.tlq_reduced_density.argtypes = [vp, vp, dp, ip, ctypes.c_int32, dp]
+        L.tlq_mps_expectation_grad.argtypes = [vp, vp, vp, dp, ctypes.c_int32, ctypes.c_int, dp, dp]
+        L.tlq_mps_expectation_grad_dev.argtypes = [vp, vp, vp, vp, ctypes.c_int32, ctypes.c_int, vp, vp, vp]
+        L.tlq_plan_mps_info.argtypes = [vp, vp, vp, ip, ctypes.POINTER(ctypes.c_int64), dp, dp]
         L.tlq_profile_enable.argtypes = [vp, ctypes.c_int]
         L.tlq_profile_last.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ip]
         L.tlq_expectation_grad_static.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp, vp, vp]
@@ -206,6 +210,36 @@ def tlq_expectation_grad_dev(ctx, circ, ham, theta_ptr, B, prec, energy_ptr, gra
                                                  ctypes.c_void_p(energy_ptr),
                                                  ctypes.c_void_p(grad_ptr) if grad_ptr else None,
                                                  ctypes.c_void_p(stream_ptr) if stream_ptr else None), ctx)
+
+
+def tlq_mps_expectation(ctx, circ, ham, theta, prec=TLQ_FP32, grad=True):
+    """Exact MPS route, host arrays: E [B] (and G [B, n_params] when grad) for theta [B, n_params]."""
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    if theta.ndim == 1:
+        theta = theta[None, :]
+    B, P = theta.shape
+    E = np.zeros(B, dtype=np.float64)
+    G = np.zeros((B, P), dtype=np.float64) if grad else None
+    _check(lib().tlq_mps_expectation_grad(ctx, circ, ham, _dptr(theta), B, prec, _dptr(E),
+                                          _dptr(G) if grad else None), ctx)
+    return E, G
+
+
+def tlq_mps_expectation_grad_dev(ctx, circ, ham, theta_ptr, B, prec, energy_ptr, grad_ptr, stream_ptr):
+    """Exact MPS route, device pointers (int addresses); grad_ptr may be 0 for energies only."""
+    return _check(lib().tlq_mps_expectation_grad_dev(ctx, circ, ham, ctypes.c_void_p(theta_ptr), B, prec,
+                                                     ctypes.c_void_p(energy_ptr),
+                                                     ctypes.c_void_p(grad_ptr) if grad_ptr else None,
+                                                     ctypes.c_void_p(stream_ptr) if stream_ptr else None), ctx)
+
+
+def tlq_plan_mps_info(ctx, circ, ham):
+    """(max_bond_bits, complex entries per set, energy flops per set, energy+gradient flops per set)."""
+    bits, el = ctypes.c_int32(), ctypes.c_int64()
+    fe, fg = ctypes.c_double(), ctypes.c_double()
+    _check(lib().tlq_plan_mps_info(ctx, circ, ham, ctypes.byref(bits), ctypes.byref(el), ctypes.byref(fe),
+                                   ctypes.byref(fg)), ctx)
+    return bits.value, el.value, fe.value, fg.value
 
 
 def tlq_expectation_grad_static(ctx, circ, ham, theta_ptr, B, energy_ptr, grad_ptr, stream_ptr):

@@ -21,7 +21,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["cone.cu", "dense.cu", "density.cu", "tiny.cu", "noalloc.cu", "api.cpp", "planner.cpp", "serving.cpp"]
+SOURCES = ["cone.cu", "dense.cu", "density.cu", "tiny.cu", "mps.cu", "noalloc.cu", "api.cpp", "planner.cpp", "serving.cpp"]
 HEADERS = ["internal.h", "runtime.h", "gates.cuh"]
 
 

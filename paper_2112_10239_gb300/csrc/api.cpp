@@ -460,6 +460,7 @@ tlq_status tlq_destroy(tlq_ctx ctx) {
         cudaStreamSynchronize((cudaStream_t)ctx->stream);
     }
     ctx->plans.clear();
+    ctx->mps_plans.clear();
     for (Circuit* c : ctx->circuits) delete static_cast<tlq_circuit_s*>(c);
     for (Ham* h : ctx->hams) delete static_cast<tlq_ham_s*>(h);
     if (!ctx->host_only()) {
@@ -519,6 +520,16 @@ static void evict_plans(Context* ctx, uint64_t circ_id, uint64_t ham_id) {
         if (it->first.first == circ_id || it->first.second == ham_id) {
             ctx->held -= it->second->device_bytes;
             it = ctx->plans.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    for (auto it = ctx->mps_plans.begin(); it != ctx->mps_plans.end();) {
+        if (it->first.first == circ_id || it->first.second == ham_id) {
+            size_t b = 0;
+            mps_info(*it->second, nullptr, nullptr, &b);
+            ctx->held -= b;
+            it = ctx->mps_plans.erase(it);
         } else {
             ++it;
         }
@@ -968,6 +979,132 @@ tlq_status tlq_profile_last(tlq_ctx ctx, float* kernel_ms, int32_t* launches) {
     TLQ_CUDA(cudaEventElapsedTime(&ms, (cudaEvent_t)ctx->prof_ev[0], (cudaEvent_t)ctx->prof_ev[1]));
     if (kernel_ms) *kernel_ms = ms;
     if (launches) *launches = ctx->last_launches;
+    return TLQ_OK;
+}
+
+}  // extern "C"
+
+// ---- exact MPS route ----------------------------------------------------------------------
+
+namespace tlq {
+
+// Cached MPS plan of (circuit, Hamiltonian); uploaded to the device when `upload`.
+static tlq_status get_mps_plan(Context* ctx, Circuit* c, Ham* h, bool upload, std::shared_ptr<MpsPlan>* out) {
+    auto key = std::make_pair(c->id, h->id);
+    auto it = ctx->mps_plans.find(key);
+    std::shared_ptr<MpsPlan> p;
+    if (it != ctx->mps_plans.end()) {
+        p = it->second;
+    } else {
+        std::string err;
+        p = make_mps_plan(*c, *h, &err);
+        if (!p) { set_error(err); return TLQ_EUNSUPPORTED; }
+        ctx->mps_plans[key] = p;
+    }
+    if (upload) {
+        size_t before = 0, after = 0;
+        mps_info(*p, nullptr, nullptr, &before);
+        const int rc = mps_upload(*p);
+        if (rc != 0) {
+            set_error(std::string("MPS plan upload: ") + cudaGetErrorString((cudaError_t)rc));
+            return TLQ_ECUDA;
+        }
+        mps_info(*p, nullptr, nullptr, &after);
+        ctx->held += after - before;
+    }
+    *out = p;
+    return TLQ_OK;
+}
+
+// Launch on `st` with device buffers; the caller holds ctx->mu and has checked the arguments.
+// `pre` bytes at the front of the workspace are the caller's (angles and results of the host
+// call); the MPS buffers follow them.
+static tlq_status mps_run(Context* ctx, Circuit* c, Ham* h, const double* theta_dev, int B, tlq_precision prec,
+                          double* energy_dev, double* grad_dev, cudaStream_t st, size_t pre, void** pre_ptr,
+                          const double* theta_host) {
+    std::shared_ptr<MpsPlan> p;
+    TLQ_TRY(get_mps_plan(ctx, c, h, true, &p));
+    const bool fp64 = prec == TLQ_FP64_REF;
+    std::string why;
+    if (!mps_fits(*p, fp64, &why)) { set_error(why); return TLQ_EUNSUPPORTED; }
+    if ((int64_t)c->n * B > INT32_MAX) { set_error("MPS route: n * B above 2^31"); return TLQ_EINVAL; }
+    const size_t work = mps_workspace_bytes(*p, B, fp64);
+    if (ctx->ws.cap < work + pre + 4096) TLQ_CUDA(cudaDeviceSynchronize());
+    TLQ_TRY(reserve(ctx, work + pre + 4096));
+    if (pre) {
+        *pre_ptr = ctx->ws.take(pre);
+        // host call: the angles are the first B * n_params doubles of the caller's block
+        if (theta_host && c->n_params > 0)
+            TLQ_CUDA(cudaMemcpyAsync(*pre_ptr, theta_host, (size_t)B * c->n_params * sizeof(double),
+                                     cudaMemcpyHostToDevice, st));
+        if (theta_host) theta_dev = (const double*)*pre_ptr;
+        energy_dev = (double*)((char*)*pre_ptr + ((size_t)B * c->n_params * sizeof(double) + 255) / 256 * 256);
+        if (grad_dev) grad_dev = energy_dev + ((size_t)B * sizeof(double) + 255) / 256 * 256 / sizeof(double);
+    }
+    void* w = ctx->ws.take(work);
+    if (ctx->profile) TLQ_CUDA(cudaEventRecord((cudaEvent_t)ctx->prof_ev[0], st));
+    int nl = 0;
+    const int rc = launch_mps(*p, c->n_params > 0 ? theta_dev : nullptr, B, fp64, energy_dev, grad_dev, w, st, &nl);
+    if (ctx->profile) TLQ_CUDA(cudaEventRecord((cudaEvent_t)ctx->prof_ev[1], st));
+    ctx->last_launches = nl;
+    if (rc != 0) {
+        set_error(std::string("MPS launch: ") + cudaGetErrorString((cudaError_t)rc));
+        return TLQ_ECUDA;
+    }
+    return TLQ_OK;
+}
+
+}  // namespace tlq
+
+extern "C" {
+
+tlq_status tlq_mps_expectation_grad_dev(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta_dev, int32_t B,
+                                        tlq_precision prec, double* energy_dev, double* grad_dev, void* cuda_stream) {
+    TLQ_TRY(check_pair(ctx, c, h, B, prec));
+    if ((!theta_dev && c->n_params > 0) || !energy_dev) { set_error("NULL device pointer"); return TLQ_EINVAL; }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TLQ_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : (cudaStream_t)ctx->stream;
+    return mps_run(ctx, c, h, theta_dev, B, prec, energy_dev, grad_dev, st, 0, nullptr, nullptr);
+}
+
+tlq_status tlq_mps_expectation_grad(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta, int32_t B,
+                                    tlq_precision prec, double* energy, double* grad) {
+    TLQ_TRY(check_pair(ctx, c, h, B, prec));
+    if (!theta && c->n_params > 0) { set_error("theta is NULL"); return TLQ_EINVAL; }
+    if (!energy) { set_error("energy is NULL"); return TLQ_EINVAL; }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TLQ_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)ctx->stream;
+    const size_t P = (size_t)c->n_params;
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    // [angles | energies | gradients] at the front of the workspace
+    const size_t pre = al(B * P * sizeof(double)) + al(B * sizeof(double)) + (grad ? al(B * P * sizeof(double)) : 0);
+    void* blk = nullptr;
+    double dummy = 0;
+    TLQ_TRY(mps_run(ctx, c, h, nullptr, B, prec, &dummy, grad ? &dummy : nullptr, st, pre, &blk, theta));
+    const double* d_e = (const double*)((const char*)blk + al(B * P * sizeof(double)));
+    const double* d_g = d_e + al(B * sizeof(double)) / sizeof(double);
+    TLQ_CUDA(cudaMemcpyAsync(energy, d_e, B * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (grad && P > 0) TLQ_CUDA(cudaMemcpyAsync(grad, d_g, B * P * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TLQ_CUDA(cudaStreamSynchronize(st));
+    return TLQ_OK;
+}
+
+tlq_status tlq_plan_mps_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* max_bond_bits, int64_t* elems_per_set,
+                             double* flops_energy, double* flops_grad) {
+    if (!ctx || !c || !h) { set_error("NULL handle"); return TLQ_EINVAL; }
+    if (c->n != h->n) { set_error("circuit and Hamiltonian qubit counts differ"); return TLQ_EINVAL; }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    std::shared_ptr<MpsPlan> p;
+    TLQ_TRY(get_mps_plan(ctx, c, h, false, &p));
+    int bits = 0;
+    int64_t el = 0;
+    mps_info(*p, &bits, &el, nullptr);
+    if (max_bond_bits) *max_bond_bits = bits;
+    if (elems_per_set) *elems_per_set = el;
+    if (flops_energy) *flops_energy = mps_flops(*p, false);
+    if (flops_grad) *flops_grad = mps_flops(*p, true);
     return TLQ_OK;
 }
 

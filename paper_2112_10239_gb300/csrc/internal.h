@@ -312,6 +312,30 @@ bool tiny_fits(int n, int n_gates, int n_terms);
 int launch_tiny_energy(const tlq_gate* gates, int n_gates, const double* theta, int n_params, int n,
                        const DenseXTermDev* terms, int n_terms, int B, double* energy, void* stream);
 
+// ---- exact matrix-product states (mps.cu) ----
+// Chain circuits (every two-qubit gate on neighbours q, q+1) as an exact MPS: each two-qubit
+// gate splits into a sum of two products of single-site operators, so the bond between q and
+// q+1 carries one bit per gate on that pair (bond dimension 2^gates, no truncation).
+constexpr int kMpsMaxBondBitsF32 = 6;     // bond dimension <= 64 in FP32
+constexpr int kMpsMaxBondBitsF64 = 5;     // <= 32 in FP64
+constexpr int kMpsMaxSiteOps = 48;        // operators on one site (gates touching the qubit)
+struct MpsPlan;                           // host + device plan (mps.cu)
+// Plans a (circuit, Hamiltonian) pair on the host; nullptr with *err set when the circuit is
+// not a chain circuit or exceeds the limits above.
+std::shared_ptr<MpsPlan> make_mps_plan(const Circuit& c, const Ham& h, std::string* err);
+// Uploads the plan's tables (once); 0 or a cudaError_t.
+int mps_upload(MpsPlan& p);
+void mps_info(const MpsPlan& p, int* max_bond_bits, int64_t* elems_per_set, size_t* device_bytes);
+// Contraction flops per parameter set of one call (energies, or energies and gradients).
+double mps_flops(const MpsPlan& p, bool grad);
+size_t mps_workspace_bytes(const MpsPlan& p, int B, bool fp64);
+// Whether the plan runs in the given precision (bond limit, shared-memory fit); *why otherwise.
+bool mps_fits(const MpsPlan& p, bool fp64, std::string* why);
+// Energies (and gradients when grad != nullptr) of B parameter sets; theta, energy and grad
+// are device pointers, work a workspace of mps_workspace_bytes. 0 or a cudaError_t.
+int launch_mps(const MpsPlan& p, const double* theta, int B, bool fp64, double* energy, double* grad,
+               void* work, void* stream, int* launches);
+
 // ---- work lists (planner.cpp) ----
 // One work item before chunking: the cone word (cone | half << kItemHalfShift), the set, the
 // state width W, the window width Wt (W + 1 for a branch) and the estimated amplitude visits.

@@ -98,6 +98,7 @@ struct Context {
     size_t h_pinned_cap = 0;
     std::mutex mu;                   // guards the plan cache and workspace
     std::map<std::pair<uint64_t, uint64_t>, std::shared_ptr<PlanEntry>> plans;
+    std::map<std::pair<uint64_t, uint64_t>, std::shared_ptr<MpsPlan>> mps_plans;   // exact MPS route
     std::vector<Circuit*> circuits;
     std::vector<Ham*> hams;
     std::atomic<uint64_t> next_id{1};

@@ -200,3 +200,50 @@ def test_partial_trace_argument_checks(B, hctx):
     assert rd([499, 500]) == B.TLQ_EINVAL
     assert rd(list(range(15))) == B.TLQ_EINVAL      # the host API returns at most 14 kept qubits
     assert rd([250, 251, 253]) == B.TLQ_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("n,L", [(1, 2), (2, 1), (8, 2), (20, 6), (500, 4)])
+def test_mps_plan_bond_dimensions(B, hctx, n, L):
+    # the brick-wall puts one CZ per layer on every neighbouring pair: 2^L bond dimension on
+    # every inner bond; per set the plan holds the site tensors (2 chi_l chi_r each), four
+    # environments per bond (chi^2 each) and two chains per bond inside each term's span
+    p = W.tfim_problem(n, L, 1, seed=0)
+    c, h = hctx.problem(p)
+    bits, elems, fe, fg = B.tlq_plan_mps_info(hctx.h, c.h, h.h)
+    assert bits == (L if n > 1 else 0)
+    assert 0 < fe < fg
+    chi = [1] + [2 ** L] * (n - 1) + [1]
+    a = sum(2 * chi[q] * chi[q + 1] for q in range(n))
+    env = sum(x * x for x in chi)
+    chain = sum(chi[k] ** 2 for _, s, _ in p.terms for k in range(min(s) + 1, max(s) + 1))
+    assert elems == a + 4 * env + 2 * chain
+
+
+def test_mps_plan_counts_gates_per_pair(B, hctx):
+    # bonds count the two-qubit gates on each pair, in either qubit order, RZZ and CZ alike
+    gates = [(W.RY, 0, -1, 0, 0.0), (W.CZ, 1, 0, -1, 0.0), (W.RZZ, 0, 1, 1, 0.0), (W.RZZ, 2, 1, 2, 0.0)]
+    c = hctx.circuit(3, gates, 3)
+    h = hctx.hamiltonian(3, [(1.0, (0, 2), "XZ")])
+    bits, elems, _, _ = B.tlq_plan_mps_info(hctx.h, c.h, h.h)
+    chi = [1, 4, 2, 1]
+    assert bits == 2
+    assert elems == (2 * (1 * 4 + 4 * 2 + 2 * 1) + 4 * (1 + 16 + 4 + 1) + 2 * (16 + 4))
+
+
+def test_mps_plan_limits(B, hctx):
+    # non-neighbouring two-qubit gates, more than 6 gates on one pair, more than 48 gates on one
+    # qubit: EUNSUPPORTED (the cone and dense paths still take such circuits)
+    q = W.qaoa_problem(10, 2, 1, seed=0)
+    c, h = hctx.problem(q)
+    assert _err(B, B.tlq_plan_mps_info, hctx.h, c.h, h.h) == B.TLQ_EUNSUPPORTED
+    hz = hctx.hamiltonian(2, [(1.0, (0, 1), "ZZ")])
+    c7 = hctx.circuit(2, [(W.CZ, 0, 1, -1, 0.0)] * 7, 0)
+    assert _err(B, B.tlq_plan_mps_info, hctx.h, c7.h, hz.h) == B.TLQ_EUNSUPPORTED
+    c6 = hctx.circuit(2, [(W.CZ, 0, 1, -1, 0.0)] * 6, 0)
+    assert B.tlq_plan_mps_info(hctx.h, c6.h, hz.h)[0] == 6
+    c49 = hctx.circuit(2, [(W.RX, 0, -1, 0, 0.0)] * 49, 1)
+    assert _err(B, B.tlq_plan_mps_info, hctx.h, c49.h, hz.h) == B.TLQ_EUNSUPPORTED
+    # compute calls need a device
+    p = W.tfim_n8_L2()
+    c8, h8 = hctx.problem(p)
+    assert _err(B, B.tlq_mps_expectation, hctx.h, c8.h, h8.h, p.theta) == B.TLQ_EUNSUPPORTED
