@@ -588,6 +588,7 @@ def main():
     if args.workload.startswith("mps_"):   # the exact MPS route alone, one replica per rank
         dev = torch.device("cuda", local)
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        torch.cuda.set_stream(torch.cuda.Stream(dev))   # a real stream handle (the legacy default is 0)
         peaks, peak_kind = measured_peaks()
         r = mps_workload(B, dev, local, flush, peaks, args.workload[4:], steps=args.steps,
                          warmup=max(3, args.warmup))

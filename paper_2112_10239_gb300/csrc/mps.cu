@@ -65,6 +65,26 @@ struct MpsTermDev {
     double coeff;
 };
 
+// Output group of a sweep step or of the per-site kernel, and its contributions.
+struct MpsGroup {
+    int64_t dst;     // sweep: the matrix written; site kernel: Rx
+    int32_t c0, nc;  // contributions [c0, c0 + nc)
+    int32_t term;    // site kernel: the term whose energy the group yields, or -1
+    int32_t pad;
+};
+struct MpsContrib {
+    int64_t src;     // sweep: the input matrix; site kernel: Lx
+    double coef;
+    int32_t pauli;
+    int32_t pad;
+};
+
+// Where the descriptors of one (kernel role, site) start: kinds 0/1 the left sweep without /
+// with gradients, 2/3 the right sweep, 4/5 the per-site kernel; entry kind * n + q.
+struct MpsDescIdx {
+    int32_t g_off, ng, c_off, nc;
+};
+
 struct MpsPlan {
     int n = 0, n_gates = 0, n_params = 0, n_terms = 0;
     int max_bits = 0;
@@ -86,6 +106,9 @@ struct MpsPlan {
     std::vector<int32_t> pg_off;      // [n_params + 1] gates of each parameter, in gate order
     std::vector<int32_t> pg_idx;
     std::vector<tlq_gate> gates;
+    std::vector<MpsDescIdx> dsc;      // [6 n] precomputed groups and contributions per site
+    std::vector<MpsGroup> dgroups;
+    std::vector<MpsContrib> dcontribs;
     // device copies
     int32_t* d_bits = nullptr;
     int64_t* d_a_off = nullptr;
@@ -100,6 +123,9 @@ struct MpsPlan {
     int32_t* d_pg_off = nullptr;
     int32_t* d_pg_idx = nullptr;
     tlq_gate* d_gates = nullptr;
+    MpsDescIdx* d_dsc = nullptr;
+    MpsGroup* d_dgroups = nullptr;
+    MpsContrib* d_dcontribs = nullptr;
     size_t device_bytes = 0;
     bool uploaded = false;
     ~MpsPlan();
@@ -119,7 +145,12 @@ MpsPlan::~MpsPlan() {
     cudaFree(d_pg_off);
     cudaFree(d_pg_idx);
     cudaFree(d_gates);
+    cudaFree(d_dsc);
+    cudaFree(d_dgroups);
+    cudaFree(d_dcontribs);
 }
+
+static void build_descriptors(MpsPlan& p);
 
 std::shared_ptr<MpsPlan> make_mps_plan(const Circuit& c, const Ham& h, std::string* err) {
     auto p = std::make_shared<MpsPlan>();
@@ -234,6 +265,7 @@ std::shared_ptr<MpsPlan> make_mps_plan(const Circuit& c, const Ham& h, std::stri
             if (G.kind != TLQ_CZ && G.param >= 0) p->pg_idx[fill[G.param]++] = g;
         }
     }
+    build_descriptors(*p);
     return p;
 }
 
@@ -264,6 +296,9 @@ int mps_upload(MpsPlan& p) {
     if (!rc) rc = up(p.pg_off, &p.d_pg_off, &b);
     if (!rc) rc = up(p.pg_idx, &p.d_pg_idx, &b);
     if (!rc) rc = up(p.gates, &p.d_gates, &b);
+    if (!rc) rc = up(p.dsc, &p.d_dsc, &b);
+    if (!rc) rc = up(p.dgroups, &p.d_dgroups, &b);
+    if (!rc) rc = up(p.dcontribs, &p.d_dcontribs, &b);
     p.device_bytes = b;
     p.uploaded = rc == 0;
     return rc;
@@ -451,20 +486,6 @@ __host__ __device__ __forceinline__ T op_grad(const MpsOp& o, T c, T s, int be, 
     return T(2) * (d0.x * w0.x + d0.y * w0.y + d1.x * w1.x + d1.y * w1.y);
 }
 
-// Output group of a sweep step or of the per-site kernel, and its contributions.
-struct MpsGroup {
-    int64_t dst;     // sweep: the matrix written; site kernel: Rx
-    int32_t c0, nc;  // contributions [c0, c0 + nc)
-    int32_t term;    // site kernel: the term whose energy the group yields, or -1
-    int32_t pad;
-};
-struct MpsContrib {
-    int64_t src;     // sweep: the input matrix; site kernel: Lx
-    double coef;
-    int32_t pauli;
-    int32_t pad;
-};
-
 template <typename T>
 struct MpsArgs {
     using V = typename Cx<T>::t;
@@ -479,6 +500,9 @@ struct MpsArgs {
     const MpsTermDev* terms;
     const uint8_t* pauli;
     const int64_t* chain_boff;
+    const MpsDescIdx* dsc;
+    const MpsGroup* dgroups;
+    const MpsContrib* dcontribs;
     int64_t a_tot, env_tot, chain_tot, stride;
     int max_elems, max_groups, max_ops;
     int ygroups_sweep, ygroups_site;
@@ -566,23 +590,90 @@ __host__ __device__ int site_desc(const MpsArgs<T>& a, int q, MpsGroup* G, MpsCo
     return ng;
 }
 
-// Site tensors: block (set b, site q); each thread builds columns (al, be) of A_q.
+// Precomputes every (role, site) descriptor list with the functions above on the plan's host
+// tables; the kernels copy a site's list into shared memory with one load per entry.
+static void build_descriptors(MpsPlan& p) {
+    MpsArgs<float> a{};
+    a.n = p.n;
+    a.bits = p.bits.data();
+    a.a_off = p.a_off.data();
+    a.env_off = p.env_off.data();
+    a.act_off = p.act_off.data();
+    a.act = p.act.data();
+    a.terms = p.terms.data();
+    a.pauli = p.pauli.data();
+    a.chain_boff = p.chain_boff.data();
+    a.a_tot = p.a_tot;
+    a.env_tot = p.env_tot;
+    a.chain_tot = p.chain_tot;
+    std::vector<MpsGroup> G(p.max_groups);
+    std::vector<MpsContrib> C(p.max_contribs);
+    p.dsc.assign((size_t)6 * p.n, MpsDescIdx{0, 0, 0, 0});
+    for (int kind = 0; kind < 6; ++kind) {
+        a.grad = kind & 1;
+        for (int q = 0; q < p.n; ++q) {
+            int ng;
+            if (kind < 4) {
+                ng = sweep_desc(a, q, kind >> 1, G.data(), C.data());
+            } else {
+                ng = site_desc(a, q, G.data(), C.data());
+            }
+            int nc = 0;
+            for (int g = 0; g < ng; ++g) nc = std::max(nc, G[g].c0 + G[g].nc);
+            p.dsc[(size_t)kind * p.n + q] = MpsDescIdx{(int32_t)p.dgroups.size(), ng, (int32_t)p.dcontribs.size(), nc};
+            p.dgroups.insert(p.dgroups.end(), G.begin(), G.begin() + ng);
+            p.dcontribs.insert(p.dcontribs.end(), C.begin(), C.begin() + nc);
+        }
+    }
+}
+
+// Shared-memory layout of the per-site kernel (bytes from the start): Aw, Gam, the Z / partials
+// region, gacc (even count of doubles), the site's (cos, sin) table and operators, groups,
+// contributions.
 template <typename T>
-__host__ __device__ void build_body(const MpsArgs<T>& a, int bid, int tid, int nt) {
+__host__ __device__ inline void site_smem_offsets(int max_elems, int ygroups, int max_ops, int max_groups, int nt,
+                                                  size_t off[7]) {
+    const size_t el = (size_t)2 * max_elems * sizeof(typename Cx<T>::t);
+    off[0] = 2 * el;                                                        // region
+    off[1] = off[0] + site_region_bytes<T>(ygroups, max_elems, max_ops, nt); // gacc
+    off[2] = off[1] + (size_t)((max_ops + 1) & ~1) * sizeof(double);        // cos / sin
+    off[3] = off[2] + (size_t)max_ops * sizeof(double2);                    // operators
+    off[4] = off[3] + (size_t)max_ops * sizeof(MpsOp);                      // groups
+    off[5] = off[4] + (size_t)max_groups * sizeof(MpsGroup);                // contributions
+    off[6] = off[5] + (size_t)max_groups * sizeof(MpsContrib);              // end
+}
+
+// Stages the operators of site q and their (cos, sin) into shared memory.
+template <typename T>
+__host__ __device__ inline void stage_ops(const MpsArgs<T>& a, int q, int b, MpsOp* sop, double2* scs, int tid,
+                                          int nt) {
+    const int o0 = a.op_off[q], m = a.op_off[q + 1] - o0;
+    const double2* tab = a.tab + (int64_t)b * a.n_gates;
+    for (int k = tid; k < m; k += nt) {
+        const MpsOp o = a.ops[o0 + k];
+        sop[k] = o;
+        scs[k] = tab[o.gate];
+    }
+}
+
+// Site tensors: block (set b, site q); each thread builds columns (al, be) of A_q from the
+// site's operators staged in shared memory (smem: [max_ops] (cos, sin), [max_ops] operators).
+#pragma nv_exec_check_disable
+template <typename T, typename Sync>
+__host__ __device__ void build_body(const MpsArgs<T>& a, int bid, int tid, int nt, unsigned char* smem, Sync sync) {
     using V = typename Cx<T>::t;
     const int q = bid % a.n, b = bid / a.n;
     const int dl = 1 << a.bits[q], dr = 1 << a.bits[q + 1];
+    const int m = a.op_off[q + 1] - a.op_off[q];
+    double2* scs = reinterpret_cast<double2*>(smem);
+    MpsOp* sop = reinterpret_cast<MpsOp*>(scs + a.max_ops);
+    stage_ops(a, q, b, sop, scs, tid, nt);
+    sync();
     V* A = a.work + (int64_t)b * a.stride + a.a_off[q];
-    const double2* tab = a.tab + (int64_t)b * a.n_gates;
-    const int o0 = a.op_off[q], o1 = a.op_off[q + 1];
     for (int col = tid; col < dl * dr; col += nt) {
         const int al = col / dr, be = col - al * dr;
         V v0 = cx<V>(1, 0), v1 = cx<V>(0, 0);
-        for (int k = o0; k < o1; ++k) {
-            const MpsOp o = a.ops[k];
-            const double2 cs = tab[o.gate];
-            op_apply(o, (T)cs.x, (T)cs.y, al, be, v0, v1);
-        }
+        for (int k = 0; k < m; ++k) op_apply(sop[k], (T)scs[k].x, (T)scs[k].y, al, be, v0, v1);
         A[col] = v0;
         A[dl * dr + col] = v1;
     }
@@ -610,8 +701,7 @@ __host__ __device__ void stage_site(const MpsArgs<T>& a, const typename Cx<T>::t
 // out_g = sum_s Aw[s]^dagger Y_g[s] (out x out), written to the group's matrix.
 #pragma nv_exec_check_disable
 template <typename T, typename Sync>
-__host__ __device__ void sweep_body(const MpsArgs<T>& a, int bid, int tid, int nt, unsigned char* smem, int* s_ng,
-                                    Sync sync) {
+__host__ __device__ void sweep_body(const MpsArgs<T>& a, int bid, int tid, int nt, unsigned char* smem, Sync sync) {
     using V = typename Cx<T>::t;
     const int dir = bid & 1, b = bid >> 1;
     V* base = a.work + (int64_t)b * a.stride;
@@ -627,10 +717,12 @@ __host__ __device__ void sweep_body(const MpsArgs<T>& a, int bid, int tid, int n
     }
     for (int step = 0; step < a.n; ++step) {
         const int q = dir ? a.n - 1 - step : step;
-        if (tid == 0) *s_ng = sweep_desc(a, q, dir, G, C);
+        const MpsDescIdx d = a.dsc[(size_t)(dir * 2 + a.grad) * a.n + q];
+        for (int i = tid; i < d.ng; i += nt) G[i] = a.dgroups[d.g_off + i];
+        for (int i = tid; i < d.nc; i += nt) C[i] = a.dcontribs[d.c_off + i];
         stage_site(a, base, q, dir, Aw, tid, nt);
         sync();
-        const int ng = *s_ng;
+        const int ng = d.ng;
         const int din = 1 << a.bits[dir ? q + 1 : q], dout = 1 << a.bits[dir ? q : q + 1];
         const int ys = 2 * din * dout;
         for (int g0 = 0; g0 < ng; g0 += a.ygroups_sweep) {
@@ -675,30 +767,35 @@ __host__ __device__ void sweep_body(const MpsArgs<T>& a, int bid, int tid, int n
 // gradient partials [max_ops][nt]; then gacc [max_ops] (doubles), groups, contributions.
 #pragma nv_exec_check_disable
 template <typename T, typename Sync>
-__host__ __device__ void site_body(const MpsArgs<T>& a, int bid, int tid, int nt, unsigned char* smem, int* s_ng,
-                                   Sync sync) {
+__host__ __device__ void site_body(const MpsArgs<T>& a, int bid, int tid, int nt, unsigned char* smem, Sync sync) {
     using V = typename Cx<T>::t;
     const int q = bid % a.n, b = bid / a.n;
     const int dl = 1 << a.bits[q], dr = 1 << a.bits[q + 1], ne = dl * dr, ys = 2 * ne;
     V* base = a.work + (int64_t)b * a.stride;
     V* Aw = reinterpret_cast<V*>(smem);
     V* Gam = Aw + 2 * a.max_elems;
-    unsigned char* region = reinterpret_cast<unsigned char*>(Gam + 2 * a.max_elems);
+    size_t off[7];
+    site_smem_offsets<T>(a.max_elems, a.ygroups_site, a.max_ops, a.max_groups, nt, off);
+    unsigned char* region = smem + off[0];
     V* Z = reinterpret_cast<V*>(region);
     double* red = reinterpret_cast<double*>(Z + (size_t)a.ygroups_site * 2 * a.max_elems);
     T* cg = reinterpret_cast<T*>(region);
-    const size_t region_bytes = site_region_bytes<T>(a.ygroups_site, a.max_elems, a.max_ops, nt);
-    double* gacc = reinterpret_cast<double*>(region + region_bytes);
-    MpsGroup* G = reinterpret_cast<MpsGroup*>(gacc + a.max_ops);
-    MpsContrib* C = reinterpret_cast<MpsContrib*>(G + a.max_groups);
-    const int o0 = a.op_off[q], m = a.op_off[q + 1] - o0;
-    if (tid == 0) *s_ng = site_desc(a, q, G, C);
+    double* gacc = reinterpret_cast<double*>(smem + off[1]);
+    double2* scs = reinterpret_cast<double2*>(smem + off[2]);
+    MpsOp* sop = reinterpret_cast<MpsOp*>(smem + off[3]);
+    MpsGroup* G = reinterpret_cast<MpsGroup*>(smem + off[4]);
+    MpsContrib* C = reinterpret_cast<MpsContrib*>(smem + off[5]);
+    const int m = a.op_off[q + 1] - a.op_off[q];
+    const MpsDescIdx d = a.dsc[(size_t)(4 + a.grad) * a.n + q];
+    for (int i = tid; i < d.ng; i += nt) G[i] = a.dgroups[d.g_off + i];
+    for (int i = tid; i < d.nc; i += nt) C[i] = a.dcontribs[d.c_off + i];
+    if (a.grad) stage_ops(a, q, b, sop, scs, tid, nt);
     stage_site(a, base, q, 0, Aw, tid, nt);
     if (a.grad)
         for (int idx = tid; idx < ys; idx += nt) Gam[idx] = cx<V>(0, 0);
     for (int k = tid; k < m; k += nt) gacc[k] = 0.0;
     sync();
-    const int ng = *s_ng;
+    const int ng = d.ng;
     for (int g0 = 0; g0 < ng; g0 += a.ygroups_site) {
         const int nb = ng - g0 < a.ygroups_site ? ng - g0 : a.ygroups_site;
         // Z_g[s] = f(s) Lx Aw[s']   (dl x dr)
@@ -756,7 +853,6 @@ __host__ __device__ void site_body(const MpsArgs<T>& a, int bid, int tid, int nt
     }
     if (!a.grad) return;
     // gradients: per column, forward products kept, then the backward pass from Gamma
-    const double2* tab = a.tab + (int64_t)b * a.n_gates;
     for (int r0 = 0; r0 < ne; r0 += nt) {
         const int col = r0 + tid;
         if (col < ne) {
@@ -765,18 +861,15 @@ __host__ __device__ void site_body(const MpsArgs<T>& a, int bid, int tid, int nt
             f0[0] = cx<V>(1, 0);
             f1[0] = cx<V>(0, 0);
             for (int k = 0; k < m; ++k) {
-                const MpsOp o = a.ops[o0 + k];
-                const double2 cs = tab[o.gate];
                 V v0 = f0[k], v1 = f1[k];
-                op_apply(o, (T)cs.x, (T)cs.y, al, be, v0, v1);
+                op_apply(sop[k], (T)scs[k].x, (T)scs[k].y, al, be, v0, v1);
                 f0[k + 1] = v0;
                 f1[k + 1] = v1;
             }
             V w0 = Gam[col], w1 = Gam[ne + col];
             for (int k = m - 1; k >= 0; --k) {
-                const MpsOp o = a.ops[o0 + k];
-                const double2 cs = tab[o.gate];
-                const T c = (T)cs.x, sn = (T)cs.y;
+                const MpsOp o = sop[k];
+                const T c = (T)scs[k].x, sn = (T)scs[k].y;
                 cg[k * nt + tid] = o.param >= 0 ? op_grad(o, c, sn, be, f0[k], f1[k], f0[k + 1], f1[k + 1], w0, w1)
                                                 : T(0);
                 op_adjoint(o, c, sn, al, be, w0, w1);
@@ -794,7 +887,7 @@ __host__ __device__ void site_body(const MpsArgs<T>& a, int bid, int tid, int nt
         sync();
     }
     for (int k = tid; k < m; k += nt) {
-        const MpsOp o = a.ops[o0 + k];
+        const MpsOp o = sop[k];
         if (o.param >= 0) a.gslot[(int64_t)b * a.n_gates + o.gate] = gacc[k];
     }
 }
@@ -819,21 +912,20 @@ __global__ void mps_table_kernel(const tlq_gate* __restrict__ gates, int n_gates
 
 template <typename T>
 __global__ void __launch_bounds__(kMpsThreads) mps_build_kernel(MpsArgs<T> a) {
-    build_body(a, blockIdx.x, threadIdx.x, blockDim.x);
+    extern __shared__ __align__(16) unsigned char mps_smem[];
+    build_body(a, blockIdx.x, threadIdx.x, blockDim.x, mps_smem, DevSync{});
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kMpsThreads) mps_sweep_kernel(MpsArgs<T> a) {
     extern __shared__ __align__(16) unsigned char mps_smem[];
-    __shared__ int s_ng;
-    sweep_body(a, blockIdx.x, threadIdx.x, blockDim.x, mps_smem, &s_ng, DevSync{});
+    sweep_body(a, blockIdx.x, threadIdx.x, blockDim.x, mps_smem, DevSync{});
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kMpsThreads) mps_site_kernel(MpsArgs<T> a) {
     extern __shared__ __align__(16) unsigned char mps_smem[];
-    __shared__ int s_ng;
-    site_body(a, blockIdx.x, threadIdx.x, blockDim.x, mps_smem, &s_ng, DevSync{});
+    site_body(a, blockIdx.x, threadIdx.x, blockDim.x, mps_smem, DevSync{});
 }
 
 // E_b = sum_t c_t <P_t> (Neumaier, term order) for i < B; g_{b,p} = sum of the gradients of the
@@ -867,7 +959,7 @@ constexpr size_t kMpsSmemCap = 220 * 1024;
 
 struct MpsSizes {
     int ygroups_sweep = 0, ygroups_site = 0;
-    size_t sweep_smem = 0, site_smem = 0;
+    size_t sweep_smem = 0, site_smem = 0, build_smem = 0;
 };
 
 template <typename T>
@@ -881,10 +973,11 @@ MpsSizes mps_sizes(const MpsPlan& p) {
         if (b <= kMpsSmemCap) { z.ygroups_sweep = y; z.sweep_smem = b; break; }
     }
     for (int y = p.max_groups; y >= 1; --y) {
-        const size_t b = 2 * el + site_region_bytes<T>(y, p.max_site_elems, p.max_site_ops, kMpsThreads) +
-                         (size_t)p.max_site_ops * sizeof(double) + desc;
-        if (b <= kMpsSmemCap) { z.ygroups_site = y; z.site_smem = b; break; }
+        size_t off[7];
+        site_smem_offsets<T>(p.max_site_elems, y, p.max_site_ops, p.max_groups, kMpsThreads, off);
+        if (off[6] <= kMpsSmemCap) { z.ygroups_site = y; z.site_smem = off[6]; break; }
     }
+    z.build_smem = (size_t)p.max_site_ops * (sizeof(double2) + sizeof(MpsOp));
     return z;
 }
 
@@ -921,6 +1014,9 @@ int launch_t(const MpsPlan& p, const double* theta, int B, double* energy, doubl
     a.terms = p.d_terms;
     a.pauli = p.d_pauli;
     a.chain_boff = p.d_chain_boff;
+    a.dsc = p.d_dsc;
+    a.dgroups = p.d_dgroups;
+    a.dcontribs = p.d_dcontribs;
     a.a_tot = p.a_tot;
     a.env_tot = p.env_tot;
     a.chain_tot = p.chain_tot;
@@ -946,7 +1042,7 @@ int launch_t(const MpsPlan& p, const double* theta, int B, double* energy, doubl
         ++nl;
     }
     const unsigned sites = (unsigned)((int64_t)p.n * B);
-    mps_build_kernel<T><<<sites, kMpsThreads, 0, st>>>(a);
+    mps_build_kernel<T><<<sites, kMpsThreads, z.build_smem, st>>>(a);
     ++nl;
     cudaError_t e = cudaFuncSetAttribute(mps_sweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)z.sweep_smem);
