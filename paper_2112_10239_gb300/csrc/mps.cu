@@ -506,8 +506,6 @@ struct MpsArgs {
     int64_t a_tot, env_tot, chain_tot, stride;
     int max_elems, max_groups, max_ops;
     int ygroups_sweep, ygroups_site;
-    int ms_cap, lr_cap;      // staging capacity (elements) for the sweep's input matrices and the
-                             // site kernel's Lx / Rx matrices; 0 reads them from global memory
     V* work;                 // B blocks of `stride` elements
     const double2* tab;      // [B][n_gates] (cos, sin) of the half angles
     double* e;               // [B][n_terms] <P_t>
@@ -630,21 +628,19 @@ static void build_descriptors(MpsPlan& p) {
 }
 
 // Shared-memory layout of the per-site kernel (bytes from the start): Aw, Gam, the Z / partials
-// region, the staged Lx / Rx matrices, gacc (even count of doubles), the site's (cos, sin) table
-// and operators, groups, contributions.
+// region, gacc (even count of doubles), the site's (cos, sin) table and operators, groups,
+// contributions.
 template <typename T>
-__host__ __device__ inline void site_smem_offsets(int max_elems, int ygroups, int max_ops, int max_groups, int lr_cap,
-                                                  int nt, size_t off[8]) {
-    using V = typename Cx<T>::t;
-    const size_t el = (size_t)2 * max_elems * sizeof(V);
-    off[0] = 2 * el;                                                         // region
-    off[1] = off[0] + site_region_bytes<T>(ygroups, max_elems, max_ops, nt); // Lx / Rx
-    off[2] = off[1] + (size_t)lr_cap * sizeof(V);                            // gacc
-    off[3] = off[2] + (size_t)((max_ops + 1) & ~1) * sizeof(double);         // cos / sin
-    off[4] = off[3] + (size_t)max_ops * sizeof(double2);                     // operators
-    off[5] = off[4] + (size_t)max_ops * sizeof(MpsOp);                       // groups
-    off[6] = off[5] + (size_t)max_groups * sizeof(MpsGroup);                 // contributions
-    off[7] = off[6] + (size_t)max_groups * sizeof(MpsContrib);               // end
+__host__ __device__ inline void site_smem_offsets(int max_elems, int ygroups, int max_ops, int max_groups, int nt,
+                                                  size_t off[7]) {
+    const size_t el = (size_t)2 * max_elems * sizeof(typename Cx<T>::t);
+    off[0] = 2 * el;                                                        // region
+    off[1] = off[0] + site_region_bytes<T>(ygroups, max_elems, max_ops, nt); // gacc
+    off[2] = off[1] + (size_t)((max_ops + 1) & ~1) * sizeof(double);        // cos / sin
+    off[3] = off[2] + (size_t)max_ops * sizeof(double2);                    // operators
+    off[4] = off[3] + (size_t)max_ops * sizeof(MpsOp);                      // groups
+    off[5] = off[4] + (size_t)max_groups * sizeof(MpsGroup);                // contributions
+    off[6] = off[5] + (size_t)max_groups * sizeof(MpsContrib);              // end
 }
 
 // Stages the operators of site q and their (cos, sin) into shared memory.
@@ -711,8 +707,7 @@ __host__ __device__ void sweep_body(const MpsArgs<T>& a, int bid, int tid, int n
     V* base = a.work + (int64_t)b * a.stride;
     V* Aw = reinterpret_cast<V*>(smem);
     V* Y = Aw + 2 * a.max_elems;
-    V* Ms = Y + (size_t)a.ygroups_sweep * 2 * a.max_elems;
-    MpsGroup* G = reinterpret_cast<MpsGroup*>(Ms + a.ms_cap);
+    MpsGroup* G = reinterpret_cast<MpsGroup*>(Y + (size_t)a.ygroups_sweep * 2 * a.max_elems);
     MpsContrib* C = reinterpret_cast<MpsContrib*>(G + a.max_groups);
     if (tid == 0) {
         const int kb = dir ? a.n : 0;
@@ -730,15 +725,6 @@ __host__ __device__ void sweep_body(const MpsArgs<T>& a, int bid, int tid, int n
         const int ng = d.ng;
         const int din = 1 << a.bits[dir ? q + 1 : q], dout = 1 << a.bits[dir ? q : q + 1];
         const int ys = 2 * din * dout;
-        // the step's input matrices (the previous step's outputs), one coalesced copy
-        const bool staged = d.nc * din * din <= a.ms_cap;
-        if (staged) {
-            for (int idx = tid; idx < d.nc * din * din; idx += nt) {
-                const int c = idx / (din * din);
-                Ms[idx] = base[C[c].src + (idx - c * din * din)];
-            }
-            sync();
-        }
         for (int g0 = 0; g0 < ng; g0 += a.ygroups_sweep) {
             const int nb = ng - g0 < a.ygroups_sweep ? ng - g0 : a.ygroups_sweep;
             for (int idx = tid; idx < nb * ys; idx += nt) {
@@ -751,7 +737,7 @@ __host__ __device__ void sweep_body(const MpsArgs<T>& a, int bid, int tid, int n
                     int sp;
                     V f;
                     pauli_row(cc.pauli, s, &sp, &f);
-                    const V* M = (staged ? Ms + (size_t)c * din * din : base + cc.src) + (int64_t)i * din;
+                    const V* M = base + cc.src + (int64_t)i * din;
                     const V* Ac = Aw + sp * din * dout + o;
                     V d = cx<V>(0, 0);
                     for (int ip = 0; ip < din; ++ip) d = cfma(M[ip], Ac[ip * dout], d);
@@ -788,18 +774,17 @@ __host__ __device__ void site_body(const MpsArgs<T>& a, int bid, int tid, int nt
     V* base = a.work + (int64_t)b * a.stride;
     V* Aw = reinterpret_cast<V*>(smem);
     V* Gam = Aw + 2 * a.max_elems;
-    size_t off[8];
-    site_smem_offsets<T>(a.max_elems, a.ygroups_site, a.max_ops, a.max_groups, a.lr_cap, nt, off);
+    size_t off[7];
+    site_smem_offsets<T>(a.max_elems, a.ygroups_site, a.max_ops, a.max_groups, nt, off);
     unsigned char* region = smem + off[0];
     V* Z = reinterpret_cast<V*>(region);
     double* red = reinterpret_cast<double*>(Z + (size_t)a.ygroups_site * 2 * a.max_elems);
     T* cg = reinterpret_cast<T*>(region);
-    V* Ls = reinterpret_cast<V*>(smem + off[1]);
-    double* gacc = reinterpret_cast<double*>(smem + off[2]);
-    double2* scs = reinterpret_cast<double2*>(smem + off[3]);
-    MpsOp* sop = reinterpret_cast<MpsOp*>(smem + off[4]);
-    MpsGroup* G = reinterpret_cast<MpsGroup*>(smem + off[5]);
-    MpsContrib* C = reinterpret_cast<MpsContrib*>(smem + off[6]);
+    double* gacc = reinterpret_cast<double*>(smem + off[1]);
+    double2* scs = reinterpret_cast<double2*>(smem + off[2]);
+    MpsOp* sop = reinterpret_cast<MpsOp*>(smem + off[3]);
+    MpsGroup* G = reinterpret_cast<MpsGroup*>(smem + off[4]);
+    MpsContrib* C = reinterpret_cast<MpsContrib*>(smem + off[5]);
     const int m = a.op_off[q + 1] - a.op_off[q];
     const MpsDescIdx d = a.dsc[(size_t)(4 + a.grad) * a.n + q];
     for (int i = tid; i < d.ng; i += nt) G[i] = a.dgroups[d.g_off + i];
@@ -811,20 +796,6 @@ __host__ __device__ void site_body(const MpsArgs<T>& a, int bid, int tid, int nt
     for (int k = tid; k < m; k += nt) gacc[k] = 0.0;
     sync();
     const int ng = d.ng;
-    // every group's Lx (dl x dl) and Rx (dr x dr), one coalesced copy
-    const bool staged = ng * (dl * dl + dr * dr) <= a.lr_cap;
-    V* Rs = Ls + (size_t)ng * dl * dl;
-    if (staged) {
-        for (int idx = tid; idx < ng * dl * dl; idx += nt) {
-            const int gi = idx / (dl * dl);
-            Ls[idx] = base[C[G[gi].c0].src + (idx - gi * dl * dl)];
-        }
-        for (int idx = tid; idx < ng * dr * dr; idx += nt) {
-            const int gi = idx / (dr * dr);
-            Rs[idx] = base[G[gi].dst + (idx - gi * dr * dr)];
-        }
-        sync();
-    }
     for (int g0 = 0; g0 < ng; g0 += a.ygroups_site) {
         const int nb = ng - g0 < a.ygroups_site ? ng - g0 : a.ygroups_site;
         // Z_g[s] = f(s) Lx Aw[s']   (dl x dr)
@@ -835,7 +806,7 @@ __host__ __device__ void site_body(const MpsArgs<T>& a, int bid, int tid, int nt
             int sp;
             V f;
             pauli_row(cc.pauli, s, &sp, &f);
-            const V* Lx = (staged ? Ls + (size_t)(g0 + gi) * dl * dl : base + cc.src) + (int64_t)al * dl;
+            const V* Lx = base + cc.src + (int64_t)al * dl;
             const V* Ac = Aw + sp * ne + be;
             V d = cx<V>(0, 0);
             for (int ap = 0; ap < dl; ++ap) d = cfma(Lx[ap], Ac[ap * dr], d);
@@ -846,7 +817,7 @@ __host__ __device__ void site_body(const MpsArgs<T>& a, int bid, int tid, int nt
         bool any_e = false;
         for (int gi = 0; gi < nb; ++gi) {
             const MpsGroup g = G[g0 + gi];
-            const V* Rx = staged ? Rs + (size_t)(g0 + gi) * dr * dr : base + g.dst;
+            const V* Rx = base + g.dst;
             const T coef = (T)C[g.c0].coef;
             double ep = 0.0;
             for (int idx = tid; idx < ys; idx += nt) {
@@ -988,35 +959,23 @@ constexpr size_t kMpsSmemCap = 220 * 1024;
 
 struct MpsSizes {
     int ygroups_sweep = 0, ygroups_site = 0;
-    int ms_cap = 0, lr_cap = 0;
     size_t sweep_smem = 0, site_smem = 0, build_smem = 0;
 };
 
-// Shared memory of the sweep and per-site kernels: as many output groups per pass as fit, with
-// the input matrices staged when they fit beside at least one group.
 template <typename T>
-MpsSizes mps_sizes(const MpsPlan& p, int force_groups = 0) {
+MpsSizes mps_sizes(const MpsPlan& p) {
     using V = typename Cx<T>::t;
     MpsSizes z;
     const size_t el = (size_t)2 * p.max_site_elems * sizeof(V);
-    const size_t chi2 = (size_t)1 << (2 * p.max_bits);
-    const size_t gdesc = (size_t)p.max_groups * sizeof(MpsGroup);
-    for (int stage = 1; stage >= 0 && !z.ygroups_sweep; --stage) {
-        const size_t ms = stage ? (size_t)p.max_contribs * chi2 : 0;
-        for (int y = force_groups ? force_groups : p.max_groups; y >= 1; --y) {
-            const size_t b = el + (size_t)y * el + ms * sizeof(V) + gdesc + (size_t)p.max_contribs * sizeof(MpsContrib);
-            if (b <= kMpsSmemCap) { z.ygroups_sweep = y; z.sweep_smem = b; z.ms_cap = (int)ms; break; }
-            if (force_groups) break;
-        }
+    const size_t desc = (size_t)p.max_groups * sizeof(MpsGroup) + (size_t)p.max_contribs * sizeof(MpsContrib);
+    for (int y = p.max_groups; y >= 1; --y) {
+        const size_t b = el + (size_t)y * el + desc;
+        if (b <= kMpsSmemCap) { z.ygroups_sweep = y; z.sweep_smem = b; break; }
     }
-    for (int stage = 1; stage >= 0 && !z.ygroups_site; --stage) {
-        const int lr = stage ? (int)((size_t)p.max_groups * 2 * chi2) : 0;
-        for (int y = force_groups ? force_groups : p.max_groups; y >= 1; --y) {
-            size_t off[8];
-            site_smem_offsets<T>(p.max_site_elems, y, p.max_site_ops, p.max_groups, lr, kMpsThreads, off);
-            if (off[7] <= kMpsSmemCap) { z.ygroups_site = y; z.site_smem = off[7]; z.lr_cap = lr; break; }
-            if (force_groups) break;
-        }
+    for (int y = p.max_groups; y >= 1; --y) {
+        size_t off[7];
+        site_smem_offsets<T>(p.max_site_elems, y, p.max_site_ops, p.max_groups, kMpsThreads, off);
+        if (off[6] <= kMpsSmemCap) { z.ygroups_site = y; z.site_smem = off[6]; break; }
     }
     z.build_smem = (size_t)p.max_site_ops * (sizeof(double2) + sizeof(MpsOp));
     return z;
@@ -1067,8 +1026,6 @@ int launch_t(const MpsPlan& p, const double* theta, int B, double* energy, doubl
     a.max_ops = p.max_site_ops;
     a.ygroups_sweep = z.ygroups_sweep;
     a.ygroups_site = z.ygroups_site;
-    a.ms_cap = z.ms_cap;
-    a.lr_cap = z.lr_cap;
     a.work = reinterpret_cast<typename Cx<T>::t*>(w);
     w += al(per * B);
     double2* tab = reinterpret_cast<double2*>(w);
