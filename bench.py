@@ -85,6 +85,19 @@ def dist_info():
     return rank, world, local
 
 
+def job_throughput(local_s, units, world, device=None):
+    """Whole-job throughput of `world` replicas that each processed `units` in `local_s` seconds:
+    all units over the slowest rank's time (a MAX all-reduce of the times when world > 1).
+    Returns (value, max_seconds)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(local_s)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_s = float(t.item())
+    return world * units / local_s, local_s
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -672,12 +685,7 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * Bsz * args.steps / total_s
+    value, total_s = job_throughput(sum(step_ms) / 1e3, Bsz * args.steps, world, dev)
 
     # end to end through the host-pointer API (H2D of theta and D2H of energy + gradient inside);
     # kernel profiling off, as for any caller (it records events around single kernels)
@@ -690,7 +698,7 @@ def main():
         t0 = time.perf_counter()
         E_h, G_h = B.tlq_expectation_grad(ctx.h, c.h, h.h, theta_h)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_value = world * Bsz * len(e2e_t) / sum(e2e_t)
+    e2e_value, _ = job_throughput(sum(e2e_t), Bsz * len(e2e_t), world, dev)
 
     # roofline of the dominant kernel (the batched cone kernel), ALU-bound FP32
     peaks, peak_kind = measured_peaks()
