@@ -299,8 +299,8 @@ tlq_status tlq_plan_dense_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n
                                int32_t* n_fwd_passes, int32_t* n_rev_store, int32_t* n_xterms, int32_t* fused);
 
 /* Kernel timing for benchmarks. While enabled, every compute call records CUDA events
- * around its dominant kernel (the batched cone kernel, or the dense pass sequence) on the
- * stream it launches on. tlq_profile_last waits for the last call's events and returns
+ * around its dominant kernel (the batched cone kernel, the dense pass sequence, the partial
+ * trace's kernels, or all five kernels of the MPS route) on the stream it launches on. tlq_profile_last waits for the last call's events and returns
  * that kernel's device time in milliseconds and the number of kernels the call launched. */
 tlq_status tlq_profile_enable(tlq_ctx ctx, int on);
 tlq_status tlq_profile_last(tlq_ctx ctx, float* kernel_ms, int32_t* launches);
