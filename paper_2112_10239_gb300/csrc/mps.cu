@@ -22,9 +22,9 @@
 //
 // Kernels (one CTA per parameter set for the two sweeps, one per (set, site) otherwise):
 //   mps_table_kernel   half-angle cos / sin per (set, gate)
-//   mps_site_kernel    A_q for every (set, site)
+//   mps_build_kernel   A_q for every (set, site)
 //   mps_sweep_kernel   left and right sweeps (blockIdx.x & 1), sequential over sites
-//   mps_site_grad_kernel  term energies, Gamma_q and per-gate gradients
+//   mps_site_kernel    term energies, Gamma_q and per-gate gradients per (set, site)
 //   mps_reduce_kernel  E_b = sum_t c_t e_t and g_{b,p} = sum over the gates of p (FP64, fixed order)
 // States and environments are FP32 (or FP64) complex; the sums of the last step are FP64.
 #include "internal.h"
