@@ -247,3 +247,36 @@ def test_mps_plan_limits(B, hctx):
     p = W.tfim_n8_L2()
     c8, h8 = hctx.problem(p)
     assert _err(B, B.tlq_mps_expectation, hctx.h, c8.h, h8.h, p.theta) == B.TLQ_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("n,L,extra", [(9, 3, False), (12, 2, True)])
+def test_mps_flop_count(B, hctx, n, L, extra):
+    # the roofline numerator of the MPS route, recounted here from the circuit and the term
+    # spans: per site q (bond dimensions dl, dr) the left sweep forms the norm group, the H group
+    # (with gradients: H plus the terms ending at q) and one chain per term continuing right;
+    # the right sweep the mirror image (chains only with gradients); the site kernel one group
+    # per covering term plus two (with gradients) or the terms ending at q (energy only)
+    p = W.tfim_problem(n, L, 1, seed=0)
+    terms = list(p.terms) + ([(0.5, (1, n - 2), "XZ")] if extra else [])
+    c = hctx.circuit(n, p.gates, p.n_params)
+    h = hctx.hamiltonian(n, terms)
+    _, _, fe, fg = B.tlq_plan_mps_info(hctx.h, c.h, h.h)
+    chi = [1] + [2 ** L] * (n - 1) + [1]
+    spans = [(min(s), max(s)) for _, s, _ in terms]
+
+    def count(grad):
+        cm = 0
+        for q in range(n):
+            dl, dr = chi[q], chi[q + 1]
+            cov = [(i, j) for i, j in spans if i <= q <= j]
+            end_l = sum(j == q for i, j in cov)
+            end_r = sum(i == q for i, j in cov)
+            cont_l, cont_r = len(cov) - end_l, len(cov) - end_r
+            ncl, ngl = 1 + (1 + end_l if grad else 0) + cont_l, 1 + (1 if grad else 0) + cont_l
+            ncr, ngr = 1 + (1 + end_r + cont_r if grad else 0), 1 + (1 + cont_r if grad else 0)
+            cm += ncl * 2 * dl * dr * dl + ngl * 2 * dr * dr * dl
+            cm += ncr * 2 * dr * dl * dr + ngr * 2 * dl * dl * dr
+            cm += (2 + len(cov) if grad else end_l) * 2 * dl * dr * (dl + dr)
+        return 8.0 * cm
+
+    assert fe == count(False) and fg == count(True)
