@@ -929,7 +929,7 @@ __global__ void __launch_bounds__(kMpsThreads) mps_site_kernel(MpsArgs<T> a) {
 }
 
 // E_b = sum_t c_t <P_t> (Neumaier, term order) for i < B; g_{b,p} = sum of the gradients of the
-// gates of p (gate order) for B <= i < B + B * n_params.
+// gates of p (Neumaier, gate order) for B <= i < B + B * n_params.
 __global__ void mps_reduce_kernel(const MpsTermDev* __restrict__ terms, int n_terms, const double* __restrict__ e,
                                   const int32_t* __restrict__ pg_off, const int32_t* __restrict__ pg_idx,
                                   int n_params, int n_gates, const double* __restrict__ gslot, int B,
@@ -950,9 +950,14 @@ __global__ void mps_reduce_kernel(const MpsTermDev* __restrict__ terms, int n_te
     const int64_t j = i - B;
     if (j >= (int64_t)B * n_params) return;
     const int b = (int)(j / n_params), p = (int)(j - (int64_t)b * n_params);
-    double sum = 0.0;
-    for (int k = pg_off[p]; k < pg_off[p + 1]; ++k) sum += gslot[(int64_t)b * n_gates + pg_idx[k]];
-    grad[j] = sum;
+    double sum = 0.0, comp = 0.0;   // Neumaier, gate order (as the energy above)
+    for (int k = pg_off[p]; k < pg_off[p + 1]; ++k) {
+        const double x = gslot[(int64_t)b * n_gates + pg_idx[k]];
+        const double y = sum + x;
+        comp += fabs(sum) >= fabs(x) ? (sum - y) + x : (x - y) + sum;
+        sum = y;
+    }
+    grad[j] = sum + comp;
 }
 
 constexpr size_t kMpsSmemCap = 220 * 1024;

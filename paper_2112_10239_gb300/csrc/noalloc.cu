@@ -32,7 +32,8 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 namespace {
 
-std::mutex g_mu;
+std::mutex g_mu;           // guards the scratch addresses and the host-plan cache
+std::mutex g_enqueue_mu;   // makes each call's sequence of copies and launches one unit
 void* g_scratch_ptr[256] = {nullptr};   // device address of g_static_scratch per device
 
 // Set-up, once per device: the device must be current.
@@ -55,10 +56,18 @@ tlq_status static_scratch(int device, void** out) {
     return TLQ_OK;
 }
 
-// Host-side plan and work list for one (context, circuit, Hamiltonian, batch), cached by a
-// fingerprint of the circuit and Hamiltonian contents (host memory only).
+// Host-side plan and work list for one (context, device, circuit, Hamiltonian, batch size,
+// gradient flag). An entry is immutable once published and is held by shared_ptr for the
+// whole of a call, so a concurrent call that evicts it from the cache cannot free what this
+// call still reads. A cache hit is confirmed by comparing the stored circuit and Hamiltonian
+// contents, not the fingerprint alone.
 struct HostPlan {
-    uint64_t key[4];
+    const Context* ctx = nullptr;
+    int device = -1;
+    uint64_t key[2] = {0, 0};
+    int n = 0, n_params = 0;
+    std::vector<tlq_gate> gates;
+    std::vector<Term> terms;
     std::shared_ptr<Plan> plan;
     int B = -1;
     bool grad = false;
@@ -67,16 +76,16 @@ struct HostPlan {
     int n_chunks_smem = 0, smem_bytes = 0, smem_threads = kCtaThreads, gsmem_bytes = 0, g_maxW = 0;
     bool accum = false;
 };
-std::vector<std::unique_ptr<HostPlan>> g_plans;   // small LRU, guarded by g_mu
+std::vector<std::shared_ptr<const HostPlan>> g_plans;   // small LRU (most recent last), guarded by g_mu
+constexpr size_t kMaxHostPlans = 16;
 
 uint64_t mix(uint64_t h, uint64_t v) {
     h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
     return h;
 }
 
-void fingerprint(const Context* ctx, const Circuit& c, const Ham& h, uint64_t out[4]) {
-    uint64_t a = mix((uint64_t)(uintptr_t)ctx, (uint64_t)c.n);
-    a = mix(a, (uint64_t)c.n_params);
+void fingerprint(const Circuit& c, const Ham& h, uint64_t out[2]) {
+    uint64_t a = mix((uint64_t)c.n, (uint64_t)c.n_params);
     for (const tlq_gate& g : c.gates) {
         a = mix(a, ((uint64_t)(uint32_t)g.kind << 32) | (uint32_t)g.q0);
         a = mix(a, ((uint64_t)(uint32_t)g.q1 << 32) | (uint32_t)g.param);
@@ -94,8 +103,27 @@ void fingerprint(const Context* ctx, const Circuit& c, const Ham& h, uint64_t ou
     }
     out[0] = a;
     out[1] = b;
-    out[2] = c.gates.size();
-    out[3] = h.terms.size();
+}
+
+bool same_gate(const tlq_gate& x, const tlq_gate& y) {
+    return x.kind == y.kind && x.q0 == y.q0 && x.q1 == y.q1 && x.param == y.param &&
+           std::memcmp(&x.angle, &y.angle, sizeof(double)) == 0;
+}
+
+bool same_term(const Term& x, const Term& y) {
+    return std::memcmp(&x.coeff, &y.coeff, sizeof(double)) == 0 && x.sites == y.sites && x.letters == y.letters;
+}
+
+bool matches(const HostPlan& hp, const Context* ctx, int device, const uint64_t key[2], const Circuit& c,
+             const Ham& h, int B, bool grad) {
+    if (hp.ctx != ctx || hp.device != device || hp.B != B || hp.grad != grad) return false;
+    if (hp.key[0] != key[0] || hp.key[1] != key[1] || hp.n != c.n || hp.n_params != c.n_params) return false;
+    if (hp.gates.size() != c.gates.size() || hp.terms.size() != h.terms.size()) return false;
+    for (size_t i = 0; i < c.gates.size(); ++i)
+        if (!same_gate(hp.gates[i], c.gates[i])) return false;
+    for (size_t i = 0; i < h.terms.size(); ++i)
+        if (!same_term(hp.terms[i], h.terms[i])) return false;
+    return true;
 }
 
 void build_host_worklist(HostPlan& hp, int B, bool grad, int smax) {
@@ -118,6 +146,17 @@ void build_host_worklist(HostPlan& hp, int B, bool grad, int smax) {
     hp.grad = grad;
 }
 
+// A kernel that finds an inconsistent work item sets the error word; this call cannot read
+// it back without synchronising, so the error is made visible in the outputs instead: every
+// energy (and gradient entry) of the call becomes NaN. Runs after the reductions.
+__global__ void poison_on_error_kernel(const int32_t* err, double* energy, int B, double* grad, int64_t n_grad) {
+    if (*err == 0) return;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int64_t i = threadIdx.x; i < B; i += blockDim.x) energy[i] = nan;
+    if (grad)
+        for (int64_t i = threadIdx.x; i < n_grad; i += blockDim.x) grad[i] = nan;
+}
+
 struct Carve {
     unsigned char* base;
     size_t used = 0;
@@ -130,6 +169,15 @@ struct Carve {
 };
 
 }  // namespace
+
+// Drops the cached host plans of a context that is being destroyed.
+void noalloc_forget(const Context* ctx) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_plans.erase(std::remove_if(g_plans.begin(), g_plans.end(),
+                                 [&](const std::shared_ptr<const HostPlan>& p) { return p->ctx == ctx; }),
+                  g_plans.end());
+}
+
 }  // namespace tlq
 
 using namespace tlq;
@@ -153,33 +201,46 @@ extern "C" tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tl
     if (st != TLQ_OK) return st;
     const bool grad = grad_dev != nullptr;
 
-    uint64_t key[4];
-    fingerprint(C, *Ci, *Hm, key);
-    HostPlan* hp = nullptr;
+    uint64_t key[2];
+    fingerprint(*Ci, *Hm, key);
+    std::shared_ptr<const HostPlan> hp;
     {
         std::lock_guard<std::mutex> g(g_mu);
-        for (auto& p : g_plans)
-            if (std::equal(key, key + 4, p->key)) { hp = p.get(); break; }
-        if (!hp) {
-            std::string err;
-            auto plan = make_plan(*Ci, *Hm, &err);
-            if (!plan) { set_error(err); return TLQ_EINVAL; }
-            if (g_plans.size() >= 16) g_plans.erase(g_plans.begin());
-            g_plans.emplace_back(new HostPlan());
-            hp = g_plans.back().get();
-            std::copy(key, key + 4, hp->key);
-            hp->plan = plan;
-        }
-        if (hp->plan->path != TLQ_PATH_CONE) {
+        for (size_t i = 0; i < g_plans.size(); ++i)
+            if (matches(*g_plans[i], C, C->device, key, *Ci, *Hm, B, grad)) {
+                hp = g_plans[i];
+                g_plans.erase(g_plans.begin() + (std::ptrdiff_t)i);   // most recently used goes last
+                g_plans.push_back(hp);
+                break;
+            }
+    }
+    if (!hp) {
+        // planning is host work on this call's own copy; the entry is published only when complete
+        std::string err;
+        auto plan = make_plan(*Ci, *Hm, &err);
+        if (!plan) { set_error(err); return TLQ_EINVAL; }
+        if (plan->path != TLQ_PATH_CONE) {
             set_error("tlq_expectation_grad_static: only nearest-neighbour circuits (cone path) are supported");
             return TLQ_EUNSUPPORTED;
         }
-        if (hp->B != B || hp->grad != grad) {
-            int smax = 0;
-            cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, C->device);
-            smax = smax > 2048 ? smax - 1024 : 48 * 1024;
-            build_host_worklist(*hp, B, grad, smax);
-        }
+        auto fresh = std::make_shared<HostPlan>();
+        fresh->ctx = C;
+        fresh->device = C->device;
+        fresh->key[0] = key[0];
+        fresh->key[1] = key[1];
+        fresh->n = Ci->n;
+        fresh->n_params = Ci->n_params;
+        fresh->gates = Ci->gates;
+        fresh->terms = Hm->terms;
+        fresh->plan = plan;
+        int smax = 0;
+        cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, C->device);
+        smax = smax > 2048 ? smax - 1024 : 48 * 1024;
+        build_host_worklist(*fresh, B, grad, smax);
+        hp = fresh;
+        std::lock_guard<std::mutex> g(g_mu);
+        if (g_plans.size() >= kMaxHostPlans) g_plans.erase(g_plans.begin());
+        g_plans.push_back(hp);
     }
     const Plan& P = *hp->plan;
     const int G = (int)Ci->gates.size();
@@ -214,6 +275,9 @@ extern "C" tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tl
         return TLQ_ENOMEM;
     }
     cudaStream_t strm = cuda_stream ? (cudaStream_t)cuda_stream : (cudaStream_t)C->stream;
+    // Calls from several threads on one stream must not interleave their copies and launches
+    // (they share the array), so the whole enqueue sequence is one critical section.
+    std::lock_guard<std::mutex> enq(g_enqueue_mu);
     auto put = [&](void* dst, const void* src, size_t bytes) {
         if (bytes && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, strm);
     };
@@ -266,7 +330,12 @@ extern "C" tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tl
     L.grad = grad_dev;
     L.fp64 = false;
     L.sm_count = C->sm_count;
-    const int rc = launch_cone(L, strm);
+    int rc = launch_cone(L, strm);
+    if (rc == 0) {
+        poison_on_error_kernel<<<1, 256, 0, strm>>>(L.err, energy_dev, B, grad_dev,
+                                                   grad ? (int64_t)B * Ci->n_params : 0);
+        rc = (int)cudaGetLastError();
+    }
     if (rc != 0) {
         set_error(std::string("tlq_expectation_grad_static: launch: ") + cudaGetErrorString((cudaError_t)rc));
         return TLQ_ECUDA;

@@ -118,5 +118,7 @@ tlq_status run_device(Context* ctx, Circuit* c, Ham* h, const double* theta_dev,
                       double* energy_dev, double* grad_dev, void* stream, Workspace* ws);
 
 void scheduler_stop(Context* ctx);
+// Drops the allocation-free entry point's cached host plans of a context (noalloc.cu).
+void noalloc_forget(const Context* ctx);
 
 }  // namespace tlq
