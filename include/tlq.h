@@ -60,8 +60,14 @@ typedef enum {
 typedef enum {
     TLQ_FP32 = 0,      /* complex64 states, FP32 arithmetic; FP64 gate tables' source
                           angles and FP64 reductions across terms */
-    TLQ_MIXED_TC = 1,  /* reserved for tensor-core fused gate blocks; currently runs the
-                          FP32 path (same accuracy contract) */
+    TLQ_MIXED_TC = 1,  /* dense statevector path: each group of up to four rotations of a
+                          forward pass is one 16 x 16 complex block applied on the tensor
+                          cores (tcgen05, split-TF32 products, FP32 accumulation), and the
+                          energy and gradient are divided by the computed <psi|psi>, which
+                          cancels the tensor cores' truncating accumulation to first order;
+                          the same accuracy contract as TLQ_FP32. The adjoint passes, the
+                          causal-cone path and circuits of at most 10 qubits run their FP32
+                          kernels in this mode. */
     TLQ_FP64_REF = 2   /* complex128 correctness mode of the same kernels (slow) */
 } tlq_precision;
 
@@ -164,7 +170,14 @@ tlq_status tlq_expectation_grad_dev(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const
  * until the process exits; no cudaMalloc/cudaFree or other allocating routine is called.
  * The first call on a device looks up that array's device address (cudaGetSymbolAddress),
  * so make the first call on each device before any stream capture. Calls share the array:
- * calls whose work overlaps on the GPU race and must be serialised by the caller.
+ * calls whose work overlaps on the GPU race and must be serialised by the caller (for
+ * example by enqueueing them on one stream: each call enqueues its copies and launches as
+ * one unit, so calls made from several threads onto one stream do not interleave). Plans and work lists are cached on the host
+ * (16 entries, keyed by context, device, batch size, gradient flag and the full circuit and
+ * Hamiltonian contents); the cache is safe to use from several threads and contexts, and a
+ * context's entries are dropped by tlq_destroy. The call does not synchronise, so it cannot
+ * return a kernel's error status: if a kernel of the call finds an inconsistent work item,
+ * every energy (and gradient entry) the call writes is NaN instead.
  * TLQ_ENOMEM (with the byte count in tlq_last_error) when the call needs more than the
  * array holds; TLQ_EUNSUPPORTED for circuits that need the dense statevector path. */
 tlq_status tlq_expectation_grad_static(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double* theta_dev, int32_t B,

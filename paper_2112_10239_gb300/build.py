@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           "-I", INCLUDE, "-I", CSRC]
 SOURCES = ["cone.cu", "dense.cu", "density.cu", "tiny.cu", "mps.cu", "noalloc.cu", "api.cpp", "planner.cpp", "serving.cpp"]
-HEADERS = ["internal.h", "runtime.h", "gates.cuh"]
+HEADERS = ["internal.h", "runtime.h", "gates.cuh", "tc.cuh"]
 
 
 def _sources():

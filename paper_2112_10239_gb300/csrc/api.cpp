@@ -200,7 +200,7 @@ size_t dense_workspace_bytes(const PlanEntry& pe, const Circuit& c, int B, bool 
 
 static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const double* theta_dev, int B,
                             double* energy_dev, double* grad_dev, bool per_gate, void* stream, Workspace* ws,
-                            void** state_out = nullptr) {
+                            void** state_out = nullptr, bool tc = false) {
     const DensePlan& D = *pe.plan->dense;
     const bool grad = grad_dev != nullptr;
     const size_t need = dense_workspace_bytes(pe, c, B, grad, ctx->sm_count);
@@ -246,6 +246,7 @@ static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const
     L.grad = grad_dev;
     L.err = ctx->d_err;
     L.per_gate = per_gate;
+    L.tc = tc;
     L.sm_count = ctx->sm_count;
     L.host_gates = c.gates.data();
     L.host_passes = D.passes.data();
@@ -302,7 +303,8 @@ tlq_status run_device(Context* ctx, Circuit* c, Ham* h, const double* theta_dev,
                       (P.path == TLQ_PATH_DENSE ? P.why_dense : std::string("plain per-gate mode")) + ")");
             return TLQ_EUNSUPPORTED;
         }
-        return run_dense(ctx, *pe, *c, theta_dev, B, energy_dev, grad_dev, plain || !P.dense->fits_fused, stream, ws);
+        return run_dense(ctx, *pe, *c, theta_dev, B, energy_dev, grad_dev, plain || !P.dense->fits_fused, stream, ws,
+                         nullptr, prec == TLQ_MIXED_TC);
     }
     TLQ_TRY(ensure_worklist(ctx, *pe, *c, B, fp64, grad));
     const int g_grid = global_grid(*pe, ctx->sm_count);
@@ -455,6 +457,7 @@ tlq_status tlq_init(const tlq_config* cfg_in, tlq_ctx* out) {
 tlq_status tlq_destroy(tlq_ctx ctx) {
     if (!ctx) return TLQ_OK;
     scheduler_stop(ctx);
+    noalloc_forget(ctx);
     if (!ctx->host_only()) {
         cudaSetDevice(ctx->device);
         cudaStreamSynchronize((cudaStream_t)ctx->stream);

@@ -23,7 +23,9 @@
 // for the gradient one sweep per gate and state) is kept as the baseline the fused passes are
 // compared against.
 #include "gates.cuh"
+#include "tc.cuh"
 
+#include <algorithm>
 #include <cstdio>
 
 namespace tlq {
@@ -52,6 +54,7 @@ struct PassArgs {
     float2* state;
     int32_t n_eff;
     double* partial;        // per-CTA energy partials
+    double* npartial;       // tensor-core passes: per-half <psi|psi> partials
     int32_t* err;           // kernel error word
     float2* lam;            // gradient mode, final pass: lam = (diagonal part of H) psi, else null
 };
@@ -102,6 +105,7 @@ __device__ __forceinline__ void wait_tiles() { asm volatile("cp.async.wait_group
 // Stage a pass's classes (diagonal phases of the layers it completes, and the energy
 // classes in the final pass) with their distance words, phase tables and split counts.
 // Called by every thread of the CTA; ends with a barrier.
+template <int NT = kThreads>
 __device__ void stage_classes(const DensePassDev& P, const DenseClassDev* classes, const DensePassClassDev* pcd,
                               const int32_t* stage, const int32_t* dists, const float2* ptab, DenseClassDev* s_cls,
                               DensePassClassDev* s_pcd, int32_t* s_woff, int32_t* s_toff, int32_t* s_dist,
@@ -119,13 +123,13 @@ __device__ void stage_classes(const DensePassDev& P, const DenseClassDev* classe
         }
     }
     for (int g = 0; g < P.ngroups; ++g)
-        for (int k = tid; k < P.group_ncls[g]; k += kThreads) s_pcd[P.group_cls[g] + k] = pcd[P.group_pcd[g] + k];
+        for (int k = tid; k < P.group_ncls[g]; k += NT) s_pcd[P.group_cls[g] + k] = pcd[P.group_pcd[g] + k];
     __syncthreads();
     for (int c = 0; c < nst; ++c) {
         const DenseClassDev& C = s_cls[c];
-        for (int w = tid; w < 2 * C.ndist; w += kThreads) s_dist[s_woff[c] + w] = dists[2 * C.dist_off + w];
+        for (int w = tid; w < 2 * C.ndist; w += NT) s_dist[s_woff[c] + w] = dists[2 * C.dist_off + w];
         if (C.kind == 0)
-            for (int e = tid; e <= C.nterms; e += kThreads) s_tab[s_toff[c] + e] = ptab[C.tab_off + e];
+            for (int e = tid; e <= C.nterms; e += NT) s_tab[s_toff[c] + e] = ptab[C.tab_off + e];
     }
     __syncthreads();
 }
@@ -149,6 +153,76 @@ __device__ __forceinline__ int split_count(const DensePassClassDev& pc, int cnt0
     if (j & 4) cnt += Ak[2];
     if (j & 8) cnt += Ak[3];
     return cnt;
+}
+
+// After group g of a pass: the diagonal phases of a completed layer and/or the energy, from
+// split class counts over the thread's 16 amplitudes v (register bits at s.., thread base index
+// `base` in tile t_id); accumulates the energy into eacc and, in gradient mode, writes lam.
+template <bool NORM = false>
+__device__ __forceinline__ void group_epilogue(const PassArgs& A, const DensePassDev& P, int g, uint32_t t_id,
+                                               int base, int s, float2 (&v)[16], float& eacc, float& nacc,
+                                               const DenseClassDev* s_cls, const DensePassClassDev* s_pcd,
+                                               const int32_t* s_woff, const int32_t* s_toff, const int32_t* s_dist,
+                                               const float2* s_tab) {
+    // after this group: diagonal phases of a completed layer and/or the energy, from split
+    // class counts; the last group then writes straight to HBM from registers
+    const int ncls = P.group_ncls[g];
+    if (ncls > 0 || g == P.measure_group) {
+        const uint32_t xb = tile_x(P, t_id, (uint32_t)base);   // register bits are zero in base
+        float2 ph[16];
+        float ez[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            ph[j] = make_float2(1.f, 0.f);
+            ez[j] = 0.f;
+        }
+        bool any_phase = false, any_energy = g == P.measure_group;
+        for (int ci = P.group_cls[g]; ci < P.group_cls[g] + ncls; ++ci) {
+            const DenseClassDev& C = s_cls[ci];
+            const DensePassClassDev& pc = s_pcd[ci];
+            const int woff = s_woff[ci], toff = s_toff[ci];
+            any_phase |= C.kind != 2;
+            any_energy |= C.kind == 2;
+            const int cnt0 = class_count(C, s_dist + woff, xb);
+            int Ak[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int inter = __popc(xb & pc.N[k]);
+                Ak[k] = C.kind == 1 ? inter : __popc(pc.N[k]) - 2 * inter + (int)((pc.single >> k) & 1u);
+            }
+            const uint32_t cw0 = pc.C[0], cw1 = pc.C[1], cw2 = pc.C[2], cw3 = pc.C[3];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const uint32_t cw = (j >> 2) == 0 ? cw0 : (j >> 2) == 1 ? cw1 : (j >> 2) == 2 ? cw2 : cw3;
+                int cnt = cnt0 + (int)((cw >> (8 * (j & 3))) & 255u);
+                if (j & 1) cnt += Ak[0];
+                if (j & 2) cnt += Ak[1];
+                if (j & 4) cnt += Ak[2];
+                if (j & 8) cnt += Ak[3];
+                if (C.kind == 0) ph[j] = cmul(ph[j], s_tab[toff + cnt]);
+                else if (C.kind == 1) { if (cnt & 1) { ph[j].x = -ph[j].x; ph[j].y = -ph[j].y; } }
+                else ez[j] += (float)C.coeff * (float)(C.nterms - 2 * cnt);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (any_phase) v[j] = cmul(v[j], ph[j]);
+            if (any_energy) {
+                if (A.n_zterms > 0) {
+                    const uint32_t x = tile_x(P, t_id, (uint32_t)(base | (j << s)));
+                    for (int k = 0; k < A.n_zterms; ++k) {
+                        const DenseZTermDev Z = A.zterms[k];
+                        ez[j] += (__popc(x & Z.mask) & 1) ? -(float)Z.coeff : (float)Z.coeff;
+                    }
+                }
+                const float pj = v[j].x * v[j].x + v[j].y * v[j].y;
+                eacc += pj * ez[j];
+                if (NORM) nacc += pj;
+                if (A.lam)
+                    A.lam[tile_x(P, t_id, (uint32_t)(base | (j << s)))] = make_float2(ez[j] * v[j].x, ez[j] * v[j].y);
+            }
+        }
+    }
 }
 
 // Persistent pass kernel: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
@@ -210,63 +284,7 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_co
             if (kd[1] >= 0) apply_rot<1>(v, kd[1], c[1], sn[1]);
             if (kd[2] >= 0) apply_rot<2>(v, kd[2], c[2], sn[2]);
             if (kd[3] >= 0) apply_rot<3>(v, kd[3], c[3], sn[3]);
-            // after this group: diagonal phases of a completed layer and/or the energy, from split
-            // class counts; the last group then writes straight to HBM from registers
-            const int ncls = P.group_ncls[g];
-            if (ncls > 0 || g == P.measure_group) {
-                const uint32_t xb = tile_x(P, t_id, (uint32_t)base);   // register bits are zero in base
-                float2 ph[16];
-                float ez[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    ph[j] = make_float2(1.f, 0.f);
-                    ez[j] = 0.f;
-                }
-                bool any_phase = false, any_energy = g == P.measure_group;
-                for (int ci = P.group_cls[g]; ci < P.group_cls[g] + ncls; ++ci) {
-                    const DenseClassDev& C = s_cls[ci];
-                    const DensePassClassDev& pc = s_pcd[ci];
-                    const int woff = s_woff[ci], toff = s_toff[ci];
-                    any_phase |= C.kind != 2;
-                    any_energy |= C.kind == 2;
-                    const int cnt0 = class_count(C, s_dist + woff, xb);
-                    int Ak[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int inter = __popc(xb & pc.N[k]);
-                        Ak[k] = C.kind == 1 ? inter : __popc(pc.N[k]) - 2 * inter + (int)((pc.single >> k) & 1u);
-                    }
-                    const uint32_t cw0 = pc.C[0], cw1 = pc.C[1], cw2 = pc.C[2], cw3 = pc.C[3];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const uint32_t cw = (j >> 2) == 0 ? cw0 : (j >> 2) == 1 ? cw1 : (j >> 2) == 2 ? cw2 : cw3;
-                        int cnt = cnt0 + (int)((cw >> (8 * (j & 3))) & 255u);
-                        if (j & 1) cnt += Ak[0];
-                        if (j & 2) cnt += Ak[1];
-                        if (j & 4) cnt += Ak[2];
-                        if (j & 8) cnt += Ak[3];
-                        if (C.kind == 0) ph[j] = cmul(ph[j], s_tab[toff + cnt]);
-                        else if (C.kind == 1) { if (cnt & 1) { ph[j].x = -ph[j].x; ph[j].y = -ph[j].y; } }
-                        else ez[j] += (float)C.coeff * (float)(C.nterms - 2 * cnt);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    if (any_phase) v[j] = cmul(v[j], ph[j]);
-                    if (any_energy) {
-                        if (A.n_zterms > 0) {
-                            const uint32_t x = tile_x(P, t_id, (uint32_t)(base | (j << s)));
-                            for (int k = 0; k < A.n_zterms; ++k) {
-                                const DenseZTermDev Z = A.zterms[k];
-                                ez[j] += (__popc(x & Z.mask) & 1) ? -(float)Z.coeff : (float)Z.coeff;
-                            }
-                        }
-                        eacc += (v[j].x * v[j].x + v[j].y * v[j].y) * ez[j];
-                        if (A.lam)
-                            A.lam[tile_x(P, t_id, (uint32_t)(base | (j << s)))] = make_float2(ez[j] * v[j].x, ez[j] * v[j].y);
-                    }
-                }
-            }
+            group_epilogue(A, P, g, t_id, base, s, v, eacc, eacc, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab);
             if (g < P.ngroups - 1) {
                 store16(v, p, stride);
                 __syncthreads();
@@ -294,6 +312,275 @@ size_t dense_pass_smem() {
     return 2 * (size_t)padded_amps(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
            kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * (sizeof(DenseClassDev) + sizeof(DensePassClassDev)) +
            2 * kMaxLayerClasses * sizeof(int32_t) + 16 * sizeof(float);
+}
+
+// ---- tensor-core passes (mixed precision: split TF32 products, FP32 accumulation) ----------
+//
+// A register group's rotations (up to four, on the group's four tile bits) form one 16 x 16
+// complex block U = R_3 (x) R_2 (x) R_1 (x) R_0 acting on a thread's 16 amplitudes, y = U a.
+// Written in real arithmetic on a row of 32 reals [Re a_0..a_15 | Im a_0..a_15] this is one
+// product with the 32 x 32 matrix M = [[Re U, -Im U], [Im U, Re U]]. On the tensor cores
+// (tcgen05, kind::tf32, FP32 accumulators in tensor memory) a group is then one GEMM per 128
+// rows of the tile: A = the rows (tensor memory, written by the threads with tcgen05.st),
+// B = M in the K-major layout (shared memory), D = the rotated rows (tensor memory).
+// FP32 accuracy comes from splitting both operands into TF32 parts, x = x_hi + x_lo with x_hi
+// and x_lo rounded to TF32 (|x - x_hi - x_lo| <= 2^-22 |x|): D = A_hi [B_hi | B_lo] +
+// A_lo B_hi, where [B_hi | B_lo] stacks the two parts of M along N (N = 64; the two 32-column
+// halves of D are added when D is read back) and the dropped A_lo B_lo is at most 2^-22 of the
+// product. The diagonal layers and the energy stay on the CUDA cores, unchanged.
+//
+// dense_tc_pass_kernel: one CTA per SM, 512 threads as two independent halves of 256 (named
+// barriers 1 and 2), each streaming its own tiles (double-buffered with cp.async) through the
+// pass's groups, as dense_pass_kernel does. The halves share the B operands of the pass's
+// groups (8 KB each, built once per CTA from the gate table) and the staged class tables; each
+// half owns 256 of the CTA's 512 tensor-memory columns: per 128-row chunk, A_hi (32 columns),
+// A_lo (32) and D (64). One thread per half issues the 16 MMAs of a group (2 chunks x 4 K-steps
+// x 2 products) and commits them to the half's mbarrier, which every thread of the half waits
+// on (bounded: an MMA that has not completed after 1 s sets error word 4 and the CTA stops).
+
+constexpr int kTcPassThreads = 2 * kThreads;
+constexpr int kTcBlockBytes = 8192;       // one group's B: 4 K-steps x (64 rows x 8 TF32)
+constexpr int kTcTmemCols = 512;
+constexpr int kMaxSms = 1024;             // bound on the tensor-core pass grid (norm partials)
+
+// Offsets in the dynamic shared memory of the tensor-core pass kernel for nblk B blocks:
+// [0] tiles (2 halves x 2 buffers), [1] B blocks, [2] phase tables, [3] distance words,
+// [4] classes, [5] split counts, [6] word offsets, [7] table offsets, [8] energy partials,
+// [9] mbarriers, [10] tensor-memory address, [11] total.
+__host__ __device__ inline void tc_pass_layout(int nblk, size_t (&off)[12]) {
+    size_t o = 0;
+    auto put = [&](int k, size_t bytes, size_t align) {
+        o = (o + align - 1) / align * align;
+        off[k] = o;
+        o += bytes;
+    };
+    put(0, 4 * (size_t)padded_amps(kDenseTileBits) * sizeof(float2), 1024);
+    put(1, (size_t)nblk * kTcBlockBytes, 1024);
+    put(2, kMaxTab * sizeof(float2), 16);
+    put(3, kMaxDistWords * sizeof(int32_t), 16);
+    put(4, kMaxLayerClasses * sizeof(DenseClassDev), 16);
+    put(5, kMaxLayerClasses * sizeof(DensePassClassDev), 16);
+    put(6, kMaxLayerClasses * sizeof(int32_t), 16);
+    put(7, kMaxLayerClasses * sizeof(int32_t), 16);
+    put(8, 4 * (kThreads / 32) * sizeof(float), 16);
+    put(9, 2 * sizeof(uint64_t), 8);
+    put(10, sizeof(uint32_t), 4);
+    off[11] = o;
+}
+
+// B operand of every rotation group of the pass: M = [[Re U, -Im U], [Im U, Re U]] (row n =
+// output real, column k = input real), rounded TF32 parts in rows 0..31 (hi) and 32..63 (lo),
+// K-major core matrices (8 rows x 16 bytes; 128 bytes apart along K, 256 along N), one 2 KB
+// block per K-step of 8. Entries of U are products of the four 2 x 2 factors, in FP64 from the
+// FP32 (cos, sin) of the gate table.
+__device__ void build_tc_blocks(const DensePassDev& P, const tlq_gate* gates, const float2* GT, unsigned char* bblk,
+                                int tid, int nthreads) {
+    for (int e = tid; e < P.ngroups * 1024; e += nthreads) {
+        const int g = e >> 10, n = (e >> 5) & 31, k = e & 31;
+        const unsigned m = P.group_mask[g];
+        if (m == 0) continue;
+        const int i = n & 15, j = k & 15;
+        double ur = 1.0, ui = 0.0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int ib = (i >> b) & 1, jb = (j >> b) & 1;
+            double fr = ib == jb ? 1.0 : 0.0, fi = 0.0;
+            if ((m >> b) & 1u) {
+                const int gate = P.gate[g][b];
+                const float2 cs = GT[gate];
+                if (ib == jb) fr = (double)cs.x;
+                else if (gates[gate].kind == TLQ_RY) fr = ib ? (double)cs.y : -(double)cs.y;   // [[c,-s],[s,c]]
+                else { fr = 0.0; fi = -(double)cs.y; }                                           // [[c,-is],[-is,c]]
+            }
+            const double nr = ur * fr - ui * fi, ni = ur * fi + ui * fr;
+            ur = nr;
+            ui = ni;
+        }
+        const double mv = n < 16 ? (k < 16 ? ur : -ui) : (k < 16 ? ui : ur);
+        const float mh = tc::tf32_rna((float)mv);
+        const float ml = tc::tf32_rna((float)(mv - (double)mh));
+        const int kk = k >> 3, kin = k & 7;
+        const int o = g * kTcBlockBytes + kk * 2048 + (n >> 3) * 256 + (kin >> 2) * 128 + (n & 7) * 16 + (kin & 3) * 4;
+        *reinterpret_cast<float*>(bblk + o) = mh;
+        *reinterpret_cast<float*>(bblk + o + 4 * 256) = ml;   // row n + 32
+    }
+}
+
+// The 16 MMAs of one group for one half: tm = the half's tensor-memory columns, b = the
+// group's B block (shared address).
+__device__ __forceinline__ void issue_group_mmas(uint32_t tm, uint32_t b) {
+    constexpr uint32_t kN64 = tc::idesc_tf32(128, 64), kN32 = tc::idesc_tf32(128, 32);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t bd = tc::sdesc(b + kk * 2048, 128, 256);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const uint32_t cb = tm + 128 * c;
+            tc::mma_tf32_ts(cb + 64, cb + 8 * kk, bd, kN64, kk > 0 ? 1u : 0u);   // A_hi [B_hi | B_lo]
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t bd = tc::sdesc(b + kk * 2048, 128, 256);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const uint32_t cb = tm + 128 * c;
+            tc::mma_tf32_ts(cb + 64, cb + 32 + 8 * kk, bd, kN32, 1u);              // A_lo B_hi
+        }
+    }
+}
+
+// Rotate the thread's 16 amplitudes by group g's block on the tensor cores (every thread of
+// the half calls this). taddr = this thread's lanes and chunk columns; tm = the half's
+// columns; returns false (uniformly over the half) when the MMAs did not complete in time.
+__device__ __forceinline__ bool tc_rotate(float2 (&v)[16], uint32_t taddr, uint32_t tm, uint32_t bblock, int th,
+                                          int bar_id, uint64_t* bar, uint32_t& phase) {
+    float hi[16], lo[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        hi[j] = tc::tf32_rna(v[j].x);
+        lo[j] = tc::tf32_rna(v[j].x - hi[j]);
+    }
+    tc::tmem_st16(taddr + 0, hi);
+    tc::tmem_st16(taddr + 32, lo);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        hi[j] = tc::tf32_rna(v[j].y);
+        lo[j] = tc::tf32_rna(v[j].y - hi[j]);
+    }
+    tc::tmem_st16(taddr + 16, hi);
+    tc::tmem_st16(taddr + 48, lo);
+    tc::tmem_wait_st();
+    tc::fence_before();
+    tc::bar_sync(bar_id, kThreads);
+    if (th == 0) {
+        tc::fence_after();
+        issue_group_mmas(tm, bblock);
+        tc::commit(bar);
+    }
+    const bool ok = tc::mbar_wait(bar, phase);
+    phase ^= 1u;
+    if (tc::bar_or(bar_id, kThreads, !ok)) return false;
+    tc::fence_after();
+    float d0[16], d1[16];
+    tc::tmem_ld16x2(taddr + 64, taddr + 96, d0, d1);    // Re y: A B_hi part, A_hi B_lo part
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j].x = d0[j] + d1[j];
+    tc::tmem_ld16x2(taddr + 80, taddr + 112, d0, d1);   // Im y
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j].y = d0[j] + d1[j];
+    tc::fence_before();   // the loads are ordered before the next group's MMAs by the next barrier
+    return true;
+}
+
+__global__ void __launch_bounds__(kTcPassThreads, 1) dense_tc_pass_kernel(const __grid_constant__ PassArgs A, int nblk) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    size_t off[12];
+    tc_pass_layout(nblk, off);
+    float2* tiles = reinterpret_cast<float2*>(smem_raw + off[0]);
+    unsigned char* bblk = smem_raw + off[1];
+    float2* s_tab = reinterpret_cast<float2*>(smem_raw + off[2]);
+    int32_t* s_dist = reinterpret_cast<int32_t*>(smem_raw + off[3]);
+    DenseClassDev* s_cls = reinterpret_cast<DenseClassDev*>(smem_raw + off[4]);
+    DensePassClassDev* s_pcd = reinterpret_cast<DensePassClassDev*>(smem_raw + off[5]);
+    int32_t* s_woff = reinterpret_cast<int32_t*>(smem_raw + off[6]);
+    int32_t* s_toff = reinterpret_cast<int32_t*>(smem_raw + off[7]);
+    float* s_red = reinterpret_cast<float*>(smem_raw + off[8]);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + off[9]);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_raw + off[10]);
+    const DensePassDev& P = A.pass;
+    const int tid = threadIdx.x;
+    const int h = tid >> 8, th = tid & (kThreads - 1);   // half, thread within the half
+    const int warp = tid >> 5, lane = tid & 31;
+    const int bar_id = 1 + h;
+    const uint32_t ntiles = 1u << (A.n_eff - kDenseTileBits);
+    const uint32_t first = 2u * blockIdx.x + (uint32_t)h, step = 2u * gridDim.x;
+    float2* buf0 = tiles + 2 * h * padded_amps(kDenseTileBits);
+
+    if (first < ntiles) issue_tile(P, first, A.state, buf0, th);
+    if (tid == 0) {
+        tc::mbar_init(&bars[0], 1);
+        tc::mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, kTcTmemCols);
+    build_tc_blocks(P, A.gates, A.GT, bblk, tid, kTcPassThreads);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B is read by the tensor core
+    stage_classes<kTcPassThreads>(P, A.classes, A.pcd, A.stage, A.dists, A.ptab, s_cls, s_pcd, s_woff, s_toff,
+                                  s_dist, s_tab, tid);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t tm = tmem + 256u * (uint32_t)h;                       // this half's columns
+    const uint32_t taddr = tm + 128u * (uint32_t)(th >> 7) + ((uint32_t)(32 * (warp & 3)) << 16);
+    const uint32_t bbase = tc::su32(bblk);
+    uint32_t phase = 0;
+    bool bad = false;
+
+    float eacc = 0.f, nacc = 0.f;
+    int i = 0;
+    for (uint32_t t_id = first; t_id < ntiles && !bad; t_id += step, ++i) {
+        const int b = i & 1;
+        float2* tile = buf0 + b * padded_amps(kDenseTileBits);
+        wait_tiles();
+        tc::bar_sync(bar_id, kThreads);
+        const uint32_t next = t_id + step;
+        if (next < ntiles) issue_tile(P, next, A.state, buf0 + (b ^ 1) * padded_amps(kDenseTileBits), th);
+        for (int g = 0; g < P.ngroups; ++g) {
+            const int s = P.group_s[g];
+            const int stride = pass_stride(s);
+            const int base = (th & ((1 << s) - 1)) | ((th >> s) << (s + 4));
+            float2* p = tile + pad16(base);
+            float2 v[16];
+            load16(v, p, stride);
+            if (P.group_mask[g] != 0 &&
+                !tc_rotate(v, taddr, tm, bbase + (uint32_t)(g * kTcBlockBytes), th, bar_id, &bars[h], phase)) {
+                bad = true;
+                break;
+            }
+            group_epilogue<true>(A, P, g, t_id, base, s, v, eacc, nacc, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab);
+            if (g < P.ngroups - 1) {
+                store16(v, p, stride);
+                tc::bar_sync(bar_id, kThreads);
+            } else if (P.store) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) A.state[tile_x(P, t_id, (uint32_t)(base | (j << s)))] = v[j];
+            }
+        }
+        if (!bad) tc::bar_sync(bar_id, kThreads);   // the buffer is free for the next copy
+    }
+    wait_tiles();   // no copy of this thread is left in flight
+    if (P.measure_group >= 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
+            nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
+        }
+        if (lane == 0) {
+            s_red[h * (kThreads / 32) + (warp & 7)] = eacc;
+            s_red[2 * (kThreads / 32) + h * (kThreads / 32) + (warp & 7)] = nacc;
+        }
+        tc::bar_sync(bar_id, kThreads);
+        if (th == 0) {
+            float e = 0.f, nn = 0.f;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                e += s_red[h * (kThreads / 32) + w];
+                nn += s_red[2 * (kThreads / 32) + h * (kThreads / 32) + w];
+            }
+            A.partial[(size_t)h * gridDim.x + blockIdx.x] = (double)e;
+            A.npartial[(size_t)h * gridDim.x + blockIdx.x] = (double)nn;   // <psi|psi> partials
+        }
+    }
+    if (bad) {
+        if (th == 0) {
+            atomicOr(A.err, 4);
+            tc::mbar_wait(&bars[h], phase ^ 1u);   // the group's MMAs, once more (bounded)
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTcTmemCols);
 }
 
 // ---- adjoint passes (gradient) ----------------------------------------------------------------
@@ -593,6 +880,24 @@ __global__ void reduce_partials_kernel(const double* partial, int n, double coef
     *out = acc.value();
 }
 
+// Tensor-core mode: divide the energy (and the gradient) by <psi|psi> = sum of the norm
+// partials (FP64, fixed order). In exact arithmetic the state has unit norm and nothing
+// changes; the tensor cores' FP32 accumulation truncates, which shrinks the state by a nearly
+// uniform factor over the passes, and the ratio cancels that factor to first order.
+__global__ void normalize_kernel(const double* npart, int n, double* energy, double* grad, int n_params) {
+    __shared__ double s_norm;
+    if (threadIdx.x == 0) {
+        Neumaier acc;
+        for (int i = 0; i < n; ++i) acc.add(npart[i]);
+        s_norm = acc.value();
+    }
+    __syncthreads();
+    const double inv = 1.0 / s_norm;
+    if (threadIdx.x == 0) *energy *= inv;
+    if (grad)
+        for (int p = threadIdx.x; p < n_params; p += blockDim.x) grad[p] *= inv;
+}
+
 // ---- plain per-gate sweeps (baseline) -----------------------------------------------------
 
 // sgn = -1 applies the inverse rotation (adjoint sweep)
@@ -779,10 +1084,14 @@ __global__ void init_state_kernel(float2* psi, uint64_t N) {
 
 }  // namespace
 
-size_t dense_partial_count(int n_eff) {
+// Energy partials (one per CTA of a pass, or per measurement block), then, from
+// dense_norm_offset on, the tensor-core passes' norm partials (two per CTA, one CTA per SM).
+size_t dense_norm_offset(int n_eff) {
     const size_t tiles = (size_t)1 << (n_eff - kDenseTileBits);
     return tiles > (size_t)kMeasBlocks ? tiles : (size_t)kMeasBlocks;
 }
+
+size_t dense_partial_count(int n_eff) { return dense_norm_offset(n_eff) + 2 * kMaxSms; }
 
 int dense_grid(int n_eff, int sm_count) {
     const int ntiles = 1 << (n_eff - kDenseTileBits);
@@ -852,6 +1161,19 @@ int launch_dense(DenseLaunch& L, void* stream) {
     const size_t asmem = dense_adjoint_smem();
     if ((e = cudaFuncSetAttribute(dense_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return (int)e;
+    size_t tc_smem = 0;
+    int tc_nblk = 0;
+    if (L.tc && !L.per_gate) {
+        const DensePassDev* fw = L.product_init ? L.host_fwd_passes : L.host_passes;
+        const int nf = L.product_init ? L.n_fwd_passes : L.n_passes;
+        for (int p = 0; p < nf; ++p) tc_nblk = fw[p].ngroups > tc_nblk ? fw[p].ngroups : tc_nblk;
+        size_t off[12];
+        tc_pass_layout(tc_nblk, off);
+        tc_smem = off[11];
+        if ((e = cudaFuncSetAttribute(dense_tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)tc_smem)) != cudaSuccess)
+            return (int)e;
+    }
     if (L.grad && !L.per_gate &&
         (e = cudaFuncSetAttribute(dense_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem)) !=
             cudaSuccess)
@@ -904,9 +1226,12 @@ int launch_dense(DenseLaunch& L, void* stream) {
             A.state = psi;
             A.n_eff = L.n_eff;
             A.partial = L.partial;
+            A.npartial = L.partial + dense_norm_offset(L.n_eff);
             A.err = L.err;
             A.lam = nullptr;
             const int grid = dense_grid(L.n_eff, L.sm_count);
+            const int ntiles = 1 << (L.n_eff - kDenseTileBits);
+            const int tc_grid = std::min(std::min((ntiles + 1) / 2, L.sm_count), kMaxSms);   // one CTA per SM
             bool measured = false;
             const DensePassDev* fwd = product_init ? L.host_fwd_passes : L.host_passes;
             const int n_fwd = product_init ? L.n_fwd_passes : L.n_passes;
@@ -916,12 +1241,13 @@ int launch_dense(DenseLaunch& L, void* stream) {
                     A.pass.store = 1;   // the adjoint starts from the final state in HBM
                     if (A.pass.measure_group >= 0) A.lam = lam;
                 }
-                dense_pass_kernel<<<grid, kThreads, smem, st>>>(A);
+                if (L.tc) dense_tc_pass_kernel<<<tc_grid, kTcPassThreads, tc_smem, st>>>(A, tc_nblk);
+                else dense_pass_kernel<<<grid, kThreads, smem, st>>>(A);
                 ++launches;
                 if (A.pass.measure_group >= 0) measured = true;
             }
             if (measured) {
-                reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, grid, 1.0, eout, 1);
+                reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, L.tc ? 2 * tc_grid : grid, 1.0, eout, 1);
                 ++launches;
             }
             for (int t = 0; t < L.n_xterms; ++t) {
@@ -959,6 +1285,11 @@ int launch_dense(DenseLaunch& L, void* stream) {
                                                                                  L.n_params, gout);
                     ++launches;
                 }
+            }
+            if (L.tc && measured) {
+                normalize_kernel<<<1, 256, 0, st>>>(L.partial + dense_norm_offset(L.n_eff), 2 * tc_grid, eout, gout,
+                                                    L.n_params);
+                ++launches;
             }
         }
         if (b == L.B - 1 && L.ev_end && (e = cudaEventRecord((cudaEvent_t)L.ev_end, st)) != cudaSuccess) return (int)e;

@@ -452,6 +452,7 @@ struct DenseLaunch {
     double* energy = nullptr;             // [B]
     double* grad = nullptr;               // [B][n_params] or null (energies only)
     bool per_gate = false;                // plain per-gate sweeps (baseline)
+    bool tc = false;                      // forward rotation groups on the tensor cores (TLQ_MIXED_TC)
     int sm_count = 0;
     void* ev_begin = nullptr;
     void* ev_end = nullptr;

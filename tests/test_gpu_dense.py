@@ -261,3 +261,33 @@ def test_dense_largest_state_n31(tlq):
     prob = W.Problem(n=31, gates=one.gates, n_params=one.n_params, terms=one.terms, theta=one.theta)
     E, _ = _energy(tlq, prob)
     check_energy(E, [m * math.cos(b) ** 2 for b in one.theta[:, 1]])
+
+
+def _golden(name):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed_tc"])
+def test_qaoa_n28_p4_vs_golden_oracle(tlq, prec):
+    """Full size, general angles: energy and gradient of the n=28, p=4 QAOA circuit against the
+    complex128 oracle's values stored in tests/golden/qaoa_n28_p4.json."""
+    from paper_2112_10239_gb300 import binding as B
+    g = _golden("qaoa_n28_p4.json")
+    gates = [tuple(x) for x in g["gates"]]
+    terms = [(c, tuple(s), l) for c, s, l in g["terms"]]
+    theta = np.array([g["theta"]], dtype=np.float64)
+    c = tlq.circuit(g["n"], gates, g["n_params"])
+    h = tlq.hamiltonian(g["n"], terms)
+    mode = {"fp32": B.TLQ_FP32, "mixed_tc": B.TLQ_MIXED_TC}[prec]
+    try:
+        E, G = B.tlq_expectation_grad(tlq.h, c.h, h.h, theta, mode)
+        E2 = B.tlq_expectation(tlq.h, c.h, h.h, theta, mode)
+    finally:
+        c.close()
+        h.close()
+    check_energy(E, [g["energy"]])
+    check_energy(E2, [g["energy"]])
+    check_grad(G, np.array([g["grad"]]))
