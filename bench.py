@@ -179,6 +179,80 @@ def algorithmic_flops(B_mod, ctx, c, h, prob, grad=True):
     return float(np.sum(f)) * prob.B
 
 
+def unfused_flops(prob, grad=True):
+    """The scope table's algorithmic count for a layered brick-wall Ising workload: every term
+    contracted over its own exact causal cone (no window sharing). For a term with support
+    [a, b] the live rotations of layer l (1..L) span [a - (L - l), b + (L - l)] clipped to the
+    chain (ZZ: width 2 + 2(L - l); X: 3 + 2(L - l), counting the two CZ neighbours of the last
+    layer); the window is the layer-1 span. Forward flops 2^W (6 sum_l live_l + 6 D + 8), with
+    D = L diagonal layers for X terms and L - 1 for Z-only terms (the last layer's diagonal
+    commutes with them); the adjoint is counted as three times the forward. Per batch."""
+    n, L = prob.n, prob.meta.get("L")
+    if L is None or prob.meta.get("layout") != "brickwall":
+        return None, None
+    fwd = 0.0
+    for _, sites, letters in prob.terms:
+        a, b = min(sites), max(sites)
+        zonly = set(letters) <= {"Z"}
+        if not zonly:           # X/Y: the CZs of the last layer reach one site further
+            a, b = a - 1, b + 1
+        live = [min(n - 1, b + (L - l)) - max(0, a - (L - l)) + 1 for l in range(1, L + 1)]
+        W = live[0]
+        D = L - 1 if zonly else L
+        fwd += 2.0 ** W * (6 * sum(live) + 6 * D + 8)
+    fwd *= prob.B
+    return fwd, (4 * fwd if grad else fwd)
+
+
+def fp64_errors(E, G, E_ref, G_ref):
+    """Max relative energy error |E - E_ref| / max(|E_ref|, 1) and gradient error
+    ||G - G_ref||_inf / max(1, ||G_ref||_inf) of a timed result against its FP64 reference."""
+    E, E_ref = np.asarray(E, dtype=np.float64), np.asarray(E_ref, dtype=np.float64)
+    out = {"energy_max_rel": float(np.max(np.abs(E - E_ref) / np.maximum(np.abs(E_ref), 1.0)))}
+    if G is not None and G_ref is not None:
+        G, G_ref = np.asarray(G, dtype=np.float64), np.asarray(G_ref, dtype=np.float64)
+        out["grad_inf_rel"] = float(np.max(np.abs(G - G_ref)) / max(1.0, float(np.max(np.abs(G_ref)))))
+    return out
+
+
+def fp64_reference(B, ctx, c, h, theta, grad=True):
+    """The same inputs through the complex128 mode of the same kernels (TLQ_FP64_REF), untimed."""
+    if grad:
+        return B.tlq_expectation_grad(ctx.h, c.h, h.h, theta, B.TLQ_FP64_REF)
+    return B.tlq_expectation(ctx.h, c.h, h.h, theta, B.TLQ_FP64_REF), None
+
+
+def plain_one_set_per_call(B, ctx, c, h, prob, dev, flush, grad=True, reps=3):
+    """The plain per-circuit path: the same kernels called once per parameter set (B = 1),
+    device pointers, all sets of the batch in sequence; device time with CUDA events (median
+    of `reps` sweeps, L2 flushed before each sweep). Returns (ms per batch, launches per batch)."""
+    import torch
+    Bsz, P = prob.theta.shape
+    stream = torch.cuda.current_stream(dev)
+    theta_d = torch.tensor(prob.theta, dtype=torch.float64, device=dev)
+    E_d = torch.empty(Bsz, dtype=torch.float64, device=dev)
+    G_d = torch.empty(Bsz, P, dtype=torch.float64, device=dev)
+
+    def sweep():
+        for b in range(Bsz):
+            B.tlq_expectation_grad_dev(ctx.h, c.h, h.h, theta_d[b].data_ptr(), 1, B.TLQ_FP32, E_d[b:].data_ptr(),
+                                       G_d[b].data_ptr() if grad else None, stream.cuda_stream)
+
+    B.tlq_profile_enable(ctx.h, False)
+    sweep()
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sweep()
+        b.record(stream)
+        b.synchronize()
+        t.append(a.elapsed_time(b))
+    return float(np.median(t))
+
+
 def run_reference(args, rank):
     """CPU oracle arm: each step evaluates energy + gradient of a sample of the workload's
     parameter sets with the complex128 statevector and its adjoint."""
@@ -336,9 +410,10 @@ def dense_bytes(B, ctx, c, h, grad):
     return total, n_fwd
 
 
-def device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3, mps=False):
+def device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3, mps=False, prec=None):
     """Time `steps` device-pointer calls (inputs resident, L2 flushed between steps); mps=True
     times the exact MPS route (tlq_mps_expectation_grad_dev) instead of the default path."""
+    prec = B.TLQ_FP32 if prec is None else prec
     import torch
     Bsz, P = prob.theta.shape
     stream = torch.cuda.current_stream(dev)
@@ -349,7 +424,7 @@ def device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3, mps=Fals
     call = B.tlq_mps_expectation_grad_dev if mps else B.tlq_expectation_grad_dev
 
     def step():
-        call(ctx.h, c.h, h.h, theta_d.data_ptr(), Bsz, B.TLQ_FP32, E_d.data_ptr(),
+        call(ctx.h, c.h, h.h, theta_d.data_ptr(), Bsz, prec, E_d.data_ptr(),
              G_d.data_ptr() if grad else None, stream.cuda_stream)
 
     for _ in range(warmup):
@@ -392,36 +467,64 @@ def mps_workload(B, dev, local, flush, peaks, name, steps=5, warmup=3):
                          "traffic": None}}
 
 
-def extra_workloads(B, dev, local, flush, peaks):
-    """The other workloads, each with its own throughput and roofline (not the headline)."""
-    import ctypes
+def golden_qaoa28():
+    """The complex128 oracle's energy and gradient of the n=28, p=4 QAOA workload (seed 2),
+    written by tests/golden/make_golden.py --large; None when absent."""
+    path = os.path.join(ROOT, "tests", "golden", "qaoa_n28_p4.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f)
+
+
+def fp32_peak_tflops(peaks):
+    return SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
+def n500_workload(B, dev, local, flush, peaks):
+    """The n=500, L=4 Ising chain, 256 sets, energy + gradient (the paper's n=500 shape): one
+    batched launch, the plain per-circuit path (one set per call) beside it, FP64 error."""
     from paper_2112_10239_gb300 import workloads as W
-    out = {}
-    # n=500, L=4 transverse-field Ising chain, 256 sets, energy + gradient (the paper's n=500 shape)
     prob = W.tfim_n500_L4_B256()
     with B.Context(device=local) as ctx:
         c, h = ctx.problem(prob)
         B.tlq_profile_enable(ctx.h, True)
         ms, kms, nl = device_steps(B, ctx, c, h, prob, True, 5, dev, flush)
         flops = algorithmic_flops(B, ctx, c, h, prob, grad=True)
-        peak = 152 * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-        out["tfim_n500_L4_B256"] = {
-            "value": prob.B / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "launches": nl,
-            "roofline": {"bound": "alu", "achieved": flops / (kms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                         "frac": flops / (kms * 1e-3) / 1e12 / peak, "kernel_ms": kms}}
+        _, flops_unf = unfused_flops(prob)
+        E, G = B.tlq_expectation_grad(ctx.h, c.h, h.h, prob.theta)
+        E64, G64 = fp64_reference(B, ctx, c, h, prob.theta)
+        plain_ms = plain_one_set_per_call(B, ctx, c, h, prob, dev, flush)
         c.close()
         h.close()
-    # the exact MPS route on the two Ising batches (bond dimension 16 and 64), beside the cone path
-    for name in ("tfim_n500_L4_B256", "tfim_n20_L6_B64"):
-        out["mps_" + name] = mps_workload(B, dev, local, flush, peaks, name, steps=3)
-    # n=8, L=2, one set: latency of the synchronous call (launch-bound; no roofline)
-    out["tfim_n8_L2_B1_latency"] = latency_n8(B, local)
-    # n=28 QAOA on a 3-regular graph (dense statevector): energy and energy + gradient, fused
-    # passes vs the plain per-gate sweeps
+    peak = fp32_peak_tflops(peaks)
+    ach = flops / (kms * 1e-3) / 1e12
+    return {"value": prob.B / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "launches": nl,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "kernel_ms": kms, "algorithmic_flops": flops, "algorithmic_flops_unfused": flops_unf,
+                         "frac_unfused": flops_unf / (kms * 1e-3) / 1e12 / peak,
+                         "traffic": NCU_TRAFFIC.get(("tfim_n500_L4_B256", "cone_kernel"))},
+            "err_vs_fp64": fp64_errors(E, G, E64, G64),
+            "plain_path": {"kind": "one parameter set per call (B = 1), same kernels", "ms_per_batch": plain_ms,
+                           "value": prob.B / (plain_ms * 1e-3), "unit": UNIT},
+            "speedup_vs_plain": plain_ms / ms}
+
+
+def qaoa28_workload(B, dev, local, flush, peaks):
+    """n=28 QAOA on a 3-regular graph (dense statevector): energy and energy + gradient with the
+    FP32 register passes, with the tensor-core blocks (TLQ_MIXED_TC), and with the plain
+    per-gate FP32 sweeps; errors against the complex128 oracle's stored values."""
+    import ctypes
+    from paper_2112_10239_gb300 import workloads as W
     prob = W.qaoa_n28_p4()
+    gold = golden_qaoa28()
+    if gold is not None and not np.array_equal(np.asarray(gold["theta"]), prob.theta[0]):
+        gold = None
     res = {}
-    for name, fk, grad, steps in (("fused", 0, False, 5), ("fused_grad", 0, True, 5),
-                                  ("per_gate", 1, False, 2), ("per_gate_grad", 1, True, 1)):
+    for name, fk, prec, grad, steps in (("fused", 0, B.TLQ_FP32, False, 5), ("fused_grad", 0, B.TLQ_FP32, True, 5),
+                                        ("tc", 0, B.TLQ_MIXED_TC, False, 5), ("tc_grad", 0, B.TLQ_MIXED_TC, True, 5),
+                                        ("per_gate", 1, B.TLQ_FP32, False, 2),
+                                        ("per_gate_grad", 1, B.TLQ_FP32, True, 1)):
         cfg = B.tlq_config(local, 0, 0, B.TLQ_FP32, fk)
         hnd = ctypes.c_void_p()
         B._check(B.lib().tlq_init(ctypes.byref(cfg), ctypes.byref(hnd)))
@@ -429,43 +532,131 @@ def extra_workloads(B, dev, local, flush, peaks):
         ctx.h = hnd
         c, h = ctx.problem(prob)
         B.tlq_profile_enable(ctx.h, True)
-        ms, kms, nl = device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3 if fk == 0 else 1)
+        ms, kms, nl = device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3 if fk == 0 else 1,
+                                   prec=prec)
         nbytes, passes = dense_bytes(B, ctx, c, h, grad)
-        res[name] = (ms, kms, nl, nbytes, passes)
+        err = None
+        if gold is not None and fk == 0:
+            B.tlq_profile_enable(ctx.h, False)
+            if grad:
+                E, G = B.tlq_expectation_grad(ctx.h, c.h, h.h, prob.theta, prec)
+                err = fp64_errors(E, G, [gold["energy"]], [gold["grad"]])
+            else:
+                err = fp64_errors(B.tlq_expectation(ctx.h, c.h, h.h, prob.theta, prec), None, [gold["energy"]], None)
+        res[name] = (ms, kms, nl, nbytes, passes, err)
         c.close()
         h.close()
         ctx.close()
 
     def hbm(key, kernel):
-        ms, kms, nl, nbytes, passes = res[key]
+        ms, kms, nl, nbytes, passes, _ = res[key]
         achieved = nbytes / (kms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                 "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None, "kernel": kernel,
                 "kernel_ms": kms, "bytes_per_eval": nbytes}
 
+    ref = "complex128 CPU oracle (tests/golden/qaoa_n28_p4.json)" if gold is not None else None
+    out = {}
     out["qaoa_n28_p4"] = {
         "value": 1.0 / (res["fused"][0] * 1e-3), "unit": "evals/s", "ms_per_eval": res["fused"][0],
-        "per_gate_ms_per_eval": res["per_gate"][0], "speedup_vs_per_gate": res["per_gate"][0] / res["fused"][0],
         "passes": res["fused"][4], "launches": res["fused"][2],
-        "roofline": hbm("fused", "dense_pass_kernel x passes (read + write of the 2 GiB state each)")}
+        "roofline": hbm("fused", "dense_pass_kernel x passes (read + write of the 2 GiB state each)"),
+        "err_vs_fp64": res["fused"][5], "fp64_reference": ref,
+        "plain_path": {"kind": "per-gate FP32 statevector sweeps", "ms_per_eval": res["per_gate"][0]},
+        "speedup_vs_plain": res["per_gate"][0] / res["fused"][0],
+        "mixed_tc": {"ms_per_eval": res["tc"][0], "value": 1.0 / (res["tc"][0] * 1e-3), "launches": res["tc"][2],
+                     "roofline": hbm("tc", "dense_tc_pass_kernel x passes (tcgen05 kind::tf32 split blocks)"),
+                     "err_vs_fp64": res["tc"][5], "speedup_vs_plain": res["per_gate"][0] / res["tc"][0],
+                     "vs_fp32_fused": res["fused"][0] / res["tc"][0]}}
     out["qaoa_n28_p4_grad"] = {
         "value": 1.0 / (res["fused_grad"][0] * 1e-3), "unit": "grad-evals/s", "ms_per_eval": res["fused_grad"][0],
-        "per_gate_ms_per_eval": res["per_gate_grad"][0],
-        "speedup_vs_per_gate": res["per_gate_grad"][0] / res["fused_grad"][0],
         "launches": res["fused_grad"][2],
         "roofline": hbm("fused_grad", "forward dense_pass_kernel x passes, then dense_adjoint_kernel x passes "
-                                      "(psi and lam read + written)")}
+                                      "(psi and lam read + written)"),
+        "err_vs_fp64": res["fused_grad"][5], "fp64_reference": ref,
+        "plain_path": {"kind": "per-gate FP32 statevector sweeps", "ms_per_eval": res["per_gate_grad"][0]},
+        "speedup_vs_plain": res["per_gate_grad"][0] / res["fused_grad"][0],
+        "mixed_tc": {"ms_per_eval": res["tc_grad"][0], "err_vs_fp64": res["tc_grad"][5],
+                     "speedup_vs_plain": res["per_gate_grad"][0] / res["tc_grad"][0],
+                     "vs_fp32_fused": res["fused_grad"][0] / res["tc_grad"][0]}}
+    return out
+
+
+SERVING_RATES = (100.0, 300.0, 1000.0, 2000.0, 5000.0)
+SERVING_REQUESTS = 10000
+
+
+def extra_workloads(B, dev, local, flush, peaks):
+    """The other workloads, each with its own throughput and roofline (not the headline)."""
+    out = {}
+    out["tfim_n500_L4_B256"] = n500_workload(B, dev, local, flush, peaks)
+    # the exact MPS route on the two Ising batches (bond dimension 16 and 64), beside the cone path
+    for name in ("tfim_n500_L4_B256", "tfim_n20_L6_B64"):
+        out["mps_" + name] = mps_workload(B, dev, local, flush, peaks, name, steps=3)
+    # n=8, L=2, one set: latency of the synchronous call (launch-bound; no roofline)
+    out["tfim_n8_L2_B1_latency"] = latency_n8(B, local)
+    out.update(qaoa28_workload(B, dev, local, flush, peaks))
     # partial traces of an n=20 state down to m=14 and m=10 qubits (the paper's density-operator
-    # sizes): rho_A = Psi Psi^dagger; FP32 ALU-bound (m=14 also writes a 2 GiB output)
+    # sizes): rho_A = Psi Psi^dagger
     out.update(partial_trace_workloads(B, dev, local, flush, peaks))
-    # serving: Poisson arrivals, continuous batching vs one request at a time
-    out["serving"] = serving_replay(B, local, 2000, 2000.0)
-    # offered-rate sweep of the batched server (below, near and above its capacity)
+    # serving: Poisson arrivals of 10,000 requests at each offered rate, continuous batching; the
+    # plain path (one request at a time through the synchronous calls) at 2000 requests/s
     sweep = []
-    for rate, count in ((300.0, 600), (1000.0, 1500), (5000.0, 3000)):
-        r = serving_replay(B, local, count, rate, seed=5, plain_path=False)
-        sweep.append({"rate_per_s": rate, "requests": count, **r["batched"]})
+    for rate in SERVING_RATES:
+        r = serving_replay(B, local, SERVING_REQUESTS, rate, seed=4, plain_path=(rate == 2000.0))
+        entry = {"rate_per_s": rate, "requests": SERVING_REQUESTS, **r["batched"]}
+        if "one_at_a_time" in r:
+            entry["one_at_a_time"] = r["one_at_a_time"]
+        sweep.append(entry)
     out["serving_sweep"] = sweep
+    return out
+
+
+def summary_of(line, extras):
+    """A compact digest of every workload's headline figures (kept short: it closes the line)."""
+    def g(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+
+    def r3(x):
+        return None if x is None else float(f"{x:.4g}")
+
+    out = {line["config"]["workload"]: {"evals_s": r3(line["value"]), "e2e_evals_s": r3(line["e2e"]["value"]),
+                               "frac": r3(line["roofline"]["frac"]),
+                               "frac_unfused": r3(line["roofline"].get("frac_unfused")),
+                               "err_vs_fp64": {k: r3(v) for k, v in (line.get("err_vs_fp64") or {}).items()},
+                               "speedup_vs_one_set_per_call": r3(g(line, "plain_path", "speedup_one_set_per_call")),
+                               "speedup_vs_per_gate": r3(g(line, "plain_path", "speedup_per_gate_statevector"))}}
+    if not extras:
+        return out
+    c4 = extras.get("tfim_n500_L4_B256", {})
+    out["tfim_n500_L4_B256"] = {"evals_s": r3(c4.get("value")), "ms": r3(c4.get("ms_per_step")),
+                                "frac": r3(g(c4, "roofline", "frac")), "frac_unfused": r3(g(c4, "roofline", "frac_unfused")),
+                                "err_vs_fp64": {k: r3(v) for k, v in (c4.get("err_vs_fp64") or {}).items()},
+                                "speedup_vs_one_set_per_call": r3(c4.get("speedup_vs_plain"))}
+    c1 = extras.get("tfim_n8_L2_B1_latency", {})
+    out["tfim_n8_L2_B1"] = {"p50_us": r3(g(c1, "gpu", "p50_us")), "p99_us": r3(g(c1, "gpu", "p99_us")),
+                            "cpu_p50_us": r3(g(c1, "cpu_oracle", "p50_us")),
+                            "err_vs_fp64": {k: r3(v) for k, v in (c1.get("err_vs_fp64") or {}).items()}}
+    c3, c3g = extras.get("qaoa_n28_p4", {}), extras.get("qaoa_n28_p4_grad", {})
+    out["qaoa_n28_p4"] = {"ms": r3(c3.get("ms_per_eval")), "frac_hbm": r3(g(c3, "roofline", "frac")),
+                          "grad_ms": r3(c3g.get("ms_per_eval")), "grad_frac_hbm": r3(g(c3g, "roofline", "frac")),
+                          "err": {k: r3(v) for k, v in (c3g.get("err_vs_fp64") or {}).items()},
+                          "tc_ms": r3(g(c3, "mixed_tc", "ms_per_eval")), "tc_grad_ms": r3(g(c3g, "mixed_tc", "ms_per_eval")),
+                          "tc_err": {k: r3(v) for k, v in (g(c3g, "mixed_tc", "err_vs_fp64") or {}).items()},
+                          "speedup_vs_per_gate": r3(c3.get("speedup_vs_plain"))}
+    for key in ("partial_trace_n20_m14", "partial_trace_n20_m10"):
+        pt = extras.get(key, {})
+        out[key] = {"ms": r3(pt.get("ms")), "bound": g(pt, "roofline", "bound"), "frac": r3(g(pt, "roofline", "frac")),
+                    "max_abs_err": r3(pt.get("max_abs_err_vs_oracle"))}
+    out["serving"] = [{"rate": s["rate_per_s"], "rps": r3(s.get("throughput_rps")), "p50_ms": r3(s.get("p50_ms")),
+                       "p99_ms": r3(s.get("p99_ms")),
+                       **({"plain_rps": r3(s["one_at_a_time"]["throughput_rps"]),
+                           "plain_p50_ms": r3(s["one_at_a_time"]["p50_ms"])} if "one_at_a_time" in s else {})}
+                      for s in extras.get("serving_sweep", [])]
     return out
 
 
@@ -486,6 +677,8 @@ def latency_n8(B, local, calls=10000):
         c, h = ctx.problem(prob)
         for _ in range(100):
             B.tlq_expectation(ctx.h, c.h, h.h, th)
+        err = fp64_errors(B.tlq_expectation(ctx.h, c.h, h.h, th), None,
+                          B.tlq_expectation(ctx.h, c.h, h.h, th, B.TLQ_FP64_REF), None)
         t = []
         for _ in range(calls):
             t0 = time.perf_counter()
@@ -499,7 +692,8 @@ def latency_n8(B, local, calls=10000):
         dense.energy(prob.n, prob.gates, prob.terms, prob.theta[0])
         cpu.append(time.perf_counter() - t0)
     return {"workload": "tfim_n8_L2_B1 (energy)", "calls": calls, "gpu": pct(t),
-            "cpu_oracle": {**pct(cpu), "calls": len(cpu)}}
+            "cpu_oracle": {**pct(cpu), "calls": len(cpu)}, "err_vs_fp64": err,
+            "fp64_reference": "TLQ_FP64_REF (complex128 mode of the same kernels)"}
 
 
 def partial_trace_workloads(B, dev, local, flush, peaks, n=20, ms=(14, 10), steps=10, warmup=3, with_cpu=True):
@@ -537,32 +731,42 @@ def partial_trace_workloads(B, dev, local, flush, peaks, n=20, ms=(14, 10), step
             D, K = 2 ** m, 2 ** (n - m)
             flops = 8.0 * D * (D + 1) / 2 * K      # Hermitian half of rho = Psi Psi^dagger (complex MACs x 8)
             kms = float(np.median(kt))
+            rho_h = rho_d.cpu().numpy().view(np.complex64).reshape(D, D)
             cpu_s = None
-            if with_cpu:
-                t0 = time.perf_counter()
-                density.reduced_density(psi, n, keep)
-                cpu_s = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            rho_ref = density.reduced_density(psi, n, keep)
+            cpu_s = time.perf_counter() - t0
+            max_err = 0.0
+            for r0 in range(0, D, 1024):   # in row blocks: the m=14 output is 2 GiB
+                blk = rho_h[r0:r0 + 1024].astype(np.complex128) - rho_ref[r0:r0 + 1024]
+                max_err = max(max_err, float(np.max(np.abs(blk))))
+            del rho_ref, rho_h
             del rho_d
             hbm_bytes = 8 * D * D + 3 * 8 * 2 ** n     # rho written; psi read, Psi written and read
             hbm_peak = float(peaks["hbm_gbs"])
+            hbm_floor = hbm_bytes / (hbm_peak * 1e9)
             if m >= 7:
-                # tensor cores: per 128 x 128 upper tile and 8 complex k, six TF32 MMAs of 128 x 256 x 8
+                # tensor cores (tcgen05 kind::tf32): the bound is set by the algorithmic flops against
+                # the TF32 peak; executed flops (six split-TF32 MMAs of 128 x 256 x 8 per 128 x 128
+                # upper tile and 8 complex k) are reported beside it
                 T = (D + 127) // 128
                 tc_flops = T * (T + 1) // 2 * (K / 8) * 6 * 2 * 128 * 256 * 8
                 ws = T * (T + 1) // 2 >= torch.cuda.get_device_properties(0).multi_processor_count and n - m >= 3
                 tf32_peak = float(peaks["bf16_tflops"]) * 1.1 / 2.25   # nominal TF32 / BF16 dense ratio
-                hbm_floor, tc_floor = hbm_bytes / (hbm_peak * 1e9), tc_flops / (tf32_peak * 1e12)
+                tc_floor = flops / (tf32_peak * 1e12)
                 if hbm_floor >= tc_floor:
                     roof = {"bound": "hbm", "achieved": hbm_bytes / (kms * 1e-3) / 1e9, "peak": hbm_peak,
                             "unit": "GB/s", "frac": hbm_bytes / (kms * 1e-3) / 1e9 / hbm_peak}
                 else:
-                    roof = {"bound": "tensor", "achieved": tc_flops / (kms * 1e-3) / 1e12, "peak": tf32_peak,
-                            "unit": "TFLOP/s", "frac": tc_flops / (kms * 1e-3) / 1e12 / tf32_peak,
+                    roof = {"bound": "tensor", "achieved": flops / (kms * 1e-3) / 1e12, "peak": tf32_peak,
+                            "unit": "TFLOP/s", "frac": flops / (kms * 1e-3) / 1e12 / tf32_peak,
                             "peak_basis": "measured bf16 dense x 1.1/2.25 (nominal TF32/BF16)"}
                 roof.update({"kernel": ("herk_ws_kernel (persistent, warp-specialised" if ws else
                                         "herk_tc_kernel (split k") + "; tcgen05 kind::tf32, TMEM accumulators)",
+                             "tensor_tflops_algorithmic": flops / (kms * 1e-3) / 1e12,
+                             "tensor_frac_algorithmic": flops / (kms * 1e-3) / 1e12 / tf32_peak,
                              "tensor_tflops_executed": tc_flops / (kms * 1e-3) / 1e12,
-                             "hbm_gbs": hbm_bytes / (kms * 1e-3) / 1e9})
+                             "hbm_gbs": hbm_bytes / (kms * 1e-3) / 1e9, "hbm_frac": hbm_bytes / (kms * 1e-3) / 1e9 / hbm_peak})
             else:
                 roof = {"bound": "alu", "achieved": flops / (kms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                         "frac": flops / (kms * 1e-3) / 1e12 / peak, "kernel": "herk_tile_kernel (FP32)"}
@@ -571,8 +775,8 @@ def partial_trace_workloads(B, dev, local, flush, peaks, n=20, ms=(14, 10), step
                          "hbm_bytes": hbm_bytes, "algorithmic_flops": flops})
             out[f"partial_trace_n{n}_m{m}"] = {
                 "value": 1e3 / float(np.median(t)), "unit": "traces/s", "ms": float(np.median(t)), "launches": nl,
-                "keep": f"qubits {keep[0]}..{keep[-1]}", "roofline": roof,
-                "cpu_baseline": None if cpu_s is None else {
+                "keep": f"qubits {keep[0]}..{keep[-1]}", "roofline": roof, "max_abs_err_vs_oracle": max_err,
+                "cpu_baseline": None if not with_cpu else {
                     "value": 1.0 / cpu_s, "unit": "traces/s", "kind": "oracle", "cores": len(os.sched_getaffinity(0)),
                     "sample": "one full trace (numpy complex128)"}}
     return out
@@ -700,6 +904,38 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
     e2e_value, _ = job_throughput(sum(e2e_t), Bsz * len(e2e_t), world, dev)
 
+    # error of the timed result (FP32) against the complex128 mode of the same kernels
+    path, *_ = B.tlq_plan_info(ctx.h, c.h, h.h, len(prob.terms))
+    err64 = None
+    if path == B.TLQ_PATH_CONE:
+        E64, G64 = fp64_reference(B, ctx, c, h, theta_h)
+        err64 = fp64_errors(E_h, G_h, E64, G64)
+
+    # the plain per-circuit FP32 path on the same GPU: one parameter set per call, and (up to 24
+    # qubits) the per-gate statevector sweeps
+    plain = None
+    if rank == 0 and not args.no_extras and path == B.TLQ_PATH_CONE:
+        import ctypes
+        one_ms = plain_one_set_per_call(B, ctx, c, h, prob, dev, flush)
+        plain = {"one_set_per_call": {"kind": "one parameter set per call (B = 1), same kernels",
+                                      "ms_per_batch": one_ms, "value": Bsz / (one_ms * 1e-3), "unit": UNIT}}
+        if prob.n <= 24:
+            cfg = B.tlq_config(local, 0, 0, B.TLQ_FP32, 1)
+            hnd = ctypes.c_void_p()
+            B._check(B.lib().tlq_init(ctypes.byref(cfg), ctypes.byref(hnd)))
+            pctx = B.Context.__new__(B.Context)
+            pctx.h = hnd
+            pc, ph = pctx.problem(prob)
+            B.tlq_profile_enable(pctx.h, True)
+            pg_ms, _, _ = device_steps(B, pctx, pc, ph, prob, True, 1, dev, flush, warmup=1)
+            pc.close()
+            ph.close()
+            pctx.close()
+            plain["per_gate_statevector"] = {"kind": "per-gate FP32 sweeps of the 2^n statevector, "
+                                                     "per-gate adjoint", "ms_per_batch": pg_ms,
+                                             "value": Bsz / (pg_ms * 1e-3), "unit": UNIT}
+        torch.cuda.set_stream(stream)
+
     # roofline of the dominant kernel (the batched cone kernel), ALU-bound FP32
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -707,7 +943,6 @@ def main():
     n_sm = props.multi_processor_count
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     kern_mean_ms = float(np.mean(kern_ms))
-    path, *_ = B.tlq_plan_info(ctx.h, c.h, h.h, len(prob.terms))
     if path == B.TLQ_PATH_DENSE:
         nbytes, passes = dense_bytes(B, ctx, c, h, True)
         achieved = nbytes / (kern_mean_ms * 1e-3) / 1e9
@@ -717,12 +952,19 @@ def main():
                     "kernel_ms": kern_mean_ms, "bytes_per_eval": nbytes, "passes": passes}
     else:
         flops = algorithmic_flops(B, ctx, c, h, prob, grad=True)
+        _, flops_unf = unfused_flops(prob)
         achieved = flops / (kern_mean_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / peak_tflops, "traffic": NCU_TRAFFIC.get((args.workload, "cone_kernel")),
                     "kernel": "cone_kernel<float,grad> (batched causal cones + adjoint)",
                     "kernel_ms": kern_mean_ms, "algorithmic_flops": flops,
+                    "algorithmic_flops_basis": "work the shared windows require (terms nested in a window are "
+                                               "measured on it)",
                     "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x {sm_max:.0f} MHz"}
+        if flops_unf is not None:
+            roofline.update({"algorithmic_flops_unfused": flops_unf,
+                             "frac_unfused": flops_unf / (kern_mean_ms * 1e-3) / 1e12 / peak_tflops,
+                             "unfused_basis": "every term on its own exact causal cone, adjoint = 3 x forward"})
 
     extras = extra_workloads(B, dev, local, flush, peaks) if rank == 0 and not args.no_extras else {}
     if rank == 0:
@@ -741,11 +983,18 @@ def main():
                     "d2h_bytes_per_step": int(E_h.nbytes + G_h.nbytes)},
             "gpu_launches": launches,
             "roofline": roofline,
+            "err_vs_fp64": err64,
+            "fp64_reference": "TLQ_FP64_REF (complex128 mode of the same kernels), same inputs" if err64 else None,
             "peak_source": peak_kind,
             "cpu_baseline": cpu,
             "clocks": clk,
-            "other_workloads": extras,
         }
+        if plain is not None:
+            for k, v in list(plain.items()):
+                plain[f"speedup_{k}"] = v["ms_per_batch"] / (1e3 * total_s / args.steps)
+            line["plain_path"] = plain
+        line["other_workloads"] = extras
+        line["summary"] = summary_of(line, extras)   # last: the compact digest closes the line
         print(json.dumps(line), flush=True)
     c.close()
     h.close()

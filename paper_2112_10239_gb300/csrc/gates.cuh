@@ -74,17 +74,58 @@ __device__ __forceinline__ void store16(const T2 (&v)[16], T2* p, int stride) {
     }
 }
 
+// ---- packed two-wide FP32 (f32x2): one instruction updates the (re, im) pair of an
+// amplitude. A real factor (RY's cos and sin, and the gradient sums of Y) acts on both parts
+// alike, so these updates take half the instructions of the scalar form; the kernels that use
+// them are bound by instruction issue, not by the FMA pipe.
+
+__device__ __forceinline__ unsigned long long pk2(float x, float y) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // RY(a) on register bit K: [[c,-s],[s,c]] on (amp with bit 0, amp with bit 1).
 template <int K, typename T2, typename real>
 __device__ __forceinline__ void apply_ry(T2 (&v)[16], real c, real s) {
+    if constexpr (sizeof(real) == 4) {
+        const unsigned long long C = pk2(c, c), S = pk2(s, s), NS = pk2(-s, -s);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        if (j & (1 << K)) continue;
-        const T2 a0 = v[j], a1 = v[j | (1 << K)];
-        v[j].x = c * a0.x - s * a1.x;
-        v[j].y = c * a0.y - s * a1.y;
-        v[j | (1 << K)].x = s * a0.x + c * a1.x;
-        v[j | (1 << K)].y = s * a0.y + c * a1.y;
+        for (int j = 0; j < 16; ++j) {
+            if (j & (1 << K)) continue;
+            const unsigned long long a0 = pk2(v[j].x, v[j].y), a1 = pk2(v[j | (1 << K)].x, v[j | (1 << K)].y);
+            const float2 r0 = upk2(fma2(C, a0, mul2(NS, a1)));   // c a0 - s a1
+            const float2 r1 = upk2(fma2(C, a1, mul2(S, a0)));    // s a0 + c a1
+            v[j].x = r0.x;
+            v[j].y = r0.y;
+            v[j | (1 << K)].x = r1.x;
+            v[j | (1 << K)].y = r1.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j & (1 << K)) continue;
+            const T2 a0 = v[j], a1 = v[j | (1 << K)];
+            v[j].x = c * a0.x - s * a1.x;
+            v[j].y = c * a0.y - s * a1.y;
+            v[j | (1 << K)].x = s * a0.x + c * a1.x;
+            v[j | (1 << K)].y = s * a0.y + c * a1.y;
+        }
     }
 }
 
@@ -112,14 +153,28 @@ __device__ __forceinline__ void apply_rot(T2 (&v)[16], int kind, real c, real s)
 // sum over pairs of Re(conj(l1) p0) - Re(conj(l0) p1).
 template <int K, typename T2, typename real>
 __device__ __forceinline__ real grad_y(const T2 (&p)[16], const T2 (&l)[16]) {
-    real acc = 0;
+    if constexpr (sizeof(real) == 4) {
+        // two packed sums: (l1 . p0) and (l0 . p1) componentwise, folded at the end
+        unsigned long long sa = pk2(0.f, 0.f), sb = pk2(0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        if (j & (1 << K)) continue;
-        const T2 p0 = p[j], p1 = p[j | (1 << K)], l0 = l[j], l1 = l[j | (1 << K)];
-        acc += (l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y);
+        for (int j = 0; j < 16; ++j) {
+            if (j & (1 << K)) continue;
+            const int j1 = j | (1 << K);
+            sa = fma2(pk2(l[j1].x, l[j1].y), pk2(p[j].x, p[j].y), sa);
+            sb = fma2(pk2(l[j].x, l[j].y), pk2(p[j1].x, p[j1].y), sb);
+        }
+        const float2 a = upk2(sa), b = upk2(sb);
+        return (a.x + a.y) - (b.x + b.y);
+    } else {
+        real acc = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j & (1 << K)) continue;
+            const T2 p0 = p[j], p1 = p[j | (1 << K)], l0 = l[j], l1 = l[j | (1 << K)];
+            acc += (l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y);
+        }
+        return acc;
     }
-    return acc;
 }
 
 // Im <lam| X |psi> = sum over pairs of Im(conj(l0) p1 + conj(l1) p0).
