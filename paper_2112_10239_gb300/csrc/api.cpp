@@ -44,6 +44,8 @@ PlanEntry::~PlanEntry() {
     cudaFree(d_dtab_mult);
     cudaFree(d_dxterms);
     cudaFree(d_dallterms);
+    cudaFree(d_dfgates);
+    cudaFree(d_dfxterms);
     cudaFree(d_dadj_off);
     cudaFree(d_dadj_idx);
     cudaFree(d_dinit_pcd);
@@ -103,6 +105,8 @@ tlq_status get_plan(Context* ctx, Circuit* c, Ham* h, std::shared_ptr<PlanEntry>
             TLQ_TRY(upload(D.tab_mult, &pe->d_dtab_mult, &bytes));
             TLQ_TRY(upload(D.xterms, &pe->d_dxterms, &bytes));
             TLQ_TRY(upload(D.all_terms, &pe->d_dallterms, &bytes));
+            TLQ_TRY(upload(D.fgates, &pe->d_dfgates, &bytes));
+            TLQ_TRY(upload(D.fxterms, &pe->d_dfxterms, &bytes));
             TLQ_TRY(upload(D.adj_off, &pe->d_dadj_off, &bytes));
             TLQ_TRY(upload(D.adj_idx, &pe->d_dadj_idx, &bytes));
             TLQ_TRY(upload(D.init_pcd, &pe->d_dinit_pcd, &bytes));
@@ -201,6 +205,9 @@ size_t dense_workspace_bytes(const PlanEntry& pe, const Circuit& c, int B, bool 
 static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const double* theta_dev, int B,
                             double* energy_dev, double* grad_dev, bool per_gate, void* stream, Workspace* ws,
                             void** state_out = nullptr, bool tc = false) {
+    // The fused passes of an expectation run in the rotation frame (DensePlan::frame_mask); a
+    // call that hands out the state (state_out) and the per-gate sweeps use the plain frame.
+    const bool framed = !per_gate && !state_out && pe.plan->dense->frame_mask != 0;
     const DensePlan& D = *pe.plan->dense;
     const bool grad = grad_dev != nullptr;
     const size_t need = dense_workspace_bytes(pe, c, B, grad, ctx->sm_count);
@@ -224,7 +231,7 @@ static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const
     L.tab_gate = pe.d_dtab_gate;
     L.tab_mult = pe.d_dtab_mult;
     L.tab_entries = (int32_t)D.tab_gate.size();
-    L.gates = pe.d_gates;
+    L.gates = framed ? pe.d_dfgates : pe.d_gates;
     L.n_gates = (int32_t)c.gates.size();
     L.n_params = c.n_params;
     L.B = B;
@@ -238,7 +245,7 @@ static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const
         L.lam = ws->take(((size_t)1 << D.n_eff) * 8);
         L.gpart = (double*)ws->take(dense_gpart_count(D, ctx->sm_count) * sizeof(double));
     }
-    L.xterms = pe.d_dxterms;
+    L.xterms = framed ? pe.d_dfxterms : pe.d_dxterms;
     L.all_terms = pe.d_dallterms;
     L.adj_off = pe.d_dadj_off;
     L.adj_idx = pe.d_dadj_idx;
@@ -258,7 +265,7 @@ static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const
     L.init_class_off = D.init_class_off;
     L.init_nclass = D.init_nclass;
     L.init_pcd = pe.d_dinit_pcd;
-    L.host_xterms = D.xterms.data();
+    L.host_xterms = framed ? D.fxterms.data() : D.xterms.data();
     L.host_all_terms = D.all_terms.data();
     L.n_all_terms = (int32_t)D.all_terms.size();
     if (ctx->profile) { L.ev_begin = ctx->prof_ev[0]; L.ev_end = ctx->prof_ev[1]; }

@@ -184,6 +184,13 @@ struct DensePlan {
     int max_classes_per_layer = 0;
     int max_dists = 0;
     bool fits_fused = true;                 // staged class data fits the pass kernel's shared memory
+    // Rotation frame of the fused passes. On a qubit whose rotations are all RX the passes carry
+    // psi' = S psi with S = diag(1, i) on that qubit: S RX(a) S^dagger = RY(a), S commutes with
+    // every diagonal gate and S|0> = |0>, so the RX gates run as the real RY form and only the
+    // X/Y letters of the measured terms change (S X S^dagger = Y, S Y S^dagger = -X).
+    uint32_t frame_mask = 0;                // qubits carried in the rotated frame
+    std::vector<tlq_gate> fgates;           // the circuit's gates with RX -> RY on those qubits
+    std::vector<DenseXTermDev> fxterms;     // xterms with the letters converted on those qubits
 };
 
 // ---------------------------------------------------------------------------------------

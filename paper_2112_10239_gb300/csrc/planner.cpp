@@ -708,6 +708,28 @@ std::shared_ptr<DensePlan> make_dense_plan(const Circuit& c, const Ham& h, std::
         for (auto& cb : kv.second) emit_class(*D, cb);
     D->energy_nclass = (int32_t)D->classes.size() - D->energy_class_off;
 
+    // rotation frame: qubits whose rotations are all RX (see DensePlan::frame_mask)
+    {
+        std::vector<int> nrx(c.n, 0), nry(c.n, 0);
+        for (const tlq_gate& g : c.gates) {
+            if (g.kind == TLQ_RX) ++nrx[g.q0];
+            if (g.kind == TLQ_RY) ++nry[g.q0];
+        }
+        for (int q = 0; q < c.n && q < 32; ++q)
+            if (nrx[q] > 0 && nry[q] == 0) D->frame_mask |= 1u << q;
+        D->fgates = c.gates;
+        for (tlq_gate& g : D->fgates)
+            if (g.kind == TLQ_RX && ((D->frame_mask >> g.q0) & 1u)) g.kind = TLQ_RY;
+        D->fxterms = D->xterms;
+        for (DenseXTermDev& x : D->fxterms) {
+            const uint32_t xs = x.flip & ~x.zy & D->frame_mask;   // X letters in the frame: -> Y
+            const uint32_t ys = x.flip & x.zy & D->frame_mask;    // Y letters in the frame: -> -X
+            x.zy = (x.zy | xs) & ~ys;
+            x.ny += __builtin_popcount(xs) - __builtin_popcount(ys);
+            if (__builtin_popcount(ys) & 1) x.coeff = -x.coeff;
+        }
+    }
+
     // Pass schedule. Tile patterns: the low tile (qubits 0..11) and strided tiles covering 8
     // higher qubits each. Greedy: each pass takes the pattern covering the most pending
     // rotations of the current layer; when a pass completes a layer it applies the layer's

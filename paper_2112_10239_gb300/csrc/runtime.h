@@ -38,6 +38,8 @@ struct PlanEntry {
     int32_t* d_dtab_mult = nullptr;
     DenseXTermDev* d_dxterms = nullptr;
     DenseXTermDev* d_dallterms = nullptr;
+    tlq_gate* d_dfgates = nullptr;           // DensePlan::fgates (rotation frame of the fused passes)
+    DenseXTermDev* d_dfxterms = nullptr;     // DensePlan::fxterms
     int32_t* d_dadj_off = nullptr;
     int32_t* d_dadj_idx = nullptr;
     DensePassClassDev* d_dinit_pcd = nullptr;

@@ -291,3 +291,42 @@ def test_qaoa_n28_p4_vs_golden_oracle(tlq, prec):
     check_energy(E, [g["energy"]])
     check_energy(E2, [g["energy"]])
     check_grad(G, np.array([g["grad"]]))
+
+
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("prec", ["fp32", "mixed_tc"])
+def test_rx_frame_with_xy_terms(tlq, seed, prec):
+    """RX-only qubits run in the rotated frame S = diag(1, i) (RX acts as RY there): X/Y letters
+    on those qubits are measured as Y / -X. QAOA-style layers (RZZ on random pairs, RX on every
+    qubit, RY on a few qubits, so some qubits stay in the plain frame) against random X/Y/Z
+    strings of 1-3 sites, energy and gradient against the oracle."""
+    from paper_2112_10239_gb300 import binding as B
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(12, 17))
+    gates, P = [], 0
+    ry_qubits = set(int(q) for q in rng.choice(n, 2, replace=False))
+    for _ in range(3):
+        for _ in range(n):
+            u, v = (int(x) for x in rng.choice(n, 2, replace=False))
+            gates.append((W.RZZ, u, v, P, 0.0)); P += 1
+        for q in range(n):
+            gates.append((W.RY if q in ry_qubits else W.RX, q, -1, P, 0.0)); P += 1
+    terms = []
+    for _ in range(2 * n):
+        k = int(rng.integers(1, 4))
+        sites = tuple(int(s) for s in rng.choice(n, k, replace=False))
+        terms.append((float(rng.uniform(-1, 1)), sites, "".join("XYZ"[int(rng.integers(3))] for _ in sites)))
+    theta = rng.uniform(0, 2 * math.pi, size=(2, P))
+    prob = W.Problem(n=n, gates=gates, n_params=P, terms=terms, theta=theta)
+    mode = {"fp32": B.TLQ_FP32, "mixed_tc": B.TLQ_MIXED_TC}[prec]
+    c, h = tlq.problem(prob)
+    try:
+        E, G = B.tlq_expectation_grad(tlq.h, c.h, h.h, theta, mode)
+        E2 = B.tlq_expectation(tlq.h, c.h, h.h, theta, mode)
+    finally:
+        c.close()
+        h.close()
+    Er, gr = _oracle_grad(prob, theta)
+    check_energy(E, Er)
+    check_energy(E2, Er)
+    check_grad(G, gr)
