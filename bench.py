@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--workload", default="tfim_n20_L6_B64",
                     help="tfim_n20_L6_B64 (default), tfim_n500_L4_B256, tfim_n8_L2_B1 or qaoa_n<N>_p<P> "
                          "(3-regular graph, dense statevector path, one parameter set)")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "mixed_tc"],
+                    help="precision of the timed workload (mixed_tc: tensor-core gate blocks on the dense path)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the chosen workload only: no other workloads, serving replay or CPU baseline "
                          "(short runs for a profiler)")
@@ -861,8 +863,10 @@ def main():
     torch.cuda.set_stream(stream)
     B.tlq_profile_enable(ctx.h, True)
 
+    prec = B.TLQ_MIXED_TC if args.prec == "mixed_tc" else B.TLQ_FP32
+
     def step():
-        B.tlq_expectation_grad_dev(ctx.h, c.h, h.h, theta_d.data_ptr(), Bsz, B.TLQ_FP32, E_d.data_ptr(),
+        B.tlq_expectation_grad_dev(ctx.h, c.h, h.h, theta_d.data_ptr(), Bsz, prec, E_d.data_ptr(),
                                    G_d.data_ptr(), stream.cuda_stream)
 
     for _ in range(max(3, args.warmup)):
@@ -896,11 +900,11 @@ def main():
     B.tlq_profile_enable(ctx.h, False)
     theta_h = np.ascontiguousarray(prob.theta)
     for _ in range(3):
-        B.tlq_expectation_grad(ctx.h, c.h, h.h, theta_h)
+        B.tlq_expectation_grad(ctx.h, c.h, h.h, theta_h, prec)
     e2e_t = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        E_h, G_h = B.tlq_expectation_grad(ctx.h, c.h, h.h, theta_h)
+        E_h, G_h = B.tlq_expectation_grad(ctx.h, c.h, h.h, theta_h, prec)
         e2e_t.append(time.perf_counter() - t0)
     e2e_value, _ = job_throughput(sum(e2e_t), Bsz * len(e2e_t), world, dev)
 
@@ -948,7 +952,8 @@ def main():
         achieved = nbytes / (kern_mean_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                     "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
-                    "kernel": "dense_pass_kernel + dense_adjoint_kernel (forward and reverse passes)",
+                    "kernel": ("dense_tc_pass_kernel" if args.prec == "mixed_tc" else "dense_pass_kernel") +
+                              " + dense_adjoint_kernel (forward and reverse passes)",
                     "kernel_ms": kern_mean_ms, "bytes_per_eval": nbytes, "passes": passes}
     else:
         flops = algorithmic_flops(B, ctx, c, h, prob, grad=True)
@@ -974,7 +979,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "n": prob.n, "L": prob.meta.get("L"), "B": Bsz,
+            "config": {"workload": args.workload, "n": prob.n, "L": prob.meta.get("L"), "B": Bsz, "prec": args.prec,
                        "n_params": P, "terms": len(prob.terms), "l2": "flushed: 256 MiB write between timed steps",
                        "parallelism": "replicas" if world > 1 else "single"},
             "latency_ms": {"p50": sm[len(sm) // 2], "p99": sm[min(len(sm) - 1, int(math.ceil(0.99 * len(sm))) - 1)],

@@ -617,6 +617,31 @@ static tlq_status check_pair(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t B, t
 // back into the staging buffer.
 static tlq_status sync_enqueue(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t B, tlq_precision prec, bool want_grad,
                                cudaStream_t st, size_t th_b, size_t e_b, size_t g_b) {
+    // Small circuits, energies only (the small-circuit kernel): the kernel reads the angles from
+    // the pinned staging buffer and writes the energies into it through its device mapping, so
+    // the call is one kernel, with no copies (the error word in the staging buffer is cleared by
+    // the host before every launch; this kernel never sets it).
+    if (!want_grad && prec != TLQ_FP64_REF && ctx->cfg.fuse_k != 1) {
+        std::shared_ptr<PlanEntry> pe;
+        TLQ_TRY(get_plan(ctx, c, h, &pe));
+        const Plan& P = *pe->plan;
+        void* dhp = nullptr;
+        if (P.dense && tiny_fits(c->n, (int)c->gates.size(), (int)P.dense->all_terms.size()) &&
+            cudaHostGetDevicePointer(&dhp, ctx->h_pinned, 0) == cudaSuccess && dhp) {
+            if (ctx->profile) TLQ_CUDA(cudaEventRecord((cudaEvent_t)ctx->prof_ev[0], st));
+            const int rc = launch_tiny_energy(pe->d_gates, (int)c->gates.size(), (const double*)dhp, c->n_params, c->n,
+                                              pe->d_dallterms, (int)P.dense->all_terms.size(), B,
+                                              (double*)((char*)dhp + th_b), st);
+            if (ctx->profile) TLQ_CUDA(cudaEventRecord((cudaEvent_t)ctx->prof_ev[1], st));
+            ctx->last_launches = 1;
+            if (rc != 0) {
+                set_error(std::string("tiny launch: ") + cudaGetErrorString((cudaError_t)rc));
+                return TLQ_ECUDA;
+            }
+            return TLQ_OK;
+        }
+        cudaGetLastError();   // no device mapping: the copy path below
+    }
     ctx->ws.used = 0;
     double* d_theta = (double*)ctx->ws.take(th_b);
     double* d_e = (double*)ctx->ws.take(e_b);
@@ -673,6 +698,7 @@ static tlq_status sync_call(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const double*
     key.ws_cap = ctx->ws.cap;
     key.pinned = ctx->h_pinned;
     key.pinned_cap = ctx->h_pinned_cap;
+    *(int32_t*)(hp + th_b + e_b + g_b) = 0;   // the error word (the copy path overwrites it)
     bool launched = false;
     if (!ctx->profile) {
         if (!(pe->graph_exec && pe->graph_key == key)) {

@@ -479,15 +479,15 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, const Team& tm, co
             if constexpr (FINAL) {
                 // layer 0: the states are not needed afterwards, and its rotations commute, so
                 // every gradient is taken at this state with nothing un-applied or stored
-                if (kd[0] >= 0) g0 = kd[0] == TLQ_RY ? grad_y<0, T2, real>(p, l) : grad_x<0, T2, real>(p, l);
-                if (kd[1] >= 0) g1 = kd[1] == TLQ_RY ? grad_y<1, T2, real>(p, l) : grad_x<1, T2, real>(p, l);
-                if (kd[2] >= 0) g2 = kd[2] == TLQ_RY ? grad_y<2, T2, real>(p, l) : grad_x<2, T2, real>(p, l);
-                if (kd[3] >= 0) g3 = kd[3] == TLQ_RY ? grad_y<3, T2, real>(p, l) : grad_x<3, T2, real>(p, l);
+                if (kd[0] >= 0) g0 = kd[0] == TLQ_RY ? grad_y<0, T2, real, false>(p, l) : grad_x<0, T2, real>(p, l);
+                if (kd[1] >= 0) g1 = kd[1] == TLQ_RY ? grad_y<1, T2, real, false>(p, l) : grad_x<1, T2, real>(p, l);
+                if (kd[2] >= 0) g2 = kd[2] == TLQ_RY ? grad_y<2, T2, real, false>(p, l) : grad_x<2, T2, real>(p, l);
+                if (kd[3] >= 0) g3 = kd[3] == TLQ_RY ? grad_y<3, T2, real, false>(p, l) : grad_x<3, T2, real>(p, l);
             } else {
-                if (kd[0] >= 0) g0 = adjoint_rot<0, T2, real>(p, l, kd[0], c[0], sn[0]);
-                if (kd[1] >= 0) g1 = adjoint_rot<1, T2, real>(p, l, kd[1], c[1], sn[1]);
-                if (kd[2] >= 0) g2 = adjoint_rot<2, T2, real>(p, l, kd[2], c[2], sn[2]);
-                if (kd[3] >= 0) g3 = adjoint_rot<3, T2, real>(p, l, kd[3], c[3], sn[3]);
+                if (kd[0] >= 0) g0 = adjoint_rot<0, T2, real, false>(p, l, kd[0], c[0], sn[0]);
+                if (kd[1] >= 0) g1 = adjoint_rot<1, T2, real, false>(p, l, kd[1], c[1], sn[1]);
+                if (kd[2] >= 0) g2 = adjoint_rot<2, T2, real, false>(p, l, kd[2], c[2], sn[2]);
+                if (kd[3] >= 0) g3 = adjoint_rot<3, T2, real, false>(p, l, kd[3], c[3], sn[3]);
                 store16(p, pp, stride);
                 store16(l, lp, stride);
             }

@@ -100,10 +100,11 @@ __device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigne
     return d;
 }
 
-// RY(a) on register bit K: [[c,-s],[s,c]] on (amp with bit 0, amp with bit 1).
-template <int K, typename T2, typename real>
+// RY(a) on register bit K: [[c,-s],[s,c]] on (amp with bit 0, amp with bit 1). PACK selects
+// the packed form for FP32 (callers whose register budget is tight keep the scalar form).
+template <int K, typename T2, typename real, bool PACK = true>
 __device__ __forceinline__ void apply_ry(T2 (&v)[16], real c, real s) {
-    if constexpr (sizeof(real) == 4) {
+    if constexpr (sizeof(real) == 4 && PACK) {
         const unsigned long long C = pk2(c, c), S = pk2(s, s), NS = pk2(-s, -s);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -151,9 +152,9 @@ __device__ __forceinline__ void apply_rot(T2 (&v)[16], int kind, real c, real s)
 
 // Im <lam| Y |psi> over the pairs of register bit K (Y|0> = i|1>, Y|1> = -i|0>):
 // sum over pairs of Re(conj(l1) p0) - Re(conj(l0) p1).
-template <int K, typename T2, typename real>
+template <int K, typename T2, typename real, bool PACK = true>
 __device__ __forceinline__ real grad_y(const T2 (&p)[16], const T2 (&l)[16]) {
-    if constexpr (sizeof(real) == 4) {
+    if constexpr (sizeof(real) == 4 && PACK) {
         // two packed sums: (l1 . p0) and (l0 . p1) componentwise, folded at the end
         unsigned long long sa = pk2(0.f, 0.f), sb = pk2(0.f, 0.f);
 #pragma unroll
@@ -191,13 +192,13 @@ __device__ __forceinline__ real grad_x(const T2 (&p)[16], const T2 (&l)[16]) {
 }
 
 // Adjoint step of one rotation on register bit K: gradient, then un-apply on psi and lam.
-template <int K, typename T2, typename real>
+template <int K, typename T2, typename real, bool PACK = true>
 __device__ __forceinline__ real adjoint_rot(T2 (&p)[16], T2 (&l)[16], int kind, real c, real s_neg) {
     real g;
     if (kind == TLQ_RY) {
-        g = grad_y<K, T2, real>(p, l);
-        apply_ry<K>(p, c, s_neg);
-        apply_ry<K>(l, c, s_neg);
+        g = grad_y<K, T2, real, PACK>(p, l);
+        apply_ry<K, T2, real, PACK>(p, c, s_neg);
+        apply_ry<K, T2, real, PACK>(l, c, s_neg);
     } else {
         g = grad_x<K, T2, real>(p, l);
         apply_rx<K>(p, c, s_neg);
