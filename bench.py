@@ -394,22 +394,13 @@ def serving_replay(B, device, count, rate, seed=4, plain_path=True):
             "batched": batched, "one_at_a_time": plain}
 
 
-def dense_bytes(B, ctx, c, h, grad):
-    """HBM bytes one evaluation of the dense pass sequence moves (the pass schedule's own
-    traffic): the start state (layer 0's product state, or |0..0>) is written once, then
-    every forward pass reads and writes the 2^n complex64 state; with the gradient the final
-    pass also writes lam = H psi, each reverse pass reads psi and lam and writes both back
-    unless nothing after it needs them, and X/Y strings add a gather sweep that reads psi and
-    lam and writes lam.
-    Returns (bytes, forward passes)."""
-    n_eff, passes, n_fwd, n_rev_store, n_x, _ = B.tlq_plan_dense_info(ctx.h, c.h, h.h)
-    S = 8 * (1 << n_eff)
-    total = S + n_fwd * 2 * S                   # write of the start state, then the forward passes
-    if grad:                                    # lambda written; reverse passes read (and some write) both
-        total += S + passes * 2 * S + n_rev_store * 2 * S
-        if n_x:
-            total += 3 * S
-    return total, n_fwd
+def dense_bytes(B, ctx, c, h, grad, prec=None):
+    """HBM bytes one evaluation of the dense pass sequence moves by its schedule (the library's
+    own count, tlq_plan_dense_bytes: start state, forward passes, X/Y sweeps, and with the
+    gradient lambda and the reverse passes). Returns (bytes, forward passes)."""
+    _, _, n_fwd, _, _, _ = B.tlq_plan_dense_info(ctx.h, c.h, h.h)
+    prec = B.TLQ_FP32 if prec is None else prec
+    return B.tlq_plan_dense_bytes(ctx.h, c.h, h.h, grad, prec), n_fwd
 
 
 def device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3, mps=False, prec=None):
@@ -536,7 +527,7 @@ def qaoa28_workload(B, dev, local, flush, peaks):
         B.tlq_profile_enable(ctx.h, True)
         ms, kms, nl = device_steps(B, ctx, c, h, prob, grad, steps, dev, flush, warmup=3 if fk == 0 else 1,
                                    prec=prec)
-        nbytes, passes = dense_bytes(B, ctx, c, h, grad)
+        nbytes, passes = dense_bytes(B, ctx, c, h, grad, prec)
         err = None
         if gold is not None and fk == 0:
             B.tlq_profile_enable(ctx.h, False)
@@ -948,7 +939,7 @@ def main():
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     kern_mean_ms = float(np.mean(kern_ms))
     if path == B.TLQ_PATH_DENSE:
-        nbytes, passes = dense_bytes(B, ctx, c, h, True)
+        nbytes, passes = dense_bytes(B, ctx, c, h, True, prec)
         achieved = nbytes / (kern_mean_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                     "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,

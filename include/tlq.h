@@ -311,6 +311,18 @@ tlq_status tlq_plan_cone_stats(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n
 tlq_status tlq_plan_dense_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n_eff, int32_t* n_passes,
                                int32_t* n_fwd_passes, int32_t* n_rev_store, int32_t* n_xterms, int32_t* fused);
 
+/* HBM bytes that one evaluation (one parameter set) on the dense statevector path moves by
+ * its pass schedule in precision `prec`, with (want_grad != 0) or without the gradient: the
+ * start state written once (none when the first forward pass generates layer 0's product
+ * state itself), each forward pass reading and writing the 2^n complex64 state (an
+ * energy-only evaluation without X/Y terms does not write the final state back), one read per
+ * term with X/Y letters, and with the gradient lambda written, the X/Y strings' gather sweep
+ * (two reads, one write) and each reverse pass reading psi and lambda and writing both back
+ * unless nothing after it needs them. Works on host-only contexts; EUNSUPPORTED without a
+ * dense plan. Used as the algorithmic byte count of the dense path's roofline. */
+tlq_status tlq_plan_dense_bytes(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int want_grad, tlq_precision prec,
+                                double* bytes);
+
 /* Kernel timing for benchmarks. While enabled, every compute call records CUDA events
  * around its dominant kernel (the batched cone kernel, the dense pass sequence, the partial
  * trace's kernels, or all five kernels of the MPS route) on the stream it launches on. tlq_profile_last waits for the last call's events and returns

@@ -28,7 +28,7 @@ SYMBOLS = ["tlq_init", "tlq_destroy", "tlq_circuit_create", "tlq_circuit_destroy
            "tlq_expectation_grad", "tlq_expectation_grad_dev", "tlq_submit", "tlq_poll",
            "tlq_last_error", "tlq_plan_info", "tlq_plan_cone_stats", "tlq_profile_enable",
            "tlq_profile_last", "tlq_serving_stats", "tlq_version", "tlq_expectation_grad_static",
-           "tlq_plan_dense_info", "tlq_partial_trace_dev", "tlq_reduced_density",
+           "tlq_plan_dense_info", "tlq_plan_dense_bytes", "tlq_partial_trace_dev", "tlq_reduced_density",
            "tlq_mps_expectation_grad", "tlq_mps_expectation_grad_dev", "tlq_plan_mps_info"]
 
 
@@ -83,6 +83,7 @@ def lib():
         L.tlq_plan_info.argtypes = [vp, vp, vp, ip, ip, ip, ip]
         L.tlq_plan_cone_stats.argtypes = [vp, vp, vp, ip, ip, ip, ip, ip, ip, ip, ip]
         L.tlq_plan_dense_info.argtypes = [vp, vp, vp, ip, ip, ip, ip, ip, ip]
+        L.tlq_plan_dense_bytes.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         L.tlq_partial_trace_dev.argtypes = [vp, vp, ctypes.c_int32, ip, ctypes.c_int32, vp, vp]
         L.tlq_reduced_density.argtypes = [vp, vp, dp, ip, ctypes.c_int32, dp]
         L.tlq_mps_expectation_grad.argtypes = [vp, vp, vp, dp, ctypes.c_int32, ctypes.c_int, dp, dp]
@@ -293,6 +294,13 @@ def tlq_plan_dense_info(ctx, circ, ham):
     v = [ctypes.c_int32() for _ in range(6)]
     _check(lib().tlq_plan_dense_info(ctx, circ, ham, *[ctypes.byref(x) for x in v]), ctx)
     return tuple(x.value for x in v)
+
+
+def tlq_plan_dense_bytes(ctx, circ, ham, want_grad, prec=TLQ_FP32):
+    """HBM bytes of one dense-path evaluation's pass schedule (see include/tlq.h)."""
+    b = ctypes.c_double()
+    _check(lib().tlq_plan_dense_bytes(ctx, circ, ham, 1 if want_grad else 0, prec, ctypes.byref(b)), ctx)
+    return b.value
 
 
 def tlq_partial_trace_dev(ctx, psi_ptr, n, keep, rho_ptr, stream_ptr=None):

@@ -254,6 +254,8 @@ static tlq_status run_dense(Context* ctx, PlanEntry& pe, const Circuit& c, const
     L.err = ctx->d_err;
     L.per_gate = per_gate;
     L.tc = tc;
+    L.keep_state = state_out != nullptr;
+    L.gen_first = D.gen_first;
     L.sm_count = ctx->sm_count;
     L.host_gates = c.gates.data();
     L.host_passes = D.passes.data();
@@ -988,6 +990,38 @@ tlq_status tlq_plan_dense_info(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int32_t* n
     }
     if (n_xterms) *n_xterms = (int32_t)D.xterms.size();
     if (fused) *fused = D.fits_fused ? 1 : 0;
+    return TLQ_OK;
+}
+
+tlq_status tlq_plan_dense_bytes(tlq_ctx ctx, tlq_circuit c, tlq_ham h, int want_grad, tlq_precision prec,
+                                double* bytes) {
+    if (!ctx || !c || !h || !bytes) { set_error("NULL handle or out pointer"); return TLQ_EINVAL; }
+    if (c->n != h->n) { set_error("circuit and Hamiltonian qubit counts differ"); return TLQ_EINVAL; }
+    if (prec < TLQ_FP32 || prec > TLQ_FP64_REF) { set_error("unknown precision"); return TLQ_EINVAL; }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    std::shared_ptr<PlanEntry> pe;
+    TLQ_TRY(get_plan(ctx, c, h, &pe));
+    if (!pe->plan->dense) { set_error("no dense statevector plan (more than 31 qubits)"); return TLQ_EUNSUPPORTED; }
+    const DensePlan& D = *pe->plan->dense;
+    const double S = 8.0 * (double)(1ull << D.n_eff);
+    const bool tc = prec == TLQ_MIXED_TC;
+    const bool gen = D.product_init && D.gen_first && !tc;
+    const std::vector<DensePassDev>& fwd = D.product_init ? D.fwd_passes : D.passes;
+    const int nx = (int)D.xterms.size();
+    double b = gen ? 0.0 : S;                              // the start state, written once
+    for (size_t p = 0; p < fwd.size(); ++p) {
+        if (!(gen && p == 0)) b += S;                      // read
+        const bool last = p + 1 == fwd.size();
+        if (want_grad || !last || nx > 0) b += S;          // write (not the last one of an energy)
+    }
+    b += nx * S;                                           // X/Y terms: one read each
+    if (want_grad) {
+        b += S;                                            // lam = (diagonal part of H) psi
+        if (nx > 0) b += 3 * S;                            // lam += X/Y strings of psi
+        for (size_t p = 0; p < D.passes.size(); ++p)      // reverse passes: read both, write both
+            b += 2 * S + (D.rev_store[p] ? 2 * S : 0.0);
+    }
+    *bytes = b;
     return TLQ_OK;
 }
 

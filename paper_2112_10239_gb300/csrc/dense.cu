@@ -33,10 +33,113 @@ namespace tlq {
 namespace {
 
 constexpr int kTile = 1 << kDenseTileBits;        // 4096 amplitudes
+__host__ __device__ constexpr int padded_amps_c(int W) { return (1 << W) + (1 << (W - 3)); }
 constexpr int kThreads = kTile / 16;                // 16 amplitudes per thread per register pass
 constexpr int kMaxLayerClasses = kDenseMaxLayerClasses;
 constexpr int kMaxDistWords = kDenseMaxDistWords;  // (d, mask) int pairs staged in shared memory
 constexpr int kMaxTab = kDenseMaxTab;              // phase-table entries staged per layer
+
+// ---- layer 0 as a product state ----------------------------------------------------------
+//
+// Layer 0 acts on |0..0>, so the state after it is written directly instead of streamed: a
+// product of single-qubit factors, amplitude(x) = prod_q f_q(x_q) with f_q(0) = cos(a_q/2) and
+// f_q(1) = sin(a_q/2) (RY) or -i sin(a_q/2) (RX), 1 and 0 for a qubit without a rotation; then
+// layer 0's diagonal classes (phase exp(-i a/2 (N - 2c)) from the phase table, or the CZ sign
+// (-1)^c). Sixteen consecutive amplitudes are built at once: the product over bits 4.. once,
+// the low four bits by doubling, the classes by split counts over bits 0..3.
+struct InitGates { int32_t gate[32]; };
+
+__device__ __forceinline__ float2 init_factor(const InitGates& I, const tlq_gate* gates, const float2* GT, int q,
+                                              int bit) {
+    const int g = I.gate[q];
+    if (g < 0) return make_float2(bit ? 0.f : 1.f, 0.f);
+    const float2 cs = GT[g];
+    if (!bit) return make_float2(cs.x, 0.f);
+    return gates[g].kind == TLQ_RY ? make_float2(cs.y, 0.f) : make_float2(0.f, -cs.y);
+}
+
+// Shared-memory staging of the product state's per-qubit factors and layer 0's classes.
+struct InitStage {
+    float2 f[32][2];
+    DenseClassDev cls[kMaxLayerClasses];
+    DensePassClassDev pcd[kMaxLayerClasses];
+    int32_t dist[kMaxDistWords];
+    int32_t woff[kMaxLayerClasses];
+    int32_t toff[kMaxLayerClasses];
+    float2 tab[kMaxTab];
+    int nc;
+    int staged;   // the phase tables fit: read from shared memory, else from global memory
+};
+
+// Stage the factors and layer 0's classes (every thread of the block calls this; ends with a
+// barrier).
+__device__ void stage_init(InitStage& S, int n_eff, const InitGates& I, const tlq_gate* gates, const float2* GT,
+                           const DenseClassDev* classes, int cls_off, int ncls, const DensePassClassDev* pcd,
+                           const int32_t* dists, const float2* ptab, int tid, int nthreads) {
+    if (tid < 32) {
+        S.f[tid][0] = tid < n_eff ? init_factor(I, gates, GT, tid, 0) : make_float2(1.f, 0.f);
+        S.f[tid][1] = tid < n_eff ? init_factor(I, gates, GT, tid, 1) : make_float2(0.f, 0.f);
+    }
+    const int nc = ncls < kMaxLayerClasses ? ncls : kMaxLayerClasses;
+    if (tid < nc) {
+        S.cls[tid] = classes[cls_off + tid];
+        S.pcd[tid] = pcd[tid];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int w = 0, t = 0;
+        for (int c = 0; c < nc; ++c) {
+            S.woff[c] = w;
+            w += 2 * S.cls[c].ndist;
+            S.toff[c] = t;
+            t += S.cls[c].kind == 0 ? S.cls[c].nterms + 1 : 0;
+        }
+        S.staged = t <= kMaxTab;
+        S.nc = nc;
+    }
+    __syncthreads();
+    for (int c = 0; c < nc; ++c) {
+        for (int k = tid; k < 2 * S.cls[c].ndist; k += nthreads)
+            if (S.woff[c] + k < kMaxDistWords) S.dist[S.woff[c] + k] = dists[2 * S.cls[c].dist_off + k];
+        if (S.staged && S.cls[c].kind == 0)
+            for (int e = tid; e <= S.cls[c].nterms; e += nthreads) S.tab[S.toff[c] + e] = ptab[S.cls[c].tab_off + e];
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int class_count(const DenseClassDev& c, const int32_t* dist, uint32_t x);
+__device__ __forceinline__ void split_deltas(const DenseClassDev& C, const DensePassClassDev& pc, uint32_t xb,
+                                             int (&Ak)[4]);
+__device__ __forceinline__ int split_count(const DensePassClassDev& pc, int cnt0, const int (&Ak)[4], int j);
+
+// The 16 amplitudes x0 | j (x0 a multiple of 16) of the state after layer 0.
+__device__ __forceinline__ void gen16(const InitStage& S, int n_eff, const float2* ptab, uint32_t x0, float2 (&v)[16]) {
+    v[0] = make_float2(1.f, 0.f);
+    for (int q = 4; q < n_eff; ++q) v[0] = cmul(v[0], S.f[q][(x0 >> q) & 1]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 f0 = S.f[k][0], f1 = S.f[k][1];
+#pragma unroll
+        for (int j = 0; j < (1 << k); ++j) {
+            v[j | (1 << k)] = cmul(v[j], f1);
+            v[j] = cmul(v[j], f0);
+        }
+    }
+    for (int ci = 0; ci < S.nc; ++ci) {
+        const DenseClassDev& C = S.cls[ci];
+        const DensePassClassDev& pc = S.pcd[ci];
+        const int cnt0 = class_count(C, S.dist + S.woff[ci], x0);
+        int Ak[4];
+        split_deltas(C, pc, x0, Ak);
+        const float2* tab = S.staged ? S.tab + S.toff[ci] : ptab + C.tab_off;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int cnt = split_count(pc, cnt0, Ak, j);
+            if (C.kind == 0) v[j] = cmul(v[j], tab[cnt]);
+            else if (cnt & 1) v[j] = make_float2(-v[j].x, -v[j].y);
+        }
+    }
+}
 
 struct PassArgs {
     DensePassDev pass;
@@ -57,6 +160,10 @@ struct PassArgs {
     double* npartial;       // tensor-core passes: per-half <psi|psi> partials
     int32_t* err;           // kernel error word
     float2* lam;            // gradient mode, final pass: lam = (diagonal part of H) psi, else null
+    // generating pass (dense_pass_kernel<true>): layer 0's product state replaces the input tiles
+    InitGates init;
+    int32_t init_class_off, init_nclass;
+    const DensePassClassDev* init_pcd;
 };
 
 // Global amplitude index of local tile index t.
@@ -228,6 +335,15 @@ __device__ __forceinline__ void group_epilogue(const PassArgs& A, const DensePas
 // Persistent pass kernel: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // with two shared-memory tile buffers; the cp.async copy of the next tile runs while the
 // current one is processed. The last register pass writes its 16 amplitudes straight to HBM.
+__host__ __device__ constexpr size_t dense_pass_smem_base() {
+    return ((2 * (size_t)padded_amps_c(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
+             kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * (sizeof(DenseClassDev) + sizeof(DensePassClassDev)) +
+             2 * kMaxLayerClasses * sizeof(int32_t) + 16 * sizeof(float)) + 15) / 16 * 16;
+}
+
+// GEN: the first forward pass of a low tile whose first group starts at bit 0 -- its input is
+// layer 0's product state, generated in registers for group 0 (gen16) instead of read from HBM.
+template <bool GEN>
 __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_constant__ PassArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2* bufs = reinterpret_cast<float2*>(smem_raw);                              // 2 x padded_amps(12)
@@ -241,21 +357,27 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_co
     const DensePassDev& P = A.pass;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
+    InitStage* S = reinterpret_cast<InitStage*>(smem_raw + dense_pass_smem_base());   // GEN only
     const uint32_t ntiles = 1u << (A.n_eff - kDenseTileBits);
 
-    if (blockIdx.x < ntiles) issue_tile(P, blockIdx.x, A.state, bufs, tid);
+    if (!GEN && blockIdx.x < ntiles) issue_tile(P, blockIdx.x, A.state, bufs, tid);
 
     stage_classes(P, A.classes, A.pcd, A.stage, A.dists, A.ptab, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab, tid);
+    if (GEN)
+        stage_init(*S, A.n_eff, A.init, A.gates, A.GT, A.classes, A.init_class_off, A.init_nclass, A.init_pcd, A.dists,
+                   A.ptab, tid, kThreads);
 
     float eacc = 0.f;
     int i = 0;
     for (uint32_t t_id = blockIdx.x; t_id < ntiles; t_id += gridDim.x, ++i) {
         const int b = i & 1;
         float2* tile = bufs + b * padded_amps(kDenseTileBits);
-        wait_tiles();        // this thread's copies of tile t_id have landed
-        __syncthreads();     // ... and everyone else's
-        const uint32_t next = t_id + gridDim.x;
-        if (next < ntiles) issue_tile(P, next, A.state, bufs + (b ^ 1) * padded_amps(kDenseTileBits), tid);
+        if (!GEN) {
+            wait_tiles();        // this thread's copies of tile t_id have landed
+            __syncthreads();     // ... and everyone else's
+            const uint32_t next = t_id + gridDim.x;
+            if (next < ntiles) issue_tile(P, next, A.state, bufs + (b ^ 1) * padded_amps(kDenseTileBits), tid);
+        }
         for (int g = 0; g < P.ngroups; ++g) {
             const int s = P.group_s[g];
             const unsigned m = P.group_mask[g];
@@ -279,7 +401,8 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_co
             const int base = (tid & lowmask) | ((tid >> s) << (s + 4));
             float2* p = tile + pad16(base);
             float2 v[16];
-            load16(v, p, stride);
+            if (GEN && g == 0) gen16(*S, A.n_eff, A.ptab, tile_x(P, t_id, (uint32_t)base), v);   // s == 0
+            else load16(v, p, stride);
             if (kd[0] >= 0) apply_rot<0>(v, kd[0], c[0], sn[0]);
             if (kd[1] >= 0) apply_rot<1>(v, kd[1], c[1], sn[1]);
             if (kd[2] >= 0) apply_rot<2>(v, kd[2], c[2], sn[2]);
@@ -313,6 +436,9 @@ size_t dense_pass_smem() {
            kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * (sizeof(DenseClassDev) + sizeof(DensePassClassDev)) +
            2 * kMaxLayerClasses * sizeof(int32_t) + 16 * sizeof(float);
 }
+
+// The generating pass keeps layer 0's staging (InitStage) after the pass kernel's own data.
+size_t dense_pass_gen_smem() { return dense_pass_smem_base() + sizeof(InitStage); }
 
 // ---- tensor-core passes (mixed precision: split TF32 products, FP32 accumulation) ----------
 //
@@ -986,91 +1112,19 @@ __global__ void __launch_bounds__(kMeasThreads) pergate_grad_kernel(const float2
 // classes (phase exp(-i a/2 (N - 2c)) from the phase table, or the CZ sign (-1)^c). Each
 // thread writes 16 consecutive amplitudes: the product over bits 4.. once, the low four bits
 // by doubling. Replaces the layer-0 passes of the forward sweep.
-struct InitGates { int32_t gate[32]; };
-
-__device__ __forceinline__ float2 init_factor(const InitGates& I, const tlq_gate* gates, const float2* GT, int q,
-                                              int bit) {
-    const int g = I.gate[q];
-    if (g < 0) return make_float2(bit ? 0.f : 1.f, 0.f);
-    const float2 cs = GT[g];
-    if (!bit) return make_float2(cs.x, 0.f);
-    return gates[g].kind == TLQ_RY ? make_float2(cs.y, 0.f) : make_float2(0.f, -cs.y);
-}
-
 __global__ void __launch_bounds__(256) dense_product_init_kernel(float2* psi, int n_eff,
                                                                   const __grid_constant__ InitGates I,
                                                                   const tlq_gate* gates, const float2* GT,
                                                                   const DenseClassDev* classes, int cls_off, int ncls,
                                                                   const DensePassClassDev* pcd, const int32_t* dists,
                                                                   const float2* ptab) {
-    // per-qubit factors and layer 0's classes, staged once per block
-    __shared__ float2 s_f[32][2];
-    __shared__ DenseClassDev s_cls[kMaxLayerClasses];
-    __shared__ DensePassClassDev s_pcd[kMaxLayerClasses];
-    __shared__ int32_t s_dist[kMaxDistWords];
-    __shared__ int32_t s_woff[kMaxLayerClasses];
-    __shared__ int32_t s_toff[kMaxLayerClasses];
-    __shared__ float2 s_tab[kMaxTab];
-    __shared__ int s_staged;
-    const int tid = threadIdx.x;
-    if (tid < 32) {
-        s_f[tid][0] = tid < n_eff ? init_factor(I, gates, GT, tid, 0) : make_float2(1.f, 0.f);
-        s_f[tid][1] = tid < n_eff ? init_factor(I, gates, GT, tid, 1) : make_float2(0.f, 0.f);
-    }
-    const int nc = ncls < kMaxLayerClasses ? ncls : kMaxLayerClasses;
-    if (tid < nc) {
-        s_cls[tid] = classes[cls_off + tid];
-        s_pcd[tid] = pcd[tid];
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int w = 0, t = 0;
-        for (int c = 0; c < nc; ++c) {
-            s_woff[c] = w;
-            w += 2 * s_cls[c].ndist;
-            s_toff[c] = t;
-            t += s_cls[c].kind == 0 ? s_cls[c].nterms + 1 : 0;
-        }
-        s_staged = t <= kMaxTab;   // the phase tables fit: read them from shared memory
-    }
-    __syncthreads();
-    for (int c = 0; c < nc; ++c) {
-        for (int k = tid; k < 2 * s_cls[c].ndist; k += blockDim.x)
-            if (s_woff[c] + k < kMaxDistWords) s_dist[s_woff[c] + k] = dists[2 * s_cls[c].dist_off + k];
-        if (s_staged && s_cls[c].kind == 0)
-            for (int e = tid; e <= s_cls[c].nterms; e += blockDim.x) s_tab[s_toff[c] + e] = ptab[s_cls[c].tab_off + e];
-    }
-    __syncthreads();
+    __shared__ InitStage S;
+    stage_init(S, n_eff, I, gates, GT, classes, cls_off, ncls, pcd, dists, ptab, threadIdx.x, blockDim.x);
     const uint64_t nblk = 1ull << (n_eff - 4);
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + tid; t < nblk; t += (uint64_t)gridDim.x * blockDim.x) {
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nblk; t += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t x0 = (uint32_t)(t << 4);
         float2 v[16];
-        v[0] = make_float2(1.f, 0.f);
-        for (int q = 4; q < n_eff; ++q) v[0] = cmul(v[0], s_f[q][(x0 >> q) & 1u]);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float2 f0 = s_f[k][0], f1 = s_f[k][1];
-#pragma unroll
-            for (int j = 0; j < (1 << k); ++j) {
-                v[j | (1 << k)] = cmul(v[j], f1);
-                v[j] = cmul(v[j], f0);
-            }
-        }
-        // layer 0's diagonal from split counts over bits 0..3 (one full count per class)
-        for (int ci = 0; ci < nc; ++ci) {
-            const DenseClassDev& C = s_cls[ci];
-            const DensePassClassDev& pc = s_pcd[ci];
-            const int cnt0 = class_count(C, s_dist + s_woff[ci], x0);
-            int Ak[4];
-            split_deltas(C, pc, x0, Ak);
-            const float2* tab = s_staged ? s_tab + s_toff[ci] : ptab + C.tab_off;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int cnt = split_count(pc, cnt0, Ak, j);
-                if (C.kind == 0) v[j] = cmul(v[j], tab[cnt]);
-                else if (cnt & 1) v[j] = make_float2(-v[j].x, -v[j].y);
-            }
-        }
+        gen16(S, n_eff, ptab, x0, v);
         float4* out = reinterpret_cast<float4*>(psi + x0);
 #pragma unroll
         for (int i = 0; i < 8; ++i) out[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
@@ -1159,7 +1213,15 @@ int launch_dense(DenseLaunch& L, void* stream) {
     int launches = 0;
     const size_t smem = dense_pass_smem();
     const size_t asmem = dense_adjoint_smem();
-    if ((e = cudaFuncSetAttribute(dense_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(dense_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return (int)e;
+    // layer 0's product state generated inside the first forward pass (no start kernel, no read
+    // of the start state) when that pass is a low tile whose first group starts at bit 0
+    const bool gen_first = !L.per_gate && !L.tc && L.product_init && L.gen_first;
+    const size_t gsmem = dense_pass_gen_smem();
+    if (gen_first && (e = cudaFuncSetAttribute(dense_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)gsmem)) != cudaSuccess)
         return (int)e;
     size_t tc_smem = 0;
     int tc_nblk = 0;
@@ -1194,16 +1256,17 @@ int launch_dense(DenseLaunch& L, void* stream) {
         }
         if (b == 0 && L.ev_begin && (e = cudaEventRecord((cudaEvent_t)L.ev_begin, st)) != cudaSuccess) return (int)e;
         const bool product_init = !L.per_gate && L.product_init;
-        if (product_init) {   // the state after layer 0, written directly
-            InitGates I;
-            for (int q = 0; q < 32; ++q) I.gate[q] = q < L.n_eff ? L.host_init_gate[q] : -1;
+        InitGates I;
+        for (int q = 0; q < 32; ++q) I.gate[q] = q < L.n_eff ? L.host_init_gate[q] : -1;
+        if (product_init && !gen_first) {   // the state after layer 0, written directly
             dense_product_init_kernel<<<grid_sweep, 256, 0, st>>>(psi, L.n_eff, I, L.gates, GT, L.classes,
                                                                   L.init_class_off, L.init_nclass, L.init_pcd,
                                                                   L.dists, PT);
-        } else {
+            ++launches;
+        } else if (!product_init) {
             init_state_kernel<<<grid_sweep, 256, 0, st>>>(psi, N);
+            ++launches;
         }
-        ++launches;
         double* eout = L.energy + b;
         if ((e = cudaMemsetAsync(eout, 0, sizeof(double), st)) != cudaSuccess) return (int)e;
         if (L.per_gate) {
@@ -1229,6 +1292,10 @@ int launch_dense(DenseLaunch& L, void* stream) {
             A.npartial = L.partial + dense_norm_offset(L.n_eff);
             A.err = L.err;
             A.lam = nullptr;
+            A.init = I;
+            A.init_class_off = L.init_class_off;
+            A.init_nclass = L.init_nclass;
+            A.init_pcd = L.init_pcd;
             const int grid = dense_grid(L.n_eff, L.sm_count);
             const int ntiles = 1 << (L.n_eff - kDenseTileBits);
             const int tc_grid = std::min(std::min((ntiles + 1) / 2, L.sm_count), kMaxSms);   // one CTA per SM
@@ -1240,9 +1307,12 @@ int launch_dense(DenseLaunch& L, void* stream) {
                 if (gout) {
                     A.pass.store = 1;   // the adjoint starts from the final state in HBM
                     if (A.pass.measure_group >= 0) A.lam = lam;
+                } else if (p == n_fwd - 1 && L.n_xterms == 0 && !L.keep_state) {
+                    A.pass.store = 0;   // energies only: nothing reads the final state
                 }
                 if (L.tc) dense_tc_pass_kernel<<<tc_grid, kTcPassThreads, tc_smem, st>>>(A, tc_nblk);
-                else dense_pass_kernel<<<grid, kThreads, smem, st>>>(A);
+                else if (gen_first && p == 0) dense_pass_kernel<true><<<grid, kThreads, gsmem, st>>>(A);
+                else dense_pass_kernel<false><<<grid, kThreads, smem, st>>>(A);
                 ++launches;
                 if (A.pass.measure_group >= 0) measured = true;
             }

@@ -188,6 +188,9 @@ struct DensePlan {
     // psi' = S psi with S = diag(1, i) on that qubit: S RX(a) S^dagger = RY(a), S commutes with
     // every diagonal gate and S|0> = |0>, so the RX gates run as the real RY form and only the
     // X/Y letters of the measured terms change (S X S^dagger = Y, S Y S^dagger = -X).
+    // The first forward pass generates layer 0's product state in registers instead of reading
+    // a start state written by a separate kernel (a low tile whose first group starts at bit 0).
+    bool gen_first = false;
     uint32_t frame_mask = 0;                // qubits carried in the rotated frame
     std::vector<tlq_gate> fgates;           // the circuit's gates with RX -> RY on those qubits
     std::vector<DenseXTermDev> fxterms;     // xterms with the letters converted on those qubits
@@ -460,6 +463,9 @@ struct DenseLaunch {
     double* grad = nullptr;               // [B][n_params] or null (energies only)
     bool per_gate = false;                // plain per-gate sweeps (baseline)
     bool tc = false;                      // forward rotation groups on the tensor cores (TLQ_MIXED_TC)
+    bool gen_first = false;               // DensePlan::gen_first (FP32 passes only)
+    bool keep_state = false;              // the caller reads the final state (else an energy-only
+                                          // call skips the last pass's store when no X/Y term needs it)
     int sm_count = 0;
     void* ev_begin = nullptr;
     void* ev_end = nullptr;

@@ -931,6 +931,8 @@ std::shared_ptr<DensePlan> make_dense_plan(const Circuit& c, const Ham& h, std::
         const int gbit0[4] = {0, 1, 2, 3};
         for (int ci = D->init_class_off; ci < D->init_class_off + D->init_nclass; ++ci)
             D->init_pcd.push_back(split_counts(D->classes[ci], gbit0));
+        D->gen_first = !D->fwd_passes.empty() && D->fwd_passes[0].strided == 0 && D->fwd_passes[0].group_s[0] == 0 &&
+                       D->init_nclass <= kDenseMaxLayerClasses;
     }
     // adjoint slots: rotation k of group g -> 4g + k; staged class ci (kind 0, a parameter) ->
     // 4 * kDenseMaxGroups + ci; collected per parameter with a counting sort (pass-major order)

@@ -168,6 +168,29 @@ def test_dense_plan_info(B, hctx):
     assert n_x == sum(1 for _, _, letters in q.terms if set(letters) - {"Z"})
 
 
+def test_dense_plan_bytes(B, hctx):
+    # the schedule's HBM traffic, recounted from the pass counts: the n=28 QAOA forward starts in
+    # a low tile at bit 0, so its first pass generates layer 0's state (no start write, no first
+    # read) and an energy without X/Y terms skips the last write; the tensor-core passes keep the
+    # start kernel
+    p = W.qaoa_n28_p4()
+    c, h = hctx.problem(p)
+    n_eff, n_passes, n_fwd, n_rev_store, n_x, _ = B.tlq_plan_dense_info(hctx.h, c.h, h.h)
+    S = 8.0 * 2 ** n_eff
+    assert B.tlq_plan_dense_bytes(hctx.h, c.h, h.h, False) == (2 * n_fwd - 2) * S
+    assert B.tlq_plan_dense_bytes(hctx.h, c.h, h.h, False, B.TLQ_MIXED_TC) == (2 * n_fwd) * S
+    grad = (2 * n_fwd - 1) * S + S + 2 * n_passes * S + 2 * n_rev_store * S
+    assert B.tlq_plan_dense_bytes(hctx.h, c.h, h.h, True) == grad
+    # X/Y terms: one read each, and the last forward write stays (the terms read the final state)
+    q = W.random_nonlocal_problem(14, 2, 1, seed=3)
+    c2, h2 = hctx.problem(q)
+    n_eff, n_passes, n_fwd, n_rev_store, n_x, _ = B.tlq_plan_dense_info(hctx.h, c2.h, h2.h)
+    assert n_x > 0
+    S = 8.0 * 2 ** n_eff
+    e = B.tlq_plan_dense_bytes(hctx.h, c2.h, h2.h, False)
+    assert e in ((2 * n_fwd - 1 + n_x) * S, (2 * n_fwd + 1 + n_x) * S)   # with or without the start kernel
+
+
 def test_partial_trace_argument_checks(B, hctx):
     # validation happens before any device work: EINVAL for bad kept-qubit lists, then the
     # host-only context reports EUNSUPPORTED for a valid request
