@@ -145,6 +145,41 @@ __device__ __forceinline__ T2 phase_of(const T2* tab, int tab1, int tab2, int W,
     return ph;
 }
 
+// Diagonal phases of the 16 amplitudes xb | (j << s), j < 16 (register bits [s, s + 4)), handed
+// to use(j, phase) one at a time. A chunk table whose index bits (its qubits and its crossing bit)
+// lie outside the register bits gives the same entry for all 16 amplitudes and is read once. Same
+// products as phase_of (up to the order of the factors when three chunks are used).
+template <typename T2, typename F>
+__device__ __forceinline__ void for_phases16(const T2* tab, int tab1, int tab2, int W, int xb, int s, F use) {
+    const int b1 = (W - 7) < 7 ? (W - 7) : 7;
+    const bool v0 = s < 7;                           // chunk 0: bits 0..6
+    const bool v1 = s <= 6 + b1 && s + 3 >= 6;       // chunk 1: crossing bit 6, bits 7..6 + b1
+    const bool v2 = W > 14 && s + 3 >= 13;           // chunk 2: crossing bit 13, bits 14..
+    auto e0 = [&](int x) {
+        const int t0 = x & 127;
+        return tab[t0 + (t0 >> 4)];
+    };
+    auto e1 = [&](int x) { return tab[tab1 + (((x >> 7) & ((1 << b1) - 1)) | (((x >> 6) & 1) << b1))]; };
+    auto e2 = [&](int x) {
+        const int b2 = W - 14;
+        return tab[tab2 + (((x >> 14) & ((1 << b2) - 1)) | (((x >> 13) & 1) << b2))];
+    };
+    if (!v0 && v1 && !v2) {          // the register bits lie in chunk 1
+        T2 h = e0(xb);
+        if (W > 14) h = cmul(h, e2(xb));
+#pragma unroll
+        for (int j = 0; j < 16; ++j) use(j, cmul(h, e1(xb | (j << s))));
+    } else if (v0 && !v1 && !v2) {   // the register bits lie in chunk 0
+        T2 h = e1(xb);
+        if (W > 14) h = cmul(h, e2(xb));
+#pragma unroll
+        for (int j = 0; j < 16; ++j) use(j, cmul(e0(xb | (j << s)), h));
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) use(j, phase_of(tab, tab1, tab2, W, xb | (j << s)));
+    }
+}
+
 // ---- kernel parameters ---------------------------------------------------------------------
 
 struct ConeArgs {
@@ -322,8 +357,7 @@ __device__ void pass_fwd(T2* psi, int s, unsigned m, bool diag, const Team& tm, 
         if (kd[3] >= 0) apply_rot<3>(v, kd[3], c[3], sn[3]);
         if (diag) {
             const int xb = base | M.hi;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = cmul(v[j], phase_of(M.tab, M.tab1, M.tab2, M.Wt, xb | (j << s)));
+            for_phases16(M.tab, M.tab1, M.tab2, M.Wt, xb, s, [&](int j, T2 ph) { v[j] = cmul(v[j], ph); });
         }
         store16(v, p, stride);
     }
@@ -467,12 +501,10 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, const Team& tm, co
                     }
                 }
             }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const T2 ph = phase_of(M.tab, M.tab1, M.tab2, M.Wt, xb | (j << s));   // conjugated table
+            for_phases16(M.tab, M.tab1, M.tab2, M.Wt, xb, s, [&](int j, T2 ph) {   // conjugated table
                 p[j] = cmul(p[j], ph);
                 l[j] = cmul(l[j], ph);
-            }
+            });
         }
         if constexpr (!DIAG) {
             real g0 = 0, g1 = 0, g2 = 0, g3 = 0;
@@ -615,8 +647,7 @@ __device__ void init_product_state(const TeamMem<T2>& M, unsigned live, bool dia
         }
         if (diag) {
             const int xb = base | M.hi;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = cmul(v[j], phase_of(M.tab, M.tab1, M.tab2, M.Wt, xb | j));
+            for_phases16(M.tab, M.tab1, M.tab2, M.Wt, xb, 0, [&](int j, T2 ph) { v[j] = cmul(v[j], ph); });
         }
         store16(v, M.psi + pad16(base), 1);
     }
