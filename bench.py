@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tlq", choices=["tlq", "reference"])
     ap.add_argument("--workload", default="tfim_n20_L6_B64",
-                    help="tfim_n20_L6_B64 (default), tfim_n500_L4_B256, tfim_n8_L2_B1 or qaoa_n<N>_p<P> "
-                         "(3-regular graph, dense statevector path, one parameter set)")
+                    help="tfim_n20_L6_B64 (default), tfim_n500_L4_B256, tfim_n8_L2_B1, tfim_n<N>_L<L>_B<B> (any "
+                         "Ising chain, h ~ U[0.5, 1.5], seed 5) or qaoa_n<N>_p<P> (3-regular graph, dense "
+                         "statevector path, one parameter set)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "mixed_tc"],
                     help="precision of the timed workload (mixed_tc: tensor-core gate blocks on the dense path)")
     ap.add_argument("--no-extras", action="store_true",
@@ -71,6 +72,12 @@ def workload(name):
         return W.tfim_n500_L4_B256()
     if name == "tfim_n8_L2_B1":
         return W.tfim_n8_L2()
+    m = re.fullmatch(r"tfim_n(\d+)_L(\d+)_B(\d+)", name)
+    if m:   # any chain: h_i ~ U[0.5, 1.5], brick-wall ansatz, seed 5
+        n, L, Bs = int(m.group(1)), int(m.group(2)), int(m.group(3))
+        if not (2 <= n and 1 <= L and 1 <= Bs):
+            raise SystemExit("tfim workloads take n >= 2, L >= 1, B >= 1")
+        return W.tfim_problem(n, L, Bs, seed=5, h_range=(0.5, 1.5), name=name)
     m = re.fullmatch(r"qaoa_n(\d+)_p(\d+)", name)
     if m:
         n, p = int(m.group(1)), int(m.group(2))
