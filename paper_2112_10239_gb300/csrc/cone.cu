@@ -45,8 +45,22 @@ namespace tlq {
 // window's. Tables and layer records still cover the whole window (`Wt` qubits); the
 // branch's top bit enters every phase lookup as the constant `hi`.
 
+// Global-tier tiles (FP32 states wider than a tile): 2^12 amplitudes, 16 per thread of a
+// 256-thread half of the CTA; the two halves take alternate tiles, each with its own buffers.
+// A high tile keeps window bits 0..7 (see TileMap). The per-sweep partial sums: three rotation
+// groups of four (slots 0..11), then the diagonal gates (an RZ and a pair per qubit, from 16).
+constexpr int kTileBits = 12;
+constexpr int kTileLowBits = 8;
+constexpr int kTileTeams = 2;
+constexpr int kMaxSweepSlots = 16 + 2 * 20;
+
+__host__ __device__ inline bool tiled_state(int W, int real_bytes, bool smem_state) {
+    return !smem_state && real_bytes == 4 && W > kTileBits;
+}
+
 struct TeamLayout {
     int psi, lam, tab, info, fac, red, bytes;
+    int tile;           // tiled global tier: the psi tile, then (gradients) the lam tile
     int tab1, tab2;     // entry offsets of chunk tables 1 and 2
     int tab_entries;    // total table entries (unpadded) built per layer
 };
@@ -62,6 +76,9 @@ __host__ __device__ inline TeamLayout team_layout(int W, int Wt, int tt, int rea
     if (smem_state) off += padded_amps(W) * r2;
     L.lam = off;
     if (smem_state && grad) off += padded_amps(W) * r2;
+    const bool tiled = tiled_state(W, real_bytes, smem_state);
+    L.tile = off;
+    if (tiled) off += kTileTeams * padded_amps(kTileBits) * r2 * (grad ? 2 : 1);
     const int b1 = (Wt - 7) < 7 ? (Wt - 7) : 7;
     const int b2 = Wt > 14 ? Wt - 14 : 0;
     L.tab1 = 136;
@@ -77,7 +94,7 @@ __host__ __device__ inline TeamLayout team_layout(int W, int Wt, int tt, int rea
     off += 128 * r2;
     off = (off + 15) & ~15;
     L.red = off;
-    off += 2 * kMaxPassSlots * nwarps_of(tt) * real_bytes;
+    off += 2 * (tiled ? kMaxSweepSlots : kMaxPassSlots) * nwarps_of(tt) * real_bytes;
     L.bytes = (off + 15) & ~15;
     return L;
 }
@@ -205,6 +222,7 @@ template <typename T2>
 struct TeamMem {
     T2* psi;
     T2* lam;
+    T2* tile;              // tiled global tier: the psi tile (the lam tile follows it)
     T2* tab;
     unsigned char* info;   // two buffers of info_bytes, then the per-qubit factor staging area
     void* red;
@@ -327,10 +345,32 @@ __device__ void stage_layer(const int32_t* lp, const T2* GT, const Team& tm, con
     tm.sync();
 }
 
+// ---- global tier: tiles ---------------------------------------------------------------------
+//
+// A state too wide for shared memory lives in global memory, and a layer is applied in a few
+// sweeps over it. A sweep stages one tile of 2^12 amplitudes at a time in shared memory, runs
+// one or more register passes on it and writes it back. A low tile holds window bits 0..11
+// (the tile index gives the bits above); a high tile holds window bits 0..7 and one 4-bit
+// register group g..g+3 (the tile index gives the bits in between and above). Window bits 0..4
+// stay the lane bits of every pass, so the passes' warp reductions are unchanged.
+struct TileMap {
+    int a;       // tile bits [0, a) are window bits [0, a)
+    int g;       // tile bits [a, 12) are window bits [g, g + 12 - a)
+    int fix;     // window bits given by the tile index
+    int s_loc;   // tile position of the pass's register bits
+    bool first;  // the half's first tile of a sweep: the pass's partial sums start from zero
+    int nw;      // partial sums: warps of the CTA (the slot stride) ...
+    int warp0;   // ... and the CTA warp index of the half's first warp
+    __device__ __forceinline__ int x(int i) const { return (i & ((1 << a) - 1)) | ((i >> a) << g) | fix; }
+};
+
 // Forward pass on register bits [s, s+4): rotations on the bits in `m`, then the
 // layer's diagonal phase when `diag`.
-template <typename real, typename T2>
-__device__ void pass_fwd(T2* psi, int s, unsigned m, bool diag, const Team& tm, const TeamMem<T2>& M, int par) {
+// TILE: psi is a shared-memory tile (tmap gives its bits); s is the window position of the
+// register bits and tmap->s_loc their tile position.
+template <typename real, typename T2, bool TILE = false>
+__device__ void pass_fwd(T2* psi, int s, unsigned m, bool diag, const Team& tm, const TeamMem<T2>& M, int par,
+                         const TileMap* tmap = nullptr) {
     const int W = M.W;
     const T2* cs = info_cs(M, par);
     const int* kinds = info_kinds(M, par);
@@ -343,11 +383,12 @@ __device__ void pass_fwd(T2* psi, int s, unsigned m, bool diag, const Team& tm, 
         c[k] = v.x;
         sn[k] = v.y;
     }
-    const int nout = 1 << (W - 4);
-    const int lowmask = (1 << s) - 1;
-    const int stride = pass_stride(s);
+    const int sl = TILE ? tmap->s_loc : s;
+    const int nout = 1 << ((TILE ? kTileBits : W) - 4);
+    const int lowmask = (1 << sl) - 1;
+    const int stride = pass_stride(sl);
     for (int o = tm.tid; o < nout; o += tm.tt) {
-        const int base = (o & lowmask) | ((o >> s) << (s + 4));
+        const int base = (o & lowmask) | ((o >> sl) << (sl + 4));
         T2* p = psi + pad16(base);
         T2 v[16];
         load16(v, p, stride);
@@ -356,7 +397,7 @@ __device__ void pass_fwd(T2* psi, int s, unsigned m, bool diag, const Team& tm, 
         if (kd[2] >= 0) apply_rot<2>(v, kd[2], c[2], sn[2]);
         if (kd[3] >= 0) apply_rot<3>(v, kd[3], c[3], sn[3]);
         if (diag) {
-            const int xb = base | M.hi;
+            const int xb = (TILE ? tmap->x(base) : base) | M.hi;
             for_phases16(M.tab, M.tab1, M.tab2, M.Wt, xb, s, [&](int j, T2 ph) { v[j] = cmul(v[j], ph); });
         }
         store16(v, p, stride);
@@ -368,14 +409,14 @@ __device__ void pass_fwd(T2* psi, int s, unsigned m, bool diag, const Team& tm, 
 // in `m`, emit Im<lam|G|psi> and un-apply it from psi and lam. Per-warp partial sums go to
 // red[slot * nw + warp]: slots 0..3 rotations (register bit), 4.. diagonal gates in program
 // order.
-template <typename real, typename T2, bool DIAG, bool FINAL = false>
+template <typename real, typename T2, bool DIAG, bool FINAL = false, bool TILE = false>
 __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, const Team& tm, const TeamMem<T2>& M, int par,
-                         real* red) {
+                         real* red, const TileMap* tmap = nullptr) {
     const int W = M.W;
     const T2* cs = info_cs(M, par);
     const int* kinds = info_kinds(M, par);
-    const int nw = nwarps_of(tm.tt);
-    const int warp = tm.tt >= 32 ? (tm.tid >> 5) : 0;
+    const int nw = TILE ? tmap->nw : nwarps_of(tm.tt);
+    const int warp = TILE ? tmap->warp0 + (tm.tid >> 5) : (tm.tt >= 32 ? (tm.tid >> 5) : 0);
     const bool leader = tm.tt >= 32 ? ((tm.tid & 31) == 0) : (tm.tid == 0);
     int kd[4];
     real c[4], sn[4];
@@ -386,12 +427,13 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, const Team& tm, co
         c[k] = v.x;
         sn[k] = -v.y;   // un-apply: angle -> -angle
     }
-    const int nout = 1 << (W - 4);
-    const int lowmask = (1 << s) - 1;
-    const int stride = pass_stride(s);
-    bool first = true;
+    const int sl = TILE ? tmap->s_loc : s;
+    const int nout = 1 << ((TILE ? kTileBits : W) - 4);
+    const int lowmask = (1 << sl) - 1;
+    const int stride = pass_stride(sl);
+    bool first = TILE ? tmap->first : true;
     for (int o = tm.tid; o < nout; o += tm.tt) {
-        const int base = (o & lowmask) | ((o >> s) << (s + 4));
+        const int base = (o & lowmask) | ((o >> sl) << (sl + 4));
         T2* pp = psi + pad16(base);
         T2* lp = lam + pad16(base);
         T2 p[16], l[16];
@@ -415,7 +457,7 @@ __device__ void pass_bwd(T2* psi, T2* lam, int s, unsigned m, const Team& tm, co
             }
             const int* zslot = info_zslot(M, par);
             const int* pslot = info_pslot(M, par);
-            const int xb = base | M.hi;   // the index bits outside the register bits
+            const int xb = (TILE ? tmap->x(base) : base) | M.hi;   // the index bits outside the register bits
             if (tm.tt >= 32) {
                 // Whole warps (W >= 9, so s >= 5: window bits 0..4 are the lane bits, the bits
                 // from 5 up to s - 1 and above the register bits are the same across the warp).
@@ -776,6 +818,233 @@ __device__ void measure(const TeamMem<T2>& M, const MeasDev* mt, int nmt, const 
 
 // One (cone, set) item: the whole window (half = 0), or the branch with the window's top
 // bit half - 1 (W = the window's width - 1). Ends with a team barrier.
+// ---- global tier: tile sweeps ----------------------------------------------------------------
+
+// The sweeps of one layer on a tiled state of W qubits (14 <= W <= 20), in forward order: the
+// low sweep takes the layer's rotations below the high groups (register groups at 0, 4 and 8,
+// as in the untiled forward), then each high sweep one group g..g+3, g = W - 4, W - 8 (at least
+// 8) while g > 12. Sweeps without rotations are dropped; the layer's diagonal goes into the last
+// forward sweep (an empty low sweep when there is none).
+struct LayerSweeps {
+    int n;
+    int g[3];           // 0 for the low sweep, else the high group's base bit (at least 8)
+    int ng[3];          // register groups of the sweep
+    int s[3][3];        // window base bit of each group
+    unsigned m[3][3];   // its rotation bits
+};
+
+__device__ __forceinline__ void layer_sweeps(unsigned todo, int W, bool diag, LayerSweeps& L) {
+    int gh[2], nh = 0;
+    for (int g = W - 4; nh < 2; g = g - 4 > kTileLowBits ? g - 4 : kTileLowBits) {
+        gh[nh++] = g;
+        if (g <= kTileBits) break;
+    }
+    const int lowtop = gh[nh - 1] < kTileBits ? gh[nh - 1] : kTileBits;
+    L.n = 0;
+    unsigned bits = todo & ((1u << lowtop) - 1u);
+    L.g[0] = 0;
+    L.ng[0] = 0;
+    while (bits && L.ng[0] < 3) {
+        const int bt = __ffs(bits) - 1;
+        const int sg = bt < 4 ? 0 : (bt < kTileBits - 4 ? bt : kTileBits - 4);
+        L.s[0][L.ng[0]] = sg;
+        L.m[0][L.ng[0]] = (bits >> sg) & 15u;
+        ++L.ng[0];
+        bits &= ~(15u << sg);
+    }
+    if (L.ng[0] > 0) L.n = 1;
+    for (int h = 0; h < nh; ++h) {
+        const unsigned m = (todo >> gh[h]) & 15u;
+        if (!m) continue;
+        L.g[L.n] = gh[h];
+        L.ng[L.n] = 1;
+        L.s[L.n][0] = gh[h];
+        L.m[L.n][0] = m;
+        ++L.n;
+    }
+    if (L.n == 0 && diag) {
+        L.g[0] = 0;
+        L.ng[0] = 0;
+        L.n = 1;
+    }
+}
+
+// Tile t of a sweep whose high group starts at g (g = 0: the low tile), for half `half`.
+__device__ __forceinline__ TileMap sweep_tile(int g, int t, int half) {
+    TileMap tp;
+    if (g == 0) {
+        tp.a = kTileBits;
+        tp.g = kTileBits;
+        tp.fix = t << kTileBits;
+    } else {   // tile index bits: window bits kTileLowBits..g-1, then g+4..
+        const int nlo = g - kTileLowBits;
+        tp.a = kTileLowBits;
+        tp.g = g;
+        tp.fix = ((t & ((1 << nlo) - 1)) << kTileLowBits) | ((t >> nlo) << (g + 4));
+    }
+    tp.s_loc = kTileLowBits;
+    tp.first = t < kTileTeams;
+    tp.nw = kGlobalCtaThreads / 32;
+    tp.warp0 = half * (kGlobalCtaThreads / kTileTeams / 32);
+    return tp;
+}
+
+// Global state (padded layout) -> shared tile (padded layout), 16-byte cp.async copies of
+// amplitude pairs (2k, 2k + 1), which are adjacent in both; then back with 16-byte stores.
+__device__ __forceinline__ void tile_fetch(float2* tile, const float2* g, const TileMap& tp, const Team& tm) {
+    for (int k = tm.tid; k < (1 << (kTileBits - 1)); k += tm.tt) {
+        const int i = 2 * k;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                         static_cast<unsigned>(__cvta_generic_to_shared(tile + pad16(i)))),
+                     "l"(g + pad16(tp.x(i)))
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void tile_fetch_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void tile_flush(const float2* tile, float2* g, const TileMap& tp, const Team& tm) {
+    for (int k = tm.tid; k < (1 << (kTileBits - 1)); k += tm.tt) {
+        const int i = 2 * k;
+        *reinterpret_cast<float4*>(g + pad16(tp.x(i))) = *reinterpret_cast<const float4*>(tile + pad16(i));
+    }
+}
+
+// The half of the CTA (256 threads, named barrier 1 or 2) that a thread works in during a sweep.
+__device__ __forceinline__ Team tile_half(const Team& tm) {
+    Team h;
+    const int per = kGlobalCtaThreads / kTileTeams;
+    h.id = tm.tid / per;
+    h.tid = tm.tid - h.id * per;
+    h.tt = per;
+    h.mask = 0xffffffffu;
+    return h;
+}
+
+// Forward layers 1.. of a tiled state (layer 0's product state is already in M.psi).
+template <typename real>
+__device__ void tiled_forward(const ConeArgs& A, const TeamMem<float2>& M, const Team& tm, const int32_t* body,
+                              const int32_t* lofs, int nl, const float2* GT) {
+    const int W = M.W;
+    const int ntiles = 1 << (W - kTileBits);
+    const Team ht = tile_half(tm);
+    float2* tile = M.tile + ht.id * padded_amps(kTileBits);
+    for (int li = 1; li < nl; ++li) {
+        const int32_t* lp = body + lofs[li];
+        const int ndiag = lp[0];
+        const int par = li & 1;
+        const unsigned todo = (unsigned)lp[1];
+        if (todo >> W) {   // a branch's top qubit has gates of layer 0 only
+            if (tm.tid == 0) atomicOr(A.err, 1);
+            return;
+        }
+        stage_layer<real, float2>(lp, GT, tm, M, par, false);
+        LayerSweeps LS;
+        layer_sweeps(todo, W, ndiag > 0, LS);
+        for (int k = 0; k < LS.n; ++k) {
+            const bool dg = ndiag > 0 && k == LS.n - 1;
+            const bool low = LS.g[k] == 0;
+            for (int t = ht.id; t < ntiles; t += kTileTeams) {
+                TileMap tp = sweep_tile(LS.g[k], t, ht.id);
+                tile_fetch(tile, M.psi, tp, ht);
+                tile_fetch_wait();
+                ht.sync();
+                if (LS.ng[k] == 0) {   // the diagonal alone
+                    pass_fwd<real, float2, true>(tile, kTileLowBits, 0u, true, ht, M, par, &tp);
+                    ht.sync();
+                }
+                for (int gi = 0; gi < LS.ng[k]; ++gi) {
+                    tp.s_loc = low ? LS.s[k][gi] : kTileLowBits;
+                    pass_fwd<real, float2, true>(tile, LS.s[k][gi], LS.m[k][gi], dg && gi == LS.ng[k] - 1, ht, M, par,
+                                                 &tp);
+                    ht.sync();
+                }
+                tile_flush(tile, M.psi, tp, ht);
+                ht.sync();
+            }
+            tm.sync();   // the next sweep reads tiles of both halves
+        }
+    }
+}
+
+// The adjoint of a tiled state, layers nl-1 .. 0: each layer's sweeps in reverse order, the
+// first of them un-applying the diagonal before its rotations. A sweep's partial sums
+// accumulate over each half's tiles (in tile order) in per-warp slots and are flushed once.
+// Layer 0 only takes gradients (its rotations are not un-applied): only its diagonal sweep
+// writes the tiles back, and the branch's top-qubit gradient follows the sweeps.
+template <typename real>
+__device__ void tiled_adjoint(const ConeArgs& A, const TeamMem<float2>& M, const Team& tm, const int32_t* body,
+                              const int32_t* lofs, int nl, const float2* GT, real* red, double* gdst) {
+    const int W = M.W;
+    const int ntiles = 1 << (W - kTileBits);
+    const int nw = nwarps_of(tm.tt);
+    const Team ht = tile_half(tm);
+    float2* tp_psi = M.tile + 2 * ht.id * padded_amps(kTileBits);
+    float2* tp_lam = tp_psi + padded_amps(kTileBits);
+    int rpar = 0;
+    for (int li = nl - 1; li >= 0; --li) {
+        const int32_t* lp = body + lofs[li];
+        const int ndiag = lp[0];
+        const int par = li & 1;
+        unsigned todo = (unsigned)lp[1];
+        const bool top = li == 0 && ((todo >> W) & 1u);   // a branch: layer 0's rotation on the top qubit
+        if (top) todo &= ~(1u << W);
+        if (todo >> W) {
+            if (tm.tid == 0) atomicOr(A.err, 1);
+            return;
+        }
+        stage_layer<real, float2>(lp, GT, tm, M, par, true);
+        LayerSweeps LS;
+        layer_sweeps(todo, W, ndiag > 0, LS);
+        for (int k = LS.n - 1; k >= 0; --k) {
+            const bool dg = ndiag > 0 && k == LS.n - 1;
+            const bool low = LS.g[k] == 0;
+            const bool store = li > 0 || dg;
+            real* rb = red + rpar * kMaxSweepSlots * nw;
+            for (int t = ht.id; t < ntiles; t += kTileTeams) {
+                TileMap tp = sweep_tile(LS.g[k], t, ht.id);
+                tile_fetch(tp_psi, M.psi, tp, ht);
+                tile_fetch(tp_lam, M.lam, tp, ht);
+                tile_fetch_wait();
+                ht.sync();
+                if (dg) {
+                    pass_bwd<real, float2, true, false, true>(tp_psi, tp_lam, low ? kTileLowBits : LS.g[k], 0u, ht, M,
+                                                              par, rb + 12 * nw, &tp);
+                    ht.sync();
+                }
+                for (int gi = 0; gi < LS.ng[k]; ++gi) {
+                    tp.s_loc = low ? LS.s[k][gi] : kTileLowBits;
+                    if (li == 0)
+                        pass_bwd<real, float2, false, true, true>(tp_psi, tp_lam, LS.s[k][gi], LS.m[k][gi], ht, M, par,
+                                                                  rb + 4 * gi * nw, &tp);
+                    else
+                        pass_bwd<real, float2, false, false, true>(tp_psi, tp_lam, LS.s[k][gi], LS.m[k][gi], ht, M,
+                                                                   par, rb + 4 * gi * nw, &tp);
+                    ht.sync();
+                }
+                if (store) {
+                    tile_flush(tp_psi, M.psi, tp, ht);
+                    tile_flush(tp_lam, M.lam, tp, ht);
+                    ht.sync();
+                }
+            }
+            tm.sync();   // both halves' tiles written back and partial sums complete
+            for (int gi = 0; gi < LS.ng[k]; ++gi)
+                flush_pass<real, float2>(rb + 4 * gi * nw, nw, LS.m[k][gi], LS.s[k][gi], M, par, false, gdst, tm);
+            if (dg) flush_pass<real, float2>(rb + 12 * nw, nw, 0u, 0, M, par, true, gdst, tm);
+            rpar ^= 1;
+        }
+        if (top) {
+            real* rb = red + rpar * kMaxSweepSlots * nw;
+            top_rotation_grad<real, float2>(M, (unsigned)lp[1], par, tm, rb);
+            tm.sync();
+            flush_pass<real, float2>(rb, nw, 1u, W, M, par, false, gdst, tm);
+            rpar ^= 1;
+        }
+    }
+}
+
 template <typename real, bool GRAD, bool GLOBAL>
 __device__ void run_cone(const ConeArgs& A, int cone_idx, int half, int b, const Team& tm, unsigned char* tb, int W,
                          int team_bytes) {
@@ -792,6 +1061,7 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int half, int b, const
         unsigned char* g = reinterpret_cast<unsigned char*>(A.gscratch) + (size_t)blockIdx.x * A.gscratch_slot;
         M.psi = reinterpret_cast<T2*>(g);
         M.lam = M.psi + padded_amps(W);
+        M.tile = reinterpret_cast<T2*>(tb + TL.tile);
     } else {
         M.psi = reinterpret_cast<T2*>(tb + TL.psi);
         M.lam = reinterpret_cast<T2*>(tb + TL.lam);
@@ -825,7 +1095,15 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int half, int b, const
         }
     }
     tm.sync();
-    for (int li = 1; li < nl; ++li) {
+    constexpr bool tiled = GLOBAL && sizeof(real) == 4;   // FP32 global-tier states are wider than a tile
+    if constexpr (tiled) {
+        if (W <= kTileBits) {
+            if (tm.tid == 0) atomicOr(A.err, 1);
+            return;
+        }
+        tiled_forward<real>(A, M, tm, body, lofs, nl, GT);
+    }
+    for (int li = 1; li < nl && !tiled; ++li) {
         const int32_t* lp = body + lofs[li];
         const int ndiag = lp[0];
         const int par = li & 1;
@@ -857,6 +1135,10 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int half, int b, const
                             A.e_part + (R ? (size_t)R->e_off : (size_t)b * A.n_terms), tm, red);
     if (!GRAD) return;
     double* gdst = A.g_part + (R ? (size_t)R->g_off : (size_t)b * A.n_slots) + cd.slot_off;
+    if constexpr (tiled) {
+        tiled_adjoint<real>(A, M, tm, body, lofs, nl, GT, red, gdst);
+        return;
+    }
     int rpar = 0;
     for (int li = nl - 1; li >= 0; --li) {
         const int32_t* lp = body + lofs[li];

@@ -241,3 +241,26 @@ def test_widest_cones_L9(tlq):
     Er, gr = _oracle(prob, prob.theta)
     check_energy(E, Er)
     check_grad(g, gr)
+
+
+@pytest.mark.parametrize("n,L,width", [(15, 8, 15), (17, 8, 17), (19, 9, 19), (20, 10, 20)])
+def test_tiled_global_tier_every_width(tlq, n, L, width):
+    # Whole-chain windows give global-tier states of 15, 17, 19 and 20 qubits; with the 14-, 16-
+    # and 18-qubit states of the tests above, every sweep plan of the tiled global tier (one or
+    # two high register groups, a low sweep with a lone bit 12) runs. Energy only and energy +
+    # gradient against the oracle, two parameter sets.
+    from paper_2112_10239_gb300 import binding as B
+    prob = W.tfim_problem(n, L, 2, seed=30 + n, h_range=(0.5, 1.5))
+    c, h = tlq.problem(prob)
+    try:
+        _, _, _, weff, _, _, split = B.tlq_plan_cone_stats(tlq.h, c.h, h.h, len(prob.terms))
+    finally:
+        c.close()
+        h.close()
+    assert width in set((weff - split).tolist())
+    Er, gr = _oracle(prob, prob.theta)
+    E0, _ = _run(tlq, prob, grad=False)
+    check_energy(E0, Er)
+    E, g = _run(tlq, prob)
+    check_energy(E, Er)
+    check_grad(g, gr)
