@@ -27,6 +27,7 @@
 #include <cstdio>
 
 #include "gates.cuh"
+#include "tc.cuh"
 
 namespace tlq {
 
@@ -889,26 +890,61 @@ __device__ __forceinline__ TileMap sweep_tile(int g, int t, int half) {
     return tp;
 }
 
-// Global state (padded layout) -> shared tile (padded layout), 16-byte cp.async copies of
-// amplitude pairs (2k, 2k + 1), which are adjacent in both; then back with 16-byte stores.
-__device__ __forceinline__ void tile_fetch(float2* tile, const float2* g, const TileMap& tp, const Team& tm) {
-    for (int k = tm.tid; k < (1 << (kTileBits - 1)); k += tm.tt) {
-        const int i = 2 * k;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                         static_cast<unsigned>(__cvta_generic_to_shared(tile + pad16(i)))),
-                     "l"(g + pad16(tp.x(i)))
-                     : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+// Tile transfers on the bulk-copy engine (cp.async.bulk). In the padded layout a low tile is
+// one contiguous block of the global state (2^12 amplitudes and their padding, 36,864 bytes)
+// and a high tile is 16 blocks, one per value of its register group (256 amplitudes and their
+// padding, 2,304 bytes each); in shared memory the blocks follow one another. One thread of a
+// half issues the copies: loads complete on the half's mbarrier (one phase per tile), stores go
+// into bulk groups that the same thread retires before its buffers are loaded again.
+struct TileSync {
+    uint64_t* bar;     // one mbarrier per half (shared memory)
+    uint32_t phase;    // this thread's half: parity of its next load
+};
+
+__device__ __forceinline__ int tile_blocks(const TileMap& tp) { return tp.a == kTileBits ? 1 : 1 << (kTileBits - kTileLowBits); }
+__device__ __forceinline__ uint32_t tile_block_bytes(const TileMap& tp) {
+    return (uint32_t)padded_amps(tp.a) * (uint32_t)sizeof(float2);
 }
 
-__device__ __forceinline__ void tile_fetch_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Issued by one thread of the half: load the tile of nst states (gs[k] -> tiles[k]).
+__device__ __forceinline__ void tile_fetch(float2* const (&tiles)[2], float2* const (&gs)[2], int nst,
+                                           const TileMap& tp, uint64_t* bar) {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // earlier stores have read the buffers
+    const int nb = tile_blocks(tp);
+    const uint32_t bytes = tile_block_bytes(tp);
+    const uint32_t b = tc::su32(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes * nb * nst) : "memory");
+    for (int k = 0; k < nst; ++k)
+        for (int r = 0; r < nb; ++r)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             tc::su32(tiles[k] + pad16(r << tp.a))),
+                         "l"(gs[k] + pad16(tp.x(r << tp.a))), "r"(bytes), "r"(b)
+                         : "memory");
+}
 
-__device__ __forceinline__ void tile_flush(const float2* tile, float2* g, const TileMap& tp, const Team& tm) {
-    for (int k = tm.tid; k < (1 << (kTileBits - 1)); k += tm.tt) {
-        const int i = 2 * k;
-        *reinterpret_cast<float4*>(g + pad16(tp.x(i))) = *reinterpret_cast<const float4*>(tile + pad16(i));
-    }
+// Issued by one thread of the half after a barrier that follows every thread's proxy fence.
+__device__ __forceinline__ void tile_store(float2* const (&tiles)[2], float2* const (&gs)[2], int nst, const TileMap& tp) {
+    const int nb = tile_blocks(tp);
+    const uint32_t bytes = tile_block_bytes(tp);
+    for (int k = 0; k < nst; ++k)
+        for (int r = 0; r < nb; ++r)
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gs[k] + pad16(tp.x(r << tp.a))),
+                         "r"(tc::su32(tiles[k] + pad16(r << tp.a))), "r"(bytes)
+                         : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Every thread of the half: wait (bounded) for the load of the half's current tile.
+__device__ __forceinline__ void tile_wait(TileSync& ts, int half, const ConeArgs& A) {
+    if (!tc::mbar_wait(ts.bar + half, ts.phase)) atomicOr(A.err, 1);
+    ts.phase ^= 1u;
+}
+
+// End of a sweep, before the CTA barrier: the half's stores are complete and visible to the
+// loads and plain reads that follow.
+__device__ __forceinline__ void tile_sweep_done(const Team& ht) {
+    if (ht.tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async;" ::: "memory");
 }
 
 // The half of the CTA (256 threads, named barrier 1 or 2) that a thread works in during a sweep.
@@ -925,11 +961,13 @@ __device__ __forceinline__ Team tile_half(const Team& tm) {
 // Forward layers 1.. of a tiled state (layer 0's product state is already in M.psi).
 template <typename real>
 __device__ void tiled_forward(const ConeArgs& A, const TeamMem<float2>& M, const Team& tm, const int32_t* body,
-                              const int32_t* lofs, int nl, const float2* GT) {
+                              const int32_t* lofs, int nl, const float2* GT, TileSync& ts) {
     const int W = M.W;
     const int ntiles = 1 << (W - kTileBits);
     const Team ht = tile_half(tm);
     float2* tile = M.tile + ht.id * padded_amps(kTileBits);
+    float2* const tiles[2] = {tile, tile};
+    float2* const gs[2] = {M.psi, M.psi};
     for (int li = 1; li < nl; ++li) {
         const int32_t* lp = body + lofs[li];
         const int ndiag = lp[0];
@@ -939,6 +977,7 @@ __device__ void tiled_forward(const ConeArgs& A, const TeamMem<float2>& M, const
             if (tm.tid == 0) atomicOr(A.err, 1);
             return;
         }
+        asm volatile("fence.proxy.async;" ::: "memory");   // plain writes of the state before the loads
         stage_layer<real, float2>(lp, GT, tm, M, par, false);
         LayerSweeps LS;
         layer_sweeps(todo, W, ndiag > 0, LS);
@@ -947,22 +986,21 @@ __device__ void tiled_forward(const ConeArgs& A, const TeamMem<float2>& M, const
             const bool low = LS.g[k] == 0;
             for (int t = ht.id; t < ntiles; t += kTileTeams) {
                 TileMap tp = sweep_tile(LS.g[k], t, ht.id);
-                tile_fetch(tile, M.psi, tp, ht);
-                tile_fetch_wait();
-                ht.sync();
-                if (LS.ng[k] == 0) {   // the diagonal alone
+                if (ht.tid == 0) tile_fetch(tiles, gs, 1, tp, ts.bar + ht.id);
+                tile_wait(ts, ht.id, A);
+                if (LS.ng[k] == 0)   // the diagonal alone
                     pass_fwd<real, float2, true>(tile, kTileLowBits, 0u, true, ht, M, par, &tp);
-                    ht.sync();
-                }
                 for (int gi = 0; gi < LS.ng[k]; ++gi) {
                     tp.s_loc = low ? LS.s[k][gi] : kTileLowBits;
                     pass_fwd<real, float2, true>(tile, LS.s[k][gi], LS.m[k][gi], dg && gi == LS.ng[k] - 1, ht, M, par,
                                                  &tp);
-                    ht.sync();
+                    if (gi < LS.ng[k] - 1) ht.sync();
                 }
-                tile_flush(tile, M.psi, tp, ht);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 ht.sync();
+                if (ht.tid == 0) tile_store(tiles, gs, 1, tp);
             }
+            tile_sweep_done(ht);
             tm.sync();   // the next sweep reads tiles of both halves
         }
     }
@@ -975,13 +1013,15 @@ __device__ void tiled_forward(const ConeArgs& A, const TeamMem<float2>& M, const
 // writes the tiles back, and the branch's top-qubit gradient follows the sweeps.
 template <typename real>
 __device__ void tiled_adjoint(const ConeArgs& A, const TeamMem<float2>& M, const Team& tm, const int32_t* body,
-                              const int32_t* lofs, int nl, const float2* GT, real* red, double* gdst) {
+                              const int32_t* lofs, int nl, const float2* GT, real* red, double* gdst, TileSync& ts) {
     const int W = M.W;
     const int ntiles = 1 << (W - kTileBits);
     const int nw = nwarps_of(tm.tt);
     const Team ht = tile_half(tm);
     float2* tp_psi = M.tile + 2 * ht.id * padded_amps(kTileBits);
     float2* tp_lam = tp_psi + padded_amps(kTileBits);
+    float2* const tiles[2] = {tp_psi, tp_lam};
+    float2* const gs[2] = {M.psi, M.lam};
     int rpar = 0;
     for (int li = nl - 1; li >= 0; --li) {
         const int32_t* lp = body + lofs[li];
@@ -994,6 +1034,7 @@ __device__ void tiled_adjoint(const ConeArgs& A, const TeamMem<float2>& M, const
             if (tm.tid == 0) atomicOr(A.err, 1);
             return;
         }
+        asm volatile("fence.proxy.async;" ::: "memory");   // plain writes of the states before the loads
         stage_layer<real, float2>(lp, GT, tm, M, par, true);
         LayerSweeps LS;
         layer_sweeps(todo, W, ndiag > 0, LS);
@@ -1004,14 +1045,12 @@ __device__ void tiled_adjoint(const ConeArgs& A, const TeamMem<float2>& M, const
             real* rb = red + rpar * kMaxSweepSlots * nw;
             for (int t = ht.id; t < ntiles; t += kTileTeams) {
                 TileMap tp = sweep_tile(LS.g[k], t, ht.id);
-                tile_fetch(tp_psi, M.psi, tp, ht);
-                tile_fetch(tp_lam, M.lam, tp, ht);
-                tile_fetch_wait();
-                ht.sync();
+                if (ht.tid == 0) tile_fetch(tiles, gs, 2, tp, ts.bar + ht.id);
+                tile_wait(ts, ht.id, A);
                 if (dg) {
                     pass_bwd<real, float2, true, false, true>(tp_psi, tp_lam, low ? kTileLowBits : LS.g[k], 0u, ht, M,
                                                               par, rb + 12 * nw, &tp);
-                    ht.sync();
+                    if (LS.ng[k] > 0 || !store) ht.sync();
                 }
                 for (int gi = 0; gi < LS.ng[k]; ++gi) {
                     tp.s_loc = low ? LS.s[k][gi] : kTileLowBits;
@@ -1021,14 +1060,15 @@ __device__ void tiled_adjoint(const ConeArgs& A, const TeamMem<float2>& M, const
                     else
                         pass_bwd<real, float2, false, false, true>(tp_psi, tp_lam, LS.s[k][gi], LS.m[k][gi], ht, M,
                                                                    par, rb + 4 * gi * nw, &tp);
-                    ht.sync();
+                    if (gi < LS.ng[k] - 1 || !store) ht.sync();
                 }
                 if (store) {
-                    tile_flush(tp_psi, M.psi, tp, ht);
-                    tile_flush(tp_lam, M.lam, tp, ht);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     ht.sync();
+                    if (ht.tid == 0) tile_store(tiles, gs, 2, tp);
                 }
             }
+            tile_sweep_done(ht);
             tm.sync();   // both halves' tiles written back and partial sums complete
             for (int gi = 0; gi < LS.ng[k]; ++gi)
                 flush_pass<real, float2>(rb + 4 * gi * nw, nw, LS.m[k][gi], LS.s[k][gi], M, par, false, gdst, tm);
@@ -1047,7 +1087,7 @@ __device__ void tiled_adjoint(const ConeArgs& A, const TeamMem<float2>& M, const
 
 template <typename real, bool GRAD, bool GLOBAL>
 __device__ void run_cone(const ConeArgs& A, int cone_idx, int half, int b, const Team& tm, unsigned char* tb, int W,
-                         int team_bytes) {
+                         int team_bytes, TileSync& ts) {
     using T2 = typename R2<real>::T;
     const SetRec* R = A.sets ? A.sets + b : nullptr;
     const ConeDev cd = R ? R->cones[cone_idx] : A.cones[cone_idx];
@@ -1101,7 +1141,7 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int half, int b, const
             if (tm.tid == 0) atomicOr(A.err, 1);
             return;
         }
-        tiled_forward<real>(A, M, tm, body, lofs, nl, GT);
+        tiled_forward<real>(A, M, tm, body, lofs, nl, GT, ts);
     }
     for (int li = 1; li < nl && !tiled; ++li) {
         const int32_t* lp = body + lofs[li];
@@ -1136,7 +1176,7 @@ __device__ void run_cone(const ConeArgs& A, int cone_idx, int half, int b, const
     if (!GRAD) return;
     double* gdst = A.g_part + (R ? (size_t)R->g_off : (size_t)b * A.n_slots) + cd.slot_off;
     if constexpr (tiled) {
-        tiled_adjoint<real>(A, M, tm, body, lofs, nl, GT, red, gdst);
+        tiled_adjoint<real>(A, M, tm, body, lofs, nl, GT, red, gdst, ts);
         return;
     }
     int rpar = 0;
@@ -1187,6 +1227,15 @@ __global__ void __launch_bounds__(GLOBAL ? kGlobalCtaThreads : kCtaThreads, GLOB
 cone_kernel(ConeArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_chunk;
+    __shared__ __align__(8) uint64_t s_tile_bar[kTileTeams];   // tiled global tier: one per half
+    TileSync ts{s_tile_bar, 0u};
+    if constexpr (GLOBAL && sizeof(real) == 4) {
+        if (threadIdx.x == 0) {
+            for (int h = 0; h < kTileTeams; ++h) tc::mbar_init(s_tile_bar + h, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
     for (;;) {
         if (threadIdx.x == 0) s_chunk = A.chunk_begin + atomicAdd(A.counter, 1);
         __syncthreads();
@@ -1211,7 +1260,7 @@ cone_kernel(ConeArgs A) {
             const int item = ch.first + team;
             const int cw = A.items[2 * item], b = A.items[2 * item + 1];
             run_cone<real, GRAD, GLOBAL>(A, cw & kItemConeMask, (cw >> kItemHalfShift) & 3, b, tm,
-                                         smem + (size_t)team * ch.team_bytes, ch.W, ch.team_bytes);
+                                         smem + (size_t)team * ch.team_bytes, ch.W, ch.team_bytes, ts);
         }
         __syncthreads();
     }
