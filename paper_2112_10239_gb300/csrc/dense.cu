@@ -174,6 +174,13 @@ __device__ __forceinline__ uint32_t tile_x(const DensePassDev& p, uint32_t tile,
     return (t & 15u) | (lo << 4) | ((t >> 4) << p.a) | (hi << (p.a + kDenseStridedBits));
 }
 
+// The global index of amplitude j of a register group at bit s is tile_x(base) + j * step:
+// register bits map to consecutive global bits (s = 0: the tile's low 4 bits; s >= 4: in a
+// strided tile, bits a + s - 4 ..).
+__device__ __forceinline__ uint32_t tile_step(const DensePassDev& p, int s) {
+    return (!p.strided || s == 0) ? (1u << s) : (1u << (s - 4 + p.a));
+}
+
 __device__ __forceinline__ int class_count(const DenseClassDev& c, const int32_t* dist, uint32_t x) {
     int cnt;
     if (c.kind == 1) {
@@ -195,14 +202,20 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 // Each thread copies its 8 x 16 bytes (2 amplitudes each) of tile `t` into the padded
 // shared buffer with cp.async (global -> shared without a register round trip), then
 // commits them as one group.
+// Copy k of a thread covers tile index i = 2 (tid + kThreads k): both its global index (the
+// row bits t >> 4 advance by 2 kThreads / 16 per k) and its padded shared slot advance by a
+// fixed step per k.
 __device__ __forceinline__ void issue_tile(const DensePassDev& P, uint32_t t, const float2* state, float2* buf,
                                            int tid) {
+    const uint32_t i0 = 2u * (uint32_t)tid;
+    const float2* src = state + tile_x(P, t, i0);
+    const uint32_t gstep = P.strided ? ((2u * kThreads / 16u) << P.a) : 2u * kThreads;
+    uint32_t dst = smem_u32(buf + pad16((int)i0));
 #pragma unroll
     for (int k = 0; k < kTile / 2 / kThreads; ++k) {
-        const uint32_t i = 2u * (uint32_t)(tid + kThreads * k);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(buf + pad16((int)i))),
-                     "l"(state + tile_x(P, t, i))
-                     : "memory");
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+        src += gstep;
+        dst += (uint32_t)(pad16(2 * kThreads) * sizeof(float2));
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -311,12 +324,13 @@ __device__ __forceinline__ void group_epilogue(const PassArgs& A, const DensePas
                 else ez[j] += (float)C.coeff * (float)(C.nterms - 2 * cnt);
             }
         }
+        const uint32_t xstep = tile_step(P, s);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             if (any_phase) v[j] = cmul(v[j], ph[j]);
             if (any_energy) {
                 if (A.n_zterms > 0) {
-                    const uint32_t x = tile_x(P, t_id, (uint32_t)(base | (j << s)));
+                    const uint32_t x = xb + j * xstep;
                     for (int k = 0; k < A.n_zterms; ++k) {
                         const DenseZTermDev Z = A.zterms[k];
                         ez[j] += (__popc(x & Z.mask) & 1) ? -(float)Z.coeff : (float)Z.coeff;
@@ -326,7 +340,7 @@ __device__ __forceinline__ void group_epilogue(const PassArgs& A, const DensePas
                 eacc += pj * ez[j];
                 if (NORM) nacc += pj;
                 if (A.lam)
-                    A.lam[tile_x(P, t_id, (uint32_t)(base | (j << s)))] = make_float2(ez[j] * v[j].x, ez[j] * v[j].y);
+                    A.lam[xb + j * xstep] = make_float2(ez[j] * v[j].x, ez[j] * v[j].y);
             }
         }
     }
@@ -400,20 +414,35 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_co
             const int stride = pass_stride(s);
             const int base = (tid & lowmask) | ((tid >> s) << (s + 4));
             float2* p = tile + pad16(base);
-            float2 v[16];
-            if (GEN && g == 0) gen16(*S, A.n_eff, A.ptab, tile_x(P, t_id, (uint32_t)base), v);   // s == 0
-            else load16(v, p, stride);
-            if (kd[0] >= 0) apply_rot<0>(v, kd[0], c[0], sn[0]);
-            if (kd[1] >= 0) apply_rot<1>(v, kd[1], c[1], sn[1]);
-            if (kd[2] >= 0) apply_rot<2>(v, kd[2], c[2], sn[2]);
-            if (kd[3] >= 0) apply_rot<3>(v, kd[3], c[3], sn[3]);
-            group_epilogue(A, P, g, t_id, base, s, v, eacc, eacc, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab);
+            pk64 u[16];   // the 16 amplitudes as packed (re, im) registers
+            if (GEN && g == 0) {   // s == 0
+                float2 v[16];
+                gen16(*S, A.n_eff, A.ptab, tile_x(P, t_id, (uint32_t)base), v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) u[j] = pk2(v[j].x, v[j].y);
+            } else {
+                load16p(u, p, stride);
+            }
+            if (kd[0] >= 0) apply_rot_p<0>(u, kd[0], c[0], sn[0]);
+            if (kd[1] >= 0) apply_rot_p<1>(u, kd[1], c[1], sn[1]);
+            if (kd[2] >= 0) apply_rot_p<2>(u, kd[2], c[2], sn[2]);
+            if (kd[3] >= 0) apply_rot_p<3>(u, kd[3], c[3], sn[3]);
+            if (P.group_ncls[g] > 0 || g == P.measure_group) {
+                float2 v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = upk2(u[j]);
+                group_epilogue(A, P, g, t_id, base, s, v, eacc, eacc, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) u[j] = pk2(v[j].x, v[j].y);
+            }
             if (g < P.ngroups - 1) {
-                store16(v, p, stride);
+                store16p(u, p, stride);
                 __syncthreads();
             } else if (P.store) {
+                pk64* dst = reinterpret_cast<pk64*>(A.state) + tile_x(P, t_id, (uint32_t)base);
+                const uint32_t step = tile_step(P, s);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) A.state[tile_x(P, t_id, (uint32_t)(base | (j << s)))] = v[j];
+                for (int j = 0; j < 16; ++j) dst[j * step] = u[j];
             }
         }
         __syncthreads();   // the buffer is free for the copy issued in the next iteration
@@ -863,11 +892,11 @@ __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid
                 store16(u, blam + pad16(base), stride);
                 __syncthreads();
             } else if (P.store) {
+                const uint32_t x0 = tile_x(P, t_id, (uint32_t)base), step = tile_step(P, s);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const uint32_t x = tile_x(P, t_id, (uint32_t)(base | (j << s)));
-                    A.psi[x] = v[j];
-                    A.lam[x] = u[j];
+                    A.psi[x0 + j * step] = v[j];
+                    A.lam[x0 + j * step] = u[j];
                 }
             }
         }

@@ -100,6 +100,113 @@ __device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigne
     return d;
 }
 
+// ---- packed register state: each amplitude lives in one 64-bit register pair (re, im) from
+// its load to its store, so the packed updates need no conversions between them.
+using pk64 = unsigned long long;
+
+__device__ __forceinline__ void load16p(pk64 (&v)[16], const float2* p, int stride) {
+    if (stride == 1) {
+        const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const ulonglong2 t = q[i];
+            v[2 * i] = t.x;
+            v[2 * i + 1] = t.y;
+        }
+    } else {
+        const pk64* q = reinterpret_cast<const pk64*>(p);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = q[j * stride];
+    }
+}
+
+__device__ __forceinline__ void store16p(const pk64 (&v)[16], float2* p, int stride) {
+    if (stride == 1) {
+        ulonglong2* q = reinterpret_cast<ulonglong2*>(p);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) q[i] = make_ulonglong2(v[2 * i], v[2 * i + 1]);
+    } else {
+        pk64* q = reinterpret_cast<pk64*>(p);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) q[j * stride] = v[j];
+    }
+}
+
+// RY(a) on register bit K of a packed state; C = (c, c), S = (s, s), NS = (-s, -s).
+template <int K>
+__device__ __forceinline__ void apply_ry_p(pk64 (&v)[16], pk64 C, pk64 S, pk64 NS) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (j & (1 << K)) continue;
+        const pk64 a0 = v[j], a1 = v[j | (1 << K)];
+        v[j] = fma2(C, a0, mul2(NS, a1));           // c a0 - s a1
+        v[j | (1 << K)] = fma2(C, a1, mul2(S, a0));  // s a0 + c a1
+    }
+}
+
+// RX(a) on register bit K of a packed state (scalar arithmetic on the unpacked pairs).
+template <int K>
+__device__ __forceinline__ void apply_rx_p(pk64 (&v)[16], float c, float s) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (j & (1 << K)) continue;
+        const float2 a0 = upk2(v[j]), a1 = upk2(v[j | (1 << K)]);
+        v[j] = pk2(c * a0.x + s * a1.y, c * a0.y - s * a1.x);
+        v[j | (1 << K)] = pk2(c * a1.x + s * a0.y, c * a1.y - s * a0.x);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void apply_rot_p(pk64 (&v)[16], int kind, float c, float s) {
+    if (kind == TLQ_RY) apply_ry_p<K>(v, pk2(c, c), pk2(s, s), pk2(-s, -s));
+    else apply_rx_p<K>(v, c, s);
+}
+
+// Im <lam| Y |psi> over the pairs of register bit K on packed states (see grad_y).
+template <int K>
+__device__ __forceinline__ float grad_y_p(const pk64 (&p)[16], const pk64 (&l)[16]) {
+    pk64 sa = pk2(0.f, 0.f), sb = pk2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (j & (1 << K)) continue;
+        sa = fma2(l[j | (1 << K)], p[j], sa);
+        sb = fma2(l[j], p[j | (1 << K)], sb);
+    }
+    const float2 a = upk2(sa), b = upk2(sb);
+    return (a.x + a.y) - (b.x + b.y);
+}
+
+// Im <lam| X |psi> over the pairs of register bit K on packed states (see grad_x).
+template <int K>
+__device__ __forceinline__ float grad_x_p(const pk64 (&p)[16], const pk64 (&l)[16]) {
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (j & (1 << K)) continue;
+        const float2 p0 = upk2(p[j]), p1 = upk2(p[j | (1 << K)]), l0 = upk2(l[j]), l1 = upk2(l[j | (1 << K)]);
+        acc += (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
+    }
+    return acc;
+}
+
+// Adjoint step of one rotation on register bit K of packed states: gradient, then un-apply
+// (angle -> -angle: s_neg = -sin(a/2)) on psi and lam.
+template <int K>
+__device__ __forceinline__ float adjoint_rot_p(pk64 (&p)[16], pk64 (&l)[16], int kind, float c, float s_neg) {
+    float g;
+    if (kind == TLQ_RY) {
+        g = grad_y_p<K>(p, l);
+        const pk64 C = pk2(c, c), S = pk2(s_neg, s_neg), NS = pk2(-s_neg, -s_neg);
+        apply_ry_p<K>(p, C, S, NS);
+        apply_ry_p<K>(l, C, S, NS);
+    } else {
+        g = grad_x_p<K>(p, l);
+        apply_rx_p<K>(p, c, s_neg);
+        apply_rx_p<K>(l, c, s_neg);
+    }
+    return g;
+}
+
 // RY(a) on register bit K: [[c,-s],[s,c]] on (amp with bit 0, amp with bit 1). PACK selects
 // the packed form for FP32 (callers whose register budget is tight keep the scalar form).
 template <int K, typename T2, typename real, bool PACK = true>
