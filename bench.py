@@ -40,8 +40,9 @@ L2_FLUSH_BYTES = 256 << 20
 # taken from one ncu capture of that kernel on that workload (summaries in profiles/). Workloads
 # without an entry report null; an entry is removed when its kernel changes after the capture.
 NCU_TRAFFIC = {
-    ("tfim_n20_L6_B64", "cone_kernel"): 849664.0 + 0.0,
-    ("tfim_n500_L4_B256", "cone_kernel"): 10268928.0 + 752384.0,
+    ("tfim_n20_L6_B64", "cone_kernel"): 856576.0 + 0.0,
+    ("tfim_n500_L4_B256", "cone_kernel"): 10280192.0 + 915968.0,
+    ("tfim_n400_L8_B1", "cone_kernel"): 12255010000.0 + 14676718000.0,
     ("partial_trace_n20_m13", "herk_ws_kernel"): 8826624.0 + 475120128.0,
 }
 
