@@ -773,24 +773,20 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
+// The thread's share of Im<lam|G|psi> for the rotation on register bit K, which is then
+// un-applied from psi and lam.
 template <int K>
-__device__ __forceinline__ void adjoint_bit(const AdjArgs& A, int g, float2 (&v)[16], float2 (&u)[16], double* acc,
-                                            int lane) {
+__device__ __forceinline__ float adjoint_bit(const AdjArgs& A, int g, float2 (&v)[16], float2 (&u)[16]) {
     const int gate = A.pass.gate[g][K];
     const float2 cs = A.GT[gate];
-    float gk = adjoint_rot<K, float2, float>(v, u, A.gates[gate].kind, cs.x, -cs.y);
-    gk = warp_sum(gk);
-    if (lane == 0) acc[4 * g + K] += (double)gk;
+    return adjoint_rot<K, float2, float>(v, u, A.gates[gate].kind, cs.x, -cs.y);
 }
 
 // Layer-0 rotation on register bit K: gradient only (see DensePassDev::group_rot0).
 template <int K>
-__device__ __forceinline__ void gradient_bit(const AdjArgs& A, int g, const float2 (&v)[16], const float2 (&u)[16],
-                                             double* acc, int lane) {
+__device__ __forceinline__ float gradient_bit(const AdjArgs& A, int g, const float2 (&v)[16], const float2 (&u)[16]) {
     const int gate = A.pass.gate[g][K];
-    float gk = A.gates[gate].kind == TLQ_RY ? grad_y<K, float2, float>(v, u) : grad_x<K, float2, float>(v, u);
-    gk = warp_sum(gk);
-    if (lane == 0) acc[4 * g + K] += (double)gk;
+    return A.gates[gate].kind == TLQ_RY ? grad_y<K, float2, float>(v, u) : grad_x<K, float2, float>(v, u);
 }
 
 __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid_constant__ AdjArgs A) {
@@ -815,7 +811,7 @@ __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid
     }
     for (int k = tid; k < (kThreads / 32) * kDenseAdjSlots; k += kThreads) s_gacc[k] = 0.0;
     stage_classes(P, A.classes, A.pcd, A.stage, A.dists, A.ptab, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab, tid);
-    double* acc = s_gacc + warp * kDenseAdjSlots;   // written by lane 0 of this warp only
+    double* acc = s_gacc + warp * kDenseAdjSlots;   // written by one lane of this warp per slot
 
     for (uint32_t t_id = blockIdx.x; t_id < ntiles; t_id += gridDim.x) {
         wait_tiles();
@@ -876,16 +872,22 @@ __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid
             // the group's rotations: gradient, then the inverse rotation on both states; layer 0's
             // rotations commute and nothing after them needs the state, so they only give gradients
             const unsigned m = P.group_mask[g];
+            float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
             if ((P.group_rot0 >> g) & 1u) {
-                if (m & 1u) gradient_bit<0>(A, g, v, u, acc, lane);
-                if (m & 2u) gradient_bit<1>(A, g, v, u, acc, lane);
-                if (m & 4u) gradient_bit<2>(A, g, v, u, acc, lane);
-                if (m & 8u) gradient_bit<3>(A, g, v, u, acc, lane);
+                if (m & 1u) g0 = gradient_bit<0>(A, g, v, u);
+                if (m & 2u) g1 = gradient_bit<1>(A, g, v, u);
+                if (m & 4u) g2 = gradient_bit<2>(A, g, v, u);
+                if (m & 8u) g3 = gradient_bit<3>(A, g, v, u);
             } else {
-                if (m & 1u) adjoint_bit<0>(A, g, v, u, acc, lane);
-                if (m & 2u) adjoint_bit<1>(A, g, v, u, acc, lane);
-                if (m & 4u) adjoint_bit<2>(A, g, v, u, acc, lane);
-                if (m & 8u) adjoint_bit<3>(A, g, v, u, acc, lane);
+                if (m & 1u) g0 = adjoint_bit<0>(A, g, v, u);
+                if (m & 2u) g1 = adjoint_bit<1>(A, g, v, u);
+                if (m & 4u) g2 = adjoint_bit<2>(A, g, v, u);
+                if (m & 8u) g3 = adjoint_bit<3>(A, g, v, u);
+            }
+            {   // the group's four warp sums in one transposing reduction: lane 8 k holds bit k's
+                const float gk = warp_sum4(g0, g1, g2, g3, lane);
+                const int k = lane >> 3;
+                if ((lane & 7) == 0 && ((m >> k) & 1u)) acc[4 * g + k] += (double)gk;
             }
             if (g > 0) {
                 store16(v, bpsi + pad16(base), stride);
