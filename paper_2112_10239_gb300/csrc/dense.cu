@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_co
 #pragma unroll
                 for (int j = 0; j < 16; ++j) u[j] = pk2(v[j].x, v[j].y);
             } else {
-                load16p(u, p, stride);
+                load16ps(u, p, s);
             }
             if (kd[0] >= 0) apply_rot_p<0>(u, kd[0], c[0], sn[0]);
             if (kd[1] >= 0) apply_rot_p<1>(u, kd[1], c[1], sn[1]);
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_co
                 for (int j = 0; j < 16; ++j) u[j] = pk2(v[j].x, v[j].y);
             }
             if (g < P.ngroups - 1) {
-                store16p(u, p, stride);
+                store16ps(u, p, s);
                 __syncthreads();
             } else if (P.store) {
                 pk64* dst = reinterpret_cast<pk64*>(A.state) + tile_x(P, t_id, (uint32_t)base);
@@ -821,8 +821,8 @@ __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid
             const int stride = pass_stride(s);
             const int base = (tid & ((1 << s) - 1)) | ((tid >> s) << (s + 4));
             float2 v[16], u[16];
-            load16(v, bpsi + pad16(base), stride);
-            load16(u, blam + pad16(base), stride);
+            load16s(v, bpsi + pad16(base), s);
+            load16s(u, blam + pad16(base), s);
             if (g == 0) {
                 __syncthreads();   // every thread holds its amplitudes: both buffers are free
                 const uint32_t next = t_id + gridDim.x;
@@ -890,8 +890,8 @@ __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid
                 if ((lane & 7) == 0 && ((m >> k) & 1u)) acc[4 * g + k] += (double)gk;
             }
             if (g > 0) {
-                store16(v, bpsi + pad16(base), stride);
-                store16(u, blam + pad16(base), stride);
+                store16s(v, bpsi + pad16(base), s);
+                store16s(u, blam + pad16(base), s);
                 __syncthreads();
             } else if (P.store) {
                 const uint32_t x0 = tile_x(P, t_id, (uint32_t)base), step = tile_step(P, s);

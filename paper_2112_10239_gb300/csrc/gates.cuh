@@ -74,6 +74,35 @@ __device__ __forceinline__ void store16(const T2 (&v)[16], T2* p, int stride) {
     }
 }
 
+// The same loads and stores with the register bits' position s dispatched to a compile-time
+// stride (s = 0 or 4..8, the positions a 2^12-amplitude tile has), so the 16 addresses are
+// immediate offsets from one register; other s take the runtime form.
+__host__ __device__ constexpr int stride_of(int s) { return s == 0 ? 1 : (1 << s) + (1 << (s - 3)); }
+
+// Calls f(stride) with a literal stride for s = 0, 4..8 (each case inlines its own copy).
+template <typename F>
+__device__ __forceinline__ void with_stride(int s, F f) {
+    switch (s) {
+        case 0: f(stride_of(0)); break;
+        case 4: f(stride_of(4)); break;
+        case 5: f(stride_of(5)); break;
+        case 6: f(stride_of(6)); break;
+        case 7: f(stride_of(7)); break;
+        case 8: f(stride_of(8)); break;
+        default: f(stride_of(s)); break;
+    }
+}
+
+template <typename T2>
+__device__ __forceinline__ void load16s(T2 (&v)[16], const T2* p, int s) {
+    with_stride(s, [&](int st) { load16(v, p, st); });
+}
+
+template <typename T2>
+__device__ __forceinline__ void store16s(const T2 (&v)[16], T2* p, int s) {
+    with_stride(s, [&](int st) { store16(v, p, st); });
+}
+
 // Warp sums of four values at once (a transposing reduction: 6 shuffles instead of 4 x 5).
 // Lane l receives the sum over the warp of value (l >> 3) & 3.
 template <typename real>
@@ -148,6 +177,14 @@ __device__ __forceinline__ void store16p(const pk64 (&v)[16], float2* p, int str
 #pragma unroll
         for (int j = 0; j < 16; ++j) q[j * stride] = v[j];
     }
+}
+
+__device__ __forceinline__ void load16ps(pk64 (&v)[16], const float2* p, int s) {
+    with_stride(s, [&](int st) { load16p(v, p, st); });
+}
+
+__device__ __forceinline__ void store16ps(const pk64 (&v)[16], float2* p, int s) {
+    with_stride(s, [&](int st) { store16p(v, p, st); });
 }
 
 // RY(a) on register bit K of a packed state; C = (c, c), S = (s, s), NS = (-s, -s).
