@@ -254,6 +254,24 @@ __device__ void stage_classes(const DensePassDev& P, const DenseClassDev* classe
     __syncthreads();
 }
 
+// The rotations of a pass's register groups, staged once per CTA: kind (-1 where the group has
+// no rotation on that bit) and (cos a/2, sin a/2) of slot 4 g + k. Ends without a barrier.
+__device__ __forceinline__ void stage_group_gates(const DensePassDev& P, const tlq_gate* gates, const float2* GT,
+                                                  int* s_gkind, float2* s_gcs, int tid) {
+    if (tid < 4 * kDenseMaxGroups) {
+        const int g = tid >> 2, k = tid & 3;
+        int kind = -1;
+        float2 cs = make_float2(1.f, 0.f);
+        if (g < P.ngroups && ((P.group_mask[g] >> k) & 1u)) {
+            const int gate = P.gate[g][k];
+            kind = gates[gate].kind;
+            cs = GT[gate];
+        }
+        s_gkind[tid] = kind;
+        s_gcs[tid] = cs;
+    }
+}
+
 // Split class count of amplitude j of a register pass: count(x_b | j) from the count at the
 // thread's base index, the per-bit deltas A_k and the in-group pairs C[j] (see DensePassClassDev).
 __device__ __forceinline__ void split_deltas(const DenseClassDev& C, const DensePassClassDev& pc, uint32_t xb,
@@ -374,8 +392,11 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_co
     InitStage* S = reinterpret_cast<InitStage*>(smem_raw + dense_pass_smem_base());   // GEN only
     const uint32_t ntiles = 1u << (A.n_eff - kDenseTileBits);
 
+    __shared__ int s_gkind[4 * kDenseMaxGroups];
+    __shared__ float2 s_gcs[4 * kDenseMaxGroups];
     if (!GEN && blockIdx.x < ntiles) issue_tile(P, blockIdx.x, A.state, bufs, tid);
 
+    stage_group_gates(P, A.gates, A.GT, s_gkind, s_gcs, tid);   // visible after the barriers below
     stage_classes(P, A.classes, A.pcd, A.stage, A.dists, A.ptab, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab, tid);
     if (GEN)
         stage_init(*S, A.n_eff, A.init, A.gates, A.GT, A.classes, A.init_class_off, A.init_nclass, A.init_pcd, A.dists,
@@ -394,24 +415,16 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_co
         }
         for (int g = 0; g < P.ngroups; ++g) {
             const int s = P.group_s[g];
-            const unsigned m = P.group_mask[g];
             int kd[4];
             float c[4], sn[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                kd[k] = -1;
-                c[k] = 1.f;
-                sn[k] = 0.f;
-                if ((m >> k) & 1) {
-                    const int gate = P.gate[g][k];
-                    kd[k] = A.gates[gate].kind;
-                    const float2 v = A.GT[gate];
-                    c[k] = v.x;
-                    sn[k] = v.y;
-                }
+                kd[k] = s_gkind[4 * g + k];
+                const float2 v = s_gcs[4 * g + k];
+                c[k] = v.x;
+                sn[k] = v.y;
             }
             const int lowmask = (1 << s) - 1;
-            const int stride = pass_stride(s);
             const int base = (tid & lowmask) | ((tid >> s) << (s + 4));
             float2* p = tile + pad16(base);
             pk64 u[16];   // the 16 amplitudes as packed (re, im) registers
@@ -773,20 +786,17 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
-// The thread's share of Im<lam|G|psi> for the rotation on register bit K, which is then
-// un-applied from psi and lam.
+// The thread's share of Im<lam|G|psi> for the rotation on register bit K (kind and
+// (cos a/2, sin a/2) from the staged group gates), which is then un-applied from psi and lam.
 template <int K>
-__device__ __forceinline__ float adjoint_bit(const AdjArgs& A, int g, float2 (&v)[16], float2 (&u)[16]) {
-    const int gate = A.pass.gate[g][K];
-    const float2 cs = A.GT[gate];
-    return adjoint_rot<K, float2, float>(v, u, A.gates[gate].kind, cs.x, -cs.y);
+__device__ __forceinline__ float adjoint_bit(int kind, float2 cs, float2 (&v)[16], float2 (&u)[16]) {
+    return adjoint_rot<K, float2, float>(v, u, kind, cs.x, -cs.y);
 }
 
 // Layer-0 rotation on register bit K: gradient only (see DensePassDev::group_rot0).
 template <int K>
-__device__ __forceinline__ float gradient_bit(const AdjArgs& A, int g, const float2 (&v)[16], const float2 (&u)[16]) {
-    const int gate = A.pass.gate[g][K];
-    return A.gates[gate].kind == TLQ_RY ? grad_y<K, float2, float>(v, u) : grad_x<K, float2, float>(v, u);
+__device__ __forceinline__ float gradient_bit(int kind, const float2 (&v)[16], const float2 (&u)[16]) {
+    return kind == TLQ_RY ? grad_y<K, float2, float>(v, u) : grad_x<K, float2, float>(v, u);
 }
 
 __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid_constant__ AdjArgs A) {
@@ -810,6 +820,9 @@ __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid
         issue_tile(P, blockIdx.x, A.lam, blam, tid);
     }
     for (int k = tid; k < (kThreads / 32) * kDenseAdjSlots; k += kThreads) s_gacc[k] = 0.0;
+    __shared__ int s_gkind[4 * kDenseMaxGroups];
+    __shared__ float2 s_gcs[4 * kDenseMaxGroups];
+    stage_group_gates(P, A.gates, A.GT, s_gkind, s_gcs, tid);   // visible after the barriers below
     stage_classes(P, A.classes, A.pcd, A.stage, A.dists, A.ptab, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab, tid);
     double* acc = s_gacc + warp * kDenseAdjSlots;   // written by one lane of this warp per slot
 
@@ -873,16 +886,18 @@ __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid
             // rotations commute and nothing after them needs the state, so they only give gradients
             const unsigned m = P.group_mask[g];
             float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+            const int* gk = s_gkind + 4 * g;
+            const float2* gcs = s_gcs + 4 * g;
             if ((P.group_rot0 >> g) & 1u) {
-                if (m & 1u) g0 = gradient_bit<0>(A, g, v, u);
-                if (m & 2u) g1 = gradient_bit<1>(A, g, v, u);
-                if (m & 4u) g2 = gradient_bit<2>(A, g, v, u);
-                if (m & 8u) g3 = gradient_bit<3>(A, g, v, u);
+                if (m & 1u) g0 = gradient_bit<0>(gk[0], v, u);
+                if (m & 2u) g1 = gradient_bit<1>(gk[1], v, u);
+                if (m & 4u) g2 = gradient_bit<2>(gk[2], v, u);
+                if (m & 8u) g3 = gradient_bit<3>(gk[3], v, u);
             } else {
-                if (m & 1u) g0 = adjoint_bit<0>(A, g, v, u);
-                if (m & 2u) g1 = adjoint_bit<1>(A, g, v, u);
-                if (m & 4u) g2 = adjoint_bit<2>(A, g, v, u);
-                if (m & 8u) g3 = adjoint_bit<3>(A, g, v, u);
+                if (m & 1u) g0 = adjoint_bit<0>(gk[0], gcs[0], v, u);
+                if (m & 2u) g1 = adjoint_bit<1>(gk[1], gcs[1], v, u);
+                if (m & 4u) g2 = adjoint_bit<2>(gk[2], gcs[2], v, u);
+                if (m & 8u) g3 = adjoint_bit<3>(gk[3], gcs[3], v, u);
             }
             {   // the group's four warp sums in one transposing reduction: lane 8 k holds bit k's
                 const float gk = warp_sum4(g0, g1, g2, g3, lane);
