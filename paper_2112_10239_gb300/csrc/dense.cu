@@ -307,19 +307,14 @@ __device__ __forceinline__ void group_epilogue(const PassArgs& A, const DensePas
     const int ncls = P.group_ncls[g];
     if (ncls > 0 || g == P.measure_group) {
         const uint32_t xb = tile_x(P, t_id, (uint32_t)base);   // register bits are zero in base
-        float2 ph[16];
         float ez[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            ph[j] = make_float2(1.f, 0.f);
-            ez[j] = 0.f;
-        }
-        bool any_phase = false, any_energy = g == P.measure_group;
+        for (int j = 0; j < 16; ++j) ez[j] = 0.f;
+        bool any_energy = g == P.measure_group;
         for (int ci = P.group_cls[g]; ci < P.group_cls[g] + ncls; ++ci) {
             const DenseClassDev& C = s_cls[ci];
             const DensePassClassDev& pc = s_pcd[ci];
             const int woff = s_woff[ci], toff = s_toff[ci];
-            any_phase |= C.kind != 2;
             any_energy |= C.kind == 2;
             const int cnt0 = class_count(C, s_dist + woff, xb);
             int Ak[4];
@@ -337,15 +332,16 @@ __device__ __forceinline__ void group_epilogue(const PassArgs& A, const DensePas
                 if (j & 2) cnt += Ak[1];
                 if (j & 4) cnt += Ak[2];
                 if (j & 8) cnt += Ak[3];
-                if (C.kind == 0) ph[j] = cmul(ph[j], s_tab[toff + cnt]);
-                else if (C.kind == 1) { if (cnt & 1) { ph[j].x = -ph[j].x; ph[j].y = -ph[j].y; } }
+                // phases multiply the amplitudes directly (|v|^2, and so the energy, does not
+                // depend on their order; lam below takes the final amplitudes)
+                if (C.kind == 0) v[j] = cmul(v[j], s_tab[toff + cnt]);
+                else if (C.kind == 1) { if (cnt & 1) { v[j].x = -v[j].x; v[j].y = -v[j].y; } }
                 else ez[j] += (float)C.coeff * (float)(C.nterms - 2 * cnt);
             }
         }
         const uint32_t xstep = tile_step(P, s);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            if (any_phase) v[j] = cmul(v[j], ph[j]);
             if (any_energy) {
                 if (A.n_zterms > 0) {
                     const uint32_t x = xb + j * xstep;
@@ -365,21 +361,28 @@ __device__ __forceinline__ void group_epilogue(const PassArgs& A, const DensePas
 }
 
 // Persistent pass kernel: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-// with two shared-memory tile buffers; the cp.async copy of the next tile runs while the
-// current one is processed. The last register pass writes its 16 amplitudes straight to HBM.
-__host__ __device__ constexpr size_t dense_pass_smem_base() {
-    return ((2 * (size_t)padded_amps_c(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
+// in one of two forms. SINGLE: one shared-memory tile buffer and three CTAs per SM (80
+// registers); once every thread holds its amplitudes of the last register pass, the cp.async
+// copy of the CTA's next tile starts, and the other CTAs of the SM keep it busy meanwhile.
+// Otherwise: two tile buffers and two CTAs per SM; the copy of the next tile runs while the
+// current one is processed. Energy-only calls take the first form, the forward of a gradient
+// call the second (measured faster for each). The last register pass writes its 16 amplitudes
+// straight to HBM.
+__host__ __device__ constexpr int dense_pass_bufs(bool single) { return single ? 1 : 2; }
+__host__ __device__ constexpr int dense_pass_ctas(bool single) { return single ? 3 : 2; }
+__host__ __device__ constexpr size_t dense_pass_smem_base(bool single) {
+    return ((dense_pass_bufs(single) * (size_t)padded_amps_c(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
              kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * (sizeof(DenseClassDev) + sizeof(DensePassClassDev)) +
              2 * kMaxLayerClasses * sizeof(int32_t) + 16 * sizeof(float)) + 15) / 16 * 16;
 }
 
 // GEN: the first forward pass of a low tile whose first group starts at bit 0 -- its input is
 // layer 0's product state, generated in registers for group 0 (gen16) instead of read from HBM.
-template <bool GEN>
-__global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_constant__ PassArgs A) {
+template <bool GEN, bool SINGLE>
+__global__ void __launch_bounds__(kThreads, dense_pass_ctas(SINGLE)) dense_pass_kernel(const __grid_constant__ PassArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float2* bufs = reinterpret_cast<float2*>(smem_raw);                              // 2 x padded_amps(12)
-    float2* s_tab = bufs + 2 * padded_amps(kDenseTileBits);                          // kMaxTab
+    float2* bufs = reinterpret_cast<float2*>(smem_raw);                     // 1 or 2 x padded_amps(12)
+    float2* s_tab = bufs + dense_pass_bufs(SINGLE) * padded_amps(kDenseTileBits);   // kMaxTab
     int32_t* s_dist = reinterpret_cast<int32_t*>(s_tab + kMaxTab);                   // kMaxDistWords
     DenseClassDev* s_cls = reinterpret_cast<DenseClassDev*>(s_dist + kMaxDistWords); // kMaxLayerClasses
     DensePassClassDev* s_pcd = reinterpret_cast<DensePassClassDev*>(s_cls + kMaxLayerClasses);
@@ -389,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_co
     const DensePassDev& P = A.pass;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    InitStage* S = reinterpret_cast<InitStage*>(smem_raw + dense_pass_smem_base());   // GEN only
+    InitStage* S = reinterpret_cast<InitStage*>(smem_raw + dense_pass_smem_base(SINGLE));   // GEN only
     const uint32_t ntiles = 1u << (A.n_eff - kDenseTileBits);
 
     __shared__ int s_gkind[4 * kDenseMaxGroups];
@@ -405,13 +408,13 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_co
     float eacc = 0.f;
     int i = 0;
     for (uint32_t t_id = blockIdx.x; t_id < ntiles; t_id += gridDim.x, ++i) {
-        const int b = i & 1;
-        float2* tile = bufs + b * padded_amps(kDenseTileBits);
+        float2* tile = bufs + (SINGLE ? 0 : (i & 1) * padded_amps(kDenseTileBits));
         if (!GEN) {
             wait_tiles();        // this thread's copies of tile t_id have landed
             __syncthreads();     // ... and everyone else's
             const uint32_t next = t_id + gridDim.x;
-            if (next < ntiles) issue_tile(P, next, A.state, bufs + (b ^ 1) * padded_amps(kDenseTileBits), tid);
+            if (!SINGLE && next < ntiles)
+                issue_tile(P, next, A.state, bufs + ((i & 1) ^ 1) * padded_amps(kDenseTileBits), tid);
         }
         for (int g = 0; g < P.ngroups; ++g) {
             const int s = P.group_s[g];
@@ -436,6 +439,11 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_co
             } else {
                 load16ps(u, p, s);
             }
+            if (SINGLE && g == P.ngroups - 1) {   // every thread holds its last amplitudes: the buffer is free
+                __syncthreads();
+                const uint32_t next = t_id + gridDim.x;
+                if (!GEN && next < ntiles) issue_tile(P, next, A.state, bufs, tid);
+            }
             if (kd[0] >= 0) apply_rot_p<0>(u, kd[0], c[0], sn[0]);
             if (kd[1] >= 0) apply_rot_p<1>(u, kd[1], c[1], sn[1]);
             if (kd[2] >= 0) apply_rot_p<2>(u, kd[2], c[2], sn[2]);
@@ -458,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_co
                 for (int j = 0; j < 16; ++j) dst[j * step] = u[j];
             }
         }
-        __syncthreads();   // the buffer is free for the copy issued in the next iteration
+        if (!SINGLE) __syncthreads();   // the buffer is free for the copy issued in the next iteration
     }
     if (P.measure_group >= 0) {
 #pragma unroll
@@ -473,14 +481,14 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(const __grid_co
     }
 }
 
-size_t dense_pass_smem() {
-    return 2 * (size_t)padded_amps(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
+size_t dense_pass_smem(bool single) {
+    return dense_pass_bufs(single) * (size_t)padded_amps(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
            kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * (sizeof(DenseClassDev) + sizeof(DensePassClassDev)) +
            2 * kMaxLayerClasses * sizeof(int32_t) + 16 * sizeof(float);
 }
 
 // The generating pass keeps layer 0's staging (InitStage) after the pass kernel's own data.
-size_t dense_pass_gen_smem() { return dense_pass_smem_base() + sizeof(InitStage); }
+size_t dense_pass_gen_smem(bool single) { return dense_pass_smem_base(single) + sizeof(InitStage); }
 
 // ---- tensor-core passes (mixed precision: split TF32 products, FP32 accumulation) ----------
 //
@@ -1195,7 +1203,13 @@ size_t dense_partial_count(int n_eff) { return dense_norm_offset(n_eff) + 2 * kM
 
 int dense_grid(int n_eff, int sm_count) {
     const int ntiles = 1 << (n_eff - kDenseTileBits);
-    return ntiles < 2 * sm_count ? ntiles : 2 * sm_count;   // two CTAs per SM
+    return ntiles < 2 * sm_count ? ntiles : 2 * sm_count;   // two CTAs per SM (the adjoint)
+}
+
+static int dense_fwd_grid(int n_eff, int sm_count, bool single) {
+    const int ntiles = 1 << (n_eff - kDenseTileBits);
+    const int g = dense_pass_ctas(single) * sm_count;
+    return ntiles < g ? ntiles : g;
 }
 
 namespace {
@@ -1257,18 +1271,26 @@ int launch_dense(DenseLaunch& L, void* stream) {
     float2* psi = (float2*)L.state;
     float2* lam = (float2*)L.lam;
     int launches = 0;
-    const size_t smem = dense_pass_smem();
+    // energy-only calls run the single-buffered passes (three CTAs per SM), gradient calls the
+    // double-buffered ones (two CTAs per SM)
+    const bool single = L.grad == nullptr;
+    const size_t smem = dense_pass_smem(single);
     const size_t asmem = dense_adjoint_smem();
-    if ((e = cudaFuncSetAttribute(dense_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-        return (int)e;
     // layer 0's product state generated inside the first forward pass (no start kernel, no read
     // of the start state) when that pass is a low tile whose first group starts at bit 0
     const bool gen_first = !L.per_gate && !L.tc && L.product_init && L.gen_first;
-    const size_t gsmem = dense_pass_gen_smem();
-    if (gen_first && (e = cudaFuncSetAttribute(dense_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)gsmem)) != cudaSuccess)
-        return (int)e;
+    const size_t gsmem = dense_pass_gen_smem(single);
+    // each kernel with its dynamic shared memory and the largest shared-memory carveout, so
+    // that its CTAs per SM fit
+    auto prepare = [](const void* k, size_t bytes) {
+        cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        return r;
+    };
+    const void* kpass = single ? (const void*)dense_pass_kernel<false, true> : (const void*)dense_pass_kernel<false, false>;
+    const void* kgen = single ? (const void*)dense_pass_kernel<true, true> : (const void*)dense_pass_kernel<true, false>;
+    if ((e = prepare(kpass, smem)) != cudaSuccess) return (int)e;
+    if (gen_first && (e = prepare(kgen, gsmem)) != cudaSuccess) return (int)e;
     size_t tc_smem = 0;
     int tc_nblk = 0;
     if (L.tc && !L.per_gate) {
@@ -1342,7 +1364,7 @@ int launch_dense(DenseLaunch& L, void* stream) {
             A.init_class_off = L.init_class_off;
             A.init_nclass = L.init_nclass;
             A.init_pcd = L.init_pcd;
-            const int grid = dense_grid(L.n_eff, L.sm_count);
+            const int grid = dense_fwd_grid(L.n_eff, L.sm_count, single);
             const int ntiles = 1 << (L.n_eff - kDenseTileBits);
             const int tc_grid = std::min(std::min((ntiles + 1) / 2, L.sm_count), kMaxSms);   // one CTA per SM
             bool measured = false;
@@ -1357,8 +1379,10 @@ int launch_dense(DenseLaunch& L, void* stream) {
                     A.pass.store = 0;   // energies only: nothing reads the final state
                 }
                 if (L.tc) dense_tc_pass_kernel<<<tc_grid, kTcPassThreads, tc_smem, st>>>(A, tc_nblk);
-                else if (gen_first && p == 0) dense_pass_kernel<true><<<grid, kThreads, gsmem, st>>>(A);
-                else dense_pass_kernel<false><<<grid, kThreads, smem, st>>>(A);
+                else if (gen_first && p == 0 && single) dense_pass_kernel<true, true><<<grid, kThreads, gsmem, st>>>(A);
+                else if (gen_first && p == 0) dense_pass_kernel<true, false><<<grid, kThreads, gsmem, st>>>(A);
+                else if (single) dense_pass_kernel<false, true><<<grid, kThreads, smem, st>>>(A);
+                else dense_pass_kernel<false, false><<<grid, kThreads, smem, st>>>(A);
                 ++launches;
                 if (A.pass.measure_group >= 0) measured = true;
             }
