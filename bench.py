@@ -59,6 +59,9 @@ def parse():
                          "statevector path, one parameter set)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "mixed_tc"],
                     help="precision of the timed workload (mixed_tc: tensor-core gate blocks on the dense path)")
+    ap.add_argument("--energy-only", action="store_true",
+                    help="time energy-only calls (expectation evals/s) instead of energy + gradient; no CPU baseline "
+                         "or plain path")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the chosen workload only: no other workloads, serving replay or CPU baseline "
                          "(short runs for a profiler)")
@@ -863,10 +866,12 @@ def main():
     B.tlq_profile_enable(ctx.h, True)
 
     prec = B.TLQ_MIXED_TC if args.prec == "mixed_tc" else B.TLQ_FP32
+    grad = not args.energy_only
+    metric, unit = (METRIC, UNIT) if grad else ("expectation evals/sec", "evals/s")
 
     def step():
         B.tlq_expectation_grad_dev(ctx.h, c.h, h.h, theta_d.data_ptr(), Bsz, prec, E_d.data_ptr(),
-                                   G_d.data_ptr(), stream.cuda_stream)
+                                   G_d.data_ptr() if grad else 0, stream.cuda_stream)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -898,12 +903,18 @@ def main():
     # kernel profiling off, as for any caller (it records events around single kernels)
     B.tlq_profile_enable(ctx.h, False)
     theta_h = np.ascontiguousarray(prob.theta)
+
+    def host_call():
+        if grad:
+            return B.tlq_expectation_grad(ctx.h, c.h, h.h, theta_h, prec)
+        return B.tlq_expectation(ctx.h, c.h, h.h, theta_h, prec), None
+
     for _ in range(3):
-        B.tlq_expectation_grad(ctx.h, c.h, h.h, theta_h, prec)
+        host_call()
     e2e_t = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        E_h, G_h = B.tlq_expectation_grad(ctx.h, c.h, h.h, theta_h, prec)
+        E_h, G_h = host_call()
         e2e_t.append(time.perf_counter() - t0)
     e2e_value, _ = job_throughput(sum(e2e_t), Bsz * len(e2e_t), world, dev)
 
@@ -911,13 +922,13 @@ def main():
     path, *_ = B.tlq_plan_info(ctx.h, c.h, h.h, len(prob.terms))
     err64 = None
     if path == B.TLQ_PATH_CONE:
-        E64, G64 = fp64_reference(B, ctx, c, h, theta_h)
+        E64, G64 = fp64_reference(B, ctx, c, h, theta_h, grad)
         err64 = fp64_errors(E_h, G_h, E64, G64)
 
     # the plain per-circuit FP32 path on the same GPU: one parameter set per call, and (up to 24
     # qubits) the per-gate statevector sweeps
     plain = None
-    if rank == 0 and not args.no_extras and path == B.TLQ_PATH_CONE:
+    if rank == 0 and not args.no_extras and grad and path == B.TLQ_PATH_CONE:
         import ctypes
         one_ms = plain_one_set_per_call(B, ctx, c, h, prob, dev, flush)
         plain = {"one_set_per_call": {"kind": "one parameter set per call (B = 1), same kernels",
@@ -947,20 +958,22 @@ def main():
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     kern_mean_ms = float(np.mean(kern_ms))
     if path == B.TLQ_PATH_DENSE:
-        nbytes, passes = dense_bytes(B, ctx, c, h, True, prec)
+        nbytes, passes = dense_bytes(B, ctx, c, h, grad, prec)
         achieved = nbytes / (kern_mean_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                     "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
                     "kernel": ("dense_tc_pass_kernel" if args.prec == "mixed_tc" else "dense_pass_kernel") +
-                              " + dense_adjoint_kernel (forward and reverse passes)",
+                              (" + dense_adjoint_kernel (forward and reverse passes)" if grad else
+                               " (forward passes)"),
                     "kernel_ms": kern_mean_ms, "bytes_per_eval": nbytes, "passes": passes}
     else:
-        flops = algorithmic_flops(B, ctx, c, h, prob, grad=True)
-        _, flops_unf = unfused_flops(prob)
+        flops = algorithmic_flops(B, ctx, c, h, prob, grad=grad)
+        _, flops_unf = unfused_flops(prob, grad=grad)
         achieved = flops / (kern_mean_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / peak_tflops, "traffic": NCU_TRAFFIC.get((args.workload, "cone_kernel")),
-                    "kernel": "cone_kernel<float,grad> (batched causal cones + adjoint)",
+                    "kernel": ("cone_kernel<float,grad> (batched causal cones + adjoint)" if grad else
+                               "cone_kernel<float,energy> (batched causal cones)"),
                     "kernel_ms": kern_mean_ms, "algorithmic_flops": flops,
                     "algorithmic_flops_basis": "work the shared windows require (terms nested in a window are "
                                                "measured on it)",
@@ -968,14 +981,15 @@ def main():
         if flops_unf is not None:
             roofline.update({"algorithmic_flops_unfused": flops_unf,
                              "frac_unfused": flops_unf / (kern_mean_ms * 1e-3) / 1e12 / peak_tflops,
-                             "unfused_basis": "every term on its own exact causal cone, adjoint = 3 x forward"})
+                             "unfused_basis": "every term on its own exact causal cone" +
+                                              (", adjoint = 3 x forward" if grad else ", forward and measurement")})
 
     extras = extra_workloads(B, dev, local, flush, peaks) if rank == 0 and not args.no_extras else {}
     if rank == 0:
-        cpu = None if args.no_extras else cpu_baseline(prob)
+        cpu = None if (args.no_extras or not grad) else cpu_baseline(prob)
         sm = sorted(step_ms)
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "n": prob.n, "L": prob.meta.get("L"), "B": Bsz, "prec": args.prec,
@@ -983,8 +997,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "latency_ms": {"p50": sm[len(sm) // 2], "p99": sm[min(len(sm) - 1, int(math.ceil(0.99 * len(sm))) - 1)],
                            "per": f"batch of {Bsz} parameter sets"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(theta_h.nbytes),
-                    "d2h_bytes_per_step": int(E_h.nbytes + G_h.nbytes)},
+            "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": int(theta_h.nbytes),
+                    "d2h_bytes_per_step": int(E_h.nbytes + (G_h.nbytes if G_h is not None else 0))},
             "gpu_launches": launches,
             "roofline": roofline,
             "err_vs_fp64": err64,
