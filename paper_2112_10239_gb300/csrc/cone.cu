@@ -79,7 +79,7 @@ __host__ __device__ inline TeamLayout team_layout(int W, int Wt, int tt, int rea
     if (smem_state && grad) off += padded_amps(W) * r2;
     const bool tiled = tiled_state(W, real_bytes, smem_state);
     L.tile = off;
-    if (tiled) off += kTileTeams * padded_amps(kTileBits) * r2 * (grad ? 2 : 1);
+    if (tiled) off += kTileTeams * padded_amps(kTileBits) * r2 * 2;   // psi and lam, or two psi buffers
     const int b1 = (Wt - 7) < 7 ? (Wt - 7) : 7;
     const int b2 = Wt > 14 ? Wt - 14 : 0;
     L.tab1 = 136;
@@ -880,8 +880,8 @@ __device__ __forceinline__ TileMap sweep_tile(int g, int t, int half) {
 // half issues the copies: loads complete on the half's mbarrier (one phase per tile), stores go
 // into bulk groups that the same thread retires before its buffers are loaded again.
 struct TileSync {
-    uint64_t* bar;     // one mbarrier per half (shared memory)
-    uint32_t phase;    // this thread's half: parity of its next load
+    uint64_t* bar;     // two mbarriers per half, one per tile buffer (shared memory)
+    uint32_t phase;    // this thread's half: bit k = parity of the next load into buffer k
 };
 
 __device__ __forceinline__ int tile_blocks(const TileMap& tp) { return tp.a == kTileBits ? 1 : 1 << (kTileBits - kTileLowBits); }
@@ -918,9 +918,9 @@ __device__ __forceinline__ void tile_store(float2* const (&tiles)[2], float2* co
 }
 
 // Every thread of the half: wait (bounded) for the load of the half's current tile.
-__device__ __forceinline__ void tile_wait(TileSync& ts, int half, const ConeArgs& A) {
-    if (!tc::mbar_wait(ts.bar + half, ts.phase)) atomicOr(A.err, 1);
-    ts.phase ^= 1u;
+__device__ __forceinline__ void tile_wait(TileSync& ts, int half, int buf, const ConeArgs& A) {
+    if (!tc::mbar_wait(ts.bar + 2 * half + buf, (ts.phase >> buf) & 1u)) atomicOr(A.err, 1);
+    ts.phase ^= 1u << buf;
 }
 
 // End of a sweep, before the CTA barrier: the half's stores are complete and visible to the
@@ -948,8 +948,10 @@ __device__ void tiled_forward(const ConeArgs& A, const TeamMem<float2>& M, const
     const int W = M.W;
     const int ntiles = 1 << (W - kTileBits);
     const Team ht = tile_half(tm);
-    float2* tile = M.tile + ht.id * padded_amps(kTileBits);
-    float2* const tiles[2] = {tile, tile};
+    // two psi buffers per half (the adjoint's psi and lam tiles): the load of the half's next
+    // tile runs while the current one is processed
+    float2* const buf[2] = {M.tile + 2 * ht.id * padded_amps(kTileBits),
+                            M.tile + (2 * ht.id + 1) * padded_amps(kTileBits)};
     float2* const gs[2] = {M.psi, M.psi};
     for (int li = 1; li < nl; ++li) {
         const int32_t* lp = body + lofs[li];
@@ -967,10 +969,19 @@ __device__ void tiled_forward(const ConeArgs& A, const TeamMem<float2>& M, const
         for (int k = 0; k < LS.n; ++k) {
             const bool dg = ndiag > 0 && k == LS.n - 1;
             const bool low = LS.g[k] == 0;
-            for (int t = ht.id; t < ntiles; t += kTileTeams) {
+            int cur = 0;
+            if (ht.tid == 0 && ht.id < ntiles) {
+                float2* const t0[2] = {buf[0], buf[0]};
+                tile_fetch(t0, gs, 1, sweep_tile(LS.g[k], ht.id, ht.id), ts.bar + 2 * ht.id);
+            }
+            for (int t = ht.id; t < ntiles; t += kTileTeams, cur ^= 1) {
                 TileMap tp = sweep_tile(LS.g[k], t, ht.id);
-                if (ht.tid == 0) tile_fetch(tiles, gs, 1, tp, ts.bar + ht.id);
-                tile_wait(ts, ht.id, A);
+                tile_wait(ts, ht.id, cur, A);
+                if (ht.tid == 0 && t + kTileTeams < ntiles) {   // every thread left buf[cur ^ 1] behind
+                    float2* const tn[2] = {buf[cur ^ 1], buf[cur ^ 1]};
+                    tile_fetch(tn, gs, 1, sweep_tile(LS.g[k], t + kTileTeams, ht.id), ts.bar + 2 * ht.id + (cur ^ 1));
+                }
+                float2* tile = buf[cur];
                 if (LS.ng[k] == 0)   // the diagonal alone
                     pass_fwd<real, float2, true>(tile, kTileLowBits, 0u, true, ht, M, par, &tp);
                 for (int gi = 0; gi < LS.ng[k]; ++gi) {
@@ -981,7 +992,10 @@ __device__ void tiled_forward(const ConeArgs& A, const TeamMem<float2>& M, const
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 ht.sync();
-                if (ht.tid == 0) tile_store(tiles, gs, 1, tp);
+                if (ht.tid == 0) {
+                    float2* const tc2[2] = {tile, tile};
+                    tile_store(tc2, gs, 1, tp);
+                }
             }
             tile_sweep_done(ht);
             tm.sync();   // the next sweep reads tiles of both halves
@@ -1028,8 +1042,8 @@ __device__ void tiled_adjoint(const ConeArgs& A, const TeamMem<float2>& M, const
             real* rb = red + rpar * kMaxSweepSlots * nw;
             for (int t = ht.id; t < ntiles; t += kTileTeams) {
                 TileMap tp = sweep_tile(LS.g[k], t, ht.id);
-                if (ht.tid == 0) tile_fetch(tiles, gs, 2, tp, ts.bar + ht.id);
-                tile_wait(ts, ht.id, A);
+                if (ht.tid == 0) tile_fetch(tiles, gs, 2, tp, ts.bar + 2 * ht.id);
+                tile_wait(ts, ht.id, 0, A);
                 if (dg) {
                     pass_bwd<real, float2, true, false, true>(tp_psi, tp_lam, low ? kTileLowBits : LS.g[k], 0u, ht, M,
                                                               par, rb + 12 * nw, &tp);
@@ -1210,11 +1224,11 @@ __global__ void __launch_bounds__(GLOBAL ? kGlobalCtaThreads : kCtaThreads, GLOB
 cone_kernel(ConeArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_chunk;
-    __shared__ __align__(8) uint64_t s_tile_bar[kTileTeams];   // tiled global tier: one per half
+    __shared__ __align__(8) uint64_t s_tile_bar[2 * kTileTeams];   // tiled global tier: two per half
     TileSync ts{s_tile_bar, 0u};
     if constexpr (GLOBAL && sizeof(real) == 4) {
         if (threadIdx.x == 0) {
-            for (int h = 0; h < kTileTeams; ++h) tc::mbar_init(s_tile_bar + h, 1);
+            for (int h = 0; h < 2 * kTileTeams; ++h) tc::mbar_init(s_tile_bar + h, 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
         __syncthreads();
