@@ -1052,12 +1052,21 @@ struct Neumaier {
 };
 
 // out[0] (+)= coeff * sum of partial[0..n) in fixed order
+// One warp: lane l sums partials l, l + 32, ... (compensated), then lane 0 adds the 32 lane
+// sums in lane order after the value already in *out; the order is fixed, whatever the launch.
 __global__ void reduce_partials_kernel(const double* partial, int n, double coeff, double* out, int accumulate) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    Neumaier mine;
+    for (int i = lane; i < n; i += 32) mine.add(coeff * partial[i]);
+    const double v = mine.value();
     Neumaier acc;
-    if (accumulate) acc.add(*out);
-    for (int i = 0; i < n; ++i) acc.add(coeff * partial[i]);
-    *out = acc.value();
+    if (lane == 0 && accumulate) acc.add(*out);
+    for (int l = 0; l < 32; ++l) {
+        const double x = __shfl_sync(0xffffffffu, v, l);
+        if (lane == 0) acc.add(x);
+    }
+    if (lane == 0) *out = acc.value();
 }
 
 // Tensor-core mode: divide the energy (and the gradient) by <psi|psi> = sum of the norm
