@@ -1290,6 +1290,8 @@ __global__ void gate_table_kernel(const tlq_gate* gates, int n_gates, const doub
 
 // ---- K5: fixed-order compensated reductions ---------------------------------------------
 
+constexpr int kReduceThreads = 64;
+
 struct Neumaier {
     double s = 0, c = 0;
     __device__ void add(double x) {
@@ -1444,11 +1446,13 @@ int launch_cone(ConeLaunch& L, void* stream) {
     if (rc) return rc;
     if (L.ev_end && (e = cudaEventRecord((cudaEvent_t)L.ev_end, st)) != cudaSuccess) return (int)e;
     {
-        const int eb = (L.B + 7) / 8;   // 8 warps per block
+        // small blocks (two warps): the compensated FP64 sums spread over every SM's FP64 units
+        const int thr = kReduceThreads;
+        const int eb = (L.B + thr / 32 - 1) / (thr / 32);   // one warp per set
         const int P = grad ? L.n_params : 0;
         const long long n = (long long)L.B * P;
-        const int gb = (int)((n + 255) / 256);
-        reduce_kernel<<<eb + gb, 256, 0, st>>>(L.e_part, L.term_coeff, L.n_terms, L.B, L.energy, eb, L.g_part,
+        const int gb = (int)((n + thr - 1) / thr);
+        reduce_kernel<<<eb + gb, thr, 0, st>>>(L.e_part, L.term_coeff, L.n_terms, L.B, L.energy, eb, L.g_part,
                                                L.pmap_off, L.pmap_idx, L.pmap_term, P, L.n_slots, L.grad);
         if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     }
