@@ -1280,15 +1280,16 @@ int launch_dense(DenseLaunch& L, void* stream) {
     float2* psi = (float2*)L.state;
     float2* lam = (float2*)L.lam;
     int launches = 0;
-    // energy-only calls run the single-buffered passes (three CTAs per SM), gradient calls the
-    // double-buffered ones (two CTAs per SM)
+    // forward passes run single-buffered at three CTAs per SM, except the pass that measures
+    // the energy of a gradient call (it also writes lambda), which runs double-buffered at two
+    // (measured faster for it)
     const bool single = L.grad == nullptr;
-    const size_t smem = dense_pass_smem(single);
+    const size_t smem = dense_pass_smem(true), smem2 = dense_pass_smem(false);
     const size_t asmem = dense_adjoint_smem();
     // layer 0's product state generated inside the first forward pass (no start kernel, no read
     // of the start state) when that pass is a low tile whose first group starts at bit 0
     const bool gen_first = !L.per_gate && !L.tc && L.product_init && L.gen_first;
-    const size_t gsmem = dense_pass_gen_smem(single);
+    const size_t gsmem = dense_pass_gen_smem(true), gsmem2 = dense_pass_gen_smem(false);
     // each kernel with its dynamic shared memory and the largest shared-memory carveout, so
     // that its CTAs per SM fit
     auto prepare = [](const void* k, size_t bytes) {
@@ -1296,10 +1297,13 @@ int launch_dense(DenseLaunch& L, void* stream) {
         if (r == cudaSuccess) r = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         return r;
     };
-    const void* kpass = single ? (const void*)dense_pass_kernel<false, true> : (const void*)dense_pass_kernel<false, false>;
-    const void* kgen = single ? (const void*)dense_pass_kernel<true, true> : (const void*)dense_pass_kernel<true, false>;
-    if ((e = prepare(kpass, smem)) != cudaSuccess) return (int)e;
-    if (gen_first && (e = prepare(kgen, gsmem)) != cudaSuccess) return (int)e;
+    if ((e = prepare((const void*)dense_pass_kernel<false, true>, smem)) != cudaSuccess) return (int)e;
+    if (gen_first && (e = prepare((const void*)dense_pass_kernel<true, true>, gsmem)) != cudaSuccess) return (int)e;
+    if (!single) {
+        if ((e = prepare((const void*)dense_pass_kernel<false, false>, smem2)) != cudaSuccess) return (int)e;
+        if (gen_first && (e = prepare((const void*)dense_pass_kernel<true, false>, gsmem2)) != cudaSuccess)
+            return (int)e;
+    }
     size_t tc_smem = 0;
     int tc_nblk = 0;
     if (L.tc && !L.per_gate) {
@@ -1373,7 +1377,10 @@ int launch_dense(DenseLaunch& L, void* stream) {
             A.init_class_off = L.init_class_off;
             A.init_nclass = L.init_nclass;
             A.init_pcd = L.init_pcd;
-            const int grid = dense_fwd_grid(L.n_eff, L.sm_count, single);
+            const int grid = dense_fwd_grid(L.n_eff, L.sm_count, true);
+            const int grid2 = dense_fwd_grid(L.n_eff, L.sm_count, false);
+            int mgrid = grid;   // CTAs of the measuring pass: its energy partials
+            const int agrid = dense_grid(L.n_eff, L.sm_count);   // the adjoint (two CTAs per SM)
             const int ntiles = 1 << (L.n_eff - kDenseTileBits);
             const int tc_grid = std::min(std::min((ntiles + 1) / 2, L.sm_count), kMaxSms);   // one CTA per SM
             bool measured = false;
@@ -1387,16 +1394,18 @@ int launch_dense(DenseLaunch& L, void* stream) {
                 } else if (p == n_fwd - 1 && L.n_xterms == 0 && !L.keep_state) {
                     A.pass.store = 0;   // energies only: nothing reads the final state
                 }
+                const bool sp = single || A.pass.measure_group < 0;
+                if (A.pass.measure_group >= 0) mgrid = sp ? grid : grid2;
                 if (L.tc) dense_tc_pass_kernel<<<tc_grid, kTcPassThreads, tc_smem, st>>>(A, tc_nblk);
-                else if (gen_first && p == 0 && single) dense_pass_kernel<true, true><<<grid, kThreads, gsmem, st>>>(A);
-                else if (gen_first && p == 0) dense_pass_kernel<true, false><<<grid, kThreads, gsmem, st>>>(A);
-                else if (single) dense_pass_kernel<false, true><<<grid, kThreads, smem, st>>>(A);
-                else dense_pass_kernel<false, false><<<grid, kThreads, smem, st>>>(A);
+                else if (gen_first && p == 0 && sp) dense_pass_kernel<true, true><<<grid, kThreads, gsmem, st>>>(A);
+                else if (gen_first && p == 0) dense_pass_kernel<true, false><<<grid2, kThreads, gsmem2, st>>>(A);
+                else if (sp) dense_pass_kernel<false, true><<<grid, kThreads, smem, st>>>(A);
+                else dense_pass_kernel<false, false><<<grid2, kThreads, smem2, st>>>(A);
                 ++launches;
                 if (A.pass.measure_group >= 0) measured = true;
             }
             if (measured) {
-                reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, L.tc ? 2 * tc_grid : grid, 1.0, eout, 1);
+                reduce_partials_kernel<<<1, 32, 0, st>>>(L.partial, L.tc ? 2 * tc_grid : mgrid, 1.0, eout, 1);
                 ++launches;
             }
             for (int t = 0; t < L.n_xterms; ++t) {
@@ -1425,12 +1434,12 @@ int launch_dense(DenseLaunch& L, void* stream) {
                 for (int p = L.n_passes - 1; p >= 0; --p) {
                     R.pass = L.host_passes[p];
                     R.pass.store = L.host_rev_store[p];   // see DensePlan::rev_store
-                    R.gpart = L.gpart + (size_t)p * kDenseAdjSlots * grid;
-                    dense_adjoint_kernel<<<grid, kThreads, asmem, st>>>(R);
+                    R.gpart = L.gpart + (size_t)p * kDenseAdjSlots * agrid;
+                    dense_adjoint_kernel<<<agrid, kThreads, asmem, st>>>(R);
                     ++launches;
                 }
                 if (L.n_params > 0) {
-                    dense_grad_reduce_kernel<<<(L.n_params + 7) / 8, 256, 0, st>>>(L.gpart, grid, L.adj_off, L.adj_idx,
+                    dense_grad_reduce_kernel<<<(L.n_params + 7) / 8, 256, 0, st>>>(L.gpart, agrid, L.adj_off, L.adj_idx,
                                                                                  L.n_params, gout);
                     ++launches;
                 }
