@@ -39,6 +39,15 @@ constexpr int kMaxLayerClasses = kDenseMaxLayerClasses;
 constexpr int kMaxDistWords = kDenseMaxDistWords;  // (d, mask) int pairs staged in shared memory
 constexpr int kMaxTab = kDenseMaxTab;              // phase-table entries staged per layer
 
+// Edge-word tables of XOR classes (see class_count): up to kEwTabs per pass, each four rows of
+// 256 words over 8-bit chunks of the index, then the 32 per-qubit words they are built from.
+// A row keeps one padding word per 16 entries, so that lanes reading entries 16 apart (the
+// thread bases of a register group at bit 0) hit distinct banks.
+constexpr int kEwTabs = 2;
+constexpr int kEwRow = 256 + 16;
+__host__ __device__ constexpr size_t ew_bytes(int ntabs) { return (size_t)ntabs * (4 * kEwRow + 32) * sizeof(uint64_t); }
+__device__ __forceinline__ int ew_slot(uint32_t b) { return (int)(b + (b >> 4)); }
+
 // ---- layer 0 as a product state ----------------------------------------------------------
 //
 // Layer 0 acts on |0..0>, so the state after it is written directly instead of streamed: a
@@ -107,7 +116,8 @@ __device__ void stage_init(InitStage& S, int n_eff, const InitGates& I, const tl
     __syncthreads();
 }
 
-__device__ __forceinline__ int class_count(const DenseClassDev& c, const int32_t* dist, uint32_t x);
+__device__ __forceinline__ int class_count(const DenseClassDev& c, const int32_t* dist, const uint64_t* ew,
+                                           uint32_t x);
 __device__ __forceinline__ void split_deltas(const DenseClassDev& C, const DensePassClassDev& pc, uint32_t xb,
                                              int (&Ak)[4]);
 __device__ __forceinline__ int split_count(const DensePassClassDev& pc, int cnt0, const int (&Ak)[4], int j);
@@ -128,7 +138,7 @@ __device__ __forceinline__ void gen16(const InitStage& S, int n_eff, const float
     for (int ci = 0; ci < S.nc; ++ci) {
         const DenseClassDev& C = S.cls[ci];
         const DensePassClassDev& pc = S.pcd[ci];
-        const int cnt0 = class_count(C, S.dist + S.woff[ci], x0);
+        const int cnt0 = class_count(C, S.dist + S.woff[ci], nullptr, x0);   // layer 0's classes: no tables
         int Ak[4];
         split_deltas(C, pc, x0, Ak);
         const float2* tab = S.staged ? S.tab + S.toff[ci] : ptab + C.tab_off;
@@ -181,7 +191,19 @@ __device__ __forceinline__ uint32_t tile_step(const DensePassDev& p, int s) {
     return (!p.strided || s == 0) ? (1u << s) : (1u << (s - 4 + p.a));
 }
 
-__device__ __forceinline__ int class_count(const DenseClassDev& c, const int32_t* dist, uint32_t x) {
+// Count of class c at index x. An XOR class (kind 0 or 2) with a staged edge-word table
+// (c.ew >= 0) takes four table reads: number its terms e = 0..N-1 and let E_q be the word with
+// bit e set for every term that contains qubit q; bit e of the XOR of E_q over the qubits set in
+// x is then x_u ^ x_v for a pair term (u, v) and x_q for a single term, so the count is the
+// popcount of that XOR, and row k of the table holds the XORs over the 256 values of bits
+// 8k..8k+7. Otherwise, popcounts over the class's distance masks.
+__device__ __forceinline__ int class_count(const DenseClassDev& c, const int32_t* dist, const uint64_t* ew,
+                                           uint32_t x) {
+    if (c.ew >= 0) {
+        const uint64_t* T = ew + (size_t)c.ew * (4 * kEwRow);
+        return __popcll(T[ew_slot(x & 255u)] ^ T[kEwRow + ew_slot((x >> 8) & 255u)] ^
+                        T[2 * kEwRow + ew_slot((x >> 16) & 255u)] ^ T[3 * kEwRow + ew_slot(x >> 24)]);
+    }
     int cnt;
     if (c.kind == 1) {
         cnt = 0;
@@ -222,34 +244,72 @@ __device__ __forceinline__ void issue_tile(const DensePassDev& P, uint32_t t, co
 
 __device__ __forceinline__ void wait_tiles() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// The 32 per-qubit edge words E_q of XOR class C (see class_count), from its distance masks.
+__device__ void build_edge_words(const DenseClassDev& C, const int32_t* dists, uint64_t* E) {
+    for (int q = 0; q < 32; ++q) E[q] = 0;
+    int e = 0;
+    for (int k = 0; k < C.ndist; ++k) {
+        const int d = dists[2 * (C.dist_off + k)];
+        for (uint32_t m = (uint32_t)dists[2 * (C.dist_off + k) + 1]; m; m &= m - 1u) {
+            const int u = __ffs((int)m) - 1;   // pair (u, u + d)
+            const uint64_t bit = 1ull << e++;
+            E[u] ^= bit;
+            if (u + d < 32) E[u + d] ^= bit;
+        }
+    }
+    for (uint32_t m = C.single; m; m &= m - 1u) E[__ffs((int)m) - 1] ^= 1ull << e++;
+}
+
 // Stage a pass's classes (diagonal phases of the layers it completes, and the energy
-// classes in the final pass) with their distance words, phase tables and split counts.
+// classes in the final pass) with their distance words, phase tables and split counts, and
+// edge-word tables (s_ew, ew_bytes(n_ew)) for the first n_ew XOR classes of at most 64 terms.
 // Called by every thread of the CTA; ends with a barrier.
 template <int NT = kThreads>
 __device__ void stage_classes(const DensePassDev& P, const DenseClassDev* classes, const DensePassClassDev* pcd,
                               const int32_t* stage, const int32_t* dists, const float2* ptab, DenseClassDev* s_cls,
                               DensePassClassDev* s_pcd, int32_t* s_woff, int32_t* s_toff, int32_t* s_dist,
-                              float2* s_tab, int tid) {
+                              float2* s_tab, uint64_t* s_ew, int n_ew, int tid) {
     const int nst = P.nstage;
     if (tid < nst) s_cls[tid] = classes[stage[P.stage_off + tid]];
     __syncthreads();
     if (tid == 0) {
-        int woff = 0, toff = 0;
+        int woff = 0, toff = 0, slot = 0;
         for (int c = 0; c < nst; ++c) {
             s_woff[c] = woff;
             s_toff[c] = toff;
             woff += 2 * s_cls[c].ndist;
             toff += s_cls[c].kind == 0 ? s_cls[c].nterms + 1 : 0;
+            const bool tab = s_cls[c].kind != 1 && s_cls[c].nterms <= 64 && slot < n_ew;
+            s_cls[c].ew = tab ? slot++ : -1;
         }
     }
     for (int g = 0; g < P.ngroups; ++g)
         for (int k = tid; k < P.group_ncls[g]; k += NT) s_pcd[P.group_cls[g] + k] = pcd[P.group_pcd[g] + k];
     __syncthreads();
+    uint64_t* s_eq = s_ew + (size_t)n_ew * 4 * kEwRow;   // [n_ew][32] per-qubit words
+    if ((tid & 31) == 0 && (tid >> 5) < n_ew) {            // lane 0 of warp w: slot w (zero if unused)
+        const int slot = tid >> 5;
+        int c = 0;
+        while (c < nst && s_cls[c].ew != slot) ++c;
+        if (c < nst) build_edge_words(s_cls[c], dists, s_eq + 32 * slot);
+        else for (int q = 0; q < 32; ++q) s_eq[32 * slot + q] = 0;
+    }
     for (int c = 0; c < nst; ++c) {
         const DenseClassDev& C = s_cls[c];
         for (int w = tid; w < 2 * C.ndist; w += NT) s_dist[s_woff[c] + w] = dists[2 * C.dist_off + w];
         if (C.kind == 0)
             for (int e = tid; e <= C.nterms; e += NT) s_tab[s_toff[c] + e] = ptab[C.tab_off + e];
+    }
+    if (n_ew > 0) {
+        __syncthreads();
+        for (int i = tid; i < n_ew * 4 * 256; i += NT) {
+            const int slot = i >> 10, k = (i >> 8) & 3, b = i & 255;
+            const uint64_t* Eq = s_eq + 32 * slot + 8 * k;
+            uint64_t w = 0;
+            for (int t = 0; t < 8; ++t)
+                if ((b >> t) & 1) w ^= Eq[t];
+            s_ew[(size_t)slot * (4 * kEwRow) + k * kEwRow + ew_slot((uint32_t)b)] = w;
+        }
     }
     __syncthreads();
 }
@@ -301,7 +361,7 @@ __device__ __forceinline__ void group_epilogue(const PassArgs& A, const DensePas
                                                int base, int s, float2 (&v)[16], float& eacc, float& nacc,
                                                const DenseClassDev* s_cls, const DensePassClassDev* s_pcd,
                                                const int32_t* s_woff, const int32_t* s_toff, const int32_t* s_dist,
-                                               const float2* s_tab) {
+                                               const float2* s_tab, const uint64_t* s_ew) {
     // after this group: diagonal phases of a completed layer and/or the energy, from split
     // class counts; the last group then writes straight to HBM from registers
     const int ncls = P.group_ncls[g];
@@ -316,7 +376,7 @@ __device__ __forceinline__ void group_epilogue(const PassArgs& A, const DensePas
             const DensePassClassDev& pc = s_pcd[ci];
             const int woff = s_woff[ci], toff = s_toff[ci];
             any_energy |= C.kind == 2;
-            const int cnt0 = class_count(C, s_dist + woff, xb);
+            const int cnt0 = class_count(C, s_dist + woff, s_ew, xb);
             int Ak[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -370,10 +430,13 @@ __device__ __forceinline__ void group_epilogue(const PassArgs& A, const DensePas
 // straight to HBM.
 __host__ __device__ constexpr int dense_pass_bufs(bool single) { return single ? 1 : 2; }
 __host__ __device__ constexpr int dense_pass_ctas(bool single) { return single ? 3 : 2; }
-__host__ __device__ constexpr size_t dense_pass_smem_base(bool single) {
+// The generating pass keeps no edge-word tables (its layer 0 staging takes their room).
+__host__ __device__ constexpr int dense_pass_ew_tabs(bool gen) { return gen ? 0 : kEwTabs; }
+__host__ __device__ constexpr size_t dense_pass_smem_base(bool single, bool gen) {
     return ((dense_pass_bufs(single) * (size_t)padded_amps_c(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
              kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * (sizeof(DenseClassDev) + sizeof(DensePassClassDev)) +
-             2 * kMaxLayerClasses * sizeof(int32_t) + 16 * sizeof(float)) + 15) / 16 * 16;
+             2 * kMaxLayerClasses * sizeof(int32_t) + 16 * sizeof(float) + ew_bytes(dense_pass_ew_tabs(gen))) + 15) /
+           16 * 16;
 }
 
 // GEN: the first forward pass of a low tile whose first group starts at bit 0 -- its input is
@@ -389,10 +452,12 @@ __global__ void __launch_bounds__(kThreads, dense_pass_ctas(SINGLE)) dense_pass_
     int32_t* s_woff = reinterpret_cast<int32_t*>(s_pcd + kMaxLayerClasses);        // kMaxLayerClasses
     int32_t* s_toff = s_woff + kMaxLayerClasses;                                    // kMaxLayerClasses
     float* s_red = reinterpret_cast<float*>(s_toff + kMaxLayerClasses);              // 16
+    uint64_t* s_ew = reinterpret_cast<uint64_t*>(s_red + 16);                       // ew_bytes(n_ew)
+    constexpr int n_ew = dense_pass_ew_tabs(GEN);
     const DensePassDev& P = A.pass;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    InitStage* S = reinterpret_cast<InitStage*>(smem_raw + dense_pass_smem_base(SINGLE));   // GEN only
+    InitStage* S = reinterpret_cast<InitStage*>(smem_raw + dense_pass_smem_base(SINGLE, GEN));   // GEN only
     const uint32_t ntiles = 1u << (A.n_eff - kDenseTileBits);
 
     __shared__ int s_gkind[4 * kDenseMaxGroups];
@@ -400,7 +465,8 @@ __global__ void __launch_bounds__(kThreads, dense_pass_ctas(SINGLE)) dense_pass_
     if (!GEN && blockIdx.x < ntiles) issue_tile(P, blockIdx.x, A.state, bufs, tid);
 
     stage_group_gates(P, A.gates, A.GT, s_gkind, s_gcs, tid);   // visible after the barriers below
-    stage_classes(P, A.classes, A.pcd, A.stage, A.dists, A.ptab, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab, tid);
+    stage_classes(P, A.classes, A.pcd, A.stage, A.dists, A.ptab, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab, s_ew,
+                  n_ew, tid);
     if (GEN)
         stage_init(*S, A.n_eff, A.init, A.gates, A.GT, A.classes, A.init_class_off, A.init_nclass, A.init_pcd, A.dists,
                    A.ptab, tid, kThreads);
@@ -452,7 +518,8 @@ __global__ void __launch_bounds__(kThreads, dense_pass_ctas(SINGLE)) dense_pass_
                 float2 v[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = upk2(u[j]);
-                group_epilogue(A, P, g, t_id, base, s, v, eacc, eacc, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab);
+                group_epilogue(A, P, g, t_id, base, s, v, eacc, eacc, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab,
+                               s_ew);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) u[j] = pk2(v[j].x, v[j].y);
             }
@@ -481,14 +548,10 @@ __global__ void __launch_bounds__(kThreads, dense_pass_ctas(SINGLE)) dense_pass_
     }
 }
 
-size_t dense_pass_smem(bool single) {
-    return dense_pass_bufs(single) * (size_t)padded_amps(kDenseTileBits) * sizeof(float2) + kMaxTab * sizeof(float2) +
-           kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * (sizeof(DenseClassDev) + sizeof(DensePassClassDev)) +
-           2 * kMaxLayerClasses * sizeof(int32_t) + 16 * sizeof(float);
-}
+size_t dense_pass_smem(bool single) { return dense_pass_smem_base(single, false); }
 
 // The generating pass keeps layer 0's staging (InitStage) after the pass kernel's own data.
-size_t dense_pass_gen_smem(bool single) { return dense_pass_smem_base(single) + sizeof(InitStage); }
+size_t dense_pass_gen_smem(bool single) { return dense_pass_smem_base(single, true) + sizeof(InitStage); }
 
 // ---- tensor-core passes (mixed precision: split TF32 products, FP32 accumulation) ----------
 //
@@ -683,7 +746,7 @@ __global__ void __launch_bounds__(kTcPassThreads, 1) dense_tc_pass_kernel(const 
     build_tc_blocks(P, A.gates, A.GT, bblk, tid, kTcPassThreads);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B is read by the tensor core
     stage_classes<kTcPassThreads>(P, A.classes, A.pcd, A.stage, A.dists, A.ptab, s_cls, s_pcd, s_woff, s_toff,
-                                  s_dist, s_tab, tid);
+                                  s_dist, s_tab, nullptr, 0, tid);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -715,7 +778,8 @@ __global__ void __launch_bounds__(kTcPassThreads, 1) dense_tc_pass_kernel(const 
                 bad = true;
                 break;
             }
-            group_epilogue<true>(A, P, g, t_id, base, s, v, eacc, nacc, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab);
+            group_epilogue<true>(A, P, g, t_id, base, s, v, eacc, nacc, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab,
+                                 nullptr);
             if (g < P.ngroups - 1) {
                 store16(v, p, stride);
                 tc::bar_sync(bar_id, kThreads);
@@ -818,6 +882,7 @@ __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid
     DensePassClassDev* s_pcd = reinterpret_cast<DensePassClassDev*>(s_cls + kMaxLayerClasses);
     int32_t* s_woff = reinterpret_cast<int32_t*>(s_pcd + kMaxLayerClasses);
     int32_t* s_toff = s_woff + kMaxLayerClasses;
+    uint64_t* s_ew = reinterpret_cast<uint64_t*>(s_toff + kMaxLayerClasses);   // ew_bytes(kEwTabs)
     const DensePassDev& P = A.pass;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -831,7 +896,8 @@ __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid
     __shared__ int s_gkind[4 * kDenseMaxGroups];
     __shared__ float2 s_gcs[4 * kDenseMaxGroups];
     stage_group_gates(P, A.gates, A.GT, s_gkind, s_gcs, tid);   // visible after the barriers below
-    stage_classes(P, A.classes, A.pcd, A.stage, A.dists, A.ptab, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab, tid);
+    stage_classes(P, A.classes, A.pcd, A.stage, A.dists, A.ptab, s_cls, s_pcd, s_woff, s_toff, s_dist, s_tab, s_ew,
+                  kEwTabs, tid);
     double* acc = s_gacc + warp * kDenseAdjSlots;   // written by one lane of this warp per slot
 
     for (uint32_t t_id = blockIdx.x; t_id < ntiles; t_id += gridDim.x) {
@@ -860,7 +926,7 @@ __global__ void __launch_bounds__(kThreads, 2) dense_adjoint_kernel(const __grid
                     const DenseClassDev& C = s_cls[ci];
                     if (C.kind == 2) continue;   // energy classes: nothing to undo
                     const DensePassClassDev& pc = s_pcd[ci];
-                    const int cnt0 = class_count(C, s_dist + s_woff[ci], xb);
+                    const int cnt0 = class_count(C, s_dist + s_woff[ci], s_ew, xb);
                     int Ak[4];
                     split_deltas(C, pc, xb, Ak);
                     if (C.kind == 0) {
@@ -938,7 +1004,7 @@ size_t dense_adjoint_smem() {
     return 2 * (size_t)padded_amps(kDenseTileBits) * sizeof(float2) +
            (size_t)(kThreads / 32) * kDenseAdjSlots * sizeof(double) + kMaxTab * sizeof(float2) +
            kMaxDistWords * sizeof(int32_t) + kMaxLayerClasses * (sizeof(DenseClassDev) + sizeof(DensePassClassDev)) +
-           2 * kMaxLayerClasses * sizeof(int32_t);
+           2 * kMaxLayerClasses * sizeof(int32_t) + ew_bytes(kEwTabs);
 }
 
 // lam (+)= sum_t c_t P_t psi over Pauli strings given by (flip, zy, ny):

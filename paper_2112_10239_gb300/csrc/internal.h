@@ -144,7 +144,7 @@ struct DenseClassDev {
     int32_t dist_off;         // (d, mask) pairs in the distance array
     int32_t tab_off;
     uint32_t single;
-    int32_t pad;
+    int32_t ew;               // a pass's staged copy: its edge-word table in shared memory (-1: none)
     double coeff;
 };
 struct DenseLayerDev { int32_t nclass, class_off, pad0, pad1; };

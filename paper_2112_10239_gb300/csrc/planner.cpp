@@ -565,6 +565,7 @@ void emit_class(DensePlan& D, const ClassBuild& cb) {
     c.single = cb.single;
     c.coeff = cb.coeff;
     c.tab_off = -1;
+    c.ew = -1;
     if (cb.kind == 0) {
         c.tab_off = (int32_t)D.tab_gate.size();
         for (int k = 0; k <= cb.nterms; ++k) {

@@ -206,6 +206,43 @@ def test_nonlocal_mixed_gradients(tlq, seed):
     check_grad(g, gr)
 
 
+@pytest.mark.parametrize("n", [14, 19])
+def test_diagonal_class_count_forms(tlq, n):
+    # Diagonal classes counted both ways in one circuit: classes of at most 64 terms read
+    # edge-word tables (the first two per pass), larger ones and the rest loop over distances.
+    # RZZ on every pair with one angle (> 64 terms), RZZ on the pairs of the first 11 qubits plus
+    # RZ on qubits 0..4 with another (60 terms), three lone RZZ angles and a CZ in the same
+    # layer; energy from ZZ on every pair (> 64 terms) plus a small ZZ / Z class and X terms.
+    rng = np.random.default_rng(90 + n)
+    pairs = [(u, v) for u in range(n) for v in range(u + 1, n)]
+    small = [(u, v) for u in range(11) for v in range(u + 1, 11)]
+    gates, P = [], 0
+    for layer in range(2):
+        for q in range(n):
+            gates.append((W.RY if (q + layer) % 3 else W.RX, q, -1, P + q, 0.0))
+        P += n
+        gates += [(W.RZZ, u, v, P, 0.0) for u, v in pairs]
+        gates += [(W.RZZ, u, v, P + 1, 0.0) for u, v in small] + [(W.RZ, q, -1, P + 1, 0.0) for q in range(5)]
+        for k in range(3):
+            gates.append((W.RZZ, k, n - 1 - k, P + 2 + k, 0.0))
+        gates.append((W.CZ, 1, n - 2, -1, 0.0))
+        P += 5
+    for q in range(n):
+        gates.append((W.RX, q, -1, P, 0.0))
+    P += 1
+    terms = [(1.0, (u, v), "ZZ") for u, v in pairs]
+    terms += [(0.5, (u, u + 3), "ZZ") for u in range(6)] + [(0.5, (q,), "Z") for q in range(4)]
+    terms += [(0.25, (q,), "X") for q in range(0, n, 3)]
+    theta = rng.uniform(0, 2 * math.pi, size=(2, P))
+    prob = W.Problem(n=n, gates=gates, n_params=P, terms=terms, theta=theta)
+    E, g = _grad(tlq, prob)
+    Er, gr = _oracle_grad(prob, theta)
+    check_energy(E, Er)
+    check_grad(g, gr)
+    E2, _ = _energy(tlq, prob)
+    check_energy(E2, Er)
+
+
 @pytest.mark.parametrize("n", [1, 2, 3])
 def test_tiny_dense_gradient(tlq, n):
     gates = [(W.RY, q, -1, q, 0.0) for q in range(n)] + [(W.RX, q, -1, n + q, 0.0) for q in range(n)]
