@@ -55,8 +55,15 @@ __device__ __forceinline__ int ew_slot(uint32_t b) { return (int)(b + (b >> 4));
 // f_q(1) = sin(a_q/2) (RY) or -i sin(a_q/2) (RX), 1 and 0 for a qubit without a rotation; then
 // layer 0's diagonal classes (phase exp(-i a/2 (N - 2c)) from the phase table, or the CZ sign
 // (-1)^c). Sixteen consecutive amplitudes are built at once: the product over bits 4.. once,
-// the low four bits by doubling, the classes by split counts over bits 0..3.
+// the low four bits by doubling, the classes by split counts over bits 0..3. The product over
+// bits 4.. is four rows of per-chunk products (bits 4..11, 12..19, 20..27, 28..30), and one XOR
+// class of at most 64 terms takes its count at the base index from the rows' edge-parity words
+// (see class_count): both are linear over the chunks.
 struct InitGates { int32_t gate[32]; };
+struct InitRow {
+    float2 f;      // product of the chunk's factors f_q(x_q)
+    uint64_t w;    // edge-parity word of the chunk's bits for class InitStage::ewc
+};
 
 __device__ __forceinline__ float2 init_factor(const InitGates& I, const tlq_gate* gates, const float2* GT, int q,
                                               int bit) {
@@ -76,9 +83,29 @@ struct InitStage {
     int32_t woff[kMaxLayerClasses];
     int32_t toff[kMaxLayerClasses];
     float2 tab[kMaxTab];
+    InitRow thr[256];     // bits 4..11: a thread's base in the generating register group
+    InitRow hi[2][256];   // bits 12..19 and 20..27
+    InitRow top[8];       // bits 28..30
     int nc;
     int staged;   // the phase tables fit: read from shared memory, else from global memory
+    int ewc;      // the class counted from the rows' words (-1: none)
 };
+
+// Bit e of the result: term e of XOR class C (pairs in distance-mask order, then singles) is
+// odd at index x. Linear over GF(2) in x, so the words of disjoint bit chunks XOR together.
+__device__ uint64_t edge_parity(const DenseClassDev& C, const int32_t* dist, uint32_t x) {
+    uint64_t w = 0;
+    int e = 0;
+    for (int k = 0; k < C.ndist; ++k) {
+        const uint32_t M = (uint32_t)dist[2 * k + 1];
+        const uint32_t odd = (x ^ (x >> dist[2 * k])) & M;
+        for (uint32_t m = M; m; m &= m - 1u, ++e)
+            if (odd & m & (0u - m)) w |= 1ull << e;
+    }
+    for (uint32_t m = C.single; m; m &= m - 1u, ++e)
+        if (x & m & (0u - m)) w |= 1ull << e;
+    return w;
+}
 
 // Stage the factors and layer 0's classes (every thread of the block calls this; ends with a
 // barrier).
@@ -96,15 +123,17 @@ __device__ void stage_init(InitStage& S, int n_eff, const InitGates& I, const tl
     }
     __syncthreads();
     if (tid == 0) {
-        int w = 0, t = 0;
+        int w = 0, t = 0, ewc = -1;
         for (int c = 0; c < nc; ++c) {
             S.woff[c] = w;
             w += 2 * S.cls[c].ndist;
             S.toff[c] = t;
             t += S.cls[c].kind == 0 ? S.cls[c].nterms + 1 : 0;
+            if (ewc < 0 && S.cls[c].kind != 1 && S.cls[c].nterms <= 64 && w <= kMaxDistWords) ewc = c;
         }
         S.staged = t <= kMaxTab;
         S.nc = nc;
+        S.ewc = ewc;
     }
     __syncthreads();
     for (int c = 0; c < nc; ++c) {
@@ -112,6 +141,19 @@ __device__ void stage_init(InitStage& S, int n_eff, const InitGates& I, const tl
             if (S.woff[c] + k < kMaxDistWords) S.dist[S.woff[c] + k] = dists[2 * S.cls[c].dist_off + k];
         if (S.staged && S.cls[c].kind == 0)
             for (int e = tid; e <= S.cls[c].nterms; e += nthreads) S.tab[S.toff[c] + e] = ptab[S.cls[c].tab_off + e];
+    }
+    __syncthreads();
+    // chunk rows: thr (bits 4..11), hi[0] (12..19), hi[1] (20..27), top (28..30)
+    for (int e = tid; e < 3 * 256 + 8; e += nthreads) {
+        const int chunk = e >> 8;   // 3: top
+        const uint32_t b = (uint32_t)(e & 255);
+        const int lo = 4 + 8 * chunk, nb = chunk < 3 ? 8 : 3;
+        float2 f = make_float2(1.f, 0.f);
+        for (int i = 0; i < nb; ++i) f = cmul(f, S.f[lo + i][(b >> i) & 1u]);
+        const uint64_t w = S.ewc >= 0 ? edge_parity(S.cls[S.ewc], S.dist + S.woff[S.ewc], b << lo) : 0ull;
+        InitRow& r = chunk == 0 ? S.thr[b] : chunk < 3 ? S.hi[chunk - 1][b] : S.top[b];
+        r.f = f;
+        r.w = w;
     }
     __syncthreads();
 }
@@ -123,9 +165,13 @@ __device__ __forceinline__ void split_deltas(const DenseClassDev& C, const Dense
 __device__ __forceinline__ int split_count(const DensePassClassDev& pc, int cnt0, const int (&Ak)[4], int j);
 
 // The 16 amplitudes x0 | j (x0 a multiple of 16) of the state after layer 0.
-__device__ __forceinline__ void gen16(const InitStage& S, int n_eff, const float2* ptab, uint32_t x0, float2 (&v)[16]) {
-    v[0] = make_float2(1.f, 0.f);
-    for (int q = 4; q < n_eff; ++q) v[0] = cmul(v[0], S.f[q][(x0 >> q) & 1]);
+__device__ __forceinline__ void gen16(const InitStage& S, const float2* ptab, uint32_t x0, float2 (&v)[16]) {
+    const InitRow& r0 = S.thr[(x0 >> 4) & 255u];
+    const InitRow& r1 = S.hi[0][(x0 >> 12) & 255u];
+    const InitRow& r2 = S.hi[1][(x0 >> 20) & 255u];
+    const InitRow& r3 = S.top[(x0 >> 28) & 7u];
+    v[0] = cmul(cmul(r0.f, r1.f), cmul(r2.f, r3.f));
+    const uint64_t W = r0.w ^ r1.w ^ r2.w ^ r3.w;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const float2 f0 = S.f[k][0], f1 = S.f[k][1];
@@ -138,7 +184,7 @@ __device__ __forceinline__ void gen16(const InitStage& S, int n_eff, const float
     for (int ci = 0; ci < S.nc; ++ci) {
         const DenseClassDev& C = S.cls[ci];
         const DensePassClassDev& pc = S.pcd[ci];
-        const int cnt0 = class_count(C, S.dist + S.woff[ci], nullptr, x0);   // layer 0's classes: no tables
+        const int cnt0 = ci == S.ewc ? __popcll(W) : class_count(C, S.dist + S.woff[ci], nullptr, x0);
         int Ak[4];
         split_deltas(C, pc, x0, Ak);
         const float2* tab = S.staged ? S.tab + S.toff[ci] : ptab + C.tab_off;
@@ -499,7 +545,7 @@ __global__ void __launch_bounds__(kThreads, dense_pass_ctas(SINGLE)) dense_pass_
             pk64 u[16];   // the 16 amplitudes as packed (re, im) registers
             if (GEN && g == 0) {   // s == 0
                 float2 v[16];
-                gen16(*S, A.n_eff, A.ptab, tile_x(P, t_id, (uint32_t)base), v);
+                gen16(*S, A.ptab, tile_x(P, t_id, (uint32_t)base), v);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) u[j] = pk2(v[j].x, v[j].y);
             } else {
@@ -1253,7 +1299,7 @@ __global__ void __launch_bounds__(256) dense_product_init_kernel(float2* psi, in
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nblk; t += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t x0 = (uint32_t)(t << 4);
         float2 v[16];
-        gen16(S, n_eff, ptab, x0, v);
+        gen16(S, ptab, x0, v);
         float4* out = reinterpret_cast<float4*>(psi + x0);
 #pragma unroll
         for (int i = 0; i < 8; ++i) out[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
