@@ -168,8 +168,8 @@ tlq_status tlq_expectation_grad_dev(tlq_ctx ctx, tlq_circuit c, tlq_ham h, const
  * work list, gate tables, per-term partials, gradient slots, counters) comes from one
  * 16 MiB array compiled into the library, which every GPU that loads the library holds
  * until the process exits; no cudaMalloc/cudaFree or other allocating routine is called.
- * The first call on a device looks up that array's device address (cudaGetSymbolAddress),
- * so make the first call on each device before any stream capture. Calls share the array:
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress).
+ * Calls share the array:
  * calls whose work overlaps on the GPU race and must be serialised by the caller (for
  * example by enqueueing them on one stream: each call enqueues its copies and launches as
  * one unit, so calls made from several threads onto one stream do not interleave). Plans and work lists are cached on the host
