@@ -21,6 +21,12 @@
 //                           psi and lambda = P psi, emitting Im<lambda|G|psi> per gate.
 //   reduce_kernel      (K5) energies and gradients in one launch: fixed-order Neumaier sums in FP64, so a
 //                           result does not depend on batching or scheduling.
+//
+// The global-memory tier's kernels (cone_kernel<real, GRAD, true>) are compiled in their own
+// translation unit, cone_global.cu, which includes this file with TLQ_CONE_GLOBAL_TU defined
+// and emits only launch_cone_global and launch_batch_global: the two tiers then take
+// different ptxas optimisation levels (the build gives this file -O1, under which the
+// shared-memory tier measured faster, and cone_global.cu the default -O3).
 #include "internal.h"
 
 #include <cuda_runtime.h>
@@ -1338,6 +1344,7 @@ __device__ __forceinline__ double grad_slots(const double* g, const int32_t* idx
     return acc.value();
 }
 
+#ifndef TLQ_CONE_GLOBAL_TU
 // Energies and gradients of a launch in one kernel: blocks [0, eb) hold one warp per set for
 // the energies, the others one thread per (set, parameter) for the gradients (P = 0: none).
 __global__ void reduce_kernel(const double* e_part, const double* coeff, int T, int B, double* energy, int eb,
@@ -1353,8 +1360,16 @@ __global__ void reduce_kernel(const double* e_part, const double* coeff, int T, 
     const int b = (int)(i / P), p = (int)(i % P);
     grad[i] = grad_slots(g_part + (size_t)b * S, idx, term, coeff, off[p], off[p + 1]);
 }
+#endif
 
 // ---- launchers -----------------------------------------------------------------------------
+
+// The global-memory tier's launches (defined in the cone_global.cu translation unit).
+int launch_cone_global(const ConeLaunch& L, cudaStream_t st, int begin, int end, int smem, int grid,
+                       int32_t* counter, bool fp64, bool grad);
+struct BatchLaunch;
+int launch_batch_global(const BatchLaunch& L, cudaStream_t st, int begin, int end, int smem, int grid,
+                        int32_t* counter, bool fp64, bool grad);
 
 template <typename real, bool GRAD, bool GLOBAL>
 static int launch_cone_t(const ConeLaunch& L, cudaStream_t st, int begin, int end, int smem, int grid,
@@ -1389,6 +1404,16 @@ static int launch_cone_t(const ConeLaunch& L, cudaStream_t st, int begin, int en
     return (int)cudaGetLastError();
 }
 
+#ifdef TLQ_CONE_GLOBAL_TU
+int launch_cone_global(const ConeLaunch& L, cudaStream_t st, int begin, int end, int smem, int grid,
+                       int32_t* counter, bool fp64, bool grad) {
+    if (fp64)
+        return grad ? launch_cone_t<double, true, true>(L, st, begin, end, smem, grid, counter, kGlobalCtaThreads)
+                    : launch_cone_t<double, false, true>(L, st, begin, end, smem, grid, counter, kGlobalCtaThreads);
+    return grad ? launch_cone_t<float, true, true>(L, st, begin, end, smem, grid, counter, kGlobalCtaThreads)
+                : launch_cone_t<float, false, true>(L, st, begin, end, smem, grid, counter, kGlobalCtaThreads);
+}
+#else
 int cone_smem_grid(bool fp64, bool grad, int smem_bytes, int sm_count, int threads) {
     int per_sm = 0;
     cudaError_t e;
@@ -1433,16 +1458,12 @@ int launch_cone(ConeLaunch& L, void* stream) {
     if (L.fp64) {
         rc = grad ? launch_cone_t<double, true, false>(L, st, 0, L.n_chunks_smem, L.smem_bytes, smem_grid, L.counters, L.smem_threads)
                   : launch_cone_t<double, false, false>(L, st, 0, L.n_chunks_smem, L.smem_bytes, smem_grid, L.counters, L.smem_threads);
-        if (rc) return rc;
-        rc = grad ? launch_cone_t<double, true, true>(L, st, L.n_chunks_smem, L.n_chunks, L.gsmem_bytes, L.g_grid, L.counters + 1, kGlobalCtaThreads)
-                  : launch_cone_t<double, false, true>(L, st, L.n_chunks_smem, L.n_chunks, L.gsmem_bytes, L.g_grid, L.counters + 1, kGlobalCtaThreads);
     } else {
         rc = grad ? launch_cone_t<float, true, false>(L, st, 0, L.n_chunks_smem, L.smem_bytes, smem_grid, L.counters, L.smem_threads)
                   : launch_cone_t<float, false, false>(L, st, 0, L.n_chunks_smem, L.smem_bytes, smem_grid, L.counters, L.smem_threads);
-        if (rc) return rc;
-        rc = grad ? launch_cone_t<float, true, true>(L, st, L.n_chunks_smem, L.n_chunks, L.gsmem_bytes, L.g_grid, L.counters + 1, kGlobalCtaThreads)
-                  : launch_cone_t<float, false, true>(L, st, L.n_chunks_smem, L.n_chunks, L.gsmem_bytes, L.g_grid, L.counters + 1, kGlobalCtaThreads);
     }
+    if (rc) return rc;
+    rc = launch_cone_global(L, st, L.n_chunks_smem, L.n_chunks, L.gsmem_bytes, L.g_grid, L.counters + 1, L.fp64, grad);
     if (rc) return rc;
     if (L.ev_end && (e = cudaEventRecord((cudaEvent_t)L.ev_end, st)) != cudaSuccess) return (int)e;
     {
@@ -1458,6 +1479,7 @@ int launch_cone(ConeLaunch& L, void* stream) {
     }
     return 0;
 }
+#endif
 
 // ---- serving batches: per-set records --------------------------------------------------------
 
@@ -1488,6 +1510,7 @@ __global__ void batch_gate_table_kernel(const SetRec* sets, typename R2<real>::T
 // reduce_kernel, so a set's results are bit-identical served or computed synchronously:
 // blocks [0, eb) hold one warp per set, the others cover (set, parameter) pairs, gx blocks of
 // 256 parameters per set.
+#ifndef TLQ_CONE_GLOBAL_TU
 __global__ void batch_reduce_kernel(const SetRec* sets, int n_sets, const double* e_part, const double* g_part,
                                     int eb, int gx) {
     if ((int)blockIdx.x < eb) {
@@ -1505,6 +1528,7 @@ __global__ void batch_reduce_kernel(const SetRec* sets, int n_sets, const double
     if (!R.grad || p >= R.n_params) return;
     R.grad[p] = grad_slots(g_part + R.g_off, R.pmap_idx, R.pmap_term, R.term_coeff, R.pmap_off[p], R.pmap_off[p + 1]);
 }
+#endif
 
 template <typename real, bool GRAD, bool GLOBAL>
 static int launch_batch_t(const BatchLaunch& L, cudaStream_t st, int begin, int end, int smem, int grid,
@@ -1533,6 +1557,16 @@ static int launch_batch_t(const BatchLaunch& L, cudaStream_t st, int begin, int 
     return (int)cudaGetLastError();
 }
 
+#ifdef TLQ_CONE_GLOBAL_TU
+int launch_batch_global(const BatchLaunch& L, cudaStream_t st, int begin, int end, int smem, int grid,
+                        int32_t* counter, bool fp64, bool grad) {
+    if (fp64)
+        return grad ? launch_batch_t<double, true, true>(L, st, begin, end, smem, grid, counter, kGlobalCtaThreads)
+                    : launch_batch_t<double, false, true>(L, st, begin, end, smem, grid, counter, kGlobalCtaThreads);
+    return grad ? launch_batch_t<float, true, true>(L, st, begin, end, smem, grid, counter, kGlobalCtaThreads)
+                : launch_batch_t<float, false, true>(L, st, begin, end, smem, grid, counter, kGlobalCtaThreads);
+}
+#else
 template <typename real>
 static int launch_batch_all(BatchLaunch& L, cudaStream_t st) {
     int rc;
@@ -1543,14 +1577,14 @@ static int launch_batch_all(BatchLaunch& L, cudaStream_t st) {
     if ((rc = launch_batch_t<real, false, false>(L, st, L.range[0], L.range[1], L.smem_bytes[0], g0, L.counters + 0,
                                                  L.smem_threads[0])))
         return rc;
-    if ((rc = launch_batch_t<real, false, true>(L, st, L.range[1], L.range[2], L.gsmem_bytes[0], L.g_grid, L.counters + 1,
-                                                kGlobalCtaThreads)))
+    if ((rc = launch_batch_global(L, st, L.range[1], L.range[2], L.gsmem_bytes[0], L.g_grid, L.counters + 1,
+                                  sizeof(real) == 8, false)))
         return rc;
     if ((rc = launch_batch_t<real, true, false>(L, st, L.range[2], L.range[3], L.smem_bytes[1], g1, L.counters + 2,
                                                 L.smem_threads[1])))
         return rc;
-    if ((rc = launch_batch_t<real, true, true>(L, st, L.range[3], L.range[4], L.gsmem_bytes[1], L.g_grid, L.counters + 3,
-                                               kGlobalCtaThreads)))
+    if ((rc = launch_batch_global(L, st, L.range[3], L.range[4], L.gsmem_bytes[1], L.g_grid, L.counters + 3,
+                                  sizeof(real) == 8, true)))
         return rc;
     for (int k = 0; k < 4; ++k) L.launches += L.range[k + 1] > L.range[k];
     return 0;
@@ -1582,5 +1616,6 @@ int launch_cone_batch(BatchLaunch& L, void* stream) {
     L.launches += 2;
     return 0;
 }
+#endif
 
 }  // namespace tlq
