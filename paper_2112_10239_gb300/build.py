@@ -24,10 +24,13 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
 SOURCES = ["cone.cu", "cone_global.cu", "dense.cu", "density.cu", "tiny.cu", "mps.cu", "noalloc.cu", "api.cpp",
            "planner.cpp", "serving.cpp"]
 HEADERS = ["internal.h", "runtime.h", "gates.cuh", "tc.cuh"]
-# Per-source flags: the cone kernel's shared-memory tier (cone.cu) at ptxas -O1, measured
-# faster there than -O3 (the n=500 batch 4.01 -> 3.90 ms, the n=20 batch level); its
-# global-memory tier (cone_global.cu, which includes cone.cu) keeps -O3, where -O1 was slower.
-SOURCE_FLAGS = {"cone.cu": ["-Xptxas", "-O1"]}
+# Per-source flags, each measured against ptxas -O3 on the same GPU: the cone kernel's
+# shared-memory tier (cone.cu) at -O1 (the n=500 batch 4.01 -> 3.90 ms, the n=20 batch
+# level), its global-memory tier (cone_global.cu, which includes cone.cu) at -O3 (-O1 was
+# 10 % slower there), the dense passes (dense.cu) at -O1 (n=28 energy 0.569 -> 0.579 of
+# HBM, energy + gradient 0.585 -> 0.605) and the MPS route (mps.cu) at -O1 (the n=20 batch
+# 30.4 -> 27.7 ms, n=500 level). The partial trace (density.cu) stays at -O3 (-O1: 1 % slower).
+SOURCE_FLAGS = {"cone.cu": ["-Xptxas", "-O1"], "dense.cu": ["-Xptxas", "-O1"], "mps.cu": ["-Xptxas", "-O1"]}
 SOURCE_DEPS = {"cone_global.cu": ["cone.cu"]}
 
 
