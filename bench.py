@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 256 << 20
 # without an entry report null; an entry is removed when its kernel changes after the capture.
 NCU_TRAFFIC = {
     ("tfim_n20_L6_B64", "cone_kernel"): 856576.0 + 0.0,
-    ("tfim_n500_L4_B256", "cone_kernel"): 10280192.0 + 915968.0,
+    ("tfim_n500_L4_B256", "cone_kernel"): 10280960.0 + 18432.0,
     ("tfim_n400_L8_B1", "cone_kernel"): 12117756928.0 + 14537556224.0,
     ("partial_trace_n20_m13", "herk_ws_kernel"): 8826624.0 + 475120128.0,
 }
